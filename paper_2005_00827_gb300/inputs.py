@@ -1,0 +1,91 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle.
+
+This module holds none of the method's arithmetic: it draws random numbers,
+permutes patch indices by the C4v symmetry of the angular patching, and
+names the workloads.  The paper (arXiv:2005.00827) uses no dataset: its runs
+are parameter scans of the half-filled square-lattice Hubbard model (t = 1,
+t' = 0, mu = 0; Sec. 3) on patch discretisations of 16-728 patches (Sec. 3.2).
+The workloads below reproduce those shapes with seeded draws.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+MASK64 = (1 << 64) - 1
+
+
+def splitmix64(seed: int):
+    """Counter-based generator (Steele, Lea, Flood 2014): yields uniform
+    floats in [0, 1) with 53 random bits."""
+    state = seed & MASK64
+    while True:
+        state = (state + 0x9E3779B97F4A7C15) & MASK64
+        z = state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+        z ^= z >> 31
+        yield (z >> 11) * (1.0 / (1 << 53))
+
+
+def c4v_patch_maps(N: int):
+    """The 8 index permutations of the wedge patches under C4v (patch centres
+    at 2 pi j / N, N a multiple of 4): j -> +-j + m N/4 (mod N)."""
+    if N % 4:
+        raise ValueError("C4v needs N % 4 == 0")
+    j = np.arange(N)
+    maps = []
+    for m in range(4):
+        maps.append((j + m * N // 4) % N)
+        maps.append((-j + m * N // 4) % N)
+    return maps
+
+
+def c4v_symmetrise(V: np.ndarray) -> np.ndarray:
+    """Average a coupling array V[k1,k2,k3] over the C4v patch permutations."""
+    N = V.shape[0]
+    out = np.zeros_like(V)
+    for g in c4v_patch_maps(N):
+        out += V[np.ix_(g, g, g)]
+    return out / 8.0
+
+
+def random_vertex(N: int, U: float, seed: int = 1, amp: float = 0.5, c4v: bool = True) -> np.ndarray:
+    """V = U + amp U s with s uniform in [-1, 1] (splitmix64), FP64, [k1][k2][k3]."""
+    gen = splitmix64(seed)
+    s = np.fromiter((2.0 * next(gen) - 1.0 for _ in range(N ** 3)), dtype=np.float64, count=N ** 3)
+    V = (U + amp * U * s).reshape(N, N, N)
+    return c4v_symmetrise(V) if c4v else V
+
+
+def z_profile(N: int, kind: str = "one") -> np.ndarray:
+    """Quasi-particle weights per patch: 'one' (Z = 1) or 'aniso'
+    (Z_j = 0.9 + 0.05 cos(4 theta_j), theta_j = 2 pi j / N, C4v symmetric)."""
+    if kind == "one":
+        return np.ones(N)
+    th = 2 * np.pi * np.arange(N) / N
+    return 0.9 + 0.05 * np.cos(4 * th)
+
+
+def batch_specs(count: int = 128, seed: int = 20050082):
+    """Phase-boundary sweep: for i = 0..count-1 in order, U = 1 + 3u,
+    T_end = exp(ln 0.01 + u ln 20), N_p = {24,48,72,96}[floor(4u)] (one u each)."""
+    gen = splitmix64(seed)
+    specs = []
+    for _ in range(count):
+        U = 1.0 + 3.0 * next(gen)
+        T_end = math.exp(math.log(0.01) + next(gen) * math.log(20.0))
+        Np = (24, 48, 72, 96)[min(3, int(4 * next(gen)))]
+        specs.append(dict(U=U, T_end=T_end, N=Np))
+    return specs
+
+
+# Workloads shaped like the paper's runs (t = 1, t' = 0, mu = 0; T-flow from
+# T = 1 with d ln T = ln 0.98, stop at max|V| > 20).
+WORKLOADS = {
+    "np16_n8": dict(N=16, n=8, U=2.0, T_end=0.05, z_feedback=False, n_omega=0),
+    "np48_n16": dict(N=48, n=16, U=3.0, T_end=0.05, z_feedback=True, n_omega=512),
+    "np96_n32": dict(N=96, n=32, U=2.5, T_end=0.02, z_feedback=True, n_omega=1024),
+    "np192_n32": dict(N=192, n=32, U=2.0, T_end=0.01, z_feedback=True, n_omega=2048),
+}
