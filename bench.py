@@ -1,0 +1,300 @@
+#!/usr/bin/env python3
+"""Benchmark of the quasi-particle fRG hot path on GB300.
+
+One step = one flow step of the N_p = 96, 32 x 32 fine-grid workload
+(t = 1, t' = 0, mu = 0, U = 2.5, temperature flow from T = 1 with
+d ln T = ln 0.98, Z feedback): the two-loop self-energy at xi_j +- 2T and the
+Z update, four right-hand-side evaluations (loop kernels + contraction of all
+N^3 couplings) and the RK4 combine with the divergence check.  The headline
+value is RHS evaluations per second over the timed steps (4 per step, the
+self-energy included in the time).  Inputs: synthetic lattice parameters,
+no dataset.  All device inputs (partner maps, bubble tables) exceed L2.
+
+--impl reference times the FP64 CPU oracle on the host cores (a bounded
+sample of output triples per step) for the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "np96_n32"
+METRIC = "fRG RHS evaluations/s (N_p=96 flow steps with Z feedback, mixed precision)"
+UNIT = "RHS/s"
+
+# Algorithmic work per loop-kernel evaluation and per self-energy pair (FP32
+# instructions and MUFU operations of the minimal formula; see the design notes).
+BUBBLE_FP32_PER_EVAL, BUBBLE_MUFU_PER_EVAL = 19, 2
+SIGMA_FP32_PER_PAIR, SIGMA_MUFU_PER_PAIR = 48, 4
+FP32_LANES_PER_SM, MUFU_PER_SM, N_SM = 128, 16, 152
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.rows = []
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if "Active" in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+# ---------------------------------------------------------------------------
+def run_qpfrg(args):
+    import numpy as np
+    import torch
+
+    from paper_2005_00827_gb300 import api, inputs
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    wl = inputs.WORKLOADS[args.workload]
+    N, n, U = wl["N"], wl["n"], wl["U"]
+    prec = api.QPFRG_MIXED if args.precision == "mixed" else api.QPFRG_FP64
+    stream = torch.cuda.current_stream()
+    ctx = api.Context(N, n, n, U=U, lambda0=1.0, precision=prec, lambda_end=wl["T_end"],
+                      z_feedback=int(wl["z_feedback"]), eta=0.02, stream=stream.cuda_stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        api.qpfrg_step(ctx.h, 1)
+    barrier()
+    api.qpfrg_set_profiling(ctx.h, True)
+    api.qpfrg_profile_reset(ctx.h)
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    steps_done = 0
+    for _ in range(args.steps):
+        r = api.qpfrg_step(ctx.h, 1)
+        steps_done += 1
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    prof = api.qpfrg_profile(ctx.h)
+    api.qpfrg_set_profiling(ctx.h, False)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = 4.0 * steps_done * world / (ms / 1e3)
+
+    # end to end: state uploaded from pinned host memory, one step, state read back
+    nbytes = api.qpfrg_state_size(ctx.h)
+    img = api.qpfrg_get_state(ctx.h)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        api.qpfrg_set_state(ctx.h, img)
+        api.qpfrg_step(ctx.h, 1)
+        img = api.qpfrg_get_state(ctx.h)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": 4.0 * args.steps * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes}
+
+    # right-hand side alone, mixed and FP64 forms (same inputs)
+    extra = {}
+    V = inputs.random_vertex(N, U, seed=1)
+    Z = inputs.z_profile(N, "aniso")
+    dV_t = torch.from_numpy(V.ravel()).cuda()
+    Z_t = torch.from_numpy(Z).cuda()
+    out = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+    for name, pr, reps in (("mixed", api.QPFRG_MIXED, 10), ("fp64", api.QPFRG_FP64, 3)):
+        with api.Context(N, n, n, U=U, precision=pr, stream=stream.cuda_stream) as c2:
+            api.qpfrg_rhs(c2.h, 0.1, dV_t, Z_t, out)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                api.qpfrg_rhs(c2.h, 0.1, dV_t, Z_t, out)
+            b.record(stream)
+            torch.cuda.synchronize()
+            extra[f"rhs_only_{name}_per_s"] = reps / (a.elapsed_time(b) / 1e3)
+    extra["mixed_vs_fp64_rhs"] = extra["rhs_only_mixed_per_s"] / extra["rhs_only_fp64_per_s"]
+
+    # roofline of the dominant kernel (ALU bound: FP32 issue and MUFU pipes)
+    peaks, peak_kind = load_peaks()
+    clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    kern = {k: v for k, v in prof.items() if v[1] > 0}
+    dom = max(kern, key=lambda k: kern[k][0])
+    M = N * n * n
+    roof = None
+    if dom in ("bubble", "sigma_z"):
+        if dom == "bubble":
+            units = 2.0 * N * N * M
+            fp32, mufu = BUBBLE_FP32_PER_EVAL, BUBBLE_MUFU_PER_EVAL
+        else:
+            units = float(N) * M * M
+            fp32, mufu = SIGMA_FP32_PER_PAIR, SIGMA_MUFU_PER_PAIR
+        clk_per_unit = max(fp32 / FP32_LANES_PER_SM, mufu / MUFU_PER_SM)
+        peak_units = N_SM * clk_mhz * 1e6 / clk_per_unit
+        avg_s = kern[dom][0] / kern[dom][1] / 1e3
+        achieved = units / avg_s
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e9, "peak": peak_units / 1e9,
+                "unit": "Geval/s" if dom == "bubble" else "Gpair/s", "frac": achieved / peak_units,
+                "traffic": None, "peak_source": f"derived: {N_SM} SM x {clk_mhz:.0f} MHz "
+                f"({peak_kind} max clock), {fp32} FP32 instr / {FP32_LANES_PER_SM} lanes, "
+                f"{mufu} MUFU / {MUFU_PER_SM} per SM"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == api.QPFRG_MIXED else "f64",
+        "data": "synthetic (seeded lattice parameters; no dataset in the paper)",
+        "config": {"workload": args.workload, "N_p": N, "fine_grid": f"{n}x{n}", "U": U,
+                   "flow": "T-flow from T=1, dlnT=ln0.98, Z feedback, eta=0.02",
+                   "precision": args.precision, "l2": "inputs larger than L2 (partner maps "
+                   f"{2 * N * N * M / 1e9:.2f} GB, bubble tables)", "parallelism": "replicas"},
+        "e2e": e2e, "gpu_launches": int(sum(v[1] for v in prof.values())),
+        "kernels_ms": {k: round(v[0], 3) for k, v in kern.items()},
+        "kernel_launches": {k: v[1] for k, v in kern.items()},
+        "roofline": roof, "clocks": clk, **extra,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_seconds)
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline(workload, budget_s=15.0, nthreads=0):
+    """Oracle RHS on a bounded sample of output triples of the same workload;
+    RHS/s = (triples per second) / N^3."""
+    import numpy as np
+
+    from oracle.oracle import Oracle, lib
+    from paper_2005_00827_gb300 import inputs
+
+    wl = inputs.WORKLOADS[workload]
+    N, n, U = wl["N"], wl["n"], wl["U"]
+    o = Oracle(N, n, n, nthreads=nthreads)
+    V = inputs.random_vertex(N, U, seed=1)
+    Z = inputs.z_profile(N, "aniso")
+    rng = np.random.default_rng(0)
+    done = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        i, j, l = rng.integers(0, N, 3)
+        o.rhs_triple(0.1, V, Z, i, j, l)
+        done += 1
+    el = time.perf_counter() - t0
+    value = done / el / N ** 3
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} output triples of the {workload} RHS at T=0.1 in {el:.1f} s "
+                      f"(each triple sums all {N * n * n} loop points in 3 channels)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    budget = max(1.0, args.cpu_seconds / max(1, args.steps))
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(args.workload, budget_s=0.5)
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(args.workload, budget_s=budget)["value"])
+    v = statistics.mean(vals)
+    cb = cpu_baseline(args.workload, budget_s=1.0)
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 4e3 / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="qpfrg", choices=["qpfrg", "reference"])
+    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    args = p.parse_args()
+    if args.warmup < 3 and args.impl == "qpfrg":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_qpfrg(args)
+
+
+if __name__ == "__main__":
+    main()

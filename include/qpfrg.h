@@ -1,0 +1,221 @@
+/*
+ * qpfrg.h -- C ABI of the GB300 (sm_103a) quasi-particle fRG flow library.
+ *
+ * Method: D. Rohe and C. Honerkamp, "Quasi-particle functional
+ * Renormalisation Group calculations in the two-dimensional half-filled
+ * Hubbard model at finite temperatures", arXiv:2005.00827.
+ *
+ *   model        H of Eq. (model_definition), xi_k of Eq. (free_dispersion_xi)
+ *   vertex flow  one-loop dV = sum V G S V, App. A.1 Eq. (vertex_flow_general),
+ *                static SU(2) coupling V(k1,k2,k3) (App. A, "static
+ *                components"), quasi-particle lines of Eq. (both_propagators_Z)
+ *                and Eq. (vertex_flow_feedback_Z)
+ *   self-energy  real-frequency two-loop term (Sec. 2.2, App. A.2/A.3), Z from
+ *                Eq. (definition_Z) with the slope taken "from outside" over
+ *                +-2T (Sec. 3.1.1, Fig. 2 caption), projected on the Fermi
+ *                surface patch (Sec. A.3)
+ *   flow         integrated until the largest coupling passes a bound
+ *                (Sec. 3.2, scale U*(T) / T*(U))
+ *
+ * Conventions shared by every call:
+ *   - Patches j = 0..N-1.  Wedge mode: angular wedges about the origin with
+ *     centres at theta_j = 2 pi j / N (N a multiple of 4); patch
+ *     representative k_F(j) on the Fermi surface along theta_j; a fine loop
+ *     grid of n_theta x n_r points per wedge (n_r even: half inside, half
+ *     outside the Fermi surface).  Lattice mode: all L x L momenta
+ *     2 pi (m1, m2)/L are patches (N = L*L, one loop point each, index
+ *     m1*L + m2): the exact finite-lattice one-loop flow, for tests.
+ *   - The coupling V is FP64, row-major V[k1][k2][k3], N^3 entries; k1 -> k3
+ *     carries spin s, k2 -> k4 = k1 + k2 - k3 carries spin s'.
+ *   - Z is FP64, one weight per patch.  Sigma is FP64, row-major [j][m]
+ *     over the real-frequency grid omega_m = linspace(omega_min, omega_max,
+ *     n_omega) (inclusive).
+ *   - Pointers named d_* are DEVICE pointers owned by the caller; they must
+ *     stay valid until the work enqueued by the call has completed.  h_*
+ *     pointers are host memory owned by the caller.  All device work is
+ *     enqueued on the CUDA stream given to qpfrg_create.
+ *   - Every call returns a qpfrg_status.  The text of the last error of a
+ *     context is available from qpfrg_last_error.  There is no host fallback:
+ *     without a CUDA device every compute call fails with QPFRG_ERR_CUDA.
+ *   - A context is not thread-safe; calls on one context must be serialised.
+ */
+#ifndef QPFRG_H
+#define QPFRG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qpfrg_ctx *qpfrg_t;      /* opaque; created and owned by the library */
+
+typedef enum {
+    QPFRG_OK = 0,
+    QPFRG_ERR_INVALID = -1,      /* bad argument; nothing was enqueued          */
+    QPFRG_ERR_CUDA = -2,         /* a CUDA call failed (no device, launch error) */
+    QPFRG_ERR_OOM = -3,          /* device or host allocation failed            */
+    QPFRG_ERR_UNSUPPORTED = -4,  /* valid request this build does not implement */
+    QPFRG_ERR_TIMEOUT = -5,      /* a bounded wait or wall-clock budget ran out  */
+    QPFRG_ERR_NONFINITE = -6     /* NaN/Inf met in an input or in the state      */
+} qpfrg_status;
+
+typedef enum {
+    QPFRG_REG_TEMPERATURE = 0,   /* Lambda = T: dV/dT with T-derivative loop kernels   */
+    QPFRG_REG_INTERACTION = 1    /* Lambda = g: G = g Z G0, S = Z^2 G0 at fixed T (App. A) */
+} qpfrg_regulator;
+
+typedef enum {
+    QPFRG_FP64 = 0,              /* every step in FP64                                */
+    QPFRG_MIXED = 1,             /* FP32 loop kernels and contraction, FP64 ODE state  */
+    QPFRG_MIXED_TC = 2           /* reserved: tensor-core contraction                  */
+} qpfrg_precision;
+
+typedef enum {
+    QPFRG_PROP_PAPER = 0,        /* G = Z/(iw - xi): Z a prefactor, Eq. (both_propagators_Z) */
+    QPFRG_PROP_QP = 1            /* G = Z/(iw - Z xi): Z also renormalises the pole          */
+} qpfrg_propagator;
+
+enum { QPFRG_CH_PP = 1, QPFRG_CH_CR = 2, QPFRG_CH_D = 4, QPFRG_CH_ALL = 7 };
+
+typedef enum { QPFRG_GRID_WEDGE = 0, QPFRG_GRID_LATTICE = 1 } qpfrg_grid_mode;
+
+typedef enum {
+    QPFRG_FLOW_RUNNING = 0,      /* neither bound nor end reached yet            */
+    QPFRG_FLOW_REACHED_END = 1,  /* Lambda reached lambda_end                    */
+    QPFRG_FLOW_DIVERGED = 2,     /* max|V| passed stop_abs_v (strong coupling)   */
+    QPFRG_FLOW_NONFINITE = 3,    /* NaN/Inf in V or Z                            */
+    QPFRG_FLOW_Z_OUT_OF_RANGE = 4,/* Z left (0, z_max]                           */
+    QPFRG_FLOW_MAX_STEPS = 5,    /* max_steps completed                          */
+    QPFRG_FLOW_TIMEOUT = 6       /* wall-clock budget of qpfrg_flow ran out      */
+} qpfrg_flow_status;
+
+typedef struct { double t, tp, mu; } qpfrg_lattice;   /* Eq. (free_dispersion_xi) */
+
+typedef struct {
+    int n_theta;                 /* angular fine points per wedge (>= 1)               */
+    int n_r;                     /* radial fine points per wedge (even, >= 2)          */
+    int mode;                    /* qpfrg_grid_mode                                    */
+} qpfrg_fine_grid;
+
+typedef struct {
+    unsigned channel_mask;       /* OR of QPFRG_CH_*; pp off = particle-hole-only flow (Sec. 3.2) */
+    int z_feedback;              /* recompute Z from Sigma once per flow step          */
+    int propagator;              /* qpfrg_propagator                                   */
+    int precision;               /* qpfrg_precision                                    */
+    double eta;                  /* Lorentzian broadening of the retarded Sigma        */
+    int n_omega;                 /* real-frequency grid of qpfrg_selfenergy (0: none)  */
+    double omega_min, omega_max;
+    double stop_abs_v;           /* divergence bound on max|V| (default 20 t)          */
+    double step;                 /* T-flow: d ln T per step (<0); g-flow: dg (>0)      */
+    double lambda_end;           /* end of the flow: T_end or g_end                    */
+    double z_max;                /* Z outside (0, z_max] stops the flow                */
+    int max_steps;               /* bound on flow steps per qpfrg_flow call            */
+    double T_fixed;              /* temperature of the interaction flow                */
+    double timeout_s;            /* wall-clock budget of one qpfrg_flow call (<=0: none) */
+} qpfrg_options;
+
+typedef struct {
+    int status;                  /* qpfrg_flow_status                                  */
+    int steps;                   /* RK4 steps completed since creation / set_state      */
+    double lambda;               /* flow parameter now (T or g)                         */
+    double lambda_c;             /* interpolated crossing of stop_abs_v (DIVERGED only) */
+    double max_abs_v;            /* max|V| of the current state                         */
+} qpfrg_flow_result;
+
+/* Fill *o with the defaults: all channels, no Z feedback, PAPER propagators,
+ * FP64, eta 0.02, no omega grid (range [-4, 4]), stop_abs_v 20, step ln 0.98,
+ * lambda_end 0.05, z_max 2, max_steps 100000, T_fixed 0.1, no timeout. */
+void qpfrg_default_options(qpfrg_options *o);
+
+/* Create a context: builds the patch geometry (FP64, on the host), uploads
+ * the fine-point tables, computes the partner-patch maps proj(Q - p) and
+ * proj(p + Q) for every transfer Q = k_F(x) +- k_F(y) and fine point p on the
+ * device (FP64), and sets the flow state to V = U, Z = 1 at Lambda = lambda0
+ * (Sec. 3.2: the flow starts from the bare Hubbard coupling).
+ * n_p: number of patches (wedge: multiple of 4, <= 256; lattice: L*L <= 256).
+ * cuda_stream: cudaStream_t (NULL = legacy default stream).
+ * Errors: QPFRG_ERR_INVALID for bad parameters, QPFRG_ERR_OOM, QPFRG_ERR_CUDA,
+ * QPFRG_ERR_UNSUPPORTED (e.g. more than 2048 fine points per wedge).
+ * On error *out is NULL. */
+qpfrg_status qpfrg_create(const qpfrg_lattice *lattice, int n_p, const qpfrg_fine_grid *grid,
+                          double U, double lambda0, qpfrg_regulator regulator,
+                          const qpfrg_options *options, void *cuda_stream, qpfrg_t *out);
+
+/* One evaluation of the one-loop right-hand side dV/dLambda (App. A.1,
+ * Eq. (vertex_flow_general); Eq. (vertex_flow_feedback_Z) with Z):
+ *   pp : Q = k1+k2, dV -= sum_p L'_pp(p,Q-p) V(k1,k2,p) V(p,Q-p,k3)
+ *   cr : Q = k3-k2, dV -= sum_p L'_ph(p,p+Q) V(k1,p,p+Q) V(p+Q,k2,k3)
+ *   d  : Q = k1-k3, dV += sum_p L'_ph(p,p+Q) [2V(k1,p,k3)V(p+Q,k2,p)
+ *                          - V(p,k1,k3)V(p+Q,k2,p) - V(k1,p,k3)V(k2,p+Q,p)]
+ * p runs over the fine points, vertex arguments are patches.  L' is Z_a Z_b
+ * dL/dT (T-flow) or g Z_a Z_b (Z_a + Z_b) L (g-flow).
+ * d_V: N^3 FP64 input, d_Z: N FP64 input (NULL = all ones), d_dV: N^3 FP64
+ * output (may not alias d_V).  lambda = T (T-flow, > 0) or g (g-flow).
+ * Uses the context's precision.  The context's flow state is not changed. */
+qpfrg_status qpfrg_rhs(qpfrg_t ctx, double lambda, const double *d_V, const double *d_Z,
+                       double *d_dV);
+
+/* Real-frequency two-loop self-energy at the patch representatives for the
+ * vertex d_V and weights d_Z at temperature T (T-flow: T = lambda):
+ *   Sigma(k_j, w) = sum_{p,q} w_p w_q Z_a Z_b Z_c W F / (w + i eta - E),
+ *   r = k_j + p - q, E = xi_q + xi_r - xi_p,
+ *   F = f_p(1-f_q)(1-f_r) + (1-f_p) f_q f_r,
+ *   W = 2 V(k_j,p,q)^2 - V(k_j,p,q) V(k_j,p,r),
+ * and Z_j = 1/(1 - [Re Sigma(xi_j+2T) - Re Sigma(xi_j-2T)]/(4T)).
+ * d_sigma_re/d_sigma_im: N x n_omega FP64 outputs (may be NULL when
+ * n_omega == 0; the frequency grid is binned, see the design notes);
+ * d_Z_out: N FP64 output (may be NULL).  Regulator must be TEMPERATURE
+ * (QPFRG_ERR_UNSUPPORTED otherwise). */
+qpfrg_status qpfrg_selfenergy(qpfrg_t ctx, double lambda, const double *d_V, const double *d_Z,
+                              double *d_sigma_re, double *d_sigma_im, double *d_Z_out);
+
+/* Advance the context's flow state by at most n_steps RK4 steps (T-flow:
+ * uniform in ln T, last step clamped onto lambda_end; g-flow: uniform in g),
+ * stopping early at divergence, end of flow, non-finite state or Z out of
+ * range.  With z_feedback, Z is recomputed from Sigma[V, Z] at the start of
+ * every step and held over its four stages.  *out (may be NULL) receives the
+ * state summary.  Blocks the host once per step to read max|V|. */
+qpfrg_status qpfrg_step(qpfrg_t ctx, int n_steps, qpfrg_flow_result *out);
+
+/* Run qpfrg_step until the flow stops (any status other than RUNNING) or
+ * max_steps / timeout_s is reached. */
+qpfrg_status qpfrg_flow(qpfrg_t ctx, qpfrg_flow_result *out);
+
+/* Checkpoint: size in bytes of the state image (64-byte header, then V as
+ * N^3 FP64, then Z as N FP64, little endian). */
+qpfrg_status qpfrg_state_size(qpfrg_t ctx, size_t *bytes);
+/* Copy the flow state into h_buf (host, at least qpfrg_state_size bytes).
+ * Synchronises the context's stream. */
+qpfrg_status qpfrg_get_state(qpfrg_t ctx, void *h_buf, size_t bytes);
+/* Replace the flow state by h_buf (as written by qpfrg_get_state).  Returns
+ * QPFRG_ERR_INVALID on a wrong header or size, QPFRG_ERR_NONFINITE (state
+ * unchanged) when V or Z holds NaN/Inf. */
+qpfrg_status qpfrg_set_state(qpfrg_t ctx, const void *h_buf, size_t bytes);
+/* Copy V (N^3 FP64) and Z (N FP64) of the flow state into device buffers
+ * (either may be NULL); enqueued on the context's stream. */
+qpfrg_status qpfrg_read_state(qpfrg_t ctx, double *d_V, double *d_Z);
+
+/* Geometry of the context as built on the host: N, the number of fine
+ * points M, k_F (N x 2 FP64) and the fine points (M x 4 FP64: kx, ky,
+ * weight, patch).  Any output pointer may be NULL. */
+qpfrg_status qpfrg_geometry(qpfrg_t ctx, int *n_p, int *n_fine, double *h_kf, double *h_fine);
+
+/* Kernel timing with CUDA events on the context's stream (off by default).
+ * qpfrg_profile_get returns the accumulated device milliseconds and launch
+ * count of kernel id (0 <= id < qpfrg_profile_count()); names via
+ * qpfrg_profile_name.  qpfrg_profile_reset clears the counters. */
+qpfrg_status qpfrg_set_profiling(qpfrg_t ctx, int on);
+qpfrg_status qpfrg_profile_reset(qpfrg_t ctx);
+int          qpfrg_profile_count(void);
+const char  *qpfrg_profile_name(int id);
+qpfrg_status qpfrg_profile_get(qpfrg_t ctx, int id, double *ms, long long *launches);
+
+const char  *qpfrg_last_error(qpfrg_t ctx);   /* never NULL; ctx may be NULL */
+const char  *qpfrg_version(void);
+void         qpfrg_destroy(qpfrg_t ctx);      /* frees device memory; NULL is a no-op */
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,306 @@
+// Loop kernels of the one-loop vertex flow, grouped by transfer momentum.
+//
+// For every transfer Q of the particle-particle family (Q = k_F(x) + k_F(y),
+// partner Q - p) and of the particle-hole family (Q = k_F(x) - k_F(y),
+// partner p + Q) this kernel bins the Z-weighted loop kernel of each fine
+// point p into the bubble table
+//     B_f[Q][a][b] = s(a,b) * sum_{p in a, proj(partner) = b} w_p L'_f(x_p, x_partner)
+// with L'_ph = dD/dT, L'_pp = -dD(x_p, -x_q)/dT in the temperature flow and
+// L'_ph = D, L'_pp = -D(x_p, -x_q) in the interaction flow, where
+// D(a,b) = (f(a) - f(b))/(a - b) is the closed-form Matsubara sum of G0 G0.
+// s(a,b) = Z_a Z_b (T-flow) or g Z_a Z_b (Z_a + Z_b) (g-flow), the line
+// weights of Eq. (both_propagators_Z) / Eq. (vertex_flow_feedback_Z).
+//
+// Launch shape: one CTA per (patch a, chunk of Q, family).  The CTA keeps its
+// wedge's fine points in registers (PPT consecutive radial points per
+// thread), streams the partner-patch bytes of each Q (coalesced), merges
+// equal consecutive partners in registers and adds runs into a shared-memory
+// row of N accumulators.  Rows are double-buffered so one barrier per Q
+// suffices.
+#include <algorithm>
+
+#include "qpfrg_internal.h"
+
+namespace qpfrg {
+
+template <typename R>
+struct BubbleArgs {
+    Problem pb;
+    FineTable<R> fine;
+    TransferTable<R> qpp, qph;
+    const uint8_t *part;
+    const double *Z;
+    R *B;
+    R T, invT, g, thr;
+    int qchunk;
+};
+
+// ---- scalar helpers ---------------------------------------------------------
+__device__ __forceinline__ float fexp(float x) { return __expf(x); }
+__device__ __forceinline__ double fexp(double x) { return exp(x); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+
+// f(x) and 1 - f(x) without cancellation: e = exp(-|x|/T)
+template <typename R>
+__device__ __forceinline__ void fermi_pair(R x, R invT, R &f, R &fc)
+{
+    const R e = fexp(-fabs(x) * invT);
+    const R lo = fdiv(e, R(1) + e), hi = fdiv(R(1), R(1) + e);
+    f = x > R(0) ? lo : hi;
+    fc = x > R(0) ? hi : lo;
+}
+
+// f(1-f) = e/(1+e)^2
+template <typename R>
+__device__ __forceinline__ R fermi_ff(R x, R invT)
+{
+    const R e = fexp(-fabs(x) * invT);
+    const R d = R(1) + e;
+    return fdiv(e, d * d);
+}
+
+// d/dT f(x) = x/T^2 f(1-f)
+template <typename R>
+__device__ __forceinline__ R fermi_dT(R x, R invT)
+{
+    return x * invT * invT * fermi_ff(x, invT);
+}
+
+// d/dx d/dT f = f'(x) (-1/T + x tanh(x/2T)/T^2), f' = -f(1-f)/T
+template <typename R>
+__device__ __forceinline__ R fermi_dxdT(R x, R invT)
+{
+    const R e = fexp(-fabs(x) * invT);
+    const R d = R(1) + e;
+    const R ff = fdiv(e, d * d);
+    R th = fdiv(R(1) - e, d);
+    th = x > R(0) ? th : -th;
+    return -ff * invT * (-invT + x * th * invT * invT);
+}
+
+// Loop kernel of one line pair (x_p, x_q), temperature flow.
+//   ph: dD(x_p, x_q)/dT = (g_p - g_q)/(x_p - x_q),   g = df/dT
+//   pp: -dD(x_p, -x_q)/dT = -(g_p + g_q)/(x_p + x_q)   (g odd in x)
+// Below |difference| < thr*T the analytic derivative at the midpoint is used.
+template <typename R>
+__device__ __forceinline__ R loop_T(bool pp, R xp, R gp, R xq, R invT, R thrT)
+{
+    const R den = pp ? xp + xq : xp - xq;
+    if (fabs(den) < thrT) {
+        const R m = R(0.5) * (pp ? xp - xq : xp + xq);
+        const R v = fermi_dxdT(m, invT);
+        return pp ? -v : v;
+    }
+    const R e = fexp(-fabs(xq) * invT);
+    const R d = R(1) + e, d2 = d * d;
+    const R gq_num = xq * invT * invT * e;           // g_q * d2
+    const R num = pp ? gp * d2 + gq_num : gp * d2 - gq_num;
+    const R v = fdiv(num, d2 * den);
+    return pp ? -v : v;
+}
+
+// Loop kernel of one line pair, interaction flow at fixed T.
+//   ph: D(x_p, x_q),  pp: -D(x_p, -x_q) = (1 - f_p - f_q)/(x_p + x_q)
+template <typename R>
+__device__ __forceinline__ R loop_g(bool pp, R xp, R fp, R fcp, R xq, R invT, R thrT)
+{
+    const R den = pp ? xp + xq : xp - xq;
+    if (fabs(den) < thrT) {
+        const R m = R(0.5) * (pp ? xp - xq : xp + xq);
+        const R v = -fermi_ff(m, invT) * invT;       // f'(m)
+        return pp ? -v : v;
+    }
+    R fq, fcq;
+    fermi_pair(xq, invT, fq, fcq);
+    // numerator f(a) - f(b) with b = x_q (ph) or -x_q (pp); f(-x_q) = fc_q
+    R fa = fp, fb = pp ? fcq : fq, ca = fcp, cb = pp ? fq : fcq;
+    const R xb = pp ? -xq : xq;
+    const R num = (xp < R(0) && xb < R(0)) ? cb - ca : fa - fb;
+    const R v = fdiv(num, den);
+    return pp ? -v : v;
+}
+
+// Partner bytes of this thread's points.  The vector path needs P % PPT == 0
+// (then every thread's run starts PPT-aligned and stays inside its patch);
+// otherwise bytes are read one by one and only for valid points.
+template <int PPT>
+__device__ __forceinline__ void load_partners(const uint8_t *src, int (&b)[PPT], bool vec, int nvalid)
+{
+    if (vec) {
+        if constexpr (PPT == 4) {
+            const uint32_t w = *reinterpret_cast<const uint32_t *>(src);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) b[u] = (w >> (8 * u)) & 0xff;
+            return;
+        } else if constexpr (PPT == 8) {
+            const uint2 w = *reinterpret_cast<const uint2 *>(src);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) b[u] = (w.x >> (8 * u)) & 0xff;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) b[4 + u] = (w.y >> (8 * u)) & 0xff;
+            return;
+        } else if constexpr (PPT == 2) {
+            const uint32_t w = *reinterpret_cast<const uint16_t *>(src);
+            b[0] = w & 0xff;
+            b[1] = (w >> 8) & 0xff;
+            return;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < PPT; ++u) b[u] = u < nvalid ? src[u] : 0;
+}
+
+template <typename R, int PPT>
+__global__ void __launch_bounds__(256) bubble_kernel(BubbleArgs<R> A)
+{
+    const int N = A.pb.N, P = A.pb.P, M = A.pb.M;
+    const long NN = (long)N * N;
+    const int a = blockIdx.x;
+    const int fam = blockIdx.z;               // 0 = pp, 1 = ph
+    const bool pp = fam == 0;
+    const int q0 = blockIdx.y * A.qchunk;
+    const int q1 = min((long)q0 + A.qchunk, NN);
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const bool tflow = A.pb.regulator == QPFRG_REG_TEMPERATURE;
+    const bool qp = A.pb.propagator == QPFRG_PROP_QP;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *acc = reinterpret_cast<R *>(smem_raw);  // 2 x N
+    R *Zs = acc + 2 * N;                       // N
+    for (int i = tid; i < 2 * N; i += nthr) acc[i] = R(0);
+    for (int i = tid; i < N; i += nthr) Zs[i] = A.Z ? (R)A.Z[i] : R(1);
+    __syncthreads();
+    const R Za = Zs[a];
+    const R invT = A.invT, thrT = A.thr * A.T;
+    const R t = (R)A.pb.t, tp = (R)A.pb.tp, mu = (R)A.pb.mu;
+
+    // this thread's fine points: local indices tid*PPT + u
+    R pcx[PPT], psx[PPT], pcy[PPT], psy[PPT], px[PPT], pw[PPT], pa[PPT], pb2[PPT];
+    bool valid[PPT];
+#pragma unroll
+    for (int u = 0; u < PPT; ++u) {
+        const int loc = tid * PPT + u;
+        valid[u] = loc < P;
+        const int p = a * P + (valid[u] ? loc : 0);
+        pcx[u] = A.fine.cx[p];
+        psx[u] = A.fine.sx[p];
+        pcy[u] = A.fine.cy[p];
+        psy[u] = A.fine.sy[p];
+        pw[u] = valid[u] ? A.fine.w[p] : R(0);
+        px[u] = qp ? Za * A.fine.xi[p] : A.fine.xi[p];
+        if (tflow) {
+            pa[u] = fermi_dT(px[u], invT);
+            pb2[u] = R(0);
+        } else {
+            fermi_pair(px[u], invT, pa[u], pb2[u]);
+        }
+    }
+    const bool any_valid = tid * PPT < P;
+    const bool vec = (P % PPT) == 0;
+    const TransferTable<R> &Qt = pp ? A.qpp : A.qph;
+
+    for (int Q = q0; Q < q1; ++Q) {
+        R *accb = acc + ((Q - q0) & 1) * N;
+        if (any_valid) {
+            const R cQx = Qt.cx[Q], sQx = Qt.sx[Q], cQy = Qt.cy[Q], sQy = Qt.sy[Q];
+            int bq[PPT];
+            load_partners<PPT>(A.part + ((long)fam * NN + Q) * (long)M + (long)a * P + tid * PPT, bq,
+                               vec, P - tid * PPT);
+            int run_b = -1;
+            R run_v = R(0);
+#pragma unroll
+            for (int u = 0; u < PPT; ++u) {
+                if (!valid[u]) continue;
+                // cos of the partner momentum components by angle addition:
+                // pp: cos(Q - p) = cQ cp + sQ sp;  ph: cos(p + Q) = cp cQ - sp sQ
+                const R cqx = pp ? cQx * pcx[u] + sQx * psx[u] : pcx[u] * cQx - psx[u] * sQx;
+                const R cqy = pp ? cQy * pcy[u] + sQy * psy[u] : pcy[u] * cQy - psy[u] * sQy;
+                R xq = R(-2) * t * (cqx + cqy) - R(4) * tp * cqx * cqy - mu;
+                const int b = bq[u];
+                if (qp) xq *= Zs[b];
+                const R v = pw[u] * (tflow ? loop_T(pp, px[u], pa[u], xq, invT, thrT)
+                                           : loop_g(pp, px[u], pa[u], pb2[u], xq, invT, thrT));
+                if (b == run_b) {
+                    run_v += v;
+                } else {
+                    if (run_b >= 0) atomicAdd(&accb[run_b], run_v);
+                    run_b = b;
+                    run_v = v;
+                }
+            }
+            if (run_b >= 0) atomicAdd(&accb[run_b], run_v);
+        }
+        __syncthreads();
+        R *dst = A.B + (((long)fam * NN + Q) * N + a) * (long)N;
+        for (int b = tid; b < N; b += nthr) {
+            const R v = accb[b];
+            accb[b] = R(0);
+            const R Zb = Zs[b];
+            const R s = tflow ? Za * Zb : A.g * Za * Zb * (Za + Zb);
+            dst[b] = v * s;
+        }
+    }
+}
+
+template <typename R, int PPT>
+static void launch_t(qpfrg_ctx *c, const BubbleArgs<R> &A, int nthr, int qchunks)
+{
+    const int N = c->pb.N;
+    dim3 grid(N, qchunks, 2);
+    const size_t smem = 3 * (size_t)N * sizeof(R);
+    bubble_kernel<R, PPT><<<grid, nthr, smem, c->stream>>>(A);
+}
+
+template <typename R>
+static qpfrg_status launch_r(qpfrg_ctx *c, double lambda, const double *d_Z, const FineTable<R> &fine,
+                             const TransferTable<R> &qpp, const TransferTable<R> &qph, R thr)
+{
+    const Problem &pb = c->pb;
+    BubbleArgs<R> A;
+    A.pb = pb;
+    A.fine = fine;
+    A.qpp = qpp;
+    A.qph = qph;
+    A.part = c->d_part;
+    A.Z = d_Z;
+    A.B = reinterpret_cast<R *>(c->d_B);
+    const bool tflow = pb.regulator == QPFRG_REG_TEMPERATURE;
+    const double T = tflow ? lambda : pb.T_fixed;
+    A.T = (R)T;
+    A.invT = (R)(1.0 / T);
+    A.g = (R)(tflow ? 1.0 : lambda);
+    A.thr = thr;
+    const long NN = (long)pb.N * pb.N;
+    A.qchunk = (int)std::max(1L, std::min(64L, NN / 16));
+    const int qchunks = div_up(NN, A.qchunk);
+
+    const int P = pb.P;
+    int ppt = (P + 255) / 256;
+    if (ppt > 8) {
+        c->err = "more than 2048 fine points per patch are not supported";
+        return QPFRG_ERR_UNSUPPORTED;
+    }
+    ppt = ppt <= 1 ? 1 : (ppt <= 2 ? 2 : (ppt <= 4 ? 4 : 8));
+    int nthr = (P + ppt - 1) / ppt;
+    nthr = std::max(32, ((nthr + 31) / 32) * 32);
+    prof_begin(c);
+    switch (ppt) {
+    case 1: launch_t<R, 1>(c, A, nthr, qchunks); break;
+    case 2: launch_t<R, 2>(c, A, nthr, qchunks); break;
+    case 4: launch_t<R, 4>(c, A, nthr, qchunks); break;
+    default: launch_t<R, 8>(c, A, nthr, qchunks); break;
+    }
+    prof_end(c, K_BUBBLE);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "bubble_kernel");
+}
+
+qpfrg_status launch_bubbles(qpfrg_ctx *c, double lambda, const double *d_Z)
+{
+    if (c->opt.precision == QPFRG_FP64)
+        return launch_r<double>(c, lambda, d_Z, c->f64, c->qpp64, c->qph64, 1e-5);
+    return launch_r<float>(c, lambda, d_Z, c->f32, c->qpp32, c->qph32, 2e-2f);
+}
+
+}  // namespace qpfrg

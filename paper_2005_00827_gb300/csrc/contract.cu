@@ -1,0 +1,180 @@
+// Contraction of the bubble tables with two vertices, all output triples.
+//
+// With B_f[Q][a][b] from bubble.cu (a = patch of the loop point p, b = patch of
+// its partner), the three channels of the one-loop flow (App. A.1,
+// Eq. (vertex_flow_general)) become, for k = (a, b) in N^2:
+//   pp (Q = k1+k2 = (i,j)):  dV[i,j,l] -= sum_k B_pp[i,j][k] V[i,j,a] * V[a,b,l]
+//   cr (Q = k3-k2 = (l,j)):  dV[i,j,l] -= sum_k B_ph[l,j][k] V[b,j,l] * V[i,a,b]
+//   d  (Q = k1-k3 = (i,l)):  dV[i,j,l] += sum_k B_ph[i,l][k] {(2V[i,a,l] - V[a,i,l]) V[b,j,a]
+//                                                          - V[i,a,l] V[j,b,a]}
+// Each channel is a GEMM with N^2 rows r, K = N^2 (2N^2 for d) and N
+// columns n, whose A operand is a row of a bubble table times a vertex
+// factor (formed while staging into shared memory) and whose B operand is a
+// permuted view of V:
+//   pp: r = (i,j), n = l;  cr: r = (j,l), n = i;  d: r = (i,l), n = j.
+// Output: out[index(r,n)] += scale * sign * sum.
+#include "qpfrg_internal.h"
+
+namespace qpfrg {
+
+constexpr int BM = 64, BN = 32, BK = 16, TM = 4, TN = 2;
+
+template <typename R, typename VR, int CH>
+struct ChannelOps {
+    const R *B;      // bubble table family (pp or ph), [Q][a][b]
+    const VR *V;     // vertex (FP64 or FP32)
+    int N;
+    long NN;
+
+    // A operand: row r, reduction index k (k >= NN: second product of d)
+    __device__ __forceinline__ R a_elem(int r, long k) const
+    {
+        if (CH == 0) {                         // pp: r = i*N + j
+            const int a = (int)(k / N);
+            return B[(long)r * NN + k] * (R)V[(long)r * N + a];
+        } else if (CH == 1) {                  // cr: r = j*N + l, table row Q = (l, j)
+            const int j = r / N, l = r % N;
+            const int a = (int)(k / N), b = (int)(k % N);
+            (void)a;
+            return B[((long)l * N + j) * NN + k] * (R)V[((long)b * N + j) * N + l];
+        } else {                               // d: r = i*N + l
+            const int i = r / N, l = r % N;
+            const bool second = k >= NN;
+            const long kk = second ? k - NN : k;
+            const int a = (int)(kk / N);
+            const R bt = B[(long)r * NN + kk];
+            const R v_ial = (R)V[((long)i * N + a) * N + l];
+            if (!second) return bt * (R(2) * v_ial - (R)V[((long)a * N + i) * N + l]);
+            return -bt * v_ial;
+        }
+    }
+    // B operand: reduction index k, column n
+    __device__ __forceinline__ R b_elem(long k, int n) const
+    {
+        if (CH == 0) return (R)V[k * N + n];                  // V[a,b,l]
+        if (CH == 1) return (R)V[(long)n * NN + k];           // V[i,a,b]
+        const bool second = k >= NN;
+        const long kk = second ? k - NN : k;
+        const int a = (int)(kk / N), b = (int)(kk % N);
+        if (!second) return (R)V[((long)b * N + n) * N + a];  // V[b,j,a]
+        return (R)V[((long)n * N + b) * N + a];               // V[j,b,a]
+    }
+    __device__ __forceinline__ long out_index(int r, int n) const
+    {
+        if (CH == 0) return (long)r * N + n;                  // (i,j,l) = (r, n)
+        if (CH == 1) return (long)n * NN + r;                 // i = n, (j,l) = r
+        const int i = r / N, l = r % N;
+        return ((long)i * N + n) * N + l;                     // j = n
+    }
+};
+
+template <typename R, typename VR, int CH>
+__global__ void __launch_bounds__(256) contract_kernel(ChannelOps<R, VR, CH> ops, double *out,
+                                                       double scale, double sign)
+{
+    const int N = ops.N;
+    const long NN = ops.NN;
+    const long K = CH == 2 ? 2 * NN : NN;
+    const int r0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int tid = threadIdx.x;
+    const int tr = tid / (BN / TN), tn = tid % (BN / TN);   // 16 x 16 thread grid
+
+    __shared__ R As[BK][BM + 1];
+    __shared__ R Bs[BK][BN + 1];
+    R acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = R(0);
+
+    for (long k0 = 0; k0 < K; k0 += BK) {
+        // stage A: BM x BK, 4 elements per thread
+#pragma unroll
+        for (int e = 0; e < (BM * BK) / 256; ++e) {
+            const int idx = tid + e * 256;
+            const int rr = idx / BK, kk = idx % BK;
+            const int r = r0 + rr;
+            const long k = k0 + kk;
+            As[kk][rr] = (r < NN && k < K) ? ops.a_elem(r, k) : R(0);
+        }
+        // stage B: BK x BN, 2 elements per thread
+#pragma unroll
+        for (int e = 0; e < (BK * BN) / 256; ++e) {
+            const int idx = tid + e * 256;
+            const int kk = idx / BN, nn = idx % BN;
+            const int n = n0 + nn;
+            const long k = k0 + kk;
+            Bs[kk][nn] = (n < N && k < K) ? ops.b_elem(k, n) : R(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            R av[TM], bv[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) av[i] = As[kk][tr * TM + i];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) bv[j] = Bs[kk][tn * TN + j];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] += av[i] * bv[j];
+        }
+        __syncthreads();
+    }
+    const double s = scale * sign;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        const int r = r0 + tr * TM + i;
+        if (r >= NN) continue;
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int n = n0 + tn * TN + j;
+            if (n >= N) continue;
+            const long o = ops.out_index(r, n);
+            out[o] += s * (double)acc[i][j];
+        }
+    }
+}
+
+template <typename R, typename VR, int CH>
+static qpfrg_status launch_channel(qpfrg_ctx *c, const R *B, const VR *V, double scale, double sign,
+                                   double *out, int kid)
+{
+    ChannelOps<R, VR, CH> ops;
+    ops.B = B;
+    ops.V = V;
+    ops.N = c->pb.N;
+    ops.NN = (long)c->pb.N * c->pb.N;
+    dim3 grid(div_up(ops.NN, BM), div_up(c->pb.N, BN));
+    prof_begin(c);
+    contract_kernel<R, VR, CH><<<grid, 256, 0, c->stream>>>(ops, out, scale, sign);
+    prof_end(c, kid);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "contract_kernel");
+}
+
+template <typename R, typename VR>
+static qpfrg_status launch_all(qpfrg_ctx *c, const VR *V, double scale, double *out)
+{
+    const R *B = reinterpret_cast<const R *>(c->d_B);
+    const long table = (long)c->pb.N * c->pb.N * c->pb.N * c->pb.N;
+    const R *Bpp = B, *Bph = B + table;
+    const unsigned ch = c->pb.channels;
+    qpfrg_status s = QPFRG_OK;
+    if ((ch & QPFRG_CH_PP) && (s = launch_channel<R, VR, 0>(c, Bpp, V, scale, -1.0, out, K_CONTRACT_PP)))
+        return s;
+    if ((ch & QPFRG_CH_CR) && (s = launch_channel<R, VR, 1>(c, Bph, V, scale, -1.0, out, K_CONTRACT_CR)))
+        return s;
+    if ((ch & QPFRG_CH_D) && (s = launch_channel<R, VR, 2>(c, Bph, V, scale, 1.0, out, K_CONTRACT_D)))
+        return s;
+    return QPFRG_OK;
+}
+
+qpfrg_status launch_contractions(qpfrg_ctx *c, const void *d_Vin, double scale, double *d_out)
+{
+    if (c->opt.precision == QPFRG_FP64)
+        return launch_all<double, double>(c, reinterpret_cast<const double *>(d_Vin), scale, d_out);
+    return launch_all<float, float>(c, reinterpret_cast<const float *>(d_Vin), scale, d_out);
+}
+
+}  // namespace qpfrg

@@ -1,0 +1,243 @@
+// Patch geometry and partner-patch maps.
+//
+// The paper fixes only patch counts (Sec. 3.2: 32 angular x 7 energy, 48
+// angular, 728 total; Fig. 4 caption: 1 and 4 patches between antinode and
+// node).  This library takes angular wedges about the origin with centres at
+// theta_j = 2 pi j / N ((pi,0) is a centre), representatives k_F(j) on the
+// Fermi surface xi = 0 (Eq. (free_dispersion_xi)) along theta_j, and a polar
+// fine grid per wedge: n_theta angular midpoints x n_r radial midpoint cells,
+// n_r/2 uniform in (0, r_F(theta)) and n_r/2 in (r_F(theta), r_BZ(theta)),
+// weight = cell area / (2 pi)^2 so that sum_p w_p ~ int d^2p/(2 pi)^2 = 1.
+// Lattice mode instead takes every momentum of an L x L lattice as a patch.
+#include <cmath>
+#include <cstring>
+
+#include "qpfrg_internal.h"
+
+namespace qpfrg {
+
+static double host_xi(const Problem &pb, double kx, double ky)
+{
+    const double ckx = std::cos(kx), cky = std::cos(ky);
+    return -2.0 * pb.t * (ckx + cky) - 4.0 * pb.tp * ckx * cky - pb.mu;
+}
+
+// Distance from the origin to the boundary of [-pi, pi]^2 along angle th.
+static double bz_radius(double th)
+{
+    return kPi / std::fmax(std::fabs(std::cos(th)), std::fabs(std::sin(th)));
+}
+
+// First zero of xi along the ray at angle th (bisection on xi < 0); the BZ
+// edge when xi stays negative, 0 when the origin is already unoccupied.
+static double fermi_radius(const Problem &pb, double th)
+{
+    const double c = std::cos(th), s = std::sin(th);
+    double hi = bz_radius(th);
+    if (host_xi(pb, hi * c, hi * s) < 0.0) return hi;
+    if (host_xi(pb, 0.0, 0.0) >= 0.0) return 0.0;
+    double lo = 0.0;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (host_xi(pb, mid * c, mid * s) < 0.0)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+qpfrg_status build_host_geometry(qpfrg_ctx *c)
+{
+    const Problem &pb = c->pb;
+    const int N = pb.N, M = pb.M;
+    c->kf.assign(2 * (size_t)N, 0.0);
+    c->fk.assign(2 * (size_t)M, 0.0);
+    c->fw.assign((size_t)M, 0.0);
+    c->fpatch.assign((size_t)M, 0);
+
+    if (pb.mode == QPFRG_GRID_LATTICE) {
+        const int L = pb.L;
+        for (int m1 = 0; m1 < L; ++m1)
+            for (int m2 = 0; m2 < L; ++m2) {
+                const int j = m1 * L + m2;
+                const double kx = kTwoPi * m1 / L, ky = kTwoPi * m2 / L;
+                c->kf[2 * j] = kx;
+                c->kf[2 * j + 1] = ky;
+                c->fk[2 * j] = kx;
+                c->fk[2 * j + 1] = ky;
+                c->fw[j] = 1.0 / N;
+                c->fpatch[j] = j;
+            }
+        return QPFRG_OK;
+    }
+
+    const double dth = kTwoPi / N;
+    const int nt = c->n_theta, nr = c->n_r, nh = c->n_r / 2;
+    for (int j = 0; j < N; ++j) {
+        const double thj = dth * j;
+        const double rfj = fermi_radius(pb, thj);
+        c->kf[2 * j] = rfj * std::cos(thj);
+        c->kf[2 * j + 1] = rfj * std::sin(thj);
+        for (int a = 0; a < nt; ++a) {
+            const double th = thj + ((a + 0.5) / nt - 0.5) * dth;
+            const double rf = fermi_radius(pb, th), rb = bz_radius(th);
+            for (int s = 0; s < nr; ++s) {
+                double r0, r1;
+                if (s < nh) {
+                    r0 = rf * s / nh;
+                    r1 = rf * (s + 1) / nh;
+                } else {
+                    r0 = rf + (rb - rf) * (s - nh) / nh;
+                    r1 = rf + (rb - rf) * (s - nh + 1) / nh;
+                }
+                const double r = 0.5 * (r0 + r1);
+                const size_t p = ((size_t)j * nt + a) * nr + s;
+                c->fk[2 * p] = r * std::cos(th);
+                c->fk[2 * p + 1] = r * std::sin(th);
+                c->fw[p] = 0.5 * (r1 * r1 - r0 * r0) * (dth / nt) / (kTwoPi * kTwoPi);
+                c->fpatch[p] = j;
+            }
+        }
+    }
+    return QPFRG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Device projection of a momentum onto its patch (FP64).  Wedge: fold each
+// component into [-pi, pi] (ties to even), angle by atan2, nearest wedge
+// centre with half-open wedges.  Lattice: nearest lattice momentum.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int project_patch(double kx, double ky, int N, int mode, int L)
+{
+    if (mode == QPFRG_GRID_LATTICE) {
+        long m1 = (long)rint(kx * L / kTwoPi) % L;
+        long m2 = (long)rint(ky * L / kTwoPi) % L;
+        if (m1 < 0) m1 += L;
+        if (m2 < 0) m2 += L;
+        return (int)(m1 * L + m2);
+    }
+    const double x = kx - kTwoPi * rint(kx / kTwoPi);
+    const double y = ky - kTwoPi * rint(ky / kTwoPi);
+    const double th = atan2(y, x);
+    long j = (long)floor(th / (kTwoPi / N) + 0.5);
+    j %= N;
+    if (j < 0) j += N;
+    return (int)j;
+}
+
+// part[f][Q][p] = patch of (Q - p) for f = 0 (pp) and of (p + Q) for f = 1 (ph).
+__global__ void partner_map_kernel(const double *__restrict__ Qpp, const double *__restrict__ Qph,
+                                   const double *__restrict__ fkx, const double *__restrict__ fky,
+                                   uint8_t *__restrict__ part, int N, int M, int mode, int L)
+{
+    const int Q = blockIdx.x, f = blockIdx.z;
+    const long NN = (long)N * N;
+    const double *Qt = f == 0 ? Qpp : Qph;
+    const double Qx = Qt[2 * Q], Qy = Qt[2 * Q + 1];
+    uint8_t *row = part + ((long)f * NN + Q) * (long)M;
+    for (int p = blockIdx.y * blockDim.x + threadIdx.x; p < M; p += gridDim.y * blockDim.x) {
+        const double px = fkx[p], py = fky[p];
+        const double qx = f == 0 ? Qx - px : px + Qx;
+        const double qy = f == 0 ? Qy - py : py + Qy;
+        row[p] = (uint8_t)project_patch(qx, qy, N, mode, L);
+    }
+}
+
+template <typename R>
+static qpfrg_status alloc_fine(qpfrg_ctx *c, FineTable<R> &t)
+{
+    const size_t M = c->pb.M;
+    R **fields[] = {&t.kx, &t.ky, &t.cx, &t.sx, &t.cy, &t.sy, &t.xi, &t.w};
+    for (R **f : fields) {
+        cudaError_t e = cudaMalloc((void **)f, M * sizeof(R));
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc(fine table)");
+    }
+    std::vector<R> h(M);
+    auto put = [&](R *dst, auto fn) -> qpfrg_status {
+        for (size_t p = 0; p < M; ++p) h[p] = (R)fn(p);
+        cudaError_t e = cudaMemcpy(dst, h.data(), M * sizeof(R), cudaMemcpyHostToDevice);
+        return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "upload fine table");
+    };
+    const std::vector<double> &fk = c->fk;
+    qpfrg_status s;
+    if ((s = put(t.kx, [&](size_t p) { return fk[2 * p]; })) != QPFRG_OK) return s;
+    if ((s = put(t.ky, [&](size_t p) { return fk[2 * p + 1]; })) != QPFRG_OK) return s;
+    if ((s = put(t.cx, [&](size_t p) { return std::cos(fk[2 * p]); })) != QPFRG_OK) return s;
+    if ((s = put(t.sx, [&](size_t p) { return std::sin(fk[2 * p]); })) != QPFRG_OK) return s;
+    if ((s = put(t.cy, [&](size_t p) { return std::cos(fk[2 * p + 1]); })) != QPFRG_OK) return s;
+    if ((s = put(t.sy, [&](size_t p) { return std::sin(fk[2 * p + 1]); })) != QPFRG_OK) return s;
+    if ((s = put(t.xi, [&](size_t p) { return host_xi(c->pb, fk[2 * p], fk[2 * p + 1]); })) != QPFRG_OK)
+        return s;
+    if ((s = put(t.w, [&](size_t p) { return c->fw[p]; })) != QPFRG_OK) return s;
+    return QPFRG_OK;
+}
+
+template <typename R>
+static qpfrg_status alloc_transfer(qpfrg_ctx *c, TransferTable<R> &t, const std::vector<double> &Q)
+{
+    const size_t NN = (size_t)c->pb.N * c->pb.N;
+    R **fields[] = {&t.cx, &t.sx, &t.cy, &t.sy};
+    for (R **f : fields) {
+        cudaError_t e = cudaMalloc((void **)f, NN * sizeof(R));
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc(transfer table)");
+    }
+    std::vector<R> h(NN);
+    for (int comp = 0; comp < 4; ++comp) {
+        for (size_t q = 0; q < NN; ++q) {
+            const double v = Q[2 * q + (comp >= 2 ? 1 : 0)];
+            h[q] = (R)((comp % 2 == 0) ? std::cos(v) : std::sin(v));
+        }
+        cudaError_t e = cudaMemcpy(*fields[comp], h.data(), NN * sizeof(R), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(c, e, "upload transfer table");
+    }
+    return QPFRG_OK;
+}
+
+qpfrg_status upload_geometry(qpfrg_ctx *c)
+{
+    const int N = c->pb.N;
+    const size_t NN = (size_t)N * N;
+    std::vector<double> Qpp(2 * NN), Qph(2 * NN);
+    for (int x = 0; x < N; ++x)
+        for (int y = 0; y < N; ++y) {
+            const size_t q = (size_t)x * N + y;
+            Qpp[2 * q] = c->kf[2 * x] + c->kf[2 * y];
+            Qpp[2 * q + 1] = c->kf[2 * x + 1] + c->kf[2 * y + 1];
+            Qph[2 * q] = c->kf[2 * x] - c->kf[2 * y];
+            Qph[2 * q + 1] = c->kf[2 * x + 1] - c->kf[2 * y + 1];
+        }
+    qpfrg_status s;
+    if ((s = alloc_fine(c, c->f64)) != QPFRG_OK) return s;
+    if ((s = alloc_fine(c, c->f32)) != QPFRG_OK) return s;
+    if ((s = alloc_transfer(c, c->qpp64, Qpp)) != QPFRG_OK) return s;
+    if ((s = alloc_transfer(c, c->qph64, Qph)) != QPFRG_OK) return s;
+    if ((s = alloc_transfer(c, c->qpp32, Qpp)) != QPFRG_OK) return s;
+    if ((s = alloc_transfer(c, c->qph32, Qph)) != QPFRG_OK) return s;
+
+    cudaError_t e;
+    if ((e = cudaMalloc((void **)&c->d_kf, 2 * N * sizeof(double))) != cudaSuccess)
+        return cuda_fail(c, e, "cudaMalloc(kf)");
+    if ((e = cudaMemcpy(c->d_kf, c->kf.data(), 2 * N * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(c, e, "upload kf");
+    if ((e = cudaMalloc((void **)&c->d_Qpp, 2 * NN * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc((void **)&c->d_Qph, 2 * NN * sizeof(double))) != cudaSuccess)
+        return cuda_fail(c, e, "cudaMalloc(Q)");
+    cudaMemcpy(c->d_Qpp, Qpp.data(), 2 * NN * sizeof(double), cudaMemcpyHostToDevice);
+    if ((e = cudaMemcpy(c->d_Qph, Qph.data(), 2 * NN * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(c, e, "upload Q");
+
+    const size_t part_bytes = 2 * NN * (size_t)c->pb.M;
+    if ((e = cudaMalloc((void **)&c->d_part, part_bytes)) != cudaSuccess)
+        return cuda_fail(c, e, "cudaMalloc(partner maps)");
+    const int pblocks = div_up(c->pb.M, 256 * 4);
+    dim3 grid((unsigned)NN, pblocks < 1 ? 1 : (pblocks > 65535 ? 65535 : pblocks), 2);
+    prof_begin(c);
+    partner_map_kernel<<<grid, 256, 0, c->stream>>>(c->d_Qpp, c->d_Qph, c->f64.kx, c->f64.ky, c->d_part,
+                                                    N, c->pb.M, c->pb.mode, c->pb.L);
+    prof_end(c, K_PARTNER_MAP);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "partner_map_kernel");
+    return QPFRG_OK;
+}
+
+}  // namespace qpfrg

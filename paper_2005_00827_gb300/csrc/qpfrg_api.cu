@@ -1,0 +1,629 @@
+// C ABI of the qpfrg library: context management, right-hand side,
+// self-energy/Z, the RK4 flow driver, checkpoints and the kernel profiler.
+// The declarations and their contracts are in include/qpfrg.h.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "qpfrg_internal.h"
+
+using namespace qpfrg;
+
+namespace {
+
+const char *const kKernelNames[K_COUNT] = {
+    "partner_map", "bubble", "contract_pp", "contract_cr", "contract_d", "sigma_z",
+    "sigma_hist", "sigma_grid", "z_update", "rk_stage", "rk_final", "convert_f32",
+};
+
+struct PendingEvent {
+    int id;
+    cudaEvent_t a, b;
+};
+
+struct Profiler {
+    std::vector<PendingEvent> pending;
+    std::vector<cudaEvent_t> spare;
+};
+
+Profiler *prof_of(qpfrg_ctx *c) { return reinterpret_cast<Profiler *>(c->profiler); }
+
+constexpr uint32_t kStateMagic = 0x52465051u;  // "QPFR"
+constexpr uint32_t kStateVersion = 1u;
+
+struct StateHeader {
+    uint32_t magic;
+    uint32_t version;
+    int32_t N;
+    int32_t status;
+    int64_t steps;
+    double lambda;
+    double max_abs_v;
+    double lambda_c;
+    double reserved[2];
+};
+static_assert(sizeof(StateHeader) == 64, "state header is 64 bytes");
+
+qpfrg_status set_err(qpfrg_ctx *c, qpfrg_status s, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+cudaEvent_t take_event(Profiler *p)
+{
+    if (!p->spare.empty()) {
+        cudaEvent_t e = p->spare.back();
+        p->spare.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void flush_profile(qpfrg_ctx *c)
+{
+    Profiler *p = prof_of(c);
+    if (!p || p->pending.empty()) return;
+    cudaStreamSynchronize(c->stream);
+    for (const PendingEvent &pe : p->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, pe.a, pe.b) == cudaSuccess) {
+            c->slots[pe.id].ms += ms;
+            c->slots[pe.id].launches += 1;
+        }
+        p->spare.push_back(pe.a);
+        p->spare.push_back(pe.b);
+    }
+    p->pending.clear();
+}
+
+bool finite_all(const double *x, size_t n, double *maxabs)
+{
+    double m = 0.0;
+    for (size_t i = 0; i < n; ++i) {
+        if (!std::isfinite(x[i])) return false;
+        m = std::fmax(m, std::fabs(x[i]));
+    }
+    if (maxabs) *maxabs = m;
+    return true;
+}
+
+template <typename T>
+qpfrg_status dev_alloc(qpfrg_ctx *c, T **p, size_t count, const char *what)
+{
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        c->err = std::string("cudaMalloc failed for ") + what + ": " + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? QPFRG_ERR_OOM : QPFRG_ERR_CUDA;
+    }
+    return QPFRG_OK;
+}
+
+long n3_of(const qpfrg_ctx *c) { return (long)c->pb.N * c->pb.N * c->pb.N; }
+
+}  // namespace
+
+namespace qpfrg {
+
+qpfrg_status cuda_fail(qpfrg_ctx *c, cudaError_t e, const char *what)
+{
+    if (c) c->err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? QPFRG_ERR_OOM : QPFRG_ERR_CUDA;
+}
+
+void prof_begin(qpfrg_ctx *c)
+{
+    if (!c->prof) return;
+    Profiler *p = prof_of(c);
+    if (p->pending.size() >= 8192) flush_profile(c);
+    PendingEvent pe{-1, take_event(p), take_event(p)};
+    cudaEventRecord(pe.a, c->stream);
+    p->pending.push_back(pe);
+}
+
+void prof_end(qpfrg_ctx *c, int id)
+{
+    if (!c->prof) return;
+    Profiler *p = prof_of(c);
+    PendingEvent &pe = p->pending.back();
+    pe.id = id;
+    cudaEventRecord(pe.b, c->stream);
+}
+
+}  // namespace qpfrg
+
+// ---------------------------------------------------------------------------
+// public API
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void qpfrg_default_options(qpfrg_options *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->channel_mask = QPFRG_CH_ALL;
+    o->z_feedback = 0;
+    o->propagator = QPFRG_PROP_PAPER;
+    o->precision = QPFRG_FP64;
+    o->eta = 0.02;
+    o->n_omega = 0;
+    o->omega_min = -4.0;
+    o->omega_max = 4.0;
+    o->stop_abs_v = 20.0;
+    o->step = std::log(0.98);
+    o->lambda_end = 0.05;
+    o->z_max = 2.0;
+    o->max_steps = 100000;
+    o->T_fixed = 0.1;
+    o->timeout_s = 0.0;
+}
+
+const char *qpfrg_version(void) { return "qpfrg 0.1 (sm_103a)"; }
+
+const char *qpfrg_last_error(qpfrg_t ctx)
+{
+    if (!ctx) return "no context";
+    return ctx->err.c_str();
+}
+
+void qpfrg_destroy(qpfrg_t c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    cudaGetLastError();
+    void *ptrs[] = {c->f64.kx, c->f64.ky, c->f64.cx, c->f64.sx, c->f64.cy, c->f64.sy, c->f64.xi, c->f64.w,
+                    c->f32.kx, c->f32.ky, c->f32.cx, c->f32.sx, c->f32.cy, c->f32.sy, c->f32.xi, c->f32.w,
+                    c->qpp64.cx, c->qpp64.sx, c->qpp64.cy, c->qpp64.sy, c->qph64.cx, c->qph64.sx,
+                    c->qph64.cy, c->qph64.sy, c->qpp32.cx, c->qpp32.sx, c->qpp32.cy, c->qpp32.sy,
+                    c->qph32.cx, c->qph32.sx, c->qph32.cy, c->qph32.sy, c->d_kf, c->d_Qpp, c->d_Qph,
+                    c->d_part, c->d_B, c->d_V, c->d_Z, c->d_Vs, c->d_k, c->d_acc, c->d_ones, c->d_Vf,
+                    c->d_Zwork, c->d_sig, c->d_hist, c->d_red};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (c->h_red) cudaFreeHost(c->h_red);
+    Profiler *p = prof_of(c);
+    if (p) {
+        for (auto &pe : p->pending) {
+            cudaEventDestroy(pe.a);
+            cudaEventDestroy(pe.b);
+        }
+        for (auto e : p->spare) cudaEventDestroy(e);
+        delete p;
+    }
+    delete c;
+}
+
+qpfrg_status qpfrg_create(const qpfrg_lattice *lattice, int n_p, const qpfrg_fine_grid *grid, double U,
+                          double lambda0, qpfrg_regulator regulator, const qpfrg_options *options,
+                          void *cuda_stream, qpfrg_t *out)
+{
+    if (!out) return QPFRG_ERR_INVALID;
+    *out = nullptr;
+    if (!lattice || !grid) return QPFRG_ERR_INVALID;
+    qpfrg_ctx *c = new (std::nothrow) qpfrg_ctx();
+    if (!c) return QPFRG_ERR_OOM;
+    c->profiler = new (std::nothrow) Profiler();
+    if (!c->profiler) {
+        delete c;
+        return QPFRG_ERR_OOM;
+    }
+    auto fail = [&](qpfrg_status s) {
+        fprintf(stderr, "qpfrg_create: %s\n", c->err.c_str());
+        qpfrg_destroy(c);
+        return s;
+    };
+    if (options)
+        c->opt = *options;
+    else
+        qpfrg_default_options(&c->opt);
+
+    // ---- validation -------------------------------------------------------
+    Problem &pb = c->pb;
+    pb.t = lattice->t;
+    pb.tp = lattice->tp;
+    pb.mu = lattice->mu;
+    pb.mode = grid->mode;
+    pb.N = n_p;
+    pb.regulator = regulator;
+    pb.propagator = c->opt.propagator;
+    pb.channels = c->opt.channel_mask & QPFRG_CH_ALL;
+    pb.T_fixed = c->opt.T_fixed;
+    pb.eta = c->opt.eta;
+    c->U = U;
+    c->lambda0 = lambda0;
+    const bool tflow = regulator == QPFRG_REG_TEMPERATURE;
+    if (!std::isfinite(pb.t) || !std::isfinite(pb.tp) || !std::isfinite(pb.mu) || !std::isfinite(U) ||
+        !std::isfinite(lambda0))
+        return fail(set_err(c, QPFRG_ERR_INVALID, "non-finite lattice, U or lambda0"));
+    if (regulator != QPFRG_REG_TEMPERATURE && regulator != QPFRG_REG_INTERACTION)
+        return fail(set_err(c, QPFRG_ERR_INVALID, "unknown regulator"));
+    if (tflow ? !(lambda0 > 0.0) : !(lambda0 >= 0.0))
+        return fail(set_err(c, QPFRG_ERR_INVALID, "lambda0 must be T > 0 (T-flow) or g >= 0 (g-flow)"));
+    if (!tflow && !(pb.T_fixed > 0.0))
+        return fail(set_err(c, QPFRG_ERR_INVALID, "interaction flow needs T_fixed > 0"));
+    if (c->opt.precision != QPFRG_FP64 && c->opt.precision != QPFRG_MIXED) {
+        if (c->opt.precision == QPFRG_MIXED_TC)
+            return fail(set_err(c, QPFRG_ERR_UNSUPPORTED, "MIXED_TC precision is not implemented"));
+        return fail(set_err(c, QPFRG_ERR_INVALID, "unknown precision"));
+    }
+    if (pb.propagator != QPFRG_PROP_PAPER && pb.propagator != QPFRG_PROP_QP)
+        return fail(set_err(c, QPFRG_ERR_INVALID, "unknown propagator mode"));
+    if (c->opt.z_feedback && !tflow)
+        return fail(set_err(c, QPFRG_ERR_UNSUPPORTED, "Z feedback is implemented for the temperature flow"));
+    if (!(pb.eta > 0.0)) return fail(set_err(c, QPFRG_ERR_INVALID, "eta must be > 0"));
+    if (c->opt.n_omega < 0 || (c->opt.n_omega > 0 && !(c->opt.omega_max >= c->opt.omega_min)))
+        return fail(set_err(c, QPFRG_ERR_INVALID, "bad frequency grid"));
+    if (!(c->opt.stop_abs_v > 0.0) || !(c->opt.z_max > 0.0) || c->opt.max_steps < 0)
+        return fail(set_err(c, QPFRG_ERR_INVALID, "bad stop_abs_v, z_max or max_steps"));
+    if (tflow ? !(c->opt.step < 0.0 && c->opt.lambda_end > 0.0) : !(c->opt.step > 0.0))
+        return fail(set_err(c, QPFRG_ERR_INVALID, "T-flow needs step < 0 and lambda_end > 0; g-flow step > 0"));
+    if (pb.mode == QPFRG_GRID_LATTICE) {
+        int L = (int)std::llround(std::sqrt((double)n_p));
+        if (L < 1 || L * L != n_p || n_p > 256)
+            return fail(set_err(c, QPFRG_ERR_INVALID, "lattice mode needs n_p = L*L <= 256"));
+        pb.L = L;
+        pb.P = 1;
+        c->n_theta = c->n_r = 1;
+    } else if (pb.mode == QPFRG_GRID_WEDGE) {
+        if (n_p < 4 || n_p % 4 != 0 || n_p > 256)
+            return fail(set_err(c, QPFRG_ERR_INVALID, "wedge mode needs n_p a multiple of 4, 4 <= n_p <= 256"));
+        if (grid->n_theta < 1 || grid->n_r < 2 || grid->n_r % 2 != 0)
+            return fail(set_err(c, QPFRG_ERR_INVALID, "fine grid needs n_theta >= 1 and even n_r >= 2"));
+        c->n_theta = grid->n_theta;
+        c->n_r = grid->n_r;
+        pb.P = grid->n_theta * grid->n_r;
+        pb.L = 0;
+        if (pb.P > 2048)
+            return fail(set_err(c, QPFRG_ERR_UNSUPPORTED, "more than 2048 fine points per patch"));
+    } else {
+        return fail(set_err(c, QPFRG_ERR_INVALID, "unknown fine-grid mode"));
+    }
+    pb.M = pb.N * pb.P;
+
+    // ---- device ------------------------------------------------------------
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return fail(set_err(c, QPFRG_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e)));
+    }
+    cudaGetDevice(&c->device);
+    c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+
+    qpfrg_status s;
+    if ((s = build_host_geometry(c)) != QPFRG_OK) return fail(s);
+    if ((s = upload_geometry(c)) != QPFRG_OK) return fail(s);
+
+    const size_t N = pb.N, n3 = N * N * N, n4 = n3 * N;
+    const size_t rsz = c->opt.precision == QPFRG_FP64 ? sizeof(double) : sizeof(float);
+    c->B_bytes = 2 * n4 * rsz;
+    if (std::getenv("QPFRG_TEST_FAIL_ALLOC")) {   // host-side fault injection for tests
+        c->err = "allocation failure injected by QPFRG_TEST_FAIL_ALLOC";
+        return fail(QPFRG_ERR_OOM);
+    }
+    if ((s = dev_alloc(c, (unsigned char **)&c->d_B, c->B_bytes, "bubble tables")) != QPFRG_OK) return fail(s);
+    if ((s = dev_alloc(c, &c->d_V, n3, "V")) || (s = dev_alloc(c, &c->d_Vs, n3, "V stage")) ||
+        (s = dev_alloc(c, &c->d_k, n3, "k")) || (s = dev_alloc(c, &c->d_acc, n3, "acc")) ||
+        (s = dev_alloc(c, &c->d_Vf, n3, "V fp32")) || (s = dev_alloc(c, &c->d_Z, N, "Z")) ||
+        (s = dev_alloc(c, &c->d_Zwork, N, "Z work")) || (s = dev_alloc(c, &c->d_ones, N, "ones")) ||
+        (s = dev_alloc(c, &c->d_sig, 2 * N, "sigma chord")) || (s = dev_alloc(c, &c->d_red, 2, "reduction")))
+        return fail(s);
+    e = cudaMallocHost((void **)&c->h_red, 2 * sizeof(unsigned long long));
+    if (e != cudaSuccess) return fail(cuda_fail(c, e, "cudaMallocHost"));
+
+    // state: V = U, Z = 1 at lambda0
+    std::vector<double> h(n3, U);
+    e = cudaMemcpy(c->d_V, h.data(), n3 * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(cuda_fail(c, e, "init V"));
+    h.assign(N, 1.0);
+    cudaMemcpy(c->d_Z, h.data(), N * sizeof(double), cudaMemcpyHostToDevice);
+    e = cudaMemcpy(c->d_ones, h.data(), N * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(cuda_fail(c, e, "init Z"));
+    c->lambda = lambda0;
+    c->steps = 0;
+    c->status = QPFRG_FLOW_RUNNING;
+    c->max_abs_v = std::fabs(U);
+    c->lambda_c = 0.0;
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(cuda_fail(c, e, "create"));
+    *out = c;
+    return QPFRG_OK;
+}
+
+qpfrg_status qpfrg_rhs(qpfrg_t c, double lambda, const double *d_V, const double *d_Z, double *d_dV)
+{
+    if (!c) return QPFRG_ERR_INVALID;
+    if (!d_V || !d_dV || d_V == d_dV) return set_err(c, QPFRG_ERR_INVALID, "bad V / dV pointers");
+    const bool tflow = c->pb.regulator == QPFRG_REG_TEMPERATURE;
+    if (!std::isfinite(lambda) || (tflow && !(lambda > 0.0)))
+        return set_err(c, QPFRG_ERR_INVALID, "lambda must be finite (and T > 0)");
+    const long n3 = n3_of(c);
+    const void *Vin = d_V;
+    qpfrg_status s;
+    if (c->opt.precision == QPFRG_MIXED) {
+        if ((s = launch_convert_f32(c, d_V, c->d_Vf, n3)) != QPFRG_OK) return s;
+        Vin = c->d_Vf;
+    }
+    if ((s = launch_bubbles(c, lambda, d_Z ? d_Z : c->d_ones)) != QPFRG_OK) return s;
+    cudaError_t e = cudaMemsetAsync(d_dV, 0, n3 * sizeof(double), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "memset dV");
+    return launch_contractions(c, Vin, 1.0, d_dV);
+}
+
+qpfrg_status qpfrg_selfenergy(qpfrg_t c, double lambda, const double *d_V, const double *d_Z,
+                              double *d_sigma_re, double *d_sigma_im, double *d_Z_out)
+{
+    if (!c) return QPFRG_ERR_INVALID;
+    if (c->pb.regulator != QPFRG_REG_TEMPERATURE)
+        return set_err(c, QPFRG_ERR_UNSUPPORTED, "self-energy is implemented for the temperature flow");
+    if (!d_V || !(lambda > 0.0) || !std::isfinite(lambda)) return set_err(c, QPFRG_ERR_INVALID, "bad V or T");
+    const double *Z = d_Z ? d_Z : c->d_ones;
+    qpfrg_status s;
+    if (d_Z_out && (s = launch_sigma_z(c, lambda, d_V, Z, d_Z_out)) != QPFRG_OK) return s;
+    if (c->opt.n_omega > 0 && d_sigma_re && d_sigma_im)
+        return launch_sigma_grid(c, lambda, d_V, Z, d_sigma_re, d_sigma_im);
+    return QPFRG_OK;
+}
+
+static void fill_result(const qpfrg_ctx *c, qpfrg_flow_result *out)
+{
+    if (!out) return;
+    out->status = c->status;
+    out->steps = c->steps;
+    out->lambda = c->lambda;
+    out->lambda_c = c->lambda_c;
+    out->max_abs_v = c->max_abs_v;
+}
+
+// One RK4 step of the flow state (see qpfrg.h).
+static qpfrg_status do_step(qpfrg_ctx *c)
+{
+    const bool tflow = c->pb.regulator == QPFRG_REG_TEMPERATURE;
+    const double x = tflow ? std::log(c->lambda) : c->lambda;
+    const double x_end = tflow ? std::log(c->opt.lambda_end) : c->opt.lambda_end;
+    if ((tflow && x - x_end <= 1e-12) || (!tflow && x_end - x <= 1e-12)) {
+        c->status = QPFRG_FLOW_REACHED_END;
+        return QPFRG_OK;
+    }
+    double h = c->opt.step;
+    if ((tflow && x + h < x_end) || (!tflow && x + h > x_end)) h = x_end - x;
+    const long n3 = n3_of(c);
+    const int N = c->pb.N;
+    const bool mixed = c->opt.precision == QPFRG_MIXED;
+    qpfrg_status s;
+    cudaError_t e;
+
+    if (c->opt.z_feedback) {
+        const double T = tflow ? c->lambda : c->pb.T_fixed;
+        if ((s = launch_sigma_z(c, T, c->d_V, c->d_Z, c->d_Zwork)) != QPFRG_OK) return s;
+        std::vector<double> hz(N);
+        e = cudaMemcpyAsync(hz.data(), c->d_Zwork, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "read Z");
+        for (int j = 0; j < N; ++j) {
+            if (!std::isfinite(hz[j])) {
+                c->status = QPFRG_FLOW_NONFINITE;
+                return QPFRG_OK;
+            }
+            if (!(hz[j] > 0.0 && hz[j] <= c->opt.z_max)) {
+                c->status = QPFRG_FLOW_Z_OUT_OF_RANGE;
+                return QPFRG_OK;
+            }
+        }
+        e = cudaMemcpyAsync(c->d_Z, c->d_Zwork, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "copy Z");
+    }
+
+    const void *Vin = c->d_V;
+    if (mixed) {
+        if ((s = launch_convert_f32(c, c->d_V, c->d_Vf, n3)) != QPFRG_OK) return s;
+        Vin = c->d_Vf;
+    }
+    const double cst[4] = {0.0, 0.5, 0.5, 1.0};
+    for (int st = 0; st < 4; ++st) {
+        const double xs = x + cst[st] * h;
+        const double lam = tflow ? std::exp(xs) : xs;
+        const double scale = tflow ? lam : 1.0;   // dV/d ln T = T dV/dT
+        if ((s = launch_bubbles(c, lam, c->d_Z)) != QPFRG_OK) return s;
+        if ((e = cudaMemsetAsync(c->d_k, 0, n3 * sizeof(double), c->stream)) != cudaSuccess)
+            return cuda_fail(c, e, "memset k");
+        if ((s = launch_contractions(c, Vin, scale, c->d_k)) != QPFRG_OK) return s;
+        if (st < 3) {
+            s = launch_rk_stage(c, st + 1, h, c->d_V, c->d_k, c->d_acc, mixed ? nullptr : c->d_Vs,
+                                mixed ? c->d_Vf : nullptr);
+            if (s != QPFRG_OK) return s;
+            Vin = mixed ? (const void *)c->d_Vf : (const void *)c->d_Vs;
+        } else if ((s = launch_rk_final(c, h, c->d_V, c->d_acc, c->d_k)) != QPFRG_OK) {
+            return s;
+        }
+    }
+    e = cudaMemcpyAsync(c->h_red, c->d_red, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "flow step");
+    double m_new;
+    std::memcpy(&m_new, &c->h_red[0], sizeof(double));
+    const double x_new = x + h;
+    c->steps += 1;
+    c->lambda = tflow ? std::exp(x_new) : x_new;
+    const double m_old = c->max_abs_v;
+    c->max_abs_v = m_new;
+    if (c->h_red[1]) {
+        c->status = QPFRG_FLOW_NONFINITE;
+        return QPFRG_OK;
+    }
+    if (m_new > c->opt.stop_abs_v) {
+        const double sfrac = (std::log(c->opt.stop_abs_v) - std::log(m_old)) / (std::log(m_new) - std::log(m_old));
+        const double xc = x + sfrac * h;
+        c->lambda_c = tflow ? std::exp(xc) : xc;
+        c->status = QPFRG_FLOW_DIVERGED;
+        return QPFRG_OK;
+    }
+    if ((tflow && x_new - x_end <= 1e-12) || (!tflow && x_end - x_new <= 1e-12)) c->status = QPFRG_FLOW_REACHED_END;
+    return QPFRG_OK;
+}
+
+qpfrg_status qpfrg_step(qpfrg_t c, int n_steps, qpfrg_flow_result *out)
+{
+    if (!c || n_steps < 0) return QPFRG_ERR_INVALID;
+    for (int i = 0; i < n_steps && c->status == QPFRG_FLOW_RUNNING; ++i) {
+        qpfrg_status s = do_step(c);
+        if (s != QPFRG_OK) {
+            fill_result(c, out);
+            return s;
+        }
+    }
+    fill_result(c, out);
+    return QPFRG_OK;
+}
+
+qpfrg_status qpfrg_flow(qpfrg_t c, qpfrg_flow_result *out)
+{
+    if (!c) return QPFRG_ERR_INVALID;
+    const auto t0 = std::chrono::steady_clock::now();
+    int done = 0;
+    while (c->status == QPFRG_FLOW_RUNNING) {
+        if (done >= c->opt.max_steps) {
+            c->status = QPFRG_FLOW_MAX_STEPS;
+            break;
+        }
+        if (c->opt.timeout_s > 0.0) {
+            const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (el > c->opt.timeout_s) {
+                c->status = QPFRG_FLOW_TIMEOUT;
+                break;
+            }
+        }
+        qpfrg_status s = do_step(c);
+        if (s != QPFRG_OK) {
+            fill_result(c, out);
+            return s;
+        }
+        ++done;
+    }
+    fill_result(c, out);
+    return QPFRG_OK;
+}
+
+qpfrg_status qpfrg_state_size(qpfrg_t c, size_t *bytes)
+{
+    if (!c || !bytes) return QPFRG_ERR_INVALID;
+    *bytes = sizeof(StateHeader) + (n3_of(c) + c->pb.N) * sizeof(double);
+    return QPFRG_OK;
+}
+
+qpfrg_status qpfrg_get_state(qpfrg_t c, void *h_buf, size_t bytes)
+{
+    size_t need = 0;
+    if (qpfrg_state_size(c, &need) != QPFRG_OK || !h_buf) return QPFRG_ERR_INVALID;
+    if (bytes < need) return set_err(c, QPFRG_ERR_INVALID, "state buffer too small");
+    StateHeader hd{};
+    hd.magic = kStateMagic;
+    hd.version = kStateVersion;
+    hd.N = c->pb.N;
+    hd.status = c->status;
+    hd.steps = c->steps;
+    hd.lambda = c->lambda;
+    hd.max_abs_v = c->max_abs_v;
+    hd.lambda_c = c->lambda_c;
+    std::memcpy(h_buf, &hd, sizeof(hd));
+    unsigned char *p = static_cast<unsigned char *>(h_buf) + sizeof(hd);
+    cudaError_t e = cudaMemcpyAsync(p, c->d_V, n3_of(c) * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p + n3_of(c) * sizeof(double), c->d_Z, c->pb.N * sizeof(double),
+                            cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "get_state");
+}
+
+qpfrg_status qpfrg_set_state(qpfrg_t c, const void *h_buf, size_t bytes)
+{
+    size_t need = 0;
+    if (qpfrg_state_size(c, &need) != QPFRG_OK || !h_buf) return QPFRG_ERR_INVALID;
+    if (bytes != need) return set_err(c, QPFRG_ERR_INVALID, "state image has the wrong size");
+    StateHeader hd;
+    std::memcpy(&hd, h_buf, sizeof(hd));
+    if (hd.magic != kStateMagic || hd.version != kStateVersion || hd.N != c->pb.N)
+        return set_err(c, QPFRG_ERR_INVALID, "state image header does not match this context");
+    if (hd.status < QPFRG_FLOW_RUNNING || hd.status > QPFRG_FLOW_TIMEOUT || hd.steps < 0)
+        return set_err(c, QPFRG_ERR_INVALID, "state image has a bad status or step count");
+    const double *V = reinterpret_cast<const double *>(static_cast<const unsigned char *>(h_buf) + sizeof(hd));
+    const double *Z = V + n3_of(c);
+    double m = 0.0;
+    if (!finite_all(V, n3_of(c), &m) || !finite_all(Z, c->pb.N, nullptr) || !std::isfinite(hd.lambda))
+        return set_err(c, QPFRG_ERR_NONFINITE, "state image holds NaN or Inf");
+    cudaError_t e = cudaMemcpyAsync(c->d_V, V, n3_of(c) * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_Z, Z, c->pb.N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set_state");
+    c->status = hd.status;
+    c->steps = (int)hd.steps;
+    c->lambda = hd.lambda;
+    c->lambda_c = hd.lambda_c;
+    c->max_abs_v = m;
+    return QPFRG_OK;
+}
+
+qpfrg_status qpfrg_read_state(qpfrg_t c, double *d_V, double *d_Z)
+{
+    if (!c) return QPFRG_ERR_INVALID;
+    cudaError_t e = cudaSuccess;
+    if (d_V) e = cudaMemcpyAsync(d_V, c->d_V, n3_of(c) * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess && d_Z)
+        e = cudaMemcpyAsync(d_Z, c->d_Z, c->pb.N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "read_state");
+}
+
+qpfrg_status qpfrg_geometry(qpfrg_t c, int *n_p, int *n_fine, double *h_kf, double *h_fine)
+{
+    if (!c) return QPFRG_ERR_INVALID;
+    if (n_p) *n_p = c->pb.N;
+    if (n_fine) *n_fine = c->pb.M;
+    if (h_kf) std::memcpy(h_kf, c->kf.data(), c->kf.size() * sizeof(double));
+    if (h_fine)
+        for (int p = 0; p < c->pb.M; ++p) {
+            h_fine[4 * p] = c->fk[2 * p];
+            h_fine[4 * p + 1] = c->fk[2 * p + 1];
+            h_fine[4 * p + 2] = c->fw[p];
+            h_fine[4 * p + 3] = c->fpatch[p];
+        }
+    return QPFRG_OK;
+}
+
+qpfrg_status qpfrg_set_profiling(qpfrg_t c, int on)
+{
+    if (!c) return QPFRG_ERR_INVALID;
+    if (!on) flush_profile(c);
+    c->prof = on != 0;
+    return QPFRG_OK;
+}
+
+qpfrg_status qpfrg_profile_reset(qpfrg_t c)
+{
+    if (!c) return QPFRG_ERR_INVALID;
+    flush_profile(c);
+    for (auto &s : c->slots) s = ProfileSlot();
+    return QPFRG_OK;
+}
+
+int qpfrg_profile_count(void) { return K_COUNT; }
+
+const char *qpfrg_profile_name(int id) { return (id >= 0 && id < K_COUNT) ? kKernelNames[id] : ""; }
+
+qpfrg_status qpfrg_profile_get(qpfrg_t c, int id, double *ms, long long *launches)
+{
+    if (!c || id < 0 || id >= K_COUNT) return QPFRG_ERR_INVALID;
+    flush_profile(c);
+    if (ms) *ms = c->slots[id].ms;
+    if (launches) *launches = c->slots[id].launches;
+    return QPFRG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,157 @@
+// Internal declarations of the qpfrg CUDA library (sm_103a).  Not part of
+// the public ABI (include/qpfrg.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/qpfrg.h"
+
+namespace qpfrg {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kTwoPi = 2.0 * kPi;
+
+// Kernel ids of the built-in profiler (order = qpfrg_profile_name).
+enum KernelId {
+    K_PARTNER_MAP = 0,
+    K_BUBBLE,
+    K_CONTRACT_PP,
+    K_CONTRACT_CR,
+    K_CONTRACT_D,
+    K_SIGMA_Z,
+    K_SIGMA_HIST,
+    K_SIGMA_GRID,
+    K_Z_UPDATE,
+    K_RK_STAGE,
+    K_RK_FINAL,
+    K_CONVERT,
+    K_COUNT
+};
+
+// Problem constants that every kernel needs, passed by value.
+struct Problem {
+    int N;           // patches
+    int M;           // fine points
+    int P;           // fine points per patch (wedge: n_theta*n_r; lattice: 1)
+    int mode;        // qpfrg_grid_mode
+    int L;           // lattice mode: side length
+    double t, tp, mu;
+    int regulator;   // qpfrg_regulator
+    int propagator;  // qpfrg_propagator
+    unsigned channels;
+    double T_fixed;
+    double eta;
+};
+
+// Device tables, FP64 and FP32 copies.  Fine points are stored patch-major:
+// point p = a*P + local, local = t*n_r + s (angle-major, radius-minor).
+template <typename R>
+struct FineTable {
+    R *kx, *ky;          // momenta
+    R *cx, *sx, *cy, *sy;// cos/sin of the momentum components
+    R *xi;               // bare dispersion
+    R *w;                // quadrature weight
+};
+
+template <typename R>
+struct TransferTable {   // for Q index x*N + y (pp: k_F(x)+k_F(y); ph: k_F(x)-k_F(y))
+    R *cx, *sx, *cy, *sy;
+};
+
+struct ProfileSlot {
+    double ms = 0.0;
+    long long launches = 0;
+};
+
+}  // namespace qpfrg
+
+struct qpfrg_ctx {
+    qpfrg::Problem pb{};
+    qpfrg_options opt{};
+    int n_theta = 0, n_r = 0;
+    double U = 0.0, lambda0 = 0.0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+
+    // host geometry (FP64)
+    std::vector<double> kf;      // N x 2
+    std::vector<double> fk;      // M x 2
+    std::vector<double> fw;      // M
+    std::vector<int> fpatch;     // M
+
+    // device geometry
+    qpfrg::FineTable<double> f64{};
+    qpfrg::FineTable<float> f32{};
+    qpfrg::TransferTable<double> qpp64{}, qph64{};
+    qpfrg::TransferTable<float> qpp32{}, qph32{};
+    double *d_kf = nullptr;      // N x 2
+    double *d_Qpp = nullptr, *d_Qph = nullptr;  // N^2 x 2 transfer momenta (FP64)
+    uint8_t *d_part = nullptr;   // 2 x N^2 x M partner patches (pp family, then ph)
+
+    // bubble tables B[f][Q][a][b] (FP32 or FP64 according to precision)
+    void *d_B = nullptr;
+    size_t B_bytes = 0;
+
+    // flow state and work buffers
+    double *d_V = nullptr, *d_Z = nullptr;
+    double *d_Vs = nullptr, *d_k = nullptr, *d_acc = nullptr, *d_ones = nullptr;
+    float *d_Vf = nullptr;       // FP32 copy of the RHS input (MIXED)
+    double *d_Zwork = nullptr;   // Z computed at the start of a step
+    double *d_sig = nullptr;     // N x 2 Re Sigma at xi_j +- 2T
+    double *d_hist = nullptr;    // Sigma frequency-grid histogram (lazily sized)
+    size_t hist_elems = 0;
+    unsigned long long *d_red = nullptr;  // [0] max|V| bits, [1] nonfinite flag
+    unsigned long long *h_red = nullptr;  // pinned mirror
+    double lambda = 0.0;
+    int steps = 0;
+    int status = QPFRG_FLOW_RUNNING;
+    double max_abs_v = 0.0;
+    double lambda_c = 0.0;
+
+    // profiling
+    bool prof = false;
+    qpfrg::ProfileSlot slots[qpfrg::K_COUNT];
+    void *profiler = nullptr;    // pending CUDA-event pairs (qpfrg_api.cu)
+
+    std::string err;
+};
+
+namespace qpfrg {
+
+// geometry.cu
+qpfrg_status build_host_geometry(qpfrg_ctx *c);
+qpfrg_status upload_geometry(qpfrg_ctx *c);
+
+// bubble.cu: fill the bubble tables for the given Lambda and Z (device ptr).
+qpfrg_status launch_bubbles(qpfrg_ctx *c, double lambda, const double *d_Z);
+
+// contract.cu: d_out (N^3 FP64) += scale * contraction of the bubble tables.
+// V input is FP64 (precision FP64) or FP32 (MIXED).
+qpfrg_status launch_contractions(qpfrg_ctx *c, const void *d_Vin, double scale, double *d_out);
+
+// sigma.cu
+qpfrg_status launch_sigma_z(qpfrg_ctx *c, double T, const double *d_V, const double *d_Z,
+                            double *d_Zout);
+qpfrg_status launch_sigma_grid(qpfrg_ctx *c, double T, const double *d_V, const double *d_Z,
+                               double *d_re, double *d_im);
+
+// ode.cu
+qpfrg_status launch_convert_f32(qpfrg_ctx *c, const double *d_in, float *d_out, long n);
+qpfrg_status launch_rk_stage(qpfrg_ctx *c, int stage, double h, const double *d_V,
+                             const double *d_k, double *d_acc, double *d_Vs, float *d_Vf);
+qpfrg_status launch_rk_final(qpfrg_ctx *c, double h, double *d_V, const double *d_acc,
+                             const double *d_k);
+qpfrg_status launch_check_finite(qpfrg_ctx *c, const double *d_x, long n);
+
+// profiling helpers (qpfrg_api.cu)
+void prof_begin(qpfrg_ctx *c);
+void prof_end(qpfrg_ctx *c, int id);
+qpfrg_status cuda_fail(qpfrg_ctx *c, cudaError_t e, const char *what);
+
+inline int div_up(long a, long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace qpfrg

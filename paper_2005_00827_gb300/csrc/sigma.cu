@@ -1,0 +1,383 @@
+// Real-frequency two-loop self-energy and the quasi-particle weight Z.
+//
+// Sigma(k_j, w) = sum_{p,q} w_p w_q Z_a Z_b Z_c W F / (w + i eta - E)
+//   r = k_j + p - q,  E = x_q + x_r - x_p,
+//   F = f_p (1-f_q)(1-f_r) + (1-f_p) f_q f_r,
+//   W = 2 V(k_j,p,q)^2 - V(k_j,p,q) V(k_j,p,r),
+// a, b, c the patches of p, q, r (the two-loop term of Sec. A.2/A.3 with the
+// static vertex and Z-weighted lines).  Z_j = (1 - slope)^-1, Eq.
+// (definition_Z), with the slope the chord of Re Sigma over xi_j +- 2T
+// ("from outside", Sec. 3.1.1).
+//
+// sigma_z_kernel evaluates Re Sigma exactly at the two chord frequencies.
+// Launch shape: grid (q blocks, patch a of p, target j), 256 threads, one q
+// per thread; the CTA stages patch a's points (k_j + p, cos/sin, Fermi
+// factors) and the vertex row V[j][a][:] in shared memory and loops over
+// them.  sigma_hist_kernel bins W F by pole energy E with moments 0..4 for
+// the frequency grid; sigma_grid_kernel resums the moments on the grid.
+#include "qpfrg_internal.h"
+
+namespace qpfrg {
+
+__device__ __forceinline__ float sexp(float x) { return __expf(x); }
+__device__ __forceinline__ double sexp(double x) { return exp(x); }
+__device__ __forceinline__ float sdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double sdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float srint(float x) { return rintf(x); }
+__device__ __forceinline__ double srint(double x) { return rint(x); }
+__device__ __forceinline__ float satan2(float y, float x) { return atan2f(y, x); }
+__device__ __forceinline__ double satan2(double y, double x) { return atan2(y, x); }
+__device__ __forceinline__ float sfloor(float x) { return floorf(x); }
+__device__ __forceinline__ double sfloor(double x) { return floor(x); }
+
+template <typename R>
+__device__ __forceinline__ void sfermi(R x, R invT, R &f, R &fc)
+{
+    const R e = sexp(-fabs(x) * invT);
+    const R lo = sdiv(e, R(1) + e), hi = sdiv(R(1), R(1) + e);
+    f = x > R(0) ? lo : hi;
+    fc = x > R(0) ? hi : lo;
+}
+
+template <typename R>
+__device__ __forceinline__ int sproject(R kx, R ky, int N, int mode, int L)
+{
+    const R tp = R(kTwoPi);
+    if (mode == QPFRG_GRID_LATTICE) {
+        int m1 = (int)srint(kx * R(L) / tp) % L;
+        int m2 = (int)srint(ky * R(L) / tp) % L;
+        if (m1 < 0) m1 += L;
+        if (m2 < 0) m2 += L;
+        return m1 * L + m2;
+    }
+    const R x = kx - tp * srint(kx / tp);
+    const R y = ky - tp * srint(ky / tp);
+    int j = (int)sfloor(satan2(y, x) / (tp / R(N)) + R(0.5));
+    j %= N;
+    if (j < 0) j += N;
+    return j;
+}
+
+template <typename R>
+struct SigmaArgs {
+    Problem pb;
+    FineTable<R> fine;
+    const double *kf;    // N x 2
+    const double *V;     // N^3 FP64
+    const double *Z;     // N
+    double *sig;         // [j][2]: Re Sigma at xi_j + 2T, xi_j - 2T
+    double T;
+    int nj;
+    const int *jlist;    // targets (may be NULL: j = blockIdx.z)
+    // frequency-grid histogram (sigma_hist_kernel)
+    double *hist;        // [j][moment 0..4][bin]
+    double e_min, inv_h;
+    int nbins;
+};
+
+template <typename R, bool HIST>
+__global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
+{
+    const int N = A.pb.N, P = A.pb.P, M = A.pb.M;
+    const int a = blockIdx.y;
+    const int jidx = blockIdx.z;
+    const int j = A.jlist ? A.jlist[jidx] : jidx;
+    const int tid = threadIdx.x;
+    const bool qp = A.pb.propagator == QPFRG_PROP_QP;
+    const R invT = R(1.0 / A.T), eta = R(A.pb.eta);
+    const R t = (R)A.pb.t, tp = (R)A.pb.tp, mu = (R)A.pb.mu;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *s_kx = reinterpret_cast<R *>(smem_raw);
+    R *s_ky = s_kx + P, *s_cx = s_ky + P, *s_sx = s_cx + P, *s_cy = s_sx + P, *s_sy = s_cy + P;
+    R *s_x = s_sy + P, *s_f = s_x + P, *s_fc = s_f + P, *s_w = s_fc + P;
+    R *s_V = s_w + P, *s_Z = s_V + N;
+
+    const double kx = A.kf[2 * j], ky = A.kf[2 * j + 1];
+    for (int i = tid; i < N; i += blockDim.x) {
+        s_V[i] = (R)A.V[((long)j * N + a) * N + i];
+        s_Z[i] = A.Z ? (R)A.Z[i] : R(1);
+    }
+    __syncthreads();
+    const R Za = s_Z[a];
+    for (int i = tid; i < P; i += blockDim.x) {
+        const int p = a * P + i;
+        // k_j + p in FP64, then cos/sin of its components
+        const double kpx = kx + (double)A.fine.kx[p], kpy = ky + (double)A.fine.ky[p];
+        double sxv, cxv, syv, cyv;
+        sincos(kpx, &sxv, &cxv);
+        sincos(kpy, &syv, &cyv);
+        s_kx[i] = (R)kpx;
+        s_ky[i] = (R)kpy;
+        s_cx[i] = (R)cxv;
+        s_sx[i] = (R)sxv;
+        s_cy[i] = (R)cyv;
+        s_sy[i] = (R)syv;
+        const R xp = qp ? Za * A.fine.xi[p] : A.fine.xi[p];
+        s_x[i] = xp;
+        R f, fc;
+        sfermi(xp, invT, f, fc);
+        s_f[i] = f;
+        s_fc[i] = fc;
+        s_w[i] = A.fine.w[p];
+    }
+    __syncthreads();
+
+    const int q = blockIdx.x * blockDim.x + tid;
+    R rp = R(0), rm = R(0);
+    if (q < M) {
+        const int b = q / P;
+        const R qx = A.fine.kx[q], qy = A.fine.ky[q];
+        const R cqx = A.fine.cx[q], sqx = A.fine.sx[q], cqy = A.fine.cy[q], sqy = A.fine.sy[q];
+        const R Zb = s_Z[b];
+        const R xq = qp ? Zb * A.fine.xi[q] : A.fine.xi[q];
+        R fq, fcq;
+        sfermi(xq, invT, fq, fcq);
+        const R wq = A.fine.w[q];
+        const R vab = s_V[b];
+        const R ZaZb = Za * Zb;
+        // chord frequencies xi_j -+ 2T (xi_j of the representative, FP64)
+        const double ckx = cos(kx), cky = cos(ky);
+        const double xij = -2.0 * A.pb.t * (ckx + cky) - 4.0 * A.pb.tp * ckx * cky - A.pb.mu;
+        const R wplus = (R)(xij + 2.0 * A.T), wminus = (R)(xij - 2.0 * A.T);
+        const R eta2 = eta * eta;
+        for (int i = 0; i < P; ++i) {
+            const R rx = s_kx[i] - qx, ry = s_ky[i] - qy;
+            const int c = sproject(rx, ry, N, A.pb.mode, A.pb.L);
+            // cos(k+p-q) by angle addition
+            const R crx = s_cx[i] * cqx + s_sx[i] * sqx;
+            const R cry = s_cy[i] * cqy + s_sy[i] * sqy;
+            R xr = R(-2) * t * (crx + cry) - R(4) * tp * crx * cry - mu;
+            const R Zc = s_Z[c];
+            if (qp) xr *= Zc;
+            R fr, fcr;
+            sfermi(xr, invT, fr, fcr);
+            const R F = s_f[i] * fcq * fcr + s_fc[i] * fq * fr;
+            const R W = ZaZb * Zc * (R(2) * vab * vab - vab * s_V[c]);
+            const R amp = s_w[i] * wq * W * F;
+            const R E = xq + xr - s_x[i];
+            if (HIST) {
+                const double eb = ((double)E - A.e_min) * A.inv_h;
+                int bin = (int)floor(eb);
+                bin = bin < 0 ? 0 : (bin >= A.nbins ? A.nbins - 1 : bin);
+                const double d = (double)E - (A.e_min + (bin + 0.5) / A.inv_h);
+                double* h = A.hist + ((long)jidx * 5) * A.nbins + bin;
+                double m = (double)amp;
+#pragma unroll
+                for (int mo = 0; mo < 5; ++mo) {
+                    atomicAdd(h + (long)mo * A.nbins, m);
+                    m *= d;
+                }
+            } else {
+                const R dp = wplus - E, dm = wminus - E;
+                rp += amp * sdiv(dp, dp * dp + eta2);
+                rm += amp * sdiv(dm, dm * dm + eta2);
+            }
+        }
+    }
+    if (HIST) return;
+    // block reduction of the two partial sums
+    __shared__ double red[2][32];
+    double vp = (double)rp, vm = (double)rm;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        vp += __shfl_down_sync(0xffffffffu, vp, off);
+        vm += __shfl_down_sync(0xffffffffu, vm, off);
+    }
+    const int lane = tid & 31, warp = tid >> 5;
+    if (lane == 0) {
+        red[0][warp] = vp;
+        red[1][warp] = vm;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        vp = lane < nw ? red[0][lane] : 0.0;
+        vm = lane < nw ? red[1][lane] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            vp += __shfl_down_sync(0xffffffffu, vp, off);
+            vm += __shfl_down_sync(0xffffffffu, vm, off);
+        }
+        if (lane == 0) {
+            atomicAdd(&A.sig[2 * jidx], vp);
+            atomicAdd(&A.sig[2 * jidx + 1], vm);
+        }
+    }
+}
+
+__global__ void z_update_kernel(const double *sig, double *Zout, int N, double T)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const double slope = (sig[2 * j] - sig[2 * j + 1]) / (4.0 * T);
+    Zout[j] = 1.0 / (1.0 - slope);
+}
+
+// Sigma on the grid from the binned moments: sum_b sum_n H_n[b] / (z - E_b)^(n+1),
+// z = w_m + i eta (Taylor expansion of 1/(z - E_b - d) in the offset d).
+__global__ void sigma_grid_kernel(const double *hist, int nbins, double e_min, double h, int n_omega,
+                                  double w0, double dw, double eta, double *re, double *im, int N)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (m >= n_omega) return;
+    const double w = w0 + dw * m;
+    const double *H = hist + (long)j * 5 * nbins;
+    double sr = 0.0, si = 0.0;
+    for (int b = 0; b < nbins; ++b) {
+        const double Eb = e_min + (b + 0.5) * h;
+        // u = 1/(z - Eb) = (dx - i eta)/(dx^2 + eta^2)
+        const double dx = w - Eb, den = dx * dx + eta * eta;
+        const double ur = dx / den, ui = -eta / den;
+        double pr = ur, pi = ui;                 // u^(n+1)
+        for (int mo = 0; mo < 5; ++mo) {
+            const double hv = H[(long)mo * nbins + b];
+            sr += hv * pr;
+            si += hv * pi;
+            const double nr = pr * ur - pi * ui, ni = pr * ui + pi * ur;
+            pr = nr;
+            pi = ni;
+        }
+    }
+    re[(long)j * n_omega + m] = sr;
+    im[(long)j * n_omega + m] = si;
+}
+
+template <typename R>
+static qpfrg_status launch_sigma(qpfrg_ctx *c, bool hist, SigmaArgs<R> &A, int kid)
+{
+    const int P = c->pb.P, N = c->pb.N;
+    const size_t smem = (size_t)(10 * P + 2 * N) * sizeof(R);
+    auto kern = hist ? sigma_kernel<R, true> : sigma_kernel<R, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(c, e, "sigma smem attribute");
+    dim3 grid(div_up(c->pb.M, 256), N, A.nj);
+    prof_begin(c);
+    kern<<<grid, 256, smem, c->stream>>>(A);
+    prof_end(c, kid);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "sigma_kernel");
+}
+
+template <typename R>
+static void fill_args(qpfrg_ctx *c, SigmaArgs<R> &A, const FineTable<R> &fine, double T, const double *d_V,
+                      const double *d_Z)
+{
+    A.pb = c->pb;
+    A.fine = fine;
+    A.kf = c->d_kf;
+    A.V = d_V;
+    A.Z = d_Z;
+    A.sig = c->d_sig;
+    A.T = T;
+    A.nj = c->pb.N;
+    A.jlist = nullptr;
+    A.hist = c->d_hist;
+    A.e_min = 0.0;
+    A.inv_h = 1.0;
+    A.nbins = 0;
+}
+
+qpfrg_status launch_sigma_z(qpfrg_ctx *c, double T, const double *d_V, const double *d_Z, double *d_Zout)
+{
+    const int N = c->pb.N;
+    cudaError_t e = cudaMemsetAsync(c->d_sig, 0, 2 * (size_t)N * sizeof(double), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "memset sigma");
+    qpfrg_status s;
+    if (c->opt.precision == QPFRG_FP64) {
+        SigmaArgs<double> A;
+        fill_args(c, A, c->f64, T, d_V, d_Z);
+        s = launch_sigma(c, false, A, K_SIGMA_Z);
+    } else {
+        SigmaArgs<float> A;
+        fill_args(c, A, c->f32, T, d_V, d_Z);
+        s = launch_sigma(c, false, A, K_SIGMA_Z);
+    }
+    if (s != QPFRG_OK) return s;
+    prof_begin(c);
+    z_update_kernel<<<div_up(N, 128), 128, 0, c->stream>>>(c->d_sig, d_Zout, N, T);
+    prof_end(c, K_Z_UPDATE);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "z_update_kernel");
+}
+
+// Bin count of the frequency-grid histogram: with h = eta/4 the offset of a
+// pole from its bin centre is at most |z - E_b|/8, so the moment expansion
+// truncated after moment 4 is accurate to 8^-5 = 3e-5 relative per pole.
+static int grid_bins(const qpfrg_ctx *c, double e_min, double e_max)
+{
+    const double h_target = 0.25 * c->opt.eta;
+    int nb = (int)std::ceil((e_max - e_min) / h_target);
+    if (nb < 64) nb = 64;
+    if (nb > 1 << 16) nb = 1 << 16;
+    return nb;
+}
+
+qpfrg_status launch_sigma_grid(qpfrg_ctx *c, double T, const double *d_V, const double *d_Z, double *d_re,
+                               double *d_im)
+{
+    const int N = c->pb.N, n_omega = c->opt.n_omega;
+    // pole energies E = x_q + x_r - x_p lie in [2 min x - max x, 2 max x - min x]
+    double xmin = 1e300, xmax = -1e300;
+    for (int p = 0; p < c->pb.M; ++p) {
+        const double kx = c->fk[2 * p], ky = c->fk[2 * p + 1];
+        const double x = -2.0 * c->pb.t * (std::cos(kx) + std::cos(ky)) -
+                         4.0 * c->pb.tp * std::cos(kx) * std::cos(ky) - c->pb.mu;
+        xmin = x < xmin ? x : xmin;
+        xmax = x > xmax ? x : xmax;
+    }
+    // r = k + p - q is not a fine point: bound its dispersion by the band
+    const double band_lo = -4.0 * std::fabs(c->pb.t) - 4.0 * std::fabs(c->pb.tp) - c->pb.mu;
+    const double band_hi = 4.0 * std::fabs(c->pb.t) + 4.0 * std::fabs(c->pb.tp) - c->pb.mu;
+    xmin = std::fmin(xmin, band_lo);
+    xmax = std::fmax(xmax, band_hi);
+    if (c->pb.propagator == QPFRG_PROP_QP) {   // Z in (0, z_max] rescales the poles
+        xmin *= c->opt.z_max;
+        xmax *= c->opt.z_max;
+    }
+    const double e_min = 2.0 * xmin - xmax - 1e-9, e_max = 2.0 * xmax - xmin + 1e-9;
+    const int nbins = grid_bins(c, e_min, e_max);
+    const size_t need = (size_t)N * 5 * nbins;
+    if (need > c->hist_elems) {
+        if (c->d_hist) cudaFree(c->d_hist);
+        c->d_hist = nullptr;
+        cudaError_t e = cudaMalloc((void **)&c->d_hist, need * sizeof(double));
+        if (e != cudaSuccess) {
+            c->hist_elems = 0;
+            return cuda_fail(c, e, "cudaMalloc(sigma histogram)");
+        }
+        c->hist_elems = need;
+    }
+    cudaError_t e = cudaMemsetAsync(c->d_hist, 0, need * sizeof(double), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "memset histogram");
+    const double h = (e_max - e_min) / nbins;
+    qpfrg_status s;
+    if (c->opt.precision == QPFRG_FP64) {
+        SigmaArgs<double> A;
+        fill_args(c, A, c->f64, T, d_V, d_Z);
+        A.e_min = e_min;
+        A.inv_h = 1.0 / h;
+        A.nbins = nbins;
+        s = launch_sigma(c, true, A, K_SIGMA_HIST);
+    } else {
+        SigmaArgs<float> A;
+        fill_args(c, A, c->f32, T, d_V, d_Z);
+        A.e_min = e_min;
+        A.inv_h = 1.0 / h;
+        A.nbins = nbins;
+        s = launch_sigma(c, true, A, K_SIGMA_HIST);
+    }
+    if (s != QPFRG_OK) return s;
+    const double w0 = c->opt.omega_min;
+    const double dw = n_omega > 1 ? (c->opt.omega_max - c->opt.omega_min) / (n_omega - 1) : 0.0;
+    dim3 grid(div_up(n_omega, 128), N);
+    prof_begin(c);
+    sigma_grid_kernel<<<grid, 128, 0, c->stream>>>(c->d_hist, nbins, e_min, h, n_omega, w0, dw, c->pb.eta,
+                                                   d_re, d_im, N);
+    prof_end(c, K_SIGMA_GRID);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "sigma_grid_kernel");
+}
+
+}  // namespace qpfrg

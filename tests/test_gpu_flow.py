@@ -1,0 +1,178 @@
+"""GPU parity of the self-energy / Z and of the RK4 flow against the FP64
+oracle, plus checkpoint/resume and host-side failure detection, through the
+C ABI.  Tolerances: Z absolute 1e-10 (FP64) / 1e-4 (mixed); vertex normwise
+1e-10 / 1e-4; divergence scale relative 1e-9 / 5e-3."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.oracle import MODE_LATTICE, Oracle
+from paper_2005_00827_gb300 import api, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64).ravel()).cuda()
+
+
+def zeros(n):
+    import torch
+    return torch.zeros(n, dtype=torch.float64, device="cuda")
+
+
+def gpu_z(ctx, T, V, Z):
+    import torch
+    out = zeros(len(Z))
+    api.qpfrg_selfenergy(ctx.h, T, dev(V), dev(Z), None, None, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec,tol", [(api.QPFRG_FP64, 1e-10), (api.QPFRG_MIXED, 1e-4)])
+@pytest.mark.parametrize("geo", [(16, 4, 4, 0, 0), (16, 1, 1, 1, 0), (16, 4, 6, 0, 1)],
+                         ids=["wedge", "lattice", "wedge_qp"])
+def test_z_matches_oracle(geo, prec, tol):
+    N, nt, nr, mode, prop = geo
+    T = 0.2
+    o = Oracle(N, nt, nr, mode=mode, eta=0.02, prop_mode=prop)
+    V = inputs.random_vertex(N, 2.0, seed=4, c4v=(mode == 0))
+    Z = inputs.z_profile(N, "aniso") if mode == 0 else np.random.default_rng(2).uniform(0.85, 1.0, N)
+    ref = o.zfactor(T, V, Z)
+    with api.Context(N, nt, nr, U=2.0, mode=mode, precision=prec, propagator=prop) as ctx:
+        got = gpu_z(ctx, T, V, Z)
+    assert np.abs(got - ref).max() < tol
+
+
+@pytest.mark.parametrize("prec", [api.QPFRG_FP64, api.QPFRG_MIXED])
+def test_sigma_grid_matches_exact_pole_sum(prec):
+    import torch
+    N, n, T, nw = 16, 4, 0.15, 64
+    o = Oracle(N, n, n, eta=0.05)
+    V = inputs.random_vertex(N, 2.0, seed=8)
+    Z = inputs.z_profile(N, "aniso")
+    w = np.linspace(-4.0, 4.0, nw)
+    with api.Context(N, n, n, U=2.0, precision=prec, eta=0.05, n_omega=nw, omega_min=-4.0,
+                     omega_max=4.0) as ctx:
+        re, im = zeros(N * nw), zeros(N * nw)
+        api.qpfrg_selfenergy(ctx.h, T, dev(V), dev(Z), re, im, None)
+        torch.cuda.synchronize()
+        got = (re.cpu().numpy() + 1j * im.cpu().numpy()).reshape(N, nw)
+    for j in (0, 3, 8):
+        ref = o.sigma(T, V, Z, j, w)
+        assert np.abs(got[j] - ref).max() / np.abs(ref).max() < 1e-4
+        assert np.all(got[j].imag <= 1e-12)
+
+
+def run_oracle_flow(o, U, T0, T_end, z_feedback, steps=None):
+    N = o.N
+    return o.flow(np.full((N, N, N), U), np.ones(N), T0, T_end, math.log(0.98), stop_abs_v=20.0,
+                  z_feedback=z_feedback, max_steps=steps or 100000)
+
+
+@pytest.mark.parametrize("prec", [api.QPFRG_FP64, api.QPFRG_MIXED])
+def test_flow_to_divergence_matches_oracle(prec):
+    """np16-shaped T-flow (N=16, coarse 4x4 fine grid for oracle speed), U=3."""
+    N, n, U = 16, 4, 3.0
+    o = Oracle(N, n, n)
+    ref = run_oracle_flow(o, U, 1.0, 0.01, False)
+    assert ref["status"] == "DIVERGED"
+    with api.Context(N, n, n, U=U, lambda0=1.0, precision=prec, lambda_end=0.01) as ctx:
+        r = api.qpfrg_flow(ctx.h).as_dict()
+    assert r["status"] == "DIVERGED" and r["steps"] == ref["steps"]
+    rel = 1e-9 if prec == api.QPFRG_FP64 else 5e-3
+    assert r["lambda_c"] == pytest.approx(ref["lambda_c"], rel=rel)
+
+
+@pytest.mark.parametrize("prec,tol", [(api.QPFRG_FP64, 1e-10), (api.QPFRG_MIXED, 1e-4)])
+def test_flow_with_z_feedback_trajectory(prec, tol):
+    """Z feedback on: vertex and Z after a fixed number of steps."""
+    import torch
+    N, n, U, steps = 16, 4, 2.0, 12
+    o = Oracle(N, n, n, eta=0.02)
+    ref = run_oracle_flow(o, U, 1.0, 0.02, True, steps=steps)
+    with api.Context(N, n, n, U=U, lambda0=1.0, precision=prec, lambda_end=0.02, z_feedback=1) as ctx:
+        r = api.qpfrg_step(ctx.h, steps).as_dict()
+        V, Z = zeros(N ** 3), zeros(N)
+        api.qpfrg_read_state(ctx.h, V, Z)
+        torch.cuda.synchronize()
+    assert r["steps"] == steps and r["lam"] == pytest.approx(ref["lam"], rel=1e-13)
+    Vg = V.cpu().numpy().reshape(N, N, N)
+    assert np.abs(Vg - ref["V"]).max() / np.abs(ref["V"]).max() < tol
+    assert np.abs(Z.cpu().numpy() - ref["Z"]).max() < tol
+    assert np.all(ref["Z"] > 0.0)
+
+
+def test_checkpoint_resume():
+    N, n, U = 16, 4, 2.5
+    with api.Context(N, n, n, U=U, lambda_end=0.05) as a:
+        api.qpfrg_step(a.h, 6)
+        img = api.qpfrg_get_state(a.h)
+        ra = api.qpfrg_step(a.h, 5).as_dict()
+        full = api.qpfrg_get_state(a.h)
+    with api.Context(N, n, n, U=U, lambda_end=0.05) as b:
+        api.qpfrg_set_state(b.h, img)
+        rb = api.qpfrg_step(b.h, 5).as_dict()
+        resumed = api.qpfrg_get_state(b.h)
+    assert ra["steps"] == rb["steps"] == 11 and ra["lam"] == rb["lam"]
+    va = np.frombuffer(full[64:], dtype=np.float64)
+    vb = np.frombuffer(resumed[64:], dtype=np.float64)
+    assert np.abs(va - vb).max() / np.abs(va).max() < 1e-13
+
+
+def test_failure_detection_host_side(monkeypatch):
+    N, n = 16, 4
+    with api.Context(N, n, n, U=2.0) as c:
+        img = bytearray(api.qpfrg_get_state(c.h))
+        bad = np.frombuffer(img, dtype=np.float64, offset=64).copy()
+        bad[17] = np.nan
+        img[64:] = bad.tobytes()
+        with pytest.raises(api.QpfrgError) as ei:
+            api.qpfrg_set_state(c.h, bytes(img))
+        assert ei.value.status == api.QPFRG_ERR_NONFINITE
+        with pytest.raises(api.QpfrgError) as ei:
+            api.qpfrg_set_state(c.h, bytes(img[:-8]))
+        assert ei.value.status == api.QPFRG_ERR_INVALID
+        # state untouched by the rejected images
+        r = api.qpfrg_step(c.h, 1).as_dict()
+        assert r["status"] == "RUNNING" and np.isfinite(r["max_abs_v"])
+    # wall-clock budget
+    with api.Context(N, n, n, U=2.0, timeout_s=1e-9) as c:
+        api.qpfrg_step(c.h, 1)
+        r = api.qpfrg_flow(c.h).as_dict()
+        assert r["status"] == "TIMEOUT"
+    # Z leaves (0, z_max]
+    with api.Context(N, n, n, U=2.0, z_feedback=1, z_max=0.5) as c:
+        r = api.qpfrg_flow(c.h).as_dict()
+        assert r["status"] == "Z_OUT_OF_RANGE" and r["steps"] == 0
+    # injected allocation failure
+    monkeypatch.setenv("QPFRG_TEST_FAIL_ALLOC", "1")
+    with pytest.raises(api.QpfrgError) as ei:
+        api.Context(N, n, n, U=2.0)
+    assert ei.value.status == api.QPFRG_ERR_OOM
+
+
+def test_invalid_arguments_rejected():
+    with pytest.raises(api.QpfrgError) as ei:
+        api.Context(18, 4, 4)
+    assert ei.value.status == api.QPFRG_ERR_INVALID
+    with pytest.raises(api.QpfrgError) as ei:
+        api.Context(16, 4, 3)
+    assert ei.value.status == api.QPFRG_ERR_INVALID
+    with pytest.raises(api.QpfrgError) as ei:
+        api.Context(16, 64, 64)
+    assert ei.value.status == api.QPFRG_ERR_UNSUPPORTED
+    with api.Context(16, 4, 4) as c:
+        with pytest.raises(api.QpfrgError):
+            api.qpfrg_rhs(c.h, -1.0, 1, None, 2)
+
+
+def test_profiler_counts_launches():
+    with api.Context(16, 4, 4, U=2.0) as c:
+        api.qpfrg_set_profiling(c.h, True)
+        api.qpfrg_step(c.h, 2)
+        prof = api.qpfrg_profile(c.h)
+    assert prof["bubble"][1] == 8 and prof["contract_pp"][1] == 8 and prof["rk_final"][1] == 2
+    assert prof["bubble"][0] > 0
