@@ -86,7 +86,7 @@ class ClockSampler:
         sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4) if "Active" in r[5 + i]})
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].strip() == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(self.rows)}
 
@@ -191,8 +191,8 @@ def run_qpfrg(args):
         if dom == "bubble":
             units = 2.0 * N * N * M
             fp32, mufu = BUBBLE_FP32_PER_EVAL, BUBBLE_MUFU_PER_EVAL
-        else:
-            units = float(N) * M * M
+        else:   # the flow evaluates the C4v-irreducible patches 0..N/8 only
+            units = float(N // 8 + 1) * M * M
             fp32, mufu = SIGMA_FP32_PER_PAIR, SIGMA_MUFU_PER_PAIR
         clk_per_unit = max(fp32 / FP32_LANES_PER_SM, mufu / MUFU_PER_SM)
         peak_units = N_SM * clk_mhz * 1e6 / clk_per_unit

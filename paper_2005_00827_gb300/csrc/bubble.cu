@@ -14,14 +14,15 @@
 // Launch shape: one CTA per (patch a, chunk of Q, family).  The CTA keeps its
 // wedge's fine points in registers (PPT consecutive radial points per
 // thread), streams the partner-patch bytes of each Q (coalesced), merges
-// equal consecutive partners in registers and adds runs into a shared-memory
-// row of N accumulators.  Rows are double-buffered so one barrier per Q
-// suffices.
+// equal consecutive partners in registers and adds runs into shared-memory
+// rows of N accumulators, G transfers per barrier, double-buffered.
 #include <algorithm>
 
 #include "qpfrg_internal.h"
 
 namespace qpfrg {
+
+constexpr int G = 4;   // transfers per barrier
 
 template <typename R>
 struct BubbleArgs {
@@ -166,9 +167,9 @@ __global__ void __launch_bounds__(256) bubble_kernel(BubbleArgs<R> A)
     const bool qp = A.pb.propagator == QPFRG_PROP_QP;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *acc = reinterpret_cast<R *>(smem_raw);  // 2 x N
-    R *Zs = acc + 2 * N;                       // N
-    for (int i = tid; i < 2 * N; i += nthr) acc[i] = R(0);
+    R *acc = reinterpret_cast<R *>(smem_raw);  // 2 x G x N
+    R *Zs = acc + 2 * G * N;                   // N
+    for (int i = tid; i < 2 * G * N; i += nthr) acc[i] = R(0);
     for (int i = tid; i < N; i += nthr) Zs[i] = A.Z ? (R)A.Z[i] : R(1);
     __syncthreads();
     const R Za = Zs[a];
@@ -200,45 +201,63 @@ __global__ void __launch_bounds__(256) bubble_kernel(BubbleArgs<R> A)
     const bool vec = (P % PPT) == 0;
     const TransferTable<R> &Qt = pp ? A.qpp : A.qph;
 
-    for (int Q = q0; Q < q1; ++Q) {
-        R *accb = acc + ((Q - q0) & 1) * N;
+    // Q's are processed in groups of G: the G partner loads are issued
+    // together, runs are added into G shared rows, one barrier per group.
+    for (int Qb = q0; Qb < q1; Qb += G) {
+        R *accb = acc + (((Qb - q0) / G) & 1) * (G * N);
         if (any_valid) {
-            const R cQx = Qt.cx[Q], sQx = Qt.sx[Q], cQy = Qt.cy[Q], sQy = Qt.sy[Q];
-            int bq[PPT];
-            load_partners<PPT>(A.part + ((long)fam * NN + Q) * (long)M + (long)a * P + tid * PPT, bq,
-                               vec, P - tid * PPT);
-            int run_b = -1;
-            R run_v = R(0);
+            int bq[G][PPT];
+            R cQx[G], sQx[G], cQy[G], sQy[G];
 #pragma unroll
-            for (int u = 0; u < PPT; ++u) {
-                if (!valid[u]) continue;
-                // cos of the partner momentum components by angle addition:
-                // pp: cos(Q - p) = cQ cp + sQ sp;  ph: cos(p + Q) = cp cQ - sp sQ
-                const R cqx = pp ? cQx * pcx[u] + sQx * psx[u] : pcx[u] * cQx - psx[u] * sQx;
-                const R cqy = pp ? cQy * pcy[u] + sQy * psy[u] : pcy[u] * cQy - psy[u] * sQy;
-                R xq = R(-2) * t * (cqx + cqy) - R(4) * tp * cqx * cqy - mu;
-                const int b = bq[u];
-                if (qp) xq *= Zs[b];
-                const R v = pw[u] * (tflow ? loop_T(pp, px[u], pa[u], xq, invT, thrT)
-                                           : loop_g(pp, px[u], pa[u], pb2[u], xq, invT, thrT));
-                if (b == run_b) {
-                    run_v += v;
-                } else {
-                    if (run_b >= 0) atomicAdd(&accb[run_b], run_v);
-                    run_b = b;
-                    run_v = v;
-                }
+            for (int g = 0; g < G; ++g) {
+                const int Q = min(Qb + g, q1 - 1);
+                load_partners<PPT>(A.part + ((long)fam * NN + Q) * (long)M + (long)a * P + tid * PPT, bq[g],
+                                   vec, P - tid * PPT);
+                cQx[g] = Qt.cx[Q];
+                sQx[g] = Qt.sx[Q];
+                cQy[g] = Qt.cy[Q];
+                sQy[g] = Qt.sy[Q];
             }
-            if (run_b >= 0) atomicAdd(&accb[run_b], run_v);
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                if (Qb + g >= q1) break;
+                R *row = accb + g * N;
+                int run_b = -1;
+                R run_v = R(0);
+#pragma unroll
+                for (int u = 0; u < PPT; ++u) {
+                    if (!valid[u]) continue;
+                    // cos of the partner momentum components by angle addition:
+                    // pp: cos(Q - p) = cQ cp + sQ sp;  ph: cos(p + Q) = cp cQ - sp sQ
+                    const R cqx = pp ? cQx[g] * pcx[u] + sQx[g] * psx[u] : pcx[u] * cQx[g] - psx[u] * sQx[g];
+                    const R cqy = pp ? cQy[g] * pcy[u] + sQy[g] * psy[u] : pcy[u] * cQy[g] - psy[u] * sQy[g];
+                    R xq = R(-2) * t * (cqx + cqy) - R(4) * tp * cqx * cqy - mu;
+                    const int b = bq[g][u];
+                    if (qp) xq *= Zs[b];
+                    const R v = pw[u] * (tflow ? loop_T(pp, px[u], pa[u], xq, invT, thrT)
+                                               : loop_g(pp, px[u], pa[u], pb2[u], xq, invT, thrT));
+                    if (b == run_b) {
+                        run_v += v;
+                    } else {
+                        if (run_b >= 0) atomicAdd(&row[run_b], run_v);
+                        run_b = b;
+                        run_v = v;
+                    }
+                }
+                if (run_b >= 0) atomicAdd(&row[run_b], run_v);
+            }
         }
         __syncthreads();
-        R *dst = A.B + (((long)fam * NN + Q) * N + a) * (long)N;
-        for (int b = tid; b < N; b += nthr) {
-            const R v = accb[b];
-            accb[b] = R(0);
-            const R Zb = Zs[b];
-            const R s = tflow ? Za * Zb : A.g * Za * Zb * (Za + Zb);
-            dst[b] = v * s;
+        for (int idx = tid; idx < G * N; idx += nthr) {
+            const int g = idx / N, b = idx - g * N;
+            const int Q = Qb + g;
+            const R v = accb[idx];
+            accb[idx] = R(0);
+            if (Q < q1) {
+                const R Zb = Zs[b];
+                const R s = tflow ? Za * Zb : A.g * Za * Zb * (Za + Zb);
+                A.B[(((long)fam * NN + Q) * N + a) * (long)N + b] = v * s;
+            }
         }
     }
 }
@@ -248,7 +267,7 @@ static void launch_t(qpfrg_ctx *c, const BubbleArgs<R> &A, int nthr, int qchunks
 {
     const int N = c->pb.N;
     dim3 grid(N, qchunks, 2);
-    const size_t smem = 3 * (size_t)N * sizeof(R);
+    const size_t smem = (2 * G + 1) * (size_t)N * sizeof(R);
     bubble_kernel<R, PPT><<<grid, nthr, smem, c->stream>>>(A);
 }
 

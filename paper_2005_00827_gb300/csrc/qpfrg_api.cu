@@ -108,6 +108,31 @@ qpfrg_status dev_alloc(qpfrg_ctx *c, T **p, size_t count, const char *what)
 
 long n3_of(const qpfrg_ctx *c) { return (long)c->pb.N * c->pb.N * c->pb.N; }
 
+// C4v images of a wedge patch (centres at 2 pi j / N, N a multiple of 4):
+// j -> +-j + m N/4.  True when V[g i][g j][g l] = V[i][j][l] and Z[g j] = Z[j]
+// for all 8 group elements, to a relative 1e-12.
+bool c4v_symmetric(const qpfrg_ctx *c, const double *V, const double *Z)
+{
+    if (c->pb.mode != QPFRG_GRID_WEDGE) return false;
+    const int N = c->pb.N, q = N / 4;
+    double vmax = 0.0, zmax = 0.0;
+    for (long i = 0; i < n3_of(c); ++i) vmax = std::fmax(vmax, std::fabs(V[i]));
+    for (int j = 0; j < N; ++j) zmax = std::fmax(zmax, std::fabs(Z[j]));
+    for (int m = 0; m < 4; ++m)
+        for (int sgn = -1; sgn <= 1; sgn += 2) {
+            auto g = [&](int j) { return ((sgn * j + m * q) % N + N) % N; };
+            for (int j = 0; j < N; ++j)
+                if (std::fabs(Z[g(j)] - Z[j]) > 1e-12 * zmax) return false;
+            for (int i = 0; i < N; ++i)
+                for (int j = 0; j < N; ++j)
+                    for (int l = 0; l < N; ++l) {
+                        const double a = V[((long)g(i) * N + g(j)) * N + g(l)], b = V[((long)i * N + j) * N + l];
+                        if (std::fabs(a - b) > 1e-12 * vmax) return false;
+                    }
+        }
+    return true;
+}
+
 }  // namespace
 
 namespace qpfrg {
@@ -184,7 +209,7 @@ void qpfrg_destroy(qpfrg_t c)
                     c->qph64.cy, c->qph64.sy, c->qpp32.cx, c->qpp32.sx, c->qpp32.cy, c->qpp32.sy,
                     c->qph32.cx, c->qph32.sx, c->qph32.cy, c->qph32.sy, c->d_kf, c->d_Qpp, c->d_Qph,
                     c->d_part, c->d_B, c->d_V, c->d_Z, c->d_Vs, c->d_k, c->d_acc, c->d_ones, c->d_Vf,
-                    c->d_Zwork, c->d_sig, c->d_hist, c->d_red};
+                    c->d_Zwork, c->d_sig, c->d_hist, c->d_red, c->d_jirr, c->d_rep};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->h_red) cudaFreeHost(c->h_red);
@@ -318,6 +343,24 @@ qpfrg_status qpfrg_create(const qpfrg_lattice *lattice, int n_p, const qpfrg_fin
     e = cudaMallocHost((void **)&c->h_red, 2 * sizeof(unsigned long long));
     if (e != cudaSuccess) return fail(cuda_fail(c, e, "cudaMallocHost"));
 
+    // C4v-irreducible patches 0..floor(N/8) and each patch's representative
+    if (pb.mode == QPFRG_GRID_WEDGE) {
+        const int q = (int)N / 4;
+        std::vector<int> jirr, rep(N);
+        for (int j = 0; 8 * j <= (int)N; ++j) jirr.push_back(j);
+        for (int j = 0; j < (int)N; ++j) {
+            int r = j % q;
+            if (2 * r > q) r = q - r;
+            rep[j] = r;
+        }
+        c->n_irr = (int)jirr.size();
+        if ((s = dev_alloc(c, &c->d_jirr, jirr.size(), "irreducible patches")) ||
+            (s = dev_alloc(c, &c->d_rep, N, "representatives")))
+            return fail(s);
+        cudaMemcpy(c->d_jirr, jirr.data(), jirr.size() * sizeof(int), cudaMemcpyHostToDevice);
+        cudaMemcpy(c->d_rep, rep.data(), N * sizeof(int), cudaMemcpyHostToDevice);
+    }
+
     // state: V = U, Z = 1 at lambda0
     std::vector<double> h(n3, U);
     e = cudaMemcpy(c->d_V, h.data(), n3 * sizeof(double), cudaMemcpyHostToDevice);
@@ -327,6 +370,7 @@ qpfrg_status qpfrg_create(const qpfrg_lattice *lattice, int n_p, const qpfrg_fin
     e = cudaMemcpy(c->d_ones, h.data(), N * sizeof(double), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return fail(cuda_fail(c, e, "init Z"));
     c->lambda = lambda0;
+    c->c4v_state = pb.mode == QPFRG_GRID_WEDGE;
     c->steps = 0;
     c->status = QPFRG_FLOW_RUNNING;
     c->max_abs_v = std::fabs(U);
@@ -366,7 +410,7 @@ qpfrg_status qpfrg_selfenergy(qpfrg_t c, double lambda, const double *d_V, const
     if (!d_V || !(lambda > 0.0) || !std::isfinite(lambda)) return set_err(c, QPFRG_ERR_INVALID, "bad V or T");
     const double *Z = d_Z ? d_Z : c->d_ones;
     qpfrg_status s;
-    if (d_Z_out && (s = launch_sigma_z(c, lambda, d_V, Z, d_Z_out)) != QPFRG_OK) return s;
+    if (d_Z_out && (s = launch_sigma_z(c, lambda, d_V, Z, d_Z_out, false)) != QPFRG_OK) return s;
     if (c->opt.n_omega > 0 && d_sigma_re && d_sigma_im)
         return launch_sigma_grid(c, lambda, d_V, Z, d_sigma_re, d_sigma_im);
     return QPFRG_OK;
@@ -402,7 +446,7 @@ static qpfrg_status do_step(qpfrg_ctx *c)
 
     if (c->opt.z_feedback) {
         const double T = tflow ? c->lambda : c->pb.T_fixed;
-        if ((s = launch_sigma_z(c, T, c->d_V, c->d_Z, c->d_Zwork)) != QPFRG_OK) return s;
+        if ((s = launch_sigma_z(c, T, c->d_V, c->d_Z, c->d_Zwork, c->c4v_state)) != QPFRG_OK) return s;
         std::vector<double> hz(N);
         e = cudaMemcpyAsync(hz.data(), c->d_Zwork, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -563,6 +607,7 @@ qpfrg_status qpfrg_set_state(qpfrg_t c, const void *h_buf, size_t bytes)
         e = cudaMemcpyAsync(c->d_Z, Z, c->pb.N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "set_state");
+    c->c4v_state = c4v_symmetric(c, V, Z);
     c->status = hd.status;
     c->steps = (int)hd.steps;
     c->lambda = hd.lambda;

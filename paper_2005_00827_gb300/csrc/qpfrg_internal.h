@@ -102,6 +102,10 @@ struct qpfrg_ctx {
     float *d_Vf = nullptr;       // FP32 copy of the RHS input (MIXED)
     double *d_Zwork = nullptr;   // Z computed at the start of a step
     double *d_sig = nullptr;     // N x 2 Re Sigma at xi_j +- 2T
+    int *d_jirr = nullptr;       // C4v-irreducible patches 0..N/8 (wedge mode)
+    int *d_rep = nullptr;        // slot of each patch's representative in d_jirr
+    int n_irr = 0;
+    bool c4v_state = false;      // flow state V, Z is C4v symmetric
     double *d_hist = nullptr;    // Sigma frequency-grid histogram (lazily sized)
     size_t hist_elems = 0;
     unsigned long long *d_red = nullptr;  // [0] max|V| bits, [1] nonfinite flag
@@ -135,7 +139,7 @@ qpfrg_status launch_contractions(qpfrg_ctx *c, const void *d_Vin, double scale, 
 
 // sigma.cu
 qpfrg_status launch_sigma_z(qpfrg_ctx *c, double T, const double *d_V, const double *d_Z,
-                            double *d_Zout);
+                            double *d_Zout, bool use_symmetry);
 qpfrg_status launch_sigma_grid(qpfrg_ctx *c, double T, const double *d_V, const double *d_Z,
                                double *d_re, double *d_im);
 

@@ -9,11 +9,13 @@
 // (definition_Z), with the slope the chord of Re Sigma over xi_j +- 2T
 // ("from outside", Sec. 3.1.1).
 //
-// sigma_z_kernel evaluates Re Sigma exactly at the two chord frequencies.
+// sigma_kernel<R,false> evaluates Re Sigma exactly at the two chord frequencies.
 // Launch shape: grid (q blocks, patch a of p, target j), 256 threads, one q
 // per thread; the CTA stages patch a's points (k_j + p, cos/sin, Fermi
 // factors) and the vertex row V[j][a][:] in shared memory and loops over
-// them.  sigma_hist_kernel bins W F by pole energy E with moments 0..4 for
+// them.  In the flow only the C4v-irreducible patches 0..N/8 are evaluated
+// (the vertex and Z keep the lattice symmetry) and Z is copied to their
+// images.  sigma_kernel<R,true> bins W F by pole energy E with moments 0..4 for
 // the frequency grid; sigma_grid_kernel resums the moments on the grid.
 #include "qpfrg_internal.h"
 
@@ -39,23 +41,65 @@ __device__ __forceinline__ void sfermi(R x, R invT, R &f, R &fc)
     fc = x > R(0) ? hi : lo;
 }
 
-template <typename R>
-__device__ __forceinline__ int sproject(R kx, R ky, int N, int mode, int L)
+// FP64 projection of a momentum onto its patch: fold into [-pi, pi] (ties to
+// even), atan2, nearest wedge centre; lattice mode: nearest lattice momentum.
+__device__ __forceinline__ int project64(double kx, double ky, int N, int mode, int L)
 {
-    const R tp = R(kTwoPi);
     if (mode == QPFRG_GRID_LATTICE) {
-        int m1 = (int)srint(kx * R(L) / tp) % L;
-        int m2 = (int)srint(ky * R(L) / tp) % L;
+        long m1 = (long)rint(kx * L / kTwoPi) % L;
+        long m2 = (long)rint(ky * L / kTwoPi) % L;
         if (m1 < 0) m1 += L;
         if (m2 < 0) m2 += L;
-        return m1 * L + m2;
+        return (int)(m1 * L + m2);
     }
-    const R x = kx - tp * srint(kx / tp);
-    const R y = ky - tp * srint(ky / tp);
-    int j = (int)sfloor(satan2(y, x) / (tp / R(N)) + R(0.5));
+    const double x = kx - kTwoPi * rint(kx / kTwoPi);
+    const double y = ky - kTwoPi * rint(ky / kTwoPi);
+    long j = (long)floor(atan2(y, x) / (kTwoPi / N) + 0.5);
     j %= N;
     if (j < 0) j += N;
-    return j;
+    return (int)j;
+}
+
+// atan2 in FP32 from an odd polynomial in t = min/max on [0, 1] fitted to
+// atan(t) (degree 11, |error| < 1.7e-6 rad), then octant reflections.
+// Caller guarantees (x, y) != (0, 0).
+__device__ __forceinline__ float atan2_poly(float y, float x)
+{
+    const float ax = fabsf(x), ay = fabsf(y);
+    const float t = __fdividef(fminf(ax, ay), fmaxf(ax, ay));
+    const float s = t * t;
+    float p = fmaf(s, -0.01172242f, 0.05265559f);
+    p = fmaf(s, p, -0.11643387f);
+    p = fmaf(s, p, 0.19354323f);
+    p = fmaf(s, p, -0.33262327f);
+    p = fmaf(s, p, 0.99997723f);
+    float a = t * p;
+    if (ay > ax) a = 1.57079633f - a;
+    if (x < 0.f) a = 3.14159265f - a;
+    return copysignf(a, y);
+}
+
+// FP32 wedge projection with a guard band: the FP32 momentum carries an
+// absolute error below 2.1e-6 per vector (FP32 rounding of k+p, q, their
+// difference and the fold) and atan2_poly below 1.7e-6 rad, so the angle is
+// trusted only when it lies more than 4e-6 + 4e-6/|r| rad from a wedge
+// boundary and the point is more than 4e-6 from the zone edge.  Returns -1
+// when the caller must project in FP64.
+__device__ __forceinline__ int project32_guarded(float rx, float ry, int N)
+{
+    const float tp = 6.28318531f;
+    const float x = rx - tp * rintf(rx * 0.159154943f);
+    const float y = ry - tp * rintf(ry * 0.159154943f);
+    const float r2 = x * x + y * y;
+    if (fabsf(x) > 3.14159265f - 4e-6f || fabsf(y) > 3.14159265f - 4e-6f || r2 < 1e-8f) return -1;
+    const float dth = tp / (float)N;
+    const float u = atan2_poly(y, x) / dth + 0.5f;
+    const float fl = floorf(u);
+    const float fr = u - fl;
+    const float m = fminf(fr, 1.f - fr) * dth;
+    if (m < 8e-6f || m * m * r2 < 6.4e-11f) return -1;
+    int j = (int)fl % N;
+    return j < 0 ? j + N : j;
 }
 
 template <typename R>
@@ -69,6 +113,7 @@ struct SigmaArgs {
     double T;
     int nj;
     const int *jlist;    // targets (may be NULL: j = blockIdx.z)
+    const double *kx64, *ky64;  // FP64 fine momenta (guarded FP32 projection)
     // frequency-grid histogram (sigma_hist_kernel)
     double *hist;        // [j][moment 0..4][bin]
     double e_min, inv_h;
@@ -92,6 +137,10 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
     R *s_ky = s_kx + P, *s_cx = s_ky + P, *s_sx = s_cx + P, *s_cy = s_sx + P, *s_sy = s_cy + P;
     R *s_x = s_sy + P, *s_f = s_x + P, *s_fc = s_f + P, *s_w = s_fc + P;
     R *s_V = s_w + P, *s_Z = s_V + N;
+    double *s_kxd = reinterpret_cast<double *>(smem_raw + (size_t)(10 * P + 2 * N) * sizeof(R) + 8 -
+                                               ((size_t)(10 * P + 2 * N) * sizeof(R)) % 8);
+    double *s_kyd = s_kxd + P;
+    constexpr bool f32 = sizeof(R) == 4;
 
     const double kx = A.kf[2 * j], ky = A.kf[2 * j + 1];
     for (int i = tid; i < N; i += blockDim.x) {
@@ -109,6 +158,10 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
         sincos(kpy, &syv, &cyv);
         s_kx[i] = (R)kpx;
         s_ky[i] = (R)kpy;
+        if (f32) {
+            s_kxd[i] = kpx;
+            s_kyd[i] = kpy;
+        }
         s_cx[i] = (R)cxv;
         s_sx[i] = (R)sxv;
         s_cy[i] = (R)cyv;
@@ -128,6 +181,7 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
     if (q < M) {
         const int b = q / P;
         const R qx = A.fine.kx[q], qy = A.fine.ky[q];
+        const double qxd = A.kx64[q], qyd = A.ky64[q];
         const R cqx = A.fine.cx[q], sqx = A.fine.sx[q], cqy = A.fine.cy[q], sqy = A.fine.sy[q];
         const R Zb = s_Z[b];
         const R xq = qp ? Zb * A.fine.xi[q] : A.fine.xi[q];
@@ -142,8 +196,15 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
         const R wplus = (R)(xij + 2.0 * A.T), wminus = (R)(xij - 2.0 * A.T);
         const R eta2 = eta * eta;
         for (int i = 0; i < P; ++i) {
-            const R rx = s_kx[i] - qx, ry = s_ky[i] - qy;
-            const int c = sproject(rx, ry, N, A.pb.mode, A.pb.L);
+            int c;
+            if (f32 && A.pb.mode == QPFRG_GRID_WEDGE) {
+                c = project32_guarded((float)(s_kx[i] - qx), (float)(s_ky[i] - qy), N);
+                if (c < 0) c = project64(s_kxd[i] - qxd, s_kyd[i] - qyd, N, A.pb.mode, A.pb.L);
+            } else if (f32) {
+                c = project64(s_kxd[i] - qxd, s_kyd[i] - qyd, N, A.pb.mode, A.pb.L);
+            } else {
+                c = project64((double)s_kx[i] - qxd, (double)s_ky[i] - qyd, N, A.pb.mode, A.pb.L);
+            }
             // cos(k+p-q) by angle addition
             const R crx = s_cx[i] * cqx + s_sx[i] * sqx;
             const R cry = s_cy[i] * cqy + s_sy[i] * sqy;
@@ -206,11 +267,14 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
     }
 }
 
-__global__ void z_update_kernel(const double *sig, double *Zout, int N, double T)
+// Z_j from the chord of Re Sigma over xi_j +- 2T.  rep[j] (may be NULL) is
+// the slot of j's C4v representative among the evaluated targets.
+__global__ void z_update_kernel(const double *sig, const int *rep, double *Zout, int N, double T)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
-    const double slope = (sig[2 * j] - sig[2 * j + 1]) / (4.0 * T);
+    const int s = rep ? rep[j] : j;
+    const double slope = (sig[2 * s] - sig[2 * s + 1]) / (4.0 * T);
     Zout[j] = 1.0 / (1.0 - slope);
 }
 
@@ -248,7 +312,7 @@ template <typename R>
 static qpfrg_status launch_sigma(qpfrg_ctx *c, bool hist, SigmaArgs<R> &A, int kid)
 {
     const int P = c->pb.P, N = c->pb.N;
-    const size_t smem = (size_t)(10 * P + 2 * N) * sizeof(R);
+    const size_t smem = (size_t)(10 * P + 2 * N) * sizeof(R) + 8 + (sizeof(R) == 4 ? 2 * (size_t)P * 8 : 0);
     auto kern = hist ? sigma_kernel<R, true> : sigma_kernel<R, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(c, e, "sigma smem attribute");
@@ -273,30 +337,39 @@ static void fill_args(qpfrg_ctx *c, SigmaArgs<R> &A, const FineTable<R> &fine, d
     A.T = T;
     A.nj = c->pb.N;
     A.jlist = nullptr;
+    A.kx64 = c->f64.kx;
+    A.ky64 = c->f64.ky;
     A.hist = c->d_hist;
     A.e_min = 0.0;
     A.inv_h = 1.0;
     A.nbins = 0;
 }
 
-qpfrg_status launch_sigma_z(qpfrg_ctx *c, double T, const double *d_V, const double *d_Z, double *d_Zout)
+qpfrg_status launch_sigma_z(qpfrg_ctx *c, double T, const double *d_V, const double *d_Z, double *d_Zout,
+                            bool use_symmetry)
 {
     const int N = c->pb.N;
+    const bool sym = use_symmetry && c->d_jirr != nullptr;
+    const int nj = sym ? c->n_irr : N;
     cudaError_t e = cudaMemsetAsync(c->d_sig, 0, 2 * (size_t)N * sizeof(double), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "memset sigma");
     qpfrg_status s;
     if (c->opt.precision == QPFRG_FP64) {
         SigmaArgs<double> A;
         fill_args(c, A, c->f64, T, d_V, d_Z);
+        A.nj = nj;
+        A.jlist = sym ? c->d_jirr : nullptr;
         s = launch_sigma(c, false, A, K_SIGMA_Z);
     } else {
         SigmaArgs<float> A;
         fill_args(c, A, c->f32, T, d_V, d_Z);
+        A.nj = nj;
+        A.jlist = sym ? c->d_jirr : nullptr;
         s = launch_sigma(c, false, A, K_SIGMA_Z);
     }
     if (s != QPFRG_OK) return s;
     prof_begin(c);
-    z_update_kernel<<<div_up(N, 128), 128, 0, c->stream>>>(c->d_sig, d_Zout, N, T);
+    z_update_kernel<<<div_up(N, 128), 128, 0, c->stream>>>(c->d_sig, sym ? c->d_rep : nullptr, d_Zout, N, T);
     prof_end(c, K_Z_UPDATE);
     e = cudaGetLastError();
     return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "z_update_kernel");

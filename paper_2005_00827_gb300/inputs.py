@@ -86,6 +86,7 @@ def batch_specs(count: int = 128, seed: int = 20050082):
 WORKLOADS = {
     "np16_n8": dict(N=16, n=8, U=2.0, T_end=0.05, z_feedback=False, n_omega=0),
     "np48_n16": dict(N=48, n=16, U=3.0, T_end=0.05, z_feedback=True, n_omega=512),
+    "np48_n32": dict(N=48, n=32, U=3.0, T_end=0.05, z_feedback=True, n_omega=512),
     "np96_n32": dict(N=96, n=32, U=2.5, T_end=0.02, z_feedback=True, n_omega=1024),
     "np192_n32": dict(N=192, n=32, U=2.0, T_end=0.01, z_feedback=True, n_omega=2048),
 }

@@ -105,6 +105,27 @@ def test_flow_with_z_feedback_trajectory(prec, tol):
     assert np.all(ref["Z"] > 0.0)
 
 
+@pytest.mark.parametrize("symmetric", [True, False])
+def test_z_feedback_after_set_state(symmetric):
+    """The flow evaluates Sigma only on the C4v-irreducible patches while the
+    state is symmetric; a state image without the symmetry switches back to
+    all patches.  Either way Z must equal the oracle's on every patch."""
+    import torch
+    N, n, U, T0 = 16, 4, 2.0, 0.7
+    V = inputs.random_vertex(N, U, seed=12, c4v=symmetric)
+    Z0 = inputs.z_profile(N, "aniso") if symmetric else np.random.default_rng(4).uniform(0.9, 1.0, N)
+    ref = Oracle(N, n, n, eta=0.02).zfactor(T0, V, Z0)
+    with api.Context(N, n, n, U=U, lambda0=T0, z_feedback=1, lambda_end=0.05) as c:
+        img = bytearray(api.qpfrg_get_state(c.h))
+        img[64:] = np.concatenate([V.ravel(), Z0]).tobytes()
+        api.qpfrg_set_state(c.h, bytes(img))
+        api.qpfrg_step(c.h, 1)
+        Zt = zeros(N)
+        api.qpfrg_read_state(c.h, None, Zt)
+        torch.cuda.synchronize()
+    assert np.abs(Zt.cpu().numpy() - ref).max() < 1e-10
+
+
 def test_checkpoint_resume():
     N, n, U = 16, 4, 2.5
     with api.Context(N, n, n, U=U, lambda_end=0.05) as a:

@@ -67,9 +67,10 @@ def test_geometry_matches_oracle():
     kf, fk, fw, fp = o.geometry()
     with api.Context(48, 16, 16) as ctx:
         gkf, fine = api.qpfrg_geometry(ctx.h)
-    assert np.abs(gkf - kf).max() < 1e-15
-    assert np.abs(fine[:, :2] - fk).max() < 1e-15
-    assert np.abs(fine[:, 2] - fw).max() < 1e-18
+    # same formulas on both sides; compilers may round a few ulp differently
+    assert np.abs(gkf - kf).max() < 4e-15
+    assert np.abs(fine[:, :2] - fk).max() < 4e-15
+    assert np.abs(fine[:, 2] - fw).max() / fw.max() < 1e-14
     assert np.array_equal(fine[:, 3].astype(int), fp)
 
 
