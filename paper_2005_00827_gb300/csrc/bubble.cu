@@ -39,6 +39,9 @@ struct BubbleArgs {
 // ---- scalar helpers ---------------------------------------------------------
 __device__ __forceinline__ float fexp(float x) { return __expf(x); }
 __device__ __forceinline__ double fexp(double x) { return exp(x); }
+// typed absolute value: plain fabs() on a float would promote to FP64
+__device__ __forceinline__ float qabs(float x) { return fabsf(x); }
+__device__ __forceinline__ double qabs(double x) { return fabs(x); }
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
 
@@ -46,7 +49,7 @@ __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
 template <typename R>
 __device__ __forceinline__ void fermi_pair(R x, R invT, R &f, R &fc)
 {
-    const R e = fexp(-fabs(x) * invT);
+    const R e = fexp(-qabs(x) * invT);
     const R lo = fdiv(e, R(1) + e), hi = fdiv(R(1), R(1) + e);
     f = x > R(0) ? lo : hi;
     fc = x > R(0) ? hi : lo;
@@ -56,7 +59,7 @@ __device__ __forceinline__ void fermi_pair(R x, R invT, R &f, R &fc)
 template <typename R>
 __device__ __forceinline__ R fermi_ff(R x, R invT)
 {
-    const R e = fexp(-fabs(x) * invT);
+    const R e = fexp(-qabs(x) * invT);
     const R d = R(1) + e;
     return fdiv(e, d * d);
 }
@@ -72,7 +75,7 @@ __device__ __forceinline__ R fermi_dT(R x, R invT)
 template <typename R>
 __device__ __forceinline__ R fermi_dxdT(R x, R invT)
 {
-    const R e = fexp(-fabs(x) * invT);
+    const R e = fexp(-qabs(x) * invT);
     const R d = R(1) + e;
     const R ff = fdiv(e, d * d);
     R th = fdiv(R(1) - e, d);
@@ -88,12 +91,12 @@ template <typename R>
 __device__ __forceinline__ R loop_T(bool pp, R xp, R gp, R xq, R invT, R thrT)
 {
     const R den = pp ? xp + xq : xp - xq;
-    if (fabs(den) < thrT) {
+    if (qabs(den) < thrT) {
         const R m = R(0.5) * (pp ? xp - xq : xp + xq);
         const R v = fermi_dxdT(m, invT);
         return pp ? -v : v;
     }
-    const R e = fexp(-fabs(xq) * invT);
+    const R e = fexp(-qabs(xq) * invT);
     const R d = R(1) + e, d2 = d * d;
     const R gq_num = xq * invT * invT * e;           // g_q * d2
     const R num = pp ? gp * d2 + gq_num : gp * d2 - gq_num;
@@ -107,7 +110,7 @@ template <typename R>
 __device__ __forceinline__ R loop_g(bool pp, R xp, R fp, R fcp, R xq, R invT, R thrT)
 {
     const R den = pp ? xp + xq : xp - xq;
-    if (fabs(den) < thrT) {
+    if (qabs(den) < thrT) {
         const R m = R(0.5) * (pp ? xp - xq : xp + xq);
         const R v = -fermi_ff(m, invT) * invT;       // f'(m)
         return pp ? -v : v;

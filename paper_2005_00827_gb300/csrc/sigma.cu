@@ -23,6 +23,9 @@ namespace qpfrg {
 
 __device__ __forceinline__ float sexp(float x) { return __expf(x); }
 __device__ __forceinline__ double sexp(double x) { return exp(x); }
+// typed absolute value: plain sabs() on a float would promote to FP64
+__device__ __forceinline__ float sabs(float x) { return fabsf(x); }
+__device__ __forceinline__ double sabs(double x) { return fabs(x); }
 __device__ __forceinline__ float sdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double sdiv(double a, double b) { return a / b; }
 __device__ __forceinline__ float srint(float x) { return rintf(x); }
@@ -32,11 +35,13 @@ __device__ __forceinline__ double satan2(double y, double x) { return atan2(y, x
 __device__ __forceinline__ float sfloor(float x) { return floorf(x); }
 __device__ __forceinline__ double sfloor(double x) { return floor(x); }
 
+// f(x) and 1 - f(x) without cancellation: with e = exp(-|x|/T) they are
+// e/(1+e) and 1/(1+e), one reciprocal.
 template <typename R>
 __device__ __forceinline__ void sfermi(R x, R invT, R &f, R &fc)
 {
-    const R e = sexp(-fabs(x) * invT);
-    const R lo = sdiv(e, R(1) + e), hi = sdiv(R(1), R(1) + e);
+    const R e = sexp(-sabs(x) * invT);
+    const R hi = sdiv(R(1), R(1) + e), lo = e * hi;
     f = x > R(0) ? lo : hi;
     fc = x > R(0) ? hi : lo;
 }
@@ -98,8 +103,10 @@ __device__ __forceinline__ int project32_guarded(float rx, float ry, int N)
     const float fr = u - fl;
     const float m = fminf(fr, 1.f - fr) * dth;
     if (m < 8e-6f || m * m * r2 < 6.4e-11f) return -1;
-    int j = (int)fl % N;
-    return j < 0 ? j + N : j;
+    int j = (int)fl;              // in [-N/2, N/2]
+    if (j < 0) j += N;
+    if (j >= N) j -= N;
+    return j;
 }
 
 template <typename R>
@@ -109,7 +116,7 @@ struct SigmaArgs {
     const double *kf;    // N x 2
     const double *V;     // N^3 FP64
     const double *Z;     // N
-    double *sig;         // [j][2]: Re Sigma at xi_j + 2T, xi_j - 2T
+    double *sig;         // [target]: chord slope of Re Sigma over xi_j +- 2T
     double T;
     int nj;
     const int *jlist;    // targets (may be NULL: j = blockIdx.z)
@@ -120,6 +127,31 @@ struct SigmaArgs {
     int nbins;
 };
 
+// Shared-memory record of one loop point p of patch a, for target k_j:
+// k+p (x, y), cos/sin of its components, line energy x_p, f_p, 1-f_p, w_p.
+constexpr int REC = 12;
+
+__device__ __forceinline__ void load_rec(const float *base, int i, float (&r)[REC])
+{
+    const float4 *p = reinterpret_cast<const float4 *>(base + REC * i);
+    const float4 a = p[0], b = p[1], c = p[2];
+    r[0] = a.x; r[1] = a.y; r[2] = a.z; r[3] = a.w;
+    r[4] = b.x; r[5] = b.y; r[6] = b.z; r[7] = b.w;
+    r[8] = c.x; r[9] = c.y; r[10] = c.z; r[11] = c.w;
+}
+
+__device__ __forceinline__ void load_rec(const double *base, int i, double (&r)[REC])
+{
+    const double2 *p = reinterpret_cast<const double2 *>(base + REC * i);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const double2 v = p[k];
+        r[2 * k] = v.x;
+        r[2 * k + 1] = v.y;
+    }
+    r[10] = r[11] = 0.0;
+}
+
 template <typename R, bool HIST>
 __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
 {
@@ -129,100 +161,100 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
     const int j = A.jlist ? A.jlist[jidx] : jidx;
     const int tid = threadIdx.x;
     const bool qp = A.pb.propagator == QPFRG_PROP_QP;
+    const bool wedge = A.pb.mode == QPFRG_GRID_WEDGE;
     const R invT = R(1.0 / A.T), eta = R(A.pb.eta);
     const R t = (R)A.pb.t, tp = (R)A.pb.tp, mu = (R)A.pb.mu;
+    constexpr bool f32 = sizeof(R) == 4;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *s_kx = reinterpret_cast<R *>(smem_raw);
-    R *s_ky = s_kx + P, *s_cx = s_ky + P, *s_sx = s_cx + P, *s_cy = s_sx + P, *s_sy = s_cy + P;
-    R *s_x = s_sy + P, *s_f = s_x + P, *s_fc = s_f + P, *s_w = s_fc + P;
-    R *s_V = s_w + P, *s_Z = s_V + N;
-    double *s_kxd = reinterpret_cast<double *>(smem_raw + (size_t)(10 * P + 2 * N) * sizeof(R) + 8 -
-                                               ((size_t)(10 * P + 2 * N) * sizeof(R)) % 8);
-    double *s_kyd = s_kxd + P;
-    constexpr bool f32 = sizeof(R) == 4;
+    R *s_rec = reinterpret_cast<R *>(smem_raw);          // P x REC
+    R *s_VZ = s_rec + (size_t)REC * P;                   // N x {V[j][a][c], Z_c}
+    double *s_kd = reinterpret_cast<double *>(s_VZ + 2 * N);   // P x {k+p} in FP64 (FP32 kernel)
 
     const double kx = A.kf[2 * j], ky = A.kf[2 * j + 1];
     for (int i = tid; i < N; i += blockDim.x) {
-        s_V[i] = (R)A.V[((long)j * N + a) * N + i];
-        s_Z[i] = A.Z ? (R)A.Z[i] : R(1);
+        s_VZ[2 * i] = (R)A.V[((long)j * N + a) * N + i];
+        s_VZ[2 * i + 1] = A.Z ? (R)A.Z[i] : R(1);
     }
     __syncthreads();
-    const R Za = s_Z[a];
+    const R Za = s_VZ[2 * a + 1];
     for (int i = tid; i < P; i += blockDim.x) {
         const int p = a * P + i;
-        // k_j + p in FP64, then cos/sin of its components
-        const double kpx = kx + (double)A.fine.kx[p], kpy = ky + (double)A.fine.ky[p];
+        // k_j + p in FP64 (from the FP64 table in either precision: the guarded
+        // FP32 projection falls back on exactly this sum), then cos/sin
+        const double kpx = kx + A.kx64[p], kpy = ky + A.ky64[p];
         double sxv, cxv, syv, cyv;
         sincos(kpx, &sxv, &cxv);
         sincos(kpy, &syv, &cyv);
-        s_kx[i] = (R)kpx;
-        s_ky[i] = (R)kpy;
-        if (f32) {
-            s_kxd[i] = kpx;
-            s_kyd[i] = kpy;
-        }
-        s_cx[i] = (R)cxv;
-        s_sx[i] = (R)sxv;
-        s_cy[i] = (R)cyv;
-        s_sy[i] = (R)syv;
+        R *rec = s_rec + (size_t)REC * i;
+        rec[0] = (R)kpx;
+        rec[1] = (R)kpy;
+        rec[2] = (R)cxv;
+        rec[3] = (R)sxv;
+        rec[4] = (R)cyv;
+        rec[5] = (R)syv;
         const R xp = qp ? Za * A.fine.xi[p] : A.fine.xi[p];
-        s_x[i] = xp;
+        rec[6] = xp;
         R f, fc;
         sfermi(xp, invT, f, fc);
-        s_f[i] = f;
-        s_fc[i] = fc;
-        s_w[i] = A.fine.w[p];
+        rec[7] = f;
+        rec[8] = fc;
+        rec[9] = A.fine.w[p];
+        rec[10] = rec[11] = R(0);
+        if (f32) {
+            s_kd[2 * i] = kpx;
+            s_kd[2 * i + 1] = kpy;
+        }
     }
     __syncthreads();
 
     const int q = blockIdx.x * blockDim.x + tid;
-    R rp = R(0), rm = R(0);
+    R acc = R(0);
     if (q < M) {
         const int b = q / P;
         const R qx = A.fine.kx[q], qy = A.fine.ky[q];
         const double qxd = A.kx64[q], qyd = A.ky64[q];
         const R cqx = A.fine.cx[q], sqx = A.fine.sx[q], cqy = A.fine.cy[q], sqy = A.fine.sy[q];
-        const R Zb = s_Z[b];
+        const R Zb = s_VZ[2 * b + 1];
         const R xq = qp ? Zb * A.fine.xi[q] : A.fine.xi[q];
         R fq, fcq;
         sfermi(xq, invT, fq, fcq);
-        const R wq = A.fine.w[q];
-        const R vab = s_V[b];
-        const R ZaZb = Za * Zb;
-        // chord frequencies xi_j -+ 2T (xi_j of the representative, FP64)
+        const R vab = s_VZ[2 * b];
+        const R pref = Za * Zb * A.fine.w[q];
+        // chord frequencies xi_j +- 2T (xi_j of the representative, FP64)
         const double ckx = cos(kx), cky = cos(ky);
         const double xij = -2.0 * A.pb.t * (ckx + cky) - 4.0 * A.pb.tp * ckx * cky - A.pb.mu;
-        const R wplus = (R)(xij + 2.0 * A.T), wminus = (R)(xij - 2.0 * A.T);
+        const R d0shift = (R)xij, twoT = (R)(2.0 * A.T);
         const R eta2 = eta * eta;
         for (int i = 0; i < P; ++i) {
+            R r[REC];
+            load_rec(s_rec, i, r);
             int c;
-            if (f32 && A.pb.mode == QPFRG_GRID_WEDGE) {
-                c = project32_guarded((float)(s_kx[i] - qx), (float)(s_ky[i] - qy), N);
-                if (c < 0) c = project64(s_kxd[i] - qxd, s_kyd[i] - qyd, N, A.pb.mode, A.pb.L);
+            if (f32 && wedge) {
+                c = project32_guarded((float)(r[0] - qx), (float)(r[1] - qy), N);
+                if (c < 0) c = project64(s_kd[2 * i] - qxd, s_kd[2 * i + 1] - qyd, N, A.pb.mode, A.pb.L);
             } else if (f32) {
-                c = project64(s_kxd[i] - qxd, s_kyd[i] - qyd, N, A.pb.mode, A.pb.L);
+                c = project64(s_kd[2 * i] - qxd, s_kd[2 * i + 1] - qyd, N, A.pb.mode, A.pb.L);
             } else {
-                c = project64((double)s_kx[i] - qxd, (double)s_ky[i] - qyd, N, A.pb.mode, A.pb.L);
+                c = project64((double)r[0] - qxd, (double)r[1] - qyd, N, A.pb.mode, A.pb.L);
             }
             // cos(k+p-q) by angle addition
-            const R crx = s_cx[i] * cqx + s_sx[i] * sqx;
-            const R cry = s_cy[i] * cqy + s_sy[i] * sqy;
+            const R crx = r[2] * cqx + r[3] * sqx;
+            const R cry = r[4] * cqy + r[5] * sqy;
             R xr = R(-2) * t * (crx + cry) - R(4) * tp * crx * cry - mu;
-            const R Zc = s_Z[c];
+            const R vac = s_VZ[2 * c], Zc = s_VZ[2 * c + 1];
             if (qp) xr *= Zc;
             R fr, fcr;
             sfermi(xr, invT, fr, fcr);
-            const R F = s_f[i] * fcq * fcr + s_fc[i] * fq * fr;
-            const R W = ZaZb * Zc * (R(2) * vab * vab - vab * s_V[c]);
-            const R amp = s_w[i] * wq * W * F;
-            const R E = xq + xr - s_x[i];
+            const R F = r[7] * fcq * fcr + r[8] * fq * fr;
+            const R amp = r[9] * pref * Zc * (R(2) * vab * vab - vab * vac) * F;
+            const R E = xq + xr - r[6];
             if (HIST) {
                 const double eb = ((double)E - A.e_min) * A.inv_h;
                 int bin = (int)floor(eb);
                 bin = bin < 0 ? 0 : (bin >= A.nbins ? A.nbins - 1 : bin);
                 const double d = (double)E - (A.e_min + (bin + 0.5) / A.inv_h);
-                double* h = A.hist + ((long)jidx * 5) * A.nbins + bin;
+                double *h = A.hist + ((long)jidx * 5) * A.nbins + bin;
                 double m = (double)amp;
 #pragma unroll
                 for (int mo = 0; mo < 5; ++mo) {
@@ -230,52 +262,40 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
                     m *= d;
                 }
             } else {
-                const R dp = wplus - E, dm = wminus - E;
-                rp += amp * sdiv(dp, dp * dp + eta2);
-                rm += amp * sdiv(dm, dm * dm + eta2);
+                // chord slope of Re 1/(w - E + i eta) over w = xi_j +- 2T:
+                // [d+/(d+^2+eta^2) - d-/(d-^2+eta^2)] / 4T
+                //   = (eta^2 - d+ d-) / ((d+^2 + eta^2)(d-^2 + eta^2))
+                const R d0 = d0shift - E;
+                const R dp = d0 + twoT, dm = d0 - twoT;
+                acc += amp * sdiv(eta2 - dp * dm, (dp * dp + eta2) * (dm * dm + eta2));
             }
         }
     }
     if (HIST) return;
-    // block reduction of the two partial sums
-    __shared__ double red[2][32];
-    double vp = (double)rp, vm = (double)rm;
+    // block reduction of the partial slopes
+    __shared__ double red[32];
+    double v = (double)acc;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        vp += __shfl_down_sync(0xffffffffu, vp, off);
-        vm += __shfl_down_sync(0xffffffffu, vm, off);
-    }
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
     const int lane = tid & 31, warp = tid >> 5;
-    if (lane == 0) {
-        red[0][warp] = vp;
-        red[1][warp] = vm;
-    }
+    if (lane == 0) red[warp] = v;
     __syncthreads();
     if (warp == 0) {
         const int nw = blockDim.x >> 5;
-        vp = lane < nw ? red[0][lane] : 0.0;
-        vm = lane < nw ? red[1][lane] : 0.0;
+        v = lane < nw ? red[lane] : 0.0;
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            vp += __shfl_down_sync(0xffffffffu, vp, off);
-            vm += __shfl_down_sync(0xffffffffu, vm, off);
-        }
-        if (lane == 0) {
-            atomicAdd(&A.sig[2 * jidx], vp);
-            atomicAdd(&A.sig[2 * jidx + 1], vm);
-        }
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) atomicAdd(&A.sig[jidx], v);
     }
 }
 
-// Z_j from the chord of Re Sigma over xi_j +- 2T.  rep[j] (may be NULL) is
-// the slot of j's C4v representative among the evaluated targets.
-__global__ void z_update_kernel(const double *sig, const int *rep, double *Zout, int N, double T)
+// Z_j = 1/(1 - slope) with the chord slope accumulated per target.  rep[j]
+// (may be NULL) is the slot of j's C4v representative among the targets.
+__global__ void z_update_kernel(const double *slope, const int *rep, double *Zout, int N)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
-    const int s = rep ? rep[j] : j;
-    const double slope = (sig[2 * s] - sig[2 * s + 1]) / (4.0 * T);
-    Zout[j] = 1.0 / (1.0 - slope);
+    Zout[j] = 1.0 / (1.0 - slope[rep ? rep[j] : j]);
 }
 
 // Sigma on the grid from the binned moments: sum_b sum_n H_n[b] / (z - E_b)^(n+1),
@@ -312,7 +332,7 @@ template <typename R>
 static qpfrg_status launch_sigma(qpfrg_ctx *c, bool hist, SigmaArgs<R> &A, int kid)
 {
     const int P = c->pb.P, N = c->pb.N;
-    const size_t smem = (size_t)(10 * P + 2 * N) * sizeof(R) + 8 + (sizeof(R) == 4 ? 2 * (size_t)P * 8 : 0);
+    const size_t smem = (size_t)(REC * P + 2 * N) * sizeof(R) + (sizeof(R) == 4 ? 2 * (size_t)P * 8 : 0);
     auto kern = hist ? sigma_kernel<R, true> : sigma_kernel<R, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(c, e, "sigma smem attribute");
@@ -349,7 +369,10 @@ qpfrg_status launch_sigma_z(qpfrg_ctx *c, double T, const double *d_V, const dou
                             bool use_symmetry)
 {
     const int N = c->pb.N;
-    const bool sym = use_symmetry && c->d_jirr != nullptr;
+    // The zone edge breaks the C4v covariance of the angular projection at
+    // the rounding level (mirror pairs land on |k_x| = pi exactly), which
+    // moves Z on symmetric patches by ~1e-6: reduce in mixed precision only.
+    const bool sym = use_symmetry && c->d_jirr != nullptr && c->opt.precision != QPFRG_FP64;
     const int nj = sym ? c->n_irr : N;
     cudaError_t e = cudaMemsetAsync(c->d_sig, 0, 2 * (size_t)N * sizeof(double), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "memset sigma");
@@ -369,7 +392,7 @@ qpfrg_status launch_sigma_z(qpfrg_ctx *c, double T, const double *d_V, const dou
     }
     if (s != QPFRG_OK) return s;
     prof_begin(c);
-    z_update_kernel<<<div_up(N, 128), 128, 0, c->stream>>>(c->d_sig, sym ? c->d_rep : nullptr, d_Zout, N, T);
+    z_update_kernel<<<div_up(N, 128), 128, 0, c->stream>>>(c->d_sig, sym ? c->d_rep : nullptr, d_Zout, N);
     prof_end(c, K_Z_UPDATE);
     e = cudaGetLastError();
     return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "z_update_kernel");
