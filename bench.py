@@ -110,7 +110,7 @@ def run_qpfrg(args):
         dist.init_process_group("nccl")
     wl = inputs.WORKLOADS[args.workload]
     N, n, U = wl["N"], wl["n"], wl["U"]
-    prec = api.QPFRG_MIXED if args.precision == "mixed" else api.QPFRG_FP64
+    prec = {"mixed": api.QPFRG_MIXED, "tc": api.QPFRG_MIXED_TC, "fp64": api.QPFRG_FP64}[args.precision]
     stream = torch.cuda.current_stream()
     ctx = api.Context(N, n, n, U=U, lambda0=1.0, precision=prec, lambda_end=wl["T_end"],
                       z_feedback=int(wl["z_feedback"]), eta=0.02, stream=stream.cuda_stream)
@@ -167,7 +167,8 @@ def run_qpfrg(args):
     dV_t = torch.from_numpy(V.ravel()).cuda()
     Z_t = torch.from_numpy(Z).cuda()
     out = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
-    for name, pr, reps in (("mixed", api.QPFRG_MIXED, 10), ("fp64", api.QPFRG_FP64, 3)):
+    forms = (("mixed", api.QPFRG_MIXED, 10), ("tc", api.QPFRG_MIXED_TC, 10), ("fp64", api.QPFRG_FP64, 3))
+    for name, pr, reps in forms:
         with api.Context(N, n, n, U=U, precision=pr, stream=stream.cuda_stream) as c2:
             api.qpfrg_rhs(c2.h, 0.1, dV_t, Z_t, out)
             torch.cuda.synchronize()
@@ -179,6 +180,7 @@ def run_qpfrg(args):
             torch.cuda.synchronize()
             extra[f"rhs_only_{name}_per_s"] = reps / (a.elapsed_time(b) / 1e3)
     extra["mixed_vs_fp64_rhs"] = extra["rhs_only_mixed_per_s"] / extra["rhs_only_fp64_per_s"]
+    extra["tc_vs_fp64_rhs"] = extra["rhs_only_tc_per_s"] / extra["rhs_only_fp64_per_s"]
 
     # roofline of the dominant kernel (ALU bound: FP32 issue and MUFU pipes)
     peaks, peak_kind = load_peaks()
@@ -207,7 +209,7 @@ def run_qpfrg(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == api.QPFRG_MIXED else "f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": {api.QPFRG_MIXED: "f32+f64", api.QPFRG_MIXED_TC: "bf16x3+f32+f64"}.get(prec, "f64"),
         "data": "synthetic (seeded lattice parameters; no dataset in the paper)",
         "config": {"workload": args.workload, "N_p": N, "fine_grid": f"{n}x{n}", "U": U,
                    "flow": "T-flow from T=1, dlnT=ln0.98, Z feedback, eta=0.02",
@@ -284,7 +286,7 @@ def main():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="qpfrg", choices=["qpfrg", "reference"])
     p.add_argument("--workload", default=WORKLOAD)
-    p.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    p.add_argument("--precision", default="mixed", choices=["mixed", "tc", "fp64"])
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     args = p.parse_args()

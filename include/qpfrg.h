@@ -68,7 +68,9 @@ typedef enum {
 typedef enum {
     QPFRG_FP64 = 0,              /* every step in FP64                                */
     QPFRG_MIXED = 1,             /* FP32 loop kernels and contraction, FP64 ODE state  */
-    QPFRG_MIXED_TC = 2           /* reserved: tensor-core contraction                  */
+    QPFRG_MIXED_TC = 2           /* as MIXED, contraction on tcgen05 tensor cores with
+                                    BF16 hi/lo split products (hi*hi + hi*lo + lo*hi) and
+                                    FP32 accumulation; needs n_p^2 % 8 == 0                */
 } qpfrg_precision;
 
 typedef enum {

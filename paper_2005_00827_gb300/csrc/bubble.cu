@@ -16,6 +16,8 @@
 // thread), streams the partner-patch bytes of each Q (coalesced), merges
 // equal consecutive partners in registers and adds runs into shared-memory
 // rows of N accumulators, G transfers per barrier, double-buffered.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 
 #include "qpfrg_internal.h"
@@ -34,7 +36,19 @@ struct BubbleArgs {
     R *B;
     R T, invT, g, thr;
     int qchunk;
+    // formed operands of the tensor-core contraction (QPFRG_MIXED_TC)
+    const float *Vf;            // stage vertex, FP32 [k1][k2][k3]
+    const float *VT;            // VT[j][l][b] = V[b][j][l]
+    __nv_bfloat16 *App[2];      // [N^2][N^2]   hi, lo: B_pp[Q][a][b] V[Q][a]
+    __nv_bfloat16 *Acr[2];      // [N^2][N^2]   row (j,l) of Q = (l,j): B_ph[Q][a][b] V[b][j][l]
+    __nv_bfloat16 *Ad[2];       // [N^2][2N^2]  B_ph[Q][a][b] (2V[i,a,l] - V[a,i,l]) | -B_ph V[i,a,l]
 };
+
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo)
+{
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
 
 // ---- scalar helpers ---------------------------------------------------------
 __device__ __forceinline__ float fexp(float x) { return __expf(x); }
@@ -155,7 +169,7 @@ __device__ __forceinline__ void load_partners(const uint8_t *src, int (&b)[PPT],
     for (int u = 0; u < PPT; ++u) b[u] = u < nvalid ? src[u] : 0;
 }
 
-template <typename R, int PPT>
+template <typename R, int PPT, bool FORM>
 __global__ void __launch_bounds__(256) bubble_kernel(BubbleArgs<R> A)
 {
     const int N = A.pb.N, P = A.pb.P, M = A.pb.M;
@@ -251,35 +265,62 @@ __global__ void __launch_bounds__(256) bubble_kernel(BubbleArgs<R> A)
             }
         }
         __syncthreads();
-        for (int idx = tid; idx < G * N; idx += nthr) {
-            const int g = idx / N, b = idx - g * N;
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+        for (int b = tid; b < N; b += nthr) {
+            const int idx = g * N + b;
             const int Q = Qb + g;
             const R v = accb[idx];
             accb[idx] = R(0);
             if (Q < q1) {
                 const R Zb = Zs[b];
                 const R s = tflow ? Za * Zb : A.g * Za * Zb * (Za + Zb);
-                A.B[(((long)fam * NN + Q) * N + a) * (long)N + b] = v * s;
+                if constexpr (!FORM) {
+                    A.B[(((long)fam * NN + Q) * N + a) * (long)N + b] = v * s;
+                } else {
+                    const float bt = (float)(v * s);
+                    const long col = (long)a * N + b;
+                    __nv_bfloat16 h, l;
+                    if (pp) {
+                        split_bf16(bt * A.Vf[(long)Q * N + a], h, l);
+                        A.App[0][(long)Q * NN + col] = h;
+                        A.App[1][(long)Q * NN + col] = l;
+                    } else {
+                        const int x = Q / N, y = Q - (Q / N) * N;          // Q = k_F(x) - k_F(y)
+                        const long rcr = (long)y * N + x;                 // cr row (j,l) = (y,x)
+                        split_bf16(bt * A.VT[rcr * N + b], h, l);
+                        A.Acr[0][rcr * NN + col] = h;
+                        A.Acr[1][rcr * NN + col] = l;
+                        const float v_ial = A.Vf[((long)x * N + a) * N + y];
+                        const float v_ail = A.Vf[((long)a * N + x) * N + y];
+                        split_bf16(bt * (2.f * v_ial - v_ail), h, l);
+                        A.Ad[0][(long)Q * 2 * NN + col] = h;
+                        A.Ad[1][(long)Q * 2 * NN + col] = l;
+                        split_bf16(-bt * v_ial, h, l);
+                        A.Ad[0][(long)Q * 2 * NN + NN + col] = h;
+                        A.Ad[1][(long)Q * 2 * NN + NN + col] = l;
+                    }
+                }
             }
         }
     }
 }
 
-template <typename R, int PPT>
+template <typename R, int PPT, bool FORM>
 static void launch_t(qpfrg_ctx *c, const BubbleArgs<R> &A, int nthr, int qchunks)
 {
     const int N = c->pb.N;
     dim3 grid(N, qchunks, 2);
     const size_t smem = (2 * G + 1) * (size_t)N * sizeof(R);
-    bubble_kernel<R, PPT><<<grid, nthr, smem, c->stream>>>(A);
+    bubble_kernel<R, PPT, FORM><<<grid, nthr, smem, c->stream>>>(A);
 }
 
-template <typename R>
+template <typename R, bool FORM>
 static qpfrg_status launch_r(qpfrg_ctx *c, double lambda, const double *d_Z, const FineTable<R> &fine,
                              const TransferTable<R> &qpp, const TransferTable<R> &qph, R thr)
 {
     const Problem &pb = c->pb;
-    BubbleArgs<R> A;
+    BubbleArgs<R> A{};
     A.pb = pb;
     A.fine = fine;
     A.qpp = qpp;
@@ -287,6 +328,13 @@ static qpfrg_status launch_r(qpfrg_ctx *c, double lambda, const double *d_Z, con
     A.part = c->d_part;
     A.Z = d_Z;
     A.B = reinterpret_cast<R *>(c->d_B);
+    A.Vf = c->d_Vf;
+    A.VT = c->tc.VT;
+    for (int h = 0; h < 2; ++h) {
+        A.App[h] = c->tc.App[h];
+        A.Acr[h] = c->tc.Acr[h];
+        A.Ad[h] = c->tc.Ad[h];
+    }
     const bool tflow = pb.regulator == QPFRG_REG_TEMPERATURE;
     const double T = tflow ? lambda : pb.T_fixed;
     A.T = (R)T;
@@ -308,10 +356,10 @@ static qpfrg_status launch_r(qpfrg_ctx *c, double lambda, const double *d_Z, con
     nthr = std::max(32, ((nthr + 31) / 32) * 32);
     prof_begin(c);
     switch (ppt) {
-    case 1: launch_t<R, 1>(c, A, nthr, qchunks); break;
-    case 2: launch_t<R, 2>(c, A, nthr, qchunks); break;
-    case 4: launch_t<R, 4>(c, A, nthr, qchunks); break;
-    default: launch_t<R, 8>(c, A, nthr, qchunks); break;
+    case 1: launch_t<R, 1, FORM>(c, A, nthr, qchunks); break;
+    case 2: launch_t<R, 2, FORM>(c, A, nthr, qchunks); break;
+    case 4: launch_t<R, 4, FORM>(c, A, nthr, qchunks); break;
+    default: launch_t<R, 8, FORM>(c, A, nthr, qchunks); break;
     }
     prof_end(c, K_BUBBLE);
     cudaError_t e = cudaGetLastError();
@@ -321,8 +369,13 @@ static qpfrg_status launch_r(qpfrg_ctx *c, double lambda, const double *d_Z, con
 qpfrg_status launch_bubbles(qpfrg_ctx *c, double lambda, const double *d_Z)
 {
     if (c->opt.precision == QPFRG_FP64)
-        return launch_r<double>(c, lambda, d_Z, c->f64, c->qpp64, c->qph64, 1e-5);
-    return launch_r<float>(c, lambda, d_Z, c->f32, c->qpp32, c->qph32, 2e-2f);
+        return launch_r<double, false>(c, lambda, d_Z, c->f64, c->qpp64, c->qph64, 1e-5);
+    if (c->opt.precision == QPFRG_MIXED_TC) {
+        qpfrg_status s = launch_tc_prep(c);       // B operands and V^T of this stage
+        if (s != QPFRG_OK) return s;
+        return launch_r<float, true>(c, lambda, d_Z, c->f32, c->qpp32, c->qph32, 2e-2f);
+    }
+    return launch_r<float, false>(c, lambda, d_Z, c->f32, c->qpp32, c->qph32, 2e-2f);
 }
 
 }  // namespace qpfrg

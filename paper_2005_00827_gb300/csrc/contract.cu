@@ -172,6 +172,23 @@ static qpfrg_status launch_all(qpfrg_ctx *c, const VR *V, double scale, double *
 
 qpfrg_status launch_contractions(qpfrg_ctx *c, const void *d_Vin, double scale, double *d_out)
 {
+    if (c->opt.precision == QPFRG_MIXED_TC) {
+        // formed operands were written by the bubble kernel of this stage
+        const int N = c->pb.N, NN = N * N, Np = c->tc.Npad;
+        const unsigned ch = c->pb.channels;
+        const TcBuffers &t = c->tc;
+        qpfrg_status s = QPFRG_OK;
+        if ((ch & QPFRG_CH_PP) &&
+            (s = launch_tc_gemm(c, t.App[0], t.App[1], t.Bpp[0], t.Bpp[1], NN, NN, N, Np, 0, -scale, d_out, K_TC_PP)))
+            return s;
+        if ((ch & QPFRG_CH_CR) &&
+            (s = launch_tc_gemm(c, t.Acr[0], t.Acr[1], t.Bcr[0], t.Bcr[1], NN, NN, N, Np, 1, -scale, d_out, K_TC_CR)))
+            return s;
+        if ((ch & QPFRG_CH_D) &&
+            (s = launch_tc_gemm(c, t.Ad[0], t.Ad[1], t.Bd[0], t.Bd[1], NN, 2 * NN, N, Np, 2, scale, d_out, K_TC_D)))
+            return s;
+        return QPFRG_OK;
+    }
     if (c->opt.precision == QPFRG_FP64)
         return launch_all<double, double>(c, reinterpret_cast<const double *>(d_Vin), scale, d_out);
     return launch_all<float, float>(c, reinterpret_cast<const float *>(d_Vin), scale, d_out);

@@ -220,6 +220,20 @@ qpfrg_status upload_geometry(qpfrg_ctx *c)
         return cuda_fail(c, e, "cudaMalloc(kf)");
     if ((e = cudaMemcpy(c->d_kf, c->kf.data(), 2 * N * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(c, e, "upload kf");
+    {
+        std::vector<double> xij(N);
+        std::vector<double2> bnd(N);
+        for (int j = 0; j < N; ++j) {
+            xij[j] = host_xi(c->pb, c->kf[2 * j], c->kf[2 * j + 1]);
+            const double th = (j - 0.5) * kTwoPi / N;
+            bnd[j] = make_double2(std::cos(th), std::sin(th));
+        }
+        if ((e = cudaMalloc((void **)&c->d_xij, N * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc((void **)&c->d_bnd, N * sizeof(double2))) != cudaSuccess)
+            return cuda_fail(c, e, "cudaMalloc(xi_j, rays)");
+        cudaMemcpy(c->d_xij, xij.data(), N * sizeof(double), cudaMemcpyHostToDevice);
+        cudaMemcpy(c->d_bnd, bnd.data(), N * sizeof(double2), cudaMemcpyHostToDevice);
+    }
     if ((e = cudaMalloc((void **)&c->d_Qpp, 2 * NN * sizeof(double))) != cudaSuccess ||
         (e = cudaMalloc((void **)&c->d_Qph, 2 * NN * sizeof(double))) != cudaSuccess)
         return cuda_fail(c, e, "cudaMalloc(Q)");

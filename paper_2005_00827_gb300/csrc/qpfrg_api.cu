@@ -17,6 +17,7 @@ namespace {
 const char *const kKernelNames[K_COUNT] = {
     "partner_map", "bubble", "contract_pp", "contract_cr", "contract_d", "sigma_z",
     "sigma_hist", "sigma_grid", "z_update", "rk_stage", "rk_final", "convert_f32",
+    "tc_prep", "tc_gemm_pp", "tc_gemm_cr", "tc_gemm_d",
 };
 
 struct PendingEvent {
@@ -209,7 +210,9 @@ void qpfrg_destroy(qpfrg_t c)
                     c->qph64.cy, c->qph64.sy, c->qpp32.cx, c->qpp32.sx, c->qpp32.cy, c->qpp32.sy,
                     c->qph32.cx, c->qph32.sx, c->qph32.cy, c->qph32.sy, c->d_kf, c->d_Qpp, c->d_Qph,
                     c->d_part, c->d_B, c->d_V, c->d_Z, c->d_Vs, c->d_k, c->d_acc, c->d_ones, c->d_Vf,
-                    c->d_Zwork, c->d_sig, c->d_hist, c->d_red, c->d_jirr, c->d_rep};
+                    c->d_Zwork, c->d_sig, c->d_hist, c->d_red, c->d_jirr, c->d_rep, c->tc.App[0], c->tc.App[1],
+                    c->tc.Acr[0], c->tc.Acr[1], c->tc.Ad[0], c->tc.Ad[1], c->tc.Bpp[0], c->tc.Bpp[1], c->tc.Bcr[0],
+                    c->tc.Bcr[1], c->tc.Bd[0], c->tc.Bd[1], c->tc.VT, c->d_tc_err, c->d_xij, c->d_bnd};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->h_red) cudaFreeHost(c->h_red);
@@ -273,11 +276,8 @@ qpfrg_status qpfrg_create(const qpfrg_lattice *lattice, int n_p, const qpfrg_fin
         return fail(set_err(c, QPFRG_ERR_INVALID, "lambda0 must be T > 0 (T-flow) or g >= 0 (g-flow)"));
     if (!tflow && !(pb.T_fixed > 0.0))
         return fail(set_err(c, QPFRG_ERR_INVALID, "interaction flow needs T_fixed > 0"));
-    if (c->opt.precision != QPFRG_FP64 && c->opt.precision != QPFRG_MIXED) {
-        if (c->opt.precision == QPFRG_MIXED_TC)
-            return fail(set_err(c, QPFRG_ERR_UNSUPPORTED, "MIXED_TC precision is not implemented"));
+    if (c->opt.precision != QPFRG_FP64 && c->opt.precision != QPFRG_MIXED && c->opt.precision != QPFRG_MIXED_TC)
         return fail(set_err(c, QPFRG_ERR_INVALID, "unknown precision"));
-    }
     if (pb.propagator != QPFRG_PROP_PAPER && pb.propagator != QPFRG_PROP_QP)
         return fail(set_err(c, QPFRG_ERR_INVALID, "unknown propagator mode"));
     if (c->opt.z_feedback && !tflow)
@@ -311,6 +311,8 @@ qpfrg_status qpfrg_create(const qpfrg_lattice *lattice, int n_p, const qpfrg_fin
         return fail(set_err(c, QPFRG_ERR_INVALID, "unknown fine-grid mode"));
     }
     pb.M = pb.N * pb.P;
+    if (c->opt.precision == QPFRG_MIXED_TC && ((long)n_p * n_p) % 8 != 0)
+        return fail(set_err(c, QPFRG_ERR_UNSUPPORTED, "tensor-core contraction needs n_p^2 % 8 == 0"));
 
     // ---- device ------------------------------------------------------------
     int ndev = 0;
@@ -328,12 +330,29 @@ qpfrg_status qpfrg_create(const qpfrg_lattice *lattice, int n_p, const qpfrg_fin
 
     const size_t N = pb.N, n3 = N * N * N, n4 = n3 * N;
     const size_t rsz = c->opt.precision == QPFRG_FP64 ? sizeof(double) : sizeof(float);
-    c->B_bytes = 2 * n4 * rsz;
+    const bool tcmode = c->opt.precision == QPFRG_MIXED_TC;
+    c->B_bytes = tcmode ? 0 : 2 * n4 * rsz;
     if (std::getenv("QPFRG_TEST_FAIL_ALLOC")) {   // host-side fault injection for tests
         c->err = "allocation failure injected by QPFRG_TEST_FAIL_ALLOC";
         return fail(QPFRG_ERR_OOM);
     }
-    if ((s = dev_alloc(c, (unsigned char **)&c->d_B, c->B_bytes, "bubble tables")) != QPFRG_OK) return fail(s);
+    if (!tcmode && (s = dev_alloc(c, (unsigned char **)&c->d_B, c->B_bytes, "bubble tables")) != QPFRG_OK)
+        return fail(s);
+    if (tcmode) {
+        TcBuffers &t = c->tc;
+        t.Npad = (int)((N + 15) / 16 * 16);
+        const size_t NN = N * N, Np = t.Npad;
+        for (int h = 0; h < 2; ++h)
+            if ((s = dev_alloc(c, &t.App[h], NN * NN, "formed pp table")) ||
+                (s = dev_alloc(c, &t.Acr[h], NN * NN, "formed cr table")) ||
+                (s = dev_alloc(c, &t.Ad[h], 2 * NN * NN, "formed d table")) ||
+                (s = dev_alloc(c, &t.Bpp[h], Np * NN, "pp operand")) ||
+                (s = dev_alloc(c, &t.Bcr[h], Np * NN, "cr operand")) || (s = dev_alloc(c, &t.Bd[h], 2 * Np * NN, "d operand")))
+                return fail(s);
+        if ((s = dev_alloc(c, &t.VT, n3, "V transpose")) || (s = dev_alloc(c, &c->d_tc_err, 1, "tc error flag")))
+            return fail(s);
+        cudaMemset(c->d_tc_err, 0, sizeof(unsigned));
+    }
     if ((s = dev_alloc(c, &c->d_V, n3, "V")) || (s = dev_alloc(c, &c->d_Vs, n3, "V stage")) ||
         (s = dev_alloc(c, &c->d_k, n3, "k")) || (s = dev_alloc(c, &c->d_acc, n3, "acc")) ||
         (s = dev_alloc(c, &c->d_Vf, n3, "V fp32")) || (s = dev_alloc(c, &c->d_Z, N, "Z")) ||
@@ -391,7 +410,7 @@ qpfrg_status qpfrg_rhs(qpfrg_t c, double lambda, const double *d_V, const double
     const long n3 = n3_of(c);
     const void *Vin = d_V;
     qpfrg_status s;
-    if (c->opt.precision == QPFRG_MIXED) {
+    if (c->opt.precision != QPFRG_FP64) {
         if ((s = launch_convert_f32(c, d_V, c->d_Vf, n3)) != QPFRG_OK) return s;
         Vin = c->d_Vf;
     }
@@ -440,7 +459,7 @@ static qpfrg_status do_step(qpfrg_ctx *c)
     if ((tflow && x + h < x_end) || (!tflow && x + h > x_end)) h = x_end - x;
     const long n3 = n3_of(c);
     const int N = c->pb.N;
-    const bool mixed = c->opt.precision == QPFRG_MIXED;
+    const bool mixed = c->opt.precision != QPFRG_FP64;
     qpfrg_status s;
     cudaError_t e;
 
@@ -489,8 +508,12 @@ static qpfrg_status do_step(qpfrg_ctx *c)
         }
     }
     e = cudaMemcpyAsync(c->h_red, c->d_red, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);
+    unsigned tc_err = 0;
+    if (e == cudaSuccess && c->d_tc_err)
+        e = cudaMemcpyAsync(&tc_err, c->d_tc_err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "flow step");
+    if (tc_err) return set_err(c, QPFRG_ERR_TIMEOUT, "a tensor-core contraction wait expired");
     double m_new;
     std::memcpy(&m_new, &c->h_red[0], sizeof(double));
     const double x_new = x + h;

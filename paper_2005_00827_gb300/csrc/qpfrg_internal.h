@@ -2,6 +2,7 @@
 // the public ABI (include/qpfrg.h).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -29,6 +30,10 @@ enum KernelId {
     K_RK_STAGE,
     K_RK_FINAL,
     K_CONVERT,
+    K_TC_PREP,
+    K_TC_PP,
+    K_TC_CR,
+    K_TC_D,
     K_COUNT
 };
 
@@ -62,6 +67,18 @@ struct TransferTable {   // for Q index x*N + y (pp: k_F(x)+k_F(y); ph: k_F(x)-k
     R *cx, *sx, *cy, *sy;
 };
 
+// Buffers of the tensor-core contraction (QPFRG_MIXED_TC), index 0 = hi, 1 = lo.
+struct TcBuffers {
+    __nv_bfloat16 *App[2] = {nullptr, nullptr};   // [N^2][N^2]
+    __nv_bfloat16 *Acr[2] = {nullptr, nullptr};   // [N^2][N^2]
+    __nv_bfloat16 *Ad[2] = {nullptr, nullptr};    // [N^2][2N^2]
+    __nv_bfloat16 *Bpp[2] = {nullptr, nullptr};   // [Npad][N^2]
+    __nv_bfloat16 *Bcr[2] = {nullptr, nullptr};   // [Npad][N^2]
+    __nv_bfloat16 *Bd[2] = {nullptr, nullptr};    // [Npad][2N^2]
+    float *VT = nullptr;                          // [N][N][N]
+    int Npad = 0;
+};
+
 struct ProfileSlot {
     double ms = 0.0;
     long long launches = 0;
@@ -89,12 +106,17 @@ struct qpfrg_ctx {
     qpfrg::TransferTable<double> qpp64{}, qph64{};
     qpfrg::TransferTable<float> qpp32{}, qph32{};
     double *d_kf = nullptr;      // N x 2
+    double *d_xij = nullptr;     // N: xi(k_F(j))
+    double2 *d_bnd = nullptr;    // N: (cos, sin) of the ray between wedges j-1 and j
     double *d_Qpp = nullptr, *d_Qph = nullptr;  // N^2 x 2 transfer momenta (FP64)
     uint8_t *d_part = nullptr;   // 2 x N^2 x M partner patches (pp family, then ph)
 
     // bubble tables B[f][Q][a][b] (FP32 or FP64 according to precision)
     void *d_B = nullptr;
     size_t B_bytes = 0;
+
+    qpfrg::TcBuffers tc;
+    unsigned *d_tc_err = nullptr;   // set by a tensor-core CTA whose bounded wait expired
 
     // flow state and work buffers
     double *d_V = nullptr, *d_Z = nullptr;
@@ -142,6 +164,12 @@ qpfrg_status launch_sigma_z(qpfrg_ctx *c, double T, const double *d_V, const dou
                             double *d_Zout, bool use_symmetry);
 qpfrg_status launch_sigma_grid(qpfrg_ctx *c, double T, const double *d_V, const double *d_Z,
                                double *d_re, double *d_im);
+
+// tc_gemm.cu / tc_prep: tensor-core contraction
+qpfrg_status launch_tc_prep(qpfrg_ctx *c);
+qpfrg_status launch_tc_gemm(qpfrg_ctx *c, const __nv_bfloat16 *Ahi, const __nv_bfloat16 *Alo,
+                            const __nv_bfloat16 *Bhi, const __nv_bfloat16 *Blo, int M, int K, int Ncol,
+                            int Npad, int map_mode, double scale, double *out, int kid);
 
 // ode.cu
 qpfrg_status launch_convert_f32(qpfrg_ctx *c, const double *d_in, float *d_out, long n);

@@ -84,29 +84,60 @@ __device__ __forceinline__ float atan2_poly(float y, float x)
     return copysignf(a, y);
 }
 
+// Round to nearest even without a conversion instruction (|x| < 2^22): the
+// float sum with 1.5 * 2^23 keeps rint(x) in its low mantissa bits.
+__device__ __forceinline__ float rint_add(float x, int &as_int)
+{
+    const float s = x + 12582912.f;
+    as_int = __float_as_int(s) - 0x4B400000;
+    return s - 12582912.f;
+}
+
 // FP32 wedge projection with a guard band: the FP32 momentum carries an
-// absolute error below 2.1e-6 per vector (FP32 rounding of k+p, q, their
+// absolute error below 1.4e-6 per component (FP32 rounding of k+p, q, their
 // difference and the fold) and atan2_poly below 1.7e-6 rad, so the angle is
-// trusted only when it lies more than 4e-6 + 4e-6/|r| rad from a wedge
+// trusted only when it lies more than 8e-6 + 8e-6/|r| rad from a wedge
 // boundary and the point is more than 4e-6 from the zone edge.  Returns -1
-// when the caller must project in FP64.
-__device__ __forceinline__ int project32_guarded(float rx, float ry, int N)
+// when the caller must decide in FP64; *jc gets the nearest-centre estimate.
+__device__ __forceinline__ int project32_guarded(float rx, float ry, int N, float inv_dth, float dth, int &jc)
 {
     const float tp = 6.28318531f;
-    const float x = rx - tp * rintf(rx * 0.159154943f);
-    const float y = ry - tp * rintf(ry * 0.159154943f);
+    int ix;
+    const float x = rx - tp * rint_add(rx * 0.159154943f, ix);
+    const float y = ry - tp * rint_add(ry * 0.159154943f, ix);
     const float r2 = x * x + y * y;
+    const float u = atan2_poly(y, x) * inv_dth;      // angle in units of the wedge width
+    int j;
+    const float fj = rint_add(u, j);                 // nearest centre
+    jc = j;
     if (fabsf(x) > 3.14159265f - 4e-6f || fabsf(y) > 3.14159265f - 4e-6f || r2 < 1e-8f) return -1;
-    const float dth = tp / (float)N;
-    const float u = atan2_poly(y, x) / dth + 0.5f;
-    const float fl = floorf(u);
-    const float fr = u - fl;
-    const float m = fminf(fr, 1.f - fr) * dth;
+    const float m = (0.5f - fabsf(u - fj)) * dth;    // distance to the nearest boundary, rad
     if (m < 8e-6f || m * m * r2 < 6.4e-11f) return -1;
-    int j = (int)fl;              // in [-N/2, N/2]
     if (j < 0) j += N;
     if (j >= N) j -= N;
     return j;
+}
+
+// FP64 decision for the guarded cases: fold (ties to even) and test the
+// point against the two boundary rays of the estimated wedge and, when it
+// lies outside, of the neighbour (wedges are narrower than pi).  bnd[m] =
+// (cos, sin) of the ray between wedges m-1 and m, at (m - 1/2) 2 pi / N.
+__device__ __forceinline__ int project64_guarded(double rx, double ry, int N, const double2 *bnd)
+{
+    const double x = rx - kTwoPi * rint(rx / kTwoPi);
+    const double y = ry - kTwoPi * rint(ry / kTwoPi);
+    if (x == 0.0 && y == 0.0) return 0;
+    int j;
+    rint_add(atan2_poly((float)y, (float)x) * (float)(N / kTwoPi), j);
+    for (int it = 0; it < 3; ++it) {
+        const int jj = ((j % N) + N) % N, jn = jj + 1 == N ? 0 : jj + 1;
+        const double2 lo = bnd[jj], hi = bnd[jn];
+        const bool ccw_lo = lo.x * y - lo.y * x >= 0.0;   // on or after the lower ray
+        const bool cw_hi = hi.x * y - hi.y * x < 0.0;     // before the upper ray
+        if (ccw_lo && cw_hi) return jj;
+        j = ccw_lo ? jj + 1 : jj - 1;
+    }
+    return ((j % N) + N) % N;
 }
 
 template <typename R>
@@ -121,6 +152,8 @@ struct SigmaArgs {
     int nj;
     const int *jlist;    // targets (may be NULL: j = blockIdx.z)
     const double *kx64, *ky64;  // FP64 fine momenta (guarded FP32 projection)
+    const double *xij;          // xi(k_F(j)), FP64
+    const double2 *bnd;         // boundary rays of the wedges (FP32 projection fallback)
     // frequency-grid histogram (sigma_hist_kernel)
     double *hist;        // [j][moment 0..4][bin]
     double e_min, inv_h;
@@ -169,30 +202,36 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *s_rec = reinterpret_cast<R *>(smem_raw);          // P x REC
     R *s_VZ = s_rec + (size_t)REC * P;                   // N x {V[j][a][c], Z_c}
-    double *s_kd = reinterpret_cast<double *>(s_VZ + 2 * N);   // P x {k+p} in FP64 (FP32 kernel)
+    double2 *s_bnd = reinterpret_cast<double2 *>(s_VZ + 2 * N + (2 * N * sizeof(R)) % 16 / sizeof(R));
 
     const double kx = A.kf[2 * j], ky = A.kf[2 * j + 1];
     for (int i = tid; i < N; i += blockDim.x) {
         s_VZ[2 * i] = (R)A.V[((long)j * N + a) * N + i];
         s_VZ[2 * i + 1] = A.Z ? (R)A.Z[i] : R(1);
+        if (f32 && wedge) s_bnd[i] = A.bnd[i];
+    }
+    // cos/sin of the target's components (once per CTA)
+    __shared__ R s_k[4];
+    if (tid == 0) {
+        double sx, cx, sy, cy;
+        sincos(kx, &sx, &cx);
+        sincos(ky, &sy, &cy);
+        s_k[0] = (R)cx; s_k[1] = (R)sx; s_k[2] = (R)cy; s_k[3] = (R)sy;
     }
     __syncthreads();
     const R Za = s_VZ[2 * a + 1];
+    const R ckx = s_k[0], skx = s_k[1], cky = s_k[2], sky = s_k[3];
     for (int i = tid; i < P; i += blockDim.x) {
         const int p = a * P + i;
-        // k_j + p in FP64 (from the FP64 table in either precision: the guarded
-        // FP32 projection falls back on exactly this sum), then cos/sin
-        const double kpx = kx + A.kx64[p], kpy = ky + A.ky64[p];
-        double sxv, cxv, syv, cyv;
-        sincos(kpx, &sxv, &cxv);
-        sincos(kpy, &syv, &cyv);
         R *rec = s_rec + (size_t)REC * i;
-        rec[0] = (R)kpx;
-        rec[1] = (R)kpy;
-        rec[2] = (R)cxv;
-        rec[3] = (R)sxv;
-        rec[4] = (R)cyv;
-        rec[5] = (R)syv;
+        // k_j + p (FP64 sum, rounded), cos/sin by angle addition from the tables
+        rec[0] = (R)(kx + A.kx64[p]);
+        rec[1] = (R)(ky + A.ky64[p]);
+        const R cpx = A.fine.cx[p], spx = A.fine.sx[p], cpy = A.fine.cy[p], spy = A.fine.sy[p];
+        rec[2] = ckx * cpx - skx * spx;
+        rec[3] = skx * cpx + ckx * spx;
+        rec[4] = cky * cpy - sky * spy;
+        rec[5] = sky * cpy + cky * spy;
         const R xp = qp ? Za * A.fine.xi[p] : A.fine.xi[p];
         rec[6] = xp;
         R f, fc;
@@ -201,10 +240,6 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
         rec[8] = fc;
         rec[9] = A.fine.w[p];
         rec[10] = rec[11] = R(0);
-        if (f32) {
-            s_kd[2 * i] = kpx;
-            s_kd[2 * i + 1] = kpy;
-        }
     }
     __syncthreads();
 
@@ -221,22 +256,23 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
         sfermi(xq, invT, fq, fcq);
         const R vab = s_VZ[2 * b];
         const R pref = Za * Zb * A.fine.w[q];
-        // chord frequencies xi_j +- 2T (xi_j of the representative, FP64)
-        const double ckx = cos(kx), cky = cos(ky);
-        const double xij = -2.0 * A.pb.t * (ckx + cky) - 4.0 * A.pb.tp * ckx * cky - A.pb.mu;
-        const R d0shift = (R)xij, twoT = (R)(2.0 * A.T);
+        const R d0shift = (R)A.xij[j], twoT = (R)(2.0 * A.T);
         const R eta2 = eta * eta;
+        const float inv_dth = (float)(N / kTwoPi), dth = (float)(kTwoPi / N);
         for (int i = 0; i < P; ++i) {
             R r[REC];
             load_rec(s_rec, i, r);
             int c;
             if (f32 && wedge) {
-                c = project32_guarded((float)(r[0] - qx), (float)(r[1] - qy), N);
-                if (c < 0) c = project64(s_kd[2 * i] - qxd, s_kd[2 * i + 1] - qyd, N, A.pb.mode, A.pb.L);
-            } else if (f32) {
-                c = project64(s_kd[2 * i] - qxd, s_kd[2 * i + 1] - qyd, N, A.pb.mode, A.pb.L);
+                int jc;
+                c = project32_guarded((float)(r[0] - qx), (float)(r[1] - qy), N, inv_dth, dth, jc);
+                if (c < 0) {
+                    const int p = a * P + i;
+                    c = project64_guarded((kx + A.kx64[p]) - qxd, (ky + A.ky64[p]) - qyd, N, s_bnd);
+                }
             } else {
-                c = project64((double)r[0] - qxd, (double)r[1] - qyd, N, A.pb.mode, A.pb.L);
+                const int p = a * P + i;
+                c = project64((kx + A.kx64[p]) - qxd, (ky + A.ky64[p]) - qyd, N, A.pb.mode, A.pb.L);
             }
             // cos(k+p-q) by angle addition
             const R crx = r[2] * cqx + r[3] * sqx;
@@ -332,7 +368,7 @@ template <typename R>
 static qpfrg_status launch_sigma(qpfrg_ctx *c, bool hist, SigmaArgs<R> &A, int kid)
 {
     const int P = c->pb.P, N = c->pb.N;
-    const size_t smem = (size_t)(REC * P + 2 * N) * sizeof(R) + (sizeof(R) == 4 ? 2 * (size_t)P * 8 : 0);
+    const size_t smem = (size_t)(REC * P + 2 * N) * sizeof(R) + 16 + (size_t)N * sizeof(double2);
     auto kern = hist ? sigma_kernel<R, true> : sigma_kernel<R, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(c, e, "sigma smem attribute");
@@ -359,6 +395,8 @@ static void fill_args(qpfrg_ctx *c, SigmaArgs<R> &A, const FineTable<R> &fine, d
     A.jlist = nullptr;
     A.kx64 = c->f64.kx;
     A.ky64 = c->f64.ky;
+    A.xij = c->d_xij;
+    A.bnd = c->d_bnd;
     A.hist = c->d_hist;
     A.e_min = 0.0;
     A.inv_h = 1.0;

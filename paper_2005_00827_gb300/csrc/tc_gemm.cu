@@ -1,0 +1,365 @@
+// Tensor-core contraction (5th-generation tensor cores, tcgen05) for the
+// mixed-precision path QPFRG_MIXED_TC.
+//
+//   D[m][n] = sum_k A[m][k] B[n][k],   A = A_hi + A_lo,  B = B_hi + B_lo  (BF16)
+//   computed as A_hi B_hi + A_hi B_lo + A_lo B_hi with FP32 accumulation in
+//   tensor memory; the dropped A_lo B_lo term is 2^-16 relative.
+//
+// A is a formed bubble table (the loop kernels of one channel times the vertex
+// factor that depends on the row and the first loop patch), B a permuted view
+// of the vertex; see contract.cu for the channel algebra.  One CTA computes
+// a 128-row tile for all N columns over a slice of K (split-K, partial sums
+// added to the FP64 output with atomics).
+//
+// Data path per 64-wide k-block: 128 threads copy the four BF16 tiles with
+// cp.async (16-byte chunks) straight into the canonical K-major, no-swizzle
+// layout of the tensor-core descriptors (core matrices of 8 rows x 16 bytes),
+// a stage ring of S buffers; one elected thread issues 4 K16 slices x 3
+// products of tcgen05.mma (M = 128, N = Npad) and commits them to the stage's
+// mbarrier, which gates the reuse of that buffer.  Waits on mbarriers are
+// bounded: on expiry the CTA raises an error flag, drains its copies, frees
+// its tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "qpfrg_internal.h"
+
+namespace qpfrg {
+
+namespace tc {
+
+constexpr int BM = 128, BK = 64, NTHR = 128;
+constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz: bounded mbarrier waits
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor: start address, leading (K-direction core
+// matrix) and stride (8-row group) byte offsets, version 1, no swizzle.
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1u << 46;      // descriptor version
+    return d;                     // layout type 0 (no swizzle), base offset 0
+}
+
+// Instruction descriptor of kind::f16: F32 accumulator, BF16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, int src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+__device__ __forceinline__ void mbar_init(uint32_t addr, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(addr), "r"(count));
+}
+
+// true when the phase with the given parity has completed
+__device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t addr, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(addr, parity))
+        if (clock64() - t0 > kWaitCycles) return false;
+    return true;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n"
+        " setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+}  // namespace tc
+
+struct TcGemmArgs {
+    const __nv_bfloat16 *Ahi, *Alo;   // [M][K]
+    const __nv_bfloat16 *Bhi, *Blo;   // [Npad][K] (rows >= Ncol are zero)
+    int M, K, Ncol, Npad;
+    int kb_per_split;                 // k-blocks of 64 per CTA along grid.y
+    int map_mode, N;                  // output index map: 0 pp, 1 cr, 2 d
+    double *out;
+    double scale;
+    unsigned *err;
+};
+
+template <int S>
+__global__ void __launch_bounds__(tc::NTHR, 1) tc_gemm_kernel(TcGemmArgs A)
+{
+    using namespace tc;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ uint64_t mbar[4];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int m0 = blockIdx.x * BM;
+    const int nkb_total = (A.K + BK - 1) / BK;
+    const int kb0 = blockIdx.y * A.kb_per_split;
+    const int kb1 = min(nkb_total, kb0 + A.kb_per_split);
+    const int nkb = kb1 - kb0;
+    const int Npad = A.Npad;
+    const uint32_t a_bytes = BM * BK * 2, b_bytes = (uint32_t)Npad * BK * 2;
+    const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
+    const uint32_t base = smem_u32(smem_raw);
+    const uint32_t tmem_cols = Npad <= 32 ? 32 : (Npad <= 64 ? 64 : (Npad <= 128 ? 128 : 256));
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) tc::mbar_init(smem_u32(&mbar[s]), 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(&tmem_slot)),
+                     "r"(tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    // copy one k-block into stage s: tiles A_hi, A_lo (BM x 64), B_hi, B_lo (Npad x 64)
+    auto load_stage = [&](int kb, int s) {
+        const uint32_t sb = base + (uint32_t)s * stage_bytes;
+        const int k0 = kb * BK;
+        // A: BM rows x 8 chunks of 16 B, two tables
+        for (int c = tid; c < BM * 8; c += NTHR) {
+            const int r = c >> 3, kc = c & 7;
+            const int row = m0 + r, k = k0 + kc * 8;
+            const bool ok = row < A.M && k < A.K;
+            const long off = ok ? (long)row * A.K + k : 0;
+            const uint32_t so = (uint32_t)((kc * (BM / 8) + (r >> 3)) * 128 + (r & 7) * 16);
+            tc::cp_async16(sb + so, A.Ahi + off, ok ? 16 : 0);
+            tc::cp_async16(sb + a_bytes + so, A.Alo + off, ok ? 16 : 0);
+        }
+        for (int c = tid; c < Npad * 8; c += NTHR) {
+            const int r = c >> 3, kc = c & 7;
+            const int k = k0 + kc * 8;
+            const bool ok = k < A.K;
+            const long off = ok ? (long)r * A.K + k : 0;
+            const uint32_t so = (uint32_t)((kc * (Npad / 8) + (r >> 3)) * 128 + (r & 7) * 16);
+            tc::cp_async16(sb + 2 * a_bytes + so, A.Bhi + off, ok ? 16 : 0);
+            tc::cp_async16(sb + 2 * a_bytes + b_bytes + so, A.Blo + off, ok ? 16 : 0);
+        }
+    };
+
+    const uint32_t idesc = tc::make_idesc(BM, Npad);
+    // prologue: k-blocks 0 .. S-2 in flight
+    for (int s = 0; s < S - 1; ++s) {
+        if (s < nkb) load_stage(kb0 + s, s);
+        tc::cp_async_commit();
+    }
+    bool ok_run = true;
+    for (int i = 0; i < nkb; ++i) {
+        tc::cp_async_wait<S - 2>();   // the copies of k-block i have landed
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (abort_flag) {
+            ok_run = false;
+            break;
+        }
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const uint32_t sb = base + (uint32_t)(i % S) * stage_bytes;
+#pragma unroll
+            for (int ks = 0; ks < BK / 16; ++ks) {
+                // K16 slice: core matrices 2ks, 2ks+1 along K
+                const uint32_t a_off = (uint32_t)(2 * ks * (BM / 8) * 128);
+                const uint32_t b_off = (uint32_t)(2 * ks * (Npad / 8) * 128);
+                const uint64_t ahi = tc::make_desc(sb + a_off, (BM / 8) * 128, 128);
+                const uint64_t alo = tc::make_desc(sb + a_bytes + a_off, (BM / 8) * 128, 128);
+                const uint64_t bhi = tc::make_desc(sb + 2 * a_bytes + b_off, (Npad / 8) * 128, 128);
+                const uint64_t blo = tc::make_desc(sb + 2 * a_bytes + b_bytes + b_off, (Npad / 8) * 128, 128);
+                const uint32_t acc = (i > 0 || ks > 0) ? 1u : 0u;
+                tc::mma_bf16(tmem, ahi, bhi, idesc, acc);
+                tc::mma_bf16(tmem, ahi, blo, idesc, 1u);
+                tc::mma_bf16(tmem, alo, bhi, idesc, 1u);
+            }
+            tc::mma_commit(smem_u32(&mbar[i % S]));
+        }
+        // refill the buffer of k-block i-1 with k-block i+S-1 once its MMAs are done
+        const int nxt = i + S - 1;
+        if (nxt < nkb) {
+            if (i >= 1 && !tc::mbar_wait_bounded(smem_u32(&mbar[(i - 1) % S]), (uint32_t)(((i - 1) / S) & 1)))
+                atomicExch(&abort_flag, 1);
+            else
+                load_stage(kb0 + nxt, nxt % S);
+        }
+        tc::cp_async_commit();
+    }
+    tc::cp_async_wait<0>();
+    // wait for the last commit before reading the accumulators
+    if (tid == 0 && nkb > 0) {
+        const int last = nkb - 1;
+        if (!tc::mbar_wait_bounded(smem_u32(&mbar[last % S]), (uint32_t)((last / S) & 1))) atomicExch(&abort_flag, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (!ok_run || abort_flag) {
+        if (tid == 0) atomicOr(A.err, 1u);
+    } else if (nkb > 0) {
+        // epilogue: warp w owns accumulator rows 32w .. 32w+31 (TMEM lanes)
+        const int r = warp * 32 + (tid & 31);
+        const int m = m0 + r;
+        const int N = A.N;
+        const long NN = (long)N * N;
+        for (int c0 = 0; c0 < Npad; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            if (m < A.M) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int n = c0 + q;
+                    if (n >= A.Ncol) continue;
+                    long o;
+                    if (A.map_mode == 0) o = (long)m * N + n;
+                    else if (A.map_mode == 1) o = (long)n * NN + m;
+                    else o = ((long)(m / N) * N + n) * N + (m % N);
+                    atomicAdd(&A.out[o], A.scale * (double)v[q]);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tmem_cols));
+}
+
+// Per-stage B operands of the three channel GEMMs from the FP32 stage vertex,
+// K-major [n][k] with k = (a, b) = a N + b, split into BF16 hi/lo, rows
+// n >= N zero:  pp: V[a,b,n];  cr: V[n,a,b];  d: V[b,n,a] (k < N^2) and
+// V[n,b,a] (k >= N^2);  plus VT[j][l][b] = V[b][j][l] for the cr factor.
+__global__ void tc_prep_kernel(const float *__restrict__ V, int N, int Npad, TcBuffers t)
+{
+    const long NN = (long)N * N, n3 = NN * N;
+    const long s_pp = (long)Npad * NN, s_d = 2 * s_pp;
+    const long total = 2 * s_pp + s_d + n3;
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        if (idx < 2 * s_pp + s_d) {
+            int which;
+            long loc;
+            if (idx < s_pp) { which = 0; loc = idx; }
+            else if (idx < 2 * s_pp) { which = 1; loc = idx - s_pp; }
+            else { which = 2; loc = idx - 2 * s_pp; }
+            const long K = which == 2 ? 2 * NN : NN;
+            const int n = (int)(loc / K);
+            const long k = loc - (long)n * K;
+            float v = 0.f;
+            if (n < N) {
+                const long kk = k >= NN ? k - NN : k;
+                const int a = (int)(kk / N), b = (int)(kk - (long)a * N);
+                if (which == 0) v = V[kk * N + n];
+                else if (which == 1) v = V[(long)n * NN + kk];
+                else if (k < NN) v = V[((long)b * N + n) * N + a];
+                else v = V[((long)n * N + b) * N + a];
+            }
+            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+            __nv_bfloat16 **dst = which == 0 ? t.Bpp : (which == 1 ? t.Bcr : t.Bd);
+            dst[0][loc] = hi;
+            dst[1][loc] = lo;
+        } else {
+            const long o = idx - (2 * s_pp + s_d);     // o = (j N + l) N + b
+            const int b = (int)(o % N), jl = (int)(o / N);
+            t.VT[o] = V[(long)b * NN + jl];
+        }
+    }
+}
+
+qpfrg_status launch_tc_prep(qpfrg_ctx *c)
+{
+    const int N = c->pb.N;
+    const long NN = (long)N * N;
+    const long total = 4 * (long)c->tc.Npad * NN + NN * N;
+    int blocks = (int)std::min<long>((total + 255) / 256, 152L * 16);
+    prof_begin(c);
+    tc_prep_kernel<<<blocks, 256, 0, c->stream>>>(c->d_Vf, N, c->tc.Npad, c->tc);
+    prof_end(c, K_TC_PREP);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "tc_prep_kernel");
+}
+
+// Host launcher: D (channel map_mode) += scale * A B^T.
+qpfrg_status launch_tc_gemm(qpfrg_ctx *c, const __nv_bfloat16 *Ahi, const __nv_bfloat16 *Alo,
+                            const __nv_bfloat16 *Bhi, const __nv_bfloat16 *Blo, int M, int K, int Ncol, int Npad,
+                            int map_mode, double scale, double *out, int kid)
+{
+    // stage ring of 3 buffers, 2 when the B tiles are wide
+    const size_t stage_bytes = 2 * (size_t)tc::BM * tc::BK * 2 + 2 * (size_t)Npad * tc::BK * 2;
+    const int S = 3 * stage_bytes <= 200 * 1024 ? 3 : 2;
+    const size_t smem = S * stage_bytes;
+    if (Npad % 16 != 0 || Npad > 256 || K % 8 != 0 || smem > 200 * 1024) {
+        c->err = "tensor-core contraction: unsupported shape";
+        return QPFRG_ERR_UNSUPPORTED;
+    }
+    auto kern = S == 3 ? tc_gemm_kernel<3> : tc_gemm_kernel<2>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tc_gemm smem attribute");
+    const int mtiles = div_up(M, tc::BM);
+    const int nkb = div_up(K, tc::BK);
+    // split K so that the grid covers the SMs about once
+    int splits = std::max(1, std::min(nkb / 8, div_up(152, mtiles)));
+    const int kb_per = div_up(nkb, splits);
+    splits = div_up(nkb, kb_per);
+    TcGemmArgs A{Ahi, Alo, Bhi, Blo, M, K, Ncol, Npad, kb_per, map_mode, c->pb.N, out, scale, c->d_tc_err};
+    prof_begin(c);
+    kern<<<dim3(mtiles, splits), tc::NTHR, smem, c->stream>>>(A);
+    prof_end(c, kid);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "tc_gemm_kernel");
+}
+
+}  // namespace qpfrg
