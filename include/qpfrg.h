@@ -184,6 +184,31 @@ qpfrg_status qpfrg_step(qpfrg_t ctx, int n_steps, qpfrg_flow_result *out);
  * max_steps / timeout_s is reached. */
 qpfrg_status qpfrg_flow(qpfrg_t ctx, qpfrg_flow_result *out);
 
+/* One flow of a batch: patch count, bare coupling U, start and end of the
+ * flow parameter (T-flow: T0 > T_end > 0). */
+typedef struct {
+    int n_p;
+    double U;
+    double lambda0;
+    double lambda_end;
+} qpfrg_flow_spec;
+
+/* Run n_flows independent flows in one call -- a sweep of the strong-coupling
+ * scale U*(T) / T*(U) over (U, T, patching) as in Sec. 3.2 and Fig. 4 -- each
+ * stopping at its own bound (max|V| > stop_abs_v), end of flow or failure.
+ * Flows with the same n_p share one geometry (partner-patch maps) and one set
+ * of per-evaluation scratch tables and queue on one internal stream; groups of
+ * different n_p run concurrently.  Every running flow advances one RK4 step
+ * per round, with one host synchronisation per round for the whole batch.
+ * options applies to every flow (its lambda_end is replaced by each spec's).
+ * results[i] receives flow i's outcome.  The call waits for the work already
+ * on cuda_stream before it starts and returns with the device idle for the
+ * batch.  Errors: as qpfrg_create for invalid specs or allocation failures;
+ * QPFRG_ERR_TIMEOUT when a tensor-core wait expired. */
+qpfrg_status qpfrg_flow_batch(const qpfrg_lattice *lattice, const qpfrg_fine_grid *grid,
+                              qpfrg_regulator regulator, const qpfrg_options *options, int n_flows,
+                              const qpfrg_flow_spec *specs, void *cuda_stream, qpfrg_flow_result *results);
+
 /* Checkpoint: size in bytes of the state image (64-byte header, then V as
  * N^3 FP64, then Z as N FP64, little endian). */
 qpfrg_status qpfrg_state_size(qpfrg_t ctx, size_t *bytes);

@@ -31,6 +31,7 @@ EXPORTS = (
     "qpfrg_flow", "qpfrg_state_size", "qpfrg_get_state", "qpfrg_set_state", "qpfrg_read_state",
     "qpfrg_geometry", "qpfrg_set_profiling", "qpfrg_profile_reset", "qpfrg_profile_count",
     "qpfrg_profile_name", "qpfrg_profile_get", "qpfrg_last_error", "qpfrg_version", "qpfrg_destroy",
+    "qpfrg_flow_batch",
 )
 
 
@@ -63,6 +64,10 @@ class qpfrg_flow_result(C.Structure):
     def as_dict(self):
         return dict(status=FLOW_STATUS.get(self.status, self.status), steps=self.steps, lam=self.lambda_,
                     lambda_c=self.lambda_c, max_abs_v=self.max_abs_v)
+
+
+class qpfrg_flow_spec(C.Structure):
+    _fields_ = [("n_p", C.c_int), ("U", C.c_double), ("lambda0", C.c_double), ("lambda_end", C.c_double)]
 
 
 _lib = None
@@ -107,6 +112,10 @@ def load(build_if_missing: bool = True):
     L.qpfrg_last_error.argtypes = [_P]
     L.qpfrg_last_error.restype = C.c_char_p
     L.qpfrg_version.restype = C.c_char_p
+    L.qpfrg_flow_batch.argtypes = [C.POINTER(qpfrg_lattice), C.POINTER(qpfrg_fine_grid), C.c_int,
+                                   C.POINTER(qpfrg_options), C.c_int, C.POINTER(qpfrg_flow_spec), _P,
+                                   C.POINTER(qpfrg_flow_result)]
+    L.qpfrg_flow_batch.restype = C.c_int
     L.qpfrg_destroy.argtypes = [_P]
     L.qpfrg_destroy.restype = None
     for name in ("qpfrg_create", "qpfrg_rhs", "qpfrg_selfenergy", "qpfrg_step", "qpfrg_flow",
@@ -168,6 +177,19 @@ def qpfrg_flow(ctx):
     r = qpfrg_flow_result()
     _check(ctx, load().qpfrg_flow(ctx, C.byref(r)))
     return r
+
+
+def qpfrg_flow_batch(lattice, grid, regulator, options, specs, cuda_stream):
+    """Run the flows of `specs` (sequence of (n_p, U, lambda0, lambda_end)) in one call."""
+    n = len(specs)
+    arr = (qpfrg_flow_spec * n)(*[qpfrg_flow_spec(int(a), float(b), float(c), float(d)) for a, b, c, d in specs])
+    res = (qpfrg_flow_result * n)()
+    st = load().qpfrg_flow_batch(C.byref(lattice), C.byref(grid), int(regulator),
+                                 C.byref(options) if options is not None else None, n, arr,
+                                 _P(cuda_stream) if cuda_stream else None, res)
+    if st != QPFRG_OK:
+        raise QpfrgError(st, "qpfrg_flow_batch failed")
+    return [r.as_dict() for r in res]
 
 
 def qpfrg_state_size(ctx) -> int:

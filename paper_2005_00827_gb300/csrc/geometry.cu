@@ -222,17 +222,30 @@ qpfrg_status upload_geometry(qpfrg_ctx *c)
         return cuda_fail(c, e, "upload kf");
     {
         std::vector<double> xij(N);
-        std::vector<double2> bnd(N);
+        std::vector<float4> bnd(N);
         for (int j = 0; j < N; ++j) {
             xij[j] = host_xi(c->pb, c->kf[2 * j], c->kf[2 * j + 1]);
-            const double th = (j - 0.5) * kTwoPi / N;
-            bnd[j] = make_double2(std::cos(th), std::sin(th));
+            const double th = (j - 0.5) * kTwoPi / N, cs = std::cos(th), sn = std::sin(th);
+            const float ch = (float)cs, sh = (float)sn;
+            bnd[j] = make_float4(ch, (float)(cs - ch), sh, (float)(sn - sh));
+        }
+        const size_t M = c->pb.M;
+        std::vector<float> xl(M), yl(M);
+        for (size_t p = 0; p < M; ++p) {
+            xl[p] = (float)(c->fk[2 * p] - (double)(float)c->fk[2 * p]);
+            yl[p] = (float)(c->fk[2 * p + 1] - (double)(float)c->fk[2 * p + 1]);
         }
         if ((e = cudaMalloc((void **)&c->d_xij, N * sizeof(double))) != cudaSuccess ||
-            (e = cudaMalloc((void **)&c->d_bnd, N * sizeof(double2))) != cudaSuccess)
-            return cuda_fail(c, e, "cudaMalloc(xi_j, rays)");
+            (e = cudaMalloc((void **)&c->d_bnd, N * sizeof(float4))) != cudaSuccess ||
+            (e = cudaMalloc((void **)&c->d_qxl, M * sizeof(float))) != cudaSuccess ||
+            (e = cudaMalloc((void **)&c->d_qyl, M * sizeof(float))) != cudaSuccess ||
+            (e = cudaMalloc((void **)&c->d_kp, (size_t)N * M * sizeof(float4))) != cudaSuccess ||
+            (e = cudaMalloc((void **)&c->d_kcs, N * sizeof(float4))) != cudaSuccess)
+            return cuda_fail(c, e, "cudaMalloc(xi_j, rays, residuals, k+p)");
         cudaMemcpy(c->d_xij, xij.data(), N * sizeof(double), cudaMemcpyHostToDevice);
-        cudaMemcpy(c->d_bnd, bnd.data(), N * sizeof(double2), cudaMemcpyHostToDevice);
+        cudaMemcpy(c->d_bnd, bnd.data(), N * sizeof(float4), cudaMemcpyHostToDevice);
+        cudaMemcpy(c->d_qxl, xl.data(), M * sizeof(float), cudaMemcpyHostToDevice);
+        cudaMemcpy(c->d_qyl, yl.data(), M * sizeof(float), cudaMemcpyHostToDevice);
     }
     if ((e = cudaMalloc((void **)&c->d_Qpp, 2 * NN * sizeof(double))) != cudaSuccess ||
         (e = cudaMalloc((void **)&c->d_Qph, 2 * NN * sizeof(double))) != cudaSuccess)

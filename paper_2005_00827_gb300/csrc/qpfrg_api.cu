@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <new>
 
 #include "qpfrg_internal.h"
@@ -204,18 +205,24 @@ void qpfrg_destroy(qpfrg_t c)
     if (!c) return;
     cudaStreamSynchronize(c->stream);
     cudaGetLastError();
-    void *ptrs[] = {c->f64.kx, c->f64.ky, c->f64.cx, c->f64.sx, c->f64.cy, c->f64.sy, c->f64.xi, c->f64.w,
-                    c->f32.kx, c->f32.ky, c->f32.cx, c->f32.sx, c->f32.cy, c->f32.sy, c->f32.xi, c->f32.w,
-                    c->qpp64.cx, c->qpp64.sx, c->qpp64.cy, c->qpp64.sy, c->qph64.cx, c->qph64.sx,
-                    c->qph64.cy, c->qph64.sy, c->qpp32.cx, c->qpp32.sx, c->qpp32.cy, c->qpp32.sy,
-                    c->qph32.cx, c->qph32.sx, c->qph32.cy, c->qph32.sy, c->d_kf, c->d_Qpp, c->d_Qph,
-                    c->d_part, c->d_B, c->d_V, c->d_Z, c->d_Vs, c->d_k, c->d_acc, c->d_ones, c->d_Vf,
-                    c->d_Zwork, c->d_sig, c->d_hist, c->d_red, c->d_jirr, c->d_rep, c->tc.App[0], c->tc.App[1],
-                    c->tc.Acr[0], c->tc.Acr[1], c->tc.Ad[0], c->tc.Ad[1], c->tc.Bpp[0], c->tc.Bpp[1], c->tc.Bcr[0],
-                    c->tc.Bcr[1], c->tc.Bd[0], c->tc.Bd[1], c->tc.VT, c->d_tc_err, c->d_xij, c->d_bnd};
-    for (void *p : ptrs)
+    // per-flow state: always owned
+    void *own[] = {c->d_V, c->d_Z, c->d_Vs, c->d_k, c->d_acc, c->d_Vf, c->d_Zwork, c->d_red};
+    for (void *p : own)
         if (p) cudaFree(p);
     if (c->h_red) cudaFreeHost(c->h_red);
+    if (!c->shares_geometry) {
+        void *ptrs[] = {c->f64.kx, c->f64.ky, c->f64.cx, c->f64.sx, c->f64.cy, c->f64.sy, c->f64.xi, c->f64.w,
+                        c->f32.kx, c->f32.ky, c->f32.cx, c->f32.sx, c->f32.cy, c->f32.sy, c->f32.xi, c->f32.w,
+                        c->qpp64.cx, c->qpp64.sx, c->qpp64.cy, c->qpp64.sy, c->qph64.cx, c->qph64.sx,
+                        c->qph64.cy, c->qph64.sy, c->qpp32.cx, c->qpp32.sx, c->qpp32.cy, c->qpp32.sy,
+                        c->qph32.cx, c->qph32.sx, c->qph32.cy, c->qph32.sy, c->d_kf, c->d_Qpp, c->d_Qph,
+                        c->d_part, c->d_B, c->d_ones, c->d_sig, c->d_hist, c->d_jirr, c->d_rep,
+                        c->tc.App[0], c->tc.App[1], c->tc.Acr[0], c->tc.Acr[1], c->tc.Ad[0], c->tc.Ad[1],
+                        c->tc.Bpp[0], c->tc.Bpp[1], c->tc.Bcr[0], c->tc.Bcr[1], c->tc.Bd[0], c->tc.Bd[1],
+                        c->tc.VT, c->d_tc_err, c->d_xij, c->d_bnd, c->d_qxl, c->d_qyl, c->d_kp, c->d_kcs};
+        for (void *p : ptrs)
+            if (p) cudaFree(p);
+    }
     Profiler *p = prof_of(c);
     if (p) {
         for (auto &pe : p->pending) {
@@ -359,7 +366,7 @@ qpfrg_status qpfrg_create(const qpfrg_lattice *lattice, int n_p, const qpfrg_fin
         (s = dev_alloc(c, &c->d_Zwork, N, "Z work")) || (s = dev_alloc(c, &c->d_ones, N, "ones")) ||
         (s = dev_alloc(c, &c->d_sig, 2 * N, "sigma chord")) || (s = dev_alloc(c, &c->d_red, 2, "reduction")))
         return fail(s);
-    e = cudaMallocHost((void **)&c->h_red, 2 * sizeof(unsigned long long));
+    e = cudaMallocHost((void **)&c->h_red, 3 * sizeof(unsigned long long));
     if (e != cudaSuccess) return fail(cuda_fail(c, e, "cudaMallocHost"));
 
     // C4v-irreducible patches 0..floor(N/8) and each patch's representative
@@ -389,6 +396,7 @@ qpfrg_status qpfrg_create(const qpfrg_lattice *lattice, int n_p, const qpfrg_fin
     e = cudaMemcpy(c->d_ones, h.data(), N * sizeof(double), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return fail(cuda_fail(c, e, "init Z"));
     c->lambda = lambda0;
+    c->lambda_end = c->opt.lambda_end;
     c->c4v_state = pb.mode == QPFRG_GRID_WEDGE;
     c->steps = 0;
     c->status = QPFRG_FLOW_RUNNING;
@@ -445,12 +453,16 @@ static void fill_result(const qpfrg_ctx *c, qpfrg_flow_result *out)
     out->max_abs_v = c->max_abs_v;
 }
 
-// One RK4 step of the flow state (see qpfrg.h).
-static qpfrg_status do_step(qpfrg_ctx *c)
+// Enqueue one RK4 step of the flow state (see qpfrg.h) on the context's
+// stream; finish_step completes it once the stream has reached the end.
+// With Z feedback the new Z is read back (and range-checked) before the
+// stages are enqueued, so that a flow whose Z left its range does not step.
+static qpfrg_status enqueue_step(qpfrg_ctx *c)
 {
+    c->pending = false;
     const bool tflow = c->pb.regulator == QPFRG_REG_TEMPERATURE;
     const double x = tflow ? std::log(c->lambda) : c->lambda;
-    const double x_end = tflow ? std::log(c->opt.lambda_end) : c->opt.lambda_end;
+    const double x_end = tflow ? std::log(c->lambda_end) : c->lambda_end;
     if ((tflow && x - x_end <= 1e-12) || (!tflow && x_end - x <= 1e-12)) {
         c->status = QPFRG_FLOW_REACHED_END;
         return QPFRG_OK;
@@ -507,19 +519,33 @@ static qpfrg_status do_step(qpfrg_ctx *c)
             return s;
         }
     }
+    c->h_red[2] = 0;
     e = cudaMemcpyAsync(c->h_red, c->d_red, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);
-    unsigned tc_err = 0;
     if (e == cudaSuccess && c->d_tc_err)
-        e = cudaMemcpyAsync(&tc_err, c->d_tc_err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        e = cudaMemcpyAsync(&c->h_red[2], c->d_tc_err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "flow step");
-    if (tc_err) return set_err(c, QPFRG_ERR_TIMEOUT, "a tensor-core contraction wait expired");
+    c->pending = true;
+    c->pend_x = x;
+    c->pend_h = h;
+    c->pend_m = c->max_abs_v;
+    return QPFRG_OK;
+}
+
+// Complete the step enqueued by enqueue_step; the stream must have drained.
+static qpfrg_status finish_step(qpfrg_ctx *c)
+{
+    if (!c->pending) return QPFRG_OK;
+    c->pending = false;
+    const bool tflow = c->pb.regulator == QPFRG_REG_TEMPERATURE;
+    const double x = c->pend_x, h = c->pend_h, m_old = c->pend_m;
+    const double x_end = tflow ? std::log(c->lambda_end) : c->lambda_end;
+    if (c->h_red[2])
+        return set_err(c, QPFRG_ERR_TIMEOUT, "a tensor-core contraction wait expired");
     double m_new;
     std::memcpy(&m_new, &c->h_red[0], sizeof(double));
     const double x_new = x + h;
     c->steps += 1;
     c->lambda = tflow ? std::exp(x_new) : x_new;
-    const double m_old = c->max_abs_v;
     c->max_abs_v = m_new;
     if (c->h_red[1]) {
         c->status = QPFRG_FLOW_NONFINITE;
@@ -534,6 +560,18 @@ static qpfrg_status do_step(qpfrg_ctx *c)
     }
     if ((tflow && x_new - x_end <= 1e-12) || (!tflow && x_end - x_new <= 1e-12)) c->status = QPFRG_FLOW_REACHED_END;
     return QPFRG_OK;
+}
+
+static qpfrg_status do_step(qpfrg_ctx *c)
+{
+    qpfrg_status s = enqueue_step(c);
+    if (s != QPFRG_OK || !c->pending) return s;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        c->pending = false;
+        return cuda_fail(c, e, "flow step");
+    }
+    return finish_step(c);
 }
 
 qpfrg_status qpfrg_step(qpfrg_t c, int n_steps, qpfrg_flow_result *out)
@@ -576,6 +614,147 @@ qpfrg_status qpfrg_flow(qpfrg_t c, qpfrg_flow_result *out)
     }
     fill_result(c, out);
     return QPFRG_OK;
+}
+
+// A flow that shares the geometry tables and the per-evaluation scratch of
+// `parent` and owns its FP64 state: V = U, Z = 1 at lambda0.  Flows sharing a
+// parent must run on the parent's stream (the scratch is reused in order).
+static qpfrg_status make_child(qpfrg_ctx *parent, double U, double lambda0, double lambda_end, qpfrg_ctx **out)
+{
+    *out = nullptr;
+    qpfrg_ctx *c = new (std::nothrow) qpfrg_ctx(*parent);
+    if (!c) return QPFRG_ERR_OOM;
+    c->shares_geometry = true;
+    c->profiler = new (std::nothrow) Profiler();
+    c->prof = false;
+    for (auto &sl : c->slots) sl = ProfileSlot();
+    c->d_V = c->d_Z = c->d_Vs = c->d_k = c->d_acc = c->d_Zwork = nullptr;
+    c->d_Vf = nullptr;
+    c->d_red = nullptr;
+    c->h_red = nullptr;
+    c->err.clear();
+    const size_t N = c->pb.N, n3 = N * N * N;
+    qpfrg_status s;
+    if (!c->profiler || (s = dev_alloc(c, &c->d_V, n3, "V")) || (s = dev_alloc(c, &c->d_Vs, n3, "V stage")) ||
+        (s = dev_alloc(c, &c->d_k, n3, "k")) || (s = dev_alloc(c, &c->d_acc, n3, "acc")) ||
+        (s = dev_alloc(c, &c->d_Vf, n3, "V fp32")) || (s = dev_alloc(c, &c->d_Z, N, "Z")) ||
+        (s = dev_alloc(c, &c->d_Zwork, N, "Z work")) || (s = dev_alloc(c, &c->d_red, 2, "reduction"))) {
+        qpfrg_destroy(c);
+        return QPFRG_ERR_OOM;
+    }
+    if (cudaMallocHost((void **)&c->h_red, 3 * sizeof(unsigned long long)) != cudaSuccess) {
+        qpfrg_destroy(c);
+        return QPFRG_ERR_OOM;
+    }
+    std::vector<double> h(n3, U);
+    cudaError_t e = cudaMemcpy(c->d_V, h.data(), n3 * sizeof(double), cudaMemcpyHostToDevice);
+    h.assign(N, 1.0);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_Z, h.data(), N * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        qpfrg_destroy(c);
+        return QPFRG_ERR_CUDA;
+    }
+    c->lambda = lambda0;
+    c->lambda_end = lambda_end;
+    c->steps = 0;
+    c->status = QPFRG_FLOW_RUNNING;
+    c->max_abs_v = std::fabs(U);
+    c->lambda_c = 0.0;
+    c->pending = false;
+    c->c4v_state = c->pb.mode == QPFRG_GRID_WEDGE;
+    *out = c;
+    return QPFRG_OK;
+}
+
+qpfrg_status qpfrg_flow_batch(const qpfrg_lattice *lattice, const qpfrg_fine_grid *grid, qpfrg_regulator regulator,
+                              const qpfrg_options *options, int n_flows, const qpfrg_flow_spec *specs,
+                              void *cuda_stream, qpfrg_flow_result *results)
+{
+    if (!lattice || !grid || !specs || !results || n_flows < 1) return QPFRG_ERR_INVALID;
+    qpfrg_options opt;
+    if (options)
+        opt = *options;
+    else
+        qpfrg_default_options(&opt);
+    const bool tflow = regulator == QPFRG_REG_TEMPERATURE;
+    for (int i = 0; i < n_flows; ++i) {
+        const qpfrg_flow_spec &f = specs[i];
+        if (!std::isfinite(f.U) || !std::isfinite(f.lambda0) || !std::isfinite(f.lambda_end)) return QPFRG_ERR_INVALID;
+        if (tflow && !(f.lambda0 > 0.0 && f.lambda_end > 0.0)) return QPFRG_ERR_INVALID;
+    }
+    // flows grouped by patch count: one geometry, one scratch set and one stream per group
+    std::vector<int> sizes;
+    for (int i = 0; i < n_flows; ++i)
+        if (std::find(sizes.begin(), sizes.end(), specs[i].n_p) == sizes.end()) sizes.push_back(specs[i].n_p);
+    const int G = (int)sizes.size();
+    std::vector<cudaStream_t> streams(G, nullptr);
+    std::vector<qpfrg_ctx *> parents(G, nullptr), flows(n_flows, nullptr);
+    std::vector<int> group_of(n_flows, 0);
+    qpfrg_status st = QPFRG_OK;
+    cudaStream_t caller = reinterpret_cast<cudaStream_t>(cuda_stream);
+    cudaEvent_t ev = nullptr;
+    cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    cudaEventRecord(ev, caller);
+    auto cleanup = [&]() {
+        for (auto *c : flows) qpfrg_destroy(c);
+        for (auto *c : parents) qpfrg_destroy(c);
+        for (auto s2 : streams)
+            if (s2) cudaStreamDestroy(s2);
+        if (ev) cudaEventDestroy(ev);
+    };
+    for (int g = 0; g < G && st == QPFRG_OK; ++g) {
+        if (cudaStreamCreateWithFlags(&streams[g], cudaStreamNonBlocking) != cudaSuccess) {
+            st = QPFRG_ERR_CUDA;
+            break;
+        }
+        cudaStreamWaitEvent(streams[g], ev, 0);
+        int first = 0;
+        while (specs[first].n_p != sizes[g]) ++first;
+        st = qpfrg_create(lattice, sizes[g], grid, specs[first].U, specs[first].lambda0, regulator, &opt,
+                          streams[g], &parents[g]);
+    }
+    for (int i = 0; i < n_flows && st == QPFRG_OK; ++i) {
+        group_of[i] = (int)(std::find(sizes.begin(), sizes.end(), specs[i].n_p) - sizes.begin());
+        st = make_child(parents[group_of[i]], specs[i].U, specs[i].lambda0, specs[i].lambda_end, &flows[i]);
+    }
+    if (st != QPFRG_OK) {
+        cleanup();
+        return st;
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    std::vector<int> done_steps(n_flows, 0);
+    for (;;) {
+        bool any = false;
+        // one step for every running flow; flows of a group queue on its stream
+        for (int i = 0; i < n_flows && st == QPFRG_OK; ++i) {
+            qpfrg_ctx *c = flows[i];
+            if (c->status != QPFRG_FLOW_RUNNING) continue;
+            if (done_steps[i] >= opt.max_steps) {
+                c->status = QPFRG_FLOW_MAX_STEPS;
+                continue;
+            }
+            st = enqueue_step(c);
+            any = any || c->pending;
+        }
+        for (int g = 0; g < G; ++g)
+            if (cudaStreamSynchronize(streams[g]) != cudaSuccess && st == QPFRG_OK) st = QPFRG_ERR_CUDA;
+        for (int i = 0; i < n_flows; ++i) {
+            if (!flows[i]->pending) continue;
+            const qpfrg_status s2 = finish_step(flows[i]);
+            ++done_steps[i];
+            if (s2 != QPFRG_OK && st == QPFRG_OK) st = s2;
+        }
+        if (st != QPFRG_OK || !any) break;
+        if (opt.timeout_s > 0.0 &&
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > opt.timeout_s) {
+            for (auto *c : flows)
+                if (c->status == QPFRG_FLOW_RUNNING) c->status = QPFRG_FLOW_TIMEOUT;
+            break;
+        }
+    }
+    for (int i = 0; i < n_flows; ++i) fill_result(flows[i], &results[i]);
+    cleanup();
+    return st;
 }
 
 qpfrg_status qpfrg_state_size(qpfrg_t c, size_t *bytes)

@@ -107,7 +107,10 @@ struct qpfrg_ctx {
     qpfrg::TransferTable<float> qpp32{}, qph32{};
     double *d_kf = nullptr;      // N x 2
     double *d_xij = nullptr;     // N: xi(k_F(j))
-    double2 *d_bnd = nullptr;    // N: (cos, sin) of the ray between wedges j-1 and j
+    float4 *d_bnd = nullptr;     // N: (cos hi, cos lo, sin hi, sin lo) of the ray between wedges j-1 and j
+    float *d_qxl = nullptr, *d_qyl = nullptr;   // M: FP32 residuals kx - (float)kx, ky - (float)ky
+    float4 *d_kp = nullptr;      // [target][p]: k_j + p as FP32 hi/lo pairs (self-energy scratch)
+    float4 *d_kcs = nullptr;     // [target]: cos/sin of k_j (self-energy scratch)
     double *d_Qpp = nullptr, *d_Qph = nullptr;  // N^2 x 2 transfer momenta (FP64)
     uint8_t *d_part = nullptr;   // 2 x N^2 x M partner patches (pp family, then ph)
 
@@ -133,6 +136,11 @@ struct qpfrg_ctx {
     unsigned long long *d_red = nullptr;  // [0] max|V| bits, [1] nonfinite flag
     unsigned long long *h_red = nullptr;  // pinned mirror
     double lambda = 0.0;
+    double lambda_end = 0.0;     // end of this flow (batched flows differ)
+    bool shares_geometry = false;  // tables and scratch belong to another context
+    // step in flight (enqueued, not yet finished): x, h, max|V| before it
+    bool pending = false;
+    double pend_x = 0.0, pend_h = 0.0, pend_m = 0.0;
     int steps = 0;
     int status = QPFRG_FLOW_RUNNING;
     double max_abs_v = 0.0;

@@ -17,6 +17,8 @@
 // (the vertex and Z keep the lattice symmetry) and Z is copied to their
 // images.  sigma_kernel<R,true> bins W F by pole energy E with moments 0..4 for
 // the frequency grid; sigma_grid_kernel resums the moments on the grid.
+#include <algorithm>
+
 #include "qpfrg_internal.h"
 
 namespace qpfrg {
@@ -98,7 +100,8 @@ __device__ __forceinline__ float rint_add(float x, int &as_int)
 // difference and the fold) and atan2_poly below 1.7e-6 rad, so the angle is
 // trusted only when it lies more than 8e-6 + 8e-6/|r| rad from a wedge
 // boundary and the point is more than 4e-6 from the zone edge.  Returns -1
-// when the caller must decide in FP64; *jc gets the nearest-centre estimate.
+// near a wedge boundary, -2 near the zone edge or the origin; jc gets the
+// nearest-centre estimate.
 __device__ __forceinline__ int project32_guarded(float rx, float ry, int N, float inv_dth, float dth, int &jc)
 {
     const float tp = 6.28318531f;
@@ -110,7 +113,7 @@ __device__ __forceinline__ int project32_guarded(float rx, float ry, int N, floa
     int j;
     const float fj = rint_add(u, j);                 // nearest centre
     jc = j;
-    if (fabsf(x) > 3.14159265f - 4e-6f || fabsf(y) > 3.14159265f - 4e-6f || r2 < 1e-8f) return -1;
+    if (fabsf(x) > 3.14159265f - 4e-6f || fabsf(y) > 3.14159265f - 4e-6f || r2 < 1e-8f) return -2;
     const float m = (0.5f - fabsf(u - fj)) * dth;    // distance to the nearest boundary, rad
     if (m < 8e-6f || m * m * r2 < 6.4e-11f) return -1;
     if (j < 0) j += N;
@@ -118,26 +121,78 @@ __device__ __forceinline__ int project32_guarded(float rx, float ry, int N, floa
     return j;
 }
 
-// FP64 decision for the guarded cases: fold (ties to even) and test the
-// point against the two boundary rays of the estimated wedge and, when it
-// lies outside, of the neighbour (wedges are narrower than pi).  bnd[m] =
-// (cos, sin) of the ray between wedges m-1 and m, at (m - 1/2) 2 pi / N.
-__device__ __forceinline__ int project64_guarded(double rx, double ry, int N, const double2 *bnd)
+// Error-free transformations on the FP32 pipes (float-float arithmetic).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
-    const double x = rx - kTwoPi * rint(rx / kTwoPi);
-    const double y = ry - kTwoPi * rint(ry / kTwoPi);
-    if (x == 0.0 && y == 0.0) return 0;
-    int j;
-    rint_add(atan2_poly((float)y, (float)x) * (float)(N / kTwoPi), j);
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// sign of cross(b, x) = b_c x_y - b_s x_x with b and x as float-float pairs;
+// accurate to ~1e-14 of |b||x|
+__device__ __forceinline__ float cross_ff(float4 b, float xh, float xl, float yh, float yl)
+{
+    const float p1 = b.x * yh, e1 = fmaf(b.x, yh, -p1);
+    const float p2 = b.z * xh, e2 = fmaf(b.z, xh, -p2);
+    float s, es;
+    two_sum(p1, -p2, s, es);
+    const float t = es + e1 - e2 + b.x * yl + b.y * yh - b.z * xl - b.w * xh;
+    return s + t;
+}
+
+// Guarded cases away from the zone edge: r = (k+p) - q in float-float, folded
+// (|r| < 3 pi; the fold decision is safe away from the zone edge), then the
+// point is tested against the boundary rays of the estimated wedge and its
+// neighbours.  bnd[m] = (cos hi, cos lo, sin hi, sin lo) of the ray between
+// wedges m-1 and m, at angle (m - 1/2) 2 pi / N.
+__device__ __forceinline__ int project_ff(float kph, float kpl, float kqh, float kql, float qxh, float qxl,
+                                          float qyh, float qyl, int jc, int N, const float4 *bnd)
+{
+    const float C1 = 6.28318548f, C2 = -1.7484555e-7f;   // 2 pi = C1 + C2 (float-float)
+    float xh, xl, yh, yl, e;
+    two_sum(kph, -qxh, xh, e);
+    xl = e + (kpl - qxl);
+    two_sum(kqh, -qyh, yh, e);
+    yl = e + (kql - qyl);
+    const float kx_ = xh > 3.14159265f ? 1.f : (xh < -3.14159265f ? -1.f : 0.f);
+    const float ky_ = yh > 3.14159265f ? 1.f : (yh < -3.14159265f ? -1.f : 0.f);
+    two_sum(xh, -kx_ * C1, xh, e);
+    xl = xl + e - kx_ * C2;
+    two_sum(yh, -ky_ * C1, yh, e);
+    yl = yl + e - ky_ * C2;
+    int j = jc;
     for (int it = 0; it < 3; ++it) {
-        const int jj = ((j % N) + N) % N, jn = jj + 1 == N ? 0 : jj + 1;
-        const double2 lo = bnd[jj], hi = bnd[jn];
-        const bool ccw_lo = lo.x * y - lo.y * x >= 0.0;   // on or after the lower ray
-        const bool cw_hi = hi.x * y - hi.y * x < 0.0;     // before the upper ray
+        const int jj = j < 0 ? j + N : (j >= N ? j - N : j);
+        const int jn = jj + 1 == N ? 0 : jj + 1;
+        const bool ccw_lo = cross_ff(bnd[jj], xh, xl, yh, yl) >= 0.f;   // on or after the lower ray
+        const bool cw_hi = cross_ff(bnd[jn], xh, xl, yh, yl) < 0.f;     // before the upper ray
         if (ccw_lo && cw_hi) return jj;
         j = ccw_lo ? jj + 1 : jj - 1;
     }
-    return ((j % N) + N) % N;
+    return j < 0 ? j + N : (j >= N ? j - N : j);
+}
+
+// Per target and loop point, once per self-energy call: k_j + p as FP32
+// hi/lo pairs (from the FP64 sum, the same sum as the FP64 path) and, per
+// target, cos/sin of k_j's components.
+__global__ void kp_table_kernel(const double *kf, const int *jlist, int nj, const double *kx64, const double *ky64,
+                                int M, float4 *kp, float4 *kcs)
+{
+    const long total = (long)nj * M;
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const int ji = (int)(idx / M), p = (int)(idx - (long)ji * M);
+        const int j = jlist ? jlist[ji] : ji;
+        const double x = kf[2 * j] + kx64[p], y = kf[2 * j + 1] + ky64[p];
+        const float xh = (float)x, yh = (float)y;
+        kp[idx] = make_float4(xh, (float)(x - xh), yh, (float)(y - yh));
+        if (p == 0) {
+            double sx, cx, sy, cy;
+            sincos(kf[2 * j], &sx, &cx);
+            sincos(kf[2 * j + 1], &sy, &cy);
+            kcs[ji] = make_float4((float)cx, (float)sx, (float)cy, (float)sy);
+        }
+    }
 }
 
 template <typename R>
@@ -153,7 +208,10 @@ struct SigmaArgs {
     const int *jlist;    // targets (may be NULL: j = blockIdx.z)
     const double *kx64, *ky64;  // FP64 fine momenta (guarded FP32 projection)
     const double *xij;          // xi(k_F(j)), FP64
-    const double2 *bnd;         // boundary rays of the wedges (FP32 projection fallback)
+    const float4 *bnd;          // boundary rays of the wedges, float-float (FP32 projection fallback)
+    const float4 *kp;           // [target][p]: k_j + p as (x hi, x lo, y hi, y lo)
+    const float4 *kcs;          // [target]: cos, sin of k_j's components
+    const float *qxl, *qyl;     // FP32 residuals of the fine momenta
     // frequency-grid histogram (sigma_hist_kernel)
     double *hist;        // [j][moment 0..4][bin]
     double e_min, inv_h;
@@ -202,7 +260,7 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R *s_rec = reinterpret_cast<R *>(smem_raw);          // P x REC
     R *s_VZ = s_rec + (size_t)REC * P;                   // N x {V[j][a][c], Z_c}
-    double2 *s_bnd = reinterpret_cast<double2 *>(s_VZ + 2 * N + (2 * N * sizeof(R)) % 16 / sizeof(R));
+    float4 *s_bnd = reinterpret_cast<float4 *>(s_VZ + 2 * N + (2 * N * sizeof(R)) % 16 / sizeof(R));
 
     const double kx = A.kf[2 * j], ky = A.kf[2 * j + 1];
     for (int i = tid; i < N; i += blockDim.x) {
@@ -210,13 +268,17 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
         s_VZ[2 * i + 1] = A.Z ? (R)A.Z[i] : R(1);
         if (f32 && wedge) s_bnd[i] = A.bnd[i];
     }
-    // cos/sin of the target's components (once per CTA)
     __shared__ R s_k[4];
     if (tid == 0) {
-        double sx, cx, sy, cy;
-        sincos(kx, &sx, &cx);
-        sincos(ky, &sy, &cy);
-        s_k[0] = (R)cx; s_k[1] = (R)sx; s_k[2] = (R)cy; s_k[3] = (R)sy;
+        if (f32) {
+            const float4 k4 = A.kcs[jidx];
+            s_k[0] = (R)k4.x; s_k[1] = (R)k4.y; s_k[2] = (R)k4.z; s_k[3] = (R)k4.w;
+        } else {
+            double sx, cx, sy, cy;
+            sincos(kx, &sx, &cx);
+            sincos(ky, &sy, &cy);
+            s_k[0] = (R)cx; s_k[1] = (R)sx; s_k[2] = (R)cy; s_k[3] = (R)sy;
+        }
     }
     __syncthreads();
     const R Za = s_VZ[2 * a + 1];
@@ -224,9 +286,18 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
     for (int i = tid; i < P; i += blockDim.x) {
         const int p = a * P + i;
         R *rec = s_rec + (size_t)REC * i;
-        // k_j + p (FP64 sum, rounded), cos/sin by angle addition from the tables
-        rec[0] = (R)(kx + A.kx64[p]);
-        rec[1] = (R)(ky + A.ky64[p]);
+        if (f32) {
+            // k_j + p as FP32 hi/lo pairs from the per-call table
+            const float4 k4 = A.kp[(long)jidx * M + p];
+            rec[0] = (R)k4.x;
+            rec[10] = (R)k4.y;
+            rec[1] = (R)k4.z;
+            rec[11] = (R)k4.w;
+        } else {
+            rec[0] = (R)(kx + A.kx64[p]);
+            rec[1] = (R)(ky + A.ky64[p]);
+            rec[10] = rec[11] = R(0);
+        }
         const R cpx = A.fine.cx[p], spx = A.fine.sx[p], cpy = A.fine.cy[p], spy = A.fine.sy[p];
         rec[2] = ckx * cpx - skx * spx;
         rec[3] = skx * cpx + ckx * spx;
@@ -239,7 +310,6 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
         rec[7] = f;
         rec[8] = fc;
         rec[9] = A.fine.w[p];
-        rec[10] = rec[11] = R(0);
     }
     __syncthreads();
 
@@ -249,6 +319,7 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
         const int b = q / P;
         const R qx = A.fine.kx[q], qy = A.fine.ky[q];
         const double qxd = A.kx64[q], qyd = A.ky64[q];
+        const float qxl = f32 ? A.qxl[q] : 0.f, qyl = f32 ? A.qyl[q] : 0.f;
         const R cqx = A.fine.cx[q], sqx = A.fine.sx[q], cqy = A.fine.cy[q], sqy = A.fine.sy[q];
         const R Zb = s_VZ[2 * b + 1];
         const R xq = qp ? Zb * A.fine.xi[q] : A.fine.xi[q];
@@ -266,9 +337,14 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
             if (f32 && wedge) {
                 int jc;
                 c = project32_guarded((float)(r[0] - qx), (float)(r[1] - qy), N, inv_dth, dth, jc);
-                if (c < 0) {
+                if (c == -1) {
+                    // near a wedge boundary: float-float decision on the FP32 pipes
+                    c = project_ff((float)r[0], (float)r[10], (float)r[1], (float)r[11], (float)qx, qxl, (float)qy,
+                                   qyl, jc, N, s_bnd);
+                } else if (c == -2) {
+                    // zone edge or origin: the exact FP64 projection
                     const int p = a * P + i;
-                    c = project64_guarded((kx + A.kx64[p]) - qxd, (ky + A.ky64[p]) - qyd, N, s_bnd);
+                    c = project64((kx + A.kx64[p]) - qxd, (ky + A.ky64[p]) - qyd, N, A.pb.mode, A.pb.L);
                 }
             } else {
                 const int p = a * P + i;
@@ -368,7 +444,12 @@ template <typename R>
 static qpfrg_status launch_sigma(qpfrg_ctx *c, bool hist, SigmaArgs<R> &A, int kid)
 {
     const int P = c->pb.P, N = c->pb.N;
-    const size_t smem = (size_t)(REC * P + 2 * N) * sizeof(R) + 16 + (size_t)N * sizeof(double2);
+    const size_t smem = (size_t)(REC * P + 2 * N) * sizeof(R) + 16 + (size_t)N * sizeof(float4);
+    if (sizeof(R) == 4) {
+        const long total = (long)A.nj * c->pb.M;
+        kp_table_kernel<<<(int)std::min<long>((total + 255) / 256, 152L * 8), 256, 0, c->stream>>>(
+            c->d_kf, A.jlist, A.nj, c->f64.kx, c->f64.ky, c->pb.M, c->d_kp, c->d_kcs);
+    }
     auto kern = hist ? sigma_kernel<R, true> : sigma_kernel<R, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(c, e, "sigma smem attribute");
@@ -397,6 +478,10 @@ static void fill_args(qpfrg_ctx *c, SigmaArgs<R> &A, const FineTable<R> &fine, d
     A.ky64 = c->f64.ky;
     A.xij = c->d_xij;
     A.bnd = c->d_bnd;
+    A.kp = c->d_kp;
+    A.kcs = c->d_kcs;
+    A.qxl = c->d_qxl;
+    A.qyl = c->d_qyl;
     A.hist = c->d_hist;
     A.e_min = 0.0;
     A.inv_h = 1.0;

@@ -22,6 +22,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cmath>
 
 #include "qpfrg_internal.h"
 
@@ -350,8 +351,19 @@ qpfrg_status launch_tc_gemm(qpfrg_ctx *c, const __nv_bfloat16 *Ahi, const __nv_b
     if (e != cudaSuccess) return cuda_fail(c, e, "tc_gemm smem attribute");
     const int mtiles = div_up(M, tc::BM);
     const int nkb = div_up(K, tc::BK);
-    // split K so that the grid covers the SMs about once
-    int splits = std::max(1, std::min(nkb / 8, div_up(152, mtiles)));
+    // split K so that the grid fills whole waves of the 152 SMs (one CTA per
+    // SM): the split count whose waves are fullest, at least 8 k-blocks each
+    int splits = 1;
+    double best = -1.0;
+    for (int sp = 1; sp <= std::max(1, nkb / 8) && sp <= 16; ++sp) {
+        const int ctas = mtiles * sp;
+        const double waves = (double)ctas / 152.0, fill = waves / std::ceil(waves);
+        const double score = fill - 0.02 * std::ceil(waves);   // prefer fewer waves at equal fill
+        if (score > best + 1e-9) {
+            best = score;
+            splits = sp;
+        }
+    }
     const int kb_per = div_up(nkb, splits);
     splits = div_up(nkb, kb_per);
     TcGemmArgs A{Ahi, Alo, Bhi, Blo, M, K, Ncol, Npad, kb_per, map_mode, c->pb.N, out, scale, c->d_tc_err};
