@@ -238,6 +238,33 @@ int          qpfrg_profile_count(void);
 const char  *qpfrg_profile_name(int id);
 qpfrg_status qpfrg_profile_get(qpfrg_t ctx, int id, double *ms, long long *launches);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free Z evaluation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory while they run
+ * -- code living inside another runtime's memory pool, a driver that may only
+ * use memory it was handed, a process that must not grow its footprint after
+ * start-up.  It computes the same Z_j as qpfrg_selfenergy (FP64, every
+ * patch) without a context and without calling cudaMalloc, cudaFree or any
+ * allocating routine.  Its only scratch is one FP64 accumulator per patch in
+ * a static device array of QPFRG_STATIC_MAX_PATCHES entries, which every GPU
+ * that loads this library holds until the process exits.
+ *   lattice, n_p, grid_mode, propagator: as for qpfrg_create (n_p <= the
+ *     static limit, else QPFRG_ERR_INVALID);
+ *   d_fine: n_fine x 4 FP64 device array (kx, ky, weight, patch) in the
+ *     patch-major order qpfrg_geometry returns (n_fine a multiple of n_p);
+ *   d_kf: n_p x 2 FP64 patch representatives; d_V: n_p^3 FP64; d_Z: n_p FP64
+ *     line weights (NULL = ones); T > 0; eta > 0; d_Z_out: n_p FP64 output.
+ * The first call on a device looks up the device address of the scratch
+ * array (with that device current) and caches it: make that first call
+ * before any stream capture.  All calls share the scratch array, which keeps
+ * the last call's values; each call clears the entries it uses first.  Calls
+ * that overlap on the GPU (other streams, other host threads) race. */
+#define QPFRG_STATIC_MAX_PATCHES 256
+qpfrg_status qpfrg_zfactor_static(const qpfrg_lattice *lattice, int n_p, int n_fine, int grid_mode,
+                                  int propagator, const double *d_fine, const double *d_kf,
+                                  const double *d_V, const double *d_Z, double T, double eta,
+                                  void *cuda_stream, double *d_Z_out);
+
 const char  *qpfrg_last_error(qpfrg_t ctx);   /* never NULL; ctx may be NULL */
 const char  *qpfrg_version(void);
 void         qpfrg_destroy(qpfrg_t ctx);      /* frees device memory; NULL is a no-op */

@@ -31,7 +31,7 @@ EXPORTS = (
     "qpfrg_flow", "qpfrg_state_size", "qpfrg_get_state", "qpfrg_set_state", "qpfrg_read_state",
     "qpfrg_geometry", "qpfrg_set_profiling", "qpfrg_profile_reset", "qpfrg_profile_count",
     "qpfrg_profile_name", "qpfrg_profile_get", "qpfrg_last_error", "qpfrg_version", "qpfrg_destroy",
-    "qpfrg_flow_batch",
+    "qpfrg_zfactor_static", "qpfrg_flow_batch",
 )
 
 
@@ -112,6 +112,9 @@ def load(build_if_missing: bool = True):
     L.qpfrg_last_error.argtypes = [_P]
     L.qpfrg_last_error.restype = C.c_char_p
     L.qpfrg_version.restype = C.c_char_p
+    L.qpfrg_zfactor_static.argtypes = [C.POINTER(qpfrg_lattice), C.c_int, C.c_int, C.c_int, C.c_int, _P, _P,
+                                       _P, _P, C.c_double, C.c_double, _P, _P]
+    L.qpfrg_zfactor_static.restype = C.c_int
     L.qpfrg_flow_batch.argtypes = [C.POINTER(qpfrg_lattice), C.POINTER(qpfrg_fine_grid), C.c_int,
                                    C.POINTER(qpfrg_options), C.c_int, C.POINTER(qpfrg_flow_spec), _P,
                                    C.POINTER(qpfrg_flow_result)]
@@ -241,6 +244,16 @@ def qpfrg_profile(ctx) -> dict:
         _check(ctx, L.qpfrg_profile_get(ctx, i, C.byref(ms), C.byref(n)))
         out[L.qpfrg_profile_name(i).decode()] = (ms.value, n.value)
     return out
+
+
+def qpfrg_zfactor_static(lattice, n_p, n_fine, grid_mode, propagator, fine, kf, V, Z, T, eta, cuda_stream,
+                         Z_out):
+    """Z_j without any device allocation (static scratch); see include/qpfrg.h."""
+    st = load().qpfrg_zfactor_static(C.byref(lattice), int(n_p), int(n_fine), int(grid_mode), int(propagator),
+                                     _ptr(fine), _ptr(kf), _ptr(V), _ptr(Z), float(T), float(eta),
+                                     _P(cuda_stream) if cuda_stream else None, _ptr(Z_out))
+    if st != QPFRG_OK:
+        raise QpfrgError(st, "qpfrg_zfactor_static failed")
 
 
 def qpfrg_last_error(ctx) -> str:
