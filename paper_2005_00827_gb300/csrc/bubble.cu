@@ -35,6 +35,7 @@ struct BubbleArgs {
     const double *Z;
     R *B;
     R T, invT, g, thr;
+    R t, tp, mu;          // hoppings and chemical potential, already in R (no per-use conversion)
     int qchunk;
     // formed operands of the tensor-core contraction (QPFRG_MIXED_TC)
     const float *Vf;            // stage vertex, FP32 [k1][k2][k3]
@@ -169,21 +170,23 @@ __device__ __forceinline__ void load_partners(const uint8_t *src, int (&b)[PPT],
     for (int u = 0; u < PPT; ++u) b[u] = u < nvalid ? src[u] : 0;
 }
 
-template <typename R, int PPT, bool FORM>
-__global__ void __launch_bounds__(256) bubble_kernel(BubbleArgs<R> A)
+// Kernel body for one transfer family (PP: particle-particle, else
+// particle-hole) and one regulator (TFLOW: temperature flow, else
+// interaction flow), both fixed at compile time.
+template <typename R, int PPT, bool FORM, bool PP, bool TFLOW>
+__device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned char *smem_raw)
 {
     const int N = A.pb.N, P = A.pb.P, M = A.pb.M;
     const long NN = (long)N * N;
     const int a = blockIdx.x;
-    const int fam = blockIdx.z;               // 0 = pp, 1 = ph
-    const bool pp = fam == 0;
+    const int fam = PP ? 0 : 1;
+    constexpr bool pp = PP;
     const int q0 = blockIdx.y * A.qchunk;
     const int q1 = min((long)q0 + A.qchunk, NN);
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const bool tflow = A.pb.regulator == QPFRG_REG_TEMPERATURE;
+    constexpr bool tflow = TFLOW;
     const bool qp = A.pb.propagator == QPFRG_PROP_QP;
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     R *acc = reinterpret_cast<R *>(smem_raw);  // 2 x G x N
     R *Zs = acc + 2 * G * N;                   // N
     for (int i = tid; i < 2 * G * N; i += nthr) acc[i] = R(0);
@@ -191,7 +194,7 @@ __global__ void __launch_bounds__(256) bubble_kernel(BubbleArgs<R> A)
     __syncthreads();
     const R Za = Zs[a];
     const R invT = A.invT, thrT = A.thr * A.T;
-    const R t = (R)A.pb.t, tp = (R)A.pb.tp, mu = (R)A.pb.mu;
+    const R t = A.t, tp = A.tp, mu = A.mu;
 
     // this thread's fine points: local indices tid*PPT + u
     R pcx[PPT], psx[PPT], pcy[PPT], psy[PPT], px[PPT], pw[PPT], pa[PPT], pb2[PPT];
@@ -307,6 +310,20 @@ __global__ void __launch_bounds__(256) bubble_kernel(BubbleArgs<R> A)
 }
 
 template <typename R, int PPT, bool FORM>
+__global__ void __launch_bounds__(256) bubble_kernel(BubbleArgs<R> A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const bool tflow = A.pb.regulator == QPFRG_REG_TEMPERATURE;
+    if (blockIdx.z == 0) {
+        if (tflow) bubble_body<R, PPT, FORM, true, true>(A, smem_raw);
+        else bubble_body<R, PPT, FORM, true, false>(A, smem_raw);
+    } else {
+        if (tflow) bubble_body<R, PPT, FORM, false, true>(A, smem_raw);
+        else bubble_body<R, PPT, FORM, false, false>(A, smem_raw);
+    }
+}
+
+template <typename R, int PPT, bool FORM>
 static void launch_t(qpfrg_ctx *c, const BubbleArgs<R> &A, int nthr, int qchunks)
 {
     const int N = c->pb.N;
@@ -341,6 +358,9 @@ static qpfrg_status launch_r(qpfrg_ctx *c, double lambda, const double *d_Z, con
     A.invT = (R)(1.0 / T);
     A.g = (R)(tflow ? 1.0 : lambda);
     A.thr = thr;
+    A.t = (R)pb.t;
+    A.tp = (R)pb.tp;
+    A.mu = (R)pb.mu;
     const long NN = (long)pb.N * pb.N;
     A.qchunk = (int)std::max(1L, std::min(64L, NN / 16));
     const int qchunks = div_up(NN, A.qchunk);

@@ -235,6 +235,10 @@ qpfrg_status upload_geometry(qpfrg_ctx *c)
             xl[p] = (float)(c->fk[2 * p] - (double)(float)c->fk[2 * p]);
             yl[p] = (float)(c->fk[2 * p + 1] - (double)(float)c->fk[2 * p + 1]);
         }
+        std::vector<float> xijf(xij.begin(), xij.end());
+        if ((e = cudaMalloc((void **)&c->d_xij_f, N * sizeof(float))) != cudaSuccess)
+            return cuda_fail(c, e, "cudaMalloc(xi_j fp32)");
+        cudaMemcpy(c->d_xij_f, xijf.data(), N * sizeof(float), cudaMemcpyHostToDevice);
         if ((e = cudaMalloc((void **)&c->d_xij, N * sizeof(double))) != cudaSuccess ||
             (e = cudaMalloc((void **)&c->d_bnd, N * sizeof(float4))) != cudaSuccess ||
             (e = cudaMalloc((void **)&c->d_qxl, M * sizeof(float))) != cudaSuccess ||

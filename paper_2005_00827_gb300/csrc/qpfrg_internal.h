@@ -107,6 +107,7 @@ struct qpfrg_ctx {
     qpfrg::TransferTable<float> qpp32{}, qph32{};
     double *d_kf = nullptr;      // N x 2
     double *d_xij = nullptr;     // N: xi(k_F(j))
+    float *d_xij_f = nullptr;    // N: xi(k_F(j)) in FP32
     float4 *d_bnd = nullptr;     // N: (cos hi, cos lo, sin hi, sin lo) of the ray between wedges j-1 and j
     float *d_qxl = nullptr, *d_qyl = nullptr;   // M: FP32 residuals kx - (float)kx, ky - (float)ky
     float4 *d_kp = nullptr;      // [target][p]: k_j + p as FP32 hi/lo pairs (self-energy scratch)

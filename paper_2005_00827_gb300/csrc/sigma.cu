@@ -212,6 +212,10 @@ struct SigmaArgs {
     const float4 *kp;           // [target][p]: k_j + p as (x hi, x lo, y hi, y lo)
     const float4 *kcs;          // [target]: cos, sin of k_j's components
     const float *qxl, *qyl;     // FP32 residuals of the fine momenta
+    // scalars of the inner loop in R (a double scalar re-read inside the loop
+    // would cost a conversion on the FP64 pipe per use)
+    R t_r, tp_r, mu_r, eta_r, invT_r, twoT_r;
+    const R *xij_r;             // xi(k_F(j)) in R
     // frequency-grid histogram (sigma_hist_kernel)
     double *hist;        // [j][moment 0..4][bin]
     double e_min, inv_h;
@@ -253,8 +257,8 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
     const int tid = threadIdx.x;
     const bool qp = A.pb.propagator == QPFRG_PROP_QP;
     const bool wedge = A.pb.mode == QPFRG_GRID_WEDGE;
-    const R invT = R(1.0 / A.T), eta = R(A.pb.eta);
-    const R t = (R)A.pb.t, tp = (R)A.pb.tp, mu = (R)A.pb.mu;
+    const R invT = A.invT_r, eta = A.eta_r;
+    const R t = A.t_r, tp = A.tp_r, mu = A.mu_r;
     constexpr bool f32 = sizeof(R) == 4;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -327,7 +331,7 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
         sfermi(xq, invT, fq, fcq);
         const R vab = s_VZ[2 * b];
         const R pref = Za * Zb * A.fine.w[q];
-        const R d0shift = (R)A.xij[j], twoT = (R)(2.0 * A.T);
+        const R d0shift = A.xij_r[j], twoT = A.twoT_r;
         const R eta2 = eta * eta;
         const float inv_dth = (float)(N / kTwoPi), dth = (float)(kTwoPi / N);
         for (int i = 0; i < P; ++i) {
@@ -477,6 +481,13 @@ static void fill_args(qpfrg_ctx *c, SigmaArgs<R> &A, const FineTable<R> &fine, d
     A.kx64 = c->f64.kx;
     A.ky64 = c->f64.ky;
     A.xij = c->d_xij;
+    A.t_r = (R)c->pb.t;
+    A.tp_r = (R)c->pb.tp;
+    A.mu_r = (R)c->pb.mu;
+    A.eta_r = (R)c->pb.eta;
+    A.invT_r = (R)(1.0 / T);
+    A.twoT_r = (R)(2.0 * T);
+    A.xij_r = sizeof(R) == 4 ? reinterpret_cast<const R *>(c->d_xij_f) : reinterpret_cast<const R *>(c->d_xij);
     A.bnd = c->d_bnd;
     A.kp = c->d_kp;
     A.kcs = c->d_kcs;
