@@ -96,6 +96,22 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def aggregate(local_ms: float, local_units: float, world: int, device=None):
+    """Whole-job throughput of independent replicas: units summed over ranks
+    divided by the slowest rank's time (max over ranks)."""
+    if world == 1:
+        return local_units / (local_ms / 1e3), local_ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([local_ms, local_units], dtype=torch.float64, device=device)
+    tmax = t[:1].clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    tsum = t[1:].clone()
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    ms = float(tmax.item())
+    return float(tsum.item()) / (ms / 1e3), ms
+
+
 # ---------------------------------------------------------------------------
 def run_qpfrg(args):
     import numpy as np
@@ -140,11 +156,7 @@ def run_qpfrg(args):
     ms = e0.elapsed_time(e1)
     prof = api.qpfrg_profile(ctx.h)
     api.qpfrg_set_profiling(ctx.h, False)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = 4.0 * steps_done * world / (ms / 1e3)
+    value, ms = aggregate(ms, 4.0 * steps_done, world, device="cuda")
 
     # end to end: state uploaded from pinned host memory, one step, state read back
     nbytes = api.qpfrg_state_size(ctx.h)

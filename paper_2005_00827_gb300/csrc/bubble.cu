@@ -140,36 +140,6 @@ __device__ __forceinline__ R loop_g(bool pp, R xp, R fp, R fcp, R xq, R invT, R 
     return pp ? -v : v;
 }
 
-// Partner bytes of this thread's points.  The vector path needs P % PPT == 0
-// (then every thread's run starts PPT-aligned and stays inside its patch);
-// otherwise bytes are read one by one and only for valid points.
-template <int PPT>
-__device__ __forceinline__ void load_partners(const uint8_t *src, int (&b)[PPT], bool vec, int nvalid)
-{
-    if (vec) {
-        if constexpr (PPT == 4) {
-            const uint32_t w = *reinterpret_cast<const uint32_t *>(src);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) b[u] = (w >> (8 * u)) & 0xff;
-            return;
-        } else if constexpr (PPT == 8) {
-            const uint2 w = *reinterpret_cast<const uint2 *>(src);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) b[u] = (w.x >> (8 * u)) & 0xff;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) b[4 + u] = (w.y >> (8 * u)) & 0xff;
-            return;
-        } else if constexpr (PPT == 2) {
-            const uint32_t w = *reinterpret_cast<const uint16_t *>(src);
-            b[0] = w & 0xff;
-            b[1] = (w >> 8) & 0xff;
-            return;
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < PPT; ++u) b[u] = u < nvalid ? src[u] : 0;
-}
-
 // Kernel body for one transfer family (PP: particle-particle, else
 // particle-hole) and one regulator (TFLOW: temperature flow, else
 // interaction flow), both fixed at compile time.
@@ -196,13 +166,20 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
     const R invT = A.invT, thrT = A.thr * A.T;
     const R t = A.t, tp = A.tp, mu = A.mu;
 
-    // this thread's fine points: local indices tid*PPT + u
+    // This thread's fine points: PPT consecutive angular points at one radius,
+    // local index (t0 + u) n_r + s with s = tid % n_r, t0 = (tid / n_r) PPT.
+    // Partners of angular neighbours are ~0.004 rad apart and mostly share a
+    // patch, so runs are long (few shared-memory atomics, which are CAS loops
+    // for floats), and the lanes of a warp sit at different radii (few
+    // conflicts).  Partner bytes of one u are contiguous across the lanes.
+    const int nr = A.pb.n_r, nt = A.pb.n_theta;
+    const int s_r = tid % nr, t0 = (tid / nr) * PPT;
     R pcx[PPT], psx[PPT], pcy[PPT], psy[PPT], px[PPT], pw[PPT], pa[PPT], pb2[PPT];
     bool valid[PPT];
 #pragma unroll
     for (int u = 0; u < PPT; ++u) {
-        const int loc = tid * PPT + u;
-        valid[u] = loc < P;
+        const int loc = (t0 + u) * nr + s_r;
+        valid[u] = t0 + u < nt;
         const int p = a * P + (valid[u] ? loc : 0);
         pcx[u] = A.fine.cx[p];
         psx[u] = A.fine.sx[p];
@@ -217,11 +194,10 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
             fermi_pair(px[u], invT, pa[u], pb2[u]);
         }
     }
-    const bool any_valid = tid * PPT < P;
-    const bool vec = (P % PPT) == 0;
+    const bool any_valid = t0 < nt;
     const TransferTable<R> &Qt = pp ? A.qpp : A.qph;
 
-    // Q's are processed in groups of G: the G partner loads are issued
+    // Q's are processed in groups of G: the G x PPT partner loads are issued
     // together, runs are added into G shared rows, one barrier per group.
     for (int Qb = q0; Qb < q1; Qb += G) {
         R *accb = acc + (((Qb - q0) / G) & 1) * (G * N);
@@ -231,8 +207,9 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
 #pragma unroll
             for (int g = 0; g < G; ++g) {
                 const int Q = min(Qb + g, q1 - 1);
-                load_partners<PPT>(A.part + ((long)fam * NN + Q) * (long)M + (long)a * P + tid * PPT, bq[g],
-                                   vec, P - tid * PPT);
+                const uint8_t *row = A.part + ((long)fam * NN + Q) * (long)M + (long)a * P + s_r;
+#pragma unroll
+                for (int u = 0; u < PPT; ++u) bq[g][u] = valid[u] ? row[(t0 + u) * nr] : 0;
                 cQx[g] = Qt.cx[Q];
                 sQx[g] = Qt.sx[Q];
                 cQy[g] = Qt.cy[Q];
@@ -372,8 +349,13 @@ static qpfrg_status launch_r(qpfrg_ctx *c, double lambda, const double *d_Z, con
         return QPFRG_ERR_UNSUPPORTED;
     }
     ppt = ppt <= 1 ? 1 : (ppt <= 2 ? 2 : (ppt <= 4 ? 4 : 8));
-    int nthr = (P + ppt - 1) / ppt;
+    // threads: n_r radii x ceil(n_theta / PPT) angular chunks
+    int nthr = pb.n_r * ((pb.n_theta + ppt - 1) / ppt);
     nthr = std::max(32, ((nthr + 31) / 32) * 32);
+    if (nthr > 256) {
+        c->err = "fine grid too large for the loop-kernel launch";
+        return QPFRG_ERR_UNSUPPORTED;
+    }
     prof_begin(c);
     switch (ppt) {
     case 1: launch_t<R, 1, FORM>(c, A, nthr, qchunks); break;

@@ -303,6 +303,7 @@ qpfrg_status qpfrg_create(const qpfrg_lattice *lattice, int n_p, const qpfrg_fin
         pb.L = L;
         pb.P = 1;
         c->n_theta = c->n_r = 1;
+        pb.n_theta = pb.n_r = 1;
     } else if (pb.mode == QPFRG_GRID_WEDGE) {
         if (n_p < 4 || n_p % 4 != 0 || n_p > 256)
             return fail(set_err(c, QPFRG_ERR_INVALID, "wedge mode needs n_p a multiple of 4, 4 <= n_p <= 256"));
@@ -310,6 +311,8 @@ qpfrg_status qpfrg_create(const qpfrg_lattice *lattice, int n_p, const qpfrg_fin
             return fail(set_err(c, QPFRG_ERR_INVALID, "fine grid needs n_theta >= 1 and even n_r >= 2"));
         c->n_theta = grid->n_theta;
         c->n_r = grid->n_r;
+        pb.n_theta = grid->n_theta;
+        pb.n_r = grid->n_r;
         pb.P = grid->n_theta * grid->n_r;
         pb.L = 0;
         if (pb.P > 2048)

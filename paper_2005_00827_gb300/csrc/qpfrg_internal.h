@@ -42,6 +42,7 @@ struct Problem {
     int N;           // patches
     int M;           // fine points
     int P;           // fine points per patch (wedge: n_theta*n_r; lattice: 1)
+    int n_theta, n_r;  // fine grid per patch (lattice: 1 x 1)
     int mode;        // qpfrg_grid_mode
     int L;           // lattice mode: side length
     double t, tp, mu;
