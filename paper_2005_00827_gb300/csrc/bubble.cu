@@ -24,7 +24,7 @@
 
 namespace qpfrg {
 
-constexpr int G = 4;   // transfers per barrier
+constexpr int G = 2;   // transfers per barrier
 
 template <typename R>
 struct BubbleArgs {
@@ -286,8 +286,14 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
     }
 }
 
+// FP32 variants with up to 4 points per thread fit 3 CTAs of 256 threads per SM
+template <typename R, int PPT>
+struct BubbleMinBlocks {
+    static constexpr int value = (sizeof(R) == 4 && PPT <= 4) ? 3 : 1;
+};
+
 template <typename R, int PPT, bool FORM>
-__global__ void __launch_bounds__(256) bubble_kernel(BubbleArgs<R> A)
+__global__ void __launch_bounds__(256, BubbleMinBlocks<R, PPT>::value) bubble_kernel(BubbleArgs<R> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const bool tflow = A.pb.regulator == QPFRG_REG_TEMPERATURE;

@@ -102,12 +102,17 @@ __device__ __forceinline__ float rint_add(float x, int &as_int)
 // boundary and the point is more than 4e-6 from the zone edge.  Returns -1
 // near a wedge boundary, -2 near the zone edge or the origin; jc gets the
 // nearest-centre estimate.
-__device__ __forceinline__ int project32_guarded(float rx, float ry, int N, float inv_dth, float dth, int &jc)
+__device__ __forceinline__ void fold32(float rx, float ry, float &x, float &y)
 {
     const float tp = 6.28318531f;
     int ix;
-    const float x = rx - tp * rint_add(rx * 0.159154943f, ix);
-    const float y = ry - tp * rint_add(ry * 0.159154943f, ix);
+    x = rx - tp * rint_add(rx * 0.159154943f, ix);
+    y = ry - tp * rint_add(ry * 0.159154943f, ix);
+}
+
+// (x, y) already folded.
+__device__ __forceinline__ int project32_guarded(float x, float y, int N, float inv_dth, float dth, int &jc)
+{
     const float r2 = x * x + y * y;
     const float u = atan2_poly(y, x) * inv_dth;      // angle in units of the wedge width
     int j;
@@ -287,8 +292,11 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
     __syncthreads();
     const R Za = s_VZ[2 * a + 1];
     const R ckx = s_k[0], skx = s_k[1], cky = s_k[2], sky = s_k[3];
+    // records in angular-minor order: storage index s * n_theta + t for the
+    // point (t, s), so consecutive records are angular neighbours
+    const int nt = A.pb.n_theta, nr = A.pb.n_r;
     for (int i = tid; i < P; i += blockDim.x) {
-        const int p = a * P + i;
+        const int p = a * P + (i % nt) * nr + i / nt;
         R *rec = s_rec + (size_t)REC * i;
         if (f32) {
             // k_j + p as FP32 hi/lo pairs from the per-call table
@@ -334,24 +342,39 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
         const R d0shift = A.xij_r[j], twoT = A.twoT_r;
         const R eta2 = eta * eta;
         const float inv_dth = (float)(N / kTwoPi), dth = (float)(kTwoPi / N);
+        // wedge of the previous pair and its two boundary rays (FP32)
+        int cprev = -1;
+        float blx = 0.f, bly = 0.f, bhx = 0.f, bhy = 0.f;
         for (int i = 0; i < P; ++i) {
             R r[REC];
             load_rec(s_rec, i, r);
             int c;
             if (f32 && wedge) {
-                int jc;
-                c = project32_guarded((float)(r[0] - qx), (float)(r[1] - qy), N, inv_dth, dth, jc);
-                if (c == -1) {
-                    // near a wedge boundary: float-float decision on the FP32 pipes
-                    c = project_ff((float)r[0], (float)r[10], (float)r[1], (float)r[11], (float)qx, qxl, (float)qy,
-                                   qyl, jc, N, s_bnd);
-                } else if (c == -2) {
-                    // zone edge or origin: the exact FP64 projection
-                    const int p = a * P + i;
-                    c = project64((kx + A.kx64[p]) - qxd, (ky + A.ky64[p]) - qyd, N, A.pb.mode, A.pb.L);
+                float x, y;
+                fold32((float)(r[0] - qx), (float)(r[1] - qy), x, y);
+                // inside the previous pair's wedge by more than the FP32 error
+                // of (x, y) (2.1e-6) plus that of the rays: same patch
+                const bool edge = fabsf(x) > 3.14159265f - 4e-6f || fabsf(y) > 3.14159265f - 4e-6f;
+                if (!edge && cprev >= 0 && blx * y - bly * x >= 4e-6f && bhx * y - bhy * x <= -4e-6f) {
+                    c = cprev;
+                } else {
+                    int jc;
+                    c = project32_guarded(x, y, N, inv_dth, dth, jc);
+                    if (c == -1) {
+                        // near a wedge boundary: float-float decision on the FP32 pipes
+                        c = project_ff((float)r[0], (float)r[10], (float)r[1], (float)r[11], (float)qx, qxl,
+                                       (float)qy, qyl, jc, N, s_bnd);
+                    } else if (c == -2) {
+                        // zone edge or origin: the exact FP64 projection
+                        const int p = a * P + (i % nt) * nr + i / nt;
+                        c = project64((kx + A.kx64[p]) - qxd, (ky + A.ky64[p]) - qyd, N, A.pb.mode, A.pb.L);
+                    }
+                    cprev = c;
+                    const float4 lo = s_bnd[c], hi = s_bnd[c + 1 == N ? 0 : c + 1];
+                    blx = lo.x; bly = lo.z; bhx = hi.x; bhy = hi.z;
                 }
             } else {
-                const int p = a * P + i;
+                const int p = a * P + (i % nt) * nr + i / nt;
                 c = project64((kx + A.kx64[p]) - qxd, (ky + A.ky64[p]) - qyd, N, A.pb.mode, A.pb.L);
             }
             // cos(k+p-q) by angle addition
