@@ -112,25 +112,30 @@ long n3_of(const qpfrg_ctx *c) { return (long)c->pb.N * c->pb.N * c->pb.N; }
 
 // C4v images of a wedge patch (centres at 2 pi j / N, N a multiple of 4):
 // j -> +-j + m N/4.  True when V[g i][g j][g l] = V[i][j][l] and Z[g j] = Z[j]
-// for all 8 group elements, to a relative 1e-12.
+// for all 8 group elements, to a relative tol (the rounding level of the
+// precision that produced the state: a mixed-precision flow keeps the
+// symmetry only to FP32 rounding).
 bool c4v_symmetric(const qpfrg_ctx *c, const double *V, const double *Z)
 {
     if (c->pb.mode != QPFRG_GRID_WEDGE) return false;
+    const double tol = c->opt.precision == QPFRG_FP64 ? 1e-12 : 1e-5;
     const int N = c->pb.N, q = N / 4;
     double vmax = 0.0, zmax = 0.0;
     for (long i = 0; i < n3_of(c); ++i) vmax = std::fmax(vmax, std::fabs(V[i]));
     for (int j = 0; j < N; ++j) zmax = std::fmax(zmax, std::fabs(Z[j]));
+    std::vector<int> g(N);
     for (int m = 0; m < 4; ++m)
         for (int sgn = -1; sgn <= 1; sgn += 2) {
-            auto g = [&](int j) { return ((sgn * j + m * q) % N + N) % N; };
+            for (int j = 0; j < N; ++j) g[j] = ((sgn * j + m * q) % N + N) % N;
             for (int j = 0; j < N; ++j)
-                if (std::fabs(Z[g(j)] - Z[j]) > 1e-12 * zmax) return false;
+                if (std::fabs(Z[g[j]] - Z[j]) > tol * zmax) return false;
             for (int i = 0; i < N; ++i)
-                for (int j = 0; j < N; ++j)
-                    for (int l = 0; l < N; ++l) {
-                        const double a = V[((long)g(i) * N + g(j)) * N + g(l)], b = V[((long)i * N + j) * N + l];
-                        if (std::fabs(a - b) > 1e-12 * vmax) return false;
-                    }
+                for (int j = 0; j < N; ++j) {
+                    const double *row = V + ((long)i * N + j) * N;
+                    const double *img = V + ((long)g[i] * N + g[j]) * N;
+                    for (int l = 0; l < N; ++l)
+                        if (std::fabs(img[g[l]] - row[l]) > tol * vmax) return false;
+                }
         }
     return true;
 }
