@@ -11,10 +11,49 @@
 // Lattice mode instead takes every momentum of an L x L lattice as a patch.
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "qpfrg_internal.h"
 
 namespace qpfrg {
+
+// Cell table of the FP32 wedge projection (sigma.cu).  A folded momentum
+// (x, y) in [-pi, pi]^2 falls in cell K = round(x W / 2 pi + W/2) per
+// component, K in 0..W, which covers [-pi + (K - 1/2) h, -pi + (K + 1/2) h],
+// h = 2 pi / W.  The entry is the lower of the at most two wedges that the
+// cell, widened by 2e-5 on every side, touches (the ray between them is then
+// tested in the kernel), or 255 when it touches three or more wedges or
+// contains the origin.  The margin exceeds the 1.4e-6 position error of the
+// FP32 momenta and the 2e-7 cell-boundary error of the FP32 index.  Rows
+// (K_y) are kProjStride bytes apart.
+static std::vector<uint8_t> build_proj_table(int N)
+{
+    const int W = kProjW, n = W + 1;
+    const double h = kTwoPi / W, m = 2e-5, dth = kTwoPi / N;
+    std::vector<uint8_t> tab((size_t)n * kProjStride, 255);
+    for (int ky = 0; ky <= W; ++ky)
+        for (int kx = 0; kx <= W; ++kx) {
+            const double x0 = std::fmax(-kPi + (kx - 0.5) * h, -kPi) - m;
+            const double x1 = std::fmin(-kPi + (kx + 0.5) * h, kPi) + m;
+            const double y0 = std::fmax(-kPi + (ky - 0.5) * h, -kPi) - m;
+            const double y1 = std::fmin(-kPi + (ky + 0.5) * h, kPi) + m;
+            if (x0 <= 0.0 && x1 >= 0.0 && y0 <= 0.0 && y1 >= 0.0) continue;
+            // the angular extent of a rectangle clear of the origin is spanned
+            // by its corners; unwrap them about the first corner
+            const double cx[4] = {x0, x1, x0, x1}, cy[4] = {y0, y0, y1, y1};
+            const double a0 = std::atan2(cy[0], cx[0]);
+            double lo = 0.0, hi = 0.0;
+            for (int k = 1; k < 4; ++k) {
+                const double d = std::remainder(std::atan2(cy[k], cx[k]) - a0, kTwoPi);
+                lo = std::fmin(lo, d);
+                hi = std::fmax(hi, d);
+            }
+            const long jl = (long)std::floor((a0 + lo) / dth + 0.5);
+            const long jh = (long)std::floor((a0 + hi) / dth + 0.5);
+            if (jh - jl <= 1) tab[(size_t)ky * kProjStride + kx] = (uint8_t)(((jl % N) + N) % N);
+        }
+    return tab;
+}
 
 static double host_xi(const Problem &pb, double kx, double ky)
 {
@@ -250,6 +289,14 @@ qpfrg_status upload_geometry(qpfrg_ctx *c)
         cudaMemcpy(c->d_bnd, bnd.data(), N * sizeof(float4), cudaMemcpyHostToDevice);
         cudaMemcpy(c->d_qxl, xl.data(), M * sizeof(float), cudaMemcpyHostToDevice);
         cudaMemcpy(c->d_qyl, yl.data(), M * sizeof(float), cudaMemcpyHostToDevice);
+        if (c->pb.mode == QPFRG_GRID_WEDGE && N <= 254) {
+            std::vector<uint8_t> tab = build_proj_table(N);
+            const size_t bytes = (tab.size() + 15) / 16 * 16;
+            tab.resize(bytes, 255);
+            if ((e = cudaMalloc((void **)&c->d_ptab, bytes)) != cudaSuccess)
+                return cuda_fail(c, e, "cudaMalloc(projection table)");
+            cudaMemcpy(c->d_ptab, tab.data(), bytes, cudaMemcpyHostToDevice);
+        }
     }
     if ((e = cudaMalloc((void **)&c->d_Qpp, 2 * NN * sizeof(double))) != cudaSuccess ||
         (e = cudaMalloc((void **)&c->d_Qph, 2 * NN * sizeof(double))) != cudaSuccess)

@@ -224,7 +224,8 @@ void qpfrg_destroy(qpfrg_t c)
                         c->d_part, c->d_B, c->d_ones, c->d_sig, c->d_hist, c->d_jirr, c->d_rep,
                         c->tc.App[0], c->tc.App[1], c->tc.Acr[0], c->tc.Acr[1], c->tc.Ad[0], c->tc.Ad[1],
                         c->tc.Bpp[0], c->tc.Bpp[1], c->tc.Bcr[0], c->tc.Bcr[1], c->tc.Bd[0], c->tc.Bd[1],
-                        c->tc.VT, c->d_tc_err, c->d_xij, c->d_bnd, c->d_qxl, c->d_qyl, c->d_kp, c->d_kcs, c->d_xij_f};
+                        c->tc.VT, c->d_tc_err, c->d_xij, c->d_bnd, c->d_qxl, c->d_qyl, c->d_kp, c->d_kcs, c->d_xij_f,
+                        c->d_ptab};
         for (void *p : ptrs)
             if (p) cudaFree(p);
     }

@@ -428,6 +428,274 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 chord-slope kernel of the wedge grid (the flow's self-energy).
+//
+// Same sum as sigma_kernel<float,false>, arranged for instruction count:
+// * the patch c of r = k_j + p - q comes from a shared-memory cell table over
+//   the folded zone (one byte per cell: the lower of the at most two wedges
+//   the cell touches) and one FP32 test against the ray between them; cells
+//   near the origin, points within 4e-6 of a ray and points within 4e-6 of
+//   the zone edge take the guarded paths of sigma_kernel (float-float rays,
+//   exact FP64 projection), so every patch decision equals the FP64 one;
+// * f_r enters only through F = A + f_r (B - A) with A = w_p f_p (1 - f_q),
+//   B = w_p (1 - f_p) f_q (times Z_a Z_b w_q), so one exp2 and one
+//   reciprocal give it;
+// * per patch c the table cz holds (Z_c, Z_c V[j][a][c], -2t l_c, -mu l_c),
+//   l_c = Z_c for quasi-particle lines (else 1), so the line energy of r
+//   (Z-scaled) is one FMA from cos(r_x) + cos(r_y);
+// * each thread owns SF_QPT loop points q, so a record of p read from shared
+//   memory serves SF_QPT pairs; the lanes of a warp own angular neighbours at
+//   one radius (angular-minor order), so their r lie on a short arc and their
+//   table cells, rays and patch slots mostly coincide (few bank conflicts,
+//   rare divergence into the guarded paths).
+// Launch: grid (ceil(M / (256 SF_QPT)), N patches a, targets), 256 threads,
+// two CTAs per SM.
+constexpr int SF_QPT = 2;
+constexpr int SF_PCH = 1024;    // loop points p staged per pass
+constexpr int SF_SLOTS = 257;   // per-patch slots: c in 0..N (c = N is patch 0 again), padded to 257
+
+struct SigmaFastArgs {
+    Problem pb;
+    FineTable<float> fine;
+    const double *V, *Z, *kx64, *ky64, *kf;
+    const float *xij_f, *qxl, *qyl;
+    const float4 *kp, *kcs, *bnd;
+    const uint8_t *ptab;
+    const int *jlist;
+    double *sig;
+    float t, tp, mu, eta2, invT, cT, twoT, fourT;   // cT = log2(e) / T
+    float inv_dth, dth;                             // N / 2 pi, 2 pi / N
+};
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// r -> r - 2 pi rint(r / 2 pi) on the FP32 pipes (|r| < 2^22)
+__device__ __forceinline__ float fold1(float r)
+{
+    const float s = fmaf(r, 0.159154943f, 12582912.f);
+    return fmaf(-6.28318531f, s - 12582912.f, r);
+}
+
+struct SfSmem {
+    size_t rA, rB, cz, ray, cd, rC, tab, total;
+};
+
+__host__ __device__ inline SfSmem sf_smem_layout(int pch)
+{
+    SfSmem L;
+    L.rA = 0;
+    L.rB = L.rA + (size_t)16 * pch;
+    L.cz = L.rB + (size_t)16 * pch;
+    L.ray = L.cz + (size_t)16 * SF_SLOTS;
+    L.cd = L.ray + (size_t)8 * SF_SLOTS;
+    L.rC = (L.cd + (size_t)4 * SF_SLOTS + 15) / 16 * 16;
+    L.tab = (L.rC + (size_t)4 * pch + 15) / 16 * 16;
+    L.total = L.tab + ((size_t)(kProjW + 1) * kProjStride + 15) / 16 * 16;
+    return L;
+}
+
+// Patch of r for a lane that left the table path: near a ray or the origin
+// (float-float ray tests) or near the zone edge (FP64 projection).
+__device__ __noinline__ int sf_slow_patch(const SigmaFastArgs &A, int jidx, int j, int p, int q, float x, float y,
+                                          bool edge, const float4 *bnd)
+{
+    const int N = A.pb.N;
+    int c = -2;
+    if (!edge) {
+        int jc;
+        c = project32_guarded(x, y, N, A.inv_dth, A.dth, jc);
+        if (c == -1) {
+            const float4 k4 = A.kp[(long)jidx * A.pb.M + p];
+            c = project_ff(k4.x, k4.y, k4.z, k4.w, A.fine.kx[q], A.qxl[q], A.fine.ky[q], A.qyl[q], jc, N, bnd);
+        }
+    }
+    if (c < 0)
+        c = project64((A.kf[2 * j] + A.kx64[p]) - A.kx64[q], (A.kf[2 * j + 1] + A.ky64[p]) - A.ky64[q], N,
+                      QPFRG_GRID_WEDGE, 0);
+    return c;
+}
+
+template <bool TP0>
+__global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
+{
+    const int N = A.pb.N, P = A.pb.P, M = A.pb.M;
+    const int a = blockIdx.y, jidx = blockIdx.z;
+    const int j = A.jlist ? A.jlist[jidx] : jidx;
+    const int tid = threadIdx.x;
+    const bool qp = A.pb.propagator == QPFRG_PROP_QP;
+    const int pch = P < SF_PCH ? P : SF_PCH;
+    const SfSmem L = sf_smem_layout(pch);
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4 *rA = reinterpret_cast<float4 *>(smem_raw + L.rA);   // (k+p)_x, (k+p)_y, cos, sin of (k+p)_x
+    float4 *rB = reinterpret_cast<float4 *>(smem_raw + L.rB);   // cos, sin of (k+p)_y, w_p f_p, w_p (1 - f_p)
+    float4 *cz = reinterpret_cast<float4 *>(smem_raw + L.cz);
+    float2 *ray = reinterpret_cast<float2 *>(smem_raw + L.ray);
+    float *cd = reinterpret_cast<float *>(smem_raw + L.cd);     // -4 t' l_c
+    float *rC = reinterpret_cast<float *>(smem_raw + L.rC);     // x_j + x_p + 2T
+    unsigned char *tab = smem_raw + L.tab;
+
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(A.ptab);
+        uint4 *dst = reinterpret_cast<uint4 *>(tab);
+        const int n16 = ((kProjW + 1) * kProjStride + 15) / 16;
+        for (int i = tid; i < n16; i += blockDim.x) dst[i] = src[i];
+    }
+    const double *Vja = A.V + ((long)j * N + a) * N;
+    for (int i = tid; i < SF_SLOTS; i += blockDim.x) {
+        if (i <= N) {
+            const int cc = i == N ? 0 : i;
+            const float Zc = A.Z ? (float)A.Z[cc] : 1.f;
+            const float lz = qp ? Zc : 1.f;
+            cz[i] = make_float4(Zc, Zc * (float)Vja[cc], -2.f * A.t * lz, -A.mu * lz);
+            cd[i] = -4.f * A.tp * lz;
+            const float4 b = A.bnd[cc];
+            ray[i] = make_float2(b.x, b.z);
+        } else {
+            cz[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            cd[i] = 0.f;
+            ray[i] = make_float2(0.f, 0.f);
+        }
+    }
+    const float Za = A.Z ? (float)A.Z[a] : 1.f;
+    const float lza = qp ? Za : 1.f;
+    const float4 kcs = A.kcs[jidx];
+    const float xj = A.xij_f[j];
+
+    // the SF_QPT loop points q of this thread (an index past M gets weight 0)
+    float qx[SF_QPT], qy[SF_QPT], cqx[SF_QPT], sqx[SF_QPT], cqy[SF_QPT], sqy[SF_QPT];
+    float fqp[SF_QPT], fcqp[SF_QPT], v2[SF_QPT], vab[SF_QPT], mxq[SF_QPT], acc[SF_QPT];
+    int qi[SF_QPT];
+#pragma unroll
+    for (int k = 0; k < SF_QPT; ++k) {
+        const int iq = blockIdx.x * (256 * SF_QPT) + k * 256 + tid;   // angular-minor index
+        const bool valid = iq < M;
+        const int ii = valid ? iq : M - 1;
+        const int bq = ii / P, rem = ii - bq * P;
+        const int qq = bq * P + (rem % A.pb.n_theta) * A.pb.n_r + rem / A.pb.n_theta;
+        qi[k] = qq;
+        const int b = qq / P;
+        const float Zb = A.Z ? (float)A.Z[b] : 1.f;
+        qx[k] = A.fine.kx[qq];
+        qy[k] = A.fine.ky[qq];
+        cqx[k] = A.fine.cx[qq];
+        sqx[k] = A.fine.sx[qq];
+        cqy[k] = A.fine.cy[qq];
+        sqy[k] = A.fine.sy[qq];
+        const float xq = (qp ? Zb : 1.f) * A.fine.xi[qq];
+        float fq, fcq;
+        sfermi(xq, A.invT, fq, fcq);
+        const float pref = valid ? Za * Zb * A.fine.w[qq] : 0.f;
+        fqp[k] = fq * pref;
+        fcqp[k] = fcq * pref;
+        vab[k] = (float)Vja[b];
+        v2[k] = 2.f * vab[k] * vab[k];
+        mxq[k] = -xq;
+        acc[k] = 0.f;
+    }
+
+    const unsigned tab_last = (kProjW + 1) * kProjStride - 1;
+    const float kW = (float)(kProjW / kTwoPi);
+    for (int p0 = 0; p0 < P; p0 += pch) {
+        const int cnt = P - p0 < pch ? P - p0 : pch;
+        __syncthreads();   // previous pass done with the records (and the tables written)
+        for (int i = tid; i < cnt; i += blockDim.x) {
+            const int p = a * P + p0 + i;
+            const float4 k4 = A.kp[(long)jidx * M + p];
+            const float cpx = A.fine.cx[p], spx = A.fine.sx[p], cpy = A.fine.cy[p], spy = A.fine.sy[p];
+            const float xp = lza * A.fine.xi[p];
+            float fp, fcp;
+            sfermi(xp, A.invT, fp, fcp);
+            const float wp = A.fine.w[p];
+            rA[i] = make_float4(k4.x, k4.z, kcs.x * cpx - kcs.y * spx, kcs.y * cpx + kcs.x * spx);
+            rB[i] = make_float4(kcs.z * cpy - kcs.w * spy, kcs.w * cpy + kcs.z * spy, wp * fp, wp * fcp);
+            rC[i] = xj + xp + A.twoT;
+        }
+        __syncthreads();
+        for (int i = 0; i < cnt; ++i) {
+            const float4 ra = rA[i], rb = rB[i];
+            const float upp = rC[i];
+            int c[SF_QPT];
+            float x[SF_QPT], y[SF_QPT];
+            bool slow_any = false;
+            unsigned slow_mask = 0;
+#pragma unroll
+            for (int k = 0; k < SF_QPT; ++k) {
+                x[k] = fold1(ra.x - qx[k]);
+                y[k] = fold1(ra.y - qy[k]);
+                const bool edge = fmaxf(fabsf(x[k]), fabsf(y[k])) > 3.14159265f - 4e-6f;
+                const float sx = fmaf(x[k], kW, 12583040.f);   // 1.5 * 2^23 + W/2: low bits = cell index
+                const float sy = fmaf(y[k], kW, 12583040.f);
+                unsigned idx = (unsigned)__float_as_int(sy) * (unsigned)kProjStride + (unsigned)__float_as_int(sx) -
+                               0x4B400000u * (unsigned)(kProjStride + 1);
+                idx = min(idx, tab_last);
+                const int e = tab[idx];
+                const float2 rr = ray[e + 1];
+                const float cr = rr.x * y[k] - rr.y * x[k];
+                c[k] = e + (cr >= 0.f ? 1 : 0);
+                const bool slow = edge || e == 255 || fabsf(cr) < 4e-6f;
+                slow_mask |= slow ? 1u << k : 0u;
+                slow_any = slow_any || slow;
+            }
+            if (slow_any) {
+#pragma unroll
+                for (int k = 0; k < SF_QPT; ++k)
+                    if (slow_mask & (1u << k)) {
+                        const bool edge = fmaxf(fabsf(x[k]), fabsf(y[k])) > 3.14159265f - 4e-6f;
+                        c[k] = sf_slow_patch(A, jidx, j, a * P + p0 + i, qi[k], x[k], y[k], edge, A.bnd);
+                    }
+            }
+#pragma unroll
+            for (int k = 0; k < SF_QPT; ++k) {
+                const float4 z = cz[c[k]];
+                const float crx = ra.z * cqx[k] + ra.w * sqx[k];
+                const float cry = rb.x * cqy[k] + rb.y * sqy[k];
+                float xr = fmaf(crx + cry, z.z, z.w);           // Z-scaled line energy of r
+                if (!TP0) xr = fmaf(crx * cry, cd[c[k]], xr);
+                const float fr = rcp_approx(1.f + ex2_approx(xr * A.cT));
+                const float Aq = rb.z * fcqp[k], Bq = rb.w * fqp[k];
+                const float F = fmaf(fr, Bq - Aq, Aq);
+                const float amp = fmaf(-vab[k], z.y, z.x * v2[k]) * F;
+                // d+- = xi_j +- 2T - E with E = x_q + x_r - x_p
+                const float dp = (upp + mxq[k]) - xr;
+                const float dm = dp - A.fourT;
+                const float den = fmaf(dp, dp, A.eta2) * fmaf(dm, dm, A.eta2);
+                const float num = fmaf(-dp, dm, A.eta2);
+                acc[k] = fmaf(amp * num, rcp_approx(den), acc[k]);
+            }
+        }
+    }
+    __shared__ double red[32];
+    double v = 0.0;
+#pragma unroll
+    for (int k = 0; k < SF_QPT; ++k) v += (double)acc[k];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    const int lane = tid & 31, warp = tid >> 5;
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        v = lane < nw ? red[lane] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) atomicAdd(&A.sig[jidx], v);
+    }
+}
+
 // Z_j = 1/(1 - slope) with the chord slope accumulated per target.  rep[j]
 // (may be NULL) is the slot of j's C4v representative among the targets.
 __global__ void z_update_kernel(const double *slope, const int *rep, double *Zout, int N)
@@ -467,15 +735,23 @@ __global__ void sigma_grid_kernel(const double *hist, int nbins, double e_min, d
     im[(long)j * n_omega + m] = si;
 }
 
+static qpfrg_status launch_kp_table(qpfrg_ctx *c, const int *jlist, int nj)
+{
+    const long total = (long)nj * c->pb.M;
+    kp_table_kernel<<<(int)std::min<long>((total + 255) / 256, 152L * 8), 256, 0, c->stream>>>(
+        c->d_kf, jlist, nj, c->f64.kx, c->f64.ky, c->pb.M, c->d_kp, c->d_kcs);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "kp_table_kernel");
+}
+
 template <typename R>
 static qpfrg_status launch_sigma(qpfrg_ctx *c, bool hist, SigmaArgs<R> &A, int kid)
 {
     const int P = c->pb.P, N = c->pb.N;
     const size_t smem = (size_t)(REC * P + 2 * N) * sizeof(R) + 16 + (size_t)N * sizeof(float4);
     if (sizeof(R) == 4) {
-        const long total = (long)A.nj * c->pb.M;
-        kp_table_kernel<<<(int)std::min<long>((total + 255) / 256, 152L * 8), 256, 0, c->stream>>>(
-            c->d_kf, A.jlist, A.nj, c->f64.kx, c->f64.ky, c->pb.M, c->d_kp, c->d_kcs);
+        const qpfrg_status s = launch_kp_table(c, A.jlist, A.nj);
+        if (s != QPFRG_OK) return s;
     }
     auto kern = hist ? sigma_kernel<R, true> : sigma_kernel<R, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -486,6 +762,51 @@ static qpfrg_status launch_sigma(qpfrg_ctx *c, bool hist, SigmaArgs<R> &A, int k
     prof_end(c, kid);
     e = cudaGetLastError();
     return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "sigma_kernel");
+}
+
+static qpfrg_status launch_sigma_fast(qpfrg_ctx *c, double T, const double *d_V, const double *d_Z,
+                                      const int *jlist, int nj)
+{
+    qpfrg_status s = launch_kp_table(c, jlist, nj);
+    if (s != QPFRG_OK) return s;
+    SigmaFastArgs A;
+    A.pb = c->pb;
+    A.fine = c->f32;
+    A.V = d_V;
+    A.Z = d_Z;
+    A.kx64 = c->f64.kx;
+    A.ky64 = c->f64.ky;
+    A.kf = c->d_kf;
+    A.xij_f = c->d_xij_f;
+    A.qxl = c->d_qxl;
+    A.qyl = c->d_qyl;
+    A.kp = c->d_kp;
+    A.kcs = c->d_kcs;
+    A.bnd = c->d_bnd;
+    A.ptab = c->d_ptab;
+    A.jlist = jlist;
+    A.sig = c->d_sig;
+    A.t = (float)c->pb.t;
+    A.tp = (float)c->pb.tp;
+    A.mu = (float)c->pb.mu;
+    A.eta2 = (float)(c->pb.eta * c->pb.eta);
+    A.invT = (float)(1.0 / T);
+    A.cT = (float)(1.4426950408889634 / T);
+    A.twoT = (float)(2.0 * T);
+    A.fourT = (float)(4.0 * T);
+    A.inv_dth = (float)(c->pb.N / kTwoPi);
+    A.dth = (float)(kTwoPi / c->pb.N);
+    const int pch = c->pb.P < SF_PCH ? c->pb.P : SF_PCH;
+    const size_t smem = sf_smem_layout(pch).total;
+    auto kern = c->pb.tp == 0.0 ? sigma_fast_kernel<true> : sigma_fast_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(c, e, "sigma_fast smem attribute");
+    dim3 grid(div_up(c->pb.M, 256 * SF_QPT), c->pb.N, nj);
+    prof_begin(c);
+    kern<<<grid, 256, smem, c->stream>>>(A);
+    prof_end(c, K_SIGMA_Z);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "sigma_fast_kernel");
 }
 
 template <typename R>
@@ -540,6 +861,8 @@ qpfrg_status launch_sigma_z(qpfrg_ctx *c, double T, const double *d_V, const dou
         A.nj = nj;
         A.jlist = sym ? c->d_jirr : nullptr;
         s = launch_sigma(c, false, A, K_SIGMA_Z);
+    } else if (c->d_ptab) {
+        s = launch_sigma_fast(c, T, d_V, d_Z, sym ? c->d_jirr : nullptr, nj);
     } else {
         SigmaArgs<float> A;
         fill_args(c, A, c->f32, T, d_V, d_Z);

@@ -46,6 +46,25 @@ def test_z_matches_oracle(geo, prec, tol):
     assert np.abs(got - ref).max() < tol
 
 
+@pytest.mark.parametrize("case", [
+    dict(N=16, nt=4, nr=4, tp=-0.2, mu=-0.3, prop=1),   # t' != 0 line energies, QP lines
+    dict(N=8, nt=34, nr=32, tp=0.0, mu=0.0, prop=0),    # P = 1088 loop points: two record passes
+    dict(N=48, nt=4, nr=4, tp=0.0, mu=0.0, prop=1),     # 48 wedges, ragged last block of q
+], ids=["tp_mu_qp", "two_passes", "np48"])
+def test_z_mixed_wedge_cases(case):
+    """Mixed-precision Z (table-driven wedge projection) against the oracle."""
+    N, nt, nr = case["N"], case["nt"], case["nr"]
+    T = 0.2
+    o = Oracle(N, nt, nr, tp=case["tp"], mu=case["mu"], eta=0.02, prop_mode=case["prop"])
+    V = inputs.random_vertex(N, 2.0, seed=5, c4v=True)
+    Z = inputs.z_profile(N, "aniso")
+    ref = o.zfactor(T, V, Z)
+    with api.Context(N, nt, nr, U=2.0, tp=case["tp"], mu=case["mu"], precision=api.QPFRG_MIXED,
+                     propagator=case["prop"]) as ctx:
+        got = gpu_z(ctx, T, V, Z)
+    assert np.abs(got - ref).max() < 1e-4
+
+
 @pytest.mark.parametrize("prec", [api.QPFRG_FP64, api.QPFRG_MIXED])
 def test_sigma_grid_matches_exact_pole_sum(prec):
     import torch
