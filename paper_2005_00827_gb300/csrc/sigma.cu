@@ -449,9 +449,10 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
 //   one radius (angular-minor order), so their r lie on a short arc and their
 //   table cells, rays and patch slots mostly coincide (few bank conflicts,
 //   rare divergence into the guarded paths).
-// Launch: grid (ceil(M / (256 SF_QPT)), N patches a, targets), 256 threads,
+// Launch: grid (ceil(M / (256 SF_QPT SF_QB)), N patches a, targets), 256 threads,
 // two CTAs per SM.
 constexpr int SF_QPT = 2;
+constexpr int SF_QB = 4;        // blocks of 256 SF_QPT loop points q per CTA
 constexpr int SF_PCH = 1024;    // loop points p staged per pass
 constexpr int SF_SLOTS = 257;   // per-patch slots: c in 0..N (c = N is patch 0 again), padded to 257
 
@@ -575,43 +576,10 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
     const float4 kcs = A.kcs[jidx];
     const float xj = A.xij_f[j];
 
-    // the SF_QPT loop points q of this thread (an index past M gets weight 0)
-    float qx[SF_QPT], qy[SF_QPT], cqx[SF_QPT], sqx[SF_QPT], cqy[SF_QPT], sqy[SF_QPT];
-    float fqp[SF_QPT], fcqp[SF_QPT], v2[SF_QPT], vab[SF_QPT], mxq[SF_QPT], acc[SF_QPT];
-    int qi[SF_QPT];
-#pragma unroll
-    for (int k = 0; k < SF_QPT; ++k) {
-        const int iq = blockIdx.x * (256 * SF_QPT) + k * 256 + tid;   // angular-minor index
-        const bool valid = iq < M;
-        const int ii = valid ? iq : M - 1;
-        const int bq = ii / P, rem = ii - bq * P;
-        const int qq = bq * P + (rem % A.pb.n_theta) * A.pb.n_r + rem / A.pb.n_theta;
-        qi[k] = qq;
-        const int b = qq / P;
-        const float Zb = A.Z ? (float)A.Z[b] : 1.f;
-        qx[k] = A.fine.kx[qq];
-        qy[k] = A.fine.ky[qq];
-        cqx[k] = A.fine.cx[qq];
-        sqx[k] = A.fine.sx[qq];
-        cqy[k] = A.fine.cy[qq];
-        sqy[k] = A.fine.sy[qq];
-        const float xq = (qp ? Zb : 1.f) * A.fine.xi[qq];
-        float fq, fcq;
-        sfermi(xq, A.invT, fq, fcq);
-        const float pref = valid ? Za * Zb * A.fine.w[qq] : 0.f;
-        fqp[k] = fq * pref;
-        fcqp[k] = fcq * pref;
-        vab[k] = (float)Vja[b];
-        v2[k] = 2.f * vab[k] * vab[k];
-        mxq[k] = -xq;
-        acc[k] = 0.f;
-    }
-
     const unsigned tab_last = (kProjW + 1) * kProjStride - 1;
     const float kW = (float)(kProjW / kTwoPi);
-    for (int p0 = 0; p0 < P; p0 += pch) {
-        const int cnt = P - p0 < pch ? P - p0 : pch;
-        __syncthreads();   // previous pass done with the records (and the tables written)
+    // records of the loop points p0 .. p0 + cnt - 1 of patch a
+    auto stage = [&](int p0, int cnt) {
         for (int i = tid; i < cnt; i += blockDim.x) {
             const int p = a * P + p0 + i;
             const float4 k4 = A.kp[(long)jidx * M + p];
@@ -624,64 +592,114 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
             rB[i] = make_float4(kcs.z * cpy - kcs.w * spy, kcs.w * cpy + kcs.z * spy, wp * fp, wp * fcp);
             rC[i] = xj + xp + A.twoT;
         }
-        __syncthreads();
-        for (int i = 0; i < cnt; ++i) {
-            const float4 ra = rA[i], rb = rB[i];
-            const float upp = rC[i];
-            int c[SF_QPT];
-            float x[SF_QPT], y[SF_QPT];
-            bool slow_any = false;
-            unsigned slow_mask = 0;
+    };
+    const bool one_pass = P <= pch;
+    if (one_pass) stage(0, P);
+    __syncthreads();   // tables (and the records of a single pass) written
+
+    double vsum = 0.0;
+    // SF_QB blocks of 256 SF_QPT loop points q per CTA reuse the staged tables
+    for (int qb = 0; qb < SF_QB; ++qb) {
+        const int blk = blockIdx.x * SF_QB + qb;
+        if (blk * (256 * SF_QPT) >= M) break;   // uniform over the CTA
+        // the SF_QPT loop points q of this thread (an index past M gets weight 0)
+        float qx[SF_QPT], qy[SF_QPT], cqx[SF_QPT], sqx[SF_QPT], cqy[SF_QPT], sqy[SF_QPT];
+        float fqp[SF_QPT], fcqp[SF_QPT], v2[SF_QPT], vab[SF_QPT], mxq[SF_QPT], acc[SF_QPT];
+        int qi[SF_QPT];
 #pragma unroll
-            for (int k = 0; k < SF_QPT; ++k) {
-                x[k] = fold1(ra.x - qx[k]);
-                y[k] = fold1(ra.y - qy[k]);
-                const bool edge = fmaxf(fabsf(x[k]), fabsf(y[k])) > 3.14159265f - 4e-6f;
-                const float sx = fmaf(x[k], kW, 12583040.f);   // 1.5 * 2^23 + W/2: low bits = cell index
-                const float sy = fmaf(y[k], kW, 12583040.f);
-                unsigned idx = (unsigned)__float_as_int(sy) * (unsigned)kProjStride + (unsigned)__float_as_int(sx) -
-                               0x4B400000u * (unsigned)(kProjStride + 1);
-                idx = min(idx, tab_last);
-                const int e = tab[idx];
-                const float2 rr = ray[e + 1];
-                const float cr = rr.x * y[k] - rr.y * x[k];
-                c[k] = e + (cr >= 0.f ? 1 : 0);
-                const bool slow = edge || e == 255 || fabsf(cr) < 4e-6f;
-                slow_mask |= slow ? 1u << k : 0u;
-                slow_any = slow_any || slow;
+        for (int k = 0; k < SF_QPT; ++k) {
+            const int iq = blk * (256 * SF_QPT) + k * 256 + tid;   // angular-minor index
+            const bool valid = iq < M;
+            const int ii = valid ? iq : M - 1;
+            const int b = ii / P, rem = ii - b * P;
+            const int qq = b * P + (rem % A.pb.n_theta) * A.pb.n_r + rem / A.pb.n_theta;
+            qi[k] = qq;
+            const float Zb = A.Z ? (float)A.Z[b] : 1.f;
+            qx[k] = A.fine.kx[qq];
+            qy[k] = A.fine.ky[qq];
+            cqx[k] = A.fine.cx[qq];
+            sqx[k] = A.fine.sx[qq];
+            cqy[k] = A.fine.cy[qq];
+            sqy[k] = A.fine.sy[qq];
+            const float xq = (qp ? Zb : 1.f) * A.fine.xi[qq];
+            float fq, fcq;
+            sfermi(xq, A.invT, fq, fcq);
+            const float pref = valid ? Za * Zb * A.fine.w[qq] : 0.f;
+            fqp[k] = fq * pref;
+            fcqp[k] = fcq * pref;
+            vab[k] = (float)Vja[b];
+            v2[k] = 2.f * vab[k] * vab[k];
+            mxq[k] = -xq;
+            acc[k] = 0.f;
+        }
+
+        for (int p0 = 0; p0 < P; p0 += pch) {
+            const int cnt = P - p0 < pch ? P - p0 : pch;
+            if (!one_pass) {
+                __syncthreads();   // previous pass done with the records
+                stage(p0, cnt);
+                __syncthreads();
             }
-            if (slow_any) {
+#pragma unroll 2
+            for (int i = 0; i < cnt; ++i) {
+                const float4 ra = rA[i], rb = rB[i];
+                const float upp = rC[i];
+                int c[SF_QPT];
+                float x[SF_QPT], y[SF_QPT];
+                bool slow_any = false;
+                unsigned slow_mask = 0;
 #pragma unroll
-                for (int k = 0; k < SF_QPT; ++k)
-                    if (slow_mask & (1u << k)) {
-                        const bool edge = fmaxf(fabsf(x[k]), fabsf(y[k])) > 3.14159265f - 4e-6f;
-                        c[k] = sf_slow_patch(A, jidx, j, a * P + p0 + i, qi[k], x[k], y[k], edge, A.bnd);
-                    }
-            }
+                for (int k = 0; k < SF_QPT; ++k) {
+                    x[k] = fold1(ra.x - qx[k]);
+                    y[k] = fold1(ra.y - qy[k]);
+                    const bool edge = fmaxf(fabsf(x[k]), fabsf(y[k])) > 3.14159265f - 4e-6f;
+                    const float sx = fmaf(x[k], kW, 12583040.f);   // 1.5 * 2^23 + W/2: low bits = cell index
+                    const float sy = fmaf(y[k], kW, 12583040.f);
+                    unsigned idx = (unsigned)__float_as_int(sy) * (unsigned)kProjStride +
+                                   (unsigned)__float_as_int(sx) - 0x4B400000u * (unsigned)(kProjStride + 1);
+                    idx = min(idx, tab_last);
+                    const int e = tab[idx];
+                    // e = 255 (cell at the origin) reads the zero ray 256: cr = 0 takes the slow path
+                    const float2 rr = ray[e + 1];
+                    const float cr = rr.x * y[k] - rr.y * x[k];
+                    c[k] = e + (cr >= 0.f ? 1 : 0);
+                    const bool slow = edge || fabsf(cr) < 4e-6f;
+                    slow_mask |= slow ? 1u << k : 0u;
+                    slow_any = slow_any || slow;
+                }
+                if (slow_any) {
 #pragma unroll
-            for (int k = 0; k < SF_QPT; ++k) {
-                const float4 z = cz[c[k]];
-                const float crx = ra.z * cqx[k] + ra.w * sqx[k];
-                const float cry = rb.x * cqy[k] + rb.y * sqy[k];
-                float xr = fmaf(crx + cry, z.z, z.w);           // Z-scaled line energy of r
-                if (!TP0) xr = fmaf(crx * cry, cd[c[k]], xr);
-                const float fr = rcp_approx(1.f + ex2_approx(xr * A.cT));
-                const float Aq = rb.z * fcqp[k], Bq = rb.w * fqp[k];
-                const float F = fmaf(fr, Bq - Aq, Aq);
-                const float amp = fmaf(-vab[k], z.y, z.x * v2[k]) * F;
-                // d+- = xi_j +- 2T - E with E = x_q + x_r - x_p
-                const float dp = (upp + mxq[k]) - xr;
-                const float dm = dp - A.fourT;
-                const float den = fmaf(dp, dp, A.eta2) * fmaf(dm, dm, A.eta2);
-                const float num = fmaf(-dp, dm, A.eta2);
-                acc[k] = fmaf(amp * num, rcp_approx(den), acc[k]);
+                    for (int k = 0; k < SF_QPT; ++k)
+                        if (slow_mask & (1u << k)) {
+                            const bool edge = fmaxf(fabsf(x[k]), fabsf(y[k])) > 3.14159265f - 4e-6f;
+                            c[k] = sf_slow_patch(A, jidx, j, a * P + p0 + i, qi[k], x[k], y[k], edge, A.bnd);
+                        }
+                }
+#pragma unroll
+                for (int k = 0; k < SF_QPT; ++k) {
+                    const float4 z = cz[c[k]];
+                    const float crx = ra.z * cqx[k] + ra.w * sqx[k];
+                    const float cry = rb.x * cqy[k] + rb.y * sqy[k];
+                    float xr = fmaf(crx + cry, z.z, z.w);           // Z-scaled line energy of r
+                    if (!TP0) xr = fmaf(crx * cry, cd[c[k]], xr);
+                    const float fr = rcp_approx(1.f + ex2_approx(xr * A.cT));
+                    const float Aq = rb.z * fcqp[k], Bq = rb.w * fqp[k];
+                    const float F = fmaf(fr, Bq - Aq, Aq);
+                    const float amp = fmaf(-vab[k], z.y, z.x * v2[k]) * F;
+                    // d+- = xi_j +- 2T - E with E = x_q + x_r - x_p
+                    const float dp = (upp + mxq[k]) - xr;
+                    const float dm = dp - A.fourT;
+                    const float den = fmaf(dp, dp, A.eta2) * fmaf(dm, dm, A.eta2);
+                    const float num = fmaf(-dp, dm, A.eta2);
+                    acc[k] = fmaf(amp * num, rcp_approx(den), acc[k]);
+                }
             }
         }
+#pragma unroll
+        for (int k = 0; k < SF_QPT; ++k) vsum += (double)acc[k];
     }
     __shared__ double red[32];
-    double v = 0.0;
-#pragma unroll
-    for (int k = 0; k < SF_QPT; ++k) v += (double)acc[k];
+    double v = vsum;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
     const int lane = tid & 31, warp = tid >> 5;
@@ -801,7 +819,7 @@ static qpfrg_status launch_sigma_fast(qpfrg_ctx *c, double T, const double *d_V,
     auto kern = c->pb.tp == 0.0 ? sigma_fast_kernel<true> : sigma_fast_kernel<false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(c, e, "sigma_fast smem attribute");
-    dim3 grid(div_up(c->pb.M, 256 * SF_QPT), c->pb.N, nj);
+    dim3 grid(div_up(div_up(c->pb.M, 256 * SF_QPT), SF_QB), c->pb.N, nj);
     prof_begin(c);
     kern<<<grid, 256, smem, c->stream>>>(A);
     prof_end(c, K_SIGMA_Z);
