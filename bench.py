@@ -10,6 +10,12 @@ value is RHS evaluations per second over the timed steps (4 per step, the
 self-energy included in the time).  Inputs: synthetic lattice parameters,
 no dataset.  All device inputs (partner maps, bubble tables) exceed L2.
 
+The default precision is QPFRG_MIXED_TC (FP32 loop kernels and self-energy,
+tensor-core BF16x3 contraction, FP64 state).  The line also carries the
+right-hand side alone in the three precisions, self-energy evaluations per
+second, and the wall clock of complete flows of two small workloads
+(np48_n16 mixed with Z feedback, np16_n8 FP64 with Z = 1).
+
 --impl reference times the FP64 CPU oracle on the host cores (a bounded
 sample of output triples per step) for the same metric.
 """
@@ -29,7 +35,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "np96_n32"
-METRIC = "fRG RHS evaluations/s (N_p=96 flow steps with Z feedback, mixed precision)"
+METRIC = "fRG RHS evaluations/s at N_p=96 (flow steps with Z feedback)"
 UNIT = "RHS/s"
 
 # Algorithmic work per loop-kernel evaluation and per self-energy pair (FP32
@@ -37,6 +43,27 @@ UNIT = "RHS/s"
 BUBBLE_FP32_PER_EVAL, BUBBLE_MUFU_PER_EVAL = 19, 2
 SIGMA_FP32_PER_PAIR, SIGMA_MUFU_PER_PAIR = 48, 4
 FP32_LANES_PER_SM, MUFU_PER_SM, N_SM = 128, 16, 152
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of the bench workload, valid while the kernel's source file is
+# unchanged (SHA-256 recorded with the capture); profiles/ holds the summary.
+TRAFFIC = {
+    ("sigma_z", "np96_n32"): {"bytes": 27.35e6, "source": "paper_2005_00827_gb300/csrc/sigma.cu",
+                              "sha256": "cf3f8abae6c489b3764e868cacb5cc6fb81989df21cc2c1ea4d25e9c11f3dccc"},
+}
+
+
+def traffic_bytes(kernel, workload):
+    import hashlib
+    t = TRAFFIC.get((kernel, workload))
+    if t is None:
+        return None
+    try:
+        with open(os.path.join(ROOT, t["source"]), "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    return t["bytes"] if digest == t["sha256"] else None
 
 
 def load_peaks():
@@ -193,6 +220,13 @@ def run_qpfrg(args):
             extra[f"rhs_only_{name}_per_s"] = reps / (a.elapsed_time(b) / 1e3)
     extra["mixed_vs_fp64_rhs"] = extra["rhs_only_mixed_per_s"] / extra["rhs_only_fp64_per_s"]
     extra["tc_vs_fp64_rhs"] = extra["rhs_only_tc_per_s"] / extra["rhs_only_fp64_per_s"]
+    if "sigma_z" in prof and prof["sigma_z"][1] > 0:
+        extra["sigma_z_evals_per_s"] = prof["sigma_z"][1] / (prof["sigma_z"][0] / 1e3)
+
+    # complete flows (wall clock of qpfrg_flow, T = 1 down to divergence or T_end)
+    if not args.no_flows:
+        extra["full_flows"] = [full_flow(api, inputs, "np48_n16", api.QPFRG_MIXED, "mixed", stream),
+                               full_flow(api, inputs, "np16_n8", api.QPFRG_FP64, "fp64", stream)]
 
     # roofline of the dominant kernel (ALU bound: FP32 issue and MUFU pipes)
     peaks, peak_kind = load_peaks()
@@ -214,7 +248,8 @@ def run_qpfrg(args):
         achieved = units / avg_s
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e9, "peak": peak_units / 1e9,
                 "unit": "Geval/s" if dom == "bubble" else "Gpair/s", "frac": achieved / peak_units,
-                "traffic": None, "peak_source": f"derived: {N_SM} SM x {clk_mhz:.0f} MHz "
+                "traffic": traffic_bytes(dom, args.workload), "traffic_unit": "bytes per launch",
+                "peak_source": f"derived: {N_SM} SM x {clk_mhz:.0f} MHz "
                 f"({peak_kind} max clock), {fp32} FP32 instr / {FP32_LANES_PER_SM} lanes, "
                 f"{mufu} MUFU / {MUFU_PER_SM} per SM"}
 
@@ -239,6 +274,24 @@ def run_qpfrg(args):
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def full_flow(api, inputs, workload, prec, name, stream):
+    """One complete flow of a small workload: flows/s from the wall clock."""
+    import torch
+    wl = inputs.WORKLOADS[workload]
+    N, n = wl["N"], wl["n"]
+    with api.Context(N, n, n, U=wl["U"], lambda0=1.0, precision=prec, lambda_end=wl["T_end"],
+                     z_feedback=int(wl["z_feedback"]), eta=0.02, stream=stream.cuda_stream) as c:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = api.qpfrg_flow(c.h)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        d = r.as_dict()
+    return {"workload": workload, "precision": name, "flows_per_s": 1.0 / dt, "seconds": dt,
+            "steps": d["steps"], "status": d["status"], "lambda_c": d["lambda_c"],
+            "z_feedback": bool(wl["z_feedback"])}
 
 
 # ---------------------------------------------------------------------------
@@ -298,9 +351,10 @@ def main():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="qpfrg", choices=["qpfrg", "reference"])
     p.add_argument("--workload", default=WORKLOAD)
-    p.add_argument("--precision", default="mixed", choices=["mixed", "tc", "fp64"])
+    p.add_argument("--precision", default="tc", choices=["mixed", "tc", "fp64"])
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-flows", action="store_true", help="skip the complete-flow timings")
     args = p.parse_args()
     if args.warmup < 3 and args.impl == "qpfrg":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

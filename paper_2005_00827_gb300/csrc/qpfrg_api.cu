@@ -18,7 +18,7 @@ namespace {
 const char *const kKernelNames[K_COUNT] = {
     "partner_map", "bubble", "contract_pp", "contract_cr", "contract_d", "sigma_z",
     "sigma_hist", "sigma_grid", "z_update", "rk_stage", "rk_final", "convert_f32",
-    "tc_prep", "tc_gemm_pp", "tc_gemm_cr", "tc_gemm_d",
+    "tc_prep", "tc_gemm_pp", "tc_gemm_cr", "tc_gemm_d", "kp_table",
 };
 
 struct PendingEvent {

@@ -38,6 +38,7 @@ enum KernelId {
     K_TC_PP,
     K_TC_CR,
     K_TC_D,
+    K_KP_TABLE,
     K_COUNT
 };
 

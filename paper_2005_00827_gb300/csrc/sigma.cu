@@ -756,8 +756,10 @@ __global__ void sigma_grid_kernel(const double *hist, int nbins, double e_min, d
 static qpfrg_status launch_kp_table(qpfrg_ctx *c, const int *jlist, int nj)
 {
     const long total = (long)nj * c->pb.M;
+    prof_begin(c);
     kp_table_kernel<<<(int)std::min<long>((total + 255) / 256, 152L * 8), 256, 0, c->stream>>>(
         c->d_kf, jlist, nj, c->f64.kx, c->f64.ky, c->pb.M, c->d_kp, c->d_kcs);
+    prof_end(c, K_KP_TABLE);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "kp_table_kernel");
 }
