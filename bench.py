@@ -16,6 +16,10 @@ right-hand side alone in the three precisions, self-energy evaluations per
 second, and the wall clock of complete flows of two small workloads
 (np48_n16 mixed with Z feedback, np16_n8 FP64 with Z = 1).
 
+--workload sweep128 instead times the 128-flow phase-boundary sweep (N_p in
+{24, 48, 72, 96}, 16 x 16 fine grid, Z = 1) through one qpfrg_flow_batch call
+and reports complete flows/s (--flows K takes the first K draws).
+
 --impl reference times the FP64 CPU oracle on the host cores (a bounded
 sample of output triples per step) for the same metric.
 """
@@ -322,6 +326,53 @@ def cpu_baseline(workload, budget_s=15.0, nthreads=0):
                       f"(each triple sums all {N * n * n} loop points in 3 channels)"}
 
 
+def run_sweep(args):
+    """The 128-flow phase-boundary sweep (N_p in {24,48,72,96}, 16 x 16 fine
+    grid, Z = 1, seeded draws) through qpfrg_flow_batch: complete flows/s."""
+    import torch
+
+    from paper_2005_00827_gb300 import api, inputs
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    prec = {"mixed": api.QPFRG_MIXED, "tc": api.QPFRG_MIXED_TC, "fp64": api.QPFRG_FP64}[args.precision]
+    n = 16
+    specs = [(d["N"], d["U"], 1.0, d["T_end"]) for d in inputs.batch_specs(128)][:args.flows]
+    stream = torch.cuda.current_stream()
+    o = api.qpfrg_default_options()
+    o.precision = prec
+    lat, grid = api.qpfrg_lattice(1.0, 0.0, 0.0), api.qpfrg_fine_grid(n, n, 0)
+    for _ in range(args.warmup):   # one short flow per patch count
+        api.qpfrg_flow_batch(lat, grid, api.QPFRG_REG_TEMPERATURE, o,
+                             [(N, 2.0, 1.0, 0.9) for N in (24, 48, 72, 96)], stream.cuda_stream)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = api.qpfrg_flow_batch(lat, grid, api.QPFRG_REG_TEMPERATURE, o, specs, stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    value, ms = aggregate(ms, float(len(specs)), world, device="cuda")
+    steps = sum(r["steps"] for r in res)
+    status = {}
+    for r in res:
+        status[r["status"]] = status.get(r["status"], 0) + 1
+    line = {"metric": "complete fRG flows/s (phase-boundary sweep, one batched call)", "value": value,
+            "unit": "flows/s", "n_gpus": world, "steps": 1, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {api.QPFRG_MIXED: "f32+f64", api.QPFRG_MIXED_TC: "bf16x3+f32+f64"}.get(prec, "f64"),
+            "data": "synthetic (seeded parameter draws, splitmix64 seed 20050082)",
+            "config": {"workload": "sweep128", "flows": len(specs), "N_p": "24/48/72/96", "fine_grid": "16x16",
+                       "flow": "T-flow from T=1 to T_end or |V|>20, dlnT=ln0.98, Z=1",
+                       "precision": args.precision, "parallelism": "replicas"},
+            "flow_steps": steps, "rhs_per_s": 4.0 * steps / (ms / 1e3), "statuses": status, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -355,11 +406,14 @@ def main():
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-flows", action="store_true", help="skip the complete-flow timings")
+    p.add_argument("--flows", type=int, default=128, help="sweep128: number of flows (first of the draws)")
     args = p.parse_args()
     if args.warmup < 3 and args.impl == "qpfrg":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "sweep128":
+        run_sweep(args)
     else:
         run_qpfrg(args)
 

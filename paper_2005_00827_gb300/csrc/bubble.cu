@@ -11,11 +11,10 @@
 // s(a,b) = Z_a Z_b (T-flow) or g Z_a Z_b (Z_a + Z_b) (g-flow), the line
 // weights of Eq. (both_propagators_Z) / Eq. (vertex_flow_feedback_Z).
 //
-// Launch shape: one CTA per (patch a, chunk of Q, family).  The CTA keeps its
-// wedge's fine points in registers (PPT consecutive radial points per
-// thread), streams the partner-patch bytes of each Q (coalesced), merges
-// equal consecutive partners in registers and adds runs into shared-memory
-// rows of N accumulators, G transfers per barrier, double-buffered.
+// Launch shape: one CTA of 8 warps per (patch a, chunk of Q, family).  The
+// CTA stages its wedge's fine points in shared memory; each warp takes one
+// transfer at a time, streams its partner-patch bytes (coalesced) and bins
+// the loop kernels into a private row of N accumulators.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -23,8 +22,6 @@
 #include "qpfrg_internal.h"
 
 namespace qpfrg {
-
-constexpr int G = 2;   // transfers per barrier
 
 template <typename R>
 struct BubbleArgs {
@@ -54,6 +51,22 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bflo
 // ---- scalar helpers ---------------------------------------------------------
 __device__ __forceinline__ float fexp(float x) { return __expf(x); }
 __device__ __forceinline__ double fexp(double x) { return exp(x); }
+// exp(-|x|/T) from k = log2(e)/T (FP32: one multiply and ex2.approx) or k = 1/T (FP64)
+__device__ __forceinline__ float exp_mT(float x, float k)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(-fabsf(x) * k));
+    return y;
+}
+__device__ __forceinline__ double exp_mT(double x, double k) { return exp(-fabs(x) * k); }
+// a / b with one reciprocal (FP32: rcp.approx; FP64: the division)
+__device__ __forceinline__ float qdiv(float a, float b)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(b));
+    return a * r;
+}
+__device__ __forceinline__ double qdiv(double a, double b) { return a / b; }
 // typed absolute value: plain fabs() on a float would promote to FP64
 __device__ __forceinline__ float qabs(float x) { return fabsf(x); }
 __device__ __forceinline__ double qabs(double x) { return fabs(x); }
@@ -103,7 +116,7 @@ __device__ __forceinline__ R fermi_dxdT(R x, R invT)
 //   pp: -dD(x_p, -x_q)/dT = -(g_p + g_q)/(x_p + x_q)   (g odd in x)
 // Below |difference| < thr*T the analytic derivative at the midpoint is used.
 template <typename R>
-__device__ __forceinline__ R loop_T(bool pp, R xp, R gp, R xq, R invT, R thrT)
+__device__ __forceinline__ R loop_T(bool pp, R xp, R gp, R xq, R invT, R invT2, R kexp, R thrT)
 {
     const R den = pp ? xp + xq : xp - xq;
     if (qabs(den) < thrT) {
@@ -111,11 +124,11 @@ __device__ __forceinline__ R loop_T(bool pp, R xp, R gp, R xq, R invT, R thrT)
         const R v = fermi_dxdT(m, invT);
         return pp ? -v : v;
     }
-    const R e = fexp(-qabs(xq) * invT);
+    const R e = exp_mT(xq, kexp);
     const R d = R(1) + e, d2 = d * d;
-    const R gq_num = xq * invT * invT * e;           // g_q * d2
+    const R gq_num = xq * invT2 * e;                 // g_q * d2
     const R num = pp ? gp * d2 + gq_num : gp * d2 - gq_num;
-    const R v = fdiv(num, d2 * den);
+    const R v = qdiv(num, d2 * den);
     return pp ? -v : v;
 }
 
@@ -140,10 +153,47 @@ __device__ __forceinline__ R loop_g(bool pp, R xp, R fp, R fcp, R xq, R invT, R 
     return pp ? -v : v;
 }
 
+// Lane layout of a patch's fine points (local index t n_r + s, t angular,
+// s radial): a warp row holds 32 points, lanes along the radius.  With
+// n_r >= 32 a row is 32 radii of one angle (radial chunks of 32, all angles of
+// a chunk before the next chunk); with n_r < 32 it is 32 / lr angles of lr
+// radii, lr = n_r rounded up to a power of two.  Consecutive rows of a lane
+// are angular neighbours at one radius, whose partners mostly share a patch.
+struct LaneMap {
+    int lr, apr, nchunk, per_chunk;   // lanes per angle, angles per row, radial chunks, rows per chunk
+    __host__ __device__ LaneMap(int nt, int nr)
+    {
+        if (nr >= 32) {
+            lr = 32;
+            apr = 1;
+            nchunk = (nr + 31) / 32;
+        } else {
+            lr = 1;
+            while (lr < nr) lr <<= 1;
+            apr = 32 / lr;
+            nchunk = 1;
+        }
+        per_chunk = (nt + apr - 1) / apr;
+    }
+};
+
+template <typename R>
+struct alignas(4 * sizeof(R)) Quad {
+    R x, y, z, w;
+};
+
 // Kernel body for one transfer family (PP: particle-particle, else
 // particle-hole) and one regulator (TFLOW: temperature flow, else
 // interaction flow), both fixed at compile time.
-template <typename R, int PPT, bool FORM, bool PP, bool TFLOW>
+//
+// One warp per transfer Q: it walks the patch's points row by row, keeps a
+// run (partner patch, partial sum) per lane, adds a run to its private
+// shared-memory row of N accumulators when the lane's partner patch changes
+// (lanes on one radius change on different wedge boundaries, so these atomic
+// adds rarely collide), flushes the last runs through a segmented warp
+// reduction (one atomic per run of equal partners among the lanes) and writes
+// the row out.  No block barrier inside the transfer loop.
+template <typename R, bool FORM, bool PP, bool TFLOW>
 __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned char *smem_raw)
 {
     const int N = A.pb.N, P = A.pb.P, M = A.pb.M;
@@ -153,106 +203,137 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
     constexpr bool pp = PP;
     const int q0 = blockIdx.y * A.qchunk;
     const int q1 = min((long)q0 + A.qchunk, NN);
-    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
     constexpr bool tflow = TFLOW;
     const bool qp = A.pb.propagator == QPFRG_PROP_QP;
+    const int nr = A.pb.n_r, nt = A.pb.n_theta;
 
-    R *acc = reinterpret_cast<R *>(smem_raw);  // 2 x G x N
-    R *Zs = acc + 2 * G * N;                   // N
-    for (int i = tid; i < 2 * G * N; i += nthr) acc[i] = R(0);
-    for (int i = tid; i < N; i += nthr) Zs[i] = A.Z ? (R)A.Z[i] : R(1);
+    Quad<R> *pc = reinterpret_cast<Quad<R> *>(smem_raw);   // cos/sin of the point's components
+    Quad<R> *pe = pc + P;                                   // x_p, f-terms, weight
+    R *Zs = reinterpret_cast<R *>(pe + P);                  // N
+    R *rows = Zs + N;                                       // 2 nwarp x N (two transfers per warp)
+    for (int i = tid; i < N; i += blockDim.x) Zs[i] = A.Z ? (R)A.Z[i] : R(1);
+    for (int i = tid; i < 2 * nwarp * N; i += blockDim.x) rows[i] = R(0);
     __syncthreads();
     const R Za = Zs[a];
-    const R invT = A.invT, thrT = A.thr * A.T;
+    const R invT = A.invT, thrT = A.thr * A.T, invT2 = invT * invT;
+    const R kexp = sizeof(R) == 4 ? invT * R(1.4426950408889634) : invT;
     const R t = A.t, tp = A.tp, mu = A.mu;
-
-    // This thread's fine points: PPT consecutive angular points at one radius,
-    // local index (t0 + u) n_r + s with s = tid % n_r, t0 = (tid / n_r) PPT.
-    // Partners of angular neighbours are ~0.004 rad apart and mostly share a
-    // patch, so runs are long (few shared-memory atomics, which are CAS loops
-    // for floats), and the lanes of a warp sit at different radii (few
-    // conflicts).  Partner bytes of one u are contiguous across the lanes.
-    const int nr = A.pb.n_r, nt = A.pb.n_theta;
-    const int s_r = tid % nr, t0 = (tid / nr) * PPT;
-    R pcx[PPT], psx[PPT], pcy[PPT], psy[PPT], px[PPT], pw[PPT], pa[PPT], pb2[PPT];
-    bool valid[PPT];
-#pragma unroll
-    for (int u = 0; u < PPT; ++u) {
-        const int loc = (t0 + u) * nr + s_r;
-        valid[u] = t0 + u < nt;
-        const int p = a * P + (valid[u] ? loc : 0);
-        pcx[u] = A.fine.cx[p];
-        psx[u] = A.fine.sx[p];
-        pcy[u] = A.fine.cy[p];
-        psy[u] = A.fine.sy[p];
-        pw[u] = valid[u] ? A.fine.w[p] : R(0);
-        px[u] = qp ? Za * A.fine.xi[p] : A.fine.xi[p];
+    for (int i = tid; i < P; i += blockDim.x) {
+        const int p = a * P + i;
+        Quad<R> c4, e4;
+        c4.x = A.fine.cx[p];
+        c4.y = A.fine.sx[p];
+        c4.z = A.fine.cy[p];
+        c4.w = A.fine.sy[p];
+        const R x = qp ? Za * A.fine.xi[p] : A.fine.xi[p];
+        e4.x = x;
         if (tflow) {
-            pa[u] = fermi_dT(px[u], invT);
-            pb2[u] = R(0);
+            e4.y = fermi_dT(x, invT);
+            e4.z = R(0);
         } else {
-            fermi_pair(px[u], invT, pa[u], pb2[u]);
+            fermi_pair(x, invT, e4.y, e4.z);
         }
+        e4.w = A.fine.w[p];
+        pc[i] = c4;
+        pe[i] = e4;
     }
-    const bool any_valid = t0 < nt;
-    const TransferTable<R> &Qt = pp ? A.qpp : A.qph;
+    __syncthreads();
 
-    // Q's are processed in groups of G: the G x PPT partner loads are issued
-    // together, runs are added into G shared rows, one barrier per group.
-    for (int Qb = q0; Qb < q1; Qb += G) {
-        R *accb = acc + (((Qb - q0) / G) & 1) * (G * N);
-        if (any_valid) {
-            int bq[G][PPT];
-            R cQx[G], sQx[G], cQy[G], sQy[G];
+    const LaneMap lm(nt, nr);
+    const TransferTable<R> &Qt = pp ? A.qpp : A.qph;
+    const int dt = lane / lm.lr, sl = lane & (lm.lr - 1);
+    const int stride = lm.apr * nr;                    // local index step between a lane's rows
+    // Each warp carries two transfers at once (independent chains for the
+    // schedulers; one shared-memory read of a point serves both).
+    for (int Q0 = q0 + warp; Q0 < q1; Q0 += 2 * nwarp) {
+        const int nq = Q0 + nwarp < q1 ? 2 : 1;       // warp-uniform
+        R cQx[2], sQx[2], cQy[2], sQy[2];
+        const uint8_t *prow[2];
+        int run_b[2];
+        R run_v[2];
 #pragma unroll
-            for (int g = 0; g < G; ++g) {
-                const int Q = min(Qb + g, q1 - 1);
-                const uint8_t *row = A.part + ((long)fam * NN + Q) * (long)M + (long)a * P + s_r;
+        for (int h = 0; h < 2; ++h) {
+            const int Q = h < nq ? Q0 + h * nwarp : Q0;
+            cQx[h] = Qt.cx[Q];
+            sQx[h] = Qt.sx[Q];
+            cQy[h] = Qt.cy[Q];
+            sQy[h] = Qt.sy[Q];
+            prow[h] = A.part + ((long)fam * NN + Q) * (long)M + (long)a * P;
+            run_b[h] = -1;
+            run_v[h] = R(0);
+        }
+        for (int ch = 0; ch < lm.nchunk; ++ch) {
+            const int s = ch * 32 + sl;
+            // rows of this lane in the chunk: t = r apr + dt < n_theta
+            const int nrow = (s < nr && dt < nt) ? (nt - dt + lm.apr - 1) / lm.apr : 0;
+            const int li0 = dt * nr + s;
+            // partner bytes of the next four rows are loaded one group ahead
+            int bb[2][4], bn[2][4];
 #pragma unroll
-                for (int u = 0; u < PPT; ++u) bq[g][u] = valid[u] ? row[(t0 + u) * nr] : 0;
-                cQx[g] = Qt.cx[Q];
-                sQx[g] = Qt.sx[Q];
-                cQy[g] = Qt.cy[Q];
-                sQy[g] = Qt.sy[Q];
-            }
+            for (int h = 0; h < 2; ++h)
 #pragma unroll
-            for (int g = 0; g < G; ++g) {
-                if (Qb + g >= q1) break;
-                R *row = accb + g * N;
-                int run_b = -1;
-                R run_v = R(0);
+                for (int k = 0; k < 4; ++k) bb[h][k] = (k < nrow && h < nq) ? prow[h][li0 + k * stride] : 0;
+            for (int r = 0; r < lm.per_chunk; r += 4) {
+                const int li = li0 + r * stride;
 #pragma unroll
-                for (int u = 0; u < PPT; ++u) {
-                    if (!valid[u]) continue;
-                    // cos of the partner momentum components by angle addition:
-                    // pp: cos(Q - p) = cQ cp + sQ sp;  ph: cos(p + Q) = cp cQ - sp sQ
-                    const R cqx = pp ? cQx[g] * pcx[u] + sQx[g] * psx[u] : pcx[u] * cQx[g] - psx[u] * sQx[g];
-                    const R cqy = pp ? cQy[g] * pcy[u] + sQy[g] * psy[u] : pcy[u] * cQy[g] - psy[u] * sQy[g];
-                    R xq = R(-2) * t * (cqx + cqy) - R(4) * tp * cqx * cqy - mu;
-                    const int b = bq[g][u];
-                    if (qp) xq *= Zs[b];
-                    const R v = pw[u] * (tflow ? loop_T(pp, px[u], pa[u], xq, invT, thrT)
-                                               : loop_g(pp, px[u], pa[u], pb2[u], xq, invT, thrT));
-                    if (b == run_b) {
-                        run_v += v;
-                    } else {
-                        if (run_b >= 0) atomicAdd(&row[run_b], run_v);
-                        run_b = b;
-                        run_v = v;
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        bn[h][k] = (r + 4 + k < nrow && h < nq) ? prow[h][li + (4 + k) * stride] : 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (r + k >= nrow) continue;
+                    const Quad<R> c4 = pc[li + k * stride], e4 = pe[li + k * stride];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        if (h >= nq) break;
+                        // cos of the partner momentum components by angle addition:
+                        // pp: cos(Q - p) = cQ cp + sQ sp;  ph: cos(p + Q) = cp cQ - sp sQ
+                        const R cqx = pp ? cQx[h] * c4.x + sQx[h] * c4.y : c4.x * cQx[h] - c4.y * sQx[h];
+                        const R cqy = pp ? cQy[h] * c4.z + sQy[h] * c4.w : c4.z * cQy[h] - c4.w * sQy[h];
+                        R xq = R(-2) * t * (cqx + cqy) - R(4) * tp * cqx * cqy - mu;
+                        const int b = bb[h][k];
+                        if (qp) xq *= Zs[b];
+                        const R v = e4.w * (tflow ? loop_T(pp, e4.x, e4.y, xq, invT, invT2, kexp, thrT)
+                                                  : loop_g(pp, e4.x, e4.y, e4.z, xq, invT, thrT));
+                        if (b != run_b[h]) {
+                            if (run_b[h] >= 0) atomicAdd(&rows[(2 * warp + h) * N + run_b[h]], run_v[h]);
+                            run_b[h] = b;
+                            run_v[h] = v;
+                        } else {
+                            run_v[h] += v;
+                        }
                     }
                 }
-                if (run_b >= 0) atomicAdd(&row[run_b], run_v);
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) bb[h][k] = bn[h][k];
             }
         }
-        __syncthreads();
+        for (int h = 0; h < nq; ++h) {
+            R *row = rows + (2 * warp + h) * N;
+            // last runs: segmented sum over lanes with equal partner patch, one
+            // atomic per segment head
+            const int key = run_b[h];
+            const int kup = __shfl_up_sync(0xffffffffu, key, 1);
+            const bool head = lane == 0 || kup != key;
+            const unsigned heads = __ballot_sync(0xffffffffu, head);
+            const unsigned above = lane == 31 ? 0u : heads >> (lane + 1);
+            const int end = above ? lane + __ffs(above) - 1 : 31;   // last lane of this segment
+            R v = run_v[h];
 #pragma unroll
-        for (int g = 0; g < G; ++g)
-        for (int b = tid; b < N; b += nthr) {
-            const int idx = g * N + b;
-            const int Q = Qb + g;
-            const R v = accb[idx];
-            accb[idx] = R(0);
-            if (Q < q1) {
+            for (int off = 1; off < 32; off <<= 1) {
+                const R o = __shfl_down_sync(0xffffffffu, v, off);
+                if (lane + off <= end) v += o;
+            }
+            if (head && key >= 0) atomicAdd(&row[key], v);
+            __syncwarp();
+            const int Q = Q0 + h * nwarp;
+            for (int b = lane; b < N; b += 32) {
+                const R v = row[b];
+                row[b] = R(0);
                 const R Zb = Zs[b];
                 const R s = tflow ? Za * Zb : A.g * Za * Zb * (Za + Zb);
                 if constexpr (!FORM) {
@@ -260,59 +341,45 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
                 } else {
                     const float bt = (float)(v * s);
                     const long col = (long)a * N + b;
-                    __nv_bfloat16 h, l;
+                    __nv_bfloat16 hi, lo;
                     if (pp) {
-                        split_bf16(bt * A.Vf[(long)Q * N + a], h, l);
-                        A.App[0][(long)Q * NN + col] = h;
-                        A.App[1][(long)Q * NN + col] = l;
+                        split_bf16(bt * A.Vf[(long)Q * N + a], hi, lo);
+                        A.App[0][(long)Q * NN + col] = hi;
+                        A.App[1][(long)Q * NN + col] = lo;
                     } else {
                         const int x = Q / N, y = Q - (Q / N) * N;          // Q = k_F(x) - k_F(y)
                         const long rcr = (long)y * N + x;                 // cr row (j,l) = (y,x)
-                        split_bf16(bt * A.VT[rcr * N + b], h, l);
-                        A.Acr[0][rcr * NN + col] = h;
-                        A.Acr[1][rcr * NN + col] = l;
+                        split_bf16(bt * A.VT[rcr * N + b], hi, lo);
+                        A.Acr[0][rcr * NN + col] = hi;
+                        A.Acr[1][rcr * NN + col] = lo;
                         const float v_ial = A.Vf[((long)x * N + a) * N + y];
                         const float v_ail = A.Vf[((long)a * N + x) * N + y];
-                        split_bf16(bt * (2.f * v_ial - v_ail), h, l);
-                        A.Ad[0][(long)Q * 2 * NN + col] = h;
-                        A.Ad[1][(long)Q * 2 * NN + col] = l;
-                        split_bf16(-bt * v_ial, h, l);
-                        A.Ad[0][(long)Q * 2 * NN + NN + col] = h;
-                        A.Ad[1][(long)Q * 2 * NN + NN + col] = l;
+                        split_bf16(bt * (2.f * v_ial - v_ail), hi, lo);
+                        A.Ad[0][(long)Q * 2 * NN + col] = hi;
+                        A.Ad[1][(long)Q * 2 * NN + col] = lo;
+                        split_bf16(-bt * v_ial, hi, lo);
+                        A.Ad[0][(long)Q * 2 * NN + NN + col] = hi;
+                        A.Ad[1][(long)Q * 2 * NN + NN + col] = lo;
                     }
                 }
             }
+            __syncwarp();
         }
     }
 }
 
-// FP32 variants with up to 4 points per thread fit 3 CTAs of 256 threads per SM
-template <typename R, int PPT>
-struct BubbleMinBlocks {
-    static constexpr int value = (sizeof(R) == 4 && PPT <= 4) ? 3 : 1;
-};
-
-template <typename R, int PPT, bool FORM>
-__global__ void __launch_bounds__(256, BubbleMinBlocks<R, PPT>::value) bubble_kernel(BubbleArgs<R> A)
+template <typename R, bool FORM>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) bubble_kernel(BubbleArgs<R> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const bool tflow = A.pb.regulator == QPFRG_REG_TEMPERATURE;
     if (blockIdx.z == 0) {
-        if (tflow) bubble_body<R, PPT, FORM, true, true>(A, smem_raw);
-        else bubble_body<R, PPT, FORM, true, false>(A, smem_raw);
+        if (tflow) bubble_body<R, FORM, true, true>(A, smem_raw);
+        else bubble_body<R, FORM, true, false>(A, smem_raw);
     } else {
-        if (tflow) bubble_body<R, PPT, FORM, false, true>(A, smem_raw);
-        else bubble_body<R, PPT, FORM, false, false>(A, smem_raw);
+        if (tflow) bubble_body<R, FORM, false, true>(A, smem_raw);
+        else bubble_body<R, FORM, false, false>(A, smem_raw);
     }
-}
-
-template <typename R, int PPT, bool FORM>
-static void launch_t(qpfrg_ctx *c, const BubbleArgs<R> &A, int nthr, int qchunks)
-{
-    const int N = c->pb.N;
-    dim3 grid(N, qchunks, 2);
-    const size_t smem = (2 * G + 1) * (size_t)N * sizeof(R);
-    bubble_kernel<R, PPT, FORM><<<grid, nthr, smem, c->stream>>>(A);
 }
 
 template <typename R, bool FORM>
@@ -345,32 +412,23 @@ static qpfrg_status launch_r(qpfrg_ctx *c, double lambda, const double *d_Z, con
     A.tp = (R)pb.tp;
     A.mu = (R)pb.mu;
     const long NN = (long)pb.N * pb.N;
-    A.qchunk = (int)std::max(1L, std::min(64L, NN / 16));
+    // transfers per CTA: 8 per warp where the grid still fills the GPU
+    A.qchunk = (int)std::max(8L, std::min(64L, NN / 16));
     const int qchunks = div_up(NN, A.qchunk);
-
-    const int P = pb.P;
-    int ppt = (P + 255) / 256;
-    if (ppt > 8) {
-        c->err = "more than 2048 fine points per patch are not supported";
-        return QPFRG_ERR_UNSUPPORTED;
-    }
-    ppt = ppt <= 1 ? 1 : (ppt <= 2 ? 2 : (ppt <= 4 ? 4 : 8));
-    // threads: n_r radii x ceil(n_theta / PPT) angular chunks
-    int nthr = pb.n_r * ((pb.n_theta + ppt - 1) / ppt);
-    nthr = std::max(32, ((nthr + 31) / 32) * 32);
-    if (nthr > 256) {
+    const int nthr = 256;
+    const size_t smem = 2 * (size_t)pb.P * sizeof(Quad<R>) + (size_t)(1 + 2 * (nthr / 32)) * pb.N * sizeof(R);
+    if (smem > 200 * 1024) {
         c->err = "fine grid too large for the loop-kernel launch";
         return QPFRG_ERR_UNSUPPORTED;
     }
+    auto kern = bubble_kernel<R, FORM>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(c, e, "bubble smem attribute");
+    dim3 grid(pb.N, qchunks, 2);
     prof_begin(c);
-    switch (ppt) {
-    case 1: launch_t<R, 1, FORM>(c, A, nthr, qchunks); break;
-    case 2: launch_t<R, 2, FORM>(c, A, nthr, qchunks); break;
-    case 4: launch_t<R, 4, FORM>(c, A, nthr, qchunks); break;
-    default: launch_t<R, 8, FORM>(c, A, nthr, qchunks); break;
-    }
+    kern<<<grid, nthr, smem, c->stream>>>(A);
     prof_end(c, K_BUBBLE);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "bubble_kernel");
 }
 
