@@ -243,8 +243,12 @@ def run_qpfrg(args):
         if dom == "bubble":
             units = 2.0 * N * N * M
             fp32, mufu = BUBBLE_FP32_PER_EVAL, BUBBLE_MUFU_PER_EVAL
-        else:   # the flow evaluates the C4v-irreducible patches 0..N/8 only
-            units = float(N // 8 + 1) * M * M
+        else:
+            # the flow evaluates the C4v-irreducible patches 0..N/8 only, and
+            # the targets on mirror lines (0, and N/8 when 8 | N) over half of
+            # the loop points p: count the reduced work
+            mirror = (1.0 if N % 8 == 0 else 0.5) if n % 2 == 0 else 0.0
+            units = (float(N // 8 + 1) - mirror) * M * M
             fp32, mufu = SIGMA_FP32_PER_PAIR, SIGMA_MUFU_PER_PAIR
         clk_per_unit = max(fp32 / FP32_LANES_PER_SM, mufu / MUFU_PER_SM)
         peak_units = N_SM * clk_mhz * 1e6 / clk_per_unit

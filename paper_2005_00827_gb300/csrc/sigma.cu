@@ -467,6 +467,7 @@ struct SigmaFastArgs {
     double *sig;
     float t, tp, mu, eta2, invT, cT, twoT, fourT;   // cT = log2(e) / T
     float inv_dth, dth;                             // N / 2 pi, 2 pi / N
+    int mirror;     // targets are the C4v-irreducible patches and n_theta is even: halve the mirror targets
 };
 
 __device__ __forceinline__ float ex2_approx(float x)
@@ -529,14 +530,36 @@ __device__ __noinline__ int sf_slow_patch(const SigmaFastArgs &A, int jidx, int 
     return c;
 }
 
-template <bool TP0>
+// UNIB: every block of 256 SF_QPT loop points q lies in one patch b (P a
+// multiple of 256 SF_QPT), so the vertex weight is a per-patch table:
+// cz[c] = (Z_c (2 V_jab^2 - V_jab V_jac), -, -2t l_c, -mu l_c); otherwise
+// cz[c] = (Z_c, Z_c V_jac, -2t l_c, -mu l_c) and the weight is formed per pair.
+template <bool TP0, bool UNIB>
 __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
 {
-    const int N = A.pb.N, P = A.pb.P, M = A.pb.M;
+    const int N = A.pb.N, M = A.pb.M;
     const int a = blockIdx.y, jidx = blockIdx.z;
     const int j = A.jlist ? A.jlist[jidx] : jidx;
     const int tid = threadIdx.x;
     const bool qp = A.pb.propagator == QPFRG_PROP_QP;
+    // A target on a mirror line of the zone (theta_j = 0 or pi/4) has a sum
+    // symmetric under that mirror: keep the patches a on one side of it with
+    // weight 2 and half of each patch the mirror maps onto itself.
+    int fac = 1, P = A.pb.P;
+    if (A.mirror) {
+        int ma = -1;
+        if (j == 0) ma = (N - a) % N;
+        else if (8 * j == N) ma = ((N / 4 - a) % N + N) % N;
+        if (ma == a) {
+            fac = 2;
+            P = A.pb.P / 2;     // angular index t < n_theta / 2
+        } else if (ma >= 0) {
+            const int rel = j == 0 ? a : ((a - N / 8) % N + N) % N;
+            fac = (rel > 0 && 2 * rel < N) ? 2 : 0;
+        }
+    }
+    if (fac == 0) return;       // the mirror patch carries this one (uniform over the CTA)
+    const int PP = A.pb.P;      // points per patch (record and loop-point indexing)
     const int pch = P < SF_PCH ? P : SF_PCH;
     const SfSmem L = sf_smem_layout(pch);
 
@@ -556,21 +579,29 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
         for (int i = tid; i < n16; i += blockDim.x) dst[i] = src[i];
     }
     const double *Vja = A.V + ((long)j * N + a) * N;
-    for (int i = tid; i < SF_SLOTS; i += blockDim.x) {
-        if (i <= N) {
-            const int cc = i == N ? 0 : i;
-            const float Zc = A.Z ? (float)A.Z[cc] : 1.f;
-            const float lz = qp ? Zc : 1.f;
-            cz[i] = make_float4(Zc, Zc * (float)Vja[cc], -2.f * A.t * lz, -A.mu * lz);
-            cd[i] = -4.f * A.tp * lz;
-            const float4 b = A.bnd[cc];
-            ray[i] = make_float2(b.x, b.z);
-        } else {
-            cz[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            cd[i] = 0.f;
-            ray[i] = make_float2(0.f, 0.f);
+    // per-patch slots; with UNIB the weight column is filled per q block (b)
+    auto fill_slots = [&](int b) {
+        const float vb = UNIB ? (float)Vja[b] : 0.f;
+        for (int i = tid; i < SF_SLOTS; i += blockDim.x) {
+            if (i <= N) {
+                const int cc = i == N ? 0 : i;
+                const float Zc = A.Z ? (float)A.Z[cc] : 1.f;
+                const float lz = qp ? Zc : 1.f;
+                const float vc = (float)Vja[cc];
+                cz[i] = UNIB ? make_float4(Zc * (2.f * vb * vb - vb * vc), 0.f, -2.f * A.t * lz, -A.mu * lz)
+                             : make_float4(Zc, Zc * vc, -2.f * A.t * lz, -A.mu * lz);
+                cd[i] = -4.f * A.tp * lz;
+                const float4 bd = A.bnd[cc];
+                ray[i] = make_float2(bd.x, bd.z);
+            } else {
+                cz[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                cd[i] = 0.f;
+                ray[i] = make_float2(0.f, 0.f);
+            }
         }
-    }
+    };
+    int b_slots = UNIB ? (blockIdx.x * SF_QB * 256 * SF_QPT) / PP : 0;
+    fill_slots(b_slots);
     const float Za = A.Z ? (float)A.Z[a] : 1.f;
     const float lza = qp ? Za : 1.f;
     const float4 kcs = A.kcs[jidx];
@@ -581,7 +612,7 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
     // records of the loop points p0 .. p0 + cnt - 1 of patch a
     auto stage = [&](int p0, int cnt) {
         for (int i = tid; i < cnt; i += blockDim.x) {
-            const int p = a * P + p0 + i;
+            const int p = a * PP + p0 + i;
             const float4 k4 = A.kp[(long)jidx * M + p];
             const float cpx = A.fine.cx[p], spx = A.fine.sx[p], cpy = A.fine.cy[p], spy = A.fine.sy[p];
             const float xp = lza * A.fine.xi[p];
@@ -602,6 +633,12 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
     for (int qb = 0; qb < SF_QB; ++qb) {
         const int blk = blockIdx.x * SF_QB + qb;
         if (blk * (256 * SF_QPT) >= M) break;   // uniform over the CTA
+        if (UNIB && blk * (256 * SF_QPT) / PP != b_slots) {
+            b_slots = blk * (256 * SF_QPT) / PP;
+            __syncthreads();   // every warp is done with the previous weights
+            fill_slots(b_slots);
+            __syncthreads();
+        }
         // the SF_QPT loop points q of this thread (an index past M gets weight 0)
         float qx[SF_QPT], qy[SF_QPT], cqx[SF_QPT], sqx[SF_QPT], cqy[SF_QPT], sqy[SF_QPT];
         float fqp[SF_QPT], fcqp[SF_QPT], v2[SF_QPT], vab[SF_QPT], mxq[SF_QPT], acc[SF_QPT];
@@ -611,8 +648,8 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
             const int iq = blk * (256 * SF_QPT) + k * 256 + tid;   // angular-minor index
             const bool valid = iq < M;
             const int ii = valid ? iq : M - 1;
-            const int b = ii / P, rem = ii - b * P;
-            const int qq = b * P + (rem % A.pb.n_theta) * A.pb.n_r + rem / A.pb.n_theta;
+            const int b = ii / PP, rem = ii - b * PP;
+            const int qq = b * PP + (rem % A.pb.n_theta) * A.pb.n_r + rem / A.pb.n_theta;
             qi[k] = qq;
             const float Zb = A.Z ? (float)A.Z[b] : 1.f;
             qx[k] = A.fine.kx[qq];
@@ -672,7 +709,7 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
                     for (int k = 0; k < SF_QPT; ++k)
                         if (slow_mask & (1u << k)) {
                             const bool edge = fmaxf(fabsf(x[k]), fabsf(y[k])) > 3.14159265f - 4e-6f;
-                            c[k] = sf_slow_patch(A, jidx, j, a * P + p0 + i, qi[k], x[k], y[k], edge, A.bnd);
+                            c[k] = sf_slow_patch(A, jidx, j, a * PP + p0 + i, qi[k], x[k], y[k], edge, A.bnd);
                         }
                 }
 #pragma unroll
@@ -685,7 +722,7 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
                     const float fr = rcp_approx(1.f + ex2_approx(xr * A.cT));
                     const float Aq = rb.z * fcqp[k], Bq = rb.w * fqp[k];
                     const float F = fmaf(fr, Bq - Aq, Aq);
-                    const float amp = fmaf(-vab[k], z.y, z.x * v2[k]) * F;
+                    const float amp = UNIB ? z.x * F : fmaf(-vab[k], z.y, z.x * v2[k]) * F;
                     // d+- = xi_j +- 2T - E with E = x_q + x_r - x_p
                     const float dp = (upp + mxq[k]) - xr;
                     const float dm = dp - A.fourT;
@@ -698,6 +735,7 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
 #pragma unroll
         for (int k = 0; k < SF_QPT; ++k) vsum += (double)acc[k];
     }
+    vsum *= fac;
     __shared__ double red[32];
     double v = vsum;
 #pragma unroll
@@ -818,7 +856,10 @@ static qpfrg_status launch_sigma_fast(qpfrg_ctx *c, double T, const double *d_V,
     A.dth = (float)(kTwoPi / c->pb.N);
     const int pch = c->pb.P < SF_PCH ? c->pb.P : SF_PCH;
     const size_t smem = sf_smem_layout(pch).total;
-    auto kern = c->pb.tp == 0.0 ? sigma_fast_kernel<true> : sigma_fast_kernel<false>;
+    A.mirror = (jlist != nullptr && c->pb.n_theta % 2 == 0) ? 1 : 0;
+    const bool unib = c->pb.P % (256 * SF_QPT) == 0;
+    auto kern = c->pb.tp == 0.0 ? (unib ? sigma_fast_kernel<true, true> : sigma_fast_kernel<true, false>)
+                                : (unib ? sigma_fast_kernel<false, true> : sigma_fast_kernel<false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(c, e, "sigma_fast smem attribute");
     dim3 grid(div_up(div_up(c->pb.M, 256 * SF_QPT), SF_QB), c->pb.N, nj);
