@@ -13,8 +13,9 @@ no dataset.  All device inputs (partner maps, bubble tables) exceed L2.
 The default precision is QPFRG_MIXED_TC (FP32 loop kernels and self-energy,
 tensor-core BF16x3 contraction, FP64 state).  The line also carries the
 right-hand side alone in the three precisions, self-energy evaluations per
-second, and the wall clock of complete flows of two small workloads
-(np48_n16 mixed with Z feedback, np16_n8 FP64 with Z = 1).
+second, and the wall clock of complete flows: the bench workload itself
+(full flows/s at N_p = 96) and two small ones (np48_n16 mixed with Z
+feedback, np16_n8 FP64 with Z = 1).
 
 --workload sweep128 instead times the 128-flow phase-boundary sweep (N_p in
 {24, 48, 72, 96}, 16 x 16 fine grid, Z = 1) through one qpfrg_flow_batch call
@@ -167,6 +168,8 @@ def run_qpfrg(args):
         if world > 1:
             torch.distributed.barrier()
 
+    # launch shapes measured on this context's own state (untimed)
+    tuning = api.qpfrg_autotune(ctx.h, 1.0) if not args.no_autotune else None
     for _ in range(args.warmup):
         api.qpfrg_step(ctx.h, 1)
     barrier()
@@ -213,6 +216,8 @@ def run_qpfrg(args):
     forms = (("mixed", api.QPFRG_MIXED, 10), ("tc", api.QPFRG_MIXED_TC, 10), ("fp64", api.QPFRG_FP64, 3))
     for name, pr, reps in forms:
         with api.Context(N, n, n, U=U, precision=pr, stream=stream.cuda_stream) as c2:
+            if tuning is not None:
+                api.qpfrg_set_tuning(c2.h, tuning["bubble_qchunk"], tuning["sigma_qblocks"], tuning["tc_splits"])
             api.qpfrg_rhs(c2.h, 0.1, dV_t, Z_t, out)
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -269,28 +274,34 @@ def run_qpfrg(args):
         "config": {"workload": args.workload, "N_p": N, "fine_grid": f"{n}x{n}", "U": U,
                    "flow": "T-flow from T=1, dlnT=ln0.98, Z feedback, eta=0.02",
                    "precision": args.precision, "l2": "inputs larger than L2 (partner maps "
-                   f"{2 * N * N * M / 1e9:.2f} GB, bubble tables)", "parallelism": "replicas"},
+                   f"{2 * N * N * M / 1e9:.2f} GB, bubble tables)", "parallelism": "replicas",
+                   "tuning": tuning},
         "e2e": e2e, "gpu_launches": int(sum(v[1] for v in prof.values())),
         "kernels_ms": {k: round(v[0], 3) for k, v in kern.items()},
         "kernel_launches": {k: v[1] for k, v in kern.items()},
         "roofline": roof, "clocks": clk, **extra,
     }
+    ctx.close()
+    if not args.no_flows:
+        # a complete flow of the bench workload itself (fresh context, same shapes)
+        line["full_flows"].insert(0, full_flow(api, inputs, args.workload, prec, args.precision, stream, tuning))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_seconds)
-    ctx.close()
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def full_flow(api, inputs, workload, prec, name, stream):
-    """One complete flow of a small workload: flows/s from the wall clock."""
+def full_flow(api, inputs, workload, prec, name, stream, tuning=None):
+    """One complete flow (T = 1 to divergence or T_end): flows/s from the wall clock."""
     import torch
     wl = inputs.WORKLOADS[workload]
     N, n = wl["N"], wl["n"]
     with api.Context(N, n, n, U=wl["U"], lambda0=1.0, precision=prec, lambda_end=wl["T_end"],
                      z_feedback=int(wl["z_feedback"]), eta=0.02, stream=stream.cuda_stream) as c:
+        if tuning is not None:
+            api.qpfrg_set_tuning(c.h, tuning["bubble_qchunk"], tuning["sigma_qblocks"], tuning["tc_splits"])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         r = api.qpfrg_flow(c.h)
@@ -345,6 +356,7 @@ def run_sweep(args):
     stream = torch.cuda.current_stream()
     o = api.qpfrg_default_options()
     o.precision = prec
+    o.autotune = 0 if args.no_autotune else 1     # shapes per patch-count group
     lat, grid = api.qpfrg_lattice(1.0, 0.0, 0.0), api.qpfrg_fine_grid(n, n, 0)
     for _ in range(args.warmup):   # one short flow per patch count
         api.qpfrg_flow_batch(lat, grid, api.QPFRG_REG_TEMPERATURE, o,
@@ -370,6 +382,7 @@ def run_sweep(args):
             "dtype": {api.QPFRG_MIXED: "f32+f64", api.QPFRG_MIXED_TC: "bf16x3+f32+f64"}.get(prec, "f64"),
             "data": "synthetic (seeded parameter draws, splitmix64 seed 20050082)",
             "config": {"workload": "sweep128", "flows": len(specs), "N_p": "24/48/72/96", "fine_grid": "16x16",
+                       "autotune": not args.no_autotune,
                        "flow": "T-flow from T=1 to T_end or |V|>20, dlnT=ln0.98, Z=1",
                        "precision": args.precision, "parallelism": "replicas"},
             "flow_steps": steps, "rhs_per_s": 4.0 * steps / (ms / 1e3), "statuses": status, "clocks": clk}
@@ -411,6 +424,7 @@ def main():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-flows", action="store_true", help="skip the complete-flow timings")
     p.add_argument("--flows", type=int, default=128, help="sweep128: number of flows (first of the draws)")
+    p.add_argument("--no-autotune", action="store_true", help="built-in launch shapes instead of qpfrg_autotune")
     args = p.parse_args()
     if args.warmup < 3 and args.impl == "qpfrg":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

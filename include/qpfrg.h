@@ -115,6 +115,8 @@ typedef struct {
     int max_steps;               /* bound on flow steps per qpfrg_flow call            */
     double T_fixed;              /* temperature of the interaction flow                */
     double timeout_s;            /* wall-clock budget of one qpfrg_flow call (<=0: none) */
+    int autotune;                /* qpfrg_flow_batch: nonzero tunes the launch shapes of
+                                    each patch-count group (qpfrg_autotune) before stepping */
 } qpfrg_options;
 
 typedef struct {
@@ -237,6 +239,39 @@ qpfrg_status qpfrg_profile_reset(qpfrg_t ctx);
 int          qpfrg_profile_count(void);
 const char  *qpfrg_profile_name(int id);
 qpfrg_status qpfrg_profile_get(qpfrg_t ctx, int id, double *ms, long long *launches);
+
+/* Launch shapes of the hot kernels; 0 in a field selects the built-in
+ * heuristic.  The paper has no counterpart: these are GPU schedule choices.
+ *   bubble_qchunk:  transfers per loop-kernel CTA (a CTA's eight warps take
+ *                   them two at a time);
+ *   sigma_qblocks:  blocks of 512 loop points q per self-energy CTA (the CTA
+ *                   stages its tables once for all of them), at most 64;
+ *   tc_splits[3]:   split-K factors of the pp, cr and d tensor-core
+ *                   contractions, clipped to the number of 64-wide k blocks;
+ *   ms_bubble, ms_sigma, ms_contract: fastest times found by qpfrg_autotune
+ *                   (outputs; ignored by qpfrg_set_tuning). */
+typedef struct {
+    int bubble_qchunk;
+    int sigma_qblocks;
+    int tc_splits[3];
+    double ms_bubble, ms_sigma, ms_contract;
+} qpfrg_tuning;
+
+/* Project-written autotuner: times candidate launch shapes on the context's
+ * own state at Lambda = lambda -- the loop kernels (transfers per CTA), the
+ * tensor-core contraction of each channel (split-K; QPFRG_MIXED_TC), the FP32
+ * self-energy of the wedge grid (q blocks per CTA) -- one untimed and one
+ * timed launch each with CUDA events on the context's stream, keeps the
+ * fastest in the context and reports them in *out (may be NULL).  The call
+ * waits for its work.  It writes only scratch buffers (bubble tables or formed
+ * operands, the RK stage buffer, the Z work buffer), never the flow state, and
+ * the profiler does not count its launches.  QPFRG_ERR_INVALID for a bad
+ * lambda (as qpfrg_rhs). */
+qpfrg_status qpfrg_autotune(qpfrg_t ctx, double lambda, qpfrg_tuning *out);
+
+/* Apply launch shapes (e.g. those qpfrg_autotune found on another context of
+ * the same size).  QPFRG_ERR_INVALID for a negative field or sigma_qblocks > 64. */
+qpfrg_status qpfrg_set_tuning(qpfrg_t ctx, const qpfrg_tuning *t);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free Z evaluation.  The paper has no counterpart: this entry

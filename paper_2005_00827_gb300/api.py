@@ -31,7 +31,7 @@ EXPORTS = (
     "qpfrg_flow", "qpfrg_state_size", "qpfrg_get_state", "qpfrg_set_state", "qpfrg_read_state",
     "qpfrg_geometry", "qpfrg_set_profiling", "qpfrg_profile_reset", "qpfrg_profile_count",
     "qpfrg_profile_name", "qpfrg_profile_get", "qpfrg_last_error", "qpfrg_version", "qpfrg_destroy",
-    "qpfrg_zfactor_static", "qpfrg_flow_batch",
+    "qpfrg_zfactor_static", "qpfrg_flow_batch", "qpfrg_autotune", "qpfrg_set_tuning",
 )
 
 
@@ -54,7 +54,18 @@ class qpfrg_options(C.Structure):
                 ("precision", C.c_int), ("eta", C.c_double), ("n_omega", C.c_int),
                 ("omega_min", C.c_double), ("omega_max", C.c_double), ("stop_abs_v", C.c_double),
                 ("step", C.c_double), ("lambda_end", C.c_double), ("z_max", C.c_double),
-                ("max_steps", C.c_int), ("T_fixed", C.c_double), ("timeout_s", C.c_double)]
+                ("max_steps", C.c_int), ("T_fixed", C.c_double), ("timeout_s", C.c_double),
+                ("autotune", C.c_int)]
+
+
+class qpfrg_tuning(C.Structure):
+    _fields_ = [("bubble_qchunk", C.c_int), ("sigma_qblocks", C.c_int), ("tc_splits", C.c_int * 3),
+                ("ms_bubble", C.c_double), ("ms_sigma", C.c_double), ("ms_contract", C.c_double)]
+
+    def as_dict(self):
+        return dict(bubble_qchunk=self.bubble_qchunk, sigma_qblocks=self.sigma_qblocks,
+                    tc_splits=list(self.tc_splits), ms_bubble=self.ms_bubble, ms_sigma=self.ms_sigma,
+                    ms_contract=self.ms_contract)
 
 
 class qpfrg_flow_result(C.Structure):
@@ -109,6 +120,8 @@ def load(build_if_missing: bool = True):
     L.qpfrg_profile_name.argtypes = [C.c_int]
     L.qpfrg_profile_name.restype = C.c_char_p
     L.qpfrg_profile_get.argtypes = [_P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+    L.qpfrg_autotune.argtypes = [_P, C.c_double, C.POINTER(qpfrg_tuning)]
+    L.qpfrg_set_tuning.argtypes = [_P, C.POINTER(qpfrg_tuning)]
     L.qpfrg_last_error.argtypes = [_P]
     L.qpfrg_last_error.restype = C.c_char_p
     L.qpfrg_version.restype = C.c_char_p
@@ -123,7 +136,8 @@ def load(build_if_missing: bool = True):
     L.qpfrg_destroy.restype = None
     for name in ("qpfrg_create", "qpfrg_rhs", "qpfrg_selfenergy", "qpfrg_step", "qpfrg_flow",
                  "qpfrg_state_size", "qpfrg_get_state", "qpfrg_set_state", "qpfrg_read_state",
-                 "qpfrg_geometry", "qpfrg_set_profiling", "qpfrg_profile_reset", "qpfrg_profile_get"):
+                 "qpfrg_geometry", "qpfrg_set_profiling", "qpfrg_profile_reset", "qpfrg_profile_get",
+                 "qpfrg_autotune", "qpfrg_set_tuning"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -233,6 +247,21 @@ def qpfrg_set_profiling(ctx, on: bool):
 
 def qpfrg_profile_reset(ctx):
     _check(ctx, load().qpfrg_profile_reset(ctx))
+
+
+def qpfrg_autotune(ctx, lam: float) -> dict:
+    """Measure and keep the fastest launch shapes at Lambda = lam."""
+    t = qpfrg_tuning()
+    _check(ctx, load().qpfrg_autotune(ctx, float(lam), C.byref(t)))
+    return t.as_dict()
+
+
+def qpfrg_set_tuning(ctx, bubble_qchunk=0, sigma_qblocks=0, tc_splits=(0, 0, 0)):
+    t = qpfrg_tuning()
+    t.bubble_qchunk, t.sigma_qblocks = int(bubble_qchunk), int(sigma_qblocks)
+    for i in range(3):
+        t.tc_splits[i] = int(tc_splits[i])
+    _check(ctx, load().qpfrg_set_tuning(ctx, C.byref(t)))
 
 
 def qpfrg_profile(ctx) -> dict:

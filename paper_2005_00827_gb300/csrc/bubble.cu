@@ -413,7 +413,8 @@ static qpfrg_status launch_r(qpfrg_ctx *c, double lambda, const double *d_Z, con
     A.mu = (R)pb.mu;
     const long NN = (long)pb.N * pb.N;
     // transfers per CTA: 8 per warp where the grid still fills the GPU
-    A.qchunk = (int)std::max(8L, std::min(64L, NN / 16));
+    A.qchunk = c->tune.bubble_qchunk > 0 ? (int)std::min<long>(c->tune.bubble_qchunk, NN)
+                                         : (int)std::max(8L, std::min(64L, NN / 16));
     const int qchunks = div_up(NN, A.qchunk);
     const int nthr = 256;
     const size_t smem = 2 * (size_t)pb.P * sizeof(Quad<R>) + (size_t)(1 + 2 * (nthr / 32)) * pb.N * sizeof(R);

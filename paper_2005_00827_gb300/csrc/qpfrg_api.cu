@@ -721,6 +721,8 @@ qpfrg_status qpfrg_flow_batch(const qpfrg_lattice *lattice, const qpfrg_fine_gri
         while (specs[first].n_p != sizes[g]) ++first;
         st = qpfrg_create(lattice, sizes[g], grid, specs[first].U, specs[first].lambda0, regulator, &opt,
                           streams[g], &parents[g]);
+        // launch shapes of the group, measured on its first flow's initial state
+        if (st == QPFRG_OK && opt.autotune) st = qpfrg_autotune(parents[g], specs[first].lambda0, nullptr);
     }
     for (int i = 0; i < n_flows && st == QPFRG_OK; ++i) {
         group_of[i] = (int)(std::find(sizes.begin(), sizes.end(), specs[i].n_p) - sizes.begin());

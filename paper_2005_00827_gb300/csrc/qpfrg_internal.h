@@ -42,6 +42,13 @@ enum KernelId {
     K_COUNT
 };
 
+// Launch shapes chosen by qpfrg_autotune (0 = built-in heuristic).
+struct Tuning {
+    int bubble_qchunk = 0;      // transfers per loop-kernel CTA
+    int sigma_qblocks = 0;      // blocks of 512 loop points q per self-energy CTA
+    int tc_splits[3] = {0, 0, 0};   // split-K factors of the pp, cr, d contractions
+};
+
 // Problem constants that every kernel needs, passed by value.
 struct Problem {
     int N;           // patches
@@ -156,6 +163,7 @@ struct qpfrg_ctx {
 
     // profiling
     bool prof = false;
+    qpfrg::Tuning tune;          // launch shapes (qpfrg_autotune / qpfrg_set_tuning)
     qpfrg::ProfileSlot slots[qpfrg::K_COUNT];
     void *profiler = nullptr;    // pending CUDA-event pairs (qpfrg_api.cu)
 

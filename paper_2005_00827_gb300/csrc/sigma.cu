@@ -449,10 +449,10 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
 //   one radius (angular-minor order), so their r lie on a short arc and their
 //   table cells, rays and patch slots mostly coincide (few bank conflicts,
 //   rare divergence into the guarded paths).
-// Launch: grid (ceil(M / (256 SF_QPT SF_QB)), N patches a, targets), 256 threads,
+// Launch: grid (ceil(M / (256 SF_QPT qb)), N patches a, targets), 256 threads,
 // two CTAs per SM.
 constexpr int SF_QPT = 2;
-constexpr int SF_QB = 4;        // blocks of 256 SF_QPT loop points q per CTA
+constexpr int SF_QB = 4;        // default blocks of 256 SF_QPT loop points q per CTA
 constexpr int SF_PCH = 1024;    // loop points p staged per pass
 constexpr int SF_SLOTS = 257;   // per-patch slots: c in 0..N (c = N is patch 0 again), padded to 257
 
@@ -468,6 +468,7 @@ struct SigmaFastArgs {
     float t, tp, mu, eta2, invT, cT, twoT, fourT;   // cT = log2(e) / T
     float inv_dth, dth;                             // N / 2 pi, 2 pi / N
     int mirror;     // targets are the C4v-irreducible patches and n_theta is even: halve the mirror targets
+    int qb;         // blocks of 256 SF_QPT loop points q per CTA
 };
 
 __device__ __forceinline__ float ex2_approx(float x)
@@ -600,7 +601,7 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
             }
         }
     };
-    int b_slots = UNIB ? (blockIdx.x * SF_QB * 256 * SF_QPT) / PP : 0;
+    int b_slots = UNIB ? (blockIdx.x * A.qb * 256 * SF_QPT) / PP : 0;
     fill_slots(b_slots);
     const float Za = A.Z ? (float)A.Z[a] : 1.f;
     const float lza = qp ? Za : 1.f;
@@ -629,9 +630,9 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
     __syncthreads();   // tables (and the records of a single pass) written
 
     double vsum = 0.0;
-    // SF_QB blocks of 256 SF_QPT loop points q per CTA reuse the staged tables
-    for (int qb = 0; qb < SF_QB; ++qb) {
-        const int blk = blockIdx.x * SF_QB + qb;
+    // A.qb blocks of 256 SF_QPT loop points q per CTA reuse the staged tables
+    for (int qb = 0; qb < A.qb; ++qb) {
+        const int blk = blockIdx.x * A.qb + qb;
         if (blk * (256 * SF_QPT) >= M) break;   // uniform over the CTA
         if (UNIB && blk * (256 * SF_QPT) / PP != b_slots) {
             b_slots = blk * (256 * SF_QPT) / PP;
@@ -862,7 +863,8 @@ static qpfrg_status launch_sigma_fast(qpfrg_ctx *c, double T, const double *d_V,
                                 : (unib ? sigma_fast_kernel<false, true> : sigma_fast_kernel<false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(c, e, "sigma_fast smem attribute");
-    dim3 grid(div_up(div_up(c->pb.M, 256 * SF_QPT), SF_QB), c->pb.N, nj);
+    A.qb = c->tune.sigma_qblocks > 0 ? c->tune.sigma_qblocks : SF_QB;
+    dim3 grid(div_up(div_up(c->pb.M, 256 * SF_QPT), A.qb), c->pb.N, nj);
     prof_begin(c);
     kern<<<grid, 256, smem, c->stream>>>(A);
     prof_end(c, K_SIGMA_Z);

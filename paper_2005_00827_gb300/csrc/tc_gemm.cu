@@ -364,6 +364,8 @@ qpfrg_status launch_tc_gemm(qpfrg_ctx *c, const __nv_bfloat16 *Ahi, const __nv_b
             splits = sp;
         }
     }
+    const int ch = kid == K_TC_PP ? 0 : (kid == K_TC_CR ? 1 : 2);
+    if (c->tune.tc_splits[ch] > 0) splits = std::min(c->tune.tc_splits[ch], nkb);
     const int kb_per = div_up(nkb, splits);
     splits = div_up(nkb, kb_per);
     TcGemmArgs A{Ahi, Alo, Bhi, Blo, M, K, Ncol, Npad, kb_per, map_mode, c->pb.N, out, scale, c->d_tc_err};
