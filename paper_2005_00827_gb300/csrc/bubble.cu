@@ -40,6 +40,7 @@ struct BubbleArgs {
     __nv_bfloat16 *App[2];      // [N^2][N^2]   hi, lo: B_pp[Q][a][b] V[Q][a]
     __nv_bfloat16 *Acr[2];      // [N^2][N^2]   row (j,l) of Q = (l,j): B_ph[Q][a][b] V[b][j][l]
     __nv_bfloat16 *Ad[2];       // [N^2][2N^2]  B_ph[Q][a][b] (2V[i,a,l] - V[a,i,l]) | -B_ph V[i,a,l]
+    long Kp, Kpd;               // reduction lengths of the tile layout (tile_index)
 };
 
 __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo)
@@ -344,22 +345,26 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
                     __nv_bfloat16 hi, lo;
                     if (pp) {
                         split_bf16(bt * A.Vf[(long)Q * N + a], hi, lo);
-                        A.App[0][(long)Q * NN + col] = hi;
-                        A.App[1][(long)Q * NN + col] = lo;
+                        const long o = tile_index(Q, col, 128, A.Kp);
+                        A.App[0][o] = hi;
+                        A.App[1][o] = lo;
                     } else {
                         const int x = Q / N, y = Q - (Q / N) * N;          // Q = k_F(x) - k_F(y)
                         const long rcr = (long)y * N + x;                 // cr row (j,l) = (y,x)
                         split_bf16(bt * A.VT[rcr * N + b], hi, lo);
-                        A.Acr[0][rcr * NN + col] = hi;
-                        A.Acr[1][rcr * NN + col] = lo;
+                        const long ocr = tile_index(rcr, col, 128, A.Kp);
+                        A.Acr[0][ocr] = hi;
+                        A.Acr[1][ocr] = lo;
                         const float v_ial = A.Vf[((long)x * N + a) * N + y];
                         const float v_ail = A.Vf[((long)a * N + x) * N + y];
                         split_bf16(bt * (2.f * v_ial - v_ail), hi, lo);
-                        A.Ad[0][(long)Q * 2 * NN + col] = hi;
-                        A.Ad[1][(long)Q * 2 * NN + col] = lo;
+                        const long od = tile_index(Q, col, 128, A.Kpd);
+                        A.Ad[0][od] = hi;
+                        A.Ad[1][od] = lo;
                         split_bf16(-bt * v_ial, hi, lo);
-                        A.Ad[0][(long)Q * 2 * NN + NN + col] = hi;
-                        A.Ad[1][(long)Q * 2 * NN + NN + col] = lo;
+                        const long od2 = tile_index(Q, NN + col, 128, A.Kpd);
+                        A.Ad[0][od2] = hi;
+                        A.Ad[1][od2] = lo;
                     }
                 }
             }
@@ -397,6 +402,8 @@ static qpfrg_status launch_r(qpfrg_ctx *c, double lambda, const double *d_Z, con
     A.B = reinterpret_cast<R *>(c->d_B);
     A.Vf = c->d_Vf;
     A.VT = c->tc.VT;
+    A.Kp = c->tc.Kp;
+    A.Kpd = c->tc.Kpd;
     for (int h = 0; h < 2; ++h) {
         A.App[h] = c->tc.App[h];
         A.Acr[h] = c->tc.Acr[h];

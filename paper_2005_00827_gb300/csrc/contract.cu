@@ -174,19 +174,12 @@ qpfrg_status launch_contractions(qpfrg_ctx *c, const void *d_Vin, double scale, 
 {
     if (c->opt.precision == QPFRG_MIXED_TC) {
         // formed operands were written by the bubble kernel of this stage
-        const int N = c->pb.N, NN = N * N, Np = c->tc.Npad;
+        const int N = c->pb.N, NN = N * N;
         const unsigned ch = c->pb.channels;
-        const TcBuffers &t = c->tc;
         qpfrg_status s = QPFRG_OK;
-        if ((ch & QPFRG_CH_PP) &&
-            (s = launch_tc_gemm(c, t.App[0], t.App[1], t.Bpp[0], t.Bpp[1], NN, NN, N, Np, 0, -scale, d_out, K_TC_PP)))
-            return s;
-        if ((ch & QPFRG_CH_CR) &&
-            (s = launch_tc_gemm(c, t.Acr[0], t.Acr[1], t.Bcr[0], t.Bcr[1], NN, NN, N, Np, 1, -scale, d_out, K_TC_CR)))
-            return s;
-        if ((ch & QPFRG_CH_D) &&
-            (s = launch_tc_gemm(c, t.Ad[0], t.Ad[1], t.Bd[0], t.Bd[1], NN, 2 * NN, N, Np, 2, scale, d_out, K_TC_D)))
-            return s;
+        if ((ch & QPFRG_CH_PP) && (s = launch_tc_gemm(c, 0, NN, -scale, d_out, K_TC_PP))) return s;
+        if ((ch & QPFRG_CH_CR) && (s = launch_tc_gemm(c, 1, NN, -scale, d_out, K_TC_CR))) return s;
+        if ((ch & QPFRG_CH_D) && (s = launch_tc_gemm(c, 2, NN, scale, d_out, K_TC_D))) return s;
         return QPFRG_OK;
     }
     if (c->opt.precision == QPFRG_FP64)

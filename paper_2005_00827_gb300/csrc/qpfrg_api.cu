@@ -358,16 +358,31 @@ qpfrg_status qpfrg_create(const qpfrg_lattice *lattice, int n_p, const qpfrg_fin
         TcBuffers &t = c->tc;
         t.Npad = (int)((N + 15) / 16 * 16);
         const size_t NN = N * N, Np = t.Npad;
+        t.Mp = (long)((NN + 127) / 128 * 128);
+        t.Kp = (long)((NN + 63) / 64 * 64);
+        t.Kpd = (long)((2 * NN + 63) / 64 * 64);
+        const size_t na = (size_t)t.Mp * t.Kp, nad = (size_t)t.Mp * t.Kpd;
+        const size_t nb = Np * (size_t)t.Kp, nbd = Np * (size_t)t.Kpd;
         for (int h = 0; h < 2; ++h)
-            if ((s = dev_alloc(c, &t.App[h], NN * NN, "formed pp table")) ||
-                (s = dev_alloc(c, &t.Acr[h], NN * NN, "formed cr table")) ||
-                (s = dev_alloc(c, &t.Ad[h], 2 * NN * NN, "formed d table")) ||
-                (s = dev_alloc(c, &t.Bpp[h], Np * NN, "pp operand")) ||
-                (s = dev_alloc(c, &t.Bcr[h], Np * NN, "cr operand")) || (s = dev_alloc(c, &t.Bd[h], 2 * Np * NN, "d operand")))
+            if ((s = dev_alloc(c, &t.App[h], na, "formed pp table")) ||
+                (s = dev_alloc(c, &t.Acr[h], na, "formed cr table")) ||
+                (s = dev_alloc(c, &t.Ad[h], nad, "formed d table")) ||
+                (s = dev_alloc(c, &t.Bpp[h], nb, "pp operand")) ||
+                (s = dev_alloc(c, &t.Bcr[h], nb, "cr operand")) || (s = dev_alloc(c, &t.Bd[h], nbd, "d operand")))
                 return fail(s);
         if ((s = dev_alloc(c, &t.VT, n3, "V transpose")) || (s = dev_alloc(c, &c->d_tc_err, 1, "tc error flag")))
             return fail(s);
-        cudaMemset(c->d_tc_err, 0, sizeof(unsigned));
+        // tile pads (rows past N^2, k past the reduction length) stay zero
+        for (int h = 0; h < 2 && e == cudaSuccess; ++h) {
+            if ((e = cudaMemset(t.App[h], 0, na * 2)) != cudaSuccess || (e = cudaMemset(t.Acr[h], 0, na * 2)) != cudaSuccess ||
+                (e = cudaMemset(t.Ad[h], 0, nad * 2)) != cudaSuccess || (e = cudaMemset(t.Bpp[h], 0, nb * 2)) != cudaSuccess ||
+                (e = cudaMemset(t.Bcr[h], 0, nb * 2)) != cudaSuccess)
+                break;
+            e = cudaMemset(t.Bd[h], 0, nbd * 2);
+        }
+        if (e == cudaSuccess) e = cudaMemset(c->d_tc_err, 0, sizeof(unsigned));
+        if (e != cudaSuccess) return fail(cuda_fail(c, e, "clear tensor-core operands"));
+        if ((s = tc_make_maps(c)) != QPFRG_OK) return fail(s);
     }
     if ((s = dev_alloc(c, &c->d_V, n3, "V")) || (s = dev_alloc(c, &c->d_Vs, n3, "V stage")) ||
         (s = dev_alloc(c, &c->d_k, n3, "k")) || (s = dev_alloc(c, &c->d_acc, n3, "acc")) ||

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -81,16 +82,34 @@ struct TransferTable {   // for Q index x*N + y (pp: k_F(x)+k_F(y); ph: k_F(x)-k
 };
 
 // Buffers of the tensor-core contraction (QPFRG_MIXED_TC), index 0 = hi, 1 = lo.
+// Every operand is stored in tensor-core tiles (tile_index): A operands in
+// 128-row x 64-wide tiles, rows padded to Mp, reduction length to Kp / Kpd;
+// B operands in Npad-row x 64-wide tiles.  Pads are zero.
 struct TcBuffers {
-    __nv_bfloat16 *App[2] = {nullptr, nullptr};   // [N^2][N^2]
-    __nv_bfloat16 *Acr[2] = {nullptr, nullptr};   // [N^2][N^2]
-    __nv_bfloat16 *Ad[2] = {nullptr, nullptr};    // [N^2][2N^2]
-    __nv_bfloat16 *Bpp[2] = {nullptr, nullptr};   // [Npad][N^2]
-    __nv_bfloat16 *Bcr[2] = {nullptr, nullptr};   // [Npad][N^2]
-    __nv_bfloat16 *Bd[2] = {nullptr, nullptr};    // [Npad][2N^2]
+    __nv_bfloat16 *App[2] = {nullptr, nullptr};   // [Mp][Kp]   rows (i,j), k = (a,b)
+    __nv_bfloat16 *Acr[2] = {nullptr, nullptr};   // [Mp][Kp]
+    __nv_bfloat16 *Ad[2] = {nullptr, nullptr};    // [Mp][Kpd]
+    __nv_bfloat16 *Bpp[2] = {nullptr, nullptr};   // [Npad][Kp]
+    __nv_bfloat16 *Bcr[2] = {nullptr, nullptr};   // [Npad][Kp]
+    __nv_bfloat16 *Bd[2] = {nullptr, nullptr};    // [Npad][Kpd]
     float *VT = nullptr;                          // [N][N][N]
     int Npad = 0;
+    long Mp = 0, Kp = 0, Kpd = 0;                 // N^2 up to 128; N^2 and 2 N^2 up to 64
+    CUtensorMap tmA[3][2], tmB[3][2];             // TMA maps of the tiles: [pp, cr, d][hi, lo]
 };
+
+// Element offset of (row r, reduction index k) in the tile layout of an
+// operand with `rows` rows per tile (128 for A, Npad for B) and reduction
+// length Kp (a multiple of 64): tiles ordered (row tile, k tile), each tile
+// in the canonical K-major no-swizzle order of the tcgen05 descriptors (core
+// matrices of 8 rows x 8 elements; K-adjacent core matrices rows/8 apart).
+__host__ __device__ inline long tile_index(long r, long k, int rows, long Kp)
+{
+    const long rt = r / rows, rr = r - rt * rows;
+    const long kt = k >> 6, kk = k & 63;
+    return (rt * (Kp >> 6) + kt) * (long)rows * 64 + ((((kk >> 3) * (rows >> 3) + (rr >> 3)) << 6) | ((rr & 7) << 3) |
+                                                      (kk & 7));
+}
 
 struct ProfileSlot {
     double ms = 0.0;
@@ -191,9 +210,8 @@ qpfrg_status launch_sigma_grid(qpfrg_ctx *c, double T, const double *d_V, const 
 
 // tc_gemm.cu / tc_prep: tensor-core contraction
 qpfrg_status launch_tc_prep(qpfrg_ctx *c);
-qpfrg_status launch_tc_gemm(qpfrg_ctx *c, const __nv_bfloat16 *Ahi, const __nv_bfloat16 *Alo,
-                            const __nv_bfloat16 *Bhi, const __nv_bfloat16 *Blo, int M, int K, int Ncol,
-                            int Npad, int map_mode, double scale, double *out, int kid);
+qpfrg_status tc_make_maps(qpfrg_ctx *c);   // TMA maps of the tensor-core operand tiles
+qpfrg_status launch_tc_gemm(qpfrg_ctx *c, int ch, int M, double scale, double *out, int kid);
 
 // ode.cu
 qpfrg_status launch_convert_f32(qpfrg_ctx *c, const double *d_in, float *d_out, long n);

@@ -11,15 +11,18 @@
 // a 128-row tile for all N columns over a slice of K (split-K, partial sums
 // added to the FP64 output with atomics).
 //
-// Data path per 64-wide k-block: 128 threads copy the four BF16 tiles with
-// cp.async (16-byte chunks) straight into the canonical K-major, no-swizzle
-// layout of the tensor-core descriptors (core matrices of 8 rows x 16 bytes),
-// a stage ring of S buffers; one elected thread issues 4 K16 slices x 3
-// products of tcgen05.mma (M = 128, N = Npad) and commits them to the stage's
-// mbarrier, which gates the reuse of that buffer.  Waits on mbarriers are
-// bounded: on expiry the CTA raises an error flag, drains its copies, frees
-// its tensor memory and returns.
+// Data path per 64-wide k-block: the operands are stored in tensor-core tiles
+// (tile_index: 128 x 64 for A, Npad x 64 for B, each in the canonical K-major
+// no-swizzle order of the descriptors), so one thread loads a stage with four
+// TMA tile copies (cp.async.bulk.tensor, 2-D maps over the tiled buffers)
+// signalled on the stage's "full" mbarrier (expect-tx bytes), issues 4 K16
+// slices x 3 products of tcgen05.mma (M = 128, N = Npad) and commits them to
+// the stage's "empty" mbarrier; the stage of k-block i-1 is refilled with
+// k-block i-1+S behind the MMAs of k-block i, a ring of S stages.  Waits are
+// bounded: on expiry the CTA raises an error flag, waits (bounded) for the
+// copies and MMAs it issued, frees its tensor memory and returns.
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -108,6 +111,22 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar)
                  : "memory");
 }
 
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// 2-D TMA tile copy global -> shared, completion counted on mbar in bytes;
+// the inner coordinate x is 0 (16-byte aligned by construction)
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 {
     uint32_t r[16];
@@ -124,10 +143,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 }  // namespace tc
 
 struct TcGemmArgs {
-    const __nv_bfloat16 *Ahi, *Alo;   // [M][K]
-    const __nv_bfloat16 *Bhi, *Blo;   // [Npad][K] (rows >= Ncol are zero)
-    int M, K, Ncol, Npad;
-    int kb_per_split;                 // k-blocks of 64 per CTA along grid.y
+    int M, Ncol, Npad;                // valid rows, valid columns, padded columns
+    int nkb_total, kb_per_split;      // 64-wide k blocks of the (padded) reduction; per CTA along grid.y
     int map_mode, N;                  // output index map: 0 pp, 1 cr, 2 d
     double *out;
     double scale;
@@ -135,19 +152,20 @@ struct TcGemmArgs {
 };
 
 template <int S>
-__global__ void __launch_bounds__(tc::NTHR, 1) tc_gemm_kernel(TcGemmArgs A)
+__global__ void __launch_bounds__(tc::NTHR, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
+                   const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo, TcGemmArgs A)
 {
     using namespace tc;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ uint64_t mbar[4];
+    __shared__ uint64_t full[S], empty[S];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int m0 = blockIdx.x * BM;
-    const int nkb_total = (A.K + BK - 1) / BK;
+    const int mt = blockIdx.x, m0 = mt * BM;
     const int kb0 = blockIdx.y * A.kb_per_split;
-    const int kb1 = min(nkb_total, kb0 + A.kb_per_split);
+    const int kb1 = min(A.nkb_total, kb0 + A.kb_per_split);
     const int nkb = kb1 - kb0;
     const int Npad = A.Npad;
     const uint32_t a_bytes = BM * BK * 2, b_bytes = (uint32_t)Npad * BK * 2;
@@ -156,7 +174,10 @@ __global__ void __launch_bounds__(tc::NTHR, 1) tc_gemm_kernel(TcGemmArgs A)
     const uint32_t tmem_cols = Npad <= 32 ? 32 : (Npad <= 64 ? 64 : (Npad <= 128 ? 128 : 256));
 
     if (tid == 0) {
-        for (int s = 0; s < S; ++s) tc::mbar_init(smem_u32(&mbar[s]), 1);
+        for (int s = 0; s < S; ++s) {
+            tc::mbar_init(smem_u32(&full[s]), 1);
+            tc::mbar_init(smem_u32(&empty[s]), 1);
+        }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
@@ -171,49 +192,30 @@ __global__ void __launch_bounds__(tc::NTHR, 1) tc_gemm_kernel(TcGemmArgs A)
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = tmem_slot;
 
-    // copy one k-block into stage s: tiles A_hi, A_lo (BM x 64), B_hi, B_lo (Npad x 64)
-    auto load_stage = [&](int kb, int s) {
-        const uint32_t sb = base + (uint32_t)s * stage_bytes;
-        const int k0 = kb * BK;
-        // A: BM rows x 8 chunks of 16 B, two tables
-        for (int c = tid; c < BM * 8; c += NTHR) {
-            const int r = c >> 3, kc = c & 7;
-            const int row = m0 + r, k = k0 + kc * 8;
-            const bool ok = row < A.M && k < A.K;
-            const long off = ok ? (long)row * A.K + k : 0;
-            const uint32_t so = (uint32_t)((kc * (BM / 8) + (r >> 3)) * 128 + (r & 7) * 16);
-            tc::cp_async16(sb + so, A.Ahi + off, ok ? 16 : 0);
-            tc::cp_async16(sb + a_bytes + so, A.Alo + off, ok ? 16 : 0);
-        }
-        for (int c = tid; c < Npad * 8; c += NTHR) {
-            const int r = c >> 3, kc = c & 7;
-            const int k = k0 + kc * 8;
-            const bool ok = k < A.K;
-            const long off = ok ? (long)r * A.K + k : 0;
-            const uint32_t so = (uint32_t)((kc * (Npad / 8) + (r >> 3)) * 128 + (r & 7) * 16);
-            tc::cp_async16(sb + 2 * a_bytes + so, A.Bhi + off, ok ? 16 : 0);
-            tc::cp_async16(sb + 2 * a_bytes + b_bytes + so, A.Blo + off, ok ? 16 : 0);
-        }
-    };
-
-    const uint32_t idesc = tc::make_idesc(BM, Npad);
-    // prologue: k-blocks 0 .. S-2 in flight
-    for (int s = 0; s < S - 1; ++s) {
-        if (s < nkb) load_stage(kb0 + s, s);
-        tc::cp_async_commit();
-    }
-    bool ok_run = true;
-    for (int i = 0; i < nkb; ++i) {
-        tc::cp_async_wait<S - 2>();   // the copies of k-block i have landed
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-        if (abort_flag) {
-            ok_run = false;
-            break;
-        }
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const uint32_t sb = base + (uint32_t)(i % S) * stage_bytes;
+    if (tid == 0 && nkb > 0) {
+        // k block kb (global index) into stage s: A tile (mt, kb) = 64 rows of
+        // the 128-wide 2-D view from row (mt nkb_total + kb) 64; B tile kb =
+        // Npad/2 rows from row kb Npad/2
+        auto issue = [&](int kb, int s) {
+            const uint32_t sb = base + (uint32_t)s * stage_bytes, fb = smem_u32(&full[s]);
+            tc::mbar_expect_tx(fb, stage_bytes);
+            const int ya = (mt * A.nkb_total + kb) * 64, yb = kb * (Npad / 2);
+            tc::tma_load_2d(sb, &mAhi, 0, ya, fb);
+            tc::tma_load_2d(sb + a_bytes, &mAlo, 0, ya, fb);
+            tc::tma_load_2d(sb + 2 * a_bytes, &mBhi, 0, yb, fb);
+            tc::tma_load_2d(sb + 2 * a_bytes + b_bytes, &mBlo, 0, yb, fb);
+        };
+        const uint32_t idesc = tc::make_idesc(BM, Npad);
+        int issued = 0, consumed = 0;   // k blocks copied / multiplied
+        for (; issued < S && issued < nkb; ++issued) issue(kb0 + issued, issued);
+        bool ok = true;
+        for (int i = 0; i < nkb && ok; ++i) {
+            const int s = i % S;
+            if (!tc::mbar_wait_bounded(smem_u32(&full[s]), (uint32_t)((i / S) & 1))) {
+                ok = false;
+                break;
+            }
+            const uint32_t sb = base + (uint32_t)s * stage_bytes;
 #pragma unroll
             for (int ks = 0; ks < BK / 16; ++ks) {
                 // K16 slice: core matrices 2ks, 2ks+1 along K
@@ -228,31 +230,64 @@ __global__ void __launch_bounds__(tc::NTHR, 1) tc_gemm_kernel(TcGemmArgs A)
                 tc::mma_bf16(tmem, ahi, blo, idesc, 1u);
                 tc::mma_bf16(tmem, alo, bhi, idesc, 1u);
             }
-            tc::mma_commit(smem_u32(&mbar[i % S]));
+            tc::mma_commit(smem_u32(&empty[s]));
+            consumed = i + 1;
+            // refill the stage of k block i-1 once its products are done (the
+            // products of k block i are already queued behind them)
+            if (i >= 1 && issued < nkb) {
+                const int j = i - 1;
+                if (!tc::mbar_wait_bounded(smem_u32(&empty[j % S]), (uint32_t)((j / S) & 1))) {
+                    ok = false;
+                    break;
+                }
+                issue(kb0 + issued, issued % S);
+                ++issued;
+            }
         }
-        // refill the buffer of k-block i-1 with k-block i+S-1 once its MMAs are done
-        const int nxt = i + S - 1;
-        if (nxt < nkb) {
-            if (i >= 1 && !tc::mbar_wait_bounded(smem_u32(&mbar[(i - 1) % S]), (uint32_t)(((i - 1) / S) & 1)))
-                atomicExch(&abort_flag, 1);
-            else
-                load_stage(kb0 + nxt, nxt % S);
+        if (ok) {
+            // all products done before the accumulators are read
+            const int last = nkb - 1;
+            ok = tc::mbar_wait_bounded(smem_u32(&empty[last % S]), (uint32_t)((last / S) & 1));
+        } else {
+            // drain: every copy issued lands and every product committed ends
+            // (bounded waits) before the CTA frees its memory
+            for (int j = consumed; j < issued; ++j)
+                tc::mbar_wait_bounded(smem_u32(&full[j % S]), (uint32_t)((j / S) & 1));
+            if (consumed > 0)
+                tc::mbar_wait_bounded(smem_u32(&empty[(consumed - 1) % S]), (uint32_t)(((consumed - 1) / S) & 1));
         }
-        tc::cp_async_commit();
-    }
-    tc::cp_async_wait<0>();
-    // wait for the last commit before reading the accumulators
-    if (tid == 0 && nkb > 0) {
-        const int last = nkb - 1;
-        if (!tc::mbar_wait_bounded(smem_u32(&mbar[last % S]), (uint32_t)((last / S) & 1))) atomicExch(&abort_flag, 1);
+        if (!ok) abort_flag = 1;
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    if (!ok_run || abort_flag) {
+    if (abort_flag) {
         if (tid == 0) atomicOr(A.err, 1u);
+    } else if (nkb > 0 && A.map_mode == 0) {
+        // pp output index m N + n is contiguous in n: the tile goes through
+        // shared memory (the stage buffers are free) so that consecutive lanes
+        // add to consecutive outputs.  Row stride Npad + 1 floats avoids bank
+        // conflicts between the rows of one warp.
+        float *tile = reinterpret_cast<float *>(smem_raw);
+        const int ld = Npad + 1;
+        const int r = warp * 32 + (tid & 31);
+        for (int c0 = 0; c0 < Npad; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) tile[r * ld + c0 + q] = v[q];
+        }
+        __syncthreads();
+        const int lane = tid & 31;
+        for (int rr = warp; rr < BM; rr += NTHR / 32) {
+            const int m = m0 + rr;
+            if (m >= A.M) break;
+            for (int n = lane; n < A.Ncol; n += 32)
+                atomicAdd(&A.out[(long)m * A.N + n], A.scale * (double)tile[rr * ld + n]);
+        }
     } else if (nkb > 0) {
-        // epilogue: warp w owns accumulator rows 32w .. 32w+31 (TMEM lanes)
+        // epilogue: warp w owns accumulator rows 32w .. 32w+31 (TMEM lanes);
+        // cr and d outputs are contiguous in the row index m
         const int r = warp * 32 + (tid & 31);
         const int m = m0 + r;
         const int N = A.N;
@@ -280,14 +315,25 @@ __global__ void __launch_bounds__(tc::NTHR, 1) tc_gemm_kernel(TcGemmArgs A)
 }
 
 // Per-stage B operands of the three channel GEMMs from the FP32 stage vertex,
-// K-major [n][k] with k = (a, b) = a N + b, split into BF16 hi/lo, rows
-// n >= N zero:  pp: V[a,b,n];  cr: V[n,a,b];  d: V[b,n,a] (k < N^2) and
-// V[n,b,a] (k >= N^2);  plus VT[j][l][b] = V[b][j][l] for the cr factor.
-__global__ void tc_prep_kernel(const float *__restrict__ V, int N, int Npad, TcBuffers t)
+// rows n (n >= N zero) by reduction index k = (a, b) = a N + b, split into
+// BF16 hi/lo and stored in tiles (tile_index, Npad rows per tile):
+// pp: V[a,b,n];  cr: V[n,a,b];  d: V[b,n,a] (k < N^2) and V[n,b,a]
+// (k >= N^2);  plus VT[j][l][b] = V[b][j][l] for the cr factor.
+struct TcPrepArgs {
+    const float *V;
+    int N, Npad;
+    long Kp, Kpd;
+    __nv_bfloat16 *Bpp[2], *Bcr[2], *Bd[2];
+    float *VT;
+};
+
+__global__ void tc_prep_kernel(TcPrepArgs t)
 {
+    const int N = t.N, Npad = t.Npad;
     const long NN = (long)N * N, n3 = NN * N;
     const long s_pp = (long)Npad * NN, s_d = 2 * s_pp;
     const long total = 2 * s_pp + s_d + n3;
+    const float *V = t.V;
     for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
         if (idx < 2 * s_pp + s_d) {
             int which;
@@ -309,9 +355,10 @@ __global__ void tc_prep_kernel(const float *__restrict__ V, int N, int Npad, TcB
             }
             const __nv_bfloat16 hi = __float2bfloat16_rn(v);
             const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-            __nv_bfloat16 **dst = which == 0 ? t.Bpp : (which == 1 ? t.Bcr : t.Bd);
-            dst[0][loc] = hi;
-            dst[1][loc] = lo;
+            __nv_bfloat16 *const *dst = which == 0 ? t.Bpp : (which == 1 ? t.Bcr : t.Bd);
+            const long o = tile_index(n, k, Npad, which == 2 ? t.Kpd : t.Kp);
+            dst[0][o] = hi;
+            dst[1][o] = lo;
         } else {
             const long o = idx - (2 * s_pp + s_d);     // o = (j N + l) N + b
             const int b = (int)(o % N), jl = (int)(o / N);
@@ -326,36 +373,99 @@ qpfrg_status launch_tc_prep(qpfrg_ctx *c)
     const long NN = (long)N * N;
     const long total = 4 * (long)c->tc.Npad * NN + NN * N;
     int blocks = (int)std::min<long>((total + 255) / 256, 152L * 16);
+    TcPrepArgs t;
+    t.V = c->d_Vf;
+    t.N = N;
+    t.Npad = c->tc.Npad;
+    t.Kp = c->tc.Kp;
+    t.Kpd = c->tc.Kpd;
+    for (int h = 0; h < 2; ++h) {
+        t.Bpp[h] = c->tc.Bpp[h];
+        t.Bcr[h] = c->tc.Bcr[h];
+        t.Bd[h] = c->tc.Bd[h];
+    }
+    t.VT = c->tc.VT;
     prof_begin(c);
-    tc_prep_kernel<<<blocks, 256, 0, c->stream>>>(c->d_Vf, N, c->tc.Npad, c->tc);
+    tc_prep_kernel<<<blocks, 256, 0, c->stream>>>(t);
     prof_end(c, K_TC_PREP);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "tc_prep_kernel");
 }
 
-// Host launcher: D (channel map_mode) += scale * A B^T.
-qpfrg_status launch_tc_gemm(qpfrg_ctx *c, const __nv_bfloat16 *Ahi, const __nv_bfloat16 *Alo,
-                            const __nv_bfloat16 *Bhi, const __nv_bfloat16 *Blo, int M, int K, int Ncol, int Npad,
-                            int map_mode, double scale, double *out, int kid)
+// 2-D TMA map over a tiled BF16 buffer of `elems` elements viewed as rows of
+// 128 elements (256 B): boxes of 128 x box_rows elements are whole tiles.
+static qpfrg_status make_tile_map(qpfrg_ctx *c, CUtensorMap *map, const void *base, long elems, int box_rows)
 {
-    // stage ring of 3 buffers, 2 when the B tiles are wide
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn) {
+            cudaGetLastError();
+            c->err = "cuTensorMapEncodeTiled is not available";
+            return QPFRG_ERR_CUDA;
+        }
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[2] = {128, (cuuint64_t)(elems / 128)};
+    const cuuint64_t strides[1] = {256};
+    const cuuint32_t box[2] = {128, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box,
+                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        c->err = "cuTensorMapEncodeTiled failed for a tensor-core operand";
+        return QPFRG_ERR_CUDA;
+    }
+    return QPFRG_OK;
+}
+
+qpfrg_status tc_make_maps(qpfrg_ctx *c)
+{
+    TcBuffers &t = c->tc;
+    const long na = t.Mp * t.Kp, nad = t.Mp * t.Kpd, nb = (long)t.Npad * t.Kp, nbd = (long)t.Npad * t.Kpd;
+    qpfrg_status s = QPFRG_OK;
+    for (int h = 0; h < 2 && s == QPFRG_OK; ++h) {
+        if ((s = make_tile_map(c, &t.tmA[0][h], t.App[h], na, 64)) ||
+            (s = make_tile_map(c, &t.tmA[1][h], t.Acr[h], na, 64)) ||
+            (s = make_tile_map(c, &t.tmA[2][h], t.Ad[h], nad, 64)) ||
+            (s = make_tile_map(c, &t.tmB[0][h], t.Bpp[h], nb, t.Npad / 2)) ||
+            (s = make_tile_map(c, &t.tmB[1][h], t.Bcr[h], nb, t.Npad / 2)))
+            break;
+        s = make_tile_map(c, &t.tmB[2][h], t.Bd[h], nbd, t.Npad / 2);
+    }
+    return s;
+}
+
+// Host launcher of channel ch (0 pp, 1 cr, 2 d): D += scale * A B^T over the
+// tiled operands, M valid rows, K valid reduction length.
+qpfrg_status launch_tc_gemm(qpfrg_ctx *c, int ch, int M, double scale, double *out, int kid)
+{
+    const TcBuffers &t = c->tc;
+    const int Npad = t.Npad;
+    const long Kp = ch == 2 ? t.Kpd : t.Kp;
+    // stage ring: as many stages of A and B tiles as fit (at most 4)
     const size_t stage_bytes = 2 * (size_t)tc::BM * tc::BK * 2 + 2 * (size_t)Npad * tc::BK * 2;
-    const int S = 3 * stage_bytes <= 200 * 1024 ? 3 : 2;
-    const size_t smem = S * stage_bytes;
-    if (Npad % 16 != 0 || Npad > 256 || K % 8 != 0 || smem > 200 * 1024) {
+    const size_t smem_max = 226 * 1024;       // leaves room for the static barriers (1 KB aligned)
+    int S = (int)std::min<size_t>(4, smem_max / stage_bytes);
+    if (Npad % 16 != 0 || Npad > 256 || S < 2) {
         c->err = "tensor-core contraction: unsupported shape";
         return QPFRG_ERR_UNSUPPORTED;
     }
-    auto kern = S == 3 ? tc_gemm_kernel<3> : tc_gemm_kernel<2>;
+    const size_t smem = S * stage_bytes;
+    auto kern = S == 4 ? tc_gemm_kernel<4> : (S == 3 ? tc_gemm_kernel<3> : tc_gemm_kernel<2>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(c, e, "tc_gemm smem attribute");
     const int mtiles = div_up(M, tc::BM);
-    const int nkb = div_up(K, tc::BK);
+    const int nkb = (int)(Kp / tc::BK);
     // split K so that the grid fills whole waves of the 152 SMs (one CTA per
-    // SM): the split count whose waves are fullest, at least 8 k-blocks each
+    // SM): the split count whose waves are fullest, at least 4 k-blocks each
     int splits = 1;
     double best = -1.0;
-    for (int sp = 1; sp <= std::max(1, nkb / 8) && sp <= 16; ++sp) {
+    for (int sp = 1; sp <= std::max(1, nkb / 4) && sp <= 16; ++sp) {
         const int ctas = mtiles * sp;
         const double waves = (double)ctas / 152.0, fill = waves / std::ceil(waves);
         const double score = fill - 0.02 * std::ceil(waves);   // prefer fewer waves at equal fill
@@ -364,13 +474,13 @@ qpfrg_status launch_tc_gemm(qpfrg_ctx *c, const __nv_bfloat16 *Ahi, const __nv_b
             splits = sp;
         }
     }
-    const int ch = kid == K_TC_PP ? 0 : (kid == K_TC_CR ? 1 : 2);
     if (c->tune.tc_splits[ch] > 0) splits = std::min(c->tune.tc_splits[ch], nkb);
     const int kb_per = div_up(nkb, splits);
     splits = div_up(nkb, kb_per);
-    TcGemmArgs A{Ahi, Alo, Bhi, Blo, M, K, Ncol, Npad, kb_per, map_mode, c->pb.N, out, scale, c->d_tc_err};
+    TcGemmArgs A{M, c->pb.N, Npad, nkb, kb_per, ch, c->pb.N, out, scale, c->d_tc_err};
     prof_begin(c);
-    kern<<<dim3(mtiles, splits), tc::NTHR, smem, c->stream>>>(A);
+    kern<<<dim3(mtiles, splits), tc::NTHR, smem, c->stream>>>(t.tmA[ch][0], t.tmA[ch][1], t.tmB[ch][0],
+                                                            t.tmB[ch][1], A);
     prof_end(c, kid);
     e = cudaGetLastError();
     return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "tc_gemm_kernel");
