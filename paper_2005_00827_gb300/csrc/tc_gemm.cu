@@ -263,31 +263,11 @@ __global__ void __launch_bounds__(tc::NTHR, 1)
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (abort_flag) {
         if (tid == 0) atomicOr(A.err, 1u);
-    } else if (nkb > 0 && A.map_mode == 0) {
-        // pp output index m N + n is contiguous in n: the tile goes through
-        // shared memory (the stage buffers are free) so that consecutive lanes
-        // add to consecutive outputs.  Row stride Npad + 1 floats avoids bank
-        // conflicts between the rows of one warp.
-        float *tile = reinterpret_cast<float *>(smem_raw);
-        const int ld = Npad + 1;
-        const int r = warp * 32 + (tid & 31);
-        for (int c0 = 0; c0 < Npad; c0 += 16) {
-            float v[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-#pragma unroll
-            for (int q = 0; q < 16; ++q) tile[r * ld + c0 + q] = v[q];
-        }
-        __syncthreads();
-        const int lane = tid & 31;
-        for (int rr = warp; rr < BM; rr += NTHR / 32) {
-            const int m = m0 + rr;
-            if (m >= A.M) break;
-            for (int n = lane; n < A.Ncol; n += 32)
-                atomicAdd(&A.out[(long)m * A.N + n], A.scale * (double)tile[rr * ld + n]);
-        }
     } else if (nkb > 0) {
-        // epilogue: warp w owns accumulator rows 32w .. 32w+31 (TMEM lanes);
-        // cr and d outputs are contiguous in the row index m
+        // epilogue: warp w owns accumulator rows 32w .. 32w+31 (TMEM lanes).
+        // The lanes of a pp store add to outputs N apart: spread over many L2
+        // slices, which the FP64 atomics need more than contiguity (a
+        // transposed, contiguous pp epilogue measured slower)
         const int r = warp * 32 + (tid & 31);
         const int m = m0 + r;
         const int N = A.N;
