@@ -194,7 +194,7 @@ struct alignas(4 * sizeof(R)) Quad {
 // adds rarely collide), flushes the last runs through a segmented warp
 // reduction (one atomic per run of equal partners among the lanes) and writes
 // the row out.  No block barrier inside the transfer loop.
-template <typename R, bool FORM, bool PP, bool TFLOW>
+template <typename R, bool FORM, bool PP, bool TFLOW, bool TP0>
 __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned char *smem_raw)
 {
     const int N = A.pb.N, P = A.pb.P, M = A.pb.M;
@@ -293,7 +293,8 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
                         // pp: cos(Q - p) = cQ cp + sQ sp;  ph: cos(p + Q) = cp cQ - sp sQ
                         const R cqx = pp ? cQx[h] * c4.x + sQx[h] * c4.y : c4.x * cQx[h] - c4.y * sQx[h];
                         const R cqy = pp ? cQy[h] * c4.z + sQy[h] * c4.w : c4.z * cQy[h] - c4.w * sQy[h];
-                        R xq = R(-2) * t * (cqx + cqy) - R(4) * tp * cqx * cqy - mu;
+                        // t' = 0 (the nested lattice): the product term drops at compile time
+                        R xq = TP0 ? R(-2) * t * (cqx + cqy) - mu : R(-2) * t * (cqx + cqy) - R(4) * tp * cqx * cqy - mu;
                         const int b = bb[h][k];
                         if (qp) xq *= Zs[b];
                         const R v = e4.w * (tflow ? loop_T(pp, e4.x, e4.y, xq, invT, invT2, kexp, thrT)
@@ -373,17 +374,17 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
     }
 }
 
-template <typename R, bool FORM>
+template <typename R, bool FORM, bool TP0>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) bubble_kernel(BubbleArgs<R> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const bool tflow = A.pb.regulator == QPFRG_REG_TEMPERATURE;
     if (blockIdx.z == 0) {
-        if (tflow) bubble_body<R, FORM, true, true>(A, smem_raw);
-        else bubble_body<R, FORM, true, false>(A, smem_raw);
+        if (tflow) bubble_body<R, FORM, true, true, TP0>(A, smem_raw);
+        else bubble_body<R, FORM, true, false, TP0>(A, smem_raw);
     } else {
-        if (tflow) bubble_body<R, FORM, false, true>(A, smem_raw);
-        else bubble_body<R, FORM, false, false>(A, smem_raw);
+        if (tflow) bubble_body<R, FORM, false, true, TP0>(A, smem_raw);
+        else bubble_body<R, FORM, false, false, TP0>(A, smem_raw);
     }
 }
 
@@ -429,7 +430,7 @@ static qpfrg_status launch_r(qpfrg_ctx *c, double lambda, const double *d_Z, con
         c->err = "fine grid too large for the loop-kernel launch";
         return QPFRG_ERR_UNSUPPORTED;
     }
-    auto kern = bubble_kernel<R, FORM>;
+    auto kern = pb.tp == 0.0 ? bubble_kernel<R, FORM, true> : bubble_kernel<R, FORM, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(c, e, "bubble smem attribute");
     dim3 grid(pb.N, qchunks, 2);

@@ -62,6 +62,20 @@ def test_rhs_matches_oracle(case, prec):
     assert normwise(got, ref) < TOL[prec]
 
 
+@pytest.mark.parametrize("prec", [api.QPFRG_FP64, api.QPFRG_MIXED, api.QPFRG_MIXED_TC])
+def test_rhs_matches_oracle_next_nearest_hopping(prec):
+    """t' = -0.2, mu = -0.3 (no nesting): the general line energy of the loop
+    kernels (the t' = 0 lattice takes a compile-time specialisation)."""
+    N, nt, nr, lam = 16, 4, 4, 0.3
+    o = Oracle(N, nt, nr, tp=-0.2, mu=-0.3)
+    V = inputs.random_vertex(N, 2.0, seed=21, c4v=True)
+    Z = inputs.z_profile(N, "aniso")
+    ref = o.rhs(lam, V, Z)
+    with api.Context(N, nt, nr, U=2.0, tp=-0.2, mu=-0.3, precision=prec) as ctx:
+        got = gpu_rhs(ctx, lam, V, Z)
+    assert normwise(got, ref) < (1e-10 if prec == api.QPFRG_FP64 else 1e-4)
+
+
 def test_geometry_matches_oracle():
     o = Oracle(48, 16, 16)
     kf, fk, fw, fp = o.geometry()
