@@ -161,7 +161,8 @@ def run_qpfrg(args):
     prec = {"mixed": api.QPFRG_MIXED, "tc": api.QPFRG_MIXED_TC, "fp64": api.QPFRG_FP64}[args.precision]
     stream = torch.cuda.current_stream()
     ctx = api.Context(N, n, n, U=U, lambda0=1.0, precision=prec, lambda_end=wl["T_end"],
-                      z_feedback=int(wl["z_feedback"]), eta=0.02, stream=stream.cuda_stream)
+                      z_feedback=int(wl["z_feedback"]), eta=0.02, n_omega=wl["n_omega"], omega_min=-4.0,
+                      omega_max=4.0, stream=stream.cuda_stream)
 
     def barrier():
         torch.cuda.synchronize()
@@ -205,6 +206,26 @@ def run_qpfrg(args):
     e2e_s = time.perf_counter() - t0
     e2e = {"value": 4.0 * args.steps * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": nbytes}
+
+    # Sigma(k_F, omega) on the workload's frequency grid from the flow's state
+    # (one untimed and one timed call; CUDA events on the context's stream)
+    if wl["n_omega"] > 0 and not args.no_flows:
+        nom = wl["n_omega"]
+        Vs = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+        Zs = torch.empty(N, dtype=torch.float64, device="cuda")
+        api.qpfrg_read_state(ctx.h, Vs, Zs)
+        re = torch.empty(N * nom, dtype=torch.float64, device="cuda")
+        im = torch.empty_like(re)
+        T_now = float(r.lambda_)       # temperature after the timed steps
+        api.qpfrg_selfenergy(ctx.h, T_now, Vs, Zs, re, im, None)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        api.qpfrg_selfenergy(ctx.h, T_now, Vs, Zs, re, im, None)
+        b.record(stream)
+        torch.cuda.synchronize()
+        gms = a.elapsed_time(b)
+        extra["sigma_grid"] = {"n_omega": nom, "patches": N, "T": T_now, "ms": gms,
+                               "evals_per_s": 1e3 / gms}
 
     # right-hand side alone, mixed and FP64 forms (same inputs)
     extra = {}

@@ -225,7 +225,7 @@ void qpfrg_destroy(qpfrg_t c)
                         c->tc.App[0], c->tc.App[1], c->tc.Acr[0], c->tc.Acr[1], c->tc.Ad[0], c->tc.Ad[1],
                         c->tc.Bpp[0], c->tc.Bpp[1], c->tc.Bcr[0], c->tc.Bcr[1], c->tc.Bd[0], c->tc.Bd[1],
                         c->tc.VT, c->d_tc_err, c->d_xij, c->d_bnd, c->d_qxl, c->d_qyl, c->d_kp, c->d_kcs, c->d_xij_f,
-                        c->d_ptab};
+                        c->d_ptab, c->d_jgrid, c->d_repgrid};
         for (void *p : ptrs)
             if (p) cudaFree(p);
     }
@@ -404,11 +404,22 @@ qpfrg_status qpfrg_create(const qpfrg_lattice *lattice, int n_p, const qpfrg_fin
             rep[j] = r;
         }
         c->n_irr = (int)jirr.size();
+        // frequency grid: zone-edge patches j = m N/4 get slots of their own
+        std::vector<int> jgrid(jirr), repgrid(rep);
+        for (int m = 1; m < 4; ++m) {
+            repgrid[m * q] = (int)jgrid.size();
+            jgrid.push_back(m * q);
+        }
+        c->n_grid = (int)jgrid.size();
         if ((s = dev_alloc(c, &c->d_jirr, jirr.size(), "irreducible patches")) ||
-            (s = dev_alloc(c, &c->d_rep, N, "representatives")))
+            (s = dev_alloc(c, &c->d_rep, N, "representatives")) ||
+            (s = dev_alloc(c, &c->d_jgrid, jgrid.size(), "grid targets")) ||
+            (s = dev_alloc(c, &c->d_repgrid, N, "grid representatives")))
             return fail(s);
         cudaMemcpy(c->d_jirr, jirr.data(), jirr.size() * sizeof(int), cudaMemcpyHostToDevice);
         cudaMemcpy(c->d_rep, rep.data(), N * sizeof(int), cudaMemcpyHostToDevice);
+        cudaMemcpy(c->d_jgrid, jgrid.data(), jgrid.size() * sizeof(int), cudaMemcpyHostToDevice);
+        cudaMemcpy(c->d_repgrid, repgrid.data(), N * sizeof(int), cudaMemcpyHostToDevice);
     }
 
     // state: V = U, Z = 1 at lambda0

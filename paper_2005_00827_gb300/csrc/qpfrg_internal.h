@@ -164,6 +164,12 @@ struct qpfrg_ctx {
     int *d_jirr = nullptr;       // C4v-irreducible patches 0..N/8 (wedge mode)
     int *d_rep = nullptr;        // slot of each patch's representative in d_jirr
     int n_irr = 0;
+    // targets of the frequency-grid self-energy of a C4v-symmetric state: the
+    // irreducible patches plus the zone-edge patches N/4, N/2, 3N/4, whose sums
+    // differ from patch 0's where a momentum lands on |k_x| or |k_y| = pi
+    int *d_jgrid = nullptr;
+    int *d_repgrid = nullptr;    // slot of each patch's representative in d_jgrid
+    int n_grid = 0;
     bool c4v_state = false;      // flow state V, Z is C4v symmetric
     double *d_hist = nullptr;    // Sigma frequency-grid histogram (lazily sized)
     size_t hist_elems = 0;

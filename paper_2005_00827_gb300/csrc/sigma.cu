@@ -467,8 +467,14 @@ struct SigmaFastArgs {
     double *sig;
     float t, tp, mu, eta2, invT, cT, twoT, fourT;   // cT = log2(e) / T
     float inv_dth, dth;                             // N / 2 pi, 2 pi / N
-    int mirror;     // targets are the C4v-irreducible patches and n_theta is even: halve the mirror targets
+    int mirror;     // n_theta even and symmetric targets: 1 halves every mirror-line target,
+                    // 2 all but the zone-edge ones (j a multiple of N/4)
     int qb;         // blocks of 256 SF_QPT loop points q per CTA
+    // grid mode: pole energies E binned from e_min in bins of h, moments 0..4
+    // of the offset from the bin centre, hist[target][moment][bin] (FP64)
+    double *hist;
+    float e_min, inv_h, h;
+    int nbins;
 };
 
 __device__ __forceinline__ float ex2_approx(float x)
@@ -493,10 +499,11 @@ __device__ __forceinline__ float fold1(float r)
 }
 
 struct SfSmem {
-    size_t rA, rB, cz, ray, cd, rC, tab, total;
+    size_t rA, rB, cz, ray, cd, rC, tab, hist, total;
 };
 
-__host__ __device__ inline SfSmem sf_smem_layout(int pch)
+// nbins > 0: a histogram of nbins x 5 FP32 moments follows the table (grid mode)
+__host__ __device__ inline SfSmem sf_smem_layout(int pch, int nbins = 0)
 {
     SfSmem L;
     L.rA = 0;
@@ -506,7 +513,8 @@ __host__ __device__ inline SfSmem sf_smem_layout(int pch)
     L.cd = L.ray + (size_t)8 * SF_SLOTS;
     L.rC = (L.cd + (size_t)4 * SF_SLOTS + 15) / 16 * 16;
     L.tab = (L.rC + (size_t)4 * pch + 15) / 16 * 16;
-    L.total = L.tab + ((size_t)(kProjW + 1) * kProjStride + 15) / 16 * 16;
+    L.hist = L.tab + ((size_t)(kProjW + 1) * kProjStride + 15) / 16 * 16;
+    L.total = L.hist + (size_t)5 * 4 * nbins;
     return L;
 }
 
@@ -535,8 +543,11 @@ __device__ __noinline__ int sf_slow_patch(const SigmaFastArgs &A, int jidx, int 
 // multiple of 256 SF_QPT), so the vertex weight is a per-patch table:
 // cz[c] = (Z_c (2 V_jab^2 - V_jab V_jac), -, -2t l_c, -mu l_c); otherwise
 // cz[c] = (Z_c, Z_c V_jac, -2t l_c, -mu l_c) and the weight is formed per pair.
-template <bool TP0, bool UNIB>
-__global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
+// GRID: instead of the chord slope, bin W F by pole energy E = x_q + x_r - x_p
+// (moments 0..4 of E - E_bin) in a shared-memory histogram per CTA, flushed to
+// the FP64 histogram once at the end (the frequency grid, sigma_grid_kernel).
+template <bool TP0, bool UNIB, bool GRID>
+__global__ void __launch_bounds__(256, GRID ? 1 : 2) sigma_fast_kernel(SigmaFastArgs A)
 {
     const int N = A.pb.N, M = A.pb.M;
     const int a = blockIdx.y, jidx = blockIdx.z;
@@ -546,23 +557,23 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
     // A target on a mirror line of the zone (theta_j = 0 or pi/4) has a sum
     // symmetric under that mirror: keep the patches a on one side of it with
     // weight 2 and half of each patch the mirror maps onto itself.
+    // The mirror line through k_j (j a multiple of N/8) reflects patch a to 2j - a.
     int fac = 1, P = A.pb.P;
-    if (A.mirror) {
-        int ma = -1;
-        if (j == 0) ma = (N - a) % N;
-        else if (8 * j == N) ma = ((N / 4 - a) % N + N) % N;
+    if (A.mirror && (8 * j) % N == 0 && !(A.mirror == 2 && (4 * j) % N == 0)) {
+        const int ma = ((2 * j - a) % N + N) % N;
         if (ma == a) {
             fac = 2;
             P = A.pb.P / 2;     // angular index t < n_theta / 2
-        } else if (ma >= 0) {
-            const int rel = j == 0 ? a : ((a - N / 8) % N + N) % N;
+        } else {
+            const int rel = ((a - j) % N + N) % N;
             fac = (rel > 0 && 2 * rel < N) ? 2 : 0;
         }
     }
     if (fac == 0) return;       // the mirror patch carries this one (uniform over the CTA)
     const int PP = A.pb.P;      // points per patch (record and loop-point indexing)
-    const int pch = P < SF_PCH ? P : SF_PCH;
-    const SfSmem L = sf_smem_layout(pch);
+    const int cap = GRID ? SF_PCH / 2 : SF_PCH;
+    const int pch = P < cap ? P : cap;
+    const SfSmem L = sf_smem_layout(pch, GRID ? A.nbins : 0);
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4 *rA = reinterpret_cast<float4 *>(smem_raw + L.rA);   // (k+p)_x, (k+p)_y, cos, sin of (k+p)_x
@@ -572,6 +583,9 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
     float *cd = reinterpret_cast<float *>(smem_raw + L.cd);     // -4 t' l_c
     float *rC = reinterpret_cast<float *>(smem_raw + L.rC);     // x_j + x_p + 2T
     unsigned char *tab = smem_raw + L.tab;
+    float *hs = reinterpret_cast<float *>(smem_raw + L.hist);   // [moment][bin] (grid mode)
+    if (GRID)
+        for (int i = tid; i < 5 * A.nbins; i += blockDim.x) hs[i] = 0.f;
 
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(A.ptab);
@@ -622,7 +636,7 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
             const float wp = A.fine.w[p];
             rA[i] = make_float4(k4.x, k4.z, kcs.x * cpx - kcs.y * spx, kcs.y * cpx + kcs.x * spx);
             rB[i] = make_float4(kcs.z * cpy - kcs.w * spy, kcs.w * cpy + kcs.z * spy, wp * fp, wp * fcp);
-            rC[i] = xj + xp + A.twoT;
+            rC[i] = GRID ? xp : xj + xp + A.twoT;
         }
     };
     const bool one_pass = P <= pch;
@@ -724,12 +738,47 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
                     const float Aq = rb.z * fcqp[k], Bq = rb.w * fqp[k];
                     const float F = fmaf(fr, Bq - Aq, Aq);
                     const float amp = UNIB ? z.x * F : fmaf(-vab[k], z.y, z.x * v2[k]) * F;
-                    // d+- = xi_j +- 2T - E with E = x_q + x_r - x_p
-                    const float dp = (upp + mxq[k]) - xr;
-                    const float dm = dp - A.fourT;
-                    const float den = fmaf(dp, dp, A.eta2) * fmaf(dm, dm, A.eta2);
-                    const float num = fmaf(-dp, dm, A.eta2);
-                    acc[k] = fmaf(amp * num, rcp_approx(den), acc[k]);
+                    if (GRID) {
+                        // pole energy E = x_q + x_r - x_p (upp holds x_p here)
+                        const float E = (xr - mxq[k]) - upp;
+                        int bin = (int)floorf((E - A.e_min) * A.inv_h);
+                        bin = bin < 0 ? 0 : (bin >= A.nbins ? A.nbins - 1 : bin);
+                        const float d = E - (A.e_min + ((float)bin + 0.5f) * A.h);
+                        float mm[5];
+                        mm[0] = amp;
+#pragma unroll
+                        for (int mo = 1; mo < 5; ++mo) mm[mo] = mm[mo - 1] * d;
+                        // neighbouring lanes often share a bin: sum runs of equal
+                        // bins with shuffles (each lane adds the lanes up to the
+                        // end of its run), then one atomic per run and moment
+                        const int lane = tid & 31;
+                        const int bup = __shfl_up_sync(0xffffffffu, bin, 1);
+                        const bool head = lane == 0 || bup != bin;
+                        const unsigned heads = __ballot_sync(0xffffffffu, head);
+                        if (heads != 0xffffffffu) {
+                            const unsigned above = lane == 31 ? 0u : heads >> (lane + 1);
+                            const int end = above ? lane + __ffs(above) - 1 : 31;
+#pragma unroll
+                            for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+                                for (int mo = 0; mo < 5; ++mo) {
+                                    const float o = __shfl_down_sync(0xffffffffu, mm[mo], off);
+                                    if (lane + off <= end) mm[mo] += o;
+                                }
+                            }
+                        }
+                        if (head) {
+#pragma unroll
+                            for (int mo = 0; mo < 5; ++mo) atomicAdd(&hs[mo * A.nbins + bin], mm[mo]);
+                        }
+                    } else {
+                        // d+- = xi_j +- 2T - E with E = x_q + x_r - x_p
+                        const float dp = (upp + mxq[k]) - xr;
+                        const float dm = dp - A.fourT;
+                        const float den = fmaf(dp, dp, A.eta2) * fmaf(dm, dm, A.eta2);
+                        const float num = fmaf(-dp, dm, A.eta2);
+                        acc[k] = fmaf(amp * num, rcp_approx(den), acc[k]);
+                    }
                 }
             }
         }
@@ -737,6 +786,15 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
         for (int k = 0; k < SF_QPT; ++k) vsum += (double)acc[k];
     }
     vsum *= fac;
+    if (GRID) {
+        __syncthreads();
+        double *H = A.hist + (long)jidx * 5 * A.nbins;
+        for (int i = tid; i < 5 * A.nbins; i += blockDim.x) {
+            const float v = hs[i];
+            if (v != 0.f) atomicAdd(&H[i], (double)v * fac);
+        }
+        return;
+    }
     __shared__ double red[32];
     double v = vsum;
 #pragma unroll
@@ -764,14 +822,16 @@ __global__ void z_update_kernel(const double *slope, const int *rep, double *Zou
 
 // Sigma on the grid from the binned moments: sum_b sum_n H_n[b] / (z - E_b)^(n+1),
 // z = w_m + i eta (Taylor expansion of 1/(z - E_b - d) in the offset d).
+// rep (may be NULL): the histogram slot of patch j's C4v representative.
 __global__ void sigma_grid_kernel(const double *hist, int nbins, double e_min, double h, int n_omega,
-                                  double w0, double dw, double eta, double *re, double *im, int N)
+                                  double w0, double dw, double eta, double *re, double *im, int N,
+                                  const int *rep)
 {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     if (m >= n_omega) return;
     const double w = w0 + dw * m;
-    const double *H = hist + (long)j * 5 * nbins;
+    const double *H = hist + (long)(rep ? rep[j] : j) * 5 * nbins;
     double sr = 0.0, si = 0.0;
     for (int b = 0; b < nbins; ++b) {
         const double Eb = e_min + (b + 0.5) * h;
@@ -823,8 +883,19 @@ static qpfrg_status launch_sigma(qpfrg_ctx *c, bool hist, SigmaArgs<R> &A, int k
     return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "sigma_kernel");
 }
 
+// Shared memory of the fast kernel (grid mode with nbins > 0)
+static size_t sigma_fast_smem(const qpfrg_ctx *c, int nbins)
+{
+    const int cap = nbins > 0 ? SF_PCH / 2 : SF_PCH;
+    const int pch = c->pb.P < cap ? c->pb.P : cap;
+    return sf_smem_layout(pch, nbins).total;
+}
+
+// nbins == 0: chord slopes into d_sig (the flow's Z); nbins > 0: the binned
+// pole density into hist (frequency grid)
 static qpfrg_status launch_sigma_fast(qpfrg_ctx *c, double T, const double *d_V, const double *d_Z,
-                                      const int *jlist, int nj)
+                                      const int *jlist, int nj, double *hist = nullptr, double e_min = 0.0,
+                                      double h = 1.0, int nbins = 0)
 {
     qpfrg_status s = launch_kp_table(c, jlist, nj);
     if (s != QPFRG_OK) return s;
@@ -855,19 +926,37 @@ static qpfrg_status launch_sigma_fast(qpfrg_ctx *c, double T, const double *d_V,
     A.fourT = (float)(4.0 * T);
     A.inv_dth = (float)(c->pb.N / kTwoPi);
     A.dth = (float)(kTwoPi / c->pb.N);
-    const int pch = c->pb.P < SF_PCH ? c->pb.P : SF_PCH;
-    const size_t smem = sf_smem_layout(pch).total;
-    A.mirror = (jlist != nullptr && c->pb.n_theta % 2 == 0) ? 1 : 0;
+    A.hist = hist;
+    A.e_min = (float)e_min;
+    A.h = (float)h;
+    A.inv_h = (float)(1.0 / h);
+    A.nbins = nbins;
+    const bool grid_mode = nbins > 0;
+    const size_t smem = sigma_fast_smem(c, nbins);
+    // The zone-edge targets' sums are mirror symmetric only up to the pairs
+    // whose momentum r lands on |r_x| or |r_y| = pi (their wedge is decided by
+    // rounding): halving them is kept for the chord slope (a relative error
+    // below 1e-4, shrinking with N) and left out on the frequency grid.
+    A.mirror = (jlist != nullptr && c->pb.n_theta % 2 == 0) ? (grid_mode ? 2 : 1) : 0;
     const bool unib = c->pb.P % (256 * SF_QPT) == 0;
-    auto kern = c->pb.tp == 0.0 ? (unib ? sigma_fast_kernel<true, true> : sigma_fast_kernel<true, false>)
-                                : (unib ? sigma_fast_kernel<false, true> : sigma_fast_kernel<false, false>);
+    using Kern = void (*)(SigmaFastArgs);
+    Kern kern;
+    if (grid_mode)
+        kern = c->pb.tp == 0.0 ? (unib ? sigma_fast_kernel<true, true, true> : sigma_fast_kernel<true, false, true>)
+                               : (unib ? sigma_fast_kernel<false, true, true> : sigma_fast_kernel<false, false, true>);
+    else
+        kern = c->pb.tp == 0.0 ? (unib ? sigma_fast_kernel<true, true, false> : sigma_fast_kernel<true, false, false>)
+                               : (unib ? sigma_fast_kernel<false, true, false> : sigma_fast_kernel<false, false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(c, e, "sigma_fast smem attribute");
-    A.qb = c->tune.sigma_qblocks > 0 ? c->tune.sigma_qblocks : SF_QB;
-    dim3 grid(div_up(div_up(c->pb.M, 256 * SF_QPT), A.qb), c->pb.N, nj);
+    // grid mode: one CTA per (patch a, target) takes every q block, so that the
+    // per-CTA histogram reaches the FP64 one with few atomics per bin
+    const int nqb = div_up(c->pb.M, 256 * SF_QPT);
+    A.qb = grid_mode ? nqb : (c->tune.sigma_qblocks > 0 ? c->tune.sigma_qblocks : SF_QB);
+    dim3 grid(div_up(nqb, A.qb), c->pb.N, nj);
     prof_begin(c);
     kern<<<grid, 256, smem, c->stream>>>(A);
-    prof_end(c, K_SIGMA_Z);
+    prof_end(c, grid_mode ? K_SIGMA_HIST : K_SIGMA_Z);
     e = cudaGetLastError();
     return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "sigma_fast_kernel");
 }
@@ -941,6 +1030,48 @@ qpfrg_status launch_sigma_z(qpfrg_ctx *c, double T, const double *d_V, const dou
     return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "z_update_kernel");
 }
 
+// Whether (V, Z) keep the C4v symmetry of the wedge patches: flag set when an
+// image V(g k1, g k2, g k3) or Z(g k) differs from the original by more than
+// tol (1 + |v|), g running over the rotations j -> j + m N/4 and the
+// reflections j -> -j + m N/4 of the patch index.
+__global__ void c4v_check_kernel(const double *V, const double *Z, int N, double tol, unsigned long long *flag)
+{
+    const long NN = (long)N * N, n3 = NN * N;
+    const int q = N / 4;
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n3; idx += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / NN), j = (int)((idx / N) % N), l = (int)(idx % N);
+        const double v = V[idx];
+        bool bad = false;
+        for (int g = 1; g < 8; ++g) {
+            const int m = g & 3, sg = g < 4 ? 1 : -1;
+            auto img = [&](int x) { return ((sg * x + m * q) % N + N) % N; };
+            const double w = V[((long)img(i) * N + img(j)) * N + img(l)];
+            bad = bad || fabs(w - v) > tol * (1.0 + fabs(v));
+            if (idx < N && Z) bad = bad || fabs(Z[img((int)idx)] - Z[idx]) > tol * (1.0 + fabs(Z[idx]));
+        }
+        if (bad) atomicOr(flag, 1ull);
+    }
+}
+
+static qpfrg_status c4v_check(qpfrg_ctx *c, const double *d_V, const double *d_Z, bool &sym)
+{
+    sym = false;
+    const int N = c->pb.N;
+    if (N % 4 != 0) return QPFRG_OK;
+    cudaError_t e = cudaMemsetAsync(c->d_red, 0, sizeof(unsigned long long), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "memset symmetry flag");
+    const long n3 = (long)N * N * N;
+    c4v_check_kernel<<<(int)std::min<long>((n3 + 255) / 256, 152L * 8), 256, 0, c->stream>>>(d_V, d_Z, N, 1e-5,
+                                                                                            c->d_red);
+    unsigned long long flag = 1;
+    if ((e = cudaGetLastError()) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&flag, c->d_red, sizeof(flag), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+        return cuda_fail(c, e, "symmetry check");
+    sym = flag == 0;
+    return QPFRG_OK;
+}
+
 // Bin count of the frequency-grid histogram: with h = eta/4 the offset of a
 // pole from its bin centre is at most |z - E_b|/8, so the moment expansion
 // truncated after moment 4 is accurate to 8^-5 = 3e-5 relative per pole.
@@ -992,7 +1123,16 @@ qpfrg_status launch_sigma_grid(qpfrg_ctx *c, double T, const double *d_V, const 
     if (e != cudaSuccess) return cuda_fail(c, e, "memset histogram");
     const double h = (e_max - e_min) / nbins;
     qpfrg_status s;
-    if (c->opt.precision == QPFRG_FP64) {
+    bool sym = false;
+    if (c->opt.precision != QPFRG_FP64 && c->d_ptab && sigma_fast_smem(c, nbins) <= 226 * 1024) {
+        // FP32 wedge grid: table projection, histogram in shared memory; a
+        // C4v-symmetric (V, Z) needs only the irreducible targets
+        if (c->d_jgrid) {
+            if ((s = c4v_check(c, d_V, d_Z, sym)) != QPFRG_OK) return s;
+        }
+        s = launch_sigma_fast(c, T, d_V, d_Z, sym ? c->d_jgrid : nullptr, sym ? c->n_grid : N, c->d_hist, e_min,
+                              h, nbins);
+    } else if (c->opt.precision == QPFRG_FP64) {
         SigmaArgs<double> A;
         fill_args(c, A, c->f64, T, d_V, d_Z);
         A.e_min = e_min;
@@ -1013,7 +1153,7 @@ qpfrg_status launch_sigma_grid(qpfrg_ctx *c, double T, const double *d_V, const 
     dim3 grid(div_up(n_omega, 128), N);
     prof_begin(c);
     sigma_grid_kernel<<<grid, 128, 0, c->stream>>>(c->d_hist, nbins, e_min, h, n_omega, w0, dw, c->pb.eta,
-                                                   d_re, d_im, N);
+                                                   d_re, d_im, N, sym ? c->d_repgrid : nullptr);
     prof_end(c, K_SIGMA_GRID);
     e = cudaGetLastError();
     return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "sigma_grid_kernel");

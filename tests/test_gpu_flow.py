@@ -66,12 +66,17 @@ def test_z_mixed_wedge_cases(case):
     assert np.abs(got - ref).max() < 1e-4
 
 
-@pytest.mark.parametrize("prec", [api.QPFRG_FP64, api.QPFRG_MIXED])
-def test_sigma_grid_matches_exact_pole_sum(prec):
+@pytest.mark.parametrize("prec,sym", [(api.QPFRG_FP64, True), (api.QPFRG_MIXED, True), (api.QPFRG_MIXED, False)],
+                         ids=["fp64", "mixed-c4v", "mixed-asym"])
+def test_sigma_grid_matches_exact_pole_sum(prec, sym):
+    """Sigma on the frequency grid against the exact pole sum.  In mixed
+    precision a C4v-symmetric (V, Z) is evaluated on the irreducible patches
+    (the mirror-line ones over half of the loop points) and copied to the
+    others; an asymmetric vertex takes every patch."""
     import torch
     N, n, T, nw = 16, 4, 0.15, 64
     o = Oracle(N, n, n, eta=0.05)
-    V = inputs.random_vertex(N, 2.0, seed=8)
+    V = inputs.random_vertex(N, 2.0, seed=8, c4v=sym)
     Z = inputs.z_profile(N, "aniso")
     w = np.linspace(-4.0, 4.0, nw)
     with api.Context(N, n, n, U=2.0, precision=prec, eta=0.05, n_omega=nw, omega_min=-4.0,
@@ -80,10 +85,31 @@ def test_sigma_grid_matches_exact_pole_sum(prec):
         api.qpfrg_selfenergy(ctx.h, T, dev(V), dev(Z), re, im, None)
         torch.cuda.synchronize()
         got = (re.cpu().numpy() + 1j * im.cpu().numpy()).reshape(N, nw)
-    for j in (0, 3, 8):
+    for j in (0, 3, 5, 8, 13):
         ref = o.sigma(T, V, Z, j, w)
         assert np.abs(got[j] - ref).max() / np.abs(ref).max() < 1e-4
         assert np.all(got[j].imag <= 1e-12)
+
+
+def test_sigma_grid_qp_p512_matches_exact_pole_sum():
+    """Frequency grid in mixed precision with quasi-particle lines, t' and mu
+    nonzero and 512 points per patch (the per-patch weight table of the
+    shared-memory histogram kernel)."""
+    import torch
+    N, nt, nr, T, nw = 8, 32, 16, 0.2, 48
+    o = Oracle(N, nt, nr, tp=-0.2, mu=-0.3, prop_mode=1, eta=0.05)
+    V = inputs.random_vertex(N, 2.0, seed=13, c4v=True)
+    Z = inputs.z_profile(N, "aniso")
+    w = np.linspace(-3.0, 3.0, nw)
+    with api.Context(N, nt, nr, U=2.0, tp=-0.2, mu=-0.3, precision=api.QPFRG_MIXED, propagator=1, eta=0.05,
+                     n_omega=nw, omega_min=-3.0, omega_max=3.0) as ctx:
+        re, im = zeros(N * nw), zeros(N * nw)
+        api.qpfrg_selfenergy(ctx.h, T, dev(V), dev(Z), re, im, None)
+        torch.cuda.synchronize()
+        got = (re.cpu().numpy() + 1j * im.cpu().numpy()).reshape(N, nw)
+    for j in (0, 3):
+        ref = o.sigma(T, V, Z, j, w)
+        assert np.abs(got[j] - ref).max() / np.abs(ref).max() < 1e-4
 
 
 def run_oracle_flow(o, U, T0, T_end, z_feedback, steps=None):
