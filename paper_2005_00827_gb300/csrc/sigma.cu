@@ -543,11 +543,231 @@ __device__ __noinline__ int sf_slow_patch(const SigmaFastArgs &A, int jidx, int 
 // multiple of 256 SF_QPT), so the vertex weight is a per-patch table:
 // cz[c] = (Z_c (2 V_jab^2 - V_jab V_jac), -, -2t l_c, -mu l_c); otherwise
 // cz[c] = (Z_c, Z_c V_jac, -2t l_c, -mu l_c) and the weight is formed per pair.
-// GRID: instead of the chord slope, bin W F by pole energy E = x_q + x_r - x_p
+template <bool TP0, bool UNIB>
+__global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
+{
+    const int N = A.pb.N, M = A.pb.M;
+    const int a = blockIdx.y, jidx = blockIdx.z;
+    const int j = A.jlist ? A.jlist[jidx] : jidx;
+    const int tid = threadIdx.x;
+    const bool qp = A.pb.propagator == QPFRG_PROP_QP;
+    // A target on a mirror line of the zone (theta_j = 0 or pi/4) has a sum
+    // symmetric under that mirror: keep the patches a on one side of it with
+    // weight 2 and half of each patch the mirror maps onto itself.
+    int fac = 1, P = A.pb.P;
+    if (A.mirror) {
+        int ma = -1;
+        if (j == 0) ma = (N - a) % N;
+        else if (8 * j == N) ma = ((N / 4 - a) % N + N) % N;
+        if (ma == a) {
+            fac = 2;
+            P = A.pb.P / 2;     // angular index t < n_theta / 2
+        } else if (ma >= 0) {
+            const int rel = j == 0 ? a : ((a - N / 8) % N + N) % N;
+            fac = (rel > 0 && 2 * rel < N) ? 2 : 0;
+        }
+    }
+    if (fac == 0) return;       // the mirror patch carries this one (uniform over the CTA)
+    const int PP = A.pb.P;      // points per patch (record and loop-point indexing)
+    const int pch = P < SF_PCH ? P : SF_PCH;
+    const SfSmem L = sf_smem_layout(pch);
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4 *rA = reinterpret_cast<float4 *>(smem_raw + L.rA);   // (k+p)_x, (k+p)_y, cos, sin of (k+p)_x
+    float4 *rB = reinterpret_cast<float4 *>(smem_raw + L.rB);   // cos, sin of (k+p)_y, w_p f_p, w_p (1 - f_p)
+    float4 *cz = reinterpret_cast<float4 *>(smem_raw + L.cz);
+    float2 *ray = reinterpret_cast<float2 *>(smem_raw + L.ray);
+    float *cd = reinterpret_cast<float *>(smem_raw + L.cd);     // -4 t' l_c
+    float *rC = reinterpret_cast<float *>(smem_raw + L.rC);     // x_j + x_p + 2T
+    unsigned char *tab = smem_raw + L.tab;
+
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(A.ptab);
+        uint4 *dst = reinterpret_cast<uint4 *>(tab);
+        const int n16 = ((kProjW + 1) * kProjStride + 15) / 16;
+        for (int i = tid; i < n16; i += blockDim.x) dst[i] = src[i];
+    }
+    const double *Vja = A.V + ((long)j * N + a) * N;
+    // per-patch slots; with UNIB the weight column is filled per q block (b)
+    auto fill_slots = [&](int b) {
+        const float vb = UNIB ? (float)Vja[b] : 0.f;
+        for (int i = tid; i < SF_SLOTS; i += blockDim.x) {
+            if (i <= N) {
+                const int cc = i == N ? 0 : i;
+                const float Zc = A.Z ? (float)A.Z[cc] : 1.f;
+                const float lz = qp ? Zc : 1.f;
+                const float vc = (float)Vja[cc];
+                cz[i] = UNIB ? make_float4(Zc * (2.f * vb * vb - vb * vc), 0.f, -2.f * A.t * lz, -A.mu * lz)
+                             : make_float4(Zc, Zc * vc, -2.f * A.t * lz, -A.mu * lz);
+                cd[i] = -4.f * A.tp * lz;
+                const float4 bd = A.bnd[cc];
+                ray[i] = make_float2(bd.x, bd.z);
+            } else {
+                cz[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                cd[i] = 0.f;
+                ray[i] = make_float2(0.f, 0.f);
+            }
+        }
+    };
+    int b_slots = UNIB ? (blockIdx.x * A.qb * 256 * SF_QPT) / PP : 0;
+    fill_slots(b_slots);
+    const float Za = A.Z ? (float)A.Z[a] : 1.f;
+    const float lza = qp ? Za : 1.f;
+    const float4 kcs = A.kcs[jidx];
+    const float xj = A.xij_f[j];
+
+    const unsigned tab_last = (kProjW + 1) * kProjStride - 1;
+    const float kW = (float)(kProjW / kTwoPi);
+    // records of the loop points p0 .. p0 + cnt - 1 of patch a
+    auto stage = [&](int p0, int cnt) {
+        for (int i = tid; i < cnt; i += blockDim.x) {
+            const int p = a * PP + p0 + i;
+            const float4 k4 = A.kp[(long)jidx * M + p];
+            const float cpx = A.fine.cx[p], spx = A.fine.sx[p], cpy = A.fine.cy[p], spy = A.fine.sy[p];
+            const float xp = lza * A.fine.xi[p];
+            float fp, fcp;
+            sfermi(xp, A.invT, fp, fcp);
+            const float wp = A.fine.w[p];
+            rA[i] = make_float4(k4.x, k4.z, kcs.x * cpx - kcs.y * spx, kcs.y * cpx + kcs.x * spx);
+            rB[i] = make_float4(kcs.z * cpy - kcs.w * spy, kcs.w * cpy + kcs.z * spy, wp * fp, wp * fcp);
+            rC[i] = xj + xp + A.twoT;
+        }
+    };
+    const bool one_pass = P <= pch;
+    if (one_pass) stage(0, P);
+    __syncthreads();   // tables (and the records of a single pass) written
+
+    double vsum = 0.0;
+    // A.qb blocks of 256 SF_QPT loop points q per CTA reuse the staged tables
+    for (int qb = 0; qb < A.qb; ++qb) {
+        const int blk = blockIdx.x * A.qb + qb;
+        if (blk * (256 * SF_QPT) >= M) break;   // uniform over the CTA
+        if (UNIB && blk * (256 * SF_QPT) / PP != b_slots) {
+            b_slots = blk * (256 * SF_QPT) / PP;
+            __syncthreads();   // every warp is done with the previous weights
+            fill_slots(b_slots);
+            __syncthreads();
+        }
+        // the SF_QPT loop points q of this thread (an index past M gets weight 0)
+        float qx[SF_QPT], qy[SF_QPT], cqx[SF_QPT], sqx[SF_QPT], cqy[SF_QPT], sqy[SF_QPT];
+        float fqp[SF_QPT], fcqp[SF_QPT], v2[SF_QPT], vab[SF_QPT], mxq[SF_QPT], acc[SF_QPT];
+        int qi[SF_QPT];
+#pragma unroll
+        for (int k = 0; k < SF_QPT; ++k) {
+            const int iq = blk * (256 * SF_QPT) + k * 256 + tid;   // angular-minor index
+            const bool valid = iq < M;
+            const int ii = valid ? iq : M - 1;
+            const int b = ii / PP, rem = ii - b * PP;
+            const int qq = b * PP + (rem % A.pb.n_theta) * A.pb.n_r + rem / A.pb.n_theta;
+            qi[k] = qq;
+            const float Zb = A.Z ? (float)A.Z[b] : 1.f;
+            qx[k] = A.fine.kx[qq];
+            qy[k] = A.fine.ky[qq];
+            cqx[k] = A.fine.cx[qq];
+            sqx[k] = A.fine.sx[qq];
+            cqy[k] = A.fine.cy[qq];
+            sqy[k] = A.fine.sy[qq];
+            const float xq = (qp ? Zb : 1.f) * A.fine.xi[qq];
+            float fq, fcq;
+            sfermi(xq, A.invT, fq, fcq);
+            const float pref = valid ? Za * Zb * A.fine.w[qq] : 0.f;
+            fqp[k] = fq * pref;
+            fcqp[k] = fcq * pref;
+            vab[k] = (float)Vja[b];
+            v2[k] = 2.f * vab[k] * vab[k];
+            mxq[k] = -xq;
+            acc[k] = 0.f;
+        }
+
+        for (int p0 = 0; p0 < P; p0 += pch) {
+            const int cnt = P - p0 < pch ? P - p0 : pch;
+            if (!one_pass) {
+                __syncthreads();   // previous pass done with the records
+                stage(p0, cnt);
+                __syncthreads();
+            }
+#pragma unroll 2
+            for (int i = 0; i < cnt; ++i) {
+                const float4 ra = rA[i], rb = rB[i];
+                const float upp = rC[i];
+                int c[SF_QPT];
+                float x[SF_QPT], y[SF_QPT];
+                bool slow_any = false;
+                unsigned slow_mask = 0;
+#pragma unroll
+                for (int k = 0; k < SF_QPT; ++k) {
+                    x[k] = fold1(ra.x - qx[k]);
+                    y[k] = fold1(ra.y - qy[k]);
+                    const bool edge = fmaxf(fabsf(x[k]), fabsf(y[k])) > 3.14159265f - 4e-6f;
+                    const float sx = fmaf(x[k], kW, 12583040.f);   // 1.5 * 2^23 + W/2: low bits = cell index
+                    const float sy = fmaf(y[k], kW, 12583040.f);
+                    unsigned idx = (unsigned)__float_as_int(sy) * (unsigned)kProjStride +
+                                   (unsigned)__float_as_int(sx) - 0x4B400000u * (unsigned)(kProjStride + 1);
+                    idx = min(idx, tab_last);
+                    const int e = tab[idx];
+                    // e = 255 (cell at the origin) reads the zero ray 256: cr = 0 takes the slow path
+                    const float2 rr = ray[e + 1];
+                    const float cr = rr.x * y[k] - rr.y * x[k];
+                    c[k] = e + (cr >= 0.f ? 1 : 0);
+                    const bool slow = edge || fabsf(cr) < 4e-6f;
+                    slow_mask |= slow ? 1u << k : 0u;
+                    slow_any = slow_any || slow;
+                }
+                if (slow_any) {
+#pragma unroll
+                    for (int k = 0; k < SF_QPT; ++k)
+                        if (slow_mask & (1u << k)) {
+                            const bool edge = fmaxf(fabsf(x[k]), fabsf(y[k])) > 3.14159265f - 4e-6f;
+                            c[k] = sf_slow_patch(A, jidx, j, a * PP + p0 + i, qi[k], x[k], y[k], edge, A.bnd);
+                        }
+                }
+#pragma unroll
+                for (int k = 0; k < SF_QPT; ++k) {
+                    const float4 z = cz[c[k]];
+                    const float crx = ra.z * cqx[k] + ra.w * sqx[k];
+                    const float cry = rb.x * cqy[k] + rb.y * sqy[k];
+                    float xr = fmaf(crx + cry, z.z, z.w);           // Z-scaled line energy of r
+                    if (!TP0) xr = fmaf(crx * cry, cd[c[k]], xr);
+                    const float fr = rcp_approx(1.f + ex2_approx(xr * A.cT));
+                    const float Aq = rb.z * fcqp[k], Bq = rb.w * fqp[k];
+                    const float F = fmaf(fr, Bq - Aq, Aq);
+                    const float amp = UNIB ? z.x * F : fmaf(-vab[k], z.y, z.x * v2[k]) * F;
+                    // d+- = xi_j +- 2T - E with E = x_q + x_r - x_p
+                    const float dp = (upp + mxq[k]) - xr;
+                    const float dm = dp - A.fourT;
+                    const float den = fmaf(dp, dp, A.eta2) * fmaf(dm, dm, A.eta2);
+                    const float num = fmaf(-dp, dm, A.eta2);
+                    acc[k] = fmaf(amp * num, rcp_approx(den), acc[k]);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < SF_QPT; ++k) vsum += (double)acc[k];
+    }
+    vsum *= fac;
+    __shared__ double red[32];
+    double v = vsum;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    const int lane = tid & 31, warp = tid >> 5;
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        v = lane < nw ? red[lane] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) atomicAdd(&A.sig[jidx], v);
+    }
+}
+
+// Frequency-grid variant of sigma_fast_kernel (instantiated with GRID = true):
+// instead of the chord slope, bin W F by pole energy E = x_q + x_r - x_p
 // (moments 0..4 of E - E_bin) in a shared-memory histogram per CTA, flushed to
-// the FP64 histogram once at the end (the frequency grid, sigma_grid_kernel).
+// the FP64 histogram once at the end (then sigma_grid_kernel).  A separate
+// kernel, so that the chord kernel of the flow keeps its own code generation.
 template <bool TP0, bool UNIB, bool GRID>
-__global__ void __launch_bounds__(256, GRID ? 1 : 2) sigma_fast_kernel(SigmaFastArgs A)
+__global__ void __launch_bounds__(256, 1) sigma_grid_fast_kernel(SigmaFastArgs A)
 {
     const int N = A.pb.N, M = A.pb.M;
     const int a = blockIdx.y, jidx = blockIdx.z;
@@ -942,11 +1162,12 @@ static qpfrg_status launch_sigma_fast(qpfrg_ctx *c, double T, const double *d_V,
     using Kern = void (*)(SigmaFastArgs);
     Kern kern;
     if (grid_mode)
-        kern = c->pb.tp == 0.0 ? (unib ? sigma_fast_kernel<true, true, true> : sigma_fast_kernel<true, false, true>)
-                               : (unib ? sigma_fast_kernel<false, true, true> : sigma_fast_kernel<false, false, true>);
+        kern = c->pb.tp == 0.0
+                   ? (unib ? sigma_grid_fast_kernel<true, true, true> : sigma_grid_fast_kernel<true, false, true>)
+                   : (unib ? sigma_grid_fast_kernel<false, true, true> : sigma_grid_fast_kernel<false, false, true>);
     else
-        kern = c->pb.tp == 0.0 ? (unib ? sigma_fast_kernel<true, true, false> : sigma_fast_kernel<true, false, false>)
-                               : (unib ? sigma_fast_kernel<false, true, false> : sigma_fast_kernel<false, false, false>);
+        kern = c->pb.tp == 0.0 ? (unib ? sigma_fast_kernel<true, true> : sigma_fast_kernel<true, false>)
+                               : (unib ? sigma_fast_kernel<false, true> : sigma_fast_kernel<false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(c, e, "sigma_fast smem attribute");
     // grid mode: one CTA per (patch a, target) takes every q block, so that the
