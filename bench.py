@@ -40,7 +40,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "np96_n32"
-METRIC = "fRG RHS evaluations/s at N_p=96 (flow steps with Z feedback)"
+METRIC = "fRG RHS evaluations/s at N_p={N} (flow steps with Z feedback)"
 UNIT = "RHS/s"
 
 # Algorithmic work per loop-kernel evaluation and per self-energy pair (FP32
@@ -288,7 +288,7 @@ def run_qpfrg(args):
                 f"{mufu} MUFU / {MUFU_PER_SM} per SM"}
 
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC.format(N=N), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": {api.QPFRG_MIXED: "f32+f64", api.QPFRG_MIXED_TC: "bf16x3+f32+f64"}.get(prec, "f64"),
         "data": "synthetic (seeded lattice parameters; no dataset in the paper)",
@@ -412,6 +412,8 @@ def run_sweep(args):
 
 
 def run_reference(args):
+    from paper_2005_00827_gb300 import inputs
+
     rank, world, _ = dist_env()
     if rank != 0:
         return
@@ -424,7 +426,7 @@ def run_reference(args):
     v = statistics.mean(vals)
     cb = cpu_baseline(args.workload, budget_s=1.0)
     cb["value"] = v
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+    line = {"impl": "reference", "metric": METRIC.format(N=inputs.WORKLOADS[args.workload]["N"]), "value": v, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 4e3 / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload},

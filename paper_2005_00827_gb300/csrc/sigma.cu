@@ -761,12 +761,12 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
     }
 }
 
-// Frequency-grid variant of sigma_fast_kernel (instantiated with GRID = true):
+// Frequency-grid variant of sigma_fast_kernel:
 // instead of the chord slope, bin W F by pole energy E = x_q + x_r - x_p
 // (moments 0..4 of E - E_bin) in a shared-memory histogram per CTA, flushed to
 // the FP64 histogram once at the end (then sigma_grid_kernel).  A separate
 // kernel, so that the chord kernel of the flow keeps its own code generation.
-template <bool TP0, bool UNIB, bool GRID>
+template <bool TP0, bool UNIB>
 __global__ void __launch_bounds__(256, 1) sigma_grid_fast_kernel(SigmaFastArgs A)
 {
     const int N = A.pb.N, M = A.pb.M;
@@ -791,9 +791,9 @@ __global__ void __launch_bounds__(256, 1) sigma_grid_fast_kernel(SigmaFastArgs A
     }
     if (fac == 0) return;       // the mirror patch carries this one (uniform over the CTA)
     const int PP = A.pb.P;      // points per patch (record and loop-point indexing)
-    const int cap = GRID ? SF_PCH / 2 : SF_PCH;
+    const int cap = SF_PCH / 2;     // room for the histogram
     const int pch = P < cap ? P : cap;
-    const SfSmem L = sf_smem_layout(pch, GRID ? A.nbins : 0);
+    const SfSmem L = sf_smem_layout(pch, A.nbins);
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4 *rA = reinterpret_cast<float4 *>(smem_raw + L.rA);   // (k+p)_x, (k+p)_y, cos, sin of (k+p)_x
@@ -804,8 +804,7 @@ __global__ void __launch_bounds__(256, 1) sigma_grid_fast_kernel(SigmaFastArgs A
     float *rC = reinterpret_cast<float *>(smem_raw + L.rC);     // x_j + x_p + 2T
     unsigned char *tab = smem_raw + L.tab;
     float *hs = reinterpret_cast<float *>(smem_raw + L.hist);   // [moment][bin] (grid mode)
-    if (GRID)
-        for (int i = tid; i < 5 * A.nbins; i += blockDim.x) hs[i] = 0.f;
+    for (int i = tid; i < 5 * A.nbins; i += blockDim.x) hs[i] = 0.f;
 
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(A.ptab);
@@ -840,7 +839,6 @@ __global__ void __launch_bounds__(256, 1) sigma_grid_fast_kernel(SigmaFastArgs A
     const float Za = A.Z ? (float)A.Z[a] : 1.f;
     const float lza = qp ? Za : 1.f;
     const float4 kcs = A.kcs[jidx];
-    const float xj = A.xij_f[j];
 
     const unsigned tab_last = (kProjW + 1) * kProjStride - 1;
     const float kW = (float)(kProjW / kTwoPi);
@@ -856,14 +854,13 @@ __global__ void __launch_bounds__(256, 1) sigma_grid_fast_kernel(SigmaFastArgs A
             const float wp = A.fine.w[p];
             rA[i] = make_float4(k4.x, k4.z, kcs.x * cpx - kcs.y * spx, kcs.y * cpx + kcs.x * spx);
             rB[i] = make_float4(kcs.z * cpy - kcs.w * spy, kcs.w * cpy + kcs.z * spy, wp * fp, wp * fcp);
-            rC[i] = GRID ? xp : xj + xp + A.twoT;
+            rC[i] = xp;
         }
     };
     const bool one_pass = P <= pch;
     if (one_pass) stage(0, P);
     __syncthreads();   // tables (and the records of a single pass) written
 
-    double vsum = 0.0;
     // A.qb blocks of 256 SF_QPT loop points q per CTA reuse the staged tables
     for (int qb = 0; qb < A.qb; ++qb) {
         const int blk = blockIdx.x * A.qb + qb;
@@ -876,7 +873,7 @@ __global__ void __launch_bounds__(256, 1) sigma_grid_fast_kernel(SigmaFastArgs A
         }
         // the SF_QPT loop points q of this thread (an index past M gets weight 0)
         float qx[SF_QPT], qy[SF_QPT], cqx[SF_QPT], sqx[SF_QPT], cqy[SF_QPT], sqy[SF_QPT];
-        float fqp[SF_QPT], fcqp[SF_QPT], v2[SF_QPT], vab[SF_QPT], mxq[SF_QPT], acc[SF_QPT];
+        float fqp[SF_QPT], fcqp[SF_QPT], v2[SF_QPT], vab[SF_QPT], mxq[SF_QPT];
         int qi[SF_QPT];
 #pragma unroll
         for (int k = 0; k < SF_QPT; ++k) {
@@ -902,7 +899,6 @@ __global__ void __launch_bounds__(256, 1) sigma_grid_fast_kernel(SigmaFastArgs A
             vab[k] = (float)Vja[b];
             v2[k] = 2.f * vab[k] * vab[k];
             mxq[k] = -xq;
-            acc[k] = 0.f;
         }
 
         for (int p0 = 0; p0 < P; p0 += pch) {
@@ -915,7 +911,7 @@ __global__ void __launch_bounds__(256, 1) sigma_grid_fast_kernel(SigmaFastArgs A
 #pragma unroll 2
             for (int i = 0; i < cnt; ++i) {
                 const float4 ra = rA[i], rb = rB[i];
-                const float upp = rC[i];
+                const float upp = rC[i];   // x_p
                 int c[SF_QPT];
                 float x[SF_QPT], y[SF_QPT];
                 bool slow_any = false;
@@ -958,76 +954,47 @@ __global__ void __launch_bounds__(256, 1) sigma_grid_fast_kernel(SigmaFastArgs A
                     const float Aq = rb.z * fcqp[k], Bq = rb.w * fqp[k];
                     const float F = fmaf(fr, Bq - Aq, Aq);
                     const float amp = UNIB ? z.x * F : fmaf(-vab[k], z.y, z.x * v2[k]) * F;
-                    if (GRID) {
-                        // pole energy E = x_q + x_r - x_p (upp holds x_p here)
-                        const float E = (xr - mxq[k]) - upp;
-                        int bin = (int)floorf((E - A.e_min) * A.inv_h);
-                        bin = bin < 0 ? 0 : (bin >= A.nbins ? A.nbins - 1 : bin);
-                        const float d = E - (A.e_min + ((float)bin + 0.5f) * A.h);
-                        float mm[5];
-                        mm[0] = amp;
+                    // pole energy E = x_q + x_r - x_p (upp holds x_p here)
+                    const float E = (xr - mxq[k]) - upp;
+                    int bin = (int)floorf((E - A.e_min) * A.inv_h);
+                    bin = bin < 0 ? 0 : (bin >= A.nbins ? A.nbins - 1 : bin);
+                    const float d = E - (A.e_min + ((float)bin + 0.5f) * A.h);
+                    float mm[5];
+                    mm[0] = amp;
 #pragma unroll
-                        for (int mo = 1; mo < 5; ++mo) mm[mo] = mm[mo - 1] * d;
-                        // neighbouring lanes often share a bin: sum runs of equal
-                        // bins with shuffles (each lane adds the lanes up to the
-                        // end of its run), then one atomic per run and moment
-                        const int lane = tid & 31;
-                        const int bup = __shfl_up_sync(0xffffffffu, bin, 1);
-                        const bool head = lane == 0 || bup != bin;
-                        const unsigned heads = __ballot_sync(0xffffffffu, head);
-                        if (heads != 0xffffffffu) {
-                            const unsigned above = lane == 31 ? 0u : heads >> (lane + 1);
-                            const int end = above ? lane + __ffs(above) - 1 : 31;
+                    for (int mo = 1; mo < 5; ++mo) mm[mo] = mm[mo - 1] * d;
+                    // neighbouring lanes often share a bin: sum runs of equal
+                    // bins with shuffles (each lane adds the lanes up to the
+                    // end of its run), then one atomic per run and moment
+                    const int lane = tid & 31;
+                    const int bup = __shfl_up_sync(0xffffffffu, bin, 1);
+                    const bool head = lane == 0 || bup != bin;
+                    const unsigned heads = __ballot_sync(0xffffffffu, head);
+                    if (heads != 0xffffffffu) {
+                        const unsigned above = lane == 31 ? 0u : heads >> (lane + 1);
+                        const int end = above ? lane + __ffs(above) - 1 : 31;
 #pragma unroll
-                            for (int off = 1; off < 32; off <<= 1) {
+                        for (int off = 1; off < 32; off <<= 1) {
 #pragma unroll
-                                for (int mo = 0; mo < 5; ++mo) {
-                                    const float o = __shfl_down_sync(0xffffffffu, mm[mo], off);
-                                    if (lane + off <= end) mm[mo] += o;
-                                }
+                            for (int mo = 0; mo < 5; ++mo) {
+                                const float o = __shfl_down_sync(0xffffffffu, mm[mo], off);
+                                if (lane + off <= end) mm[mo] += o;
                             }
                         }
-                        if (head) {
+                    }
+                    if (head) {
 #pragma unroll
-                            for (int mo = 0; mo < 5; ++mo) atomicAdd(&hs[mo * A.nbins + bin], mm[mo]);
-                        }
-                    } else {
-                        // d+- = xi_j +- 2T - E with E = x_q + x_r - x_p
-                        const float dp = (upp + mxq[k]) - xr;
-                        const float dm = dp - A.fourT;
-                        const float den = fmaf(dp, dp, A.eta2) * fmaf(dm, dm, A.eta2);
-                        const float num = fmaf(-dp, dm, A.eta2);
-                        acc[k] = fmaf(amp * num, rcp_approx(den), acc[k]);
+                        for (int mo = 0; mo < 5; ++mo) atomicAdd(&hs[mo * A.nbins + bin], mm[mo]);
                     }
                 }
             }
         }
-#pragma unroll
-        for (int k = 0; k < SF_QPT; ++k) vsum += (double)acc[k];
     }
-    vsum *= fac;
-    if (GRID) {
-        __syncthreads();
-        double *H = A.hist + (long)jidx * 5 * A.nbins;
-        for (int i = tid; i < 5 * A.nbins; i += blockDim.x) {
-            const float v = hs[i];
-            if (v != 0.f) atomicAdd(&H[i], (double)v * fac);
-        }
-        return;
-    }
-    __shared__ double red[32];
-    double v = vsum;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    const int lane = tid & 31, warp = tid >> 5;
-    if (lane == 0) red[warp] = v;
     __syncthreads();
-    if (warp == 0) {
-        const int nw = blockDim.x >> 5;
-        v = lane < nw ? red[lane] : 0.0;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-        if (lane == 0) atomicAdd(&A.sig[jidx], v);
+    double *H = A.hist + (long)jidx * 5 * A.nbins;
+    for (int i = tid; i < 5 * A.nbins; i += blockDim.x) {
+        const float v = hs[i];
+        if (v != 0.f) atomicAdd(&H[i], (double)v * fac);
     }
 }
 
@@ -1163,8 +1130,8 @@ static qpfrg_status launch_sigma_fast(qpfrg_ctx *c, double T, const double *d_V,
     Kern kern;
     if (grid_mode)
         kern = c->pb.tp == 0.0
-                   ? (unib ? sigma_grid_fast_kernel<true, true, true> : sigma_grid_fast_kernel<true, false, true>)
-                   : (unib ? sigma_grid_fast_kernel<false, true, true> : sigma_grid_fast_kernel<false, false, true>);
+                   ? (unib ? sigma_grid_fast_kernel<true, true> : sigma_grid_fast_kernel<true, false>)
+                   : (unib ? sigma_grid_fast_kernel<false, true> : sigma_grid_fast_kernel<false, false>);
     else
         kern = c->pb.tp == 0.0 ? (unib ? sigma_fast_kernel<true, true> : sigma_fast_kernel<true, false>)
                                : (unib ? sigma_fast_kernel<false, true> : sigma_fast_kernel<false, false>);
