@@ -50,12 +50,31 @@ SIGMA_FP32_PER_PAIR, SIGMA_MUFU_PER_PAIR = 48, 4
 FP32_LANES_PER_SM, MUFU_PER_SM, N_SM = 128, 16, 152
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
-# ncu capture of the bench workload, valid while the kernel's source file is
-# unchanged (SHA-256 recorded with the capture); profiles/ holds the summary.
+# ncu capture of the bench workload, valid while the kernel's own source (its
+# definition, from the template line to the matching brace) is unchanged: the
+# SHA-256 of that text is recorded with the capture; profiles/ holds the summary.
 TRAFFIC = {
     ("sigma_z", "np96_n32"): {"bytes": 25.50e6, "source": "paper_2005_00827_gb300/csrc/sigma.cu",
-                              "sha256": "6b96a2590b75a186ce54bb535405057dbfc45623230bf65c02ab5cd0c6302d9e"},
+                              "kernel": "sigma_fast_kernel",
+                              "sha256": "9e581f5914f06d32f157911775e8be070a3c341dab66351fa1a49db3fb89b946"},
 }
+
+
+def kernel_text(path, name):
+    """Source of the __global__ function `name` in `path`: from the line before
+    its signature (the template line) to the brace that closes its body."""
+    src = open(path).read()
+    i = src.find(f" {name}(")
+    if i < 0:
+        return None
+    start = src.rfind("\n", 0, src.rfind("\n", 0, i)) + 1
+    j = src.find("{", i)
+    depth = 0
+    for k in range(j, len(src)):
+        depth += {"{": 1, "}": -1}.get(src[k], 0)
+        if depth == 0:
+            return src[start:k + 1]
+    return None
 
 
 def traffic_bytes(kernel, workload):
@@ -64,11 +83,12 @@ def traffic_bytes(kernel, workload):
     if t is None:
         return None
     try:
-        with open(os.path.join(ROOT, t["source"]), "rb") as f:
-            digest = hashlib.sha256(f.read()).hexdigest()
+        text = kernel_text(os.path.join(ROOT, t["source"]), t["kernel"])
     except OSError:
         return None
-    return t["bytes"] if digest == t["sha256"] else None
+    if text is None:
+        return None
+    return t["bytes"] if hashlib.sha256(text.encode()).hexdigest() == t["sha256"] else None
 
 
 def load_peaks():
