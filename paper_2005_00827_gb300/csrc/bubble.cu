@@ -183,6 +183,78 @@ struct alignas(4 * sizeof(R)) Quad {
     R x, y, z, w;
 };
 
+// Offsets in the A-operand tile layout (tile_index with 128 rows per tile):
+// row part (tile row block and position in the core matrix) and k part.
+__device__ __forceinline__ long tile_row_base(long r, long Kp)
+{
+    return (((r >> 7) * (Kp >> 6)) << 13) + (((r & 127) >> 3) << 6) + ((r & 7) << 3);
+}
+__device__ __forceinline__ long tile_k_off(long k) { return ((k >> 6) << 13) + (((k & 63) >> 3) << 10) + (k & 7); }
+
+__device__ __forceinline__ void split_bf16x2(float x0, float x1, __nv_bfloat162 &hi, __nv_bfloat162 &lo)
+{
+    hi = __floats2bfloat162_rn(x0, x1);
+    lo = __floats2bfloat162_rn(x0 - __low2float(hi), x1 - __high2float(hi));
+}
+
+// Write-out of one transfer's row of N bins as formed tensor-core operands
+// (BF16 hi/lo in tiles); the row is cleared.  Each lane takes two adjacent
+// partner patches b, b+1 (N is a multiple of 4 here), which are adjacent in k
+// = a N + b and so share a 4-byte bf16x2 store; the vertex factors that are
+// uniform over the row are read once.
+template <bool PP, bool TFLOW>
+__device__ __forceinline__ void form_row(const BubbleArgs<float> &A, float *row, const float *Zs, float Za, int Q,
+                                         int a, int lane)
+{
+    const int N = A.pb.N;
+    const long NN = (long)N * N;
+    const long col0 = (long)a * N;
+    auto weight = [&](float Zb) { return TFLOW ? Za * Zb : A.g * Za * Zb * (Za + Zb); };
+    if (PP) {
+        const float fv = A.Vf[(long)Q * N + a];
+        const long rb = tile_row_base(Q, A.Kp);
+        for (int b = 2 * lane; b < N; b += 64) {
+            const float2 v = *reinterpret_cast<const float2 *>(row + b);
+            *reinterpret_cast<float2 *>(row + b) = make_float2(0.f, 0.f);
+            const float2 z = *reinterpret_cast<const float2 *>(Zs + b);
+            const float t0 = v.x * weight(z.x) * fv, t1 = v.y * weight(z.y) * fv;
+            __nv_bfloat162 hi, lo;
+            split_bf16x2(t0, t1, hi, lo);
+            const long o = rb + tile_k_off(col0 + b);
+            *reinterpret_cast<__nv_bfloat162 *>(A.App[0] + o) = hi;
+            *reinterpret_cast<__nv_bfloat162 *>(A.App[1] + o) = lo;
+        }
+    } else {
+        const int x = Q / N, y = Q - x * N;                  // Q = k_F(x) - k_F(y)
+        const long rcr = (long)y * N + x;                     // cr row (j,l) = (y,x)
+        const float v_ial = A.Vf[((long)x * N + a) * N + y];
+        const float v_ail = A.Vf[((long)a * N + x) * N + y];
+        const float f1 = 2.f * v_ial - v_ail, f2 = -v_ial;
+        const long rb_cr = tile_row_base(rcr, A.Kp), rb_d = tile_row_base(Q, A.Kpd);
+        const float *vt = A.VT + rcr * N;
+        for (int b = 2 * lane; b < N; b += 64) {
+            const float2 v = *reinterpret_cast<const float2 *>(row + b);
+            *reinterpret_cast<float2 *>(row + b) = make_float2(0.f, 0.f);
+            const float2 z = *reinterpret_cast<const float2 *>(Zs + b);
+            const float t0 = v.x * weight(z.x), t1 = v.y * weight(z.y);
+            const float2 c = *reinterpret_cast<const float2 *>(vt + b);
+            __nv_bfloat162 hi, lo;
+            split_bf16x2(t0 * c.x, t1 * c.y, hi, lo);
+            const long ocr = rb_cr + tile_k_off(col0 + b);
+            *reinterpret_cast<__nv_bfloat162 *>(A.Acr[0] + ocr) = hi;
+            *reinterpret_cast<__nv_bfloat162 *>(A.Acr[1] + ocr) = lo;
+            split_bf16x2(t0 * f1, t1 * f1, hi, lo);
+            const long od = rb_d + tile_k_off(col0 + b);
+            *reinterpret_cast<__nv_bfloat162 *>(A.Ad[0] + od) = hi;
+            *reinterpret_cast<__nv_bfloat162 *>(A.Ad[1] + od) = lo;
+            split_bf16x2(t0 * f2, t1 * f2, hi, lo);
+            const long od2 = rb_d + tile_k_off(NN + col0 + b);
+            *reinterpret_cast<__nv_bfloat162 *>(A.Ad[0] + od2) = hi;
+            *reinterpret_cast<__nv_bfloat162 *>(A.Ad[1] + od2) = lo;
+        }
+    }
+}
+
 // Kernel body for one transfer family (PP: particle-particle, else
 // particle-hole) and one regulator (TFLOW: temperature flow, else
 // interaction flow), both fixed at compile time.
@@ -333,41 +405,16 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
             if (head && key >= 0) atomicAdd(&row[key], v);
             __syncwarp();
             const int Q = Q0 + h * nwarp;
-            for (int b = lane; b < N; b += 32) {
-                const R v = row[b];
-                row[b] = R(0);
-                const R Zb = Zs[b];
-                const R s = tflow ? Za * Zb : A.g * Za * Zb * (Za + Zb);
-                if constexpr (!FORM) {
+            if constexpr (!FORM) {
+                for (int b = lane; b < N; b += 32) {
+                    const R v = row[b];
+                    row[b] = R(0);
+                    const R Zb = Zs[b];
+                    const R s = tflow ? Za * Zb : A.g * Za * Zb * (Za + Zb);
                     A.B[(((long)fam * NN + Q) * N + a) * (long)N + b] = v * s;
-                } else {
-                    const float bt = (float)(v * s);
-                    const long col = (long)a * N + b;
-                    __nv_bfloat16 hi, lo;
-                    if (pp) {
-                        split_bf16(bt * A.Vf[(long)Q * N + a], hi, lo);
-                        const long o = tile_index(Q, col, 128, A.Kp);
-                        A.App[0][o] = hi;
-                        A.App[1][o] = lo;
-                    } else {
-                        const int x = Q / N, y = Q - (Q / N) * N;          // Q = k_F(x) - k_F(y)
-                        const long rcr = (long)y * N + x;                 // cr row (j,l) = (y,x)
-                        split_bf16(bt * A.VT[rcr * N + b], hi, lo);
-                        const long ocr = tile_index(rcr, col, 128, A.Kp);
-                        A.Acr[0][ocr] = hi;
-                        A.Acr[1][ocr] = lo;
-                        const float v_ial = A.Vf[((long)x * N + a) * N + y];
-                        const float v_ail = A.Vf[((long)a * N + x) * N + y];
-                        split_bf16(bt * (2.f * v_ial - v_ail), hi, lo);
-                        const long od = tile_index(Q, col, 128, A.Kpd);
-                        A.Ad[0][od] = hi;
-                        A.Ad[1][od] = lo;
-                        split_bf16(-bt * v_ial, hi, lo);
-                        const long od2 = tile_index(Q, NN + col, 128, A.Kpd);
-                        A.Ad[0][od2] = hi;
-                        A.Ad[1][od2] = lo;
-                    }
                 }
+            } else {
+                form_row<PP, TFLOW>(A, row, Zs, Za, Q, a, lane);
             }
             __syncwarp();
         }
