@@ -307,6 +307,24 @@ def run_qpfrg(args):
                 f"({peak_kind} max clock), {fp32} FP32 instr / {FP32_LANES_PER_SM} lanes, "
                 f"{mufu} MUFU / {MUFU_PER_SM} per SM"}
 
+    # the right-hand side's own kernels against their bounds (per RHS of the step)
+    rhs_roof = {}
+    if "bubble" in kern:
+        evals = 2.0 * N * N * M
+        b_s = kern["bubble"][0] / kern["bubble"][1] / 1e3
+        b_peak = N_SM * clk_mhz * 1e6 / max(BUBBLE_FP32_PER_EVAL / FP32_LANES_PER_SM, BUBBLE_MUFU_PER_EVAL / MUFU_PER_SM)
+        rhs_roof["bubble"] = {"bound": "alu", "achieved": evals / b_s / 1e9, "peak": b_peak / 1e9, "unit": "Geval/s",
+                              "frac": evals / b_s / b_peak, "partner_map_gbs": 2.0 * N * N * M / b_s / 1e9}
+    tc = [k for k in ("tc_gemm_pp", "tc_gemm_cr", "tc_gemm_d") if k in kern]
+    if len(tc) == 3:
+        # formed A operands, BF16 hi + lo (4 B per element), read once per RHS
+        a_bytes = 4.0 * (2 * N ** 4 + 2 * N ** 4)
+        t_s = sum(kern[k][0] / kern[k][1] for k in tc) / 1e3
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        rhs_roof["tc_gemm"] = {"bound": "hbm", "achieved": a_bytes / t_s / 1e9, "peak": hbm, "unit": "GB/s",
+                               "frac": a_bytes / t_s / 1e9 / hbm, "bytes_per_rhs": a_bytes,
+                               "peak_source": f"{peak_kind} hbm_gbs"}
+
     line = {
         "metric": METRIC.format(N=N), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -320,7 +338,7 @@ def run_qpfrg(args):
         "e2e": e2e, "gpu_launches": int(sum(v[1] for v in prof.values())),
         "kernels_ms": {k: round(v[0], 3) for k, v in kern.items()},
         "kernel_launches": {k: v[1] for k, v in kern.items()},
-        "roofline": roof, "clocks": clk, **extra,
+        "roofline": roof, "rhs_roofline": rhs_roof, "clocks": clk, **extra,
     }
     ctx.close()
     if not args.no_flows:

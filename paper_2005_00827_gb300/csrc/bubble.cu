@@ -157,9 +157,11 @@ __device__ __forceinline__ R loop_g(bool pp, R xp, R fp, R fcp, R xq, R invT, R 
 // Lane layout of a patch's fine points (local index t n_r + s, t angular,
 // s radial): a warp row holds 32 points, lanes along the radius.  With
 // n_r >= 32 a row is 32 radii of one angle (radial chunks of 32, all angles of
-// a chunk before the next chunk); with n_r < 32 it is 32 / lr angles of lr
-// radii, lr = n_r rounded up to a power of two.  Consecutive rows of a lane
-// are angular neighbours at one radius, whose partners mostly share a patch.
+// a chunk before the next chunk); with n_r < 32 the warp splits into 32 / lr
+// groups of lr lanes (lr = n_r rounded up to a power of two), group g taking
+// the g-th contiguous block of per_chunk angles.  Either way consecutive rows
+// of a lane are adjacent angles at one radius, whose partners mostly share a
+// patch (runs are long, flushes rare).
 struct LaneMap {
     int lr, apr, nchunk, per_chunk;   // lanes per angle, angles per row, radial chunks, rows per chunk
     __host__ __device__ LaneMap(int nt, int nr)
@@ -316,7 +318,7 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
     const LaneMap lm(nt, nr);
     const TransferTable<R> &Qt = pp ? A.qpp : A.qph;
     const int dt = lane / lm.lr, sl = lane & (lm.lr - 1);
-    const int stride = lm.apr * nr;                    // local index step between a lane's rows
+    const int stride = nr;                             // local index step between a lane's rows
     // Each warp carries two transfers at once (independent chains for the
     // schedulers; one shared-memory read of a point serves both).
     for (int Q0 = q0 + warp; Q0 < q1; Q0 += 2 * nwarp) {
@@ -338,9 +340,10 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
         }
         for (int ch = 0; ch < lm.nchunk; ++ch) {
             const int s = ch * 32 + sl;
-            // rows of this lane in the chunk: t = r apr + dt < n_theta
-            const int nrow = (s < nr && dt < nt) ? (nt - dt + lm.apr - 1) / lm.apr : 0;
-            const int li0 = dt * nr + s;
+            // rows of this lane in the chunk: t = dt per_chunk + r < n_theta
+            const int t0 = dt * lm.per_chunk;
+            const int nrow = (s < nr && t0 < nt) ? min(lm.per_chunk, nt - t0) : 0;
+            const int li0 = t0 * nr + s;
             // partner bytes of the next four rows are loaded one group ahead
             int bb[2][4], bn[2][4];
 #pragma unroll
