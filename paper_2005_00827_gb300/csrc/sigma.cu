@@ -506,13 +506,13 @@ struct SfSmem {
 __host__ __device__ inline SfSmem sf_smem_layout(int pch, int nbins = 0)
 {
     SfSmem L;
-    L.rA = 0;
-    L.rB = L.rA + (size_t)16 * pch;
-    L.cz = L.rB + (size_t)16 * pch;
+    L.rA = 0;                                  // pch + 1 records: room for a pad record
+    L.rB = L.rA + (size_t)16 * (pch + 1);
+    L.cz = L.rB + (size_t)16 * (pch + 1);
     L.ray = L.cz + (size_t)16 * SF_SLOTS;
     L.cd = L.ray + (size_t)8 * SF_SLOTS;
     L.rC = (L.cd + (size_t)4 * SF_SLOTS + 15) / 16 * 16;
-    L.tab = (L.rC + (size_t)4 * pch + 15) / 16 * 16;
+    L.tab = (L.rC + (size_t)4 * (pch + 1) + 15) / 16 * 16;
     L.hist = L.tab + ((size_t)(kProjW + 1) * kProjStride + 15) / 16 * 16;
     L.total = L.hist + (size_t)5 * 4 * nbins;
     return L;
@@ -631,6 +631,11 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
             rA[i] = make_float4(k4.x, k4.z, kcs.x * cpx - kcs.y * spx, kcs.y * cpx + kcs.x * spx);
             rB[i] = make_float4(kcs.z * cpy - kcs.w * spy, kcs.w * cpy + kcs.z * spy, wp * fp, wp * fcp);
             rC[i] = xj + xp + A.twoT;
+            if (i == cnt - 1 && (cnt & 1)) {   // pad: the same point with weight 0
+                rA[i + 1] = rA[i];
+                rB[i + 1] = make_float4(rB[i].x, rB[i].y, 0.f, 0.f);
+                rC[i + 1] = rC[i];
+            }
         }
     };
     const bool one_pass = P <= pch;
@@ -686,59 +691,74 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
                 stage(p0, cnt);
                 __syncthreads();
             }
-#pragma unroll 2
-            for (int i = 0; i < cnt; ++i) {
-                const float4 ra = rA[i], rb = rB[i];
-                const float upp = rC[i];
-                int c[SF_QPT];
-                float x[SF_QPT], y[SF_QPT];
-                bool slow_any = false;
+            // two records per iteration: the patches of all 2 x SF_QPT pairs
+            // first, one rarely taken branch for the guarded ones, then the
+            // arithmetic of all of them (one large block for the scheduler);
+            // an odd count reads the zero-weight pad record after the last one
+            for (int i = 0; i < cnt; i += 2) {
+                float4 ra[2], rb[2];
+                float upp[2];
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    ra[r] = rA[i + r];
+                    rb[r] = rB[i + r];
+                    upp[r] = rC[i + r];
+                }
+                int c[2][SF_QPT];
+                float x[2][SF_QPT], y[2][SF_QPT];
                 unsigned slow_mask = 0;
 #pragma unroll
-                for (int k = 0; k < SF_QPT; ++k) {
-                    x[k] = fold1(ra.x - qx[k]);
-                    y[k] = fold1(ra.y - qy[k]);
-                    const bool edge = fmaxf(fabsf(x[k]), fabsf(y[k])) > 3.14159265f - 4e-6f;
-                    const float sx = fmaf(x[k], kW, 12583040.f);   // 1.5 * 2^23 + W/2: low bits = cell index
-                    const float sy = fmaf(y[k], kW, 12583040.f);
-                    unsigned idx = (unsigned)__float_as_int(sy) * (unsigned)kProjStride +
-                                   (unsigned)__float_as_int(sx) - 0x4B400000u * (unsigned)(kProjStride + 1);
-                    idx = min(idx, tab_last);
-                    const int e = tab[idx];
-                    // e = 255 (cell at the origin) reads the zero ray 256: cr = 0 takes the slow path
-                    const float2 rr = ray[e + 1];
-                    const float cr = rr.x * y[k] - rr.y * x[k];
-                    c[k] = e + (cr >= 0.f ? 1 : 0);
-                    const bool slow = edge || fabsf(cr) < 4e-6f;
-                    slow_mask |= slow ? 1u << k : 0u;
-                    slow_any = slow_any || slow;
-                }
-                if (slow_any) {
+                for (int r = 0; r < 2; ++r)
 #pragma unroll
-                    for (int k = 0; k < SF_QPT; ++k)
-                        if (slow_mask & (1u << k)) {
-                            const bool edge = fmaxf(fabsf(x[k]), fabsf(y[k])) > 3.14159265f - 4e-6f;
-                            c[k] = sf_slow_patch(A, jidx, j, a * PP + p0 + i, qi[k], x[k], y[k], edge, A.bnd);
-                        }
+                    for (int k = 0; k < SF_QPT; ++k) {
+                        x[r][k] = fold1(ra[r].x - qx[k]);
+                        y[r][k] = fold1(ra[r].y - qy[k]);
+                        const bool edge = fmaxf(fabsf(x[r][k]), fabsf(y[r][k])) > 3.14159265f - 4e-6f;
+                        const float sx = fmaf(x[r][k], kW, 12583040.f);   // 1.5 * 2^23 + W/2: low bits = cell index
+                        const float sy = fmaf(y[r][k], kW, 12583040.f);
+                        unsigned idx = (unsigned)__float_as_int(sy) * (unsigned)kProjStride +
+                                       (unsigned)__float_as_int(sx) - 0x4B400000u * (unsigned)(kProjStride + 1);
+                        idx = min(idx, tab_last);
+                        const int e = tab[idx];
+                        // e = 255 (cell at the origin) reads the zero ray 256: cr = 0 takes the slow path
+                        const float2 rr = ray[e + 1];
+                        const float cr = rr.x * y[r][k] - rr.y * x[r][k];
+                        c[r][k] = e + (cr >= 0.f ? 1 : 0);
+                        // the pad record (weight 0) keeps its table patch
+                        const bool slow = (edge || fabsf(cr) < 4e-6f) && i + r < cnt;
+                        slow_mask |= slow ? 1u << (r * SF_QPT + k) : 0u;
+                    }
+                if (slow_mask) {
+#pragma unroll
+                    for (int r = 0; r < 2; ++r)
+#pragma unroll
+                        for (int k = 0; k < SF_QPT; ++k)
+                            if (slow_mask & (1u << (r * SF_QPT + k))) {
+                                const bool edge = fmaxf(fabsf(x[r][k]), fabsf(y[r][k])) > 3.14159265f - 4e-6f;
+                                c[r][k] = sf_slow_patch(A, jidx, j, a * PP + p0 + i + r, qi[k], x[r][k], y[r][k], edge,
+                                                        A.bnd);
+                            }
                 }
 #pragma unroll
-                for (int k = 0; k < SF_QPT; ++k) {
-                    const float4 z = cz[c[k]];
-                    const float crx = ra.z * cqx[k] + ra.w * sqx[k];
-                    const float cry = rb.x * cqy[k] + rb.y * sqy[k];
-                    float xr = fmaf(crx + cry, z.z, z.w);           // Z-scaled line energy of r
-                    if (!TP0) xr = fmaf(crx * cry, cd[c[k]], xr);
-                    const float fr = rcp_approx(1.f + ex2_approx(xr * A.cT));
-                    const float Aq = rb.z * fcqp[k], Bq = rb.w * fqp[k];
-                    const float F = fmaf(fr, Bq - Aq, Aq);
-                    const float amp = UNIB ? z.x * F : fmaf(-vab[k], z.y, z.x * v2[k]) * F;
-                    // d+- = xi_j +- 2T - E with E = x_q + x_r - x_p
-                    const float dp = (upp + mxq[k]) - xr;
-                    const float dm = dp - A.fourT;
-                    const float den = fmaf(dp, dp, A.eta2) * fmaf(dm, dm, A.eta2);
-                    const float num = fmaf(-dp, dm, A.eta2);
-                    acc[k] = fmaf(amp * num, rcp_approx(den), acc[k]);
-                }
+                for (int r = 0; r < 2; ++r)
+#pragma unroll
+                    for (int k = 0; k < SF_QPT; ++k) {
+                        const float4 z = cz[c[r][k]];
+                        const float crx = ra[r].z * cqx[k] + ra[r].w * sqx[k];
+                        const float cry = rb[r].x * cqy[k] + rb[r].y * sqy[k];
+                        float xr = fmaf(crx + cry, z.z, z.w);           // Z-scaled line energy of r
+                        if (!TP0) xr = fmaf(crx * cry, cd[c[r][k]], xr);
+                        const float fr = rcp_approx(1.f + ex2_approx(xr * A.cT));
+                        const float Aq = rb[r].z * fcqp[k], Bq = rb[r].w * fqp[k];
+                        const float F = fmaf(fr, Bq - Aq, Aq);
+                        const float amp = UNIB ? z.x * F : fmaf(-vab[k], z.y, z.x * v2[k]) * F;
+                        // d+- = xi_j +- 2T - E with E = x_q + x_r - x_p
+                        const float dp = (upp[r] + mxq[k]) - xr;
+                        const float dm = dp - A.fourT;
+                        const float den = fmaf(dp, dp, A.eta2) * fmaf(dm, dm, A.eta2);
+                        const float num = fmaf(-dp, dm, A.eta2);
+                        acc[k] = fmaf(amp * num, rcp_approx(den), acc[k]);
+                    }
             }
         }
 #pragma unroll
