@@ -357,29 +357,47 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
                         bn[h][k] = (r + 4 + k < nrow && h < nq) ? prow[h][li + (4 + k) * stride] : 0;
+                // two rows at a time: the loop kernels of 2 rows x 2 transfers
+                // first (a block of independent arithmetic), then the runs in
+                // row order
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if (r + k >= nrow) continue;
-                    const Quad<R> c4 = pc[li + k * stride], e4 = pe[li + k * stride];
+                for (int k0 = 0; k0 < 4; k0 += 2) {
+                    R vv[2][2];
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        if (h >= nq) break;
-                        // cos of the partner momentum components by angle addition:
-                        // pp: cos(Q - p) = cQ cp + sQ sp;  ph: cos(p + Q) = cp cQ - sp sQ
-                        const R cqx = pp ? cQx[h] * c4.x + sQx[h] * c4.y : c4.x * cQx[h] - c4.y * sQx[h];
-                        const R cqy = pp ? cQy[h] * c4.z + sQy[h] * c4.w : c4.z * cQy[h] - c4.w * sQy[h];
-                        // t' = 0 (the nested lattice): the product term drops at compile time
-                        R xq = TP0 ? R(-2) * t * (cqx + cqy) - mu : R(-2) * t * (cqx + cqy) - R(4) * tp * cqx * cqy - mu;
-                        const int b = bb[h][k];
-                        if (qp) xq *= Zs[b];
-                        const R v = e4.w * (tflow ? loop_T(pp, e4.x, e4.y, xq, invT, invT2, kexp, thrT)
-                                                  : loop_g(pp, e4.x, e4.y, e4.z, xq, invT, thrT));
-                        if (b != run_b[h]) {
-                            if (run_b[h] >= 0) atomicAdd(&rows[(2 * warp + h) * N + run_b[h]], run_v[h]);
-                            run_b[h] = b;
-                            run_v[h] = v;
-                        } else {
-                            run_v[h] += v;
+                    for (int kk = 0; kk < 2; ++kk) {
+                        const int k = k0 + kk;
+                        const bool ok = r + k < nrow;
+                        const int lk = ok ? li + k * stride : 0;
+                        const Quad<R> c4 = pc[lk], e4 = pe[lk];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            // cos of the partner momentum components by angle addition:
+                            // pp: cos(Q - p) = cQ cp + sQ sp;  ph: cos(p + Q) = cp cQ - sp sQ
+                            const R cqx = pp ? cQx[h] * c4.x + sQx[h] * c4.y : c4.x * cQx[h] - c4.y * sQx[h];
+                            const R cqy = pp ? cQy[h] * c4.z + sQy[h] * c4.w : c4.z * cQy[h] - c4.w * sQy[h];
+                            // t' = 0 (the nested lattice): the product term drops at compile time
+                            R xq = TP0 ? R(-2) * t * (cqx + cqy) - mu
+                                       : R(-2) * t * (cqx + cqy) - R(4) * tp * cqx * cqy - mu;
+                            if (qp) xq *= Zs[bb[h][k]];
+                            vv[kk][h] = e4.w * (tflow ? loop_T(pp, e4.x, e4.y, xq, invT, invT2, kexp, thrT)
+                                                      : loop_g(pp, e4.x, e4.y, e4.z, xq, invT, thrT));
+                        }
+                    }
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                        const int k = k0 + kk;
+                        if (r + k >= nrow) continue;
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            if (h >= nq) break;
+                            const int b = bb[h][k];
+                            if (b != run_b[h]) {
+                                if (run_b[h] >= 0) atomicAdd(&rows[(2 * warp + h) * N + run_b[h]], run_v[h]);
+                                run_b[h] = b;
+                                run_v[h] = vv[kk][h];
+                            } else {
+                                run_v[h] += vv[kk][h];
+                            }
                         }
                     }
                 }
