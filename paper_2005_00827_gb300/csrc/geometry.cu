@@ -17,26 +17,24 @@
 
 namespace qpfrg {
 
-// Cell table of the FP32 wedge projection (sigma.cu).  A folded momentum
-// (x, y) in [-pi, pi]^2 falls in cell K = round(x W / 2 pi + W/2) per
-// component, K in 0..W, which covers [-pi + (K - 1/2) h, -pi + (K + 1/2) h],
-// h = 2 pi / W.  The entry is the lower of the at most two wedges that the
-// cell, widened by 2e-5 on every side, touches (the ray between them is then
-// tested in the kernel), or 255 when it touches three or more wedges or
-// contains the origin.  The margin exceeds the 1.4e-6 position error of the
-// FP32 momenta and the 2e-7 cell-boundary error of the FP32 index.  Rows
-// (K_y) are kProjStride bytes apart.
+// Cell table of the FP32 wedge projection (sigma.cu).  The kernels hold a
+// folded momentum as fixed-point turns X = x 2^32 / 2 pi in [-2^31, 2^31), so
+// the cell of a component is its top byte: K = (X >> 24) + W/2, K in 0..W-1,
+// covering [-pi + K h, -pi + (K + 1) h), h = 2 pi / W (W = 256).  The entry is
+// the lower of the at most two wedges that the cell, widened by 2e-5 on every
+// side, touches (the ray between them is then tested in the kernel), or 255
+// when it touches three or more wedges or contains the origin.  The margin
+// exceeds the 2e-7 rad position error of the fixed-point momenta and of their
+// FP32 conversion.  Rows (K_y) are kProjStride bytes apart.
 static std::vector<uint8_t> build_proj_table(int N)
 {
-    const int W = kProjW, n = W + 1;
+    const int W = kProjW;
     const double h = kTwoPi / W, m = 2e-5, dth = kTwoPi / N;
-    std::vector<uint8_t> tab((size_t)n * kProjStride, 255);
-    for (int ky = 0; ky <= W; ++ky)
-        for (int kx = 0; kx <= W; ++kx) {
-            const double x0 = std::fmax(-kPi + (kx - 0.5) * h, -kPi) - m;
-            const double x1 = std::fmin(-kPi + (kx + 0.5) * h, kPi) + m;
-            const double y0 = std::fmax(-kPi + (ky - 0.5) * h, -kPi) - m;
-            const double y1 = std::fmin(-kPi + (ky + 0.5) * h, kPi) + m;
+    std::vector<uint8_t> tab((size_t)W * kProjStride, 255);
+    for (int ky = 0; ky < W; ++ky)
+        for (int kx = 0; kx < W; ++kx) {
+            const double x0 = -kPi + kx * h - m, x1 = -kPi + (kx + 1) * h + m;
+            const double y0 = -kPi + ky * h - m, y1 = -kPi + (ky + 1) * h + m;
             if (x0 <= 0.0 && x1 >= 0.0 && y0 <= 0.0 && y1 >= 0.0) continue;
             // the angular extent of a rectangle clear of the origin is spanned
             // by its corners; unwrap them about the first corner

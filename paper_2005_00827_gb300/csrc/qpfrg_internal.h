@@ -16,7 +16,8 @@ namespace qpfrg {
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kTwoPi = 2.0 * kPi;
-// cells per 2 pi of the FP32 wedge-projection table (a power of two)
+// cells per 2 pi of the FP32 wedge-projection table (rows = columns = kProjW;
+// 256: the cell index of a fixed-point coordinate is its top byte)
 constexpr int kProjW = 256;
 // row stride of that table in bytes: 65 words, so adjacent rows start in adjacent banks
 constexpr int kProjStride = 260;
@@ -144,7 +145,7 @@ struct qpfrg_ctx {
     float *d_qxl = nullptr, *d_qyl = nullptr;   // M: FP32 residuals kx - (float)kx, ky - (float)ky
     float4 *d_kp = nullptr;      // [target][p]: k_j + p as FP32 hi/lo pairs (self-energy scratch)
     float4 *d_kcs = nullptr;     // [target]: cos/sin of k_j (self-energy scratch)
-    uint8_t *d_ptab = nullptr;   // (W+1) rows x kProjStride bytes: cell table of the FP32 wedge projection (wedge mode, N <= 254)
+    uint8_t *d_ptab = nullptr;   // W rows x kProjStride bytes: cell table of the FP32 wedge projection (wedge mode, N <= 254)
     double *d_Qpp = nullptr, *d_Qph = nullptr;  // N^2 x 2 transfer momenta (FP64)
     uint8_t *d_part = nullptr;   // 2 x N^2 x M partner patches (pp family, then ph)
 

@@ -432,18 +432,24 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
 // FP32 chord-slope kernel of the wedge grid (the flow's self-energy).
 //
 // Same sum as sigma_kernel<float,false>, arranged for instruction count:
-// * the patch c of r = k_j + p - q comes from a shared-memory cell table over
-//   the folded zone (one byte per cell: the lower of the at most two wedges
-//   the cell touches) and one FP32 test against the ray between them; cells
-//   near the origin, points within 4e-6 of a ray and points within 4e-6 of
-//   the zone edge take the guarded paths of sigma_kernel (float-float rays,
-//   exact FP64 projection), so every patch decision equals the FP64 one;
+// * momenta are fixed-point turns (angle_fx), so r = k_j + p - q folds by
+//   integer wrap-around; the patch c of r comes from a shared-memory cell
+//   table over the folded zone indexed by the top bytes (one byte per cell:
+//   the lower of the at most two wedges the cell touches) and one FP32 test
+//   against the ray between them; cells near the origin, points within 4e-6
+//   of a ray and points within 4e-6 of the zone edge take the guarded paths
+//   of sigma_kernel (float-float rays, exact FP64 projection), so every patch
+//   decision equals the FP64 one;
 // * f_r enters only through F = A + f_r (B - A) with A = w_p f_p (1 - f_q),
 //   B = w_p (1 - f_p) f_q (times Z_a Z_b w_q), so one exp2 and one
 //   reciprocal give it;
-// * per patch c the table cz holds (Z_c, Z_c V[j][a][c], -2t l_c, -mu l_c),
-//   l_c = Z_c for quasi-particle lines (else 1), so the line energy of r
-//   (Z-scaled) is one FMA from cos(r_x) + cos(r_y);
+// * per patch c the table cz holds (Z_c, Z_c V[j][a][c], -2t l_c, -mu l_c)
+//   times (1, 1, log2(e)/T, log2(e)/T), l_c = Z_c for quasi-particle lines
+//   (else 1), so the line energy of r (Z-scaled, in units of T/log2(e)) is one
+//   FMA from cos(r_x) + cos(r_y) and feeds exp2 directly;
+// * with d0 = xi_j - E the chord term is -u / (u^2 + 4 eta^2 d0^2),
+//   u = d0^2 - 4T^2 - eta^2 (the product of the two Lorentzian denominators
+//   written out);
 // * each thread owns SF_QPT loop points q, so a record of p read from shared
 //   memory serves SF_QPT pairs; the lanes of a warp own angular neighbours at
 //   one radius (angular-minor order), so their r lie on a short arc and their
@@ -466,6 +472,7 @@ struct SigmaFastArgs {
     const int *jlist;
     double *sig;
     float t, tp, mu, eta2, invT, cT, twoT, fourT;   // cT = log2(e) / T
+    float tln2, kchord, eta2x4;                     // T ln 2, 4 T^2 + eta^2, 4 eta^2
     float inv_dth, dth;                             // N / 2 pi, 2 pi / N
     int mirror;     // n_theta even and symmetric targets: 1 halves every mirror-line target,
                     // 2 all but the zone-edge ones (j a multiple of N/4)
@@ -491,11 +498,40 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
-// r -> r - 2 pi rint(r / 2 pi) on the FP32 pipes (|r| < 2^22)
-__device__ __forceinline__ float fold1(float r)
+// Fixed-point angles: a momentum component as turns x 2^32 in an int32, so
+// that the difference of two wraps into [-pi, pi) by itself (the zone fold,
+// ties at -pi) and the projection table's cell is the top byte.  The FP32
+// value of such a difference is off by at most 64 units (9.4e-8 rad).
+constexpr double kFxPerRad = 4294967296.0 / kTwoPi;
+constexpr float kRadPerFx = (float)(kTwoPi / 4294967296.0);
+// guard bands of the FP32 decisions in fixed-point units: 4e-6 rad from a ray
+// and from the zone edge
+constexpr float kFxGuard = (float)(4e-6 * kFxPerRad);
+constexpr float kFxEdge = (float)((kPi - 4e-6) * kFxPerRad);
+
+__device__ __forceinline__ int angle_fx(double r)
 {
-    const float s = fmaf(r, 0.159154943f, 12582912.f);
-    return fmaf(-6.28318531f, s - 12582912.f, r);
+    const double t = r * (1.0 / kTwoPi);
+    return (int)(unsigned)__double2ll_rn((t - rint(t)) * 4294967296.0);
+}
+
+// Table patch of r = (k+p) - q from fixed-point components: the lower wedge e
+// of the cell and the side of the ray between e and e + 1 (c = e or e + 1).
+// slow: within the guard band of that ray, of the zone edge, or in a cell of
+// three or more wedges (e = 255 reads the zero ray 256, cr = 0).  tabc points
+// at the cell of the origin; x, y come back in fixed-point units.
+__device__ __forceinline__ int fx_patch(int kpx, int kpy, int qx, int qy, const unsigned char *tabc,
+                                        const float2 *ray, float &x, float &y, bool &slow)
+{
+    const int X = (int)((unsigned)kpx - (unsigned)qx);
+    const int Y = (int)((unsigned)kpy - (unsigned)qy);
+    x = __int2float_rn(X);
+    y = __int2float_rn(Y);
+    const int e = tabc[(Y >> 24) * kProjStride + (X >> 24)];
+    const float2 rr = ray[e + 1];
+    const float cr = rr.x * y - rr.y * x;
+    slow = fmaxf(fabsf(x), fabsf(y)) > kFxEdge || fabsf(cr) < kFxGuard;
+    return e + (cr >= 0.f ? 1 : 0);
 }
 
 struct SfSmem {
@@ -513,7 +549,7 @@ __host__ __device__ inline SfSmem sf_smem_layout(int pch, int nbins = 0)
     L.cd = L.ray + (size_t)8 * SF_SLOTS;
     L.rC = (L.cd + (size_t)4 * SF_SLOTS + 15) / 16 * 16;
     L.tab = (L.rC + (size_t)4 * (pch + 1) + 15) / 16 * 16;
-    L.hist = L.tab + ((size_t)(kProjW + 1) * kProjStride + 15) / 16 * 16;
+    L.hist = L.tab + ((size_t)kProjW * kProjStride + 15) / 16 * 16;
     L.total = L.hist + (size_t)5 * 4 * nbins;
     return L;
 }
@@ -584,7 +620,7 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(A.ptab);
         uint4 *dst = reinterpret_cast<uint4 *>(tab);
-        const int n16 = ((kProjW + 1) * kProjStride + 15) / 16;
+        const int n16 = (kProjW * kProjStride + 15) / 16;
         for (int i = tid; i < n16; i += blockDim.x) dst[i] = src[i];
     }
     const double *Vja = A.V + ((long)j * N + a) * N;
@@ -597,9 +633,10 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
                 const float Zc = A.Z ? (float)A.Z[cc] : 1.f;
                 const float lz = qp ? Zc : 1.f;
                 const float vc = (float)Vja[cc];
-                cz[i] = UNIB ? make_float4(Zc * (2.f * vb * vb - vb * vc), 0.f, -2.f * A.t * lz, -A.mu * lz)
-                             : make_float4(Zc, Zc * vc, -2.f * A.t * lz, -A.mu * lz);
-                cd[i] = -4.f * A.tp * lz;
+                const float lzc = lz * A.cT;     // energies of r in units of T / log2(e)
+                cz[i] = UNIB ? make_float4(Zc * (2.f * vb * vb - vb * vc), 0.f, -2.f * A.t * lzc, -A.mu * lzc)
+                             : make_float4(Zc, Zc * vc, -2.f * A.t * lzc, -A.mu * lzc);
+                cd[i] = -4.f * A.tp * lzc;
                 const float4 bd = A.bnd[cc];
                 ray[i] = make_float2(bd.x, bd.z);
             } else {
@@ -616,8 +653,7 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
     const float4 kcs = A.kcs[jidx];
     const float xj = A.xij_f[j];
 
-    const unsigned tab_last = (kProjW + 1) * kProjStride - 1;
-    const float kW = (float)(kProjW / kTwoPi);
+    const unsigned char *tabc = tab + (kProjW / 2) * (kProjStride + 1);   // the cell of the origin
     // records of the loop points p0 .. p0 + cnt - 1 of patch a
     auto stage = [&](int p0, int cnt) {
         for (int i = tid; i < cnt; i += blockDim.x) {
@@ -628,9 +664,11 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
             float fp, fcp;
             sfermi(xp, A.invT, fp, fcp);
             const float wp = A.fine.w[p];
-            rA[i] = make_float4(k4.x, k4.z, kcs.x * cpx - kcs.y * spx, kcs.y * cpx + kcs.x * spx);
+            const int kx = angle_fx((double)k4.x + (double)k4.y), ky = angle_fx((double)k4.z + (double)k4.w);
+            rA[i] = make_float4(__int_as_float(kx), __int_as_float(ky), kcs.x * cpx - kcs.y * spx,
+                                kcs.y * cpx + kcs.x * spx);
             rB[i] = make_float4(kcs.z * cpy - kcs.w * spy, kcs.w * cpy + kcs.z * spy, wp * fp, wp * fcp);
-            rC[i] = xj + xp + A.twoT;
+            rC[i] = xj + xp;
             if (i == cnt - 1 && (cnt & 1)) {   // pad: the same point with weight 0
                 rA[i + 1] = rA[i];
                 rB[i + 1] = make_float4(rB[i].x, rB[i].y, 0.f, 0.f);
@@ -654,9 +692,9 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
             __syncthreads();
         }
         // the SF_QPT loop points q of this thread (an index past M gets weight 0)
-        float qx[SF_QPT], qy[SF_QPT], cqx[SF_QPT], sqx[SF_QPT], cqy[SF_QPT], sqy[SF_QPT];
+        float cqx[SF_QPT], sqx[SF_QPT], cqy[SF_QPT], sqy[SF_QPT];
         float fqp[SF_QPT], fcqp[SF_QPT], v2[SF_QPT], vab[SF_QPT], mxq[SF_QPT], acc[SF_QPT];
-        int qi[SF_QPT];
+        int qi[SF_QPT], qx[SF_QPT], qy[SF_QPT];
 #pragma unroll
         for (int k = 0; k < SF_QPT; ++k) {
             const int iq = blk * (256 * SF_QPT) + k * 256 + tid;   // angular-minor index
@@ -666,8 +704,8 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
             const int qq = b * PP + (rem % A.pb.n_theta) * A.pb.n_r + rem / A.pb.n_theta;
             qi[k] = qq;
             const float Zb = A.Z ? (float)A.Z[b] : 1.f;
-            qx[k] = A.fine.kx[qq];
-            qy[k] = A.fine.ky[qq];
+            qx[k] = angle_fx(A.kx64[qq]);
+            qy[k] = angle_fx(A.ky64[qq]);
             cqx[k] = A.fine.cx[qq];
             sqx[k] = A.fine.sx[qq];
             cqy[k] = A.fine.cy[qq];
@@ -705,39 +743,33 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
                     upp[r] = rC[i + r];
                 }
                 int c[2][SF_QPT];
-                float x[2][SF_QPT], y[2][SF_QPT];
-                unsigned slow_mask = 0;
+                bool slow_any = false;
 #pragma unroll
                 for (int r = 0; r < 2; ++r)
 #pragma unroll
                     for (int k = 0; k < SF_QPT; ++k) {
-                        x[r][k] = fold1(ra[r].x - qx[k]);
-                        y[r][k] = fold1(ra[r].y - qy[k]);
-                        const bool edge = fmaxf(fabsf(x[r][k]), fabsf(y[r][k])) > 3.14159265f - 4e-6f;
-                        const float sx = fmaf(x[r][k], kW, 12583040.f);   // 1.5 * 2^23 + W/2: low bits = cell index
-                        const float sy = fmaf(y[r][k], kW, 12583040.f);
-                        unsigned idx = (unsigned)__float_as_int(sy) * (unsigned)kProjStride +
-                                       (unsigned)__float_as_int(sx) - 0x4B400000u * (unsigned)(kProjStride + 1);
-                        idx = min(idx, tab_last);
-                        const int e = tab[idx];
-                        // e = 255 (cell at the origin) reads the zero ray 256: cr = 0 takes the slow path
-                        const float2 rr = ray[e + 1];
-                        const float cr = rr.x * y[r][k] - rr.y * x[r][k];
-                        c[r][k] = e + (cr >= 0.f ? 1 : 0);
-                        // the pad record (weight 0) keeps its table patch
-                        const bool slow = (edge || fabsf(cr) < 4e-6f) && i + r < cnt;
-                        slow_mask |= slow ? 1u << (r * SF_QPT + k) : 0u;
+                        float x, y;
+                        bool slow;
+                        c[r][k] = fx_patch(__float_as_int(ra[r].x), __float_as_int(ra[r].y), qx[k], qy[k], tabc, ray,
+                                           x, y, slow);
+                        slow_any |= slow;
                     }
-                if (slow_mask) {
+                if (slow_any) {
 #pragma unroll
                     for (int r = 0; r < 2; ++r)
 #pragma unroll
-                        for (int k = 0; k < SF_QPT; ++k)
-                            if (slow_mask & (1u << (r * SF_QPT + k))) {
-                                const bool edge = fmaxf(fabsf(x[r][k]), fabsf(y[r][k])) > 3.14159265f - 4e-6f;
-                                c[r][k] = sf_slow_patch(A, jidx, j, a * PP + p0 + i + r, qi[k], x[r][k], y[r][k], edge,
-                                                        A.bnd);
+                        for (int k = 0; k < SF_QPT; ++k) {
+                            float x, y;
+                            bool slow;
+                            fx_patch(__float_as_int(ra[r].x), __float_as_int(ra[r].y), qx[k], qy[k], tabc, ray, x, y,
+                                     slow);
+                            // the pad record (weight 0) keeps its table patch
+                            if (slow && i + r < cnt) {
+                                const bool edge = fmaxf(fabsf(x), fabsf(y)) > kFxEdge;
+                                c[r][k] = sf_slow_patch(A, jidx, j, a * PP + p0 + i + r, qi[k], x * kRadPerFx,
+                                                        y * kRadPerFx, edge, A.bnd);
                             }
+                        }
                 }
 #pragma unroll
                 for (int r = 0; r < 2; ++r)
@@ -746,23 +778,22 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
                         const float4 z = cz[c[r][k]];
                         const float crx = ra[r].z * cqx[k] + ra[r].w * sqx[k];
                         const float cry = rb[r].x * cqy[k] + rb[r].y * sqy[k];
-                        float xr = fmaf(crx + cry, z.z, z.w);           // Z-scaled line energy of r
+                        float xr = fmaf(crx + cry, z.z, z.w);           // Z-scaled line energy of r / (T ln 2)
                         if (!TP0) xr = fmaf(crx * cry, cd[c[r][k]], xr);
-                        const float fr = rcp_approx(1.f + ex2_approx(xr * A.cT));
+                        const float fr = rcp_approx(1.f + ex2_approx(xr));
                         const float Aq = rb[r].z * fcqp[k], Bq = rb[r].w * fqp[k];
                         const float F = fmaf(fr, Bq - Aq, Aq);
                         const float amp = UNIB ? z.x * F : fmaf(-vab[k], z.y, z.x * v2[k]) * F;
-                        // d+- = xi_j +- 2T - E with E = x_q + x_r - x_p
-                        const float dp = (upp[r] + mxq[k]) - xr;
-                        const float dm = dp - A.fourT;
-                        const float den = fmaf(dp, dp, A.eta2) * fmaf(dm, dm, A.eta2);
-                        const float num = fmaf(-dp, dm, A.eta2);
-                        acc[k] = fmaf(amp * num, rcp_approx(den), acc[k]);
+                        // d0 = xi_j - E, E = x_q + x_r - x_p
+                        const float d0 = fmaf(xr, -A.tln2, upp[r] + mxq[k]);
+                        const float u = fmaf(d0, d0, -A.kchord);
+                        const float den = fmaf(A.eta2x4 * d0, d0, u * u);
+                        acc[k] = fmaf(amp * u, rcp_approx(den), acc[k]);
                     }
             }
         }
 #pragma unroll
-        for (int k = 0; k < SF_QPT; ++k) vsum += (double)acc[k];
+        for (int k = 0; k < SF_QPT; ++k) vsum -= (double)acc[k];   // the chord term is -u / den
     }
     vsum *= fac;
     __shared__ double red[32];
@@ -829,7 +860,7 @@ __global__ void __launch_bounds__(256, 1) sigma_grid_fast_kernel(SigmaFastArgs A
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(A.ptab);
         uint4 *dst = reinterpret_cast<uint4 *>(tab);
-        const int n16 = ((kProjW + 1) * kProjStride + 15) / 16;
+        const int n16 = (kProjW * kProjStride + 15) / 16;
         for (int i = tid; i < n16; i += blockDim.x) dst[i] = src[i];
     }
     const double *Vja = A.V + ((long)j * N + a) * N;
@@ -860,8 +891,7 @@ __global__ void __launch_bounds__(256, 1) sigma_grid_fast_kernel(SigmaFastArgs A
     const float lza = qp ? Za : 1.f;
     const float4 kcs = A.kcs[jidx];
 
-    const unsigned tab_last = (kProjW + 1) * kProjStride - 1;
-    const float kW = (float)(kProjW / kTwoPi);
+    const unsigned char *tabc = tab + (kProjW / 2) * (kProjStride + 1);   // the cell of the origin
     // records of the loop points p0 .. p0 + cnt - 1 of patch a
     auto stage = [&](int p0, int cnt) {
         for (int i = tid; i < cnt; i += blockDim.x) {
@@ -872,7 +902,9 @@ __global__ void __launch_bounds__(256, 1) sigma_grid_fast_kernel(SigmaFastArgs A
             float fp, fcp;
             sfermi(xp, A.invT, fp, fcp);
             const float wp = A.fine.w[p];
-            rA[i] = make_float4(k4.x, k4.z, kcs.x * cpx - kcs.y * spx, kcs.y * cpx + kcs.x * spx);
+            const int kx = angle_fx((double)k4.x + (double)k4.y), ky = angle_fx((double)k4.z + (double)k4.w);
+            rA[i] = make_float4(__int_as_float(kx), __int_as_float(ky), kcs.x * cpx - kcs.y * spx,
+                                kcs.y * cpx + kcs.x * spx);
             rB[i] = make_float4(kcs.z * cpy - kcs.w * spy, kcs.w * cpy + kcs.z * spy, wp * fp, wp * fcp);
             rC[i] = xp;
         }
@@ -892,9 +924,9 @@ __global__ void __launch_bounds__(256, 1) sigma_grid_fast_kernel(SigmaFastArgs A
             __syncthreads();
         }
         // the SF_QPT loop points q of this thread (an index past M gets weight 0)
-        float qx[SF_QPT], qy[SF_QPT], cqx[SF_QPT], sqx[SF_QPT], cqy[SF_QPT], sqy[SF_QPT];
+        float cqx[SF_QPT], sqx[SF_QPT], cqy[SF_QPT], sqy[SF_QPT];
         float fqp[SF_QPT], fcqp[SF_QPT], v2[SF_QPT], vab[SF_QPT], mxq[SF_QPT];
-        int qi[SF_QPT];
+        int qi[SF_QPT], qx[SF_QPT], qy[SF_QPT];
 #pragma unroll
         for (int k = 0; k < SF_QPT; ++k) {
             const int iq = blk * (256 * SF_QPT) + k * 256 + tid;   // angular-minor index
@@ -904,8 +936,8 @@ __global__ void __launch_bounds__(256, 1) sigma_grid_fast_kernel(SigmaFastArgs A
             const int qq = b * PP + (rem % A.pb.n_theta) * A.pb.n_r + rem / A.pb.n_theta;
             qi[k] = qq;
             const float Zb = A.Z ? (float)A.Z[b] : 1.f;
-            qx[k] = A.fine.kx[qq];
-            qy[k] = A.fine.ky[qq];
+            qx[k] = angle_fx(A.kx64[qq]);
+            qy[k] = angle_fx(A.ky64[qq]);
             cqx[k] = A.fine.cx[qq];
             sqx[k] = A.fine.sx[qq];
             cqy[k] = A.fine.cy[qq];
@@ -938,20 +970,9 @@ __global__ void __launch_bounds__(256, 1) sigma_grid_fast_kernel(SigmaFastArgs A
                 unsigned slow_mask = 0;
 #pragma unroll
                 for (int k = 0; k < SF_QPT; ++k) {
-                    x[k] = fold1(ra.x - qx[k]);
-                    y[k] = fold1(ra.y - qy[k]);
-                    const bool edge = fmaxf(fabsf(x[k]), fabsf(y[k])) > 3.14159265f - 4e-6f;
-                    const float sx = fmaf(x[k], kW, 12583040.f);   // 1.5 * 2^23 + W/2: low bits = cell index
-                    const float sy = fmaf(y[k], kW, 12583040.f);
-                    unsigned idx = (unsigned)__float_as_int(sy) * (unsigned)kProjStride +
-                                   (unsigned)__float_as_int(sx) - 0x4B400000u * (unsigned)(kProjStride + 1);
-                    idx = min(idx, tab_last);
-                    const int e = tab[idx];
-                    // e = 255 (cell at the origin) reads the zero ray 256: cr = 0 takes the slow path
-                    const float2 rr = ray[e + 1];
-                    const float cr = rr.x * y[k] - rr.y * x[k];
-                    c[k] = e + (cr >= 0.f ? 1 : 0);
-                    const bool slow = edge || fabsf(cr) < 4e-6f;
+                    bool slow;
+                    c[k] = fx_patch(__float_as_int(ra.x), __float_as_int(ra.y), qx[k], qy[k], tabc, ray, x[k], y[k],
+                                    slow);
                     slow_mask |= slow ? 1u << k : 0u;
                     slow_any = slow_any || slow;
                 }
@@ -959,8 +980,9 @@ __global__ void __launch_bounds__(256, 1) sigma_grid_fast_kernel(SigmaFastArgs A
 #pragma unroll
                     for (int k = 0; k < SF_QPT; ++k)
                         if (slow_mask & (1u << k)) {
-                            const bool edge = fmaxf(fabsf(x[k]), fabsf(y[k])) > 3.14159265f - 4e-6f;
-                            c[k] = sf_slow_patch(A, jidx, j, a * PP + p0 + i, qi[k], x[k], y[k], edge, A.bnd);
+                            const bool edge = fmaxf(fabsf(x[k]), fabsf(y[k])) > kFxEdge;
+                            c[k] = sf_slow_patch(A, jidx, j, a * PP + p0 + i, qi[k], x[k] * kRadPerFx,
+                                                 y[k] * kRadPerFx, edge, A.bnd);
                         }
                 }
 #pragma unroll
@@ -1131,6 +1153,9 @@ static qpfrg_status launch_sigma_fast(qpfrg_ctx *c, double T, const double *d_V,
     A.cT = (float)(1.4426950408889634 / T);
     A.twoT = (float)(2.0 * T);
     A.fourT = (float)(4.0 * T);
+    A.tln2 = (float)(0.6931471805599453 * T);
+    A.kchord = (float)(4.0 * T * T + c->pb.eta * c->pb.eta);
+    A.eta2x4 = (float)(4.0 * c->pb.eta * c->pb.eta);
     A.inv_dth = (float)(c->pb.N / kTwoPi);
     A.dth = (float)(kTwoPi / c->pb.N);
     A.hist = hist;
