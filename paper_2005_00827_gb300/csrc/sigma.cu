@@ -450,8 +450,10 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
 // * with d0 = xi_j - E the chord term is -u / (u^2 + 4 eta^2 d0^2),
 //   u = d0^2 - 4T^2 - eta^2 (the product of the two Lorentzian denominators
 //   written out);
-// * each thread owns SF_QPT loop points q, so a record of p read from shared
-//   memory serves SF_QPT pairs; the lanes of a warp own angular neighbours at
+// * each thread owns SF_QPT = 2 loop points q, so a record of p read from
+//   shared memory serves two pairs, whose arithmetic runs as the two lanes of
+//   packed FP32x2 instructions (Fermi factor, weight, chord term, sum), and
+//   cos r_x, cos r_y of one pair form one packed FMA pair; the lanes of a warp own angular neighbours at
 //   one radius (angular-minor order), so their r lie on a short arc and their
 //   table cells, rays and patch slots mostly coincide (few bank conflicts,
 //   rare divergence into the guarded paths).
@@ -609,8 +611,8 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
     const SfSmem L = sf_smem_layout(pch);
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float4 *rA = reinterpret_cast<float4 *>(smem_raw + L.rA);   // (k+p)_x, (k+p)_y, cos, sin of (k+p)_x
-    float4 *rB = reinterpret_cast<float4 *>(smem_raw + L.rB);   // cos, sin of (k+p)_y, w_p f_p, w_p (1 - f_p)
+    float4 *rA = reinterpret_cast<float4 *>(smem_raw + L.rA);   // (k+p)_x, (k+p)_y (fixed point), cos of both
+    float4 *rB = reinterpret_cast<float4 *>(smem_raw + L.rB);   // sin of both, w_p f_p, w_p (1 - f_p)
     float4 *cz = reinterpret_cast<float4 *>(smem_raw + L.cz);
     float2 *ray = reinterpret_cast<float2 *>(smem_raw + L.ray);
     float *cd = reinterpret_cast<float *>(smem_raw + L.cd);     // -4 t' l_c
@@ -666,8 +668,8 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
             const float wp = A.fine.w[p];
             const int kx = angle_fx((double)k4.x + (double)k4.y), ky = angle_fx((double)k4.z + (double)k4.w);
             rA[i] = make_float4(__int_as_float(kx), __int_as_float(ky), kcs.x * cpx - kcs.y * spx,
-                                kcs.y * cpx + kcs.x * spx);
-            rB[i] = make_float4(kcs.z * cpy - kcs.w * spy, kcs.w * cpy + kcs.z * spy, wp * fp, wp * fcp);
+                                kcs.z * cpy - kcs.w * spy);
+            rB[i] = make_float4(kcs.y * cpx + kcs.x * spx, kcs.w * cpy + kcs.z * spy, wp * fp, wp * fcp);
             rC[i] = xj + xp;
             if (i == cnt - 1 && (cnt & 1)) {   // pad: the same point with weight 0
                 rA[i + 1] = rA[i];
@@ -680,6 +682,9 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
     if (one_pass) stage(0, P);
     __syncthreads();   // tables (and the records of a single pass) written
 
+    static_assert(SF_QPT == 2, "the loop points of a thread are the two lanes of the packed arithmetic");
+    const float2 one2 = make_float2(1.f, 1.f), ntln2 = make_float2(-A.tln2, -A.tln2);
+    const float2 nkchord = make_float2(-A.kchord, -A.kchord), eta2x4 = make_float2(A.eta2x4, A.eta2x4);
     double vsum = 0.0;
     // A.qb blocks of 256 SF_QPT loop points q per CTA reuse the staged tables
     for (int qb = 0; qb < A.qb; ++qb) {
@@ -692,8 +697,10 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
             __syncthreads();
         }
         // the SF_QPT loop points q of this thread (an index past M gets weight 0)
-        float cqx[SF_QPT], sqx[SF_QPT], cqy[SF_QPT], sqy[SF_QPT];
-        float fqp[SF_QPT], fcqp[SF_QPT], v2[SF_QPT], vab[SF_QPT], mxq[SF_QPT], acc[SF_QPT];
+        // (cos, sin) of (q_x, q_y) as pairs: cos r_x and cos r_y in one packed FMA
+        float2 cq[SF_QPT], sq[SF_QPT];
+        float fqp[SF_QPT], fcqp[SF_QPT], v2[SF_QPT], vab[SF_QPT], mxq[SF_QPT];
+        float2 acc = make_float2(0.f, 0.f);     // the SF_QPT = 2 loop points as the two lanes
         int qi[SF_QPT], qx[SF_QPT], qy[SF_QPT];
 #pragma unroll
         for (int k = 0; k < SF_QPT; ++k) {
@@ -706,10 +713,8 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
             const float Zb = A.Z ? (float)A.Z[b] : 1.f;
             qx[k] = angle_fx(A.kx64[qq]);
             qy[k] = angle_fx(A.ky64[qq]);
-            cqx[k] = A.fine.cx[qq];
-            sqx[k] = A.fine.sx[qq];
-            cqy[k] = A.fine.cy[qq];
-            sqy[k] = A.fine.sy[qq];
+            cq[k] = make_float2(A.fine.cx[qq], A.fine.cy[qq]);
+            sq[k] = make_float2(A.fine.sx[qq], A.fine.sy[qq]);
             const float xq = (qp ? Zb : 1.f) * A.fine.xi[qq];
             float fq, fcq;
             sfermi(xq, A.invT, fq, fcq);
@@ -719,7 +724,6 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
             vab[k] = (float)Vja[b];
             v2[k] = 2.f * vab[k] * vab[k];
             mxq[k] = -xq;
-            acc[k] = 0.f;
         }
 
         for (int p0 = 0; p0 < P; p0 += pch) {
@@ -771,29 +775,41 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
                             }
                         }
                 }
+                // the arithmetic: the two loop points q of a record as the
+                // lanes of packed FP32x2 operations where the operands pair up
 #pragma unroll
-                for (int r = 0; r < 2; ++r)
+                for (int r = 0; r < 2; ++r) {
+                    float2 xr, amp, sum;
+                    float2 fr, aq, dq;
 #pragma unroll
                     for (int k = 0; k < SF_QPT; ++k) {
                         const float4 z = cz[c[r][k]];
-                        const float crx = ra[r].z * cqx[k] + ra[r].w * sqx[k];
-                        const float cry = rb[r].x * cqy[k] + rb[r].y * sqy[k];
-                        float xr = fmaf(crx + cry, z.z, z.w);           // Z-scaled line energy of r / (T ln 2)
-                        if (!TP0) xr = fmaf(crx * cry, cd[c[r][k]], xr);
-                        const float fr = rcp_approx(1.f + ex2_approx(xr));
-                        const float Aq = rb[r].z * fcqp[k], Bq = rb[r].w * fqp[k];
-                        const float F = fmaf(fr, Bq - Aq, Aq);
-                        const float amp = UNIB ? z.x * F : fmaf(-vab[k], z.y, z.x * v2[k]) * F;
-                        // d0 = xi_j - E, E = x_q + x_r - x_p
-                        const float d0 = fmaf(xr, -A.tln2, upp[r] + mxq[k]);
-                        const float u = fmaf(d0, d0, -A.kchord);
-                        const float den = fmaf(A.eta2x4 * d0, d0, u * u);
-                        acc[k] = fmaf(amp * u, rcp_approx(den), acc[k]);
+                        // (cos r_x, cos r_y) by angle addition
+                        const float2 cr2 = __ffma2_rn(make_float2(ra[r].z, ra[r].w), cq[k],
+                                                      __fmul2_rn(make_float2(rb[r].x, rb[r].y), sq[k]));
+                        float x = fmaf(cr2.x + cr2.y, z.z, z.w);       // Z-scaled line energy of r / (T ln 2)
+                        if (!TP0) x = fmaf(cr2.x * cr2.y, cd[c[r][k]], x);
+                        const float ex = ex2_approx(x);
+                        const float a = rb[r].z * fcqp[k];
+                        const float d = fmaf(rb[r].w, fqp[k], -a);
+                        const float w = UNIB ? z.x : fmaf(-vab[k], z.y, z.x * v2[k]);
+                        const float sm = upp[r] + mxq[k];
+                        if (k == 0) { xr.x = x; fr.x = ex; aq.x = a; dq.x = d; amp.x = w; sum.x = sm; }
+                        else        { xr.y = x; fr.y = ex; aq.y = a; dq.y = d; amp.y = w; sum.y = sm; }
                     }
+                    const float2 g = __fadd2_rn(fr, one2);
+                    fr = make_float2(rcp_approx(g.x), rcp_approx(g.y));
+                    const float2 F = __ffma2_rn(fr, dq, aq);           // A + f_r (B - A)
+                    amp = __fmul2_rn(amp, F);
+                    // d0 = xi_j - E, E = x_q + x_r - x_p
+                    const float2 d0 = __ffma2_rn(xr, ntln2, sum);
+                    const float2 u = __ffma2_rn(d0, d0, nkchord);
+                    const float2 den = __ffma2_rn(__fmul2_rn(eta2x4, d0), d0, __fmul2_rn(u, u));
+                    acc = __ffma2_rn(__fmul2_rn(amp, u), make_float2(rcp_approx(den.x), rcp_approx(den.y)), acc);
+                }
             }
         }
-#pragma unroll
-        for (int k = 0; k < SF_QPT; ++k) vsum -= (double)acc[k];   // the chord term is -u / den
+        vsum -= (double)acc.x + (double)acc.y;   // the chord term is -u / den
     }
     vsum *= fac;
     __shared__ double red[32];
