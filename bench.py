@@ -43,20 +43,21 @@ WORKLOAD = "np96_n32"
 METRIC = "fRG RHS evaluations/s at N_p={N} (flow steps with Z feedback)"
 UNIT = "RHS/s"
 
-# Algorithmic work per loop-kernel evaluation and per self-energy pair (FP32
-# instructions and MUFU operations of the minimal formula; see the design notes).
-BUBBLE_FP32_PER_EVAL, BUBBLE_MUFU_PER_EVAL = 19, 2
-SIGMA_FP32_PER_PAIR, SIGMA_MUFU_PER_PAIR = 48, 4
-FP32_LANES_PER_SM, MUFU_PER_SM, N_SM = 128, 16, 152
+# Algorithmic work per loop-kernel evaluation and per self-energy pair: issue
+# slots of the minimal formula (every instruction, MUFU included; a packed
+# FP32x2 instruction counts one half per pair) and its MUFU operations.
+BUBBLE_ISSUE_PER_EVAL, BUBBLE_MUFU_PER_EVAL = 21, 2
+SIGMA_ISSUE_PER_PAIR, SIGMA_MUFU_PER_PAIR = 36, 3
+ISSUE_LANES_PER_SM, MUFU_PER_SM, N_SM = 128, 16, 152
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of the bench workload, valid while the kernel's own source (its
 # definition, from the template line to the matching brace) is unchanged: the
 # SHA-256 of that text is recorded with the capture; profiles/ holds the summary.
 TRAFFIC = {
-    ("sigma_z", "np96_n32"): {"bytes": 25.43e6, "source": "paper_2005_00827_gb300/csrc/sigma.cu",
+    ("sigma_z", "np96_n32"): {"bytes": 25.52e6, "source": "paper_2005_00827_gb300/csrc/sigma.cu",
                               "kernel": "sigma_fast_kernel",
-                              "sha256": "b39d6db3ae3a6551c755e731d76b71cbc11e4abda40e41fb8d5bca0c53ee0077"},
+                              "sha256": "29b95d430c2d02f590dbed387d2ff5e72646086a280942beea2a3af228a3d674"},
 }
 
 
@@ -288,15 +289,15 @@ def run_qpfrg(args):
     if dom in ("bubble", "sigma_z"):
         if dom == "bubble":
             units = 2.0 * N * N * M
-            fp32, mufu = BUBBLE_FP32_PER_EVAL, BUBBLE_MUFU_PER_EVAL
+            issue, mufu = BUBBLE_ISSUE_PER_EVAL, BUBBLE_MUFU_PER_EVAL
         else:
             # the flow evaluates the C4v-irreducible patches 0..N/8 only, and
             # the targets on mirror lines (0, and N/8 when 8 | N) over half of
             # the loop points p: count the reduced work
             mirror = (1.0 if N % 8 == 0 else 0.5) if n % 2 == 0 else 0.0
             units = (float(N // 8 + 1) - mirror) * M * M
-            fp32, mufu = SIGMA_FP32_PER_PAIR, SIGMA_MUFU_PER_PAIR
-        clk_per_unit = max(fp32 / FP32_LANES_PER_SM, mufu / MUFU_PER_SM)
+            issue, mufu = SIGMA_ISSUE_PER_PAIR, SIGMA_MUFU_PER_PAIR
+        clk_per_unit = max(issue / ISSUE_LANES_PER_SM, mufu / MUFU_PER_SM)
         peak_units = N_SM * clk_mhz * 1e6 / clk_per_unit
         avg_s = kern[dom][0] / kern[dom][1] / 1e3
         achieved = units / avg_s
@@ -304,7 +305,7 @@ def run_qpfrg(args):
                 "unit": "Geval/s" if dom == "bubble" else "Gpair/s", "frac": achieved / peak_units,
                 "traffic": traffic_bytes(dom, args.workload), "traffic_unit": "bytes per launch",
                 "peak_source": f"derived: {N_SM} SM x {clk_mhz:.0f} MHz "
-                f"({peak_kind} max clock), {fp32} FP32 instr / {FP32_LANES_PER_SM} lanes, "
+                f"({peak_kind} max clock), {issue} issue slots / {ISSUE_LANES_PER_SM} lanes, "
                 f"{mufu} MUFU / {MUFU_PER_SM} per SM"}
 
     # the right-hand side's own kernels against their bounds (per RHS of the step)
@@ -312,7 +313,7 @@ def run_qpfrg(args):
     if "bubble" in kern:
         evals = 2.0 * N * N * M
         b_s = kern["bubble"][0] / kern["bubble"][1] / 1e3
-        b_peak = N_SM * clk_mhz * 1e6 / max(BUBBLE_FP32_PER_EVAL / FP32_LANES_PER_SM, BUBBLE_MUFU_PER_EVAL / MUFU_PER_SM)
+        b_peak = N_SM * clk_mhz * 1e6 / max(BUBBLE_ISSUE_PER_EVAL / ISSUE_LANES_PER_SM, BUBBLE_MUFU_PER_EVAL / MUFU_PER_SM)
         rhs_roof["bubble"] = {"bound": "alu", "achieved": evals / b_s / 1e9, "peak": b_peak / 1e9, "unit": "Geval/s",
                               "frac": evals / b_s / b_peak, "partner_map_gbs": 2.0 * N * N * M / b_s / 1e9}
     tc = [k for k in ("tc_gemm_pp", "tc_gemm_cr", "tc_gemm_d") if k in kern]
