@@ -286,9 +286,14 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
     Quad<R> *pc = reinterpret_cast<Quad<R> *>(smem_raw);   // cos/sin of the point's components
     Quad<R> *pe = pc + P;                                   // x_p, f-terms, weight
     R *Zs = reinterpret_cast<R *>(pe + P);                  // N
-    R *rows = Zs + N;                                       // 2 nwarp x N (two transfers per warp)
+    // 2 nwarp rows (two transfers per warp) of N accumulators and a sink (slot
+    // N) for lanes without points, so that a change of partner is one add of
+    // the finished run; the row stride N + 2 is even, keeping every row 8-byte
+    // aligned for form_row's float2 reads
+    const int RS = N + 2;
+    R *rows = Zs + N;
     for (int i = tid; i < N; i += blockDim.x) Zs[i] = A.Z ? (R)A.Z[i] : R(1);
-    for (int i = tid; i < 2 * nwarp * N; i += blockDim.x) rows[i] = R(0);
+    for (int i = tid; i < 2 * nwarp * RS; i += blockDim.x) rows[i] = R(0);
     __syncthreads();
     const R Za = Zs[a];
     const R invT = A.invT, thrT = A.thr * A.T, invT2 = invT * invT;
@@ -319,6 +324,7 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
     const TransferTable<R> &Qt = pp ? A.qpp : A.qph;
     const int dt = lane / lm.lr, sl = lane & (lm.lr - 1);
     const int stride = nr;                             // local index step between a lane's rows
+    const bool vec4 = nt % 4 == 0 && lm.per_chunk % 4 == 0;
     // Each warp carries two transfers at once (independent chains for the
     // schedulers; one shared-memory read of a point serves both).
     for (int Q0 = q0 + warp; Q0 < q1; Q0 += 2 * nwarp) {
@@ -335,7 +341,7 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
             cQy[h] = Qt.cy[Q];
             sQy[h] = Qt.sy[Q];
             prow[h] = A.part + ((long)fam * NN + Q) * (long)M + (long)a * P;
-            run_b[h] = -1;
+            run_b[h] = N;
             run_v[h] = R(0);
         }
         for (int ch = 0; ch < lm.nchunk; ++ch) {
@@ -343,20 +349,37 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
             // rows of this lane in the chunk: t = dt per_chunk + r < n_theta
             const int t0 = dt * lm.per_chunk;
             const int nrow = (s < nr && t0 < nt) ? min(lm.per_chunk, nt - t0) : 0;
-            const int li0 = t0 * nr + s;
-            // partner bytes of the next four rows are loaded one group ahead
-            int bb[2][4], bn[2][4];
+            const int li0 = t0 * nr + s;     // staged point of the lane's first row
+            // partner bytes of the rows rr .. rr+3 of transfer h as one word
+            // (one aligned 4-byte load, coalesced over the warp's radii, where
+            // n_theta and the row blocks are multiples of 4), loaded one group ahead
+            auto part_word = [&](int h, int rr) -> unsigned {
+                if (rr >= nrow || h >= nq) return 0u;
+                if (vec4)
+                    return __ldg(reinterpret_cast<const unsigned *>(prow[h] + part_byte(t0 + rr, s, nt, nr)));
+                unsigned w = 0u;
+                for (int k = 0; k < 4; ++k)
+                    if (rr + k < nrow) w |= (unsigned)__ldg(prow[h] + part_byte(t0 + rr + k, s, nt, nr)) << (8 * k);
+                return w;
+            };
+            unsigned wb[2], wn[2];
 #pragma unroll
-            for (int h = 0; h < 2; ++h)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) bb[h][k] = (k < nrow && h < nq) ? prow[h][li0 + k * stride] : 0;
+            for (int h = 0; h < 2; ++h) {
+                wb[h] = part_word(h, 0);
+                // a lane's first run starts on its first partner patch: no flush
+                // of an empty run (all lanes flushing into one slot at once would
+                // serialise the compare-and-swap of the shared float add)
+                if (ch == 0 && nrow > 0) run_b[h] = (int)(wb[h] & 255u);
+            }
             for (int r = 0; r < lm.per_chunk; r += 4) {
                 const int li = li0 + r * stride;
 #pragma unroll
+                for (int h = 0; h < 2; ++h) wn[h] = part_word(h, r + 4);
+                int bb[2][4];
+#pragma unroll
                 for (int h = 0; h < 2; ++h)
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        bn[h][k] = (r + 4 + k < nrow && h < nq) ? prow[h][li + (4 + k) * stride] : 0;
+                    for (int k = 0; k < 4; ++k) bb[h][k] = (int)__byte_perm(wb[h], 0u, 0x4440u | k);
                 // two rows at a time: the loop kernels of 2 rows x 2 transfers
                 // first (a block of independent arithmetic), then the runs in
                 // row order
@@ -391,24 +414,19 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
                         for (int h = 0; h < 2; ++h) {
                             if (h >= nq) break;
                             const int b = bb[h][k];
-                            if (b != run_b[h]) {
-                                if (run_b[h] >= 0) atomicAdd(&rows[(2 * warp + h) * N + run_b[h]], run_v[h]);
-                                run_b[h] = b;
-                                run_v[h] = vv[kk][h];
-                            } else {
-                                run_v[h] += vv[kk][h];
-                            }
+                            const bool change = b != run_b[h];
+                            if (change) atomicAdd(&rows[(2 * warp + h) * RS + run_b[h]], run_v[h]);
+                            run_v[h] = (change ? R(0) : run_v[h]) + vv[kk][h];
+                            run_b[h] = b;
                         }
                     }
                 }
 #pragma unroll
-                for (int h = 0; h < 2; ++h)
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) bb[h][k] = bn[h][k];
+                for (int h = 0; h < 2; ++h) wb[h] = wn[h];
             }
         }
         for (int h = 0; h < nq; ++h) {
-            R *row = rows + (2 * warp + h) * N;
+            R *row = rows + (2 * warp + h) * RS;
             // last runs: segmented sum over lanes with equal partner patch, one
             // atomic per segment head
             const int key = run_b[h];
@@ -423,7 +441,7 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
                 const R o = __shfl_down_sync(0xffffffffu, v, off);
                 if (lane + off <= end) v += o;
             }
-            if (head && key >= 0) atomicAdd(&row[key], v);
+            if (head) atomicAdd(&row[key], v);
             __syncwarp();
             const int Q = Q0 + h * nwarp;
             if constexpr (!FORM) {
@@ -493,7 +511,8 @@ static qpfrg_status launch_r(qpfrg_ctx *c, double lambda, const double *d_Z, con
                                          : (int)std::max(8L, std::min(64L, NN / 16));
     const int qchunks = div_up(NN, A.qchunk);
     const int nthr = 256;
-    const size_t smem = 2 * (size_t)pb.P * sizeof(Quad<R>) + (size_t)(1 + 2 * (nthr / 32)) * pb.N * sizeof(R);
+    const size_t smem =
+        2 * (size_t)pb.P * sizeof(Quad<R>) + ((size_t)pb.N + 2 * (nthr / 32) * (size_t)(pb.N + 2)) * sizeof(R);
     if (smem > 200 * 1024) {
         c->err = "fine grid too large for the loop-kernel launch";
         return QPFRG_ERR_UNSUPPORTED;

@@ -163,10 +163,12 @@ __device__ __forceinline__ int project_patch(double kx, double ky, int N, int mo
     return (int)j;
 }
 
-// part[f][Q][p] = patch of (Q - p) for f = 0 (pp) and of (p + Q) for f = 1 (ph).
+// part[f][Q][a P + part_byte(t, s)] = patch of (Q - p) for f = 0 (pp) and of
+// (p + Q) for f = 1 (ph), p = a P + t n_r + s the fine point (t angular, s
+// radial); part_byte orders a patch's bytes for the loop kernels' reads.
 __global__ void partner_map_kernel(const double *__restrict__ Qpp, const double *__restrict__ Qph,
                                    const double *__restrict__ fkx, const double *__restrict__ fky,
-                                   uint8_t *__restrict__ part, int N, int M, int mode, int L)
+                                   uint8_t *__restrict__ part, int N, int M, int P, int nt, int nr, int mode, int L)
 {
     const int Q = blockIdx.x, f = blockIdx.z;
     const long NN = (long)N * N;
@@ -177,7 +179,8 @@ __global__ void partner_map_kernel(const double *__restrict__ Qpp, const double 
         const double px = fkx[p], py = fky[p];
         const double qx = f == 0 ? Qx - px : px + Qx;
         const double qy = f == 0 ? Qy - py : py + Qy;
-        row[p] = (uint8_t)project_patch(qx, qy, N, mode, L);
+        const int a = p / P, li = p - a * P, t = li / nr, s = li - t * nr;
+        row[a * P + part_byte(t, s, nt, nr)] = (uint8_t)project_patch(qx, qy, N, mode, L);
     }
 }
 
@@ -310,7 +313,8 @@ qpfrg_status upload_geometry(qpfrg_ctx *c)
     dim3 grid((unsigned)NN, pblocks < 1 ? 1 : (pblocks > 65535 ? 65535 : pblocks), 2);
     prof_begin(c);
     partner_map_kernel<<<grid, 256, 0, c->stream>>>(c->d_Qpp, c->d_Qph, c->f64.kx, c->f64.ky, c->d_part,
-                                                    N, c->pb.M, c->pb.mode, c->pb.L);
+                                                    N, c->pb.M, c->pb.P, c->pb.n_theta, c->pb.n_r,
+                                                    c->pb.mode, c->pb.L);
     prof_end(c, K_PARTNER_MAP);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "partner_map_kernel");
     return QPFRG_OK;

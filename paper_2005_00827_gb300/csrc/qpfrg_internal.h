@@ -22,6 +22,16 @@ constexpr int kProjW = 256;
 // row stride of that table in bytes: 65 words, so adjacent rows start in adjacent banks
 constexpr int kProjStride = 260;
 
+// Byte of fine point (t, s) (t angular, s radial) of a patch in the partner
+// maps.  With n_theta a multiple of 4 the bytes come in blocks of four angles,
+// radius-major inside a block: one lane of the loop kernels reads the partner
+// patches of four consecutive angles at its radius as one aligned word, and the
+// 32 lanes of a warp (32 radii) read 128 contiguous bytes.  Otherwise angle-major.
+__host__ __device__ inline int part_byte(int t, int s, int nt, int nr)
+{
+    return nt % 4 == 0 ? (((t >> 2) * nr + s) << 2) + (t & 3) : t * nr + s;
+}
+
 // Kernel ids of the built-in profiler (order = qpfrg_profile_name).
 enum KernelId {
     K_PARTNER_MAP = 0,
