@@ -133,6 +133,29 @@ __device__ __forceinline__ R loop_T(bool pp, R xp, R gp, R xq, R invT, R invT2, 
     return pp ? -v : v;
 }
 
+// Two loop_T values of one fine point (x_p, g_p) against two partners, as
+// packed FP32x2 arithmetic, times the point's weight w; a lane whose difference
+// is near-degenerate is replaced by loop_T's midpoint derivative.
+__device__ __forceinline__ float2 loop_T2(bool pp, float xp, float gp, float w, float2 xq, float invT,
+                                          float invT2, float kexp, float thrT)
+{
+    const float sd = pp ? 1.f : -1.f;
+    const float2 den = __ffma2_rn(xq, make_float2(sd, sd), make_float2(xp, xp));
+    const float2 e = make_float2(exp_mT(xq.x, kexp), exp_mT(xq.y, kexp));
+    const float2 d = __fadd2_rn(e, make_float2(1.f, 1.f));
+    const float2 d2 = __fmul2_rn(d, d);
+    const float sg = pp ? invT2 : -invT2;        // +- g_q (1 + e)^2 = +- x_q e / T^2
+    const float2 num = __ffma2_rn(make_float2(gp, gp), d2, __fmul2_rn(__fmul2_rn(xq, make_float2(sg, sg)), e));
+    const float2 dd = __fmul2_rn(d2, den);
+    const float2 v = __fmul2_rn(num, make_float2(qdiv(1.f, dd.x), qdiv(1.f, dd.y)));
+    const float ws = pp ? -w : w;
+    float2 r = __fmul2_rn(v, make_float2(ws, ws));
+    // a near-degenerate lane takes the midpoint derivative instead
+    if (fabsf(den.x) < thrT) r.x = w * loop_T(pp, xp, gp, xq.x, invT, invT2, kexp, thrT);
+    if (fabsf(den.y) < thrT) r.y = w * loop_T(pp, xp, gp, xq.y, invT, invT2, kexp, thrT);
+    return r;
+}
+
 // Loop kernel of one line pair, interaction flow at fixed T.
 //   ph: D(x_p, x_q),  pp: -D(x_p, -x_q) = (1 - f_p - f_q)/(x_p + x_q)
 template <typename R>
@@ -283,7 +306,7 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
     const bool qp = A.pb.propagator == QPFRG_PROP_QP;
     const int nr = A.pb.n_r, nt = A.pb.n_theta;
 
-    Quad<R> *pc = reinterpret_cast<Quad<R> *>(smem_raw);   // cos/sin of the point's components
+    Quad<R> *pc = reinterpret_cast<Quad<R> *>(smem_raw);   // cos p_x, cos p_y, sin p_x, sin p_y
     Quad<R> *pe = pc + P;                                   // x_p, f-terms, weight
     R *Zs = reinterpret_cast<R *>(pe + P);                  // N
     // 2 nwarp rows (two transfers per warp) of N accumulators and a sink (slot
@@ -303,8 +326,8 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
         const int p = a * P + i;
         Quad<R> c4, e4;
         c4.x = A.fine.cx[p];
-        c4.y = A.fine.sx[p];
-        c4.z = A.fine.cy[p];
+        c4.y = A.fine.cy[p];
+        c4.z = A.fine.sx[p];
         c4.w = A.fine.sy[p];
         const R x = qp ? Za * A.fine.xi[p] : A.fine.xi[p];
         e4.x = x;
@@ -330,6 +353,7 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
     for (int Q0 = q0 + warp; Q0 < q1; Q0 += 2 * nwarp) {
         const int nq = Q0 + nwarp < q1 ? 2 : 1;       // warp-uniform
         R cQx[2], sQx[2], cQy[2], sQy[2];
+        float2 CQ[2], SQ[2];    // FP32: (cos Q_x, cos Q_y), +-(sin Q_x, sin Q_y) (+ pp, - ph)
         const uint8_t *prow[2];
         int run_b[2];
         R run_v[2];
@@ -340,6 +364,8 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
             sQx[h] = Qt.sx[Q];
             cQy[h] = Qt.cy[Q];
             sQy[h] = Qt.sy[Q];
+            CQ[h] = make_float2((float)cQx[h], (float)cQy[h]);
+            SQ[h] = pp ? make_float2((float)sQx[h], (float)sQy[h]) : make_float2(-(float)sQx[h], -(float)sQy[h]);
             prow[h] = A.part + ((long)fam * NN + Q) * (long)M + (long)a * P;
             run_b[h] = N;
             run_v[h] = R(0);
@@ -392,18 +418,37 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
                         const bool ok = r + k < nrow;
                         const int lk = ok ? li + k * stride : 0;
                         const Quad<R> c4 = pc[lk], e4 = pe[lk];
+                        if constexpr (sizeof(R) == 4 && TFLOW) {
+                            // FP32 temperature flow: the two transfers are the two
+                            // lanes of packed FP32x2 arithmetic
+                            const float2 cp = make_float2(c4.x, c4.y), sp = make_float2(c4.z, c4.w);
+                            float2 xq2;
 #pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            // cos of the partner momentum components by angle addition:
-                            // pp: cos(Q - p) = cQ cp + sQ sp;  ph: cos(p + Q) = cp cQ - sp sQ
-                            const R cqx = pp ? cQx[h] * c4.x + sQx[h] * c4.y : c4.x * cQx[h] - c4.y * sQx[h];
-                            const R cqy = pp ? cQy[h] * c4.z + sQy[h] * c4.w : c4.z * cQy[h] - c4.w * sQy[h];
-                            // t' = 0 (the nested lattice): the product term drops at compile time
-                            R xq = TP0 ? R(-2) * t * (cqx + cqy) - mu
-                                       : R(-2) * t * (cqx + cqy) - R(4) * tp * cqx * cqy - mu;
-                            if (qp) xq *= Zs[bb[h][k]];
-                            vv[kk][h] = e4.w * (tflow ? loop_T(pp, e4.x, e4.y, xq, invT, invT2, kexp, thrT)
-                                                      : loop_g(pp, e4.x, e4.y, e4.z, xq, invT, thrT));
+                            for (int h = 0; h < 2; ++h) {
+                                // (cos q_x, cos q_y) of the partner by angle addition:
+                                // pp: cos(Q - p) = cQ cp + sQ sp;  ph: cos(p + Q) = cp cQ - sp sQ
+                                const float2 cq = __ffma2_rn(cp, CQ[h], __fmul2_rn(sp, SQ[h]));
+                                float xq = TP0 ? -2.f * t * (cq.x + cq.y) - mu
+                                               : -2.f * t * (cq.x + cq.y) - 4.f * tp * cq.x * cq.y - mu;
+                                if (qp) xq *= Zs[bb[h][k]];
+                                if (h == 0) xq2.x = xq;
+                                else xq2.y = xq;
+                            }
+                            const float2 v = loop_T2(pp, e4.x, e4.y, e4.w, xq2, invT, invT2, kexp, thrT);
+                            vv[kk][0] = v.x;
+                            vv[kk][1] = v.y;
+                        } else {
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const R cqx = pp ? cQx[h] * c4.x + sQx[h] * c4.z : c4.x * cQx[h] - c4.z * sQx[h];
+                                const R cqy = pp ? cQy[h] * c4.y + sQy[h] * c4.w : c4.y * cQy[h] - c4.w * sQy[h];
+                                // t' = 0 (the nested lattice): the product term drops at compile time
+                                R xq = TP0 ? R(-2) * t * (cqx + cqy) - mu
+                                           : R(-2) * t * (cqx + cqy) - R(4) * tp * cqx * cqy - mu;
+                                if (qp) xq *= Zs[bb[h][k]];
+                                vv[kk][h] = e4.w * (tflow ? loop_T(pp, e4.x, e4.y, xq, invT, invT2, kexp, thrT)
+                                                          : loop_g(pp, e4.x, e4.y, e4.z, xq, invT, thrT));
+                            }
                         }
                     }
 #pragma unroll
