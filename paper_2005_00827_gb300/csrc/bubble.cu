@@ -150,9 +150,13 @@ __device__ __forceinline__ float2 loop_T2(bool pp, float xp, float gp, float w, 
     const float2 v = __fmul2_rn(num, make_float2(qdiv(1.f, dd.x), qdiv(1.f, dd.y)));
     const float ws = pp ? -w : w;
     float2 r = __fmul2_rn(v, make_float2(ws, ws));
-    // a near-degenerate lane takes the midpoint derivative instead
-    if (fabsf(den.x) < thrT) r.x = w * loop_T(pp, xp, gp, xq.x, invT, invT2, kexp, thrT);
-    if (fabsf(den.y) < thrT) r.y = w * loop_T(pp, xp, gp, xq.y, invT, invT2, kexp, thrT);
+    // a near-degenerate lane takes the midpoint derivative instead (one rarely
+    // taken branch for both lanes)
+    const bool m0 = fabsf(den.x) < thrT, m1 = fabsf(den.y) < thrT;
+    if (m0 || m1) {
+        if (m0) r.x = w * loop_T(pp, xp, gp, xq.x, invT, invT2, kexp, thrT);
+        if (m1) r.y = w * loop_T(pp, xp, gp, xq.y, invT, invT2, kexp, thrT);
+    }
     return r;
 }
 
