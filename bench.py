@@ -216,13 +216,14 @@ def run_qpfrg(args):
 
     # end to end: state uploaded from pinned host memory, one step, state read back
     nbytes = api.qpfrg_state_size(ctx.h)
-    img = api.qpfrg_get_state(ctx.h)
+    img = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    api.qpfrg_get_state_into(ctx.h, img)
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        api.qpfrg_set_state(ctx.h, img)
+        api.qpfrg_set_state_from(ctx.h, img)
         api.qpfrg_step(ctx.h, 1)
-        img = api.qpfrg_get_state(ctx.h)
+        api.qpfrg_get_state_into(ctx.h, img)
     barrier()
     e2e_s = time.perf_counter() - t0
     e2e = {"value": 4.0 * args.steps * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,

@@ -214,12 +214,17 @@ qpfrg_status qpfrg_flow_batch(const qpfrg_lattice *lattice, const qpfrg_fine_gri
 /* Checkpoint: size in bytes of the state image (64-byte header, then V as
  * N^3 FP64, then Z as N FP64, little endian). */
 qpfrg_status qpfrg_state_size(qpfrg_t ctx, size_t *bytes);
-/* Copy the flow state into h_buf (host, at least qpfrg_state_size bytes).
- * Synchronises the context's stream. */
+/* Copy the flow state into h_buf (host, at least qpfrg_state_size bytes;
+ * page-locked memory makes the copy a direct DMA).  Synchronises the
+ * context's stream. */
 qpfrg_status qpfrg_get_state(qpfrg_t ctx, void *h_buf, size_t bytes);
-/* Replace the flow state by h_buf (as written by qpfrg_get_state).  Returns
- * QPFRG_ERR_INVALID on a wrong header or size, QPFRG_ERR_NONFINITE (state
- * unchanged) when V or Z holds NaN/Inf. */
+/* Replace the flow state by h_buf (as written by qpfrg_get_state; host,
+ * page-locked memory preferred).  The image is uploaded into scratch space and
+ * checked on the device (finiteness, max|V|, C4v symmetry of the state, which
+ * selects the self-energy's irreducible targets); synchronises the context's
+ * stream.  Returns QPFRG_ERR_INVALID on a wrong header or size,
+ * QPFRG_ERR_NONFINITE (state unchanged) when V or Z holds NaN/Inf.  Between
+ * steps only (it reuses the RK scratch buffers). */
 qpfrg_status qpfrg_set_state(qpfrg_t ctx, const void *h_buf, size_t bytes);
 /* Copy V (N^3 FP64) and Z (N FP64) of the flow state into device buffers
  * (either may be NULL); enqueued on the context's stream. */

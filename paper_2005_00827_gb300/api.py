@@ -227,6 +227,17 @@ def qpfrg_set_state(ctx, image: bytes):
     _check(ctx, load().qpfrg_set_state(ctx, buf, len(image)))
 
 
+def qpfrg_get_state_into(ctx, buf):
+    """qpfrg_get_state into a caller-owned host buffer (e.g. a pinned uint8
+    tensor of qpfrg_state_size bytes): no allocation or copy on the Python side."""
+    _check(ctx, load().qpfrg_get_state(ctx, C.c_void_p(buf.data_ptr()), buf.numel() * buf.element_size()))
+
+
+def qpfrg_set_state_from(ctx, buf):
+    """qpfrg_set_state from a caller-owned host buffer (e.g. a pinned uint8 tensor)."""
+    _check(ctx, load().qpfrg_set_state(ctx, C.c_void_p(buf.data_ptr()), buf.numel() * buf.element_size()))
+
+
 def qpfrg_read_state(ctx, V, Z):
     _check(ctx, load().qpfrg_read_state(ctx, _ptr(V), _ptr(Z)))
 

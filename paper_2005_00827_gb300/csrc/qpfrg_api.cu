@@ -84,17 +84,6 @@ void flush_profile(qpfrg_ctx *c)
     p->pending.clear();
 }
 
-bool finite_all(const double *x, size_t n, double *maxabs)
-{
-    double m = 0.0;
-    for (size_t i = 0; i < n; ++i) {
-        if (!std::isfinite(x[i])) return false;
-        m = std::fmax(m, std::fabs(x[i]));
-    }
-    if (maxabs) *maxabs = m;
-    return true;
-}
-
 template <typename T>
 qpfrg_status dev_alloc(qpfrg_ctx *c, T **p, size_t count, const char *what)
 {
@@ -109,36 +98,6 @@ qpfrg_status dev_alloc(qpfrg_ctx *c, T **p, size_t count, const char *what)
 }
 
 long n3_of(const qpfrg_ctx *c) { return (long)c->pb.N * c->pb.N * c->pb.N; }
-
-// C4v images of a wedge patch (centres at 2 pi j / N, N a multiple of 4):
-// j -> +-j + m N/4.  True when V[g i][g j][g l] = V[i][j][l] and Z[g j] = Z[j]
-// for all 8 group elements, to a relative tol (the rounding level of the
-// precision that produced the state: a mixed-precision flow keeps the
-// symmetry only to FP32 rounding).
-bool c4v_symmetric(const qpfrg_ctx *c, const double *V, const double *Z)
-{
-    if (c->pb.mode != QPFRG_GRID_WEDGE) return false;
-    const double tol = c->opt.precision == QPFRG_FP64 ? 1e-12 : 1e-5;
-    const int N = c->pb.N, q = N / 4;
-    double vmax = 0.0, zmax = 0.0;
-    for (long i = 0; i < n3_of(c); ++i) vmax = std::fmax(vmax, std::fabs(V[i]));
-    for (int j = 0; j < N; ++j) zmax = std::fmax(zmax, std::fabs(Z[j]));
-    std::vector<int> g(N);
-    for (int m = 0; m < 4; ++m)
-        for (int sgn = -1; sgn <= 1; sgn += 2) {
-            for (int j = 0; j < N; ++j) g[j] = ((sgn * j + m * q) % N + N) % N;
-            for (int j = 0; j < N; ++j)
-                if (std::fabs(Z[g[j]] - Z[j]) > tol * zmax) return false;
-            for (int i = 0; i < N; ++i)
-                for (int j = 0; j < N; ++j) {
-                    const double *row = V + ((long)i * N + j) * N;
-                    const double *img = V + ((long)g[i] * N + g[j]) * N;
-                    for (int l = 0; l < N; ++l)
-                        if (std::fabs(img[g[l]] - row[l]) > tol * vmax) return false;
-                }
-        }
-    return true;
-}
 
 }  // namespace
 
@@ -388,9 +347,9 @@ qpfrg_status qpfrg_create(const qpfrg_lattice *lattice, int n_p, const qpfrg_fin
         (s = dev_alloc(c, &c->d_k, n3, "k")) || (s = dev_alloc(c, &c->d_acc, n3, "acc")) ||
         (s = dev_alloc(c, &c->d_Vf, n3, "V fp32")) || (s = dev_alloc(c, &c->d_Z, N, "Z")) ||
         (s = dev_alloc(c, &c->d_Zwork, N, "Z work")) || (s = dev_alloc(c, &c->d_ones, N, "ones")) ||
-        (s = dev_alloc(c, &c->d_sig, 2 * N, "sigma chord")) || (s = dev_alloc(c, &c->d_red, 2, "reduction")))
+        (s = dev_alloc(c, &c->d_sig, 2 * N, "sigma chord")) || (s = dev_alloc(c, &c->d_red, 5, "reduction")))
         return fail(s);
-    e = cudaMallocHost((void **)&c->h_red, 3 * sizeof(unsigned long long));
+    e = cudaMallocHost((void **)&c->h_red, 5 * sizeof(unsigned long long));
     if (e != cudaSuccess) return fail(cuda_fail(c, e, "cudaMallocHost"));
 
     // C4v-irreducible patches 0..floor(N/8) and each patch's representative
@@ -673,11 +632,11 @@ static qpfrg_status make_child(qpfrg_ctx *parent, double U, double lambda0, doub
     if (!c->profiler || (s = dev_alloc(c, &c->d_V, n3, "V")) || (s = dev_alloc(c, &c->d_Vs, n3, "V stage")) ||
         (s = dev_alloc(c, &c->d_k, n3, "k")) || (s = dev_alloc(c, &c->d_acc, n3, "acc")) ||
         (s = dev_alloc(c, &c->d_Vf, n3, "V fp32")) || (s = dev_alloc(c, &c->d_Z, N, "Z")) ||
-        (s = dev_alloc(c, &c->d_Zwork, N, "Z work")) || (s = dev_alloc(c, &c->d_red, 2, "reduction"))) {
+        (s = dev_alloc(c, &c->d_Zwork, N, "Z work")) || (s = dev_alloc(c, &c->d_red, 5, "reduction"))) {
         qpfrg_destroy(c);
         return QPFRG_ERR_OOM;
     }
-    if (cudaMallocHost((void **)&c->h_red, 3 * sizeof(unsigned long long)) != cudaSuccess) {
+    if (cudaMallocHost((void **)&c->h_red, 5 * sizeof(unsigned long long)) != cudaSuccess) {
         qpfrg_destroy(c);
         return QPFRG_ERR_OOM;
     }
@@ -838,15 +797,33 @@ qpfrg_status qpfrg_set_state(qpfrg_t c, const void *h_buf, size_t bytes)
         return set_err(c, QPFRG_ERR_INVALID, "state image has a bad status or step count");
     const double *V = reinterpret_cast<const double *>(static_cast<const unsigned char *>(h_buf) + sizeof(hd));
     const double *Z = V + n3_of(c);
-    double m = 0.0;
-    if (!finite_all(V, n3_of(c), &m) || !finite_all(Z, c->pb.N, nullptr) || !std::isfinite(hd.lambda))
-        return set_err(c, QPFRG_ERR_NONFINITE, "state image holds NaN or Inf");
-    cudaError_t e = cudaMemcpyAsync(c->d_V, V, n3_of(c) * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (!std::isfinite(hd.lambda)) return set_err(c, QPFRG_ERR_NONFINITE, "state image holds NaN or Inf");
+    // The image is staged in the RK scratch buffers (free between steps) and
+    // checked there on the device: finiteness, max|V|, and the C4v symmetry of
+    // V and Z to the rounding level of the precision that produced them (a
+    // mixed-precision flow keeps it only to FP32 rounding).  A rejected image
+    // leaves the state untouched.
+    const bool wedge = c->pb.mode == QPFRG_GRID_WEDGE;
+    const double tol = c->opt.precision == QPFRG_FP64 ? 1e-12 : 1e-5;
+    cudaError_t e = cudaMemcpyAsync(c->d_k, V, n3_of(c) * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(c->d_Z, Z, c->pb.N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "set_state");
-    c->c4v_state = c4v_symmetric(c, V, Z);
+        e = cudaMemcpyAsync(c->d_acc, Z, c->pb.N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set_state upload");
+    qpfrg_status st = launch_state_check(c, c->d_k, c->d_acc, wedge, tol);
+    if (st != QPFRG_OK) return st;
+    if ((e = cudaMemcpyAsync(c->h_red, c->d_red, 5 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                             c->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+        return cuda_fail(c, e, "set_state check");
+    if (c->h_red[1] || c->h_red[3]) return set_err(c, QPFRG_ERR_NONFINITE, "state image holds NaN or Inf");
+    double m = 0.0;
+    std::memcpy(&m, &c->h_red[0], sizeof(double));
+    if ((e = cudaMemcpyAsync(c->d_V, c->d_k, n3_of(c) * sizeof(double), cudaMemcpyDeviceToDevice, c->stream)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(c->d_Z, c->d_acc, c->pb.N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream)) !=
+            cudaSuccess)
+        return cuda_fail(c, e, "set_state");
+    c->c4v_state = wedge && c->h_red[4] == 0;
     c->status = hd.status;
     c->steps = (int)hd.steps;
     c->lambda = hd.lambda;

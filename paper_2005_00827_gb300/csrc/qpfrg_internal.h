@@ -184,7 +184,7 @@ struct qpfrg_ctx {
     bool c4v_state = false;      // flow state V, Z is C4v symmetric
     double *d_hist = nullptr;    // Sigma frequency-grid histogram (lazily sized)
     size_t hist_elems = 0;
-    unsigned long long *d_red = nullptr;  // [0] max|V| bits, [1] nonfinite flag
+    unsigned long long *d_red = nullptr;  // [0] max|V| bits, [1] nonfinite flag; [2..4] state-image checks
     unsigned long long *h_red = nullptr;  // pinned mirror
     double lambda = 0.0;
     double lambda_end = 0.0;     // end of this flow (batched flows differ)
@@ -234,6 +234,7 @@ qpfrg_status launch_tc_gemm(qpfrg_ctx *c, int ch, int M, double scale, double *o
 qpfrg_status launch_convert_f32(qpfrg_ctx *c, const double *d_in, float *d_out, long n);
 qpfrg_status launch_rk_stage(qpfrg_ctx *c, int stage, double h, const double *d_V,
                              const double *d_k, double *d_acc, double *d_Vs, float *d_Vf);
+qpfrg_status launch_state_check(qpfrg_ctx *c, const double *d_V, const double *d_Z, bool c4v_test, double tol);
 qpfrg_status launch_rk_final(qpfrg_ctx *c, double h, double *d_V, const double *d_acc,
                              const double *d_k);
 qpfrg_status launch_check_finite(qpfrg_ctx *c, const double *d_x, long n);

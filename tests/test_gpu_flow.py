@@ -197,6 +197,23 @@ def test_checkpoint_resume():
     assert np.abs(va - vb).max() / np.abs(va).max() < 1e-13
 
 
+def test_state_round_trip_through_pinned_buffer():
+    """qpfrg_get_state_into / qpfrg_set_state_from with a page-locked buffer
+    write and read the same image as the bytes interface."""
+    import torch
+    N, n = 16, 4
+    with api.Context(N, n, n, U=2.5, lambda_end=0.05) as c:
+        api.qpfrg_step(c.h, 3)
+        ref = api.qpfrg_get_state(c.h)
+        buf = torch.empty(api.qpfrg_state_size(c.h), dtype=torch.uint8, pin_memory=True)
+        api.qpfrg_get_state_into(c.h, buf)
+        assert bytes(buf.numpy()) == ref
+        api.qpfrg_step(c.h, 2)
+        api.qpfrg_set_state_from(c.h, buf)
+        assert api.qpfrg_get_state(c.h) == ref
+        assert api.qpfrg_step(c.h, 1).as_dict()["steps"] == 4
+
+
 def test_failure_detection_host_side(monkeypatch):
     N, n = 16, 4
     with api.Context(N, n, n, U=2.0) as c:
