@@ -151,6 +151,36 @@ def test_flow_with_z_feedback_trajectory(prec, tol):
     assert np.all(ref["Z"] > 0.0)
 
 
+def test_flow_z_full_size_matches_all_targets():
+    """np96_n32, the bench workload, in its launch configuration (MIXED_TC,
+    autotuned shapes): Z from the flow's self-energy (the 13 C4v-irreducible
+    targets, mirror-line targets over half of the loop points) equals Z from
+    all 96 targets evaluated independently (qpfrg_selfenergy).  The chord
+    slope 1 - 1/Z is quadratic in the vertex, and doubling V is exact in
+    floating point, so slope(2V) = 4 slope(V) to the reduction order."""
+    import torch
+    N, n, T0 = 96, 32, 0.7
+    V = inputs.random_vertex(N, 2.5, seed=21, c4v=True)
+    Z0 = inputs.z_profile(N, "aniso")
+    with api.Context(N, n, n, U=2.5, lambda0=T0, z_feedback=1, lambda_end=0.05,
+                     precision=api.QPFRG_MIXED_TC) as c:
+        api.qpfrg_autotune(c.h, T0)
+        img = bytearray(api.qpfrg_get_state(c.h))
+        img[64:] = np.concatenate([V.ravel(), Z0]).tobytes()
+        api.qpfrg_set_state(c.h, bytes(img))
+        api.qpfrg_step(c.h, 1)
+        Zflow = zeros(N)
+        api.qpfrg_read_state(c.h, None, Zflow)
+        torch.cuda.synchronize()
+        Zall = gpu_z(c, T0, V, Z0)
+        Z2 = gpu_z(c, T0, 2.0 * V, Z0)
+    Zflow = Zflow.cpu().numpy()
+    assert np.all(np.isfinite(Zall)) and np.all(np.isfinite(Zflow))
+    assert np.abs(Zflow - Zall).max() < 1e-4
+    s1, s2 = 1.0 - 1.0 / Zall, 1.0 - 1.0 / Z2
+    assert np.abs(s2 - 4.0 * s1).max() < 1e-9 * np.abs(4.0 * s1).max()
+
+
 @pytest.mark.parametrize("symmetric,prec,N,n", [
     (True, api.QPFRG_FP64, 16, 4), (False, api.QPFRG_FP64, 16, 4),
     (True, api.QPFRG_MIXED, 16, 4),     # irreducible targets, mirror halving of targets 0 and N/8
