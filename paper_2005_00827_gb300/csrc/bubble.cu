@@ -32,6 +32,8 @@ struct BubbleArgs {
     const double *Z;
     R *B;
     R T, invT, g, thr;
+    // FP32 rows accumulate as 32-bit fixed point: bin = int / fscale (finv = 1/fscale)
+    float fscale, finv;
     R t, tp, mu;          // hoppings and chemical potential, already in R (no per-use conversion)
     int qchunk;
     // formed operands of the tensor-core contraction (QPFRG_MIXED_TC)
@@ -226,6 +228,23 @@ __device__ __forceinline__ void split_bf16x2(float x0, float x1, __nv_bfloat162 
     lo = __floats2bfloat162_rn(x0 - __low2float(hi), x1 - __high2float(hi));
 }
 
+// Row accumulators.  FP32: 32-bit fixed point in units of 1/fscale, so that a
+// run's flush is one native integer shared-memory add (a float add on shared
+// memory is a compare-and-swap loop, which diverges the warp); the host picks
+// fscale from the bound |bin| <= P w_max max|L| (max|dD/dT| = 1/(4T^2),
+// max|D| = 1/(4T)) with a factor 2 to spare, so no bin leaves +-2^29.  FP64:
+// double adds.
+__device__ __forceinline__ void row_add(float *slot, float v, float fscale)
+{
+    atomicAdd(reinterpret_cast<int *>(slot), __float2int_rn(v * fscale));
+}
+__device__ __forceinline__ void row_add(double *slot, double v, float) { atomicAdd(slot, v); }
+__device__ __forceinline__ float row_get(const float *slot, float finv)
+{
+    return (float)*reinterpret_cast<const int *>(slot) * finv;
+}
+__device__ __forceinline__ double row_get(const double *slot, float) { return *slot; }
+
 // Write-out of one transfer's row of N bins as formed tensor-core operands
 // (BF16 hi/lo in tiles); the row is cleared.  Each lane takes two adjacent
 // partner patches b, b+1 (N is a multiple of 4 here), which are adjacent in k
@@ -243,7 +262,8 @@ __device__ __forceinline__ void form_row(const BubbleArgs<float> &A, float *row,
         const float fv = A.Vf[(long)Q * N + a];
         const long rb = tile_row_base(Q, A.Kp);
         for (int b = 2 * lane; b < N; b += 64) {
-            const float2 v = *reinterpret_cast<const float2 *>(row + b);
+            const int2 iv = *reinterpret_cast<const int2 *>(row + b);
+            const float2 v = make_float2((float)iv.x * A.finv, (float)iv.y * A.finv);
             *reinterpret_cast<float2 *>(row + b) = make_float2(0.f, 0.f);
             const float2 z = *reinterpret_cast<const float2 *>(Zs + b);
             const float t0 = v.x * weight(z.x) * fv, t1 = v.y * weight(z.y) * fv;
@@ -262,7 +282,8 @@ __device__ __forceinline__ void form_row(const BubbleArgs<float> &A, float *row,
         const long rb_cr = tile_row_base(rcr, A.Kp), rb_d = tile_row_base(Q, A.Kpd);
         const float *vt = A.VT + rcr * N;
         for (int b = 2 * lane; b < N; b += 64) {
-            const float2 v = *reinterpret_cast<const float2 *>(row + b);
+            const int2 iv = *reinterpret_cast<const int2 *>(row + b);
+            const float2 v = make_float2((float)iv.x * A.finv, (float)iv.y * A.finv);
             *reinterpret_cast<float2 *>(row + b) = make_float2(0.f, 0.f);
             const float2 z = *reinterpret_cast<const float2 *>(Zs + b);
             const float t0 = v.x * weight(z.x), t1 = v.y * weight(z.y);
@@ -464,7 +485,7 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
                             if (h >= nq) break;
                             const int b = bb[h][k];
                             const bool change = b != run_b[h];
-                            if (change) atomicAdd(&rows[(2 * warp + h) * RS + run_b[h]], run_v[h]);
+                            if (change) row_add(&rows[(2 * warp + h) * RS + run_b[h]], run_v[h], A.fscale);
                             run_v[h] = (change ? R(0) : run_v[h]) + vv[kk][h];
                             run_b[h] = b;
                         }
@@ -490,12 +511,12 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
                 const R o = __shfl_down_sync(0xffffffffu, v, off);
                 if (lane + off <= end) v += o;
             }
-            if (head) atomicAdd(&row[key], v);
+            if (head) row_add(&row[key], v, A.fscale);
             __syncwarp();
             const int Q = Q0 + h * nwarp;
             if constexpr (!FORM) {
                 for (int b = lane; b < N; b += 32) {
-                    const R v = row[b];
+                    const R v = row_get(row + b, A.finv);
                     row[b] = R(0);
                     const R Zb = Zs[b];
                     const R s = tflow ? Za * Zb : A.g * Za * Zb * (Za + Zb);
@@ -551,6 +572,11 @@ static qpfrg_status launch_r(qpfrg_ctx *c, double lambda, const double *d_Z, con
     A.invT = (R)(1.0 / T);
     A.g = (R)(tflow ? 1.0 : lambda);
     A.thr = thr;
+    // fixed-point scale of the FP32 row accumulators (see row_add)
+    const double lmax = tflow ? 0.25 / (T * T) : 0.25 / T;
+    const double bin_max = 2.0 * pb.P * c->fw_max * lmax;
+    A.fscale = bin_max > 0.0 ? (float)(1073741824.0 / bin_max) : 1.f;
+    A.finv = 1.f / A.fscale;
     A.t = (R)pb.t;
     A.tp = (R)pb.tp;
     A.mu = (R)pb.mu;

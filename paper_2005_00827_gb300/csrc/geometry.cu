@@ -106,6 +106,7 @@ qpfrg_status build_host_geometry(qpfrg_ctx *c)
                 c->fw[j] = 1.0 / N;
                 c->fpatch[j] = j;
             }
+        c->fw_max = 1.0 / N;
         return QPFRG_OK;
     }
 
@@ -137,6 +138,8 @@ qpfrg_status build_host_geometry(qpfrg_ctx *c)
             }
         }
     }
+    c->fw_max = 0.0;
+    for (double w : c->fw) c->fw_max = std::fmax(c->fw_max, w);
     return QPFRG_OK;
 }
 

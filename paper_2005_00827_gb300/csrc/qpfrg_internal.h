@@ -141,6 +141,7 @@ struct qpfrg_ctx {
     std::vector<double> kf;      // N x 2
     std::vector<double> fk;      // M x 2
     std::vector<double> fw;      // M
+    double fw_max = 0.0;         // max of fw
     std::vector<int> fpatch;     // M
 
     // device geometry
