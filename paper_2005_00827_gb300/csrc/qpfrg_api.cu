@@ -628,13 +628,13 @@ static qpfrg_status make_child(qpfrg_ctx *parent, double U, double lambda0, doub
     c->h_red = nullptr;
     c->err.clear();
     const size_t N = c->pb.N, n3 = N * N * N;
-    qpfrg_status s;
+    qpfrg_status s = QPFRG_ERR_OOM;
     if (!c->profiler || (s = dev_alloc(c, &c->d_V, n3, "V")) || (s = dev_alloc(c, &c->d_Vs, n3, "V stage")) ||
         (s = dev_alloc(c, &c->d_k, n3, "k")) || (s = dev_alloc(c, &c->d_acc, n3, "acc")) ||
         (s = dev_alloc(c, &c->d_Vf, n3, "V fp32")) || (s = dev_alloc(c, &c->d_Z, N, "Z")) ||
         (s = dev_alloc(c, &c->d_Zwork, N, "Z work")) || (s = dev_alloc(c, &c->d_red, 5, "reduction"))) {
         qpfrg_destroy(c);
-        return QPFRG_ERR_OOM;
+        return s;
     }
     if (cudaMallocHost((void **)&c->h_red, 5 * sizeof(unsigned long long)) != cudaSuccess) {
         qpfrg_destroy(c);
