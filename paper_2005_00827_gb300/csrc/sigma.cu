@@ -737,9 +737,9 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
             // first, one rarely taken branch for the guarded ones, then the
             // arithmetic of all of them (one large block for the scheduler);
             // an odd count reads the zero-weight pad record after the last one;
-            // the loop is unrolled once more (four records per trip: half the
-            // loop overhead, 119 registers)
-#pragma unroll 2
+            // the loop is unrolled four times (eight records per trip, 122
+            // registers: the loop overhead amortised, more independent work)
+#pragma unroll 4
             for (int i = 0; i < cnt; i += 2) {
                 float4 ra[2], rb[2];
                 float upp[2];
