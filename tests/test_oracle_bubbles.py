@@ -74,3 +74,23 @@ def test_pp_is_reflected_ph(oracle_mod):
         assert o.Lpp(a, b, 0.2) == -o.D(a, -b, 0.2)
         assert o.Lph(a, b, 0.2) < 0.0
         assert o.Lpp(a, b, 0.2) > 0.0
+
+
+@pytest.mark.parametrize("T", TEMPS)
+def test_loop_kernel_magnitude_bounds(oracle_mod, T):
+    """|D| <= 1/(4T) and |dD/dT| <= 1/(4T^2) for every pair of line energies
+    (mean value theorem: D is f' and dD/dT is d^2f/dxdT somewhere between the
+    energies, both largest at x = 0).  The FP32 loop-kernel rows accumulate as
+    fixed point with a scale taken from exactly these bounds, so they must hold
+    for the pp and ph kernels alike, including near-degenerate pairs."""
+    o = oracle_mod
+    xs = np.concatenate([np.linspace(-6.0, 6.0, 121), np.linspace(-4.0, 4.0, 17) * T])
+    pairs = [(a, b) for a in xs for b in xs] + [(a, a + e * T) for a in xs for e in (1e-7, 9.9e-6, 1e-3)]
+    bD, bT = 0.25 / T, 0.25 / T ** 2
+    worst_D = max(max(abs(o.Lph(a, b, T)), abs(o.Lpp(a, b, T))) for a, b in pairs)
+    worst_T = max(max(abs(o.dLph_dT(a, b, T)), abs(o.dLpp_dT(a, b, T))) for a, b in pairs)
+    assert worst_D <= bD * (1.0 + 1e-12)
+    assert worst_T <= bT * (1.0 + 1e-12)
+    # the bounds are attained at the Fermi level (degenerate pair at x = 0)
+    assert abs(o.Lph(0.0, 0.0, T)) == pytest.approx(bD, rel=1e-12)
+    assert abs(o.dLph_dT(0.0, 0.0, T)) == pytest.approx(bT, rel=1e-12)
