@@ -187,6 +187,50 @@ __global__ void partner_map_kernel(const double *__restrict__ Qpp, const double 
     }
 }
 
+// Wedge-mode partner maps from fixed-point momenta (angle_fx): the cell table
+// and one FP32 test against the ray between its two wedges decide, as in the
+// self-energy kernels; points within the guard bands of a ray or of the zone
+// edge, or in a cell of three or more wedges, take project_patch, so every
+// byte equals the FP64 projection.  Qfx[f][Q], pfx[p]: fixed-point momenta.
+__global__ void partner_map_fx_kernel(const int2 *__restrict__ Qfx, const double *__restrict__ Qpp,
+                                      const double *__restrict__ Qph, const int2 *__restrict__ pfx,
+                                      const double *__restrict__ fkx, const double *__restrict__ fky,
+                                      const uint8_t *__restrict__ ptab, const float4 *__restrict__ bnd,
+                                      uint8_t *__restrict__ part, int N, int M, int P, int nt, int nr)
+{
+    const int Q = blockIdx.x, f = blockIdx.z;
+    const long NN = (long)N * N;
+    const int2 qf = Qfx[f * NN + Q];
+    const double *Qt = f == 0 ? Qpp : Qph;
+    uint8_t *row = part + ((long)f * NN + Q) * (long)M;
+    const uint8_t *tabc = ptab + (kProjW / 2) * (kProjStride + 1);   // the cell of the origin
+    for (int p = blockIdx.y * blockDim.x + threadIdx.x; p < M; p += gridDim.y * blockDim.x) {
+        const int2 pf = pfx[p];
+        // pp: Q - p, ph: p + Q, folded by the wrap of 32-bit arithmetic
+        const int X = (int)(f == 0 ? (unsigned)qf.x - (unsigned)pf.x : (unsigned)pf.x + (unsigned)qf.x);
+        const int Y = (int)(f == 0 ? (unsigned)qf.y - (unsigned)pf.y : (unsigned)pf.y + (unsigned)qf.y);
+        const float x = __int2float_rn(X), y = __int2float_rn(Y);
+        const int e = __ldg(tabc + (Y >> 24) * kProjStride + (X >> 24));
+        float rx = 0.f, ry = 0.f;   // ray between wedges e and e + 1 (none for e = 255)
+        if (e + 1 <= N) {
+            const float4 b = __ldg(bnd + (e + 1 == N ? 0 : e + 1));
+            rx = b.x;
+            ry = b.z;
+        }
+        const float cr = rx * y - ry * x;
+        int c;
+        if (fmaxf(fabsf(x), fabsf(y)) > kFxEdge || fabsf(cr) < kFxGuard) {
+            const double px = fkx[p], py = fky[p], Qx = Qt[2 * Q], Qy = Qt[2 * Q + 1];
+            c = project_patch(f == 0 ? Qx - px : px + Qx, f == 0 ? Qy - py : py + Qy, N, QPFRG_GRID_WEDGE, 0);
+        } else {
+            c = e + (cr >= 0.f ? 1 : 0);
+            if (c == N) c = 0;
+        }
+        const int a = p / P, li = p - a * P, t = li / nr, s = li - t * nr;
+        row[a * P + part_byte(t, s, nt, nr)] = (uint8_t)c;
+    }
+}
+
 template <typename R>
 static qpfrg_status alloc_fine(qpfrg_ctx *c, FineTable<R> &t)
 {
@@ -314,6 +358,35 @@ qpfrg_status upload_geometry(qpfrg_ctx *c)
         return cuda_fail(c, e, "cudaMalloc(partner maps)");
     const int pblocks = div_up(c->pb.M, 256 * 4);
     dim3 grid((unsigned)NN, pblocks < 1 ? 1 : (pblocks > 65535 ? 65535 : pblocks), 2);
+    if (c->d_ptab) {
+        // wedge mode: fixed-point decisions, FP64 only in the guard bands
+        const size_t M = c->pb.M;
+        std::vector<int2> qfx(2 * NN), pfx(M);
+        for (size_t q = 0; q < NN; ++q) {
+            qfx[q] = make_int2(angle_fx(Qpp[2 * q]), angle_fx(Qpp[2 * q + 1]));
+            qfx[NN + q] = make_int2(angle_fx(Qph[2 * q]), angle_fx(Qph[2 * q + 1]));
+        }
+        for (size_t p = 0; p < M; ++p) pfx[p] = make_int2(angle_fx(c->fk[2 * p]), angle_fx(c->fk[2 * p + 1]));
+        int2 *d_qfx = nullptr, *d_pfx = nullptr;
+        if ((e = cudaMalloc((void **)&d_qfx, 2 * NN * sizeof(int2))) != cudaSuccess ||
+            (e = cudaMalloc((void **)&d_pfx, M * sizeof(int2))) != cudaSuccess) {
+            cudaFree(d_qfx);
+            return cuda_fail(c, e, "cudaMalloc(fixed-point momenta)");
+        }
+        cudaMemcpy(d_qfx, qfx.data(), 2 * NN * sizeof(int2), cudaMemcpyHostToDevice);
+        cudaMemcpy(d_pfx, pfx.data(), M * sizeof(int2), cudaMemcpyHostToDevice);
+        prof_begin(c);
+        partner_map_fx_kernel<<<grid, 256, 0, c->stream>>>(d_qfx, c->d_Qpp, c->d_Qph, d_pfx, c->f64.kx, c->f64.ky,
+                                                           c->d_ptab, c->d_bnd, c->d_part, N, c->pb.M, c->pb.P,
+                                                           c->pb.n_theta, c->pb.n_r);
+        prof_end(c, K_PARTNER_MAP);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // before the momenta are released
+        cudaFree(d_qfx);
+        cudaFree(d_pfx);
+        if (e != cudaSuccess) return cuda_fail(c, e, "partner_map_fx_kernel");
+        return QPFRG_OK;
+    }
     prof_begin(c);
     partner_map_kernel<<<grid, 256, 0, c->stream>>>(c->d_Qpp, c->d_Qph, c->f64.kx, c->f64.ky, c->d_part,
                                                     N, c->pb.M, c->pb.P, c->pb.n_theta, c->pb.n_r,

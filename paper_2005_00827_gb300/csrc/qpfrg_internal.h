@@ -6,6 +6,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -21,6 +22,25 @@ constexpr double kTwoPi = 2.0 * kPi;
 constexpr int kProjW = 256;
 // row stride of that table in bytes: 65 words, so adjacent rows start in adjacent banks
 constexpr int kProjStride = 260;
+
+// Fixed-point angles: a momentum component as turns x 2^32 in an int32, so
+// that the difference of two wraps into [-pi, pi) by itself (the zone fold,
+// ties at -pi) and the projection table's cell is the top byte.  The FP32
+// value of such a difference is off by at most 64 units (9.4e-8 rad).
+constexpr double kFxPerRad = 4294967296.0 / kTwoPi;
+constexpr float kRadPerFx = (float)(kTwoPi / 4294967296.0);
+// guard bands of the FP32 decisions in fixed-point units: 4e-6 rad from a ray
+// and from the zone edge
+constexpr float kFxGuard = (float)(4e-6 * kFxPerRad);
+constexpr float kFxEdge = (float)((kPi - 4e-6) * kFxPerRad);
+
+// angle (rad, FP64) -> fixed point; the same on host and device (round to
+// nearest even of the same FP64 product)
+__host__ __device__ inline int angle_fx(double r)
+{
+    const double t = r * (1.0 / kTwoPi);
+    return (int)(unsigned)(long long)llrint((t - rint(t)) * 4294967296.0);
+}
 
 // Byte of fine point (t, s) (t angular, s radial) of a patch in the partner
 // maps.  With n_theta a multiple of 4 the bytes come in blocks of four angles,

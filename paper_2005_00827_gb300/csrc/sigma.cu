@@ -500,23 +500,6 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
-// Fixed-point angles: a momentum component as turns x 2^32 in an int32, so
-// that the difference of two wraps into [-pi, pi) by itself (the zone fold,
-// ties at -pi) and the projection table's cell is the top byte.  The FP32
-// value of such a difference is off by at most 64 units (9.4e-8 rad).
-constexpr double kFxPerRad = 4294967296.0 / kTwoPi;
-constexpr float kRadPerFx = (float)(kTwoPi / 4294967296.0);
-// guard bands of the FP32 decisions in fixed-point units: 4e-6 rad from a ray
-// and from the zone edge
-constexpr float kFxGuard = (float)(4e-6 * kFxPerRad);
-constexpr float kFxEdge = (float)((kPi - 4e-6) * kFxPerRad);
-
-__device__ __forceinline__ int angle_fx(double r)
-{
-    const double t = r * (1.0 / kTwoPi);
-    return (int)(unsigned)__double2ll_rn((t - rint(t)) * 4294967296.0);
-}
-
 // Table patch of r = (k+p) - q from fixed-point components: the lower wedge e
 // of the cell and the side of the ray between e and e + 1 (c = e or e + 1).
 // slow: within the guard band of that ray, of the zone edge, or in a cell of
