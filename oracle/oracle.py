@@ -91,6 +91,7 @@ def lib():
         L.orc_rhs.argtypes = [C.c_void_p, C.c_double, _D, _D, _D, C.c_int]
         L.orc_sigma.argtypes = [C.c_void_p, C.c_double, _D, _D, C.c_int, C.c_int, _D, _D, _D, C.c_int]
         L.orc_zfactor.argtypes = [C.c_void_p, C.c_double, _D, _D, _D, C.c_int]
+        L.orc_zfactor_targets.argtypes = [C.c_void_p, C.c_double, _D, _D, C.c_int, _I, _D, C.c_int]
         L.orc_rk4_step.argtypes = [C.c_void_p, C.c_double, C.c_double, _D, _D, C.c_int]
         L.orc_flow.argtypes = [C.c_void_p, C.POINTER(FlowOpts), _D, _D, C.POINTER(FlowResult), C.c_int]
         _lib = L
@@ -164,6 +165,15 @@ class Oracle:
         V = np.ascontiguousarray(V, dtype=np.float64); Z = np.ascontiguousarray(Z, dtype=np.float64)
         Zo = np.zeros(self.N)
         lib().orc_zfactor(self._h, float(T), _dp(V), _dp(Z), _dp(Zo), self.nthreads)
+        return Zo
+
+    def zfactor_targets(self, T, V, Z, targets):
+        """Z of the listed patches only (same arithmetic as zfactor)."""
+        V = np.ascontiguousarray(V, dtype=np.float64); Z = np.ascontiguousarray(Z, dtype=np.float64)
+        js = np.ascontiguousarray(targets, dtype=np.int32)
+        Zo = np.zeros(len(js))
+        lib().orc_zfactor_targets(self._h, float(T), _dp(V), _dp(Z), len(js), js.ctypes.data_as(_I), _dp(Zo),
+                                  self.nthreads)
         return Zo
 
     # ODE -----------------------------------------------------------------------

@@ -406,21 +406,36 @@ void orc_sigma(const orc_geom *g, double T, const double *V, const double *Z, in
     (void)nthreads;
 }
 
-/* Z_j = (1 - dRe Sigma/dw)^-1, Eq. (definition_Z), with the slope taken as  */
-/* the chord over w = xi_j +- 2T ("from outside", Sec. 3.1.1).  Returns 0 or  */
-/* ORC_NONFINITE when a value is not finite.                                 */
-int orc_zfactor(const orc_geom *g, double T, const double *V, const double *Zin,
-                double *Zout, int nthreads)
+/* Z_j = (1 - dRe Sigma/dw)^-1, Eq. (definition_Z): the derivative at       */
+/* w = xi_j, taken as the chord over w = xi_j +- 2T ("from outside" with a    */
+/* margin of 2T, Sec. 3.1.1), for the n targets js[0..n-1]; Zout[m] belongs  */
+/* to js[m].  Returns 0 or ORC_NONFINITE when a value is not finite.          */
+int orc_zfactor_targets(const orc_geom *g, double T, const double *V, const double *Zin,
+                        int n, const int *js, double *Zout, int nthreads)
 {
     int st = 0;
-    for (int j = 0; j < g->P.N; ++j) {
+    for (int m = 0; m < n; ++m) {
+        const int j = js[m];
         double xij = orc_xi(&g->P, g->kf[2 * j], g->kf[2 * j + 1]);
         double w[2] = {xij + 2.0 * T, xij - 2.0 * T}, re[2], im[2];
         orc_sigma(g, T, V, Zin, j, 2, w, re, im, nthreads);
         double slope = (re[0] - re[1]) / (4.0 * T);
-        Zout[j] = 1.0 / (1.0 - slope);
-        if (!isfinite(Zout[j])) st = ORC_NONFINITE;
+        Zout[m] = 1.0 / (1.0 - slope);
+        if (!isfinite(Zout[m])) st = ORC_NONFINITE;
     }
+    return st;
+}
+
+/* Z of every patch (the flow's Z update) */
+int orc_zfactor(const orc_geom *g, double T, const double *V, const double *Zin,
+                double *Zout, int nthreads)
+{
+    const int N = g->P.N;
+    int *js = (int *)malloc(sizeof(int) * N);
+    if (!js) return ORC_NONFINITE;
+    for (int j = 0; j < N; ++j) js[j] = j;
+    int st = orc_zfactor_targets(g, T, V, Zin, N, js, Zout, nthreads);
+    free(js);
     return st;
 }
 

@@ -103,6 +103,8 @@ void orc_sigma(const orc_geom *g, double T, const double *V, const double *Z, in
                int n_omega, const double *omega, double *re, double *im, int nthreads);
 int  orc_zfactor(const orc_geom *g, double T, const double *V, const double *Zin,
                  double *Zout, int nthreads);
+int  orc_zfactor_targets(const orc_geom *g, double T, const double *V, const double *Zin,
+                         int n, const int *js, double *Zout, int nthreads);
 
 /* ODE ------------------------------------------------------------------------ */
 void orc_rk4_step(const orc_geom *g, double lambda, double h, double *V, const double *Z,

@@ -108,3 +108,42 @@ def test_sopt_z_below_one_at_weak_coupling_wedge():
     # C4v: Z is constant on symmetry-related patches
     for g in inputs.c4v_patch_maps(N):
         assert np.allclose(Z[g], Z, rtol=1e-12)
+
+
+def _single_pole_chord(A, E, eta, centre, margin, denom):
+    """Chord of Re[A/(w + i eta - E)] = A (w - E)/((w - E)^2 + eta^2) between
+    centre - margin and centre + margin, divided by denom (closed form)."""
+    re = lambda w: A * (w - E) / ((w - E) ** 2 + eta ** 2)
+    return (re(centre + margin) - re(centre - margin)) / denom
+
+
+@pytest.mark.parametrize("case", [
+    dict(t=0.25, U=2.0, T=0.5, eta=0.05, z=1.0, qp=False),
+    dict(t=0.25, U=1.5, T=0.2, eta=0.02, z=0.8, qp=False),
+    dict(t=0.3, U=2.5, T=0.35, eta=0.1, z=0.7, qp=True),
+    dict(t=1.0, U=3.0, T=1.5, eta=0.02, z=1.0, qp=False),
+], ids=["z1", "zlines", "qp", "wide"])
+def test_z_chord_single_pole_closed_form(case):
+    """Pin of the Z chord (Eq. (definition_Z), slope "from outside" with a
+    margin of 2T, Sec. 3.1.1): on the one-point lattice (L = 1: p = q = r = 0)
+    the self-energy is a single pole, Sigma(w) = A / (w + i eta - E) with
+    E = x_0 (x_0 = Z xi_0 for quasi-particle lines, else xi_0 = -4t),
+    A = Z^3 V^2 f(x_0)(1 - f(x_0)) (W = Z^3 (2V^2 - V^2), F = f(1-f)).  Its
+    chord over xi_0 +- 2T is A (E-terms in closed form) / 4T, so Z is fixed
+    without the oracle's pole sum.  The alternative readings -- margin T,
+    denominator 2T, centre w = 0 instead of xi_0 -- give Z values far from it."""
+    t, U, T, eta, z, qp = (case[k] for k in ("t", "U", "T", "eta", "z", "qp"))
+    o = Oracle(1, mode=MODE_LATTICE, t=t, eta=eta, prop_mode=PROP_QP if qp else 0)
+    xi0 = -4.0 * t
+    x0 = z * xi0 if qp else xi0
+    f = 1.0 / (1.0 + np.exp(x0 / T))
+    A = z ** 3 * U * U * f * (1.0 - f)
+    slope = _single_pole_chord(A, x0, eta, xi0, 2 * T, 4 * T)
+    ref = 1.0 / (1.0 - slope)
+    got = o.zfactor(T, np.full((1, 1, 1), U), np.full(1, z))[0]
+    assert got == pytest.approx(ref, rel=1e-12)
+    # discriminating power of the pin: each misreading moves Z by > 1 %
+    for alt in (_single_pole_chord(A, x0, eta, xi0, T, 2 * T),        # margin T
+                _single_pole_chord(A, x0, eta, xi0, 2 * T, 2 * T),    # denominator 2T
+                _single_pole_chord(A, x0, eta, 0.0, 2 * T, 4 * T)):   # centred on w = 0
+        assert abs(1.0 / (1.0 - alt) - ref) > 1e-2 * abs(ref)
