@@ -19,6 +19,7 @@
 // the frequency grid; sigma_grid_kernel resums the moments on the grid.
 #include <algorithm>
 
+#include "atan_poly.h"
 #include "qpfrg_internal.h"
 
 namespace qpfrg {
@@ -67,19 +68,20 @@ __device__ __forceinline__ int project64(double kx, double ky, int N, int mode, 
     return (int)j;
 }
 
-// atan2 in FP32 from an odd polynomial in t = min/max on [0, 1] fitted to
-// atan(t) (degree 11, |error| < 1.7e-6 rad), then octant reflections.
-// Caller guarantees (x, y) != (0, 0).
+// atan2 in FP32 from the odd polynomial t P(t^2), t = min/max on [0, 1], a
+// Remez minimax fit of atan(t) (degree 11; coefficients and the error bound
+// kAtanErr = 1.75e-6 rad of the FP32 evaluation generated by atan_fit.py into
+// atan_poly.h), then octant reflections.  Caller guarantees (x, y) != (0, 0).
 __device__ __forceinline__ float atan2_poly(float y, float x)
 {
     const float ax = fabsf(x), ay = fabsf(y);
     const float t = __fdividef(fminf(ax, ay), fmaxf(ax, ay));
     const float s = t * t;
-    float p = fmaf(s, -0.01172242f, 0.05265559f);
-    p = fmaf(s, p, -0.11643387f);
-    p = fmaf(s, p, 0.19354323f);
-    p = fmaf(s, p, -0.33262327f);
-    p = fmaf(s, p, 0.99997723f);
+    float p = fmaf(s, kAtanC5, kAtanC4);
+    p = fmaf(s, p, kAtanC3);
+    p = fmaf(s, p, kAtanC2);
+    p = fmaf(s, p, kAtanC1);
+    p = fmaf(s, p, kAtanC0);
     float a = t * p;
     if (ay > ax) a = 1.57079633f - a;
     if (x < 0.f) a = 3.14159265f - a;
@@ -97,7 +99,8 @@ __device__ __forceinline__ float rint_add(float x, int &as_int)
 
 // FP32 wedge projection with a guard band: the FP32 momentum carries an
 // absolute error below 1.4e-6 per component (FP32 rounding of k+p, q, their
-// difference and the fold) and atan2_poly below 1.7e-6 rad, so the angle is
+// difference and the fold) and atan2_poly below 2.3e-6 rad (kAtanErr, the
+// approximate quotient t and the rounding of the octant reflections), so the angle is
 // trusted only when it lies more than 8e-6 + 8e-6/|r| rad from a wedge
 // boundary and the point is more than 4e-6 from the zone edge.  Returns -1
 // near a wedge boundary, -2 near the zone edge or the origin; jc gets the
