@@ -290,13 +290,20 @@ qpfrg_status qpfrg_set_tuning(qpfrg_t ctx, const qpfrg_tuning *t);
  * that loads this library holds until the process exits.
  *   lattice, n_p, grid_mode, propagator: as for qpfrg_create (n_p <= the
  *     static limit, else QPFRG_ERR_INVALID);
- *   d_fine: n_fine x 4 FP64 device array (kx, ky, weight, patch) in the
- *     patch-major order qpfrg_geometry returns (n_fine a multiple of n_p);
+ *   d_fine: n_fine x 4 FP64 device array (kx, ky, weight, patch) exactly as
+ *     qpfrg_geometry returns it: patch-major, n_fine / n_p points per patch
+ *     (at most 2048, the limit of qpfrg_create; else QPFRG_ERR_UNSUPPORTED).
+ *     The patch of point q is taken as q / (n_fine / n_p); the patch column is
+ *     not read, so an array in another order gives wrong Z without an error;
  *   d_kf: n_p x 2 FP64 patch representatives; d_V: n_p^3 FP64; d_Z: n_p FP64
  *     line weights (NULL = ones); T > 0; eta > 0; d_Z_out: n_p FP64 output.
  * The first call on a device looks up the device address of the scratch
  * array (with that device current) and caches it: make that first call
- * before any stream capture.  All calls share the scratch array, which keeps
+ * before any stream capture.  The cached address lives as long as the
+ * process: after cudaDeviceReset (or any teardown of the device's primary
+ * context) the entry point must not be called again in that process.  A
+ * CUDA error already pending when the call starts is returned as
+ * QPFRG_ERR_CUDA without launching anything (and is left pending).  All calls share the scratch array, which keeps
  * the last call's values; each call clears the entries it uses first.  Calls
  * that overlap on the GPU (other streams, other host threads) race. */
 #define QPFRG_STATIC_MAX_PATCHES 256

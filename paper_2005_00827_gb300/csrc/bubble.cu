@@ -549,6 +549,13 @@ static qpfrg_status launch_r(qpfrg_ctx *c, double lambda, const double *d_Z, con
                              const TransferTable<R> &qpp, const TransferTable<R> &qph, R thr)
 {
     const Problem &pb = c->pb;
+    // form_row reads two adjacent bins as one 8-byte word: rows of stride
+    // N + 2 stay 8-byte aligned only for even N (qpfrg_create enforces N % 4
+    // == 0 for wedges and N^2 % 8 == 0 for the tensor-core path)
+    if (FORM && (pb.N & 1)) {
+        c->err = "formed tensor-core operands need an even patch count";
+        return QPFRG_ERR_UNSUPPORTED;
+    }
     BubbleArgs<R> A{};
     A.pb = pb;
     A.fine = fine;

@@ -181,8 +181,9 @@ extern "C" qpfrg_status qpfrg_zfactor_static(const qpfrg_lattice *lattice, int n
     } else if (grid_mode != QPFRG_GRID_WEDGE || n_p % 4 != 0) {
         return QPFRG_ERR_INVALID;
     }
+    // the fine-grid limit of qpfrg_create: more points per patch is unsupported
+    if (A.P > 2048) return QPFRG_ERR_UNSUPPORTED;
     const size_t smem = 10 * (size_t)A.P * sizeof(double);
-    if (smem > 200 * 1024) return QPFRG_ERR_UNSUPPORTED;
     A.t = lattice->t;
     A.tp = lattice->tp;
     A.mu = lattice->mu;
@@ -193,6 +194,9 @@ extern "C" qpfrg_status qpfrg_zfactor_static(const qpfrg_lattice *lattice, int n
     A.kf = d_kf;
     A.V = d_V;
     A.Z = d_Z;
+    // an error left pending by earlier, unrelated work is not this call's:
+    // report it without launching and without clearing it
+    if (cudaPeekAtLastError() != cudaSuccess) return QPFRG_ERR_CUDA;
     cudaError_t e;
     double *slope = zstatic::scratch_for_current_device(&e);
     if (!slope) return QPFRG_ERR_CUDA;
@@ -200,9 +204,10 @@ extern "C" qpfrg_status qpfrg_zfactor_static(const qpfrg_lattice *lattice, int n
     e = cudaFuncSetAttribute(zstatic::pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return QPFRG_ERR_CUDA;
     zstatic::zero_kernel<<<1, 256, 0, st>>>(slope, n_p);
+    if (cudaGetLastError() != cudaSuccess) return QPFRG_ERR_CUDA;
     dim3 grid(div_up(n_fine, 256), n_p, n_p);
     zstatic::pair_kernel<<<grid, 256, smem, st>>>(A, slope);
+    if (cudaGetLastError() != cudaSuccess) return QPFRG_ERR_CUDA;
     zstatic::finish_kernel<<<div_up(n_p, 128), 128, 0, st>>>(slope, d_Z_out, n_p);
-    e = cudaGetLastError();
-    return e == cudaSuccess ? QPFRG_OK : QPFRG_ERR_CUDA;
+    return cudaGetLastError() == cudaSuccess ? QPFRG_OK : QPFRG_ERR_CUDA;
 }
