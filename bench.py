@@ -43,12 +43,53 @@ WORKLOAD = "np96_n32"
 METRIC = "fRG RHS evaluations/s at N_p={N} (flow steps with Z feedback)"
 UNIT = "RHS/s"
 
-# Algorithmic work per loop-kernel evaluation and per self-energy pair: issue
-# slots of the minimal formula (every instruction, MUFU included; a packed
-# FP32x2 instruction counts one half per pair) and its MUFU operations.
-BUBBLE_ISSUE_PER_EVAL, BUBBLE_MUFU_PER_EVAL = 21, 2
-SIGMA_ISSUE_PER_PAIR, SIGMA_MUFU_PER_PAIR = 36, 3
+# Algorithmic work of the method (what any implementation must do), per
+# loop-kernel evaluation: ~14 FP32 operations (partner dispersion by angle
+# addition, the loop kernel, weight and deposit) + 1 ex2 + 1 reciprocal; per
+# self-energy pair: ~20 FP32 operations + 1 ex2 + 1 reciprocal (Fermi factor
+# of r) + 2 complex reciprocals (the two chord frequencies), counted as 4 MUFU.
+# The time bound is the slowest pipe: FP32 and MUFU operations share the
+# 128 issue lanes per SM per clock, MUFU alone runs 16 per SM per clock.
+BUBBLE_FP32_PER_EVAL, BUBBLE_MUFU_PER_EVAL = 14, 2
+SIGMA_FP32_PER_PAIR, SIGMA_MUFU_PER_PAIR = 20, 4
+# issue slots of the formulas as built (instructions per unit; a packed FP32x2
+# instruction counts one half per unit): the issue efficiency of the kernels
+BUBBLE_ISSUE_AS_BUILT, SIGMA_ISSUE_AS_BUILT = 21, 36
 ISSUE_LANES_PER_SM, MUFU_PER_SM, N_SM = 128, 16, 152
+
+
+def alu_clk_per_unit(fp32, mufu):
+    """SM clocks per unit of work at the slowest pipe (issue lanes or MUFU)."""
+    return max((fp32 + mufu) / ISSUE_LANES_PER_SM, mufu / MUFU_PER_SM)
+
+
+def sigma_units(N, n):
+    """(p, q) pairs of one flow-step self-energy launch: the C4v-irreducible
+    targets 0..N/8, the mirror-line ones (0, and N/8 when 8 | N) over half of
+    the loop points p (the reduced work the kernel does)."""
+    M = N * n * n
+    mirror = (1.0 if N % 8 == 0 else 0.5) if n % 2 == 0 else 0.0
+    return (float(N // 8 + 1) - mirror) * M * M
+
+
+def bubble_units(N, M, evals_computed=None):
+    """Loop-kernel evaluations of one RHS: 2 N^2 M, or the number the library
+    reports it computed (a symmetry-reduced launch)."""
+    return float(evals_computed) if evals_computed else 2.0 * N * N * M
+
+
+def cpu_info():
+    """Host cores and CPU model of the machine the oracle runs on."""
+    info = {"nproc": os.cpu_count()}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() in ("Model name", "Architecture", "CPU(s)", "Thread(s) per core", "Socket(s)"):
+                info[k.strip()] = v.strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return info
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of the bench workload, valid while the kernel's own source (its
@@ -256,7 +297,8 @@ def run_qpfrg(args):
     dV_t = torch.from_numpy(V.ravel()).cuda()
     Z_t = torch.from_numpy(Z).cuda()
     out = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
-    forms = (("mixed", api.QPFRG_MIXED, 10), ("tc", api.QPFRG_MIXED_TC, 10), ("fp64", api.QPFRG_FP64, 3))
+    forms = (("fp64", api.QPFRG_FP64, 3), ("mixed", api.QPFRG_MIXED, 10), ("tc", api.QPFRG_MIXED_TC, 10))
+    ref_fp64 = None
     for name, pr, reps in forms:
         with api.Context(N, n, n, U=U, precision=pr, stream=stream.cuda_stream) as c2:
             if tuning is not None:
@@ -270,6 +312,11 @@ def run_qpfrg(args):
             b.record(stream)
             torch.cuda.synchronize()
             extra[f"rhs_only_{name}_per_s"] = reps / (a.elapsed_time(b) / 1e3)
+            if pr == api.QPFRG_FP64:
+                ref_fp64 = out.clone()
+            else:
+                # normwise error against the FP64 GPU form on the same inputs
+                extra[f"rhs_only_{name}_err_vs_fp64"] = float((out - ref_fp64).abs().max() / ref_fp64.abs().max())
     extra["mixed_vs_fp64_rhs"] = extra["rhs_only_mixed_per_s"] / extra["rhs_only_fp64_per_s"]
     extra["tc_vs_fp64_rhs"] = extra["rhs_only_tc_per_s"] / extra["rhs_only_fp64_per_s"]
     if "sigma_z" in prof and prof["sigma_z"][1] > 0:
@@ -286,37 +333,40 @@ def run_qpfrg(args):
     kern = {k: v for k, v in prof.items() if v[1] > 0}
     dom = max(kern, key=lambda k: kern[k][0])
     M = N * n * n
+    peak_note = (f"derived, not measured: {N_SM} SM x {clk_mhz:.0f} MHz ({peak_kind} sm_max_mhz) x nominal "
+                 f"{ISSUE_LANES_PER_SM} FP32 issue lanes and {MUFU_PER_SM} MUFU per SM per clock "
+                 "(MEASURED_PEAKS.json holds no FP32 or MUFU figure)")
     roof = None
     if dom in ("bubble", "sigma_z"):
         if dom == "bubble":
-            units = 2.0 * N * N * M
-            issue, mufu = BUBBLE_ISSUE_PER_EVAL, BUBBLE_MUFU_PER_EVAL
+            units = bubble_units(N, M)
+            fp32, mufu, built = BUBBLE_FP32_PER_EVAL, BUBBLE_MUFU_PER_EVAL, BUBBLE_ISSUE_AS_BUILT
         else:
-            # the flow evaluates the C4v-irreducible patches 0..N/8 only, and
-            # the targets on mirror lines (0, and N/8 when 8 | N) over half of
-            # the loop points p: count the reduced work
-            mirror = (1.0 if N % 8 == 0 else 0.5) if n % 2 == 0 else 0.0
-            units = (float(N // 8 + 1) - mirror) * M * M
-            issue, mufu = SIGMA_ISSUE_PER_PAIR, SIGMA_MUFU_PER_PAIR
-        clk_per_unit = max(issue / ISSUE_LANES_PER_SM, mufu / MUFU_PER_SM)
-        peak_units = N_SM * clk_mhz * 1e6 / clk_per_unit
+            units = sigma_units(N, n)
+            fp32, mufu, built = SIGMA_FP32_PER_PAIR, SIGMA_MUFU_PER_PAIR, SIGMA_ISSUE_AS_BUILT
+        peak_units = N_SM * clk_mhz * 1e6 / alu_clk_per_unit(fp32, mufu)
         avg_s = kern[dom][0] / kern[dom][1] / 1e3
         achieved = units / avg_s
+        built_peak = N_SM * clk_mhz * 1e6 * ISSUE_LANES_PER_SM / built
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved / 1e9, "peak": peak_units / 1e9,
                 "unit": "Geval/s" if dom == "bubble" else "Gpair/s", "frac": achieved / peak_units,
                 "traffic": traffic_bytes(dom, args.workload), "traffic_unit": "bytes per launch",
-                "peak_source": f"derived: {N_SM} SM x {clk_mhz:.0f} MHz "
-                f"({peak_kind} max clock), {issue} issue slots / {ISSUE_LANES_PER_SM} lanes, "
-                f"{mufu} MUFU / {MUFU_PER_SM} per SM"}
+                "units_per_launch": units, "ms_per_launch": avg_s * 1e3,
+                "work_per_unit": f"{fp32} FP32 + {mufu} MUFU (algorithmic)",
+                "peak_source": peak_note,
+                "issue_efficiency": {"issue_slots_as_built": built, "peak": built_peak / 1e9,
+                                     "frac": achieved / built_peak}}
 
     # the right-hand side's own kernels against their bounds (per RHS of the step)
     rhs_roof = {}
     if "bubble" in kern:
         evals = 2.0 * N * N * M
+        red = bubble_units(N, M)
         b_s = kern["bubble"][0] / kern["bubble"][1] / 1e3
-        b_peak = N_SM * clk_mhz * 1e6 / max(BUBBLE_ISSUE_PER_EVAL / ISSUE_LANES_PER_SM, BUBBLE_MUFU_PER_EVAL / MUFU_PER_SM)
-        rhs_roof["bubble"] = {"bound": "alu", "achieved": evals / b_s / 1e9, "peak": b_peak / 1e9, "unit": "Geval/s",
-                              "frac": evals / b_s / b_peak, "partner_map_gbs": 2.0 * N * N * M / b_s / 1e9}
+        b_peak = N_SM * clk_mhz * 1e6 / alu_clk_per_unit(BUBBLE_FP32_PER_EVAL, BUBBLE_MUFU_PER_EVAL)
+        rhs_roof["bubble"] = {"bound": "alu", "achieved": red / b_s / 1e9, "peak": b_peak / 1e9, "unit": "Geval/s",
+                              "frac": red / b_s / b_peak, "evals_per_rhs": evals, "evals_computed": red,
+                              "peak_source": peak_note}
     tc = [k for k in ("tc_gemm_pp", "tc_gemm_cr", "tc_gemm_d") if k in kern]
     if len(tc) == 3:
         # formed A operands, BF16 hi + lo (4 B per element), read once per RHS
@@ -346,8 +396,13 @@ def run_qpfrg(args):
     if not args.no_flows:
         # a complete flow of the bench workload itself (fresh context, same shapes)
         line["full_flows"].insert(0, full_flow(api, inputs, args.workload, prec, args.precision, stream, tuning))
+    if not args.no_sweep:
+        # the 128-flow phase-boundary sweep through one qpfrg_flow_batch call
+        line["sweep128"] = sweep128(api, inputs, stream, args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_seconds)
+        line["cpu_baseline_all_cores"] = cpu_baseline(args.workload, budget_s=args.cpu_seconds,
+                                                      nthreads=os.cpu_count() or 1)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -375,31 +430,74 @@ def full_flow(api, inputs, workload, prec, name, stream, tuning=None):
 
 
 # ---------------------------------------------------------------------------
-def cpu_baseline(workload, budget_s=15.0, nthreads=0):
+def cpu_baseline(workload, budget_s=15.0, nthreads=1):
     """Oracle RHS on a bounded sample of output triples of the same workload;
-    RHS/s = (triples per second) / N^3."""
+    RHS/s = (triples per second) / N^3.  nthreads > 1 runs that many triples at
+    once on host threads (the oracle call releases the interpreter lock)."""
+    import concurrent.futures as cf
+
     import numpy as np
 
-    from oracle.oracle import Oracle, lib
+    from oracle.oracle import Oracle
     from paper_2005_00827_gb300 import inputs
 
     wl = inputs.WORKLOADS[workload]
     N, n, U = wl["N"], wl["n"], wl["U"]
-    o = Oracle(N, n, n, nthreads=nthreads)
+    o = Oracle(N, n, n)
     V = inputs.random_vertex(N, U, seed=1)
     Z = inputs.z_profile(N, "aniso")
-    rng = np.random.default_rng(0)
-    done = 0
+    nthreads = max(1, int(nthreads))
+    stop = time.perf_counter() + budget_s
+
+    def worker(seed):
+        rng = np.random.default_rng(seed)
+        k = 0
+        while time.perf_counter() < stop:
+            i, j, l = rng.integers(0, N, 3)
+            o.rhs_triple(0.1, V, Z, i, j, l)
+            k += 1
+        return k
+
     t0 = time.perf_counter()
-    while time.perf_counter() - t0 < budget_s:
-        i, j, l = rng.integers(0, N, 3)
-        o.rhs_triple(0.1, V, Z, i, j, l)
-        done += 1
+    with cf.ThreadPoolExecutor(max_workers=nthreads) as ex:
+        done = sum(ex.map(worker, range(nthreads)))
     el = time.perf_counter() - t0
     value = done / el / N ** 3
-    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{done} output triples of the {workload} RHS at T=0.1 in {el:.1f} s "
-                      f"(each triple sums all {N * n * n} loop points in 3 channels)"}
+    return {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle", "host": cpu_info(),
+            "sample": f"{done} output triples of the {workload} RHS at T=0.1 in {el:.1f} s on {nthreads} "
+                      f"host thread(s) (each triple sums all {N * n * n} loop points in 3 channels); "
+                      "RHS/s = triples/s / N^3"}
+
+
+def sweep128(api, inputs, stream, args):
+    """The 128-flow phase-boundary sweep (N_p in {24,48,72,96}, 16 x 16 fine
+    grid, Z = 1, seeded draws) through one qpfrg_flow_batch call: complete
+    flows/s by CUDA events on the caller's stream (the call returns with its
+    work done), the flow steps and the outcomes."""
+    import torch
+    prec = {"mixed": api.QPFRG_MIXED, "tc": api.QPFRG_MIXED_TC, "fp64": api.QPFRG_FP64}[args.sweep_precision]
+    specs = [(d["N"], d["U"], 1.0, d["T_end"]) for d in inputs.batch_specs(128)][:args.flows]
+    o = api.qpfrg_default_options()
+    o.precision = prec
+    o.autotune = 0 if args.no_autotune else 1
+    lat, grid = api.qpfrg_lattice(1.0, 0.0, 0.0), api.qpfrg_fine_grid(16, 16, 0)
+    api.qpfrg_flow_batch(lat, grid, api.QPFRG_REG_TEMPERATURE, o,
+                         [(N, 2.0, 1.0, 0.9) for N in (24, 48, 72, 96)], stream.cuda_stream)   # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = api.qpfrg_flow_batch(lat, grid, api.QPFRG_REG_TEMPERATURE, o, specs, stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    steps = sum(r["steps"] for r in res)
+    status = {}
+    for r in res:
+        status[r["status"]] = status.get(r["status"], 0) + 1
+    return {"flows": len(specs), "flows_per_s": len(specs) / (ms / 1e3), "seconds": ms / 1e3,
+            "flow_steps": steps, "rhs_per_s": 4.0 * steps / (ms / 1e3), "statuses": status,
+            "precision": args.sweep_precision, "fine_grid": "16x16", "N_p": "24/48/72/96",
+            "flow": "T-flow from T=1 to T_end or |V|>20, dlnT=ln0.98, Z=1"}
 
 
 def run_sweep(args):
@@ -468,6 +566,8 @@ def run_reference(args):
     cb["value"] = v
     line = {"impl": "reference", "metric": METRIC.format(N=inputs.WORKLOADS[args.workload]["N"]), "value": v, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 4e3 / v,
+            "ms_per_step_kind": "extrapolated: one step is 4 RHS of N^3 triples; each timed step runs "
+                                f"{budget:.1f} s on a sample of triples and scales by N^3 / triples done",
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload},
             "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -488,6 +588,8 @@ def main():
     p.add_argument("--no-flows", action="store_true", help="skip the complete-flow timings")
     p.add_argument("--flows", type=int, default=128, help="sweep128: number of flows (first of the draws)")
     p.add_argument("--no-autotune", action="store_true", help="built-in launch shapes instead of qpfrg_autotune")
+    p.add_argument("--no-sweep", action="store_true", help="skip the 128-flow sweep summary of the default line")
+    p.add_argument("--sweep-precision", default="tc", choices=["mixed", "tc", "fp64"])
     args = p.parse_args()
     if args.warmup < 3 and args.impl == "qpfrg":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
