@@ -64,6 +64,14 @@ class FlowResult(C.Structure):
                 ("lambda_c", C.c_double), ("max_abs_v", C.c_double)]
 
 
+class GFlowOpts(C.Structure):
+    _fields_ = [("g0", C.c_double), ("g_end", C.c_double), ("dg", C.c_double), ("stop_abs_v", C.c_double),
+                ("z_feedback", C.c_int), ("katanin", C.c_int), ("a_mode", C.c_int), ("freeze_vertex", C.c_int),
+                ("max_steps", C.c_int), ("n_omega", C.c_int), ("omega", C.POINTER(C.c_double))]
+
+
+A_AVG, A_MIN, A_MAX, A_DROP = 0, 1, 2, 3
+
 _lib = None
 _D = C.POINTER(C.c_double)
 _I = C.POINTER(C.c_int)
@@ -92,6 +100,13 @@ def lib():
         L.orc_sigma.argtypes = [C.c_void_p, C.c_double, _D, _D, C.c_int, C.c_int, _D, _D, _D, C.c_int]
         L.orc_zfactor.argtypes = [C.c_void_p, C.c_double, _D, _D, _D, C.c_int]
         L.orc_zfactor_targets.argtypes = [C.c_void_p, C.c_double, _D, _D, C.c_int, _I, _D, C.c_int]
+        L.orc_sigma_gflow.argtypes = [C.c_void_p, C.c_double, _D, _D, _D, C.c_int, C.c_int, _D, _D, _D, C.c_int]
+        L.orc_gflow_zka.argtypes = [C.c_void_p, C.POINTER(GFlowOpts), C.c_double, _D, _D, _D, _D, _D, _D]
+        L.orc_gflow_rhs.argtypes = [C.c_void_p, C.POINTER(GFlowOpts), C.c_double, _D, _D, _D, _D, _D, _D, _D,
+                                    _D, _D, _D, C.c_int]
+        L.orc_gflow.argtypes = [C.c_void_p, C.POINTER(GFlowOpts), _D, _D, _D, _D, _D, C.POINTER(FlowResult),
+                                C.c_int]
+        L.orc_spectral.argtypes = [C.c_void_p, C.c_int, C.c_int, _D, _D, _D, C.c_double, _D, _D]
         L.orc_rk4_step.argtypes = [C.c_void_p, C.c_double, C.c_double, _D, _D, C.c_int]
         L.orc_flow.argtypes = [C.c_void_p, C.POINTER(FlowOpts), _D, _D, C.POINTER(FlowResult), C.c_int]
         _lib = L
@@ -175,6 +190,55 @@ class Oracle:
         lib().orc_zfactor_targets(self._h, float(T), _dp(V), _dp(Z), len(js), js.ctypes.data_as(_I), _dp(Zo),
                                   self.nthreads)
         return Zo
+
+    def spectral(self, j, omega, sigma, Zj):
+        """A(k_j, w) and its Fermi-liquid Gaussian approximation from Sigma on the grid."""
+        w = np.ascontiguousarray(omega, dtype=np.float64)
+        re = np.ascontiguousarray(np.real(sigma), dtype=np.float64)
+        im = np.ascontiguousarray(np.imag(sigma), dtype=np.float64)
+        A = np.zeros_like(w); Afl = np.zeros_like(w)
+        lib().orc_spectral(self._h, int(j), len(w), _dp(w), _dp(re), _dp(im), float(Zj), _dp(A), _dp(Afl))
+        return A, Afl
+
+    # interaction flow with the self-energy ODE ----------------------------------
+    def _gopts(self, g0=0.0, g_end=1.0, dg=0.05, omega=(), z_feedback=True, katanin=False, a_mode=A_AVG,
+               freeze_vertex=False, stop_abs_v=20.0, max_steps=100000):
+        w = np.ascontiguousarray(np.asarray(omega, dtype=np.float64))
+        self._gw = w                     # keep the grid alive for the call
+        return GFlowOpts(g0, g_end, dg, stop_abs_v, int(z_feedback), int(katanin), int(a_mode),
+                         int(freeze_vertex), max_steps, len(w), _dp(w) if len(w) else None)
+
+    def sigma_gflow(self, T, V, Z, K, j, omega):
+        V = np.ascontiguousarray(V, dtype=np.float64)
+        Z = np.ascontiguousarray(Z, dtype=np.float64); K = np.ascontiguousarray(K, dtype=np.float64)
+        w = np.ascontiguousarray(np.atleast_1d(omega), dtype=np.float64)
+        re = np.zeros_like(w); im = np.zeros_like(w)
+        lib().orc_sigma_gflow(self._h, float(T), _dp(V), _dp(Z), _dp(K), int(j), len(w), _dp(w), _dp(re), _dp(im),
+                              self.nthreads)
+        return re + 1j * im
+
+    def gflow_zka(self, gv, S, D, **kw):
+        """Z, K, A per patch and the A that enters the flow, from the state's
+        Sigma and Sigma' (arrays N x (2 + n_omega), chord points first)."""
+        o = self._gopts(**kw)
+        Sre = np.ascontiguousarray(np.real(S), dtype=np.float64); Dre = np.ascontiguousarray(np.real(D), dtype=np.float64)
+        Z, K, A = np.zeros(self.N), np.zeros(self.N), np.zeros(self.N)
+        Ab = C.c_double()
+        lib().orc_gflow_zka(self._h, C.byref(o), float(gv), _dp(Sre), _dp(Dre), _dp(Z), _dp(K), _dp(A), C.byref(Ab))
+        return Z, K, A, Ab.value
+
+    def gflow(self, U, **kw):
+        """Interaction flow from g0 with V = U, Sigma = Sigma' = 0: returns the
+        final V, Sigma and Sigma' (N x (2 + n_omega), frequencies xi_j + 2T,
+        xi_j - 2T, then the grid) and the flow outcome."""
+        o = self._gopts(**kw)
+        N, nw = self.N, 2 + o.n_omega
+        V = np.full((N, N, N), float(U))
+        Sre, Sim, Dre, Dim = (np.zeros((N, nw)) for _ in range(4))
+        r = FlowResult()
+        lib().orc_gflow(self._h, C.byref(o), _dp(V), _dp(Sre), _dp(Sim), _dp(Dre), _dp(Dim), C.byref(r), self.nthreads)
+        return dict(status=STATUS[r.status], steps=r.steps, g=r.lambda_, g_c=r.lambda_c, max_abs_v=r.max_abs_v,
+                    V=V, S=Sre + 1j * Sim, D=Dre + 1j * Dim)
 
     # ODE -----------------------------------------------------------------------
     def rk4_step(self, x, h, V, Z):

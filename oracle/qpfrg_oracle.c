@@ -252,7 +252,10 @@ static double line_xi(const orc_geom *g, const double *Z, double xi, int patch)
     return g->P.prop_mode == ORC_PROP_QP ? Z[patch] * xi : xi;
 }
 
-static double loop_weight(const orc_geom *g, double lambda, const double *Z, int pp,
+/* K (may be NULL = ones): the Katanin factor of App. A.5 on the S line of   */
+/* the g-flow, Eq. (vertex_flow_feedback_Z_with_Katanin): G S + S G with      */
+/* G = g Z G0, S = K Z^2 G0 gives g Z_a Z_b (K_a Z_a + K_b Z_b) L.             */
+static double loop_weight(const orc_geom *g, double lambda, const double *Z, const double *K, int pp,
                           double xi_p, int a, double xi_q, int b)
 {
     double xa = line_xi(g, Z, xi_p, a), xb = line_xi(g, Z, xi_q, b);
@@ -263,7 +266,8 @@ static double loop_weight(const orc_geom *g, double lambda, const double *Z, int
     }
     double T = g->P.T_fixed, gg = lambda;
     double l = pp ? orc_Lpp(xa, xb, T) : orc_Lph(xa, xb, T);
-    return gg * Z[a] * Z[b] * (Z[a] + Z[b]) * l;
+    double ka = K ? K[a] : 1.0, kb = K ? K[b] : 1.0;
+    return gg * Z[a] * Z[b] * (ka * Z[a] + kb * Z[b]) * l;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -280,8 +284,17 @@ static double loop_weight(const orc_geom *g, double lambda, const double *Z, int
 /* ------------------------------------------------------------------------- */
 #define VV(a, b, c) V[((size_t)(a) * N + (b)) * N + (c)]
 
+static void rhs_triple_k(const orc_geom *g, double lambda, const double *V, const double *Z,
+                         const double *K, int i, int j, int l, double out[3]);
+
 void orc_rhs_triple(const orc_geom *g, double lambda, const double *V, const double *Z,
                     int i, int j, int l, double out[3])
+{
+    rhs_triple_k(g, lambda, V, Z, NULL, i, j, l, out);
+}
+
+static void rhs_triple_k(const orc_geom *g, double lambda, const double *V, const double *Z,
+                         const double *K, int i, int j, int l, double out[3])
 {
     const int N = g->P.N, M = g->M;
     const orc_params *P = &g->P;
@@ -297,21 +310,21 @@ void orc_rhs_triple(const orc_geom *g, double lambda, const double *V, const dou
             double Qx = kf[2 * i] + kf[2 * j], Qy = kf[2 * i + 1] + kf[2 * j + 1];
             double qx = Qx - px, qy = Qy - py;
             int b = orc_proj(g, qx, qy);
-            double L = loop_weight(g, lambda, Z, 1, xi_p, a, orc_xi(P, qx, qy), b);
+            double L = loop_weight(g, lambda, Z, K, 1, xi_p, a, orc_xi(P, qx, qy), b);
             s_pp -= w * L * VV(i, j, a) * VV(a, b, l);
         }
         if (P->channels & ORC_CH_CR) {
             double Qx = kf[2 * l] - kf[2 * j], Qy = kf[2 * l + 1] - kf[2 * j + 1];
             double qx = px + Qx, qy = py + Qy;
             int b = orc_proj(g, qx, qy);
-            double L = loop_weight(g, lambda, Z, 0, xi_p, a, orc_xi(P, qx, qy), b);
+            double L = loop_weight(g, lambda, Z, K, 0, xi_p, a, orc_xi(P, qx, qy), b);
             s_cr -= w * L * VV(i, a, b) * VV(b, j, l);
         }
         if (P->channels & ORC_CH_D) {
             double Qx = kf[2 * i] - kf[2 * l], Qy = kf[2 * i + 1] - kf[2 * l + 1];
             double qx = px + Qx, qy = py + Qy;
             int b = orc_proj(g, qx, qy);
-            double L = loop_weight(g, lambda, Z, 0, xi_p, a, orc_xi(P, qx, qy), b);
+            double L = loop_weight(g, lambda, Z, K, 0, xi_p, a, orc_xi(P, qx, qy), b);
             s_d += w * L * (2.0 * VV(i, a, l) * VV(b, j, a)
                             - VV(a, i, l) * VV(b, j, a)
                             - VV(i, a, l) * VV(j, b, a));
@@ -322,8 +335,8 @@ void orc_rhs_triple(const orc_geom *g, double lambda, const double *V, const dou
     out[2] = s_d;
 }
 
-void orc_rhs(const orc_geom *g, double lambda, const double *V, const double *Z,
-             double *dV, int nthreads)
+static void rhs_k(const orc_geom *g, double lambda, const double *V, const double *Z, const double *K,
+                  double *dV, int nthreads)
 {
     const int N = g->P.N;
     const long n3 = (long)N * N * N;
@@ -334,10 +347,16 @@ void orc_rhs(const orc_geom *g, double lambda, const double *V, const double *Z,
     for (long idx = 0; idx < n3; ++idx) {
         int i = (int)(idx / ((long)N * N)), j = (int)((idx / N) % N), l = (int)(idx % N);
         double o[3];
-        orc_rhs_triple(g, lambda, V, Z, i, j, l, o);
+        rhs_triple_k(g, lambda, V, Z, K, i, j, l, o);
         dV[idx] = o[0] + o[1] + o[2];
     }
     (void)nthreads;
+}
+
+void orc_rhs(const orc_geom *g, double lambda, const double *V, const double *Z,
+             double *dV, int nthreads)
+{
+    rhs_k(g, lambda, V, Z, NULL, dV, nthreads);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -378,6 +397,9 @@ void orc_sigma(const orc_geom *g, double T, const double *V, const double *Z, in
             const double fp = orc_fermi(xp, T), fpc = orc_fermi(-xp, T);
             for (int q = 0; q < M; ++q) {
                 const int b = g->fpatch[q];
+                /* W = V(k,p,q) (2 V(k,p,q) - V(k,p,r)) vanishes with V(k,p,q): such a
+                   pair adds exactly zero, so it is not evaluated */
+                if (VV(j, a, b) == 0.0) continue;
                 const double qx = g->fk[2 * q], qy = g->fk[2 * q + 1];
                 const double rx = kx + px - qx, ry = ky + py - qy;
                 const int c = orc_proj(g, rx, ry);
@@ -437,6 +459,39 @@ int orc_zfactor(const orc_geom *g, double T, const double *V, const double *Zin,
     int st = orc_zfactor_targets(g, T, V, Zin, N, js, Zout, nthreads);
     free(js);
     return st;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Single-particle spectral function on the Fermi-surface patch k_j from the  */
+/* real-frequency self-energy (Sec. 3.1.1, Figs. 2-3: A(k, w) of SOPT):        */
+/*   A(w) = -(1/pi) Im [w - xi_j - Sigma(k_j, w)]^-1,                          */
+/* and its Fermi-liquid (Gaussian) approximation of Fig. 3: a Gaussian of      */
+/* weight Z_j centred on xi_j whose value there equals the full A, taken by   */
+/* linear interpolation of A on the grid w_0 < ... < w_{n-1}:                 */
+/*   A_FL(w) = A(xi_j) exp(-pi A(xi_j)^2 (w - xi_j)^2 / Z_j^2).                */
+/* Inputs: Sigma on the grid (re, im), Z_j; outputs A and A_FL on the grid.   */
+/* ------------------------------------------------------------------------- */
+void orc_spectral(const orc_geom *g, int j, int n_omega, const double *omega, const double *re,
+                  const double *im, double Zj, double *A, double *Afl)
+{
+    const double xij = orc_xi(&g->P, g->kf[2 * j], g->kf[2 * j + 1]);
+    for (int m = 0; m < n_omega; ++m) {
+        /* G = 1 / (x - i y), x = w - xi - Re Sigma, y = Im Sigma: Im G = y / (x^2 + y^2) */
+        const double x = omega[m] - xij - re[m], y = im[m];
+        const double d = x * x + y * y;
+        A[m] = d > 0.0 ? -(1.0 / M_PI) * y / d : 0.0;   /* Sigma = 0 at w = xi: delta peak, no grid value */
+    }
+    double A0 = 0.0;
+    for (int m = 0; m + 1 < n_omega; ++m)
+        if (omega[m] <= xij && xij <= omega[m + 1]) {
+            const double u = (xij - omega[m]) / (omega[m + 1] - omega[m]);
+            A0 = (1.0 - u) * A[m] + u * A[m + 1];
+            break;
+        }
+    for (int m = 0; m < n_omega; ++m) {
+        const double d = omega[m] - xij;
+        Afl[m] = A0 * exp(-M_PI * A0 * A0 * d * d / (Zj * Zj));
+    }
 }
 
 /* ------------------------------------------------------------------------- */
@@ -543,3 +598,213 @@ int orc_flow(const orc_geom *g, const orc_flow_opts *o, double *V, double *Z,
     free(Znew);
     return res->status;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Interaction flow with the self-energy ODE, App. A.2-A.5, Eq. (nutshell_2):  */
+/*   d/dg Sigma   = Sigma'                                                     */
+/*   d/dg Sigma'  = Abar Sigma' + 6 g T2[V, Z, K](w)                           */
+/*   d/dg V       = one-loop RHS with G = g Z G0, S = K Z^2 G0                 */
+/* at fixed T (T_fixed), from g0 with V = U, Sigma = Sigma' = 0 (App. B).      */
+/* Per patch j, from the chord slopes "from outside" (margin 2T, Sec. 3.1.1)  */
+/* of the state at w = xi_j +- 2T, s1 = slope Re Sigma, s2 = slope Re Sigma':  */
+/*   Z = (1 - g s1)^-1           Eq. (definition_Z) applied to g Sigma_g       */
+/*   K = 1 + g^2 s2              Eq. (K_definition) (1 without Katanin)        */
+/*   A = 2 Z (s1 + g s2)         Eq. (single_scale_propagator_extended_2)      */
+/*                               (= 2 (dZ/dg)/Z = -(2/g)(1 - Z K), Eq. (A_g_simple)) */
+/* and Abar is the mean of A over the Fermi-surface patches (Eq.              */
+/* (second_derivative_sigma_approximation)), or its minimum / maximum (the    */
+/* bracket flows of App. B), or 0 (the one-loop term dropped, App. A.4).      */
+/* T2 is the two-loop term at the static vertex, Sigma of orc_sigma with the  */
+/* line weights of a G, an S and an inner K S line averaged over their six    */
+/* assignments to the lines a, b, c:                                          */
+/*   Z_a Z_b Z_c (1/6) [K_a Z_a (Z_b + Z_c) + K_b Z_b (Z_a + Z_c) + K_c Z_c (Z_a + Z_b)] */
+/* (= Z_a Z_b Z_c (Z_a Z_b + Z_b Z_c + Z_a Z_c)/3 at K = 1); the factor 6g     */
+/* makes g Sigma_g at g = 1 the second-order self-energy of U for a frozen    */
+/* vertex and Z = 1 (Eq. (sigma_flow_simple): g Sigma_g is the self-energy    */
+/* of the bare coupling g^2 U, App. A.3).                                     */
+/* ------------------------------------------------------------------------- */
+void orc_sigma_gflow(const orc_geom *g, double T, const double *V, const double *Z, const double *K, int j,
+                     int n_omega, const double *omega, double *re, double *im, int nthreads)
+{
+    const int N = g->P.N, M = g->M;
+    const orc_params *P = &g->P;
+    const double kx = g->kf[2 * j], ky = g->kf[2 * j + 1], eta = P->eta;
+    for (int m = 0; m < n_omega; ++m) { re[m] = 0.0; im[m] = 0.0; }
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        double *lre = (double *)calloc((size_t)n_omega, sizeof(double));
+        double *lim = (double *)calloc((size_t)n_omega, sizeof(double));
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 8)
+#endif
+        for (int p = 0; p < M; ++p) {
+            const int a = g->fpatch[p];
+            const double px = g->fk[2 * p], py = g->fk[2 * p + 1];
+            const double xp = orc_xi(P, px, py);
+            const double fp = orc_fermi(xp, T), fpc = orc_fermi(-xp, T);
+            for (int q = 0; q < M; ++q) {
+                const int b = g->fpatch[q];
+                const double qx = g->fk[2 * q], qy = g->fk[2 * q + 1];
+                const double rx = kx + px - qx, ry = ky + py - qy;
+                const int c = orc_proj(g, rx, ry);
+                const double xq = orc_xi(P, qx, qy), xr = orc_xi(P, rx, ry);
+                const double F = fp * orc_fermi(-xq, T) * orc_fermi(-xr, T)
+                               + fpc * orc_fermi(xq, T) * orc_fermi(xr, T);
+                const double vab = VV(j, a, b), vac = VV(j, a, c);
+                const double lines = Z[a] * Z[b] * Z[c]
+                    * (K[a] * Z[a] * (Z[b] + Z[c]) + K[b] * Z[b] * (Z[a] + Z[c]) + K[c] * Z[c] * (Z[a] + Z[b])) / 6.0;
+                const double amp = g->fw[p] * g->fw[q] * lines * (2.0 * vab * vab - vab * vac) * F;
+                const double E = xq + xr - xp;
+                for (int m = 0; m < n_omega; ++m) {
+                    double d = omega[m] - E, den = d * d + eta * eta;
+                    lre[m] += amp * d / den;
+                    lim[m] -= amp * eta / den;
+                }
+            }
+        }
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+        for (int m = 0; m < n_omega; ++m) { re[m] += lre[m]; im[m] += lim[m]; }
+        free(lre);
+        free(lim);
+    }
+    (void)nthreads;
+}
+
+/* frequencies of patch j: xi_j + 2T, xi_j - 2T, then the grid */
+static void gflow_freqs(const orc_geom *g, const orc_gflow_opts *o, int j, double *w)
+{
+    const double T = g->P.T_fixed, xij = orc_xi(&g->P, g->kf[2 * j], g->kf[2 * j + 1]);
+    w[0] = xij + 2.0 * T;
+    w[1] = xij - 2.0 * T;
+    for (int m = 0; m < o->n_omega; ++m) w[2 + m] = o->omega[m];
+}
+
+void orc_gflow_zka(const orc_geom *g, const orc_gflow_opts *o, double gv, const double *Sre, const double *Dre,
+                   double *Z, double *K, double *A, double *Abar)
+{
+    const int N = g->P.N, nw = 2 + o->n_omega;
+    const double T = g->P.T_fixed;
+    double sum = 0.0, amin = 0.0, amax = 0.0;
+    for (int j = 0; j < N; ++j) {
+        const double s1 = (Sre[j * nw] - Sre[j * nw + 1]) / (4.0 * T);
+        const double s2 = (Dre[j * nw] - Dre[j * nw + 1]) / (4.0 * T);
+        if (o->z_feedback) {
+            Z[j] = 1.0 / (1.0 - gv * s1);
+            K[j] = o->katanin ? 1.0 + gv * gv * s2 : 1.0;
+            A[j] = 2.0 * Z[j] * (s1 + gv * s2);
+        } else {
+            Z[j] = 1.0;
+            K[j] = 1.0;
+            A[j] = 0.0;
+        }
+        sum += A[j];
+        if (j == 0 || A[j] < amin) amin = A[j];
+        if (j == 0 || A[j] > amax) amax = A[j];
+    }
+    switch (o->a_mode) {
+    case ORC_A_MIN: *Abar = amin; break;
+    case ORC_A_MAX: *Abar = amax; break;
+    case ORC_A_DROP: *Abar = 0.0; break;
+    default: *Abar = sum / N; break;
+    }
+}
+
+/* right-hand side of the whole state at g = gv */
+void orc_gflow_rhs(const orc_geom *g, const orc_gflow_opts *o, double gv, const double *V, const double *Sre,
+                   const double *Sim, const double *Dre, const double *Dim, double *dV, double *dSre,
+                   double *dSim, double *dDre, double *dDim, int nthreads)
+{
+    const int N = g->P.N, nw = 2 + o->n_omega;
+    const long n3 = (long)N * N * N;
+    double *Z = (double *)malloc(sizeof(double) * N), *K = (double *)malloc(sizeof(double) * N);
+    double *A = (double *)malloc(sizeof(double) * N), *w = (double *)malloc(sizeof(double) * nw);
+    double *tr = (double *)malloc(sizeof(double) * nw), *ti = (double *)malloc(sizeof(double) * nw);
+    double Abar;
+    orc_gflow_zka(g, o, gv, Sre, Dre, Z, K, A, &Abar);
+    if (o->freeze_vertex) memset(dV, 0, sizeof(double) * n3);
+    else rhs_k(g, gv, V, Z, K, dV, nthreads);
+    for (int j = 0; j < N; ++j) {
+        gflow_freqs(g, o, j, w);
+        orc_sigma_gflow(g, g->P.T_fixed, V, Z, K, j, nw, w, tr, ti, nthreads);
+        for (int m = 0; m < nw; ++m) {
+            const int i = j * nw + m;
+            dSre[i] = Dre[i];
+            dSim[i] = Dim[i];
+            dDre[i] = Abar * Dre[i] + 6.0 * gv * tr[m];
+            dDim[i] = Abar * Dim[i] + 6.0 * gv * ti[m];
+        }
+    }
+    free(Z); free(K); free(A); free(w); free(tr); free(ti);
+}
+
+/* RK4 in g over (V, Sigma, Sigma'); stops like orc_flow (divergence of max|V|
+   with g_c interpolated in ln max|V|, end of the flow, non-finite state) */
+int orc_gflow(const orc_geom *g, const orc_gflow_opts *o, double *V, double *Sre, double *Sim, double *Dre,
+              double *Dim, orc_flow_result *res, int nthreads)
+{
+    const int N = g->P.N, nw = 2 + o->n_omega;
+    const long n3 = (long)N * N * N, ns = (long)N * nw;
+    const long tot = n3 + 4 * ns;
+    memset(res, 0, sizeof(*res));
+    if (g->P.regulator != ORC_REG_INTERACTION) { res->status = ORC_NONFINITE; return res->status; }
+    double *y = (double *)malloc(sizeof(double) * tot), *ys = (double *)malloc(sizeof(double) * tot);
+    double *k[4], *acc = (double *)malloc(sizeof(double) * tot);
+    for (int s = 0; s < 4; ++s) k[s] = (double *)malloc(sizeof(double) * tot);
+#define PACK(dst) do { memcpy(dst, V, sizeof(double) * n3); memcpy(dst + n3, Sre, sizeof(double) * ns); \
+        memcpy(dst + n3 + ns, Sim, sizeof(double) * ns); memcpy(dst + n3 + 2 * ns, Dre, sizeof(double) * ns); \
+        memcpy(dst + n3 + 3 * ns, Dim, sizeof(double) * ns); } while (0)
+#define RHS(src, gv, out) orc_gflow_rhs(g, o, gv, src, src + n3, src + n3 + ns, src + n3 + 2 * ns, src + n3 + 3 * ns, \
+        out, out + n3, out + n3 + ns, out + n3 + 2 * ns, out + n3 + 3 * ns, nthreads)
+    PACK(y);
+    double x = o->g0;
+    int finite;
+    double m = max_abs(y, n3, &finite);
+    res->lambda = x;
+    res->max_abs_v = m;
+    for (int step = 0;; ++step) {
+        if (o->g_end - x < 1e-12) { res->status = ORC_END; break; }
+        if (step >= o->max_steps) { res->status = ORC_MAX_STEPS; break; }
+        double h = o->dg;
+        if (x + h > o->g_end) h = o->g_end - x;
+        RHS(y, x, k[0]);
+        for (long i = 0; i < tot; ++i) ys[i] = y[i] + 0.5 * h * k[0][i];
+        RHS(ys, x + 0.5 * h, k[1]);
+        for (long i = 0; i < tot; ++i) ys[i] = y[i] + 0.5 * h * k[1][i];
+        RHS(ys, x + 0.5 * h, k[2]);
+        for (long i = 0; i < tot; ++i) ys[i] = y[i] + h * k[2][i];
+        RHS(ys, x + h, k[3]);
+        for (long i = 0; i < tot; ++i) y[i] += h / 6.0 * (k[0][i] + 2.0 * k[1][i] + 2.0 * k[2][i] + k[3][i]);
+        const double m_new = max_abs(y, n3, &finite);
+        int fin_s = 1;
+        max_abs(y + n3, 4 * ns, &fin_s);
+        res->steps = step + 1;
+        res->lambda = x + h;
+        res->max_abs_v = m_new;
+        if (!finite || !fin_s) { res->status = ORC_NONFINITE; x += h; break; }
+        if (m_new > o->stop_abs_v) {
+            const double sfrac = (log(o->stop_abs_v) - log(m)) / (log(m_new) - log(m));
+            res->lambda_c = x + sfrac * h;
+            res->status = ORC_DIVERGED;
+            x += h;
+            break;
+        }
+        x += h;
+        m = m_new;
+    }
+#undef RHS
+    memcpy(V, y, sizeof(double) * n3);
+    memcpy(Sre, y + n3, sizeof(double) * ns);
+    memcpy(Sim, y + n3 + ns, sizeof(double) * ns);
+    memcpy(Dre, y + n3 + 2 * ns, sizeof(double) * ns);
+    memcpy(Dim, y + n3 + 3 * ns, sizeof(double) * ns);
+#undef PACK
+    free(y); free(ys); free(acc);
+    for (int s = 0; s < 4; ++s) free(k[s]);
+    return res->status;
+}
+

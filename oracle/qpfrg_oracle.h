@@ -106,6 +106,35 @@ int  orc_zfactor(const orc_geom *g, double T, const double *V, const double *Zin
 int  orc_zfactor_targets(const orc_geom *g, double T, const double *V, const double *Zin,
                          int n, const int *js, double *Zout, int nthreads);
 
+/* interaction flow with the self-energy ODE (App. A.2-A.5) ------------------- */
+enum { ORC_A_AVG = 0, ORC_A_MIN = 1, ORC_A_MAX = 2, ORC_A_DROP = 3 };
+
+typedef struct orc_gflow_opts {
+    double g0, g_end, dg;  /* flow parameter: start, end, RK4 step                     */
+    double stop_abs_v;     /* divergence bound on max |V|                               */
+    int z_feedback;        /* Z, K, A from the self-energy; 0: Z = K = 1, A = 0          */
+    int katanin;           /* Katanin factor K on the S lines (App. A.5)                */
+    int a_mode;            /* ORC_A_AVG / _MIN / _MAX / _DROP (App. B, App. A.4)         */
+    int freeze_vertex;     /* dV/dg = 0 (the self-energy ODE at the bare vertex)        */
+    int max_steps;
+    int n_omega;           /* frequency grid of Sigma besides xi_j +- 2T                */
+    const double *omega;
+} orc_gflow_opts;
+
+void orc_sigma_gflow(const orc_geom *g, double T, const double *V, const double *Z, const double *K, int j,
+                     int n_omega, const double *omega, double *re, double *im, int nthreads);
+void orc_gflow_zka(const orc_geom *g, const orc_gflow_opts *o, double gv, const double *Sre, const double *Dre,
+                   double *Z, double *K, double *A, double *Abar);
+void orc_gflow_rhs(const orc_geom *g, const orc_gflow_opts *o, double gv, const double *V, const double *Sre,
+                   const double *Sim, const double *Dre, const double *Dim, double *dV, double *dSre,
+                   double *dSim, double *dDre, double *dDim, int nthreads);
+int  orc_gflow(const orc_geom *g, const orc_gflow_opts *o, double *V, double *Sre, double *Sim, double *Dre,
+               double *Dim, orc_flow_result *res, int nthreads);
+
+/* spectral function and its Fermi-liquid (Gaussian) approximation ------------- */
+void orc_spectral(const orc_geom *g, int j, int n_omega, const double *omega, const double *re,
+                  const double *im, double Zj, double *A, double *Afl);
+
 /* ODE ------------------------------------------------------------------------ */
 void orc_rk4_step(const orc_geom *g, double lambda, double h, double *V, const double *Z,
                   int nthreads);
