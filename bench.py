@@ -233,6 +233,7 @@ def run_qpfrg(args):
 
     # launch shapes measured on this context's own state (untimed)
     tuning = api.qpfrg_autotune(ctx.h, 1.0) if not args.no_autotune else None
+    work = api.qpfrg_rhs_work(ctx.h)
     for _ in range(args.warmup):
         api.qpfrg_step(ctx.h, 1)
     barrier()
@@ -339,7 +340,7 @@ def run_qpfrg(args):
     roof = None
     if dom in ("bubble", "sigma_z"):
         if dom == "bubble":
-            units = bubble_units(N, M)
+            units = bubble_units(N, M, work["loop_evals"])
             fp32, mufu, built = BUBBLE_FP32_PER_EVAL, BUBBLE_MUFU_PER_EVAL, BUBBLE_ISSUE_AS_BUILT
         else:
             units = sigma_units(N, n)
@@ -361,21 +362,22 @@ def run_qpfrg(args):
     rhs_roof = {}
     if "bubble" in kern:
         evals = 2.0 * N * N * M
-        red = bubble_units(N, M)
+        red = bubble_units(N, M, work["loop_evals"])
         b_s = kern["bubble"][0] / kern["bubble"][1] / 1e3
         b_peak = N_SM * clk_mhz * 1e6 / alu_clk_per_unit(BUBBLE_FP32_PER_EVAL, BUBBLE_MUFU_PER_EVAL)
         rhs_roof["bubble"] = {"bound": "alu", "achieved": red / b_s / 1e9, "peak": b_peak / 1e9, "unit": "Geval/s",
                               "frac": red / b_s / b_peak, "evals_per_rhs": evals, "evals_computed": red,
                               "peak_source": peak_note}
-    tc = [k for k in ("tc_gemm_pp", "tc_gemm_cr", "tc_gemm_d") if k in kern]
+    tc = [k for k in ("tc_fused_pp", "tc_fused_cr", "tc_fused_d") if k in kern]
     if len(tc) == 3:
-        # formed A operands, BF16 hi + lo (4 B per element), read once per RHS
-        a_bytes = 4.0 * (2 * N ** 4 + 2 * N ** 4)
+        # three BF16 products (hi hi, hi lo, lo hi) of M = N^2 rows, N columns
+        # and K = N^2 (pp, cr) + 2 N^2 (d): 24 N^5 flop per RHS on the tensor cores
+        flop = 24.0 * N ** 5
         t_s = sum(kern[k][0] / kern[k][1] for k in tc) / 1e3
-        hbm = float(peaks.get("hbm_gbs", 6800.0))
-        rhs_roof["tc_gemm"] = {"bound": "hbm", "achieved": a_bytes / t_s / 1e9, "peak": hbm, "unit": "GB/s",
-                               "frac": a_bytes / t_s / 1e9 / hbm, "bytes_per_rhs": a_bytes,
-                               "peak_source": f"{peak_kind} hbm_gbs"}
+        bf16 = float(peaks.get("bf16_tflops", 1900.0))
+        rhs_roof["tc_fused"] = {"bound": "tensor", "achieved": flop / t_s / 1e12, "peak": bf16, "unit": "TFLOP/s",
+                                "frac": flop / t_s / 1e12 / bf16, "flop_per_rhs": flop, "ms_per_rhs": t_s * 1e3,
+                                "peak_source": f"{peak_kind} bf16_tflops (burst)"}
 
     line = {
         "metric": METRIC.format(N=N), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -387,7 +389,7 @@ def run_qpfrg(args):
                    "precision": args.precision, "l2": "inputs larger than L2 (partner maps "
                    f"{2 * N * N * M / 1e9:.2f} GB, bubble tables)", "parallelism": "replicas",
                    "tuning": tuning},
-        "e2e": e2e, "gpu_launches": int(sum(v[1] for v in prof.values())),
+        "e2e": e2e, "gpu_launches": int(sum(v[1] for v in prof.values())), "rhs_work": work,
         "kernels_ms": {k: round(v[0], 3) for k, v in kern.items()},
         "kernel_launches": {k: v[1] for k, v in kern.items()},
         "roofline": roof, "rhs_roofline": rhs_roof, "clocks": clk, **extra,

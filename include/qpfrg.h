@@ -117,6 +117,14 @@ typedef struct {
     double timeout_s;            /* wall-clock budget of one qpfrg_flow call (<=0: none) */
     int autotune;                /* qpfrg_flow_batch: nonzero tunes the launch shapes of
                                     each patch-count group (qpfrg_autotune) before stepping */
+    int no_loop_symmetry;        /* nonzero: evaluate every loop-kernel row instead of one
+                                    row per C4v orbit of (transfer, patch) (wedge mode) */
+    /* interaction flow only: the self-energy ODE of App. A.2-A.5 (state V,
+       Sigma, Sigma'; see qpfrg_read_sigma_flow) */
+    int sigma_ode;               /* nonzero: carry Sigma, Sigma' and feed Z (z_feedback) */
+    int katanin;                 /* nonzero: Katanin factor K on the S lines (App. A.5)  */
+    int a_mode;                  /* 0: patch average of A, 1: its minimum, 2: its maximum
+                                    (the bracket flows of App. B), 3: one-loop term dropped */
 } qpfrg_options;
 
 typedef struct {
@@ -174,6 +182,22 @@ qpfrg_status qpfrg_rhs(qpfrg_t ctx, double lambda, const double *d_V, const doub
 qpfrg_status qpfrg_selfenergy(qpfrg_t ctx, double lambda, const double *d_V, const double *d_Z,
                               double *d_sigma_re, double *d_sigma_im, double *d_Z_out);
 
+/* Single-particle spectral function on the patch representatives k_j from a
+ * real-frequency self-energy on the context's frequency grid (as written by
+ * qpfrg_selfenergy), the observable of Sec. 3.1.1 and Figs. 3 and 7:
+ *   A(k_j, w_m) = -(1/pi) Im [w_m - xi_j - Sigma(k_j, w_m)]^-1,
+ * and its Fermi-liquid (Gaussian) approximation of Fig. 3: a Gaussian of
+ * weight Z_j centred on xi_j with the value of A there (A interpolated
+ * linearly on the grid; 0 when xi_j lies outside it):
+ *   A_FL(k_j, w) = A0 exp(-pi A0^2 (w - xi_j)^2 / Z_j^2).
+ * d_sigma_re, d_sigma_im: N x n_omega FP64 inputs ([j][m]); d_Z: N FP64
+ * (NULL = ones); d_A: N x n_omega FP64 output; d_A_fl: N x n_omega FP64
+ * output (may be NULL).  Where Sigma vanishes exactly at w = xi_j the grid
+ * holds no value of the delta peak and A is written as 0.  Needs n_omega > 0
+ * (QPFRG_ERR_INVALID otherwise). */
+qpfrg_status qpfrg_spectral(qpfrg_t ctx, const double *d_sigma_re, const double *d_sigma_im, const double *d_Z,
+                            double *d_A, double *d_A_fl);
+
 /* Advance the context's flow state by at most n_steps RK4 steps (T-flow:
  * uniform in ln T, last step clamped onto lambda_end; g-flow: uniform in g),
  * stopping early at divergence, end of flow, non-finite state or Z out of
@@ -212,7 +236,8 @@ qpfrg_status qpfrg_flow_batch(const qpfrg_lattice *lattice, const qpfrg_fine_gri
                               const qpfrg_flow_spec *specs, void *cuda_stream, qpfrg_flow_result *results);
 
 /* Checkpoint: size in bytes of the state image (64-byte header, then V as
- * N^3 FP64, then Z as N FP64, little endian). */
+ * N^3 FP64, then Z as N FP64, then -- with the self-energy ODE -- its state
+ * [s1, s2, Re S, Im S, Re S', Im S'] (2N + 4 N n_omega FP64), little endian). */
 qpfrg_status qpfrg_state_size(qpfrg_t ctx, size_t *bytes);
 /* Copy the flow state into h_buf (host, at least qpfrg_state_size bytes;
  * page-locked memory makes the copy a direct DMA).  Synchronises the
@@ -230,6 +255,31 @@ qpfrg_status qpfrg_set_state(qpfrg_t ctx, const void *h_buf, size_t bytes);
  * (either may be NULL); enqueued on the context's stream. */
 qpfrg_status qpfrg_read_state(qpfrg_t ctx, double *d_V, double *d_Z);
 
+/* Interaction flow with the self-energy ODE (options.sigma_ode, regulator
+ * QPFRG_REG_INTERACTION, QPFRG_PROP_PAPER lines): App. A.2-A.5, Eq.
+ * (nutshell_2).  The flow state is (V, Sigma, Sigma') at fixed T = T_fixed,
+ * from g = lambda0 with Sigma = Sigma' = 0:
+ *   d/dg Sigma  = Sigma',
+ *   d/dg Sigma' = Abar Sigma' + 6 g T2(w),
+ *   d/dg V      = the one-loop RHS with G = g Z G0, S = K Z^2 G0,
+ * with per patch j, s1 and s2 the chord slopes of Re Sigma and Re Sigma' over
+ * w = xi_j +- 2T: Z = (1 - g s1)^-1 (Eq. (definition_Z) for g Sigma_g),
+ * K = 1 + g^2 s2 with the Katanin correction (Eq. (K_definition), else 1),
+ * A = 2 Z (s1 + g s2) (Eq. (single_scale_propagator_extended_2)), and Abar the
+ * patch average of A (or its minimum / maximum / 0 by options.a_mode).  Without
+ * z_feedback, Z = K = 1 and A = 0 (App. A.3 Step 1).  T2 is the two-loop term
+ * of qpfrg_selfenergy with the lines of a G, an S and an inner K S line
+ * averaged over their assignments, Z_a Z_b Z_c (1/6)[K_a Z_a (Z_b + Z_c) +
+ * K_b Z_b (Z_a + Z_c) + K_c Z_c (Z_a + Z_b)]; 6 g makes g Sigma_g at g = 1 the
+ * second-order self-energy for a frozen vertex and Z = 1 (App. A.3).
+ * Copies the current state into device buffers (each may be NULL):
+ *   d_slopes: 2N FP64, s1 then s2;
+ *   d_sigma:  4 x N x n_omega FP64, Re Sigma, Im Sigma, Re Sigma', Im Sigma'
+ *             on the frequency grid (n_omega > 0);
+ *   d_zka:    3N + 1 FP64, Z, K, A of the state and Abar.
+ * QPFRG_ERR_INVALID for a context without the self-energy ODE. */
+qpfrg_status qpfrg_read_sigma_flow(qpfrg_t ctx, double *d_slopes, double *d_sigma, double *d_zka);
+
 /* Geometry of the context as built on the host: N, the number of fine
  * points M, k_F (N x 2 FP64) and the fine points (M x 4 FP64: kx, ky,
  * weight, patch).  Any output pointer may be NULL. */
@@ -244,6 +294,23 @@ qpfrg_status qpfrg_profile_reset(qpfrg_t ctx);
 int          qpfrg_profile_count(void);
 const char  *qpfrg_profile_name(int id);
 qpfrg_status qpfrg_profile_get(qpfrg_t ctx, int id, double *ms, long long *launches);
+
+/* Work of one right-hand-side evaluation.  In wedge mode the loop kernels
+ * evaluate one row per orbit of (transfer Q, patch a) under the point group
+ * C4v and write it to every image row with its columns permuted: the
+ * dispersion and the fine grid are C4v invariant, so B[gQ][ga][gb] =
+ * B[Q][a][b] wherever the patch projection is covariant, which the context
+ * checks byte by byte on its partner maps at creation (rows that differ are
+ * evaluated by themselves).  With quasi-particle lines (QPFRG_PROP_QP) the
+ * reduction needs a C4v-symmetric Z.
+ *   loop_evals: loop-kernel evaluations of one reduced RHS;
+ *   loop_evals_full: 2 N^2 M, the evaluations of the unreduced RHS;
+ *   rows_unreduced: rows evaluated by themselves because the covariance check
+ *     failed for them.
+ * All outputs may be NULL; loop_evals equals loop_evals_full when the
+ * reduction is off (lattice mode, no_loop_symmetry). */
+qpfrg_status qpfrg_rhs_work(qpfrg_t ctx, long long *loop_evals, long long *loop_evals_full,
+                            long long *rows_unreduced);
 
 /* Launch shapes of the hot kernels; 0 in a field selects the built-in
  * heuristic.  The paper has no counterpart: these are GPU schedule choices.

@@ -31,7 +31,8 @@ EXPORTS = (
     "qpfrg_flow", "qpfrg_state_size", "qpfrg_get_state", "qpfrg_set_state", "qpfrg_read_state",
     "qpfrg_geometry", "qpfrg_set_profiling", "qpfrg_profile_reset", "qpfrg_profile_count",
     "qpfrg_profile_name", "qpfrg_profile_get", "qpfrg_last_error", "qpfrg_version", "qpfrg_destroy",
-    "qpfrg_zfactor_static", "qpfrg_flow_batch", "qpfrg_autotune", "qpfrg_set_tuning",
+    "qpfrg_zfactor_static", "qpfrg_flow_batch", "qpfrg_autotune", "qpfrg_set_tuning", "qpfrg_rhs_work",
+    "qpfrg_spectral", "qpfrg_read_sigma_flow",
 )
 
 
@@ -55,7 +56,8 @@ class qpfrg_options(C.Structure):
                 ("omega_min", C.c_double), ("omega_max", C.c_double), ("stop_abs_v", C.c_double),
                 ("step", C.c_double), ("lambda_end", C.c_double), ("z_max", C.c_double),
                 ("max_steps", C.c_int), ("T_fixed", C.c_double), ("timeout_s", C.c_double),
-                ("autotune", C.c_int)]
+                ("autotune", C.c_int), ("no_loop_symmetry", C.c_int), ("sigma_ode", C.c_int),
+                ("katanin", C.c_int), ("a_mode", C.c_int)]
 
 
 class qpfrg_tuning(C.Structure):
@@ -132,6 +134,12 @@ def load(build_if_missing: bool = True):
                                    C.POINTER(qpfrg_options), C.c_int, C.POINTER(qpfrg_flow_spec), _P,
                                    C.POINTER(qpfrg_flow_result)]
     L.qpfrg_flow_batch.restype = C.c_int
+    L.qpfrg_read_sigma_flow.argtypes = [_P, _P, _P, _P]
+    L.qpfrg_read_sigma_flow.restype = C.c_int
+    L.qpfrg_spectral.argtypes = [_P, _P, _P, _P, _P, _P]
+    L.qpfrg_spectral.restype = C.c_int
+    L.qpfrg_rhs_work.argtypes = [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
+    L.qpfrg_rhs_work.restype = C.c_int
     L.qpfrg_destroy.argtypes = [_P]
     L.qpfrg_destroy.restype = None
     for name in ("qpfrg_create", "qpfrg_rhs", "qpfrg_selfenergy", "qpfrg_step", "qpfrg_flow",
@@ -294,6 +302,22 @@ def qpfrg_zfactor_static(lattice, n_p, n_fine, grid_mode, propagator, fine, kf, 
                                      _P(cuda_stream) if cuda_stream else None, _ptr(Z_out))
     if st != QPFRG_OK:
         raise QpfrgError(st, "qpfrg_zfactor_static failed")
+
+
+def qpfrg_spectral(ctx, sigma_re, sigma_im, Z, A, A_fl):
+    _check(ctx, load().qpfrg_spectral(ctx, _ptr(sigma_re), _ptr(sigma_im), _ptr(Z), _ptr(A), _ptr(A_fl)))
+
+
+def qpfrg_read_sigma_flow(ctx, slopes, sigma, zka):
+    _check(ctx, load().qpfrg_read_sigma_flow(ctx, _ptr(slopes), _ptr(sigma), _ptr(zka)))
+
+
+def qpfrg_rhs_work(ctx) -> dict:
+    """Loop-kernel evaluations of one RHS (C4v-reduced and full) and the rows
+    evaluated by themselves because their partner maps broke covariance."""
+    a, b, r = C.c_longlong(), C.c_longlong(), C.c_longlong()
+    _check(ctx, load().qpfrg_rhs_work(ctx, C.byref(a), C.byref(b), C.byref(r)))
+    return dict(loop_evals=a.value, loop_evals_full=b.value, rows_unreduced=r.value)
 
 
 def qpfrg_last_error(ctx) -> str:

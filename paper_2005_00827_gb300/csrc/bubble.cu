@@ -11,12 +11,15 @@
 // s(a,b) = Z_a Z_b (T-flow) or g Z_a Z_b (Z_a + Z_b) (g-flow), the line
 // weights of Eq. (both_propagators_Z) / Eq. (vertex_flow_feedback_Z).
 //
-// Launch shape: one CTA of 8 warps per (patch a, chunk of Q, family).  The
-// CTA stages its wedge's fine points in shared memory; each warp takes one
-// transfer at a time, streams its partner-patch bytes (coalesced) and bins
-// the loop kernels into a private row of N accumulators.
-#include <cuda_bf16.h>
-
+// Launch shape: one CTA of 8 warps per (patch a, chunk of Q, family) -- or,
+// in wedge mode, per task of the C4v-reduced launch (symmetry.cu: one row per
+// orbit of (Q, a) under the point group, written to every image row with its
+// columns permuted).  The CTA stages its wedge's fine points in shared
+// memory; each warp takes one transfer at a time, streams its partner-patch
+// bytes (coalesced) and bins the loop kernels into a private row of N
+// accumulators.  Output: the weighted tables B_f[Q][a][b] (FP64, or FP32 for
+// the SIMT and the tensor-core contractions), every image row written with
+// coalesced stores.
 #include <algorithm>
 
 #include "qpfrg_internal.h"
@@ -30,26 +33,23 @@ struct BubbleArgs {
     TransferTable<R> qpp, qph;
     const uint8_t *part;
     const double *Z;
+    const double *K;      // Katanin factors of the interaction flow's S line (NULL = 1)
     R *B;
     R T, invT, g, thr;
     // FP32 rows accumulate as 32-bit fixed point: bin = int / fscale (finv = 1/fscale)
     float fscale, finv;
     R t, tp, mu;          // hoppings and chemical potential, already in R (no per-use conversion)
     int qchunk;
-    // formed operands of the tensor-core contraction (QPFRG_MIXED_TC)
-    const float *Vf;            // stage vertex, FP32 [k1][k2][k3]
-    const float *VT;            // VT[j][l][b] = V[b][j][l]
-    __nv_bfloat16 *App[2];      // [N^2][N^2]   hi, lo: B_pp[Q][a][b] V[Q][a]
-    __nv_bfloat16 *Acr[2];      // [N^2][N^2]   row (j,l) of Q = (l,j): B_ph[Q][a][b] V[b][j][l]
-    __nv_bfloat16 *Ad[2];       // [N^2][2N^2]  B_ph[Q][a][b] (2V[i,a,l] - V[a,i,l]) | -B_ph V[i,a,l]
-    long Kp, Kpd;               // reduction lengths of the tile layout (tile_index)
+    // C4v-reduced launch (symmetry.cu; tasks == nullptr: every row evaluated):
+    // CTA task (family, patch, first representative, count); per
+    // representative its transfer and its image rows (Q', a' | g << 16)
+    const int4 *tasks;
+    const int *repQ;
+    const int *nimg;
+    const int2 *img;
+    // batched flows: a device flag read by every CTA; 0 = nothing to do
+    const int *active;
 };
-
-__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo)
-{
-    hi = __float2bfloat16_rn(x);
-    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-}
 
 // ---- scalar helpers ---------------------------------------------------------
 __device__ __forceinline__ float fexp(float x) { return __expf(x); }
@@ -214,20 +214,6 @@ struct alignas(4 * sizeof(R)) Quad {
     R x, y, z, w;
 };
 
-// Offsets in the A-operand tile layout (tile_index with 128 rows per tile):
-// row part (tile row block and position in the core matrix) and k part.
-__device__ __forceinline__ long tile_row_base(long r, long Kp)
-{
-    return (((r >> 7) * (Kp >> 6)) << 13) + (((r & 127) >> 3) << 6) + ((r & 7) << 3);
-}
-__device__ __forceinline__ long tile_k_off(long k) { return ((k >> 6) << 13) + (((k & 63) >> 3) << 10) + (k & 7); }
-
-__device__ __forceinline__ void split_bf16x2(float x0, float x1, __nv_bfloat162 &hi, __nv_bfloat162 &lo)
-{
-    hi = __floats2bfloat162_rn(x0, x1);
-    lo = __floats2bfloat162_rn(x0 - __low2float(hi), x1 - __high2float(hi));
-}
-
 // Row accumulators.  FP32: 32-bit fixed point in units of 1/fscale, so that a
 // run's flush is one native integer shared-memory add (a float add on shared
 // memory is a compare-and-swap loop, which diverges the warp); the host picks
@@ -245,63 +231,31 @@ __device__ __forceinline__ float row_get(const float *slot, float finv)
 }
 __device__ __forceinline__ double row_get(const double *slot, float) { return *slot; }
 
-// Write-out of one transfer's row of N bins as formed tensor-core operands
-// (BF16 hi/lo in tiles); the row is cleared.  Each lane takes two adjacent
-// partner patches b, b+1 (N is a multiple of 4 here), which are adjacent in k
-// = a N + b and so share a 4-byte bf16x2 store; the vertex factors that are
-// uniform over the row are read once.
-template <bool PP, bool TFLOW>
-__device__ __forceinline__ void form_row(const BubbleArgs<float> &A, float *row, const float *Zs, float Za, int Q,
-                                         int a, int lane)
+// Column b of the image row under g (g = m | reflection << 2: b -> +-b + m N/4)
+// holds the representative's bin g^-1(b).
+__device__ __forceinline__ int img_src(int b, int off, bool refl, int N)
+{
+    const int r = refl ? off - b : b - off;
+    return r < 0 ? r + N : r;
+}
+
+// Write-out of one row to the bubble table B[fam][Qi][ai][:] of the image row
+// under g, with the line weights s(ai, b) (interaction flow: g Z_a Z_b
+// (K_a Z_a + K_b Z_b)).  The row is read, not cleared.
+template <typename R, bool TFLOW>
+__device__ __forceinline__ void table_row(const BubbleArgs<R> &A, const R *row, const R *Zs, const R *Ks, int fam,
+                                          int Qi, int ai, int g, int lane)
 {
     const int N = A.pb.N;
     const long NN = (long)N * N;
-    const long col0 = (long)a * N;
-    auto weight = [&](float Zb) { return TFLOW ? Za * Zb : A.g * Za * Zb * (Za + Zb); };
-    if (PP) {
-        const float fv = A.Vf[(long)Q * N + a];
-        const long rb = tile_row_base(Q, A.Kp);
-        for (int b = 2 * lane; b < N; b += 64) {
-            const int2 iv = *reinterpret_cast<const int2 *>(row + b);
-            const float2 v = make_float2((float)iv.x * A.finv, (float)iv.y * A.finv);
-            *reinterpret_cast<float2 *>(row + b) = make_float2(0.f, 0.f);
-            const float2 z = *reinterpret_cast<const float2 *>(Zs + b);
-            const float t0 = v.x * weight(z.x) * fv, t1 = v.y * weight(z.y) * fv;
-            __nv_bfloat162 hi, lo;
-            split_bf16x2(t0, t1, hi, lo);
-            const long o = rb + tile_k_off(col0 + b);
-            *reinterpret_cast<__nv_bfloat162 *>(A.App[0] + o) = hi;
-            *reinterpret_cast<__nv_bfloat162 *>(A.App[1] + o) = lo;
-        }
-    } else {
-        const int x = Q / N, y = Q - x * N;                  // Q = k_F(x) - k_F(y)
-        const long rcr = (long)y * N + x;                     // cr row (j,l) = (y,x)
-        const float v_ial = A.Vf[((long)x * N + a) * N + y];
-        const float v_ail = A.Vf[((long)a * N + x) * N + y];
-        const float f1 = 2.f * v_ial - v_ail, f2 = -v_ial;
-        const long rb_cr = tile_row_base(rcr, A.Kp), rb_d = tile_row_base(Q, A.Kpd);
-        const float *vt = A.VT + rcr * N;
-        for (int b = 2 * lane; b < N; b += 64) {
-            const int2 iv = *reinterpret_cast<const int2 *>(row + b);
-            const float2 v = make_float2((float)iv.x * A.finv, (float)iv.y * A.finv);
-            *reinterpret_cast<float2 *>(row + b) = make_float2(0.f, 0.f);
-            const float2 z = *reinterpret_cast<const float2 *>(Zs + b);
-            const float t0 = v.x * weight(z.x), t1 = v.y * weight(z.y);
-            const float2 c = *reinterpret_cast<const float2 *>(vt + b);
-            __nv_bfloat162 hi, lo;
-            split_bf16x2(t0 * c.x, t1 * c.y, hi, lo);
-            const long ocr = rb_cr + tile_k_off(col0 + b);
-            *reinterpret_cast<__nv_bfloat162 *>(A.Acr[0] + ocr) = hi;
-            *reinterpret_cast<__nv_bfloat162 *>(A.Acr[1] + ocr) = lo;
-            split_bf16x2(t0 * f1, t1 * f1, hi, lo);
-            const long od = rb_d + tile_k_off(col0 + b);
-            *reinterpret_cast<__nv_bfloat162 *>(A.Ad[0] + od) = hi;
-            *reinterpret_cast<__nv_bfloat162 *>(A.Ad[1] + od) = lo;
-            split_bf16x2(t0 * f2, t1 * f2, hi, lo);
-            const long od2 = rb_d + tile_k_off(NN + col0 + b);
-            *reinterpret_cast<__nv_bfloat162 *>(A.Ad[0] + od2) = hi;
-            *reinterpret_cast<__nv_bfloat162 *>(A.Ad[1] + od2) = lo;
-        }
+    const int off = (g & 3) * (N / 4);
+    const bool refl = (g & 4) != 0;
+    const R Za = Zs[ai], KZa = Ks[ai] * Za;
+    for (int b = lane; b < N; b += 32) {
+        const R v = row_get(row + img_src(b, off, refl, N), A.finv);
+        const R Zb = Zs[b];
+        const R sw = TFLOW ? Za * Zb : A.g * Za * Zb * (KZa + Ks[b] * Zb);
+        A.B[(((long)fam * NN + Qi) * N + ai) * (long)N + b] = v * sw;
     }
 }
 
@@ -316,16 +270,17 @@ __device__ __forceinline__ void form_row(const BubbleArgs<float> &A, float *row,
 // adds rarely collide), flushes the last runs through a segmented warp
 // reduction (one atomic per run of equal partners among the lanes) and writes
 // the row out.  No block barrier inside the transfer loop.
-template <typename R, bool FORM, bool PP, bool TFLOW, bool TP0>
-__device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned char *smem_raw)
+//
+// Rows k in [q0, q1): the transfer Q = k (unreduced launch) or the
+// representative k of the C4v-reduced launch, Q = repQ[k], written to each of
+// its image rows.
+template <typename R, bool PP, bool TFLOW, bool TP0>
+__device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned char *smem_raw, int a, int q0, int q1)
 {
     const int N = A.pb.N, P = A.pb.P, M = A.pb.M;
     const long NN = (long)N * N;
-    const int a = blockIdx.x;
     const int fam = PP ? 0 : 1;
     constexpr bool pp = PP;
-    const int q0 = blockIdx.y * A.qchunk;
-    const int q1 = min((long)q0 + A.qchunk, NN);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
     constexpr bool tflow = TFLOW;
     const bool qp = A.pb.propagator == QPFRG_PROP_QP;
@@ -340,7 +295,11 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
     // aligned for form_row's float2 reads
     const int RS = N + 2;
     R *rows = Zs + N;
-    for (int i = tid; i < N; i += blockDim.x) Zs[i] = A.Z ? (R)A.Z[i] : R(1);
+    R *Ks = rows + 2 * nwarp * RS;                          // N Katanin factors
+    for (int i = tid; i < N; i += blockDim.x) {
+        Zs[i] = A.Z ? (R)A.Z[i] : R(1);
+        Ks[i] = A.K ? (R)A.K[i] : R(1);
+    }
     for (int i = tid; i < 2 * nwarp * RS; i += blockDim.x) rows[i] = R(0);
     __syncthreads();
     const R Za = Zs[a];
@@ -384,7 +343,8 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
         R run_v[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int Q = h < nq ? Q0 + h * nwarp : Q0;
+            const int kq = h < nq ? Q0 + h * nwarp : Q0;
+            const int Q = A.repQ ? A.repQ[kq] : kq;
             cQx[h] = Qt.cx[Q];
             sQx[h] = Qt.sx[Q];
             cQy[h] = Qt.cy[Q];
@@ -513,49 +473,61 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
             }
             if (head) row_add(&row[key], v, A.fscale);
             __syncwarp();
-            const int Q = Q0 + h * nwarp;
-            if constexpr (!FORM) {
-                for (int b = lane; b < N; b += 32) {
-                    const R v = row_get(row + b, A.finv);
-                    row[b] = R(0);
-                    const R Zb = Zs[b];
-                    const R s = tflow ? Za * Zb : A.g * Za * Zb * (Za + Zb);
-                    A.B[(((long)fam * NN + Q) * N + a) * (long)N + b] = v * s;
+            const int kq = Q0 + h * nwarp;
+            // the row's image rows: (Q', a', g) of the representative, or the row itself
+            const int nimg = A.repQ ? A.nimg[kq] : 1;
+            for (int im = 0; im < nimg; ++im) {
+                int Qi = kq, ai = a, g = 0;
+                if (A.repQ) {
+                    const int2 e = A.img[8 * (long)kq + im];
+                    Qi = e.x;
+                    ai = e.y & 0xffff;
+                    g = e.y >> 16;
                 }
-            } else {
-                form_row<PP, TFLOW>(A, row, Zs, Za, Q, a, lane);
+                table_row<R, TFLOW>(A, row, Zs, Ks, fam, Qi, ai, g, lane);
             }
+            __syncwarp();
+            for (int b = lane; b < N; b += 32) row[b] = R(0);
             __syncwarp();
         }
     }
 }
 
-template <typename R, bool FORM, bool TP0>
+template <typename R, bool TP0>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) bubble_kernel(BubbleArgs<R> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (A.active && *A.active == 0) return;      // uniform over the grid
     const bool tflow = A.pb.regulator == QPFRG_REG_TEMPERATURE;
-    if (blockIdx.z == 0) {
-        if (tflow) bubble_body<R, FORM, true, true, TP0>(A, smem_raw);
-        else bubble_body<R, FORM, true, false, TP0>(A, smem_raw);
+    int fam, a, q0, q1;
+    if (A.tasks) {
+        const int4 t = A.tasks[blockIdx.x];
+        fam = t.x;
+        a = t.y;
+        q0 = t.z;
+        q1 = t.z + t.w;
     } else {
-        if (tflow) bubble_body<R, FORM, false, true, TP0>(A, smem_raw);
-        else bubble_body<R, FORM, false, false, TP0>(A, smem_raw);
+        const long NN = (long)A.pb.N * A.pb.N;
+        fam = blockIdx.z;
+        a = blockIdx.x;
+        q0 = blockIdx.y * A.qchunk;
+        q1 = (int)min((long)q0 + A.qchunk, NN);
+    }
+    if (fam == 0) {
+        if (tflow) bubble_body<R, true, true, TP0>(A, smem_raw, a, q0, q1);
+        else bubble_body<R, true, false, TP0>(A, smem_raw, a, q0, q1);
+    } else {
+        if (tflow) bubble_body<R, false, true, TP0>(A, smem_raw, a, q0, q1);
+        else bubble_body<R, false, false, TP0>(A, smem_raw, a, q0, q1);
     }
 }
 
-template <typename R, bool FORM>
-static qpfrg_status launch_r(qpfrg_ctx *c, double lambda, const double *d_Z, const FineTable<R> &fine,
-                             const TransferTable<R> &qpp, const TransferTable<R> &qph, R thr)
+template <typename R>
+static qpfrg_status launch_r(qpfrg_ctx *c, double lambda, const double *d_Z, const double *d_K, bool z_symmetric,
+                             const FineTable<R> &fine, const TransferTable<R> &qpp, const TransferTable<R> &qph,
+                             R thr)
 {
     const Problem &pb = c->pb;
-    // form_row reads two adjacent bins as one 8-byte word: rows of stride
-    // N + 2 stay 8-byte aligned only for even N (qpfrg_create enforces N % 4
-    // == 0 for wedges and N^2 % 8 == 0 for the tensor-core path)
-    if (FORM && (pb.N & 1)) {
-        c->err = "formed tensor-core operands need an even patch count";
-        return QPFRG_ERR_UNSUPPORTED;
-    }
     BubbleArgs<R> A{};
     A.pb = pb;
     A.fine = fine;
@@ -563,16 +535,9 @@ static qpfrg_status launch_r(qpfrg_ctx *c, double lambda, const double *d_Z, con
     A.qph = qph;
     A.part = c->d_part;
     A.Z = d_Z;
-    A.B = reinterpret_cast<R *>(c->d_B);
-    A.Vf = c->d_Vf;
-    A.VT = c->tc.VT;
-    A.Kp = c->tc.Kp;
-    A.Kpd = c->tc.Kpd;
-    for (int h = 0; h < 2; ++h) {
-        A.App[h] = c->tc.App[h];
-        A.Acr[h] = c->tc.Acr[h];
-        A.Ad[h] = c->tc.Ad[h];
-    }
+    A.K = d_K;
+    A.B = reinterpret_cast<R *>(c->loop_out ? c->loop_out : c->d_B);
+    A.active = c->loop_active;
     const bool tflow = pb.regulator == QPFRG_REG_TEMPERATURE;
     const double T = tflow ? lambda : pb.T_fixed;
     A.T = (R)T;
@@ -592,17 +557,29 @@ static qpfrg_status launch_r(qpfrg_ctx *c, double lambda, const double *d_Z, con
     A.qchunk = c->tune.bubble_qchunk > 0 ? (int)std::min<long>(c->tune.bubble_qchunk, NN)
                                          : (int)std::max(8L, std::min(64L, NN / 16));
     const int qchunks = div_up(NN, A.qchunk);
+    // C4v-reduced launch: one row per orbit (the Z-free loop kernels of
+    // quasi-particle lines depend on Z, which must then be symmetric)
+    const bool red = c->loop_red && (pb.propagator == QPFRG_PROP_PAPER || z_symmetric);
+    int ntask = 0;
+    if (red) {
+        qpfrg_status st = loop_tasks(c, A.qchunk, &ntask);
+        if (st != QPFRG_OK) return st;
+        A.tasks = c->d_ltask;
+        A.repQ = c->d_lrepQ;
+        A.nimg = c->d_lnimg;
+        A.img = c->d_limg;
+    }
     const int nthr = 256;
     const size_t smem =
-        2 * (size_t)pb.P * sizeof(Quad<R>) + ((size_t)pb.N + 2 * (nthr / 32) * (size_t)(pb.N + 2)) * sizeof(R);
+        2 * (size_t)pb.P * sizeof(Quad<R>) + (2 * (size_t)pb.N + 2 * (nthr / 32) * (size_t)(pb.N + 2)) * sizeof(R);
     if (smem > 200 * 1024) {
         c->err = "fine grid too large for the loop-kernel launch";
         return QPFRG_ERR_UNSUPPORTED;
     }
-    auto kern = pb.tp == 0.0 ? bubble_kernel<R, FORM, true> : bubble_kernel<R, FORM, false>;
+    auto kern = pb.tp == 0.0 ? bubble_kernel<R, true> : bubble_kernel<R, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(c, e, "bubble smem attribute");
-    dim3 grid(pb.N, qchunks, 2);
+    const dim3 grid = red ? dim3(ntask) : dim3(pb.N, qchunks, 2);
     prof_begin(c);
     kern<<<grid, nthr, smem, c->stream>>>(A);
     prof_end(c, K_BUBBLE);
@@ -610,16 +587,28 @@ static qpfrg_status launch_r(qpfrg_ctx *c, double lambda, const double *d_Z, con
     return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "bubble_kernel");
 }
 
-qpfrg_status launch_bubbles(qpfrg_ctx *c, double lambda, const double *d_Z)
+qpfrg_status launch_bubbles(qpfrg_ctx *c, double lambda, const double *d_Z, bool z_symmetric, const double *d_K)
 {
     if (c->opt.precision == QPFRG_FP64)
-        return launch_r<double, false>(c, lambda, d_Z, c->f64, c->qpp64, c->qph64, 1e-5);
+        return launch_r<double>(c, lambda, d_Z, d_K, z_symmetric, c->f64, c->qpp64, c->qph64, 1e-5);
     if (c->opt.precision == QPFRG_MIXED_TC) {
         qpfrg_status s = launch_tc_prep(c);       // B operands and V^T of this stage
         if (s != QPFRG_OK) return s;
-        return launch_r<float, true>(c, lambda, d_Z, c->f32, c->qpp32, c->qph32, 2e-2f);
     }
-    return launch_r<float, false>(c, lambda, d_Z, c->f32, c->qpp32, c->qph32, 2e-2f);
+    return launch_r<float>(c, lambda, d_Z, d_K, z_symmetric, c->f32, c->qpp32, c->qph32, 2e-2f);
+}
+
+// The loop kernel alone into an explicit buffer (batched flows): the table
+// B[f][Q][a][b] at Lambda with Z = 1; every CTA returns at once when
+// *active == 0.  No vertex operands are prepared.
+qpfrg_status launch_loop_rows(qpfrg_ctx *c, double lambda, float *rows, const int *active)
+{
+    c->loop_out = rows;
+    c->loop_active = active;
+    const qpfrg_status s = launch_r<float>(c, lambda, c->d_ones, nullptr, true, c->f32, c->qpp32, c->qph32, 2e-2f);
+    c->loop_out = nullptr;
+    c->loop_active = nullptr;
+    return s;
 }
 
 }  // namespace qpfrg

@@ -173,13 +173,12 @@ static qpfrg_status launch_all(qpfrg_ctx *c, const VR *V, double scale, double *
 qpfrg_status launch_contractions(qpfrg_ctx *c, const void *d_Vin, double scale, double *d_out)
 {
     if (c->opt.precision == QPFRG_MIXED_TC) {
-        // formed operands were written by the bubble kernel of this stage
-        const int N = c->pb.N, NN = N * N;
+        // the weighted tables of this stage, formed into A tiles inside the contraction
         const unsigned ch = c->pb.channels;
         qpfrg_status s = QPFRG_OK;
-        if ((ch & QPFRG_CH_PP) && (s = launch_tc_gemm(c, 0, NN, -scale, d_out, K_TC_PP))) return s;
-        if ((ch & QPFRG_CH_CR) && (s = launch_tc_gemm(c, 1, NN, -scale, d_out, K_TC_CR))) return s;
-        if ((ch & QPFRG_CH_D) && (s = launch_tc_gemm(c, 2, NN, scale, d_out, K_TC_D))) return s;
+        if ((ch & QPFRG_CH_PP) && (s = launch_tc_fused(c, 0, -scale, d_out, K_TC_PP))) return s;
+        if ((ch & QPFRG_CH_CR) && (s = launch_tc_fused(c, 1, -scale, d_out, K_TC_CR))) return s;
+        if ((ch & QPFRG_CH_D) && (s = launch_tc_fused(c, 2, scale, d_out, K_TC_D))) return s;
         return QPFRG_OK;
     }
     if (c->opt.precision == QPFRG_FP64)

@@ -18,7 +18,7 @@ namespace {
 const char *const kKernelNames[K_COUNT] = {
     "partner_map", "bubble", "contract_pp", "contract_cr", "contract_d", "sigma_z",
     "sigma_hist", "sigma_grid", "z_update", "rk_stage", "rk_final", "convert_f32",
-    "tc_prep", "tc_gemm_pp", "tc_gemm_cr", "tc_gemm_d", "kp_table",
+    "tc_prep", "tc_fused_pp", "tc_fused_cr", "tc_fused_d", "kp_table",
 };
 
 struct PendingEvent {
@@ -170,7 +170,8 @@ void qpfrg_destroy(qpfrg_t c)
     cudaStreamSynchronize(c->stream);
     cudaGetLastError();
     // per-flow state: always owned
-    void *own[] = {c->d_V, c->d_Z, c->d_Vs, c->d_k, c->d_acc, c->d_Vf, c->d_Zwork, c->d_red};
+    void *own[] = {c->d_V, c->d_Z, c->d_Vs, c->d_k, c->d_acc, c->d_Vf, c->d_Zwork, c->d_red,
+                   c->d_gy, c->d_gys, c->d_gk, c->d_gacc, c->d_gzka, c->d_gt2};
     for (void *p : own)
         if (p) cudaFree(p);
     if (c->h_red) cudaFreeHost(c->h_red);
@@ -181,10 +182,9 @@ void qpfrg_destroy(qpfrg_t c)
                         c->qph64.cy, c->qph64.sy, c->qpp32.cx, c->qpp32.sx, c->qpp32.cy, c->qpp32.sy,
                         c->qph32.cx, c->qph32.sx, c->qph32.cy, c->qph32.sy, c->d_kf, c->d_Qpp, c->d_Qph,
                         c->d_part, c->d_B, c->d_ones, c->d_sig, c->d_hist, c->d_jirr, c->d_rep,
-                        c->tc.App[0], c->tc.App[1], c->tc.Acr[0], c->tc.Acr[1], c->tc.Ad[0], c->tc.Ad[1],
                         c->tc.Bpp[0], c->tc.Bpp[1], c->tc.Bcr[0], c->tc.Bcr[1], c->tc.Bd[0], c->tc.Bd[1],
                         c->tc.VT, c->d_tc_err, c->d_xij, c->d_bnd, c->d_qxl, c->d_qyl, c->d_kp, c->d_kcs, c->d_xij_f,
-                        c->d_ptab, c->d_jgrid, c->d_repgrid};
+                        c->d_ptab, c->d_jgrid, c->d_repgrid, c->d_lrepQ, c->d_lnimg, c->d_limg, c->d_ltask};
         for (void *p : ptrs)
             if (p) cudaFree(p);
     }
@@ -252,8 +252,13 @@ qpfrg_status qpfrg_create(const qpfrg_lattice *lattice, int n_p, const qpfrg_fin
         return fail(set_err(c, QPFRG_ERR_INVALID, "unknown precision"));
     if (pb.propagator != QPFRG_PROP_PAPER && pb.propagator != QPFRG_PROP_QP)
         return fail(set_err(c, QPFRG_ERR_INVALID, "unknown propagator mode"));
-    if (c->opt.z_feedback && !tflow)
-        return fail(set_err(c, QPFRG_ERR_UNSUPPORTED, "Z feedback is implemented for the temperature flow"));
+    if (c->opt.sigma_ode && (tflow || pb.propagator != QPFRG_PROP_PAPER))
+        return fail(set_err(c, QPFRG_ERR_UNSUPPORTED,
+                            "the self-energy ODE is implemented for the interaction flow with QPFRG_PROP_PAPER lines"));
+    if (c->opt.a_mode < 0 || c->opt.a_mode > 3) return fail(set_err(c, QPFRG_ERR_INVALID, "unknown a_mode"));
+    if (c->opt.z_feedback && !tflow && !c->opt.sigma_ode)
+        return fail(set_err(c, QPFRG_ERR_UNSUPPORTED,
+                            "Z feedback of the interaction flow needs the self-energy ODE (sigma_ode)"));
     if (!(pb.eta > 0.0)) return fail(set_err(c, QPFRG_ERR_INVALID, "eta must be > 0"));
     if (c->opt.n_omega < 0 || (c->opt.n_omega > 0 && !(c->opt.omega_max >= c->opt.omega_min)))
         return fail(set_err(c, QPFRG_ERR_INVALID, "bad frequency grid"));
@@ -302,40 +307,33 @@ qpfrg_status qpfrg_create(const qpfrg_lattice *lattice, int n_p, const qpfrg_fin
     qpfrg_status s;
     if ((s = build_host_geometry(c)) != QPFRG_OK) return fail(s);
     if ((s = upload_geometry(c)) != QPFRG_OK) return fail(s);
+    if ((s = build_loop_orbits(c)) != QPFRG_OK) return fail(s);
 
     const size_t N = pb.N, n3 = N * N * N, n4 = n3 * N;
     const size_t rsz = c->opt.precision == QPFRG_FP64 ? sizeof(double) : sizeof(float);
     const bool tcmode = c->opt.precision == QPFRG_MIXED_TC;
-    c->B_bytes = tcmode ? 0 : 2 * n4 * rsz;
+    c->B_bytes = 2 * n4 * rsz;
     if (std::getenv("QPFRG_TEST_FAIL_ALLOC")) {   // host-side fault injection for tests
         c->err = "allocation failure injected by QPFRG_TEST_FAIL_ALLOC";
         return fail(QPFRG_ERR_OOM);
     }
-    if (!tcmode && (s = dev_alloc(c, (unsigned char **)&c->d_B, c->B_bytes, "bubble tables")) != QPFRG_OK)
-        return fail(s);
+    if ((s = dev_alloc(c, (unsigned char **)&c->d_B, c->B_bytes, "bubble tables")) != QPFRG_OK) return fail(s);
     if (tcmode) {
         TcBuffers &t = c->tc;
         t.Npad = (int)((N + 15) / 16 * 16);
         const size_t NN = N * N, Np = t.Npad;
-        t.Mp = (long)((NN + 127) / 128 * 128);
         t.Kp = (long)((NN + 63) / 64 * 64);
         t.Kpd = (long)((2 * NN + 63) / 64 * 64);
-        const size_t na = (size_t)t.Mp * t.Kp, nad = (size_t)t.Mp * t.Kpd;
         const size_t nb = Np * (size_t)t.Kp, nbd = Np * (size_t)t.Kpd;
         for (int h = 0; h < 2; ++h)
-            if ((s = dev_alloc(c, &t.App[h], na, "formed pp table")) ||
-                (s = dev_alloc(c, &t.Acr[h], na, "formed cr table")) ||
-                (s = dev_alloc(c, &t.Ad[h], nad, "formed d table")) ||
-                (s = dev_alloc(c, &t.Bpp[h], nb, "pp operand")) ||
-                (s = dev_alloc(c, &t.Bcr[h], nb, "cr operand")) || (s = dev_alloc(c, &t.Bd[h], nbd, "d operand")))
+            if ((s = dev_alloc(c, &t.Bpp[h], nb, "pp operand")) || (s = dev_alloc(c, &t.Bcr[h], nb, "cr operand")) ||
+                (s = dev_alloc(c, &t.Bd[h], nbd, "d operand")))
                 return fail(s);
         if ((s = dev_alloc(c, &t.VT, n3, "V transpose")) || (s = dev_alloc(c, &c->d_tc_err, 1, "tc error flag")))
             return fail(s);
-        // tile pads (rows past N^2, k past the reduction length) stay zero
+        // tile pads (rows past N, k past the reduction length) stay zero
         for (int h = 0; h < 2 && e == cudaSuccess; ++h) {
-            if ((e = cudaMemset(t.App[h], 0, na * 2)) != cudaSuccess || (e = cudaMemset(t.Acr[h], 0, na * 2)) != cudaSuccess ||
-                (e = cudaMemset(t.Ad[h], 0, nad * 2)) != cudaSuccess || (e = cudaMemset(t.Bpp[h], 0, nb * 2)) != cudaSuccess ||
-                (e = cudaMemset(t.Bcr[h], 0, nb * 2)) != cudaSuccess)
+            if ((e = cudaMemset(t.Bpp[h], 0, nb * 2)) != cudaSuccess || (e = cudaMemset(t.Bcr[h], 0, nb * 2)) != cudaSuccess)
                 break;
             e = cudaMemset(t.Bd[h], 0, nbd * 2);
         }
@@ -351,6 +349,7 @@ qpfrg_status qpfrg_create(const qpfrg_lattice *lattice, int n_p, const qpfrg_fin
         return fail(s);
     e = cudaMallocHost((void **)&c->h_red, 5 * sizeof(unsigned long long));
     if (e != cudaSuccess) return fail(cuda_fail(c, e, "cudaMallocHost"));
+    if (c->opt.sigma_ode && (s = gflow_alloc(c)) != QPFRG_OK) return fail(s);
 
     // C4v-irreducible patches 0..floor(N/8) and each patch's representative
     if (pb.mode == QPFRG_GRID_WEDGE) {
@@ -416,7 +415,7 @@ qpfrg_status qpfrg_rhs(qpfrg_t c, double lambda, const double *d_V, const double
         if ((s = launch_convert_f32(c, d_V, c->d_Vf, n3)) != QPFRG_OK) return s;
         Vin = c->d_Vf;
     }
-    if ((s = launch_bubbles(c, lambda, d_Z ? d_Z : c->d_ones)) != QPFRG_OK) return s;
+    if ((s = launch_bubbles(c, lambda, d_Z ? d_Z : c->d_ones, d_Z == nullptr)) != QPFRG_OK) return s;
     cudaError_t e = cudaMemsetAsync(d_dV, 0, n3 * sizeof(double), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "memset dV");
     return launch_contractions(c, Vin, 1.0, d_dV);
@@ -469,6 +468,10 @@ static qpfrg_status enqueue_step(qpfrg_ctx *c)
     qpfrg_status s;
     cudaError_t e;
 
+    if (c->opt.sigma_ode) {
+        // interaction flow of (V, Sigma, Sigma'): Z, K, A from the state at every stage
+        if ((s = gflow_enqueue_stages(c, x, h)) != QPFRG_OK) return s;
+    } else {
     if (c->opt.z_feedback) {
         const double T = tflow ? c->lambda : c->pb.T_fixed;
         if ((s = launch_sigma_z(c, T, c->d_V, c->d_Z, c->d_Zwork, c->c4v_state)) != QPFRG_OK) return s;
@@ -500,7 +503,7 @@ static qpfrg_status enqueue_step(qpfrg_ctx *c)
         const double xs = x + cst[st] * h;
         const double lam = tflow ? std::exp(xs) : xs;
         const double scale = tflow ? lam : 1.0;   // dV/d ln T = T dV/dT
-        if ((s = launch_bubbles(c, lam, c->d_Z)) != QPFRG_OK) return s;
+        if ((s = launch_bubbles(c, lam, c->d_Z, c->c4v_state)) != QPFRG_OK) return s;
         if ((e = cudaMemsetAsync(c->d_k, 0, n3 * sizeof(double), c->stream)) != cudaSuccess)
             return cuda_fail(c, e, "memset k");
         if ((s = launch_contractions(c, Vin, scale, c->d_k)) != QPFRG_OK) return s;
@@ -512,6 +515,7 @@ static qpfrg_status enqueue_step(qpfrg_ctx *c)
         } else if ((s = launch_rk_final(c, h, c->d_V, c->d_acc, c->d_k)) != QPFRG_OK) {
             return s;
         }
+    }
     }
     c->h_red[2] = 0;
     e = cudaMemcpyAsync(c->h_red, c->d_red, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream);
@@ -626,6 +630,7 @@ static qpfrg_status make_child(qpfrg_ctx *parent, double U, double lambda0, doub
     c->d_Vf = nullptr;
     c->d_red = nullptr;
     c->h_red = nullptr;
+    c->d_gy = c->d_gys = c->d_gk = c->d_gacc = c->d_gzka = c->d_gt2 = nullptr;
     c->err.clear();
     const size_t N = c->pb.N, n3 = N * N * N;
     qpfrg_status s = QPFRG_ERR_OOM;
@@ -639,6 +644,10 @@ static qpfrg_status make_child(qpfrg_ctx *parent, double U, double lambda0, doub
     if (cudaMallocHost((void **)&c->h_red, 5 * sizeof(unsigned long long)) != cudaSuccess) {
         qpfrg_destroy(c);
         return QPFRG_ERR_OOM;
+    }
+    if (c->opt.sigma_ode && (s = gflow_alloc(c)) != QPFRG_OK) {
+        qpfrg_destroy(c);
+        return s;
     }
     std::vector<double> h(n3, U);
     cudaError_t e = cudaMemcpy(c->d_V, h.data(), n3 * sizeof(double), cudaMemcpyHostToDevice);
@@ -675,6 +684,15 @@ qpfrg_status qpfrg_flow_batch(const qpfrg_lattice *lattice, const qpfrg_fine_gri
         const qpfrg_flow_spec &f = specs[i];
         if (!std::isfinite(f.U) || !std::isfinite(f.lambda0) || !std::isfinite(f.lambda_end)) return QPFRG_ERR_INVALID;
         if (tflow && !(f.lambda0 > 0.0 && f.lambda_end > 0.0)) return QPFRG_ERR_INVALID;
+    }
+    // the batched device path: every group's steps on the device, flows
+    // stopping there, captured as CUDA graphs (batch.cu)
+    if (batch_device_path(grid, regulator, opt, n_flows, specs)) {
+        std::string err;
+        const qpfrg_status st = flow_batch_device(lattice, grid, opt, n_flows, specs,
+                                                  reinterpret_cast<cudaStream_t>(cuda_stream), results, err);
+        if (st != QPFRG_OK) fprintf(stderr, "qpfrg_flow_batch: %s\n", err.c_str());
+        return st;
     }
     // flows grouped by patch count: one geometry, one scratch set and one stream per group
     std::vector<int> sizes;
@@ -756,7 +774,7 @@ qpfrg_status qpfrg_flow_batch(const qpfrg_lattice *lattice, const qpfrg_fine_gri
 qpfrg_status qpfrg_state_size(qpfrg_t c, size_t *bytes)
 {
     if (!c || !bytes) return QPFRG_ERR_INVALID;
-    *bytes = sizeof(StateHeader) + (n3_of(c) + c->pb.N) * sizeof(double);
+    *bytes = sizeof(StateHeader) + (n3_of(c) + c->pb.N + (c->d_gy ? gflow_small_len(c) : 0)) * sizeof(double);
     return QPFRG_OK;
 }
 
@@ -779,6 +797,9 @@ qpfrg_status qpfrg_get_state(qpfrg_t c, void *h_buf, size_t bytes)
     cudaError_t e = cudaMemcpyAsync(p, c->d_V, n3_of(c) * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(p + n3_of(c) * sizeof(double), c->d_Z, c->pb.N * sizeof(double),
+                            cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && c->d_gy)
+        e = cudaMemcpyAsync(p + (n3_of(c) + c->pb.N) * sizeof(double), c->d_gy, gflow_small_len(c) * sizeof(double),
                             cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "get_state");
@@ -823,6 +844,10 @@ qpfrg_status qpfrg_set_state(qpfrg_t c, const void *h_buf, size_t bytes)
         (e = cudaMemcpyAsync(c->d_Z, c->d_acc, c->pb.N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream)) !=
             cudaSuccess)
         return cuda_fail(c, e, "set_state");
+    if (c->d_gy &&
+        (e = cudaMemcpyAsync(c->d_gy, Z + c->pb.N, gflow_small_len(c) * sizeof(double), cudaMemcpyHostToDevice,
+                             c->stream)) != cudaSuccess)
+        return cuda_fail(c, e, "set_state (self-energy ODE)");
     c->c4v_state = wedge && c->h_red[4] == 0;
     c->status = hd.status;
     c->steps = (int)hd.steps;

@@ -112,21 +112,18 @@ struct TransferTable {   // for Q index x*N + y (pp: k_F(x)+k_F(y); ph: k_F(x)-k
     R *cx, *sx, *cy, *sy;
 };
 
-// Buffers of the tensor-core contraction (QPFRG_MIXED_TC), index 0 = hi, 1 = lo.
-// Every operand is stored in tensor-core tiles (tile_index): A operands in
-// 128-row x 64-wide tiles, rows padded to Mp, reduction length to Kp / Kpd;
-// B operands in Npad-row x 64-wide tiles.  Pads are zero.
+// Buffers of the tensor-core contraction (QPFRG_MIXED_TC), index 0 = hi, 1 = lo:
+// the vertex (B) operands in tensor-core tiles (tile_index, Npad-row x 64-wide
+// tiles, reduction length padded to Kp / Kpd with zeros) and their TMA maps.
+// The A operands are formed in shared memory by the contraction itself.
 struct TcBuffers {
-    __nv_bfloat16 *App[2] = {nullptr, nullptr};   // [Mp][Kp]   rows (i,j), k = (a,b)
-    __nv_bfloat16 *Acr[2] = {nullptr, nullptr};   // [Mp][Kp]
-    __nv_bfloat16 *Ad[2] = {nullptr, nullptr};    // [Mp][Kpd]
     __nv_bfloat16 *Bpp[2] = {nullptr, nullptr};   // [Npad][Kp]
     __nv_bfloat16 *Bcr[2] = {nullptr, nullptr};   // [Npad][Kp]
     __nv_bfloat16 *Bd[2] = {nullptr, nullptr};    // [Npad][Kpd]
     float *VT = nullptr;                          // [N][N][N]
     int Npad = 0;
-    long Mp = 0, Kp = 0, Kpd = 0;                 // N^2 up to 128; N^2 and 2 N^2 up to 64
-    CUtensorMap tmA[3][2], tmB[3][2];             // TMA maps of the tiles: [pp, cr, d][hi, lo]
+    long Kp = 0, Kpd = 0;                         // N^2 and 2 N^2 up to 64
+    CUtensorMap tmB[3][2];                        // TMA maps of the tiles: [pp, cr, d][hi, lo]
 };
 
 // Element offset of (row r, reduction index k) in the tile layout of an
@@ -145,6 +142,12 @@ __host__ __device__ inline long tile_index(long r, long k, int rows, long Kp)
 struct ProfileSlot {
     double ms = 0.0;
     long long launches = 0;
+};
+
+// Representatives of one (family, patch) of the C4v-reduced loop kernels:
+// d_lrepQ[start .. start + count) (symmetry.cu).
+struct LoopGroup {
+    int fam, a, start, count;
 };
 
 }  // namespace qpfrg
@@ -180,9 +183,25 @@ struct qpfrg_ctx {
     double *d_Qpp = nullptr, *d_Qph = nullptr;  // N^2 x 2 transfer momenta (FP64)
     uint8_t *d_part = nullptr;   // 2 x N^2 x M partner patches (pp family, then ph)
 
+    // C4v-reduced loop kernels (symmetry.cu): one row per orbit of (Q, a),
+    // written to its images; rows whose partner maps break covariance are
+    // evaluated by themselves
+    bool loop_red = false;
+    std::vector<qpfrg::LoopGroup> lgroups;
+    int *d_lrepQ = nullptr;      // transfer Q of each representative row (families concatenated)
+    int *d_lnimg = nullptr;      // number of image rows of each representative
+    int2 *d_limg = nullptr;      // 8 slots per representative: (Q', a' | g << 16)
+    int4 *d_ltask = nullptr;     // (family, patch, first representative, count) per CTA
+    long n_lrep = 0;
+    int ltask_qchunk = 0, n_ltask = 0;
+    long long loop_evals_red = 0;   // loop-kernel evaluations of one reduced RHS
+    long loop_mismatch_rows = 0;    // rows evaluated by themselves (covariance broken)
+
     // bubble tables B[f][Q][a][b] (FP32 or FP64 according to precision)
     void *d_B = nullptr;
     size_t B_bytes = 0;
+    void *loop_out = nullptr;           // set only inside launch_loop_rows
+    const int *loop_active = nullptr;   // set only inside launch_loop_rows
 
     qpfrg::TcBuffers tc;
     unsigned *d_tc_err = nullptr;   // set by a tensor-core CTA whose bounded wait expired
@@ -192,6 +211,11 @@ struct qpfrg_ctx {
     double *d_Vs = nullptr, *d_k = nullptr, *d_acc = nullptr, *d_ones = nullptr;
     float *d_Vf = nullptr;       // FP32 copy of the RHS input (MIXED)
     double *d_Zwork = nullptr;   // Z computed at the start of a step
+    // interaction flow with the self-energy ODE (gflow.cu): small state
+    // [s1, s2, Re S, Im S, Re S', Im S'], its RK4 stage, derivative and sum;
+    // Z, K, A (N each) and Abar; the binned two-loop term on the grid
+    double *d_gy = nullptr, *d_gys = nullptr, *d_gk = nullptr, *d_gacc = nullptr;
+    double *d_gzka = nullptr, *d_gt2 = nullptr;
     double *d_sig = nullptr;     // N x 2 Re Sigma at xi_j +- 2T
     int *d_jirr = nullptr;       // C4v-irreducible patches 0..N/8 (wedge mode)
     int *d_rep = nullptr;        // slot of each patch's representative in d_jirr
@@ -234,7 +258,17 @@ qpfrg_status build_host_geometry(qpfrg_ctx *c);
 qpfrg_status upload_geometry(qpfrg_ctx *c);
 
 // bubble.cu: fill the bubble tables for the given Lambda and Z (device ptr).
-qpfrg_status launch_bubbles(qpfrg_ctx *c, double lambda, const double *d_Z);
+// z_symmetric: Z is C4v symmetric (needed by the reduced launch with
+// quasi-particle lines, whose loop kernels depend on Z).
+// d_K: Katanin factors of the interaction flow's S line (nullptr = 1).
+qpfrg_status launch_bubbles(qpfrg_ctx *c, double lambda, const double *d_Z, bool z_symmetric,
+                            const double *d_K = nullptr);
+
+qpfrg_status launch_loop_rows(qpfrg_ctx *c, double lambda, float *rows, const int *active);
+
+// symmetry.cu: C4v orbits of the loop-kernel rows and the reduced launch's tasks
+qpfrg_status build_loop_orbits(qpfrg_ctx *c);
+qpfrg_status loop_tasks(qpfrg_ctx *c, int qchunk, int *ntask);
 
 // contract.cu: d_out (N^3 FP64) += scale * contraction of the bubble tables.
 // V input is FP64 (precision FP64) or FP32 (MIXED).
@@ -243,13 +277,57 @@ qpfrg_status launch_contractions(qpfrg_ctx *c, const void *d_Vin, double scale, 
 // sigma.cu
 qpfrg_status launch_sigma_z(qpfrg_ctx *c, double T, const double *d_V, const double *d_Z,
                             double *d_Zout, bool use_symmetry);
+// d_K: the interaction flow's line weights with these Katanin factors (the
+// generic kernel); nullptr: the temperature flow's Z_a Z_b Z_c
 qpfrg_status launch_sigma_grid(qpfrg_ctx *c, double T, const double *d_V, const double *d_Z,
-                               double *d_re, double *d_im);
+                               double *d_re, double *d_im, const double *d_K = nullptr);
+qpfrg_status launch_sigma_lines(qpfrg_ctx *c, double T, const double *d_V, const double *d_Z, const double *d_K);
 
-// tc_gemm.cu / tc_prep: tensor-core contraction
+// gflow.cu: interaction flow with the self-energy ODE
+long gflow_small_len(const qpfrg_ctx *c);
+qpfrg_status gflow_alloc(qpfrg_ctx *c);
+qpfrg_status gflow_enqueue_stages(qpfrg_ctx *c, double x, double h);
+
+// Per-flow vertex operands of the batched tensor-core contraction (batch.cu)
+struct TcPrepFlow {
+    const float *Vf;             // stage vertex (FP32)
+    float *VT;                   // VT[j][l][b] = V[b][j][l]
+    __nv_bfloat16 *B[3][2];      // B operands of pp, cr, d: hi, lo (tiles)
+};
+qpfrg_status launch_tc_prep_batch(qpfrg_ctx *c, const TcPrepFlow *d_flows, const int *d_status, const double *d_h_tab,
+                                  int step, int nflows);
+qpfrg_status make_tile_map(qpfrg_ctx *c, CUtensorMap *map, const void *base, long elems, int box_rows);
+// Batched flows (batch.cu): grid.z runs over the flows of a patch-count group;
+// each flow brings its table slot, stage vertex, output and B tensor maps,
+// and is skipped (uniformly, before any barrier) when it is not running or
+// has no step at this row of the schedule.
+struct TcBatch {
+    int nflows;                       // 0: a single flow (the fields below unused)
+    int step;                         // schedule row
+    double cst;                       // stage offset of h (0, 1/2, 1/2, 1)
+    const int *status;                // per flow, QPFRG_FLOW_RUNNING runs
+    const double *h_tab;              // [step][flow] step in ln T (0: no step)
+    const signed char *slot_tab;      // [step][flow] table slot
+    const double *x;                  // per flow: ln T at the start of the step
+    float *const *rows;               // table per slot
+    const float *const *Vf, *const *VT;
+    double *const *out;
+    const CUtensorMap *maps;          // [flow][ch][hi, lo]
+};
+
+qpfrg_status launch_tc_fused_batch(qpfrg_ctx *c, int ch, const TcBatch &bt, double sign);
+
+// batch.cu: batched temperature flows (qpfrg_flow_batch)
+bool batch_device_path(const qpfrg_fine_grid *grid, qpfrg_regulator regulator, const qpfrg_options &opt, int n,
+                       const qpfrg_flow_spec *specs);
+qpfrg_status flow_batch_device(const qpfrg_lattice *lattice, const qpfrg_fine_grid *grid, const qpfrg_options &opt,
+                               int n, const qpfrg_flow_spec *specs, cudaStream_t caller, qpfrg_flow_result *results,
+                               std::string &err);
+
+// tc_prep.cu / tc_fused.cu: tensor-core contraction
 qpfrg_status launch_tc_prep(qpfrg_ctx *c);
 qpfrg_status tc_make_maps(qpfrg_ctx *c);   // TMA maps of the tensor-core operand tiles
-qpfrg_status launch_tc_gemm(qpfrg_ctx *c, int ch, int M, double scale, double *out, int kid);
+qpfrg_status launch_tc_fused(qpfrg_ctx *c, int ch, double scale, double *out, int kid);
 
 // ode.cu
 qpfrg_status launch_convert_f32(qpfrg_ctx *c, const double *d_in, float *d_out, long n);

@@ -210,6 +210,10 @@ struct SigmaArgs {
     const double *kf;    // N x 2
     const double *V;     // N^3 FP64
     const double *Z;     // N
+    // interaction flow with the self-energy ODE: Katanin factors per patch
+    // (NULL otherwise); the lines then carry the weights of a G, an S and an
+    // inner K S line averaged over their assignments (see gflow.cu)
+    const double *K;
     double *sig;         // [target]: chord slope of Re Sigma over xi_j +- 2T
     double T;
     int nj;
@@ -273,12 +277,14 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
     R *s_rec = reinterpret_cast<R *>(smem_raw);          // P x REC
     R *s_VZ = s_rec + (size_t)REC * P;                   // N x {V[j][a][c], Z_c}
     float4 *s_bnd = reinterpret_cast<float4 *>(s_VZ + 2 * N + (2 * N * sizeof(R)) % 16 / sizeof(R));
+    R *s_K = reinterpret_cast<R *>(s_bnd + N);           // N Katanin factors (interaction-flow lines)
 
     const double kx = A.kf[2 * j], ky = A.kf[2 * j + 1];
     for (int i = tid; i < N; i += blockDim.x) {
         s_VZ[2 * i] = (R)A.V[((long)j * N + a) * N + i];
         s_VZ[2 * i + 1] = A.Z ? (R)A.Z[i] : R(1);
         if (f32 && wedge) s_bnd[i] = A.bnd[i];
+        if (A.K) s_K[i] = (R)A.K[i];
     }
     __shared__ R s_k[4];
     if (tid == 0) {
@@ -342,6 +348,9 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
         sfermi(xq, invT, fq, fcq);
         const R vab = s_VZ[2 * b];
         const R pref = Za * Zb * A.fine.w[q];
+        const bool glines = A.K != nullptr;
+        const R uab = glines ? s_K[a] * Za * Zb + s_K[b] * Zb * Za : R(0);   // K_a Z_a Z_b + K_b Z_b Z_a
+        const R kza = glines ? s_K[a] * Za : R(0), kzb = glines ? s_K[b] * Zb : R(0);
         const R d0shift = A.xij_r[j], twoT = A.twoT_r;
         const R eta2 = eta * eta;
         const float inv_dth = (float)(N / kTwoPi), dth = (float)(kTwoPi / N);
@@ -389,7 +398,9 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
             R fr, fcr;
             sfermi(xr, invT, fr, fcr);
             const R F = r[7] * fcq * fcr + r[8] * fq * fr;
-            const R amp = r[9] * pref * Zc * (R(2) * vab * vab - vab * vac) * F;
+            R amp = r[9] * pref * Zc * (R(2) * vab * vab - vab * vac) * F;
+            if (glines)   // (1/6)[K_a Z_a (Z_b + Z_c) + K_b Z_b (Z_a + Z_c) + K_c Z_c (Z_a + Z_b)]
+                amp *= (uab + Zc * (kza + kzb) + s_K[c] * Zc * (Za + Zb)) * R(1.0 / 6.0);
             const R E = xq + xr - r[6];
             if (HIST) {
                 const double eb = ((double)E - A.e_min) * A.inv_h;
@@ -1101,7 +1112,7 @@ template <typename R>
 static qpfrg_status launch_sigma(qpfrg_ctx *c, bool hist, SigmaArgs<R> &A, int kid)
 {
     const int P = c->pb.P, N = c->pb.N;
-    const size_t smem = (size_t)(REC * P + 2 * N) * sizeof(R) + 16 + (size_t)N * sizeof(float4);
+    const size_t smem = (size_t)(REC * P + 2 * N) * sizeof(R) + 16 + (size_t)N * sizeof(float4) + (size_t)N * sizeof(R);
     if (sizeof(R) == 4) {
         const qpfrg_status s = launch_kp_table(c, A.jlist, A.nj);
         if (s != QPFRG_OK) return s;
@@ -1208,6 +1219,7 @@ static void fill_args(qpfrg_ctx *c, SigmaArgs<R> &A, const FineTable<R> &fine, d
     A.kf = c->d_kf;
     A.V = d_V;
     A.Z = d_Z;
+    A.K = nullptr;
     A.sig = c->d_sig;
     A.T = T;
     A.nj = c->pb.N;
@@ -1322,8 +1334,27 @@ static int grid_bins(const qpfrg_ctx *c, double e_min, double e_max)
     return nb;
 }
 
+// Chord slopes of the two-loop term with the interaction flow's line weights
+// (Katanin factors d_K, ones without the correction) for every patch, into
+// c->d_sig: the generic kernel, exact projection.
+qpfrg_status launch_sigma_lines(qpfrg_ctx *c, double T, const double *d_V, const double *d_Z, const double *d_K)
+{
+    cudaError_t e = cudaMemsetAsync(c->d_sig, 0, 2 * (size_t)c->pb.N * sizeof(double), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "memset sigma");
+    if (c->opt.precision == QPFRG_FP64) {
+        SigmaArgs<double> A;
+        fill_args(c, A, c->f64, T, d_V, d_Z);
+        A.K = d_K;
+        return launch_sigma(c, false, A, K_SIGMA_Z);
+    }
+    SigmaArgs<float> A;
+    fill_args(c, A, c->f32, T, d_V, d_Z);
+    A.K = d_K;
+    return launch_sigma(c, false, A, K_SIGMA_Z);
+}
+
 qpfrg_status launch_sigma_grid(qpfrg_ctx *c, double T, const double *d_V, const double *d_Z, double *d_re,
-                               double *d_im)
+                               double *d_im, const double *d_K)
 {
     const int N = c->pb.N, n_omega = c->opt.n_omega;
     // pole energies E = x_q + x_r - x_p lie in [2 min x - max x, 2 max x - min x]
@@ -1362,7 +1393,7 @@ qpfrg_status launch_sigma_grid(qpfrg_ctx *c, double T, const double *d_V, const 
     const double h = (e_max - e_min) / nbins;
     qpfrg_status s;
     bool sym = false;
-    if (c->opt.precision != QPFRG_FP64 && c->d_ptab && sigma_fast_smem(c, nbins) <= 226 * 1024) {
+    if (!d_K && c->opt.precision != QPFRG_FP64 && c->d_ptab && sigma_fast_smem(c, nbins) <= 226 * 1024) {
         // FP32 wedge grid: table projection, histogram in shared memory; a
         // C4v-symmetric (V, Z) needs only the irreducible targets
         if (c->d_jgrid) {
@@ -1373,6 +1404,7 @@ qpfrg_status launch_sigma_grid(qpfrg_ctx *c, double T, const double *d_V, const 
     } else if (c->opt.precision == QPFRG_FP64) {
         SigmaArgs<double> A;
         fill_args(c, A, c->f64, T, d_V, d_Z);
+        A.K = d_K;
         A.e_min = e_min;
         A.inv_h = 1.0 / h;
         A.nbins = nbins;
@@ -1380,6 +1412,7 @@ qpfrg_status launch_sigma_grid(qpfrg_ctx *c, double T, const double *d_V, const 
     } else {
         SigmaArgs<float> A;
         fill_args(c, A, c->f32, T, d_V, d_Z);
+        A.K = d_K;
         A.e_min = e_min;
         A.inv_h = 1.0 / h;
         A.nbins = nbins;
@@ -1398,3 +1431,65 @@ qpfrg_status launch_sigma_grid(qpfrg_ctx *c, double T, const double *d_V, const 
 }
 
 }  // namespace qpfrg
+
+namespace qpfrg {
+
+// Spectral function of patch j on the frequency grid, A = -(1/pi) Im G with
+// G = 1/(w - xi_j - Sigma), and its Fermi-liquid (Gaussian) approximation: a
+// Gaussian of weight Z_j centred on xi_j, equal to A there (linear
+// interpolation on the grid): A_FL = A0 exp(-pi A0^2 (w - xi_j)^2 / Z_j^2).
+// One CTA per patch; A at the grid points, then A0 and A_FL.
+__global__ void spectral_kernel(const double *re, const double *im, const double *Z, const double *xij, int n_omega,
+                                double w0, double dw, double *A, double *Afl)
+{
+    const int j = blockIdx.x;
+    const double x0 = xij[j];
+    const double *sr = re + (long)j * n_omega, *si = im + (long)j * n_omega;
+    double *a = A + (long)j * n_omega;
+    for (int m = threadIdx.x; m < n_omega; m += blockDim.x) {
+        const double x = w0 + dw * m - x0 - sr[m], y = si[m];
+        const double d = x * x + y * y;
+        a[m] = d > 0.0 ? -y / (kPi * d) : 0.0;    // Sigma = 0 exactly at w = xi: no grid value
+    }
+    __syncthreads();
+    __shared__ double A0;
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        if (n_omega > 1 && dw > 0.0) {
+            const double t = (x0 - w0) / dw;
+            long m0 = (long)floor(t);
+            if (m0 == n_omega - 1 && t == (double)m0) m0 -= 1;   // xi on the last grid point
+            if (m0 >= 0 && m0 + 1 < n_omega) {
+                const double u = t - (double)m0;
+                v = (1.0 - u) * a[m0] + u * a[m0 + 1];
+            }
+        }
+        A0 = v;
+    }
+    __syncthreads();
+    if (!Afl) return;
+    const double zj = Z ? Z[j] : 1.0;
+    const double k = kPi * A0 * A0 / (zj * zj);
+    for (int m = threadIdx.x; m < n_omega; m += blockDim.x) {
+        const double d = w0 + dw * m - x0;
+        Afl[(long)j * n_omega + m] = A0 * exp(-k * d * d);
+    }
+}
+
+}  // namespace qpfrg
+
+extern "C" qpfrg_status qpfrg_spectral(qpfrg_t c, const double *d_sigma_re, const double *d_sigma_im, const double *d_Z,
+                                       double *d_A, double *d_A_fl)
+{
+    using namespace qpfrg;
+    if (!c) return QPFRG_ERR_INVALID;
+    if (c->opt.n_omega < 1 || !d_sigma_re || !d_sigma_im || !d_A) {
+        c->err = "qpfrg_spectral needs the frequency grid (n_omega > 0), Sigma and an output";
+        return QPFRG_ERR_INVALID;
+    }
+    const int n = c->opt.n_omega;
+    const double w0 = c->opt.omega_min, dw = n > 1 ? (c->opt.omega_max - c->opt.omega_min) / (n - 1) : 0.0;
+    spectral_kernel<<<c->pb.N, 256, 0, c->stream>>>(d_sigma_re, d_sigma_im, d_Z, c->d_xij, n, w0, dw, d_A, d_A_fl);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "spectral_kernel");
+}

@@ -1,0 +1,233 @@
+// C4v orbits of the loop-kernel rows (wedge mode).
+//
+// The point group C4v of the square lattice acts on the wedge patches as
+// g = (m, s): j -> s j + m N/4 (mod N), s = +-1, on the transfers
+// Q = (x, y) (Q = k_F(x) +- k_F(y)) as (x, y) -> (g x, g y), and on the fine
+// points of a patch as (a, t, r) -> (g a, t, r) for the rotations and
+// (g a, n_theta - 1 - t, r) for the reflections.  The dispersion (Eq.
+// (free_dispersion_xi)) and the quadrature weights are invariant, and where
+// the patch projection is covariant, proj(g k) = g proj(k), the Z-free binned
+// loop kernels satisfy
+//     B_f[g Q][g a][g b] = B_f[Q][a][b].
+// So one row per orbit of (Q, a) is evaluated and written to every image,
+// its columns permuted by g (the Z weights and vertex factors are applied per
+// image).  Covariance is not assumed: check_covariance_kernel compares every
+// image row of the partner maps with its representative's row, byte by byte,
+// and a row that differs anywhere is evaluated by itself.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "qpfrg_internal.h"
+
+namespace qpfrg {
+
+// g = m | (reflection << 2) acting on a patch index
+__host__ __device__ inline int c4v_apply(int g, int j, int N)
+{
+    const int off = (g & 3) * (N / 4);
+    int r = (g & 4) ? off - j : j + off;
+    r %= N;
+    return r < 0 ? r + N : r;
+}
+
+// inverse element: rotations by m -> by 4 - m; every reflection is an involution
+__host__ __device__ inline int c4v_inverse(int g) { return (g & 4) ? g : ((4 - (g & 3)) & 3); }
+
+// flag[f][Q N + a] = 1 where the partner-map row (f, Q, a) is not the image
+// of its representative's row under g.  rep[Q N + a] = representative's Q N + a,
+// gof[Q N + a] = g with (Q, a) = g (representative).
+__global__ void check_covariance_kernel(const uint8_t *__restrict__ part, const int *__restrict__ rep,
+                                        const uint8_t *__restrict__ gof, uint8_t *__restrict__ flag, int N, int M,
+                                        int P, int nt, int nr)
+{
+    const int Q = blockIdx.x, f = blockIdx.y;
+    const long NN = (long)N * N;
+    __shared__ int bad;
+    for (int a = 0; a < N; ++a) {
+        const long row = (long)Q * N + a;
+        const int r = rep[row];
+        if (r == row) continue;                    // uniform over the block
+        const int g = gof[row];
+        const int Qr = r / N, ar = r - Qr * N;
+        const uint8_t *src = part + ((long)f * NN + Qr) * (long)M + (long)ar * P;
+        const uint8_t *dst = part + ((long)f * NN + Q) * (long)M + (long)a * P;
+        if (threadIdx.x == 0) bad = 0;
+        __syncthreads();
+        int mine = 0;
+        for (int li = threadIdx.x; li < P; li += blockDim.x) {
+            const int t = li / nr, s = li - t * nr;
+            const int ts = (g & 4) ? nt - 1 - t : t;   // the representative's point mapped onto (t, s)
+            const int want = c4v_apply(g, src[part_byte(ts, s, nt, nr)], N);
+            if (dst[part_byte(t, s, nt, nr)] != want) mine = 1;
+        }
+        if (mine) bad = 1;
+        __syncthreads();
+        if (threadIdx.x == 0) flag[(long)f * NN * N + row] = (uint8_t)bad;
+        __syncthreads();
+    }
+}
+
+qpfrg_status build_loop_orbits(qpfrg_ctx *c)
+{
+    c->loop_red = false;
+    if (c->pb.mode != QPFRG_GRID_WEDGE || c->pb.N % 4 != 0 || c->opt.no_loop_symmetry) return QPFRG_OK;
+    const int N = c->pb.N;
+    const long NN = (long)N * N, rows = NN * N;
+    // canonical representative of every (Q, a): the image with the smallest
+    // (a, Q); its patch lies in the fundamental domain 0..N/8
+    std::vector<int> rep(rows);
+    std::vector<uint8_t> gof(rows);
+    for (int x = 0; x < N; ++x)
+        for (int y = 0; y < N; ++y)
+            for (int a = 0; a < N; ++a) {
+                long best = -1;
+                int bg = 0;
+                for (int g = 0; g < 8; ++g) {
+                    const long ga = c4v_apply(g, a, N);
+                    const long gQ = (long)c4v_apply(g, x, N) * N + c4v_apply(g, y, N);
+                    const long key = ga * NN + gQ;
+                    if (best < 0 || key < best) {
+                        best = key;
+                        bg = g;
+                    }
+                }
+                const long ra = best / NN, rQ = best - ra * NN;
+                const long row = ((long)x * N + y) * N + a;
+                rep[row] = (int)(rQ * N + ra);
+                gof[row] = (uint8_t)c4v_inverse(bg);    // (Q, a) = g^-1 applied to the representative
+            }
+    int *d_rep = nullptr;
+    uint8_t *d_g = nullptr, *d_flag = nullptr;
+    auto release = [&]() {
+        cudaFree(d_rep);
+        cudaFree(d_g);
+        cudaFree(d_flag);
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc((void **)&d_rep, rows * sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc((void **)&d_g, rows)) != cudaSuccess || (e = cudaMalloc((void **)&d_flag, 2 * rows)) != cudaSuccess) {
+        release();
+        return cuda_fail(c, e, "cudaMalloc(loop orbits)");
+    }
+    std::vector<uint8_t> flag(2 * rows);
+    e = cudaMemcpyAsync(d_rep, rep.data(), rows * sizeof(int), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_g, gof.data(), rows, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_flag, 0, 2 * rows, c->stream);
+    if (e == cudaSuccess) {
+        check_covariance_kernel<<<dim3((unsigned)NN, 2), 256, 0, c->stream>>>(c->d_part, d_rep, d_g, d_flag, N, c->pb.M,
+                                                                          c->pb.P, c->pb.n_theta, c->pb.n_r);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(flag.data(), d_flag, 2 * rows, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    release();
+    if (e != cudaSuccess) return cuda_fail(c, e, "partner-map covariance check");
+
+    // representatives per family grouped by patch, each with its images;
+    // rows whose partner bytes broke covariance are representatives of themselves
+    struct Rep {
+        int a, Q, n;
+        int2 img[8];
+    };
+    std::vector<Rep> reps[2];
+    long mism = 0;
+    for (int f = 0; f < 2; ++f) {
+        const uint8_t *fl = flag.data() + (long)f * rows;
+        for (long row = 0; row < rows; ++row) {
+            const int Q = (int)(row / N), a = (int)(row - (long)Q * N);
+            if (fl[row]) {
+                ++mism;
+                Rep r{a, Q, 1, {}};
+                r.img[0] = make_int2(Q, a);
+                reps[f].push_back(r);
+                continue;
+            }
+            if (rep[row] != row) continue;
+            Rep r{a, Q, 0, {}};
+            const int x = Q / N, y = Q - x * N;
+            for (int g = 0; g < 8; ++g) {
+                const int Qi = c4v_apply(g, x, N) * N + c4v_apply(g, y, N), ai = c4v_apply(g, a, N);
+                const long irow = (long)Qi * N + ai;
+                if (fl[irow]) continue;                // evaluated by itself
+                bool dup = false;
+                for (int k = 0; k < r.n; ++k) dup |= r.img[k].x == Qi && (r.img[k].y & 0xffff) == ai;
+                if (!dup) r.img[r.n++] = make_int2(Qi, ai | (g << 16));
+            }
+            reps[f].push_back(r);
+        }
+        std::stable_sort(reps[f].begin(), reps[f].end(), [](const Rep &u, const Rep &v) { return u.a < v.a; });
+    }
+    const long nrep = (long)reps[0].size() + (long)reps[1].size();
+    std::vector<int> hQ(nrep), hn(nrep);
+    std::vector<int2> himg(8 * nrep, make_int2(0, 0));
+    c->lgroups.clear();
+    long k = 0, evals = 0;
+    for (int f = 0; f < 2; ++f) {
+        long start = k;
+        for (size_t i = 0; i < reps[f].size(); ++i, ++k) {
+            const Rep &r = reps[f][i];
+            hQ[k] = r.Q;
+            hn[k] = r.n;
+            for (int m = 0; m < r.n; ++m) himg[8 * k + m] = r.img[m];
+            evals += c->pb.P;
+            const bool last = i + 1 == reps[f].size() || reps[f][i + 1].a != r.a;
+            if (last) {
+                c->lgroups.push_back({f, r.a, (int)start, (int)(k + 1 - start)});
+                start = k + 1;
+            }
+        }
+    }
+    if ((e = cudaMalloc((void **)&c->d_lrepQ, nrep * sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc((void **)&c->d_lnimg, nrep * sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc((void **)&c->d_limg, 8 * nrep * sizeof(int2))) != cudaSuccess ||
+        (e = cudaMalloc((void **)&c->d_ltask, (nrep + 2 * (long)N + 8) * sizeof(int4))) != cudaSuccess)
+        return cuda_fail(c, e, "cudaMalloc(loop representatives)");
+    e = cudaMemcpy(c->d_lrepQ, hQ.data(), nrep * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_lnimg, hn.data(), nrep * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_limg, himg.data(), 8 * nrep * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "upload loop representatives");
+    c->n_lrep = nrep;
+    c->ltask_qchunk = 0;
+    c->loop_evals_red = evals;
+    c->loop_mismatch_rows = mism;
+    c->loop_red = true;
+    return QPFRG_OK;
+}
+
+// Tasks of the reduced loop-kernel launch for a chunk size: (family, patch,
+// first representative, count) per CTA; rebuilt when the chunk size changes.
+qpfrg_status loop_tasks(qpfrg_ctx *c, int qchunk, int *ntask)
+{
+    if (c->ltask_qchunk == qchunk) {
+        *ntask = c->n_ltask;
+        return QPFRG_OK;
+    }
+    std::vector<int4> t;
+    for (const LoopGroup &g : c->lgroups)
+        for (int s = 0; s < g.count; s += qchunk) t.push_back(make_int4(g.fam, g.a, g.start + s, std::min(qchunk, g.count - s)));
+    if ((long)t.size() > c->n_lrep + 2L * c->pb.N + 8) {
+        c->err = "loop-kernel task list overflow";
+        return QPFRG_ERR_INVALID;
+    }
+    cudaError_t e = cudaMemcpyAsync(c->d_ltask, t.data(), t.size() * sizeof(int4), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "upload loop tasks");
+    c->ltask_qchunk = qchunk;
+    c->n_ltask = (int)t.size();
+    *ntask = c->n_ltask;
+    return QPFRG_OK;
+}
+
+}  // namespace qpfrg
+
+extern "C" qpfrg_status qpfrg_rhs_work(qpfrg_t c, long long *loop_evals, long long *loop_evals_full,
+                                       long long *rows_unreduced)
+{
+    if (!c) return QPFRG_ERR_INVALID;
+    const long long full = 2LL * c->pb.N * c->pb.N * c->pb.M;
+    if (loop_evals) *loop_evals = c->loop_red ? c->loop_evals_red : full;
+    if (loop_evals_full) *loop_evals_full = full;
+    if (rows_unreduced) *rows_unreduced = c->loop_red ? c->loop_mismatch_rows : 0;
+    return QPFRG_OK;
+}

@@ -107,3 +107,56 @@ def test_rhs_full_size_sampled(prec):
     # C4v covariance of the whole GPU output (V and Z are C4v symmetric)
     for gmap in inputs.c4v_patch_maps(N)[1:3]:
         assert np.abs(got[np.ix_(gmap, gmap, gmap)] - got).max() / scale < 10 * TOL[prec]
+
+
+SYM_CASES = [
+    # (N, n_theta, n_r, regulator, propagator, lam)
+    (16, 4, 4, 0, 0, 0.3),
+    (24, 4, 6, 0, 1, 0.05),      # quasi-particle lines with a C4v-symmetric Z
+    (12, 3, 2, 0, 0, 0.5),       # odd angular count: points on the wedge centre lines
+    (16, 4, 4, 1, 0, 0.8),       # interaction flow
+    (48, 8, 8, 0, 0, 0.1),
+]
+
+
+@pytest.mark.parametrize("prec", [api.QPFRG_FP64, api.QPFRG_MIXED, api.QPFRG_MIXED_TC])
+@pytest.mark.parametrize("case", SYM_CASES, ids=[f"N{c[0]}_n{c[1]}x{c[2]}_r{c[3]}_p{c[4]}" for c in SYM_CASES])
+def test_loop_symmetry_matches_unreduced(case, prec):
+    """The C4v-reduced loop kernels (one row per orbit of (transfer, patch),
+    written to its images) give the results of the unreduced launch: to
+    rounding in FP64, to FP32 rounding of the image points' coordinates
+    otherwise.  Checked on qpfrg_rhs and on one flow step from a symmetric
+    (V, Z) state (the path that reduces with quasi-particle lines, whose loop
+    kernels depend on Z); the work report says how many evaluations the
+    reduced RHS does."""
+    import torch
+    N, nt, nr, reg, prop, lam = case
+    if prec == api.QPFRG_MIXED_TC and (N * N) % 8:
+        pytest.skip("tensor-core path needs N^2 % 8 == 0")
+    V = inputs.random_vertex(N, 2.0, seed=N + 1, c4v=True)
+    Z = inputs.z_profile(N, "aniso")
+    out, step, work = {}, {}, {}
+    for nosym in (0, 1):
+        opts = dict(precision=prec, propagator=prop, T_fixed=0.15, no_loop_symmetry=nosym)
+        lam0 = 0.0 if reg == 1 else 1.0
+        if reg == 1:
+            opts.update(step=0.01, lambda_end=1.0)
+        with api.Context(N, nt, nr, U=2.0, lambda0=lam0, regulator=reg, **opts) as ctx:
+            out[nosym] = gpu_rhs(ctx, lam, V, Z)
+            img = bytearray(api.qpfrg_get_state(ctx.h))
+            img[64:] = np.concatenate([V.ravel(), Z]).tobytes()
+            api.qpfrg_set_state(ctx.h, bytes(img))
+            api.qpfrg_step(ctx.h, 1)
+            Vs = torch.zeros(N ** 3, dtype=torch.float64, device="cuda")
+            api.qpfrg_read_state(ctx.h, Vs, None)
+            torch.cuda.synchronize()
+            step[nosym] = Vs.cpu().numpy() - V.ravel()
+            work[nosym] = api.qpfrg_rhs_work(ctx.h)
+    tol = 1e-12 if prec == api.QPFRG_FP64 else 1e-5
+    assert normwise(out[0], out[1]) < tol
+    assert normwise(step[0], step[1]) < tol
+    full = 2 * N * N * N * nt * nr
+    assert work[1]["loop_evals"] == full and work[0]["loop_evals_full"] == full
+    if nt % 2 == 0:
+        assert work[0]["rows_unreduced"] == 0
+        assert work[0]["loop_evals"] < full / 6
