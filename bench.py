@@ -577,6 +577,43 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_rhs_only(args):
+    """One context of the workload at one precision, right-hand sides only
+    (Z feedback off, fixed seeded vertex): the small single-context command
+    that kernel captures run under.  Prints its own JSON line (not a bench
+    line): RHS/s over the timed calls and the per-kernel profile."""
+    import torch
+
+    from paper_2005_00827_gb300 import api, inputs
+
+    torch.cuda.set_device(0)
+    wl = inputs.WORKLOADS[args.workload]
+    N, n, U = wl["N"], wl["n"], wl["U"]
+    prec = {"mixed": api.QPFRG_MIXED, "tc": api.QPFRG_MIXED_TC, "fp64": api.QPFRG_FP64}[args.rhs_only]
+    stream = torch.cuda.current_stream()
+    V = torch.from_numpy(inputs.random_vertex(N, U, seed=1).ravel()).cuda()
+    Z = torch.from_numpy(inputs.z_profile(N, "aniso")).cuda()
+    out = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+    with api.Context(N, n, n, U=U, precision=prec, stream=stream.cuda_stream) as c:
+        for _ in range(args.warmup):
+            api.qpfrg_rhs(c.h, 0.1, V, Z, out)
+        torch.cuda.synchronize()
+        api.qpfrg_set_profiling(c.h, True)
+        api.qpfrg_profile_reset(c.h)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            api.qpfrg_rhs(c.h, 0.1, V, Z, out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        prof = api.qpfrg_profile(c.h)
+    ms = a.elapsed_time(b)
+    print(json.dumps({"mode": "rhs_only", "workload": args.workload, "precision": args.rhs_only,
+                      "rhs_per_s": args.steps / (ms / 1e3), "ms_per_rhs": ms / args.steps,
+                      "kernels_ms_per_rhs": {k: v[0] / args.steps for k, v in prof.items() if v[1] > 0},
+                      "launches": {k: v[1] for k, v in prof.items() if v[1] > 0}}))
+
+
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -592,11 +629,15 @@ def main():
     p.add_argument("--no-autotune", action="store_true", help="built-in launch shapes instead of qpfrg_autotune")
     p.add_argument("--no-sweep", action="store_true", help="skip the 128-flow sweep summary of the default line")
     p.add_argument("--sweep-precision", default="tc", choices=["mixed", "tc", "fp64"])
+    p.add_argument("--rhs-only", choices=["mixed", "tc", "fp64"],
+                   help="time right-hand sides of one context only (kernel captures); prints its own line")
     args = p.parse_args()
     if args.warmup < 3 and args.impl == "qpfrg":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.rhs_only:
+        run_rhs_only(args)
     elif args.workload == "sweep128":
         run_sweep(args)
     else:

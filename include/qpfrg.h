@@ -80,7 +80,18 @@ typedef enum {
 
 enum { QPFRG_CH_PP = 1, QPFRG_CH_CR = 2, QPFRG_CH_D = 4, QPFRG_CH_ALL = 7 };
 
-typedef enum { QPFRG_GRID_WEDGE = 0, QPFRG_GRID_LATTICE = 1 } qpfrg_grid_mode;
+/* Patch geometry (Sec. 3.2 gives only patch counts):
+ *   WEDGE   -- n_p angular wedges about the origin, representatives on the Fermi
+ *              surface along the wedge centres, polar fine grid per wedge;
+ *   LATTICE -- the n_p = L*L momenta of an L x L lattice (exact finite-lattice sums);
+ *   SHELL   -- (angle, energy) patches, Sec. 3.2's "7 shells in the energy direction
+ *              and 32 angular sections": n_p / n_shell wedges (a multiple of 4),
+ *              each cut into n_shell (odd) energy shells of width shell_width centred
+ *              on the Fermi surface (outer shells reach the band edges), patch
+ *              j = wedge * n_shell + shell; representatives on the wedge's centre ray
+ *              at the shell's middle energy (k_F for the Fermi shell; the ray's zone-
+ *              edge point where the band ends below that energy); n_shell = 1 is WEDGE. */
+typedef enum { QPFRG_GRID_WEDGE = 0, QPFRG_GRID_LATTICE = 1, QPFRG_GRID_SHELL = 2 } qpfrg_grid_mode;
 
 typedef enum {
     QPFRG_FLOW_RUNNING = 0,      /* neither bound nor end reached yet            */
@@ -98,6 +109,9 @@ typedef struct {
     int n_theta;                 /* angular fine points per wedge (>= 1)               */
     int n_r;                     /* radial fine points per wedge (even, >= 2)          */
     int mode;                    /* qpfrg_grid_mode                                    */
+    int n_shell;                 /* SHELL: energy shells per wedge (odd >= 1; else ignored) */
+    double shell_width;          /* SHELL: energy width of a shell; <= 0: the band width
+                                    2 max|xi| over n_shell                               */
 } qpfrg_fine_grid;
 
 typedef struct {
@@ -295,13 +309,14 @@ int          qpfrg_profile_count(void);
 const char  *qpfrg_profile_name(int id);
 qpfrg_status qpfrg_profile_get(qpfrg_t ctx, int id, double *ms, long long *launches);
 
-/* Work of one right-hand-side evaluation.  In wedge mode the loop kernels
+/* Work of one right-hand-side evaluation.  In wedge and shell modes the loop kernels
  * evaluate one row per orbit of (transfer Q, patch a) under the point group
  * C4v and write it to every image row with its columns permuted: the
  * dispersion and the fine grid are C4v invariant, so B[gQ][ga][gb] =
  * B[Q][a][b] wherever the patch projection is covariant, which the context
  * checks byte by byte on its partner maps at creation (rows that differ are
- * evaluated by themselves).  With quasi-particle lines (QPFRG_PROP_QP) the
+ * evaluated by themselves; C4v moves the wedge of a patch and keeps its
+ * energy shell).  With quasi-particle lines (QPFRG_PROP_QP) the
  * reduction needs a C4v-symmetric Z.
  *   loop_evals: loop-kernel evaluations of one reduced RHS;
  *   loop_evals_full: 2 N^2 M, the evaluations of the unreduced RHS;

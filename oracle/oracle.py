@@ -23,7 +23,7 @@ _SRC = os.path.join(_HERE, "qpfrg_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 
-MODE_WEDGE, MODE_LATTICE = 0, 1
+MODE_WEDGE, MODE_LATTICE, MODE_SHELL = 0, 1, 2
 REG_TEMPERATURE, REG_INTERACTION = 0, 1
 PROP_PAPER, PROP_QP = 0, 1
 CH_PP, CH_CR, CH_D = 1, 2, 4
@@ -50,7 +50,8 @@ class Params(C.Structure):
     _fields_ = [("t", C.c_double), ("tp", C.c_double), ("mu", C.c_double),
                 ("mode", C.c_int), ("N", C.c_int), ("n_theta", C.c_int), ("n_r", C.c_int),
                 ("regulator", C.c_int), ("prop_mode", C.c_int), ("channels", C.c_uint),
-                ("T_fixed", C.c_double), ("eta", C.c_double)]
+                ("T_fixed", C.c_double), ("eta", C.c_double), ("n_shell", C.c_int),
+                ("shell_width", C.c_double)]
 
 
 class FlowOpts(C.Structure):
@@ -89,6 +90,8 @@ def lib():
         L.orc_proj.argtypes = [C.c_void_p, C.c_double, C.c_double]
         L.orc_xi.argtypes = [C.POINTER(Params), C.c_double, C.c_double]
         L.orc_xi.restype = C.c_double
+        L.orc_shell_width.argtypes = [C.POINTER(Params)]
+        L.orc_shell_width.restype = C.c_double
         for name in ("orc_fermi", "orc_dfermi_dT"):
             getattr(L, name).argtypes = [C.c_double, C.c_double]
             getattr(L, name).restype = C.c_double
@@ -123,9 +126,9 @@ class Oracle:
 
     def __init__(self, N, n_theta=8, n_r=8, mode=MODE_WEDGE, t=1.0, tp=0.0, mu=0.0,
                  regulator=REG_TEMPERATURE, prop_mode=PROP_PAPER, channels=CH_ALL,
-                 T_fixed=0.1, eta=0.02, nthreads=0):
+                 T_fixed=0.1, eta=0.02, nthreads=0, n_shell=1, shell_width=0.0):
         self.P = Params(t, tp, mu, mode, N, n_theta, n_r, regulator, prop_mode, channels,
-                        T_fixed, eta)
+                        T_fixed, eta, n_shell, shell_width)
         self.N = N
         self.nthreads = nthreads
         h = C.c_void_p()
@@ -153,6 +156,9 @@ class Oracle:
 
     def xi(self, kx, ky):
         return lib().orc_xi(C.byref(self.P), float(kx), float(ky))
+
+    def shell_width(self):
+        return lib().orc_shell_width(C.byref(self.P))
 
     # right-hand side --------------------------------------------------------
     def rhs_triple(self, lam, V, Z, i, j, l):

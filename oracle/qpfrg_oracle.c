@@ -39,6 +39,22 @@ double orc_xi(const orc_params *P, double kx, double ky)
 /*  lattice mode -- all L*L momenta 2 pi (m1, m2)/L are patches; each patch   */
 /*                 holds one loop point of weight 1/L^2; projection = nearest */
 /*                 lattice momentum.  This is the exact finite-lattice sum.   */
+/*  shell mode  -- (angle, energy) patches (Sec. 3.2: 32 angular sections x  */
+/*                 7 shells in the energy direction = 224).  N_a = N/n_s      */
+/*                 wedges as above, each cut into n_s (odd) energy shells of  */
+/*                 width D centred on the Fermi surface: shell s holds        */
+/*                 xi in [(s - n_s/2) D, (s + 1 - n_s/2) D), the outer shells */
+/*                 extended to the band edges; D defaults to the band width   */
+/*                 2 max|xi| over n_s.  Patch j = w n_s + s.  Representative:  */
+/*                 the point of the wedge's centre ray at the shell's middle  */
+/*                 energy (s - (n_s-1)/2) D (k_F for the Fermi shell), the    */
+/*                 zone edge of the ray when the ray ends below that energy.  */
+/*                 Fine grid: per angular midpoint ray, the shell's radial    */
+/*                 segment between the radii where xi crosses its two edges  */
+/*                 (xi increases along every ray: checked) in n_r midpoint    */
+/*                 cells, the Fermi shell's n_r/2 below and n_r/2 above       */
+/*                 r_F(theta), so n_s = 1 is wedge mode.  Projection: wedge   */
+/*                 by angle, shell by xi of the folded momentum.              */
 /* ------------------------------------------------------------------------- */
 static double r_bz(double th)
 {
@@ -46,17 +62,53 @@ static double r_bz(double th)
     return M_PI / fmax(fabs(cos(th)), fabs(sin(th)));
 }
 
-static double r_fermi(const orc_params *P, double th)
+static double ray_radius(const orc_params *P, double th, double eps)
 {
-    /* first sign change of xi along the ray, by bisection */
+    /* first crossing of xi = eps along the ray, by bisection; the zone edge */
+    /* when xi stays below eps, 0 when the origin is already at or above it  */
     double lo = 0.0, hi = r_bz(th);
-    if (orc_xi(P, hi * cos(th), hi * sin(th)) < 0.0) return hi;
-    if (orc_xi(P, 0.0, 0.0) >= 0.0) return 0.0;
+    if (orc_xi(P, hi * cos(th), hi * sin(th)) < eps) return hi;
+    if (orc_xi(P, 0.0, 0.0) >= eps) return 0.0;
     for (int it = 0; it < 200; ++it) {
         double mid = 0.5 * (lo + hi);
-        if (orc_xi(P, mid * cos(th), mid * sin(th)) < 0.0) lo = mid; else hi = mid;
+        if (orc_xi(P, mid * cos(th), mid * sin(th)) < eps) lo = mid; else hi = mid;
     }
     return 0.5 * (lo + hi);
+}
+
+static double r_fermi(const orc_params *P, double th) { return ray_radius(P, th, 0.0); }
+
+double orc_shell_width(const orc_params *P)
+{
+    if (P->shell_width > 0.0) return P->shell_width;
+    /* band extremes at (0,0), (pi,pi) and (pi,0) for |t'| <= t/2 */
+    double w = fabs(orc_xi(P, 0.0, 0.0));
+    w = fmax(w, fabs(orc_xi(P, M_PI, M_PI)));
+    w = fmax(w, fabs(orc_xi(P, M_PI, 0.0)));
+    return 2.0 * w / P->n_shell;
+}
+
+/* shell of an energy: floor(xi / D + n_s / 2), clamped to the outer shells */
+static int shell_of(const orc_params *P, double D, double xi)
+{
+    long s = (long)floor(xi / D + 0.5 * P->n_shell);
+    if (s < 0) s = 0;
+    if (s > P->n_shell - 1) s = P->n_shell - 1;
+    return (int)s;
+}
+
+/* xi non-decreasing along the ray (checked on 512 points) */
+static int ray_monotone(const orc_params *P, double th)
+{
+    const double rb = r_bz(th);
+    double prev = orc_xi(P, 0.0, 0.0);
+    for (int i = 1; i <= 512; ++i) {
+        const double r = rb * i / 512.0;
+        const double x = orc_xi(P, r * cos(th), r * sin(th));
+        if (x < prev - 1e-12) return 0;
+        prev = x;
+    }
+    return 1;
 }
 
 static double fold_bz(double x)
@@ -82,13 +134,16 @@ int orc_proj(const orc_geom *g, double kx, double ky)
         if (m2 < 0) m2 += L;
         return (int)(m1 * L + m2);
     }
+    const int ns = g->P.mode == ORC_MODE_SHELL ? g->P.n_shell : 1;
+    const int Na = N / ns;
     double x = fold_bz(kx), y = fold_bz(ky);
     double th = atan2(y, x);
-    double dth = TWO_PI / N;
+    double dth = TWO_PI / Na;
     long j = (long)floor(th / dth + 0.5);
-    j %= N;
-    if (j < 0) j += N;
-    return (int)j;
+    j %= Na;
+    if (j < 0) j += Na;
+    if (ns == 1) return (int)j;
+    return (int)(j * ns + shell_of(&g->P, orc_shell_width(&g->P), orc_xi(&g->P, x, y)));
 }
 
 int orc_geom_create(const orc_params *P, orc_geom **out)
@@ -104,7 +159,12 @@ int orc_geom_create(const orc_params *P, orc_geom **out)
         if (L < 1) { free(g); return -1; }
         g->M = N;
     } else {
-        if (N % 4 != 0 || P->n_theta < 1 || P->n_r < 2 || (P->n_r % 2) != 0) { free(g); return -1; }
+        const int ns = P->mode == ORC_MODE_SHELL ? P->n_shell : 1;
+        if (ns < 1 || ns % 2 == 0 || N % ns != 0 || (N / ns) % 4 != 0 || P->n_theta < 1 || P->n_r < 2 ||
+            (P->n_r % 2) != 0) {
+            free(g);
+            return -1;
+        }
         g->M = N * P->n_theta * P->n_r;
     }
     const int M = g->M;
@@ -126,6 +186,51 @@ int orc_geom_create(const orc_params *P, orc_geom **out)
                 g->fw[j] = 1.0 / N;
                 g->fpatch[j] = j;
             }
+        *out = g;
+        return 0;
+    }
+
+    if (P->mode == ORC_MODE_SHELL) {
+        const int ns = P->n_shell, Na = N / ns, nt = P->n_theta, nr = P->n_r, half = P->n_r / 2;
+        const int sF = ns / 2;
+        const double dth = TWO_PI / Na, D = orc_shell_width(P);
+        for (int w = 0; w < Na; ++w) {
+            const double thw = dth * w;
+            if (!ray_monotone(P, thw)) { orc_geom_free(g); return -1; }
+            for (int t = 0; t < nt; ++t)
+                if (!ray_monotone(P, thw + ((t + 0.5) / nt - 0.5) * dth)) { orc_geom_free(g); return -1; }
+            for (int sh = 0; sh < ns; ++sh) {
+                const int j = w * ns + sh;
+                const double rj = sh == sF ? r_fermi(P, thw) : ray_radius(P, thw, (sh - sF) * D);
+                g->kf[2 * j + 0] = rj * cos(thw);
+                g->kf[2 * j + 1] = rj * sin(thw);
+                for (int t = 0; t < nt; ++t) {
+                    const double th = thw + ((t + 0.5) / nt - 0.5) * dth;
+                    const double r0 = sh == 0 ? 0.0 : ray_radius(P, th, (sh - 0.5 * ns) * D);
+                    const double r1 = sh == ns - 1 ? r_bz(th) : ray_radius(P, th, (sh + 1 - 0.5 * ns) * D);
+                    const double rF = r_fermi(P, th);
+                    for (int i = 0; i < nr; ++i) {
+                        double rlo, rhi;
+                        if (sh != sF) {
+                            rlo = r0 + (r1 - r0) * i / nr;
+                            rhi = r0 + (r1 - r0) * (i + 1) / nr;
+                        } else if (i < half) {
+                            rlo = r0 + (rF - r0) * i / half;
+                            rhi = r0 + (rF - r0) * (i + 1) / half;
+                        } else {
+                            rlo = rF + (r1 - rF) * (i - half) / half;
+                            rhi = rF + (r1 - rF) * (i - half + 1) / half;
+                        }
+                        const double r = 0.5 * (rlo + rhi);
+                        const int p = (j * nt + t) * nr + i;
+                        g->fk[2 * p + 0] = r * cos(th);
+                        g->fk[2 * p + 1] = r * sin(th);
+                        g->fw[p] = 0.5 * (rhi * rhi - rlo * rlo) * (dth / nt) / (TWO_PI * TWO_PI);
+                        g->fpatch[p] = j;
+                    }
+                }
+            }
+        }
         *out = g;
         return 0;
     }
@@ -689,7 +794,11 @@ void orc_gflow_zka(const orc_geom *g, const orc_gflow_opts *o, double gv, const 
 {
     const int N = g->P.N, nw = 2 + o->n_omega;
     const double T = g->P.T_fixed;
+    /* A-bar runs over the Fermi surface (App. B): every patch of the angular  */
+    /* modes, the Fermi shell s = n_s / 2 of every wedge in shell mode        */
+    const int ns = g->P.mode == ORC_MODE_SHELL ? g->P.n_shell : 1;
     double sum = 0.0, amin = 0.0, amax = 0.0;
+    int nfs = 0;
     for (int j = 0; j < N; ++j) {
         const double s1 = (Sre[j * nw] - Sre[j * nw + 1]) / (4.0 * T);
         const double s2 = (Dre[j * nw] - Dre[j * nw + 1]) / (4.0 * T);
@@ -702,15 +811,17 @@ void orc_gflow_zka(const orc_geom *g, const orc_gflow_opts *o, double gv, const 
             K[j] = 1.0;
             A[j] = 0.0;
         }
+        if (j % ns != ns / 2) continue;
         sum += A[j];
-        if (j == 0 || A[j] < amin) amin = A[j];
-        if (j == 0 || A[j] > amax) amax = A[j];
+        if (nfs == 0 || A[j] < amin) amin = A[j];
+        if (nfs == 0 || A[j] > amax) amax = A[j];
+        ++nfs;
     }
     switch (o->a_mode) {
     case ORC_A_MIN: *Abar = amin; break;
     case ORC_A_MAX: *Abar = amax; break;
     case ORC_A_DROP: *Abar = 0.0; break;
-    default: *Abar = sum / N; break;
+    default: *Abar = sum / nfs; break;
     }
 }
 

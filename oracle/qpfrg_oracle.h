@@ -29,7 +29,7 @@
 extern "C" {
 #endif
 
-enum { ORC_MODE_WEDGE = 0, ORC_MODE_LATTICE = 1 };
+enum { ORC_MODE_WEDGE = 0, ORC_MODE_LATTICE = 1, ORC_MODE_SHELL = 2 };
 enum { ORC_REG_TEMPERATURE = 0, ORC_REG_INTERACTION = 1 };
 enum { ORC_PROP_PAPER = 0, ORC_PROP_QP = 1 };
 enum { ORC_CH_PP = 1, ORC_CH_CR = 2, ORC_CH_D = 4 };
@@ -37,14 +37,16 @@ enum { ORC_END = 0, ORC_DIVERGED = 1, ORC_NONFINITE = 2, ORC_Z_RANGE = 3, ORC_MA
 
 typedef struct orc_params {
     double t, tp, mu;      /* hoppings t, t' and chemical potential (Sec. 2.1)        */
-    int mode;              /* ORC_MODE_WEDGE or ORC_MODE_LATTICE                       */
-    int N;                 /* number of patches (lattice mode: N = L*L)                */
+    int mode;              /* ORC_MODE_WEDGE, ORC_MODE_LATTICE or ORC_MODE_SHELL       */
+    int N;                 /* number of patches (lattice: L*L; shell: wedges x shells) */
     int n_theta, n_r;      /* fine loop grid per wedge: angular x radial points        */
     int regulator;         /* ORC_REG_TEMPERATURE (Lambda = T) or _INTERACTION (g)     */
     int prop_mode;         /* ORC_PROP_PAPER: G = Z/(iw - xi); _QP: G = Z/(iw - Z xi)   */
     unsigned channels;     /* OR of ORC_CH_*                                           */
     double T_fixed;        /* temperature of the interaction flow                      */
     double eta;            /* Lorentzian broadening of the retarded self-energy        */
+    int n_shell;           /* shell mode: energy shells per angular wedge (odd)        */
+    double shell_width;    /* shell mode: energy width of a shell (<= 0: band / n_shell) */
 } orc_params;
 
 typedef struct orc_geom {
@@ -81,6 +83,7 @@ int    orc_geom_M(const orc_geom *g);
 void   orc_geom_export(const orc_geom *g, double *kf, double *fk, double *fw, int *fpatch);
 int    orc_proj(const orc_geom *g, double kx, double ky);
 double orc_xi(const orc_params *P, double kx, double ky);
+double orc_shell_width(const orc_params *P);   /* shell mode: the energy width of a shell */
 
 /* Fermi functions and bubbles ------------------------------------------------- */
 double orc_fermi(double x, double T);

@@ -21,7 +21,7 @@ QPFRG_REG_TEMPERATURE, QPFRG_REG_INTERACTION = 0, 1
 QPFRG_FP64, QPFRG_MIXED, QPFRG_MIXED_TC = 0, 1, 2
 QPFRG_PROP_PAPER, QPFRG_PROP_QP = 0, 1
 QPFRG_CH_PP, QPFRG_CH_CR, QPFRG_CH_D, QPFRG_CH_ALL = 1, 2, 4, 7
-QPFRG_GRID_WEDGE, QPFRG_GRID_LATTICE = 0, 1
+QPFRG_GRID_WEDGE, QPFRG_GRID_LATTICE, QPFRG_GRID_SHELL = 0, 1, 2
 FLOW_STATUS = {0: "RUNNING", 1: "REACHED_END", 2: "DIVERGED", 3: "NONFINITE", 4: "Z_OUT_OF_RANGE",
                5: "MAX_STEPS", 6: "TIMEOUT"}
 
@@ -47,7 +47,8 @@ class qpfrg_lattice(C.Structure):
 
 
 class qpfrg_fine_grid(C.Structure):
-    _fields_ = [("n_theta", C.c_int), ("n_r", C.c_int), ("mode", C.c_int)]
+    _fields_ = [("n_theta", C.c_int), ("n_r", C.c_int), ("mode", C.c_int), ("n_shell", C.c_int),
+                ("shell_width", C.c_double)]
 
 
 class qpfrg_options(C.Structure):
@@ -337,7 +338,7 @@ class Context:
     """Convenience owner of a qpfrg context (destroys it on close)."""
 
     def __init__(self, N, n_theta=8, n_r=8, U=2.0, lambda0=1.0, mode=QPFRG_GRID_WEDGE, t=1.0, tp=0.0,
-                 mu=0.0, regulator=QPFRG_REG_TEMPERATURE, stream=None, **opts):
+                 mu=0.0, regulator=QPFRG_REG_TEMPERATURE, stream=None, n_shell=1, shell_width=0.0, **opts):
         o = qpfrg_default_options()
         for k, v in opts.items():
             if not hasattr(o, k):
@@ -348,8 +349,8 @@ class Context:
             stream = torch.cuda.current_stream().cuda_stream
         self.N = N
         self.options = o
-        self.h = qpfrg_create(qpfrg_lattice(t, tp, mu), N, qpfrg_fine_grid(n_theta, n_r, mode), U, lambda0,
-                              regulator, o, stream)
+        grid = qpfrg_fine_grid(n_theta, n_r, mode, n_shell, shell_width)
+        self.h = qpfrg_create(qpfrg_lattice(t, tp, mu), N, grid, U, lambda0, regulator, o, stream)
 
     def close(self):
         if self.h:

@@ -151,6 +151,7 @@ struct Group {
     double **d_V = nullptr, **d_k = nullptr, **d_acc = nullptr;
     const float **d_Vf = nullptr, **d_VT = nullptr;
     CUtensorMap *d_maps = nullptr;
+    CUtensorMap *d_tmaps = nullptr;    // table map per slot
 
     Group() = default;
     Group(const Group &) = delete;
@@ -303,11 +304,15 @@ qpfrg_status setup_group(Group &g, const qpfrg_lattice *lattice, const qpfrg_fin
         (s = galloc(g, &g.d_act, g.nslots, "batch slots")) ||
         (s = galloc(g, &g.d_h, std::max<size_t>(1, g.h_tab.size()), "batch schedule")) ||
         (s = galloc(g, &g.d_slot, std::max<size_t>(1, g.slot_tab.size()), "batch slots table")) ||
-        (s = galloc(g, &g.d_rows, g.nslots, "batch rows ptrs")))
+        (s = galloc(g, &g.d_rows, g.nslots, "batch rows ptrs")) ||
+        (s = galloc(g, &g.d_tmaps, g.nslots, "batch table maps")))
         return s;
     g.rows.assign(g.nslots, nullptr);
-    for (int sl = 0; sl < g.nslots; ++sl)
+    std::vector<CUtensorMap> tmaps(g.nslots);
+    for (int sl = 0; sl < g.nslots; ++sl) {
         if ((e = cudaMalloc((void **)&g.rows[sl], c->B_bytes)) != cudaSuccess) return cuda_fail(c, e, "batch rows");
+        if ((s = make_table_map(c, &tmaps[sl], g.rows[sl], N)) != QPFRG_OK) return s;
+    }
     std::vector<int> act(g.nslots, 0);
     if (g.nsteps > 0)
         for (int i = 0; i < F; ++i) act[g.slot_tab[i]] = 1;
@@ -332,7 +337,8 @@ qpfrg_status setup_group(Group &g, const qpfrg_lattice *lattice, const qpfrg_fin
                {g.d_act, act.data(), g.nslots * sizeof(int)},
                {g.d_h, g.h_tab.data(), g.h_tab.size() * sizeof(double)},
                {g.d_slot, g.slot_tab.data(), g.slot_tab.size()},
-               {g.d_rows, g.rows.data(), g.nslots * sizeof(float *)}};
+               {g.d_rows, g.rows.data(), g.nslots * sizeof(float *)},
+               {g.d_tmaps, tmaps.data(), g.nslots * sizeof(CUtensorMap)}};
     for (const Up &u : ups)
         if (u.bytes && (e = cudaMemcpy(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice)) != cudaSuccess)
             return cuda_fail(c, e, "batch upload");
@@ -372,6 +378,7 @@ qpfrg_status enqueue_group_step(Group &g, int k, double stop)
         bt.VT = g.d_VT;
         bt.out = g.d_k;
         bt.maps = g.d_maps;
+        bt.tab_maps = g.d_tmaps;
         const unsigned ch = c->pb.channels;
         if ((ch & QPFRG_CH_PP) && (s = launch_tc_fused_batch(c, 0, bt, -1.0))) return s;
         if ((ch & QPFRG_CH_CR) && (s = launch_tc_fused_batch(c, 1, bt, -1.0))) return s;

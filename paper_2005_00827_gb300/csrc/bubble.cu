@@ -231,12 +231,18 @@ __device__ __forceinline__ float row_get(const float *slot, float finv)
 }
 __device__ __forceinline__ double row_get(const double *slot, float) { return *slot; }
 
-// Column b of the image row under g (g = m | reflection << 2: b -> +-b + m N/4)
-// holds the representative's bin g^-1(b).
-__device__ __forceinline__ int img_src(int b, int off, bool refl, int N)
+// Column b of the image row under g (g = m | reflection << 2 acting on the
+// wedge w of b = w ns + s: w -> +-w + m N_a/4, the shell s kept) holds the
+// representative's bin g^-1(b).
+__device__ __forceinline__ int img_src(int b, int off, bool refl, int N, int ns)
 {
-    const int r = refl ? off - b : b - off;
-    return r < 0 ? r + N : r;
+    if (ns == 1) {
+        const int r = refl ? off - b : b - off;
+        return r < 0 ? r + N : r;
+    }
+    const int w = b / ns, sh = b - w * ns, Na = N / ns;
+    const int r = refl ? off - w : w - off;
+    return (r < 0 ? r + Na : r) * ns + sh;
 }
 
 // Write-out of one row to the bubble table B[fam][Qi][ai][:] of the image row
@@ -246,13 +252,13 @@ template <typename R, bool TFLOW>
 __device__ __forceinline__ void table_row(const BubbleArgs<R> &A, const R *row, const R *Zs, const R *Ks, int fam,
                                           int Qi, int ai, int g, int lane)
 {
-    const int N = A.pb.N;
+    const int N = A.pb.N, ns = A.pb.n_shell;
     const long NN = (long)N * N;
-    const int off = (g & 3) * (N / 4);
+    const int off = (g & 3) * (N / ns / 4);
     const bool refl = (g & 4) != 0;
     const R Za = Zs[ai], KZa = Ks[ai] * Za;
     for (int b = lane; b < N; b += 32) {
-        const R v = row_get(row + img_src(b, off, refl, N), A.finv);
+        const R v = row_get(row + img_src(b, off, refl, N, ns), A.finv);
         const R Zb = Zs[b];
         const R sw = TFLOW ? Za * Zb : A.g * Za * Zb * (KZa + Ks[b] * Zb);
         A.B[(((long)fam * NN + Qi) * N + ai) * (long)N + b] = v * sw;

@@ -65,23 +65,108 @@ static double bz_radius(double th)
     return kPi / std::fmax(std::fabs(std::cos(th)), std::fabs(std::sin(th)));
 }
 
-// First zero of xi along the ray at angle th (bisection on xi < 0); the BZ
-// edge when xi stays negative, 0 when the origin is already unoccupied.
-static double fermi_radius(const Problem &pb, double th)
+// First crossing of xi = eps along the ray at angle th (bisection on
+// xi < eps); the BZ edge when xi stays below eps, 0 when the origin is
+// already at or above it.
+static double level_radius(const Problem &pb, double th, double eps)
 {
     const double c = std::cos(th), s = std::sin(th);
     double hi = bz_radius(th);
-    if (host_xi(pb, hi * c, hi * s) < 0.0) return hi;
-    if (host_xi(pb, 0.0, 0.0) >= 0.0) return 0.0;
+    if (host_xi(pb, hi * c, hi * s) < eps) return hi;
+    if (host_xi(pb, 0.0, 0.0) >= eps) return 0.0;
     double lo = 0.0;
     for (int it = 0; it < 200; ++it) {
         const double mid = 0.5 * (lo + hi);
-        if (host_xi(pb, mid * c, mid * s) < 0.0)
+        if (host_xi(pb, mid * c, mid * s) < eps)
             lo = mid;
         else
             hi = mid;
     }
     return 0.5 * (lo + hi);
+}
+
+// The Fermi surface along the ray: the level xi = 0.
+static double fermi_radius(const Problem &pb, double th) { return level_radius(pb, th, 0.0); }
+
+// Shell width of shell mode: the given width, else the band width 2 max|xi|
+// (band extremes at (0,0), (pi,pi), (pi,0) for |t'| <= t/2) over the shells.
+double shell_width(const Problem &pb, double given)
+{
+    if (given > 0.0) return given;
+    const double w = std::fmax(std::fabs(host_xi(pb, 0.0, 0.0)),
+                               std::fmax(std::fabs(host_xi(pb, kPi, kPi)), std::fabs(host_xi(pb, kPi, 0.0))));
+    return 2.0 * w / pb.n_shell;
+}
+
+// Whether xi does not decrease along the ray (512 samples): the shells then
+// cut every ray in one segment each.
+static bool ray_monotone(const Problem &pb, double th)
+{
+    const double rb = bz_radius(th), c = std::cos(th), s = std::sin(th);
+    double prev = host_xi(pb, 0.0, 0.0);
+    for (int i = 1; i <= 512; ++i) {
+        const double r = rb * i / 512.0;
+        const double x = host_xi(pb, r * c, r * s);
+        if (x < prev - 1e-12) return false;
+        prev = x;
+    }
+    return true;
+}
+
+// Shell mode: N_a = N / n_s wedges, each cut at the shell edges
+// e_b = (b - n_s/2) D; patch j = w n_s + s.  Per angular midpoint ray the
+// shell's segment [r(e_s), r(e_{s+1})] (0 and the zone edge for the outer
+// shells) is split into n_r midpoint cells, the Fermi shell's at r_F(theta)
+// into n_r/2 + n_r/2, so that one shell reproduces the wedge grid.
+static qpfrg_status build_shell_geometry(qpfrg_ctx *c)
+{
+    const Problem &pb = c->pb;
+    const int ns = pb.n_shell, Na = pb.N / ns, sF = ns / 2;
+    const int nt = c->n_theta, nr = c->n_r, nh = c->n_r / 2;
+    const double dth = kTwoPi / Na, D = pb.shell_D;
+    for (int w = 0; w < Na; ++w) {
+        const double thw = dth * w;
+        bool mono = ray_monotone(pb, thw);
+        for (int a = 0; a < nt && mono; ++a) mono = ray_monotone(pb, thw + ((a + 0.5) / nt - 0.5) * dth);
+        if (!mono) {
+            c->err = "shell mode needs xi increasing along every ray from the origin to the zone edge";
+            return QPFRG_ERR_UNSUPPORTED;
+        }
+        for (int sh = 0; sh < ns; ++sh) {
+            const int j = w * ns + sh;
+            const double rj = sh == sF ? fermi_radius(pb, thw) : level_radius(pb, thw, (sh - sF) * D);
+            c->kf[2 * j] = rj * std::cos(thw);
+            c->kf[2 * j + 1] = rj * std::sin(thw);
+            for (int a = 0; a < nt; ++a) {
+                const double th = thw + ((a + 0.5) / nt - 0.5) * dth;
+                const double r0 = sh == 0 ? 0.0 : level_radius(pb, th, (sh - 0.5 * ns) * D);
+                const double r1 = sh == ns - 1 ? bz_radius(th) : level_radius(pb, th, (sh + 1 - 0.5 * ns) * D);
+                const double rf = fermi_radius(pb, th);
+                for (int i = 0; i < nr; ++i) {
+                    double q0, q1;
+                    if (sh != sF) {
+                        q0 = r0 + (r1 - r0) * i / nr;
+                        q1 = r0 + (r1 - r0) * (i + 1) / nr;
+                    } else if (i < nh) {
+                        q0 = r0 + (rf - r0) * i / nh;
+                        q1 = r0 + (rf - r0) * (i + 1) / nh;
+                    } else {
+                        q0 = rf + (r1 - rf) * (i - nh) / nh;
+                        q1 = rf + (r1 - rf) * (i - nh + 1) / nh;
+                    }
+                    const double r = 0.5 * (q0 + q1);
+                    const size_t p = ((size_t)j * nt + a) * nr + i;
+                    c->fk[2 * p] = r * std::cos(th);
+                    c->fk[2 * p + 1] = r * std::sin(th);
+                    c->fw[p] = 0.5 * (q1 * q1 - q0 * q0) * (dth / nt) / (kTwoPi * kTwoPi);
+                    c->fpatch[p] = j;
+                }
+            }
+        }
+    }
+    c->fw_max = 0.0;
+    for (double w : c->fw) c->fw_max = std::fmax(c->fw_max, w);
+    return QPFRG_OK;
 }
 
 qpfrg_status build_host_geometry(qpfrg_ctx *c)
@@ -109,6 +194,7 @@ qpfrg_status build_host_geometry(qpfrg_ctx *c)
         c->fw_max = 1.0 / N;
         return QPFRG_OK;
     }
+    if (pb.mode == QPFRG_GRID_SHELL) return build_shell_geometry(c);
 
     const double dth = kTwoPi / N;
     const int nt = c->n_theta, nr = c->n_r, nh = c->n_r / 2;
@@ -143,36 +229,14 @@ qpfrg_status build_host_geometry(qpfrg_ctx *c)
     return QPFRG_OK;
 }
 
-// ---------------------------------------------------------------------------
-// Device projection of a momentum onto its patch (FP64).  Wedge: fold each
-// component into [-pi, pi] (ties to even), angle by atan2, nearest wedge
-// centre with half-open wedges.  Lattice: nearest lattice momentum.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ int project_patch(double kx, double ky, int N, int mode, int L)
-{
-    if (mode == QPFRG_GRID_LATTICE) {
-        long m1 = (long)rint(kx * L / kTwoPi) % L;
-        long m2 = (long)rint(ky * L / kTwoPi) % L;
-        if (m1 < 0) m1 += L;
-        if (m2 < 0) m2 += L;
-        return (int)(m1 * L + m2);
-    }
-    const double x = kx - kTwoPi * rint(kx / kTwoPi);
-    const double y = ky - kTwoPi * rint(ky / kTwoPi);
-    const double th = atan2(y, x);
-    long j = (long)floor(th / (kTwoPi / N) + 0.5);
-    j %= N;
-    if (j < 0) j += N;
-    return (int)j;
-}
-
 // part[f][Q][a P + part_byte(t, s)] = patch of (Q - p) for f = 0 (pp) and of
 // (p + Q) for f = 1 (ph), p = a P + t n_r + s the fine point (t angular, s
 // radial); part_byte orders a patch's bytes for the loop kernels' reads.
 __global__ void partner_map_kernel(const double *__restrict__ Qpp, const double *__restrict__ Qph,
                                    const double *__restrict__ fkx, const double *__restrict__ fky,
-                                   uint8_t *__restrict__ part, int N, int M, int P, int nt, int nr, int mode, int L)
+                                   uint8_t *__restrict__ part, Problem pb)
 {
+    const int N = pb.N, M = pb.M, P = pb.P, nt = pb.n_theta, nr = pb.n_r;
     const int Q = blockIdx.x, f = blockIdx.z;
     const long NN = (long)N * N;
     const double *Qt = f == 0 ? Qpp : Qph;
@@ -183,7 +247,7 @@ __global__ void partner_map_kernel(const double *__restrict__ Qpp, const double 
         const double qx = f == 0 ? Qx - px : px + Qx;
         const double qy = f == 0 ? Qy - py : py + Qy;
         const int a = p / P, li = p - a * P, t = li / nr, s = li - t * nr;
-        row[a * P + part_byte(t, s, nt, nr)] = (uint8_t)project_patch(qx, qy, N, mode, L);
+        row[a * P + part_byte(t, s, nt, nr)] = (uint8_t)project_fp64(qx, qy, pb);
     }
 }
 
@@ -196,8 +260,9 @@ __global__ void partner_map_fx_kernel(const int2 *__restrict__ Qfx, const double
                                       const double *__restrict__ Qph, const int2 *__restrict__ pfx,
                                       const double *__restrict__ fkx, const double *__restrict__ fky,
                                       const uint8_t *__restrict__ ptab, const float4 *__restrict__ bnd,
-                                      uint8_t *__restrict__ part, int N, int M, int P, int nt, int nr)
+                                      uint8_t *__restrict__ part, Problem pb)
 {
+    const int N = pb.N, M = pb.M, P = pb.P, nt = pb.n_theta, nr = pb.n_r;
     const int Q = blockIdx.x, f = blockIdx.z;
     const long NN = (long)N * N;
     const int2 qf = Qfx[f * NN + Q];
@@ -221,7 +286,7 @@ __global__ void partner_map_fx_kernel(const int2 *__restrict__ Qfx, const double
         int c;
         if (fmaxf(fabsf(x), fabsf(y)) > kFxEdge || fabsf(cr) < kFxGuard) {
             const double px = fkx[p], py = fky[p], Qx = Qt[2 * Q], Qy = Qt[2 * Q + 1];
-            c = project_patch(f == 0 ? Qx - px : px + Qx, f == 0 ? Qy - py : py + Qy, N, QPFRG_GRID_WEDGE, 0);
+            c = project_fp64(f == 0 ? Qx - px : px + Qx, f == 0 ? Qy - py : py + Qy, pb);
         } else {
             c = e + (cr >= 0.f ? 1 : 0);
             if (c == N) c = 0;
@@ -312,7 +377,9 @@ qpfrg_status upload_geometry(qpfrg_ctx *c)
         std::vector<float4> bnd(N);
         for (int j = 0; j < N; ++j) {
             xij[j] = host_xi(c->pb, c->kf[2 * j], c->kf[2 * j + 1]);
-            const double th = (j - 0.5) * kTwoPi / N, cs = std::cos(th), sn = std::sin(th);
+            // ray between wedges w - 1 and w (entries past the N_a wedges repeat them)
+            const int Na = N / c->pb.n_shell;
+            const double th = (j % Na - 0.5) * kTwoPi / Na, cs = std::cos(th), sn = std::sin(th);
             const float ch = (float)cs, sh = (float)sn;
             bnd[j] = make_float4(ch, (float)(cs - ch), sh, (float)(sn - sh));
         }
@@ -377,8 +444,7 @@ qpfrg_status upload_geometry(qpfrg_ctx *c)
         cudaMemcpy(d_pfx, pfx.data(), M * sizeof(int2), cudaMemcpyHostToDevice);
         prof_begin(c);
         partner_map_fx_kernel<<<grid, 256, 0, c->stream>>>(d_qfx, c->d_Qpp, c->d_Qph, d_pfx, c->f64.kx, c->f64.ky,
-                                                           c->d_ptab, c->d_bnd, c->d_part, N, c->pb.M, c->pb.P,
-                                                           c->pb.n_theta, c->pb.n_r);
+                                                           c->d_ptab, c->d_bnd, c->d_part, c->pb);
         prof_end(c, K_PARTNER_MAP);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);   // before the momenta are released
@@ -388,9 +454,7 @@ qpfrg_status upload_geometry(qpfrg_ctx *c)
         return QPFRG_OK;
     }
     prof_begin(c);
-    partner_map_kernel<<<grid, 256, 0, c->stream>>>(c->d_Qpp, c->d_Qph, c->f64.kx, c->f64.ky, c->d_part,
-                                                    N, c->pb.M, c->pb.P, c->pb.n_theta, c->pb.n_r,
-                                                    c->pb.mode, c->pb.L);
+    partner_map_kernel<<<grid, 256, 0, c->stream>>>(c->d_Qpp, c->d_Qph, c->f64.kx, c->f64.ky, c->d_part, c->pb);
     prof_end(c, K_PARTNER_MAP);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "partner_map_kernel");
     return QPFRG_OK;

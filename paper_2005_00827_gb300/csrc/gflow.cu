@@ -8,7 +8,9 @@
 //   Z = (1 - g s1)^-1   (Eq. (definition_Z) for g Sigma_g)
 //   K = 1 + g^2 s2      (Eq. (K_definition); 1 without the Katanin correction)
 //   A = 2 Z (s1 + g s2) (Eq. (single_scale_propagator_extended_2) = Eq. (A_g_simple))
-// and Abar is the patch average of A (Eq. (second_derivative_sigma_approximation)),
+// and Abar is the average of A over the Fermi surface -- every patch of the
+// angular patchings, the Fermi shell of shell mode (Eq.
+// (second_derivative_sigma_approximation)),
 // its minimum or maximum (the bracket flows of App. B) or 0 (the one-loop term
 // dropped, App. A.4).  T2 is the two-loop term at the static vertex with the
 // lines of a G, an S and an inner K S line averaged over their assignments;
@@ -28,8 +30,8 @@
 namespace qpfrg {
 
 // Z, K, A of every patch and Abar from the small state at g (one block)
-__global__ void gflow_zka_kernel(const double *y, int N, double g, int z_feedback, int katanin, int a_mode, double *Z,
-                                 double *K, double *A, double *Abar)
+__global__ void gflow_zka_kernel(const double *y, int N, int ns, double g, int z_feedback, int katanin, int a_mode,
+                                 double *Z, double *K, double *A, double *Abar)
 {
     __shared__ double sh_sum[256], sh_min[256], sh_max[256];
     double sum = 0.0, mn = 1e300, mx = -1e300;
@@ -44,6 +46,7 @@ __global__ void gflow_zka_kernel(const double *y, int N, double g, int z_feedbac
         Z[j] = z;
         K[j] = k;
         A[j] = a;
+        if (j % ns != ns / 2) continue;     // Abar over the Fermi surface: the Fermi shell
         sum += a;
         mn = fmin(mn, a);
         mx = fmax(mx, a);
@@ -59,7 +62,7 @@ __global__ void gflow_zka_kernel(const double *y, int N, double g, int z_feedbac
             lo = fmin(lo, sh_min[t]);
             hi = fmax(hi, sh_max[t]);
         }
-        *Abar = a_mode == 1 ? lo : (a_mode == 2 ? hi : (a_mode == 3 ? 0.0 : s / N));
+        *Abar = a_mode == 1 ? lo : (a_mode == 2 ? hi : (a_mode == 3 ? 0.0 : s / (N / ns)));
     }
 }
 
@@ -127,7 +130,7 @@ static qpfrg_status zka(qpfrg_ctx *c, const double *y, double g)
 {
     const int N = c->pb.N;
     double *Z = c->d_gzka, *K = Z + N, *A = K + N, *Ab = A + N;
-    gflow_zka_kernel<<<1, 256, 0, c->stream>>>(y, N, g, c->opt.z_feedback, c->opt.katanin, c->opt.a_mode, Z, K, A,
+    gflow_zka_kernel<<<1, 256, 0, c->stream>>>(y, N, c->pb.n_shell, g, c->opt.z_feedback, c->opt.katanin, c->opt.a_mode, Z, K, A,
                                                Ab);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "gflow_zka_kernel");

@@ -231,6 +231,7 @@ qpfrg_status qpfrg_create(const qpfrg_lattice *lattice, int n_p, const qpfrg_fin
     pb.mu = lattice->mu;
     pb.mode = grid->mode;
     pb.N = n_p;
+    pb.n_shell = 1;
     pb.regulator = regulator;
     pb.propagator = c->opt.propagator;
     pb.channels = c->opt.channel_mask & QPFRG_CH_ALL;
@@ -274,7 +275,16 @@ qpfrg_status qpfrg_create(const qpfrg_lattice *lattice, int n_p, const qpfrg_fin
         pb.P = 1;
         c->n_theta = c->n_r = 1;
         pb.n_theta = pb.n_r = 1;
-    } else if (pb.mode == QPFRG_GRID_WEDGE) {
+    } else if (pb.mode == QPFRG_GRID_WEDGE || pb.mode == QPFRG_GRID_SHELL) {
+        if (pb.mode == QPFRG_GRID_SHELL) {
+            const int ns = grid->n_shell;
+            if (ns < 1 || ns % 2 == 0 || n_p % ns != 0 || (n_p / ns) % 4 != 0 || n_p > 256 ||
+                !std::isfinite(grid->shell_width))
+                return fail(set_err(c, QPFRG_ERR_INVALID,
+                                    "shell mode needs an odd n_shell and n_p / n_shell a multiple of 4, n_p <= 256"));
+            pb.n_shell = ns;
+            pb.shell_D = shell_width(pb, grid->shell_width);
+        }
         if (n_p < 4 || n_p % 4 != 0 || n_p > 256)
             return fail(set_err(c, QPFRG_ERR_INVALID, "wedge mode needs n_p a multiple of 4, 4 <= n_p <= 256"));
         if (grid->n_theta < 1 || grid->n_r < 2 || grid->n_r % 2 != 0)
@@ -323,7 +333,7 @@ qpfrg_status qpfrg_create(const qpfrg_lattice *lattice, int n_p, const qpfrg_fin
         t.Npad = (int)((N + 15) / 16 * 16);
         const size_t NN = N * N, Np = t.Npad;
         t.Kp = (long)((NN + 63) / 64 * 64);
-        t.Kpd = (long)((2 * NN + 63) / 64 * 64);
+        t.Kpd = 2 * t.Kp;
         const size_t nb = Np * (size_t)t.Kp, nbd = Np * (size_t)t.Kpd;
         for (int h = 0; h < 2; ++h)
             if ((s = dev_alloc(c, &t.Bpp[h], nb, "pp operand")) || (s = dev_alloc(c, &t.Bcr[h], nb, "cr operand")) ||

@@ -89,6 +89,8 @@ struct Problem {
     int n_theta, n_r;  // fine grid per patch (lattice: 1 x 1)
     int mode;        // qpfrg_grid_mode
     int L;           // lattice mode: side length
+    int n_shell;     // energy shells per wedge (1 outside shell mode)
+    double shell_D;  // shell mode: energy width of a shell
     double t, tp, mu;
     int regulator;   // qpfrg_regulator
     int propagator;  // qpfrg_propagator
@@ -122,8 +124,9 @@ struct TcBuffers {
     __nv_bfloat16 *Bd[2] = {nullptr, nullptr};    // [Npad][Kpd]
     float *VT = nullptr;                          // [N][N][N]
     int Npad = 0;
-    long Kp = 0, Kpd = 0;                         // N^2 and 2 N^2 up to 64
+    long Kp = 0, Kpd = 0;                         // N^2 up to 64 and 2 Kp (d: halves at 0 and Kp)
     CUtensorMap tmB[3][2];                        // TMA maps of the tiles: [pp, cr, d][hi, lo]
+    CUtensorMap tmTab;                            // TMA map of the FP32 weighted loop-kernel table
 };
 
 // Element offset of (row r, reduction index k) in the tile layout of an
@@ -137,6 +140,38 @@ __host__ __device__ inline long tile_index(long r, long k, int rows, long Kp)
     const long kt = k >> 6, kk = k & 63;
     return (rt * (Kp >> 6) + kt) * (long)rows * 64 + ((((kk >> 3) * (rows >> 3) + (rr >> 3)) << 6) | ((rr & 7) << 3) |
                                                       (kk & 7));
+}
+
+// FP64 projection of a momentum onto its patch.  Lattice: nearest lattice
+// momentum.  Wedge and shell: fold each component into [-pi, pi] (ties to
+// even), wedge of the angle (nearest centre 2 pi w / N_a, half-open), and in
+// shell mode the shell floor(xi / D + n_s / 2) of the folded momentum's
+// energy, clamped to the outer shells (the products of xi rounded one by one,
+// as written, without fused multiply-adds).
+__device__ __forceinline__ int project_fp64(double kx, double ky, const Problem &pb)
+{
+    if (pb.mode == QPFRG_GRID_LATTICE) {
+        const int L = pb.L;
+        long m1 = (long)rint(kx * L / kTwoPi) % L;
+        long m2 = (long)rint(ky * L / kTwoPi) % L;
+        if (m1 < 0) m1 += L;
+        if (m2 < 0) m2 += L;
+        return (int)(m1 * L + m2);
+    }
+    const double x = __dsub_rn(kx, __dmul_rn(kTwoPi, rint(kx / kTwoPi)));
+    const double y = __dsub_rn(ky, __dmul_rn(kTwoPi, rint(ky / kTwoPi)));
+    const int ns = pb.n_shell, Na = pb.N / ns;
+    long w = (long)floor(atan2(y, x) / (kTwoPi / Na) + 0.5);
+    w %= Na;
+    if (w < 0) w += Na;
+    if (ns == 1) return (int)w;
+    const double cx = cos(x), cy = cos(y);
+    const double xi = __dsub_rn(__dsub_rn(__dmul_rn(-2.0 * pb.t, __dadd_rn(cx, cy)),
+                                          __dmul_rn(__dmul_rn(4.0 * pb.tp, cx), cy)),
+                                pb.mu);
+    long sh = (long)floor(__dadd_rn(xi / pb.shell_D, 0.5 * ns));
+    sh = sh < 0 ? 0 : (sh > ns - 1 ? ns - 1 : sh);
+    return (int)(w * ns + sh);
 }
 
 struct ProfileSlot {
@@ -255,6 +290,7 @@ namespace qpfrg {
 
 // geometry.cu
 qpfrg_status build_host_geometry(qpfrg_ctx *c);
+double shell_width(const Problem &pb, double given);   // shell mode: the width of a shell
 qpfrg_status upload_geometry(qpfrg_ctx *c);
 
 // bubble.cu: fill the bubble tables for the given Lambda and Z (device ptr).
@@ -297,6 +333,9 @@ struct TcPrepFlow {
 qpfrg_status launch_tc_prep_batch(qpfrg_ctx *c, const TcPrepFlow *d_flows, const int *d_status, const double *d_h_tab,
                                   int step, int nflows);
 qpfrg_status make_tile_map(qpfrg_ctx *c, CUtensorMap *map, const void *base, long elems, int box_rows);
+// TMA map of a weighted loop-kernel table [2][N^2][N^2] (FP32): boxes of
+// 128 rows x 32 columns, 128-byte swizzle
+qpfrg_status make_table_map(qpfrg_ctx *c, CUtensorMap *map, const float *table, int N);
 // Batched flows (batch.cu): grid.z runs over the flows of a patch-count group;
 // each flow brings its table slot, stage vertex, output and B tensor maps,
 // and is skipped (uniformly, before any barrier) when it is not running or
@@ -313,6 +352,7 @@ struct TcBatch {
     const float *const *Vf, *const *VT;
     double *const *out;
     const CUtensorMap *maps;          // [flow][ch][hi, lo]
+    const CUtensorMap *tab_maps;      // table map per slot
 };
 
 qpfrg_status launch_tc_fused_batch(qpfrg_ctx *c, int ch, const TcBatch &bt, double sign);

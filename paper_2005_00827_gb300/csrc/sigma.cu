@@ -49,25 +49,6 @@ __device__ __forceinline__ void sfermi(R x, R invT, R &f, R &fc)
     fc = x > R(0) ? hi : lo;
 }
 
-// FP64 projection of a momentum onto its patch: fold into [-pi, pi] (ties to
-// even), atan2, nearest wedge centre; lattice mode: nearest lattice momentum.
-__device__ __forceinline__ int project64(double kx, double ky, int N, int mode, int L)
-{
-    if (mode == QPFRG_GRID_LATTICE) {
-        long m1 = (long)rint(kx * L / kTwoPi) % L;
-        long m2 = (long)rint(ky * L / kTwoPi) % L;
-        if (m1 < 0) m1 += L;
-        if (m2 < 0) m2 += L;
-        return (int)(m1 * L + m2);
-    }
-    const double x = kx - kTwoPi * rint(kx / kTwoPi);
-    const double y = ky - kTwoPi * rint(ky / kTwoPi);
-    long j = (long)floor(atan2(y, x) / (kTwoPi / N) + 0.5);
-    j %= N;
-    if (j < 0) j += N;
-    return (int)j;
-}
-
 // atan2 in FP32 from the odd polynomial t P(t^2), t = min/max on [0, 1], a
 // Remez minimax fit of atan(t) (degree 11; coefficients and the error bound
 // kAtanErr = 1.75e-6 rad of the FP32 evaluation generated by atan_fit.py into
@@ -268,7 +249,10 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
     const int j = A.jlist ? A.jlist[jidx] : jidx;
     const int tid = threadIdx.x;
     const bool qp = A.pb.propagator == QPFRG_PROP_QP;
-    const bool wedge = A.pb.mode == QPFRG_GRID_WEDGE;
+    // wedge and shell modes: the FP32 path decides the wedge by guarded ray
+    // tests (and the shell by the FP32 line energy, guarded)
+    const bool angular = A.pb.mode == QPFRG_GRID_WEDGE || A.pb.mode == QPFRG_GRID_SHELL;
+    const int ns = A.pb.n_shell, Na = N / ns;
     const R invT = A.invT_r, eta = A.eta_r;
     const R t = A.t_r, tp = A.tp_r, mu = A.mu_r;
     constexpr bool f32 = sizeof(R) == 4;
@@ -283,7 +267,7 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
     for (int i = tid; i < N; i += blockDim.x) {
         s_VZ[2 * i] = (R)A.V[((long)j * N + a) * N + i];
         s_VZ[2 * i + 1] = A.Z ? (R)A.Z[i] : R(1);
-        if (f32 && wedge) s_bnd[i] = A.bnd[i];
+        if (f32 && angular) s_bnd[i] = A.bnd[i];
         if (A.K) s_K[i] = (R)A.K[i];
     }
     __shared__ R s_k[4];
@@ -353,46 +337,73 @@ __global__ void __launch_bounds__(256) sigma_kernel(SigmaArgs<R> A)
         const R kza = glines ? s_K[a] * Za : R(0), kzb = glines ? s_K[b] * Zb : R(0);
         const R d0shift = A.xij_r[j], twoT = A.twoT_r;
         const R eta2 = eta * eta;
-        const float inv_dth = (float)(N / kTwoPi), dth = (float)(kTwoPi / N);
+        const float inv_dth = (float)(Na / kTwoPi), dth = (float)(kTwoPi / Na);
+        const float invD = ns > 1 ? (float)(1.0 / A.pb.shell_D) : 0.f, half_ns = 0.5f * ns;
+        // guard band of the shell decision in units of the shell width: ten
+        // times the error bound of the FP32 line energy (products of FP32-rounded
+        // cosines: 1.2e-6 per unit of 2|t| + 4|t'|, 1.2e-7 |mu|) plus the
+        // rounding of u itself
+        const float gu = 10.f * (1.2e-6f * (2.f * fabsf((float)A.pb.t) + 4.f * fabsf((float)A.pb.tp)) +
+                                 1.2e-7f * fabsf((float)A.pb.mu)) * invD + 1e-6f;
         // wedge of the previous pair and its two boundary rays (FP32)
         int cprev = -1;
         float blx = 0.f, bly = 0.f, bhx = 0.f, bhy = 0.f;
         for (int i = 0; i < P; ++i) {
             R r[REC];
             load_rec(s_rec, i, r);
-            int c;
-            if (f32 && wedge) {
-                float x, y;
-                fold32((float)(r[0] - qx), (float)(r[1] - qy), x, y);
-                // inside the previous pair's wedge by more than the FP32 error
-                // of (x, y) (2.1e-6) plus that of the rays: same patch
-                const bool edge = fabsf(x) > 3.14159265f - 4e-6f || fabsf(y) > 3.14159265f - 4e-6f;
-                if (!edge && cprev >= 0 && blx * y - bly * x >= 4e-6f && bhx * y - bhy * x <= -4e-6f) {
-                    c = cprev;
-                } else {
-                    int jc;
-                    c = project32_guarded(x, y, N, inv_dth, dth, jc);
-                    if (c == -1) {
-                        // near a wedge boundary: float-float decision on the FP32 pipes
-                        c = project_ff((float)r[0], (float)r[10], (float)r[1], (float)r[11], (float)qx, qxl,
-                                       (float)qy, qyl, jc, N, s_bnd);
-                    } else if (c == -2) {
-                        // zone edge or origin: the exact FP64 projection
-                        const int p = a * P + (i % nt) * nr + i / nt;
-                        c = project64((kx + A.kx64[p]) - qxd, (ky + A.ky64[p]) - qyd, N, A.pb.mode, A.pb.L);
-                    }
-                    cprev = c;
-                    const float4 lo = s_bnd[c], hi = s_bnd[c + 1 == N ? 0 : c + 1];
-                    blx = lo.x; bly = lo.z; bhx = hi.x; bhy = hi.z;
-                }
-            } else {
-                const int p = a * P + (i % nt) * nr + i / nt;
-                c = project64((kx + A.kx64[p]) - qxd, (ky + A.ky64[p]) - qyd, N, A.pb.mode, A.pb.L);
-            }
-            // cos(k+p-q) by angle addition
+            // cos(k+p-q) by angle addition, and the bare line energy of r
             const R crx = r[2] * cqx + r[3] * sqx;
             const R cry = r[4] * cqy + r[5] * sqy;
             R xr = R(-2) * t * (crx + cry) - R(4) * tp * crx * cry - mu;
+            int c = -1;
+            if (f32 && angular) {
+                float x, y;
+                fold32((float)(r[0] - qx), (float)(r[1] - qy), x, y);
+                // inside the previous pair's wedge by more than the FP32 error
+                // of (x, y) (2.1e-6) plus that of the rays: same wedge
+                const bool edge = fabsf(x) > 3.14159265f - 4e-6f || fabsf(y) > 3.14159265f - 4e-6f;
+                int cw;
+                if (!edge && cprev >= 0 && blx * y - bly * x >= 4e-6f && bhx * y - bhy * x <= -4e-6f) {
+                    cw = cprev;
+                } else {
+                    int jc;
+                    cw = project32_guarded(x, y, Na, inv_dth, dth, jc);
+                    if (cw == -1) {
+                        // near a wedge boundary: float-float decision on the FP32 pipes
+                        cw = project_ff((float)r[0], (float)r[10], (float)r[1], (float)r[11], (float)qx, qxl,
+                                        (float)qy, qyl, jc, Na, s_bnd);
+                    } else if (cw == -2) {
+                        // zone edge or origin: the exact FP64 projection
+                        const int p = a * P + (i % nt) * nr + i / nt;
+                        c = project_fp64((kx + A.kx64[p]) - qxd, (ky + A.ky64[p]) - qyd, A.pb);
+                        cw = c / ns;
+                    }
+                    cprev = cw;
+                    const float4 lo = s_bnd[cw], hi = s_bnd[cw + 1 == Na ? 0 : cw + 1];
+                    blx = lo.x; bly = lo.z; bhx = hi.x; bhy = hi.z;
+                }
+                if (c < 0) {
+                    if (ns == 1) {
+                        c = cw;
+                    } else {
+                        // shell of the FP32 line energy; within the guard band of
+                        // a shell edge the exact FP64 projection decides
+                        const float u = (float)xr * invD + half_ns;
+                        const float ur = rintf(u);
+                        if (fabsf(u - ur) < gu && ur >= 1.f && ur <= (float)(ns - 1)) {
+                            const int p = a * P + (i % nt) * nr + i / nt;
+                            c = project_fp64((kx + A.kx64[p]) - qxd, (ky + A.ky64[p]) - qyd, A.pb);
+                        } else {
+                            int sh = (int)floorf(u);
+                            sh = sh < 0 ? 0 : (sh > ns - 1 ? ns - 1 : sh);
+                            c = cw * ns + sh;
+                        }
+                    }
+                }
+            } else {
+                const int p = a * P + (i % nt) * nr + i / nt;
+                c = project_fp64((kx + A.kx64[p]) - qxd, (ky + A.ky64[p]) - qyd, A.pb);
+            }
             const R vac = s_VZ[2 * c], Zc = s_VZ[2 * c + 1];
             if (qp) xr *= Zc;
             R fr, fcr;
@@ -569,8 +580,7 @@ __device__ __noinline__ int sf_slow_patch(const SigmaFastArgs &A, int jidx, int 
         }
     }
     if (c < 0)
-        c = project64((A.kf[2 * j] + A.kx64[p]) - A.kx64[q], (A.kf[2 * j + 1] + A.ky64[p]) - A.ky64[q], N,
-                      QPFRG_GRID_WEDGE, 0);
+        c = project_fp64((A.kf[2 * j] + A.kx64[p]) - A.kx64[q], (A.kf[2 * j + 1] + A.ky64[p]) - A.ky64[q], A.pb);
     return c;
 }
 

@@ -1,7 +1,8 @@
-// C4v orbits of the loop-kernel rows (wedge mode).
+// C4v orbits of the loop-kernel rows (wedge and shell modes).
 //
-// The point group C4v of the square lattice acts on the wedge patches as
-// g = (m, s): j -> s j + m N/4 (mod N), s = +-1, on the transfers
+// The point group C4v of the square lattice acts on the wedges as
+// g = (m, s): w -> s w + m N_a/4 (mod N_a), s = +-1, and leaves the energy
+// shells in place (patch j = w n_s + s -> (g w) n_s + s), on the transfers
 // Q = (x, y) (Q = k_F(x) +- k_F(y)) as (x, y) -> (g x, g y), and on the fine
 // points of a patch as (a, t, r) -> (g a, t, r) for the rotations and
 // (g a, n_theta - 1 - t, r) for the reflections.  The dispersion (Eq.
@@ -22,13 +23,14 @@
 
 namespace qpfrg {
 
-// g = m | (reflection << 2) acting on a patch index
-__host__ __device__ inline int c4v_apply(int g, int j, int N)
+// g = m | (reflection << 2) acting on a patch index (ns shells per wedge)
+__host__ __device__ inline int c4v_apply(int g, int j, int N, int ns)
 {
-    const int off = (g & 3) * (N / 4);
-    int r = (g & 4) ? off - j : j + off;
-    r %= N;
-    return r < 0 ? r + N : r;
+    const int Na = N / ns, w = j / ns, sh = j - w * ns;
+    const int off = (g & 3) * (Na / 4);
+    int r = (g & 4) ? off - w : w + off;
+    r %= Na;
+    return (r < 0 ? r + Na : r) * ns + sh;
 }
 
 // inverse element: rotations by m -> by 4 - m; every reflection is an involution
@@ -39,7 +41,7 @@ __host__ __device__ inline int c4v_inverse(int g) { return (g & 4) ? g : ((4 - (
 // gof[Q N + a] = g with (Q, a) = g (representative).
 __global__ void check_covariance_kernel(const uint8_t *__restrict__ part, const int *__restrict__ rep,
                                         const uint8_t *__restrict__ gof, uint8_t *__restrict__ flag, int N, int M,
-                                        int P, int nt, int nr)
+                                        int P, int nt, int nr, int ns)
 {
     const int Q = blockIdx.x, f = blockIdx.y;
     const long NN = (long)N * N;
@@ -58,7 +60,7 @@ __global__ void check_covariance_kernel(const uint8_t *__restrict__ part, const 
         for (int li = threadIdx.x; li < P; li += blockDim.x) {
             const int t = li / nr, s = li - t * nr;
             const int ts = (g & 4) ? nt - 1 - t : t;   // the representative's point mapped onto (t, s)
-            const int want = c4v_apply(g, src[part_byte(ts, s, nt, nr)], N);
+            const int want = c4v_apply(g, src[part_byte(ts, s, nt, nr)], N, ns);
             if (dst[part_byte(t, s, nt, nr)] != want) mine = 1;
         }
         if (mine) bad = 1;
@@ -71,8 +73,10 @@ __global__ void check_covariance_kernel(const uint8_t *__restrict__ part, const 
 qpfrg_status build_loop_orbits(qpfrg_ctx *c)
 {
     c->loop_red = false;
-    if (c->pb.mode != QPFRG_GRID_WEDGE || c->pb.N % 4 != 0 || c->opt.no_loop_symmetry) return QPFRG_OK;
-    const int N = c->pb.N;
+    if ((c->pb.mode != QPFRG_GRID_WEDGE && c->pb.mode != QPFRG_GRID_SHELL) || c->opt.no_loop_symmetry)
+        return QPFRG_OK;
+    const int N = c->pb.N, ns = c->pb.n_shell;
+    if ((N / ns) % 4 != 0) return QPFRG_OK;
     const long NN = (long)N * N, rows = NN * N;
     // canonical representative of every (Q, a): the image with the smallest
     // (a, Q); its patch lies in the fundamental domain 0..N/8
@@ -84,8 +88,8 @@ qpfrg_status build_loop_orbits(qpfrg_ctx *c)
                 long best = -1;
                 int bg = 0;
                 for (int g = 0; g < 8; ++g) {
-                    const long ga = c4v_apply(g, a, N);
-                    const long gQ = (long)c4v_apply(g, x, N) * N + c4v_apply(g, y, N);
+                    const long ga = c4v_apply(g, a, N, ns);
+                    const long gQ = (long)c4v_apply(g, x, N, ns) * N + c4v_apply(g, y, N, ns);
                     const long key = ga * NN + gQ;
                     if (best < 0 || key < best) {
                         best = key;
@@ -116,7 +120,7 @@ qpfrg_status build_loop_orbits(qpfrg_ctx *c)
     if (e == cudaSuccess) e = cudaMemsetAsync(d_flag, 0, 2 * rows, c->stream);
     if (e == cudaSuccess) {
         check_covariance_kernel<<<dim3((unsigned)NN, 2), 256, 0, c->stream>>>(c->d_part, d_rep, d_g, d_flag, N, c->pb.M,
-                                                                          c->pb.P, c->pb.n_theta, c->pb.n_r);
+                                                                          c->pb.P, c->pb.n_theta, c->pb.n_r, ns);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(flag.data(), d_flag, 2 * rows, cudaMemcpyDeviceToHost, c->stream);
@@ -147,7 +151,7 @@ qpfrg_status build_loop_orbits(qpfrg_ctx *c)
             Rep r{a, Q, 0, {}};
             const int x = Q / N, y = Q - x * N;
             for (int g = 0; g < 8; ++g) {
-                const int Qi = c4v_apply(g, x, N) * N + c4v_apply(g, y, N), ai = c4v_apply(g, a, N);
+                const int Qi = c4v_apply(g, x, N, ns) * N + c4v_apply(g, y, N, ns), ai = c4v_apply(g, a, N, ns);
                 const long irow = (long)Qi * N + ai;
                 if (fl[irow]) continue;                // evaluated by itself
                 bool dup = false;

@@ -5,27 +5,30 @@
 //   computed as A_hi B_hi + A_hi B_lo + A_lo B_hi with FP32 accumulation in
 //   tensor memory (the dropped A_lo B_lo term is 2^-16 relative).
 //
-// A row m of channel ch is a row of the weighted loop-kernel table (bubble.cu:
-// the loop kernels binned by partner patch, times the line weights) times the
-// vertex factor of (row, first loop patch) -- the channel algebra of
-// contract.cu:
-//   pp: m = (i,j), Q = (i,j), A[m][(a,b)] = B_pp[Q][a][b] V[i,j,a]
-//   cr: m = (j,l), Q = (l,j), A[m][(a,b)] = B_ph[Q][a][b] V[b,j,l]
-//   d : m = (i,l), Q = (i,l), A[m][(a,b)] = B_ph[Q][a][b] (2V[i,a,l] - V[a,i,l]),
-//                             A[m][N^2 + (a,b)] = -B_ph[Q][a][b] V[i,a,l]
-// so a row of A is a contiguous slice of the table (k = a N + b, taken
-// modulo N^2 in the d channel) scaled elementwise.
+// Row Q of A in channel ch is row Q of the weighted loop-kernel table
+// (bubble.cu: the loop kernels binned by partner patch, times the line
+// weights) times the vertex factor of (row, first loop patch a) -- the
+// channel algebra of contract.cu, with the rows taken in transfer order so
+// that a block of A rows is a block of table rows:
+//   pp: Q = (i,j), out row (i,j),  A[Q][(a,b)] = B_pp[Q][a][b] V[i,j,a]
+//   cr: Q = (l,j), out row (j,l),  A[Q][(a,b)] = B_ph[Q][a][b] V[b,j,l]
+//   d : Q = (i,l), out row (i,l),  A[Q][(a,b)] = B_ph[Q][a][b] (2V[i,a,l] - V[a,i,l]),
+//                                  A[Q][Kp + (a,b)] = -B_ph[Q][a][b] V[i,a,l]
 //
-// Warp roles (160 threads): warps 0-3 are producers -- they form each 128 x 64
-// A block (coalesced reads of the table, BF16 hi/lo split) straight into the
-// shared-memory stage in the canonical K-major no-swizzle order,
-// makes its writes visible to the tensor cores (fence.proxy.async) and
-// arrives on the stage's "full" mbarrier -- and afterwards read the
-// accumulators back (tcgen05.ld) and add them to the FP64 output; warp 4 loads
-// the B blocks (pre-formed per stage by tc_prep_kernel) with TMA and one of its
-// threads issues the MMAs, committing each block to the stage's "empty"
-// mbarrier.  A ring of S stages; every wait is bounded by a clock budget and
-// aborts the CTA (error flag, bounded drain, tensor memory freed).
+// Per 64-wide k block and stage: one thread (warp 4) loads the raw FP32 table
+// block (128 rows x 64 columns, two TMA boxes of 32 columns with 128-byte
+// swizzle) and the B blocks (pre-formed per stage by tc_prep_kernel); the
+// producer warps 0-3 (one A row per thread) read their rows, scale by the
+// vertex factor and overwrite them, in place, with BF16 hi and lo in the
+// K-major no-swizzle order of the MMA descriptors.  The A layout puts each
+// 8-row group's 64 k contiguously (8-row groups 1024 B apart, K-adjacent core
+// matrices 128 B apart), so a warp's 32 rows of hi occupy exactly the bytes
+// of its 32 raw rows of columns 0-31 and its lo those of columns 32-63: a
+// warp converts its rows with no barrier beyond its own lanes.  The thread of
+// warp 4 then issues the MMAs and commits each block to the stage's "empty"
+// mbarrier, after which the stage is refilled.  Every wait is bounded by a
+// clock budget and aborts the CTA (error flag, bounded drain, tensor memory
+// freed).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -41,6 +44,7 @@ namespace {
 
 constexpr int kProducers = 128;                 // threads forming A (one row each)
 constexpr int kFusedThreads = kProducers + 32;  // + the TMA / MMA warp
+constexpr uint32_t kRawBytes = tc::BM * tc::BK * 4;   // FP32 table block = hi + lo of A
 
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar)
 {
@@ -71,8 +75,8 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float x0, float x1)
 struct TcFusedArgs {
     int M, Ncol, Npad, N;             // valid rows, valid columns, padded columns, patches
     int nkb_total, kb_per_split;      // 64-wide k blocks of the padded reduction; per CTA along grid.y
+    int nkb_half;                     // k blocks per half of the d reduction (Kp / 64)
     int ch;                           // 0 pp, 1 cr, 2 d
-    const float *table;               // weighted loop-kernel table [f][Q][a][b] (FP32)
     const float *Vf, *VT;             // stage vertex [k1][k2][k3] and VT[j][l][b] = V[b][j][l]
     double *out;
     double scale;
@@ -83,28 +87,91 @@ struct TcFusedArgs {
     long long test_wait;
 };
 
-template <int S>
+// Vertex factors of row Q for the 64 columns of a k block starting at kk0
+// (within the table row).  N8: N % 8 == 0, so every 8-column chunk lies
+// within one first loop patch a and no chunk passes N^2.
+template <bool N8>
+__device__ __forceinline__ void row_factors(const TcFusedArgs &A, const float *Vf, const float *VT, int Q, bool valid,
+                                            int kk0, bool second, float (&f)[64])
+{
+    const int N = A.N;
+    const int NN = N * N;
+    if (!valid) {
+#pragma unroll
+        for (int e = 0; e < 64; ++e) f[e] = 0.f;
+        return;
+    }
+    const int qa = Q / N, qb = Q - qa * N;
+    if (N8) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int k = kk0 + 8 * c, a = k / N, b = k - a * N;
+            if (A.ch == 1) {
+                // row (j,l) = (qb, qa): V[b][j][l] = VT[((j N + l) N + b]
+                const float4 *vt = reinterpret_cast<const float4 *>(VT + ((long)qb * N + qa) * N + b);
+                const float4 c0 = __ldg(vt), c1 = __ldg(vt + 1);
+                f[8 * c + 0] = c0.x; f[8 * c + 1] = c0.y; f[8 * c + 2] = c0.z; f[8 * c + 3] = c0.w;
+                f[8 * c + 4] = c1.x; f[8 * c + 5] = c1.y; f[8 * c + 6] = c1.z; f[8 * c + 7] = c1.w;
+            } else {
+                float fac;
+                if (A.ch == 0) {
+                    fac = __ldg(Vf + (long)Q * N + a);
+                } else {
+                    // Q = (i,l) = (qa, qb)
+                    const float v_ial = __ldg(Vf + ((long)qa * N + a) * N + qb);
+                    fac = second ? -v_ial : 2.f * v_ial - __ldg(Vf + ((long)a * N + qa) * N + qb);
+                }
+#pragma unroll
+                for (int e = 0; e < 8; ++e) f[8 * c + e] = fac;
+            }
+        }
+    } else {
+        int a = kk0 / N, b = kk0 - (kk0 / N) * N;
+#pragma unroll
+        for (int e = 0; e < 64; ++e) {
+            float fac = 0.f;
+            if (kk0 + e < NN) {
+                if (A.ch == 0) {
+                    fac = __ldg(Vf + (long)Q * N + a);
+                } else if (A.ch == 1) {
+                    fac = __ldg(VT + ((long)qb * N + qa) * N + b);
+                } else {
+                    const float v_ial = __ldg(Vf + ((long)qa * N + a) * N + qb);
+                    fac = second ? -v_ial : 2.f * v_ial - __ldg(Vf + ((long)a * N + qa) * N + qb);
+                }
+            }
+            f[e] = fac;
+            if (++b == N) {
+                b = 0;
+                ++a;
+            }
+        }
+    }
+}
+
+template <int S, bool N8>
 __global__ void __launch_bounds__(kFusedThreads, 1)
-    tc_fused_kernel(const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo, TcFusedArgs A)
+    tc_fused_kernel(const __grid_constant__ CUtensorMap mTab, const __grid_constant__ CUtensorMap mBhi,
+                    const __grid_constant__ CUtensorMap mBlo, TcFusedArgs A)
 {
     using namespace tc;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ uint64_t full[S], empty[S], never;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ uint64_t rfull[S], full[S], empty[S], never;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
 
     // the flow of this CTA (batched launch) or the context's single flow
-    const float *tab_base = A.table, *Vf = A.Vf, *VT = A.VT;
+    const float *Vf = A.Vf, *VT = A.VT;
     double *out = A.out;
     double scale = A.scale;
-    const CUtensorMap *mhi = &mBhi, *mlo = &mBlo;
+    const CUtensorMap *mtab = &mTab, *mhi = &mBhi, *mlo = &mBlo;
     if (A.batch.nflows) {
         const TcBatch &Bt = A.batch;
         const int f = blockIdx.z;
         const long sf = (long)Bt.step * Bt.nflows + f;
         const double h = Bt.h_tab[sf];
         if (Bt.status[f] != QPFRG_FLOW_RUNNING || h == 0.0) return;   // uniform, before any barrier
-        tab_base = Bt.rows[Bt.slot_tab[sf]];
+        mtab = Bt.tab_maps + Bt.slot_tab[sf];
         Vf = Bt.Vf[f];
         VT = Bt.VT[f];
         out = Bt.out[f];
@@ -118,14 +185,20 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     const int kb1 = min(A.nkb_total, kb0 + A.kb_per_split);
     const int nkb = kb1 - kb0;
     const int Npad = A.Npad, N = A.N;
-    const uint32_t a_bytes = BM * BK * 2, b_bytes = (uint32_t)Npad * BK * 2;
-    const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
-    const uint32_t base = smem_u32(smem_raw);
+    const int NN = N * N;
+    const int fam = A.ch == 0 ? 0 : 1;
+    const uint32_t b_bytes = (uint32_t)Npad * BK * 2;
+    const uint32_t stage_bytes = kRawBytes + 2 * b_bytes;
+    // stages on 1024-byte boundaries (the 128-byte swizzle repeats every 1024 B)
+    const uint32_t raw_base = smem_u32(smem_raw);
+    const uint32_t base = (raw_base + 1023u) & ~1023u;
+    unsigned char *const sbase = smem_raw + (base - raw_base);
     const uint32_t tmem_cols = Npad <= 32 ? 32 : (Npad <= 64 ? 64 : (Npad <= 128 ? 128 : 256));
 
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
-            mbar_init(smem_u32(&full[s]), kProducers + 1);   // producers + the B copy's expect-tx arrival
+            mbar_init(smem_u32(&rfull[s]), 1);            // the copies' expect-tx arrival (table and B)
+            mbar_init(smem_u32(&full[s]), kProducers);    // the producers' A rows
             mbar_init(smem_u32(&empty[s]), 1);
         }
         mbar_init(smem_u32(&never), 1);
@@ -145,104 +218,55 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     volatile int *abort_v = &abort_flag;
 
     if (warp < 4) {
-        // ---- producers: each warp forms rows 32 w .. 32 w + 31 of every A
-        // block in eight rounds of four rows; lane (rg, kc) = (lane / 8, lane % 8)
-        // takes row 4 q + rg of round q and the 8-wide k chunk kc.  A row of the
-        // channel is a contiguous slice of the weighted table (pp: B_pp[Q]; cr,
-        // d: B_ph[Q], k taken modulo N^2), so the eight lanes of a row read 256
-        // contiguous bytes as two aligned 16-byte loads each, then scale by the
-        // vertex factor and write one 16-byte chunk of hi and of lo.
-        const long NN = (long)N * N;
-        const int lane = tid & 31, rg = lane >> 3, kc = lane & 7;
-        const int ch = A.ch, fam = ch == 0 ? 0 : 1;
-        const long Kvalid = ch == 2 ? 2 * NN : NN;
-        const bool n8 = (N & 7) == 0;                // a chunk of 8 lies within one a
+        // ---- producers: thread tid owns row rr = tid of every block ----
+        const int rr = tid;
+        const int Q = m0 + rr;
+        const bool valid = Q < A.M;
+        // raw row rr of the half h, 16-byte chunk c: rr 128 + (c ^ (rr % 8)) 16
+        // (128-byte swizzle); A row rr, k chunk kc: (rr / 8) 1024 + kc 128 + (rr % 8) 16
+        const uint32_t raw_row = (uint32_t)rr * 128, sw = (uint32_t)(rr & 7);
+        const uint32_t a_row = (uint32_t)(rr >> 3) * 1024 + (uint32_t)(rr & 7) * 16;
         bool ok = true;
         for (int it = 0; it < nkb && ok; ++it) {
             const int s = it % S;
-            if (it >= S && !mbar_wait_abortable(smem_u32(&empty[s]), (uint32_t)(((it / S) - 1) & 1), abort_v)) {
+            const int kb = kb0 + it;
+            const bool second = A.ch == 2 && kb >= A.nkb_half;
+            const int kk0 = (kb - (second ? A.nkb_half : 0)) * BK;
+            float f[64];
+            row_factors<N8>(A, Vf, VT, Q, valid, kk0, second, f);     // loads in flight during the wait
+            const bool got = mbar_wait_abortable(smem_u32(&rfull[s]), (uint32_t)((it / S) & 1), abort_v);
+            if (!__all_sync(0xffffffffu, got)) {
                 ok = false;
                 break;
             }
-            const long k0 = (long)(kb0 + it) * BK + kc * 8;     // first k of this lane's chunk
-            unsigned char *st = smem_raw + (size_t)s * stage_bytes;
-#pragma unroll 2
-            for (int q = 0; q < 8; ++q) {
-                const int rr = warp * 32 + 4 * q + rg;          // row within the block
-                const int r = m0 + rr;
-                float v[8];
+            unsigned char *st = sbase + (size_t)s * stage_bytes;
+            float v[64];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] = 0.f;
-                if (r < A.M && k0 < Kvalid) {                    // N^2 % 8 == 0: a chunk never crosses Kvalid
-                    int Qr, ri = 0, rl = 0;
-                    if (ch == 0) {
-                        Qr = r;
-                    } else if (ch == 1) {
-                        const int j = r / N, l = r - j * N;
-                        Qr = l * N + j;
-                    } else {
-                        ri = r / N;
-                        rl = r - ri * N;
-                        Qr = r;
-                    }
-                    const bool second = ch == 2 && k0 >= NN;
-                    const int kk = (int)(second ? k0 - NN : k0);
-                    const float4 *src = reinterpret_cast<const float4 *>(tab_base + ((long)fam * NN + Qr) * NN + kk);
-                    const float4 t0 = __ldg(src), t1 = __ldg(src + 1);
-                    const float t[8] = {t0.x, t0.y, t0.z, t0.w, t1.x, t1.y, t1.z, t1.w};
-                    int a = kk / N, b = kk - a * N;
-                    if (n8) {
-                        if (ch == 1) {
-                            // V[b][j][l] = VT[(j N + l) N + b] for b .. b+7 (aligned)
-                            const float4 *vt = reinterpret_cast<const float4 *>(VT + (long)r * N + b);
-                            const float4 c0 = __ldg(vt), c1 = __ldg(vt + 1);
-                            const float c[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+            for (int h = 0; h < 2; ++h)
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) v[e] = t[e] * c[e];
-                        } else {
-                            float fac;
-                            if (ch == 0) {
-                                fac = __ldg(Vf + (long)Qr * N + a);
-                            } else {
-                                const float v_ial = __ldg(Vf + ((long)ri * N + a) * N + rl);
-                                fac = second ? -v_ial : 2.f * v_ial - __ldg(Vf + ((long)a * N + ri) * N + rl);
-                            }
-#pragma unroll
-                            for (int e = 0; e < 8; ++e) v[e] = t[e] * fac;
-                        }
-                    } else {
-                        // N not a multiple of 8: the chunk may cross to the next a
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            float fac;
-                            if (ch == 0) {
-                                fac = __ldg(Vf + (long)Qr * N + a);
-                            } else if (ch == 1) {
-                                fac = __ldg(VT + (long)r * N + b);
-                            } else {
-                                const float v_ial = __ldg(Vf + ((long)ri * N + a) * N + rl);
-                                fac = second ? -v_ial : 2.f * v_ial - __ldg(Vf + ((long)a * N + ri) * N + rl);
-                            }
-                            v[e] = t[e] * fac;
-                            if (++b == N) {
-                                b = 0;
-                                ++a;
-                            }
-                        }
-                    }
+                for (int c = 0; c < 8; ++c) {
+                    const float4 x = *reinterpret_cast<const float4 *>(st + h * (kRawBytes / 2) + raw_row +
+                                                                       ((c ^ sw) << 4));
+                    v[32 * h + 4 * c + 0] = x.x;
+                    v[32 * h + 4 * c + 1] = x.y;
+                    v[32 * h + 4 * c + 2] = x.z;
+                    v[32 * h + 4 * c + 3] = x.w;
                 }
+            __syncwarp();      // the warp's raw rows are read before they are overwritten
+#pragma unroll
+            for (int kc = 0; kc < 8; ++kc) {
                 uint4 hi, lo;
-                uint32_t *h = &hi.x, *l = &lo.x;
+                uint32_t *hp = &hi.x, *lp = &lo.x;
 #pragma unroll
-                for (int qq = 0; qq < 4; ++qq) {
-                    const __nv_bfloat162 hh = __floats2bfloat162_rn(v[2 * qq], v[2 * qq + 1]);
-                    h[qq] = *reinterpret_cast<const uint32_t *>(&hh);
-                    l[qq] = pack_bf16x2(v[2 * qq] - __low2float(hh), v[2 * qq + 1] - __high2float(hh));
+                for (int q = 0; q < 4; ++q) {
+                    const float x0 = v[8 * kc + 2 * q] * f[8 * kc + 2 * q];
+                    const float x1 = v[8 * kc + 2 * q + 1] * f[8 * kc + 2 * q + 1];
+                    const __nv_bfloat162 hh = __floats2bfloat162_rn(x0, x1);
+                    hp[q] = *reinterpret_cast<const uint32_t *>(&hh);
+                    lp[q] = pack_bf16x2(x0 - __low2float(hh), x1 - __high2float(hh));
                 }
-                // core matrix (kc, row group) at ((kc (BM/8) + rr/8) 128) + (rr%8) 16 bytes
-                const uint32_t o = (uint32_t)kc * (BM / 8) * 128 + (uint32_t)((rr >> 3) * 128 + (rr & 7) * 16);
-                *reinterpret_cast<uint4 *>(st + o) = hi;
-                *reinterpret_cast<uint4 *>(st + a_bytes + o) = lo;
+                *reinterpret_cast<uint4 *>(st + a_row + kc * 128) = hi;
+                *reinterpret_cast<uint4 *>(st + kRawBytes / 2 + a_row + kc * 128) = lo;
             }
             fence_async_shared();
             mbar_arrive(smem_u32(&full[s]));
@@ -254,13 +278,19 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
             if (!mbar_wait_abortable(smem_u32(&empty[last % S]), (uint32_t)((last / S) & 1), abort_v)) abort_flag = 1;
         }
     } else if (tid == 128 && nkb > 0) {
-        // ---- B copies and MMAs ----
-        auto issue_b = [&](int kb, int s) {
-            const uint32_t sb = base + (uint32_t)s * stage_bytes, fb = smem_u32(&full[s]);
-            mbar_expect_tx(fb, 2 * b_bytes);
+        // ---- table and B copies, MMAs ----
+        const int ytab = fam * NN + m0;
+        auto issue = [&](int kb, int s) {
+            const uint32_t sb = base + (uint32_t)s * stage_bytes;
+            const bool second = A.ch == 2 && kb >= A.nkb_half;
+            const int kk0 = (kb - (second ? A.nkb_half : 0)) * BK;
+            const uint32_t rb = smem_u32(&rfull[s]);
+            mbar_expect_tx(rb, kRawBytes + 2 * b_bytes);
+            tma_load_2d(sb, mtab, kk0, ytab, rb);
+            tma_load_2d(sb + kRawBytes / 2, mtab, kk0 + 32, ytab, rb);
             const int yb = kb * (Npad / 2);
-            tma_load_2d(sb + 2 * a_bytes, mhi, 0, yb, fb);
-            tma_load_2d(sb + 2 * a_bytes + b_bytes, mlo, 0, yb, fb);
+            tma_load_2d(sb + kRawBytes, mhi, 0, yb, rb);
+            tma_load_2d(sb + kRawBytes + b_bytes, mlo, 0, yb, rb);
         };
         const uint32_t idesc = make_idesc(BM, Npad);
         int issued = 0, consumed = 0;
@@ -274,10 +304,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                     break;
                 }
         }
-        for (; ok && issued < S && issued < nkb; ++issued) issue_b(kb0 + issued, issued);
+        for (; ok && issued < S && issued < nkb; ++issued) issue(kb0 + issued, issued);
         for (int i = 0; i < nkb && ok; ++i) {
             const int s = i % S;
-            if (!mbar_wait_abortable(smem_u32(&full[s]), (uint32_t)((i / S) & 1), abort_v)) {
+            // the A rows formed, and (already complete by then) the B copies
+            if (!mbar_wait_abortable(smem_u32(&full[s]), (uint32_t)((i / S) & 1), abort_v) ||
+                !mbar_wait_abortable(smem_u32(&rfull[s]), (uint32_t)((i / S) & 1), abort_v)) {
                 ok = false;
                 break;
             }
@@ -285,12 +317,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
             const uint32_t sb = base + (uint32_t)s * stage_bytes;
 #pragma unroll
             for (int ks = 0; ks < BK / 16; ++ks) {
-                const uint32_t a_off = (uint32_t)(2 * ks * (BM / 8) * 128);
+                const uint32_t a_off = (uint32_t)(ks * 256);                  // two 128-byte core matrices
                 const uint32_t b_off = (uint32_t)(2 * ks * (Npad / 8) * 128);
-                const uint64_t ahi = make_desc(sb + a_off, (BM / 8) * 128, 128);
-                const uint64_t alo = make_desc(sb + a_bytes + a_off, (BM / 8) * 128, 128);
-                const uint64_t bhi = make_desc(sb + 2 * a_bytes + b_off, (Npad / 8) * 128, 128);
-                const uint64_t blo = make_desc(sb + 2 * a_bytes + b_bytes + b_off, (Npad / 8) * 128, 128);
+                const uint64_t ahi = make_desc(sb + a_off, 128, 1024);
+                const uint64_t alo = make_desc(sb + kRawBytes / 2 + a_off, 128, 1024);
+                const uint64_t bhi = make_desc(sb + kRawBytes + b_off, (Npad / 8) * 128, 128);
+                const uint64_t blo = make_desc(sb + kRawBytes + b_bytes + b_off, (Npad / 8) * 128, 128);
                 const uint32_t acc = (i > 0 || ks > 0) ? 1u : 0u;
                 mma_bf16(tmem, ahi, bhi, idesc, acc);
                 mma_bf16(tmem, ahi, blo, idesc, 1u);
@@ -298,22 +330,22 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
             }
             mma_commit(smem_u32(&empty[s]));
             consumed = i + 1;
-            // refill the B half of the stage of block i-1 once its products are done
+            // refill the stage of block i-1 once its products are done
             if (i >= 1 && issued < nkb) {
                 const int j = i - 1;
                 if (!mbar_wait_abortable(smem_u32(&empty[j % S]), (uint32_t)((j / S) & 1), abort_v)) {
                     ok = false;
                     break;
                 }
-                issue_b(kb0 + issued, issued % S);
+                issue(kb0 + issued, issued % S);
                 ++issued;
             }
         }
         if (!ok) {
             abort_flag = 1;
-            // drain (bounded): the B copies issued land and the products committed end
+            // drain (bounded): the copies issued land and the products committed end
             for (int j = consumed; j < issued; ++j)
-                mbar_wait_bounded(smem_u32(&full[j % S]), (uint32_t)((j / S) & 1));
+                mbar_wait_bounded(smem_u32(&rfull[j % S]), (uint32_t)((j / S) & 1));
             if (consumed > 0)
                 mbar_wait_bounded(smem_u32(&empty[(consumed - 1) % S]), (uint32_t)(((consumed - 1) / S) & 1));
         }
@@ -325,20 +357,20 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         if (tid == 0) atomicOr(A.err, 1u);
     } else if (nkb > 0 && warp < 4) {
         // epilogue: warp w reads accumulator rows 32w .. 32w+31 (its TMEM lanes)
-        const int r = m0 + tid;
-        const long NN = (long)N * N;
+        const int Q = m0 + tid;
+        const int qa = Q / N, qb = Q - qa * N;
         for (int c0 = 0; c0 < Npad; c0 += 16) {
             float v[16];
             tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            if (r < A.M) {
+            if (Q < A.M) {
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
                     const int n = c0 + q;
                     if (n >= A.Ncol) continue;
                     long o;
-                    if (A.ch == 0) o = (long)r * N + n;
-                    else if (A.ch == 1) o = (long)n * NN + r;
-                    else o = ((long)(r / N) * N + n) * N + (r % N);
+                    if (A.ch == 0) o = (long)Q * N + n;                          // (i, j, n)
+                    else if (A.ch == 1) o = (long)n * NN + (long)qb * N + qa;     // (n, j, l)
+                    else o = ((long)qa * N + n) * N + qb;                         // (i, n, l)
                     atomicAdd(&out[o], scale * (double)v[q]);
                 }
             }
@@ -357,20 +389,23 @@ static qpfrg_status launch_fused(qpfrg_ctx *c, int ch, TcFusedArgs &A, int nz, i
     const int N = c->pb.N, Npad = t.Npad;
     const long NN = (long)N * N;
     const long Kp = ch == 2 ? t.Kpd : t.Kp;
-    const size_t stage_bytes = 2 * (size_t)tc::BM * tc::BK * 2 + 2 * (size_t)Npad * tc::BK * 2;
-    // as many stages as fit beside the kernel's static shared memory (barriers,
-    // Z and K tables) within the 227 KB a block may opt into
+    const size_t stage_bytes = kRawBytes + 2 * (size_t)Npad * tc::BK * 2;
+    // as many stages as fit beside the kernel's static shared memory (barriers)
+    // and the 1 KB of alignment slack within the 227 KB a block may opt into
     cudaFuncAttributes fa{};
-    cudaError_t e = cudaFuncGetAttributes(&fa, tc_fused_kernel<4>);
+    cudaError_t e = cudaFuncGetAttributes(&fa, tc_fused_kernel<4, true>);
     if (e != cudaSuccess) return cuda_fail(c, e, "tc_fused attributes");
-    const size_t smem_max = 227 * 1024 - fa.sharedSizeBytes;
+    const size_t smem_max = 227 * 1024 - 1024 - fa.sharedSizeBytes;
     int S = (int)std::min<size_t>(4, smem_max / stage_bytes);
-    if (Npad % 16 != 0 || Npad > 256 || N > 256 || S < 2) {
+    if (Npad % 16 != 0 || Npad > 256 || N > 256 || (N & 1) || S < 2) {
         c->err = "tensor-core contraction: unsupported shape";
         return QPFRG_ERR_UNSUPPORTED;
     }
-    const size_t smem = S * stage_bytes;
-    auto kern = S == 4 ? tc_fused_kernel<4> : (S == 3 ? tc_fused_kernel<3> : tc_fused_kernel<2>);
+    const size_t smem = S * stage_bytes + 1024;
+    const bool n8 = (N & 7) == 0;
+    auto kern = n8 ? (S == 4 ? tc_fused_kernel<4, true> : (S == 3 ? tc_fused_kernel<3, true> : tc_fused_kernel<2, true>))
+                   : (S == 4 ? tc_fused_kernel<4, false>
+                             : (S == 3 ? tc_fused_kernel<3, false> : tc_fused_kernel<2, false>));
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(c, e, "tc_fused smem attribute");
     const int M = (int)NN;
@@ -397,11 +432,12 @@ static qpfrg_status launch_fused(qpfrg_ctx *c, int ch, TcFusedArgs &A, int nz, i
     A.N = N;
     A.nkb_total = nkb;
     A.kb_per_split = kb_per;
+    A.nkb_half = (int)(t.Kp / tc::BK);
     A.ch = ch;
     A.err = c->d_tc_err;
     A.test_wait = std::getenv("QPFRG_TEST_TC_WAIT") ? 10000000LL : 0;   // ~5 ms
     prof_begin(c);
-    kern<<<dim3(mtiles, splits, nz), kFusedThreads, smem, c->stream>>>(t.tmB[ch][0], t.tmB[ch][1], A);
+    kern<<<dim3(mtiles, splits, nz), kFusedThreads, smem, c->stream>>>(t.tmTab, t.tmB[ch][0], t.tmB[ch][1], A);
     prof_end(c, kid);
     e = cudaGetLastError();
     return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "tc_fused_kernel");
@@ -412,7 +448,6 @@ static qpfrg_status launch_fused(qpfrg_ctx *c, int ch, TcFusedArgs &A, int nz, i
 qpfrg_status launch_tc_fused(qpfrg_ctx *c, int ch, double scale, double *out, int kid)
 {
     TcFusedArgs A{};
-    A.table = reinterpret_cast<const float *>(c->d_B);
     A.Vf = c->d_Vf;
     A.VT = c->tc.VT;
     A.out = out;

@@ -16,8 +16,10 @@ namespace qpfrg {
 // Per-stage B operands of the three channel GEMMs from the FP32 stage vertex,
 // rows n (n >= N zero) by reduction index k = (a, b) = a N + b, split into
 // BF16 hi/lo and stored in tiles (tile_index, Npad rows per tile):
-// pp: V[a,b,n];  cr: V[n,a,b];  d: V[b,n,a] (k < N^2) and V[n,b,a]
-// (k >= N^2);  plus VT[j][l][b] = V[b][j][l] for the cr factor.
+// pp: V[a,b,n];  cr: V[n,a,b];  d: V[b,n,a] at k and V[n,b,a] at Kp + k, so
+// that each half of the d reduction starts on a 64-wide block;  pads (n >= N,
+// k >= N^2 within a half) are written as zeros;  plus VT[j][l][b] = V[b][j][l]
+// for the cr factor.
 struct TcPrepArgs {
     const float *V;
     int N, Npad;
@@ -29,8 +31,8 @@ struct TcPrepArgs {
 __device__ __forceinline__ void tc_prep_body(const TcPrepArgs &t)
 {
     const int N = t.N, Npad = t.Npad;
-    const long NN = (long)N * N, n3 = NN * N;
-    const long s_pp = (long)Npad * NN, s_d = 2 * s_pp;
+    const long NN = (long)N * N, n3 = NN * N, Kp = t.Kp;
+    const long s_pp = (long)Npad * Kp, s_d = 2 * s_pp;
     const long total = 2 * s_pp + s_d + n3;
     const float *V = t.V;
     for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
@@ -40,16 +42,17 @@ __device__ __forceinline__ void tc_prep_body(const TcPrepArgs &t)
             if (idx < s_pp) { which = 0; loc = idx; }
             else if (idx < 2 * s_pp) { which = 1; loc = idx - s_pp; }
             else { which = 2; loc = idx - 2 * s_pp; }
-            const long K = which == 2 ? 2 * NN : NN;
+            const long K = which == 2 ? 2 * Kp : Kp;
             const int n = (int)(loc / K);
             const long k = loc - (long)n * K;
+            const bool second = k >= Kp;
+            const long kk = second ? k - Kp : k;
             float v = 0.f;
-            if (n < N) {
-                const long kk = k >= NN ? k - NN : k;
+            if (n < N && kk < NN) {
                 const int a = (int)(kk / N), b = (int)(kk - (long)a * N);
                 if (which == 0) v = V[kk * N + n];
                 else if (which == 1) v = V[(long)n * NN + kk];
-                else if (k < NN) v = V[((long)b * N + n) * N + a];
+                else if (!second) v = V[((long)b * N + n) * N + a];
                 else v = V[((long)n * N + b) * N + a];
             }
             const __nv_bfloat16 hi = __float2bfloat16_rn(v);
@@ -91,7 +94,7 @@ qpfrg_status launch_tc_prep_batch(qpfrg_ctx *c, const TcPrepFlow *d_flows, const
 {
     const int N = c->pb.N;
     const long NN = (long)N * N;
-    const long total = 4 * (long)c->tc.Npad * NN + NN * N;
+    const long total = 4 * (long)c->tc.Npad * c->tc.Kp + NN * N;
     const int blocks = (int)std::min<long>((total + 255) / 256, 152L * 4);
     TcPrepArgs t{};
     t.N = N;
@@ -109,7 +112,7 @@ qpfrg_status launch_tc_prep(qpfrg_ctx *c)
 {
     const int N = c->pb.N;
     const long NN = (long)N * N;
-    const long total = 4 * (long)c->tc.Npad * NN + NN * N;
+    const long total = 4 * (long)c->tc.Npad * c->tc.Kp + NN * N;
     int blocks = (int)std::min<long>((total + 255) / 256, 152L * 16);
     TcPrepArgs t;
     t.V = c->d_Vf;
@@ -132,7 +135,8 @@ qpfrg_status launch_tc_prep(qpfrg_ctx *c)
 
 // 2-D TMA map over a tiled BF16 buffer of `elems` elements viewed as rows of
 // 128 elements (256 B): boxes of 128 x box_rows elements are whole tiles.
-qpfrg_status make_tile_map(qpfrg_ctx *c, CUtensorMap *map, const void *base, long elems, int box_rows)
+// The driver's tensor-map encoder, looked up once.
+static PFN_cuTensorMapEncodeTiled_v12000 map_encoder(qpfrg_ctx *c)
 {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
@@ -143,10 +147,38 @@ qpfrg_status make_tile_map(qpfrg_ctx *c, CUtensorMap *map, const void *base, lon
             q != cudaDriverEntryPointSuccess || !fn) {
             cudaGetLastError();
             c->err = "cuTensorMapEncodeTiled is not available";
-            return QPFRG_ERR_CUDA;
+            return nullptr;
         }
         encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
+    return encode;
+}
+
+qpfrg_status make_table_map(qpfrg_ctx *c, CUtensorMap *map, const float *table, int N)
+{
+    const auto encode = map_encoder(c);
+    if (!encode) return QPFRG_ERR_CUDA;
+    const cuuint64_t NN = (cuuint64_t)N * N;
+    // rows of N^2 floats (a multiple of 16 bytes for even N); columns past
+    // N^2 and rows past the two families read as zeros
+    const cuuint64_t dims[2] = {NN, 2 * NN};
+    const cuuint64_t strides[1] = {NN * sizeof(float)};
+    const cuuint32_t box[2] = {32, 128};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(table), dims, strides, box,
+                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        c->err = "cuTensorMapEncodeTiled failed for the loop-kernel table";
+        return QPFRG_ERR_CUDA;
+    }
+    return QPFRG_OK;
+}
+
+qpfrg_status make_tile_map(qpfrg_ctx *c, CUtensorMap *map, const void *base, long elems, int box_rows)
+{
+    const auto encode = map_encoder(c);
+    if (!encode) return QPFRG_ERR_CUDA;
     const cuuint64_t dims[2] = {128, (cuuint64_t)(elems / 128)};
     const cuuint64_t strides[1] = {256};
     const cuuint32_t box[2] = {128, (cuuint32_t)box_rows};
@@ -172,6 +204,7 @@ qpfrg_status tc_make_maps(qpfrg_ctx *c)
             break;
         s = make_tile_map(c, &t.tmB[2][h], t.Bd[h], nbd, t.Npad / 2);
     }
+    if (s == QPFRG_OK) s = make_table_map(c, &t.tmTab, reinterpret_cast<const float *>(c->d_B), c->pb.N);
     return s;
 }
 

@@ -1,4 +1,4 @@
-// Inline-PTX helpers of the tcgen05 contractions (tc_gemm.cu, tc_fused.cu):
+// Inline-PTX helpers of the tcgen05 contraction (tc_fused.cu):
 // shared-memory matrix and instruction descriptors, mbarrier waits bounded by
 // a clock budget, TMA tile loads, tcgen05 MMA / commit / TMEM loads.
 #pragma once
@@ -94,7 +94,7 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes)
 }
 
 // 2-D TMA tile copy global -> shared, completion counted on mbar in bytes;
-// the inner coordinate x is 0 (16-byte aligned by construction)
+// callers pass an inner coordinate x whose byte offset is a multiple of 16
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar)
 {
     asm volatile(

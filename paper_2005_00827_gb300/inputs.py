@@ -29,43 +29,49 @@ def splitmix64(seed: int):
         yield (z >> 11) * (1.0 / (1 << 53))
 
 
-def c4v_patch_maps(N: int):
-    """The 8 index permutations of the wedge patches under C4v (patch centres
-    at 2 pi j / N, N a multiple of 4): j -> +-j + m N/4 (mod N)."""
-    if N % 4:
-        raise ValueError("C4v needs N % 4 == 0")
-    j = np.arange(N)
+def c4v_patch_maps(N: int, n_shell: int = 1):
+    """The 8 index permutations of the angular patches under C4v (wedge
+    centres at 2 pi w / N_a, N_a = N / n_shell a multiple of 4; patch
+    j = w n_shell + s): w -> +-w + m N_a/4 (mod N_a), the shell s kept."""
+    Na = N // n_shell
+    if N % n_shell or Na % 4:
+        raise ValueError("C4v needs N / n_shell % 4 == 0")
+    w, sh = np.divmod(np.arange(N), n_shell)
     maps = []
     for m in range(4):
-        maps.append((j + m * N // 4) % N)
-        maps.append((-j + m * N // 4) % N)
+        maps.append(((w + m * Na // 4) % Na) * n_shell + sh)
+        maps.append(((-w + m * Na // 4) % Na) * n_shell + sh)
     return maps
 
 
-def c4v_symmetrise(V: np.ndarray) -> np.ndarray:
+def c4v_symmetrise(V: np.ndarray, n_shell: int = 1) -> np.ndarray:
     """Average a coupling array V[k1,k2,k3] over the C4v patch permutations."""
     N = V.shape[0]
     out = np.zeros_like(V)
-    for g in c4v_patch_maps(N):
+    for g in c4v_patch_maps(N, n_shell):
         out += V[np.ix_(g, g, g)]
     return out / 8.0
 
 
-def random_vertex(N: int, U: float, seed: int = 1, amp: float = 0.5, c4v: bool = True) -> np.ndarray:
+def random_vertex(N: int, U: float, seed: int = 1, amp: float = 0.5, c4v: bool = True,
+                  n_shell: int = 1) -> np.ndarray:
     """V = U + amp U s with s uniform in [-1, 1] (splitmix64), FP64, [k1][k2][k3]."""
     gen = splitmix64(seed)
     s = np.fromiter((2.0 * next(gen) - 1.0 for _ in range(N ** 3)), dtype=np.float64, count=N ** 3)
     V = (U + amp * U * s).reshape(N, N, N)
-    return c4v_symmetrise(V) if c4v else V
+    return c4v_symmetrise(V, n_shell) if c4v else V
 
 
-def z_profile(N: int, kind: str = "one") -> np.ndarray:
+def z_profile(N: int, kind: str = "one", n_shell: int = 1) -> np.ndarray:
     """Quasi-particle weights per patch: 'one' (Z = 1) or 'aniso'
-    (Z_j = 0.9 + 0.05 cos(4 theta_j), theta_j = 2 pi j / N, C4v symmetric)."""
+    (Z_j = 0.9 + 0.05 cos(4 theta_j) - 0.02 s', theta_j = 2 pi w / N_a the
+    angle of patch j = w n_shell + s and s' = |s - n_shell // 2| its distance
+    from the Fermi shell; C4v symmetric)."""
     if kind == "one":
         return np.ones(N)
-    th = 2 * np.pi * np.arange(N) / N
-    return 0.9 + 0.05 * np.cos(4 * th)
+    w, sh = np.divmod(np.arange(N), n_shell)
+    th = 2 * np.pi * w / (N // n_shell)
+    return 0.9 + 0.05 * np.cos(4 * th) - 0.02 * np.abs(sh - n_shell // 2)
 
 
 def batch_specs(count: int = 128, seed: int = 20050082):
@@ -89,4 +95,7 @@ WORKLOADS = {
     "np48_n32": dict(N=48, n=32, U=3.0, T_end=0.05, z_feedback=True, n_omega=512),
     "np96_n32": dict(N=96, n=32, U=2.5, T_end=0.02, z_feedback=True, n_omega=1024),
     "np192_n32": dict(N=192, n=32, U=2.0, T_end=0.01, z_feedback=True, n_omega=2048),
+    # energy-shell patching (Sec. 3.2): 32 angular sections x 7 shells = 224 patches,
+    # per patch 8 angular x 8 radial fine points
+    "np224_s7": dict(N=224, n=8, U=2.0, T_end=0.05, z_feedback=True, n_omega=0, n_shell=7),
 }

@@ -30,8 +30,8 @@ def normwise(a, b):
 
 
 @pytest.mark.parametrize("case", [(16, 4, 4, 0, 7), (24, 4, 6, 0, 7), (16, 1, 1, 1, 7), (16, 4, 4, 0, 1),
-                                  (16, 4, 4, 0, 2), (16, 4, 4, 0, 4), (36, 1, 1, 1, 7)],
-                         ids=["w16", "w24_ragged", "lat4", "pp_only", "cr_only", "d_only", "lat6"])
+                                  (16, 4, 4, 0, 2), (16, 4, 4, 0, 4), (36, 1, 1, 1, 7), (20, 2, 4, 0, 7)],
+                         ids=["w16", "w24_ragged", "lat4", "pp_only", "cr_only", "d_only", "lat6", "w20_ragged_k"])
 def test_tc_rhs_matches_oracle(case):
     N, nt, nr, mode, ch = case
     T = 0.25
