@@ -331,6 +331,7 @@ def run_qpfrg(args):
     # roofline of the dominant kernel (ALU bound: FP32 issue and MUFU pipes)
     peaks, peak_kind = load_peaks()
     clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
     kern = {k: v for k, v in prof.items() if v[1] > 0}
     dom = max(kern, key=lambda k: kern[k][0])
     M = N * n * n
@@ -370,14 +371,20 @@ def run_qpfrg(args):
                               "peak_source": peak_note}
     tc = [k for k in ("tc_fused_pp", "tc_fused_cr", "tc_fused_d") if k in kern]
     if len(tc) == 3:
-        # three BF16 products (hi hi, hi lo, lo hi) of M = N^2 rows, N columns
-        # and K = N^2 (pp, cr) + 2 N^2 (d): 24 N^5 flop per RHS on the tensor cores
-        flop = 24.0 * N ** 5
+        # The channel GEMMs stream the FP32 weighted table: pp its pp family
+        # (N^4 floats), cr the ph family, d the ph family twice (K = 2 N^2):
+        # 16 N^4 bytes per RHS, against the HBM copy peak.  On the tensor
+        # cores: three BF16 products (hi hi, hi lo, lo hi) of N^2 rows, N
+        # columns and K = N^2 (pp, cr) + 2 N^2 (d): 24 N^5 flop per RHS.
+        nbytes, flop = 16.0 * N ** 4, 24.0 * N ** 5
         t_s = sum(kern[k][0] / kern[k][1] for k in tc) / 1e3
         bf16 = float(peaks.get("bf16_tflops", 1900.0))
-        rhs_roof["tc_fused"] = {"bound": "tensor", "achieved": flop / t_s / 1e12, "peak": bf16, "unit": "TFLOP/s",
-                                "frac": flop / t_s / 1e12 / bf16, "flop_per_rhs": flop, "ms_per_rhs": t_s * 1e3,
-                                "peak_source": f"{peak_kind} bf16_tflops (burst)"}
+        rhs_roof["tc_fused"] = {"bound": "hbm", "achieved": nbytes / t_s / 1e9, "peak": hbm, "unit": "GB/s",
+                                "frac": nbytes / t_s / 1e9 / hbm, "bytes_per_rhs": nbytes, "ms_per_rhs": t_s * 1e3,
+                                "peak_source": f"{peak_kind} hbm_gbs",
+                                "tensor": {"achieved": flop / t_s / 1e12, "peak": bf16, "unit": "TFLOP/s",
+                                           "frac": flop / t_s / 1e12 / bf16, "flop_per_rhs": flop,
+                                           "peak_source": f"{peak_kind} bf16_tflops (burst)"}}
 
     line = {
         "metric": METRIC.format(N=N), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -589,12 +596,14 @@ def run_rhs_only(args):
     torch.cuda.set_device(0)
     wl = inputs.WORKLOADS[args.workload]
     N, n, U = wl["N"], wl["n"], wl["U"]
+    ns = wl.get("n_shell", 1)
+    mode = api.QPFRG_GRID_SHELL if ns > 1 else api.QPFRG_GRID_WEDGE
     prec = {"mixed": api.QPFRG_MIXED, "tc": api.QPFRG_MIXED_TC, "fp64": api.QPFRG_FP64}[args.rhs_only]
     stream = torch.cuda.current_stream()
-    V = torch.from_numpy(inputs.random_vertex(N, U, seed=1).ravel()).cuda()
-    Z = torch.from_numpy(inputs.z_profile(N, "aniso")).cuda()
+    V = torch.from_numpy(inputs.random_vertex(N, U, seed=1, n_shell=ns).ravel()).cuda()
+    Z = torch.from_numpy(inputs.z_profile(N, "aniso", n_shell=ns)).cuda()
     out = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
-    with api.Context(N, n, n, U=U, precision=prec, stream=stream.cuda_stream) as c:
+    with api.Context(N, n, n, U=U, precision=prec, mode=mode, n_shell=ns, stream=stream.cuda_stream) as c:
         for _ in range(args.warmup):
             api.qpfrg_rhs(c.h, 0.1, V, Z, out)
         torch.cuda.synchronize()
@@ -607,11 +616,23 @@ def run_rhs_only(args):
         b.record(stream)
         torch.cuda.synchronize()
         prof = api.qpfrg_profile(c.h)
-    ms = a.elapsed_time(b)
+        ms = a.elapsed_time(b)
+        sig_ms = None
+        if args.sigma:
+            # one evaluation of Z on every patch (chord about xi_j), after an untimed one
+            api.qpfrg_set_profiling(c.h, False)
+            zo = torch.empty(N, dtype=torch.float64, device="cuda")
+            api.qpfrg_selfenergy(c.h, 0.1, V, Z, None, None, zo)
+            a.record(stream)
+            api.qpfrg_selfenergy(c.h, 0.1, V, Z, None, None, zo)
+            b.record(stream)
+            torch.cuda.synchronize()
+            sig_ms = a.elapsed_time(b)
     print(json.dumps({"mode": "rhs_only", "workload": args.workload, "precision": args.rhs_only,
                       "rhs_per_s": args.steps / (ms / 1e3), "ms_per_rhs": ms / args.steps,
                       "kernels_ms_per_rhs": {k: v[0] / args.steps for k, v in prof.items() if v[1] > 0},
-                      "launches": {k: v[1] for k, v in prof.items() if v[1] > 0}}))
+                      "launches": {k: v[1] for k, v in prof.items() if v[1] > 0},
+                      "sigma_z_ms": sig_ms}))
 
 
 def main():
@@ -631,6 +652,7 @@ def main():
     p.add_argument("--sweep-precision", default="tc", choices=["mixed", "tc", "fp64"])
     p.add_argument("--rhs-only", choices=["mixed", "tc", "fp64"],
                    help="time right-hand sides of one context only (kernel captures); prints its own line")
+    p.add_argument("--sigma", action="store_true", help="--rhs-only: also time one Z evaluation")
     args = p.parse_args()
     if args.warmup < 3 and args.impl == "qpfrg":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

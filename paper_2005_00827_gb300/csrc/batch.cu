@@ -310,8 +310,10 @@ qpfrg_status setup_group(Group &g, const qpfrg_lattice *lattice, const qpfrg_fin
     g.rows.assign(g.nslots, nullptr);
     std::vector<CUtensorMap> tmaps(g.nslots);
     for (int sl = 0; sl < g.nslots; ++sl) {
-        if ((e = cudaMalloc((void **)&g.rows[sl], c->B_bytes)) != cudaSuccess) return cuda_fail(c, e, "batch rows");
-        if ((s = make_table_map(c, &tmaps[sl], g.rows[sl], N)) != QPFRG_OK) return s;
+        if ((e = cudaMalloc((void **)&g.rows[sl], c->B_bytes)) != cudaSuccess ||
+            (e = cudaMemset(g.rows[sl], 0, c->B_bytes)) != cudaSuccess)
+            return cuda_fail(c, e, "batch rows");
+        if ((s = make_table_map(c, &tmaps[sl], g.rows[sl])) != QPFRG_OK) return s;
     }
     std::vector<int> act(g.nslots, 0);
     if (g.nsteps > 0)

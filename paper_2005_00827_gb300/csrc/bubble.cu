@@ -49,6 +49,8 @@ struct BubbleArgs {
     const int2 *img;
     // batched flows: a device flag read by every CTA; 0 = nothing to do
     const int *active;
+    // tensor-core path: the table in tiles (tc_table_index; tRT = 0: row-major)
+    long tRT, tKB;
 };
 
 // ---- scalar helpers ---------------------------------------------------------
@@ -261,7 +263,9 @@ __device__ __forceinline__ void table_row(const BubbleArgs<R> &A, const R *row, 
         const R v = row_get(row + img_src(b, off, refl, N, ns), A.finv);
         const R Zb = Zs[b];
         const R sw = TFLOW ? Za * Zb : A.g * Za * Zb * (KZa + Ks[b] * Zb);
-        A.B[(((long)fam * NN + Qi) * N + ai) * (long)N + b] = v * sw;
+        const long o = A.tRT ? tc_table_index(fam, Qi, (long)ai * N + b, A.tRT, A.tKB)
+                             : (((long)fam * NN + Qi) * N + ai) * (long)N + b;
+        A.B[o] = v * sw;
     }
 }
 
@@ -544,6 +548,10 @@ static qpfrg_status launch_r(qpfrg_ctx *c, double lambda, const double *d_Z, con
     A.K = d_K;
     A.B = reinterpret_cast<R *>(c->loop_out ? c->loop_out : c->d_B);
     A.active = c->loop_active;
+    if (c->opt.precision == QPFRG_MIXED_TC) {
+        A.tRT = c->tc.RT;
+        A.tKB = c->tc.KB;
+    }
     const bool tflow = pb.regulator == QPFRG_REG_TEMPERATURE;
     const double T = tflow ? lambda : pb.T_fixed;
     A.T = (R)T;

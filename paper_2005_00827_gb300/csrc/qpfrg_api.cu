@@ -323,6 +323,14 @@ qpfrg_status qpfrg_create(const qpfrg_lattice *lattice, int n_p, const qpfrg_fin
     const size_t rsz = c->opt.precision == QPFRG_FP64 ? sizeof(double) : sizeof(float);
     const bool tcmode = c->opt.precision == QPFRG_MIXED_TC;
     c->B_bytes = 2 * n4 * rsz;
+    if (tcmode) {
+        // tiled table of the tensor-core path (tc_table_index): padded to
+        // whole 128-row tiles and 64-wide k blocks
+        const size_t NN = N * N, RT = (NN + 127) / 128, KB = (NN + 63) / 64;
+        c->tc.RT = (long)RT;
+        c->tc.KB = (long)KB;
+        c->B_bytes = 2 * RT * KB * 128 * 64 * sizeof(float);
+    }
     if (std::getenv("QPFRG_TEST_FAIL_ALLOC")) {   // host-side fault injection for tests
         c->err = "allocation failure injected by QPFRG_TEST_FAIL_ALLOC";
         return fail(QPFRG_ERR_OOM);
@@ -348,6 +356,8 @@ qpfrg_status qpfrg_create(const qpfrg_lattice *lattice, int n_p, const qpfrg_fin
             e = cudaMemset(t.Bd[h], 0, nbd * 2);
         }
         if (e == cudaSuccess) e = cudaMemset(c->d_tc_err, 0, sizeof(unsigned));
+        // the table's pads (rows past N^2, columns past N^2 in the last block) stay zero
+        if (e == cudaSuccess) e = cudaMemset(c->d_B, 0, c->B_bytes);
         if (e != cudaSuccess) return fail(cuda_fail(c, e, "clear tensor-core operands"));
         if ((s = tc_make_maps(c)) != QPFRG_OK) return fail(s);
     }

@@ -125,6 +125,7 @@ struct TcBuffers {
     float *VT = nullptr;                          // [N][N][N]
     int Npad = 0;
     long Kp = 0, Kpd = 0;                         // N^2 up to 64 and 2 Kp (d: halves at 0 and Kp)
+    long RT = 0, KB = 0;                          // row tiles (N^2 / 128) and k blocks (Kp / 64) of the table
     CUtensorMap tmB[3][2];                        // TMA maps of the tiles: [pp, cr, d][hi, lo]
     CUtensorMap tmTab;                            // TMA map of the FP32 weighted loop-kernel table
 };
@@ -172,6 +173,15 @@ __device__ __forceinline__ int project_fp64(double kx, double ky, const Problem 
     long sh = (long)floor(__dadd_rn(xi / pb.shell_D, 0.5 * ns));
     sh = sh < 0 ? 0 : (sh > ns - 1 ? ns - 1 : sh);
     return (int)(w * ns + sh);
+}
+
+// Element offset of (family f, row Q, column k) in the tiled loop-kernel
+// table of the tensor-core path, [f][Q / 128][k / 64][(k % 64) / 32][Q % 128][k % 32]
+// with RT = ceil(N^2 / 128) row tiles and KB = ceil(N^2 / 64) k blocks per
+// family: one 128 x 32 box of the contraction is 16 KB of contiguous memory.
+__host__ __device__ inline long tc_table_index(int f, long Q, long k, long RT, long KB)
+{
+    return ((((f * RT + (Q >> 7)) * KB + (k >> 6)) * 2 + ((k >> 5) & 1)) * 128 + (Q & 127)) * 32 + (k & 31);
 }
 
 struct ProfileSlot {
@@ -333,9 +343,9 @@ struct TcPrepFlow {
 qpfrg_status launch_tc_prep_batch(qpfrg_ctx *c, const TcPrepFlow *d_flows, const int *d_status, const double *d_h_tab,
                                   int step, int nflows);
 qpfrg_status make_tile_map(qpfrg_ctx *c, CUtensorMap *map, const void *base, long elems, int box_rows);
-// TMA map of a weighted loop-kernel table [2][N^2][N^2] (FP32): boxes of
-// 128 rows x 32 columns, 128-byte swizzle
-qpfrg_status make_table_map(qpfrg_ctx *c, CUtensorMap *map, const float *table, int N);
+// TMA map of a tiled weighted loop-kernel table (tc_table_index, FP32):
+// rows of 32 floats, boxes of 128 rows, 128-byte swizzle
+qpfrg_status make_table_map(qpfrg_ctx *c, CUtensorMap *map, const float *table);
 // Batched flows (batch.cu): grid.z runs over the flows of a patch-count group;
 // each flow brings its table slot, stage vertex, output and B tensor maps,
 // and is skipped (uniformly, before any barrier) when it is not running or

@@ -15,9 +15,11 @@
 //   d : Q = (i,l), out row (i,l),  A[Q][(a,b)] = B_ph[Q][a][b] (2V[i,a,l] - V[a,i,l]),
 //                                  A[Q][Kp + (a,b)] = -B_ph[Q][a][b] V[i,a,l]
 //
-// Per 64-wide k block and stage: one thread (warp 4) loads the raw FP32 table
-// block (128 rows x 64 columns, two TMA boxes of 32 columns with 128-byte
-// swizzle) and the B blocks (pre-formed per stage by tc_prep_kernel); the
+// The table of the tensor-core path is stored in tiles (tc_table_index:
+// [f][row tile][k block][half][128 rows][32 floats]), so a 128 x 64 block is
+// two contiguous 16 KB boxes.  Per 64-wide k block and stage: one thread
+// (warp 4) loads the raw FP32 block (two TMA boxes, 128-byte swizzle) and the
+// B blocks (pre-formed per stage by tc_prep_kernel); the
 // producer warps 0-3 (one A row per thread) read their rows, scale by the
 // vertex factor and overwrite them, in place, with BF16 hi and lo in the
 // K-major no-swizzle order of the MMA descriptors.  The A layout puts each
@@ -76,6 +78,7 @@ struct TcFusedArgs {
     int M, Ncol, Npad, N;             // valid rows, valid columns, padded columns, patches
     int nkb_total, kb_per_split;      // 64-wide k blocks of the padded reduction; per CTA along grid.y
     int nkb_half;                     // k blocks per half of the d reduction (Kp / 64)
+    long RT, KB;                      // row tiles and k blocks per family of the tiled table
     int ch;                           // 0 pp, 1 cr, 2 d
     const float *Vf, *VT;             // stage vertex [k1][k2][k3] and VT[j][l][b] = V[b][j][l]
     double *out;
@@ -279,15 +282,16 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         }
     } else if (tid == 128 && nkb > 0) {
         // ---- table and B copies, MMAs ----
-        const int ytab = fam * NN + m0;
+        const long tile0 = ((long)fam * A.RT + blockIdx.x) * A.KB;   // first k block of this row tile
         auto issue = [&](int kb, int s) {
             const uint32_t sb = base + (uint32_t)s * stage_bytes;
             const bool second = A.ch == 2 && kb >= A.nkb_half;
-            const int kk0 = (kb - (second ? A.nkb_half : 0)) * BK;
+            const int kbl = kb - (second ? A.nkb_half : 0);           // k block within the table row
+            const int y = (int)((tile0 + kbl) * 256);                 // two halves of 128 rows of 32 floats
             const uint32_t rb = smem_u32(&rfull[s]);
             mbar_expect_tx(rb, kRawBytes + 2 * b_bytes);
-            tma_load_2d(sb, mtab, kk0, ytab, rb);
-            tma_load_2d(sb + kRawBytes / 2, mtab, kk0 + 32, ytab, rb);
+            tma_load_2d(sb, mtab, 0, y, rb);
+            tma_load_2d(sb + kRawBytes / 2, mtab, 0, y + 128, rb);
             const int yb = kb * (Npad / 2);
             tma_load_2d(sb + kRawBytes, mhi, 0, yb, rb);
             tma_load_2d(sb + kRawBytes + b_bytes, mlo, 0, yb, rb);
@@ -433,6 +437,8 @@ static qpfrg_status launch_fused(qpfrg_ctx *c, int ch, TcFusedArgs &A, int nz, i
     A.nkb_total = nkb;
     A.kb_per_split = kb_per;
     A.nkb_half = (int)(t.Kp / tc::BK);
+    A.RT = t.RT;
+    A.KB = t.KB;
     A.ch = ch;
     A.err = c->d_tc_err;
     A.test_wait = std::getenv("QPFRG_TEST_TC_WAIT") ? 10000000LL : 0;   // ~5 ms

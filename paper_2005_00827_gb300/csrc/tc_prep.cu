@@ -154,15 +154,14 @@ static PFN_cuTensorMapEncodeTiled_v12000 map_encoder(qpfrg_ctx *c)
     return encode;
 }
 
-qpfrg_status make_table_map(qpfrg_ctx *c, CUtensorMap *map, const float *table, int N)
+qpfrg_status make_table_map(qpfrg_ctx *c, CUtensorMap *map, const float *table)
 {
     const auto encode = map_encoder(c);
     if (!encode) return QPFRG_ERR_CUDA;
-    const cuuint64_t NN = (cuuint64_t)N * N;
-    // rows of N^2 floats (a multiple of 16 bytes for even N); columns past
-    // N^2 and rows past the two families read as zeros
-    const cuuint64_t dims[2] = {NN, 2 * NN};
-    const cuuint64_t strides[1] = {NN * sizeof(float)};
+    // the tiled table as rows of 32 floats: 2 families x RT x KB x 2 halves x 128
+    const cuuint64_t rows = 2ull * (cuuint64_t)c->tc.RT * (cuuint64_t)c->tc.KB * 256ull;
+    const cuuint64_t dims[2] = {32, rows};
+    const cuuint64_t strides[1] = {32 * sizeof(float)};
     const cuuint32_t box[2] = {32, 128};
     const cuuint32_t estr[2] = {1, 1};
     const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(table), dims, strides, box,
@@ -204,7 +203,7 @@ qpfrg_status tc_make_maps(qpfrg_ctx *c)
             break;
         s = make_tile_map(c, &t.tmB[2][h], t.Bd[h], nbd, t.Npad / 2);
     }
-    if (s == QPFRG_OK) s = make_table_map(c, &t.tmTab, reinterpret_cast<const float *>(c->d_B), c->pb.N);
+    if (s == QPFRG_OK) s = make_table_map(c, &t.tmTab, reinterpret_cast<const float *>(c->d_B));
     return s;
 }
 
