@@ -52,9 +52,12 @@ UNIT = "RHS/s"
 # 128 issue lanes per SM per clock, MUFU alone runs 16 per SM per clock.
 BUBBLE_FP32_PER_EVAL, BUBBLE_MUFU_PER_EVAL = 14, 2
 SIGMA_FP32_PER_PAIR, SIGMA_MUFU_PER_PAIR = 20, 4
-# issue slots of the formulas as built (instructions per unit; a packed FP32x2
-# instruction counts one half per unit): the issue efficiency of the kernels
-BUBBLE_ISSUE_AS_BUILT, SIGMA_ISSUE_AS_BUILT = 21, 36
+# issue slots per unit as built: the self-energy's per-pair formula (a packed
+# FP32x2 instruction counts one half per pair); the loop kernels' measured
+# instructions per computed evaluation, the write-out of the C4v image rows
+# included (ncu smsp__inst_executed x 32 / evaluations at np96_n32:
+# 5.71e8 x 32 / 2.27e8)
+BUBBLE_ISSUE_AS_BUILT, SIGMA_ISSUE_AS_BUILT = 80, 36
 ISSUE_LANES_PER_SM, MUFU_PER_SM, N_SM = 128, 16, 152
 
 
@@ -408,6 +411,9 @@ def run_qpfrg(args):
     if not args.no_sweep:
         # the 128-flow phase-boundary sweep through one qpfrg_flow_batch call
         line["sweep128"] = sweep128(api, inputs, stream, args)
+    if not args.no_shell:
+        # energy-shell patching, 32 x 7 = 224 patches
+        line["shell224"] = shell224(api, inputs, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_seconds)
         line["cpu_baseline_all_cores"] = cpu_baseline(args.workload, budget_s=args.cpu_seconds,
@@ -507,6 +513,49 @@ def sweep128(api, inputs, stream, args):
             "flow_steps": steps, "rhs_per_s": 4.0 * steps / (ms / 1e3), "statuses": status,
             "precision": args.sweep_precision, "fine_grid": "16x16", "N_p": "24/48/72/96",
             "flow": "T-flow from T=1 to T_end or |V|>20, dlnT=ln0.98, Z=1"}
+
+
+def shell224(api, inputs, stream):
+    """Energy-shell patching (32 angular sections x 7 shells = 224 patches,
+    8 x 8 fine points per patch, tensor-core precision): right-hand sides/s,
+    one Z evaluation (C4v-irreducible targets) and Z-feedback flow steps/s,
+    all by CUDA events on the caller's stream."""
+    import torch
+    wl = inputs.WORKLOADS["np224_s7"]
+    N, n, U, ns = wl["N"], wl["n"], wl["U"], wl["n_shell"]
+    kw = dict(U=U, lambda0=1.0, precision=api.QPFRG_MIXED_TC, mode=api.QPFRG_GRID_SHELL, n_shell=ns,
+              lambda_end=wl["T_end"], z_feedback=1, eta=0.02, stream=stream.cuda_stream)
+    V = torch.from_numpy(inputs.random_vertex(N, U, seed=1, n_shell=ns).ravel()).cuda()
+    Z = torch.from_numpy(inputs.z_profile(N, "aniso", n_shell=ns)).cuda()
+    out, zo = torch.empty(N ** 3, dtype=torch.float64, device="cuda"), torch.empty(N, dtype=torch.float64,
+                                                                                   device="cuda")
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {"workload": "np224_s7", "N_p": N, "shells": ns, "fine_grid": f"{n}x{n} per patch",
+           "precision": "tc"}
+    with api.Context(N, n, n, **kw) as c:
+        api.qpfrg_rhs(c.h, 0.1, V, Z, out)
+        api.qpfrg_selfenergy(c.h, 0.1, V, Z, None, None, zo)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(3):
+            api.qpfrg_rhs(c.h, 0.1, V, Z, out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        res["rhs_per_s"] = 3 / (a.elapsed_time(b) / 1e3)
+        a.record(stream)
+        api.qpfrg_selfenergy(c.h, 0.1, V, Z, None, None, zo)
+        b.record(stream)
+        torch.cuda.synchronize()
+        res["sigma_z_ms_all_patches"] = a.elapsed_time(b)
+        api.qpfrg_step(c.h, 1)
+        torch.cuda.synchronize()
+        a.record(stream)
+        api.qpfrg_step(c.h, 3)
+        b.record(stream)
+        torch.cuda.synchronize()
+        res["flow_steps_per_s"] = 3 / (a.elapsed_time(b) / 1e3)
+        res["flow_rhs_per_s"] = 4 * res["flow_steps_per_s"]
+    return res
 
 
 def run_sweep(args):
@@ -650,6 +699,7 @@ def main():
     p.add_argument("--no-autotune", action="store_true", help="built-in launch shapes instead of qpfrg_autotune")
     p.add_argument("--no-sweep", action="store_true", help="skip the 128-flow sweep summary of the default line")
     p.add_argument("--sweep-precision", default="tc", choices=["mixed", "tc", "fp64"])
+    p.add_argument("--no-shell", action="store_true", help="skip the energy-shell summary of the default line")
     p.add_argument("--rhs-only", choices=["mixed", "tc", "fp64"],
                    help="time right-hand sides of one context only (kernel captures); prints its own line")
     p.add_argument("--sigma", action="store_true", help="--rhs-only: also time one Z evaluation")

@@ -249,7 +249,7 @@ qpfrg_status setup_group(Group &g, const qpfrg_lattice *lattice, const qpfrg_fin
     const size_t bper = 2 * (2 * nb + nbd);
     if ((s = galloc(g, &V, F * n3, "batch V")) || (s = galloc(g, &k, F * n3, "batch k")) ||
         (s = galloc(g, &acc, F * n3, "batch acc")) || (s = galloc(g, &Vf, F * n3, "batch V fp32")) ||
-        (s = galloc(g, &VT, F * n3, "batch V^T")) || (s = galloc(g, &B, F * bper, "batch operands")))
+        (s = galloc(g, &VT, F * 3 * n3, "batch row-factor tables")) || (s = galloc(g, &B, F * bper, "batch operands")))
         return s;
     if ((e = cudaMemsetAsync(k, 0, F * n3 * sizeof(double), g.stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(B, 0, F * bper * sizeof(__nv_bfloat16), g.stream)) != cudaSuccess)
@@ -273,10 +273,10 @@ qpfrg_status setup_group(Group &g, const qpfrg_lattice *lattice, const qpfrg_fin
         pk[i] = k + i * n3;
         pacc[i] = acc + i * n3;
         pVf[i] = Vf + i * n3;
-        pVT[i] = VT + i * n3;
+        pVT[i] = VT + i * 3 * n3;
         __nv_bfloat16 *bb = B + i * bper;
         pf[i].Vf = Vf + i * n3;
-        pf[i].VT = VT + i * n3;
+        pf[i].VT = VT + i * 3 * n3;
         pf[i].B[0][0] = bb;
         pf[i].B[0][1] = bb + nb;
         pf[i].B[1][0] = bb + 2 * nb;

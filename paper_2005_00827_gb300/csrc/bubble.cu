@@ -259,13 +259,17 @@ __device__ __forceinline__ void table_row(const BubbleArgs<R> &A, const R *row, 
     const int off = (g & 3) * (N / ns / 4);
     const bool refl = (g & 4) != 0;
     const R Za = Zs[ai], KZa = Ks[ai] * Za;
+    // column b goes to k = ai N + b of row Qi: row-major at base + k, tiled
+    // (tc_table_index) at base + (k / 32) 4096 + k % 32
+    const int k0 = ai * N;
+    R *dst = A.B + (A.tRT ? ((long)fam * A.tRT + (Qi >> 7)) * A.tKB * 8192 + (Qi & 127) * 32
+                          : ((long)fam * NN + Qi) * NN);
     for (int b = lane; b < N; b += 32) {
         const R v = row_get(row + img_src(b, off, refl, N, ns), A.finv);
         const R Zb = Zs[b];
         const R sw = TFLOW ? Za * Zb : A.g * Za * Zb * (KZa + Ks[b] * Zb);
-        const long o = A.tRT ? tc_table_index(fam, Qi, (long)ai * N + b, A.tRT, A.tKB)
-                             : (((long)fam * NN + Qi) * N + ai) * (long)N + b;
-        A.B[o] = v * sw;
+        const int k = k0 + b;
+        dst[A.tRT ? ((long)(k >> 5) << 12) + (k & 31) : (long)k] = v * sw;
     }
 }
 

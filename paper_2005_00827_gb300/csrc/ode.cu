@@ -73,22 +73,23 @@ __global__ void check_finite_kernel(const double *__restrict__ x, long n, unsign
 }
 
 // C4v test of a state image: red[4] is set when an element's image under one
-// of the 7 non-trivial group elements j -> +-j + m N/4 (N a multiple of 4)
-// differs from it by more than tol max|V| (tol max|Z| for Z); red[0] and red[2]
-// hold max|V| and max|Z| (bits) from check_finite_kernel.
-__global__ void state_c4v_kernel(const double *__restrict__ V, const double *__restrict__ Z, int N, double tol,
-                                 unsigned long long *red)
+// of the 7 non-trivial group elements (wedge w -> +-w + m N_a/4 of patch
+// j = w ns + s, the shell s kept; N_a = N / ns a multiple of 4) differs from
+// it by more than tol max|V| (tol max|Z| for Z); red[0] and red[2] hold max|V|
+// and max|Z| (bits) from check_finite_kernel.
+__global__ void state_c4v_kernel(const double *__restrict__ V, const double *__restrict__ Z, int N, int ns,
+                                 double tol, unsigned long long *red)
 {
     const double tv = tol * __longlong_as_double(red[0]), tz = tol * __longlong_as_double(red[2]);
     const long NN = (long)N * N, n3 = NN * N;
-    const int q = N / 4;
+    const int Na = N / ns, q = Na / 4;
     unsigned bad = 0;
     for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n3; idx += (long)gridDim.x * blockDim.x) {
         const int i = (int)(idx / NN), j = (int)((idx / N) % N), l = (int)(idx % N);
         const double v = V[idx];
         for (int g = 1; g < 8; ++g) {
             const int m = g & 3, sg = g < 4 ? 1 : -1;
-            auto img = [&](int x) { return ((sg * x + m * q) % N + N) % N; };
+            auto img = [&](int x) { return ((sg * (x / ns) + m * q) % Na + Na) % Na * ns + x % ns; };
             if (fabs(V[((long)img(i) * N + img(j)) * N + img(l)] - v) > tv) bad = 1;
             if (idx < N && fabs(Z[img((int)idx)] - Z[idx]) > tz) bad = 1;
         }
@@ -133,7 +134,8 @@ qpfrg_status launch_state_check(qpfrg_ctx *c, const double *d_V, const double *d
     if (e != cudaSuccess) return cuda_fail(c, e, "memset state check");
     check_finite_kernel<<<grid_for(n), 256, 0, c->stream>>>(d_V, n, c->d_red);
     check_finite_kernel<<<1, 256, 0, c->stream>>>(d_Z, c->pb.N, c->d_red + 2);
-    if (c4v_test) state_c4v_kernel<<<grid_for(n), 256, 0, c->stream>>>(d_V, d_Z, c->pb.N, tol, c->d_red);
+    if (c4v_test)
+        state_c4v_kernel<<<grid_for(n), 256, 0, c->stream>>>(d_V, d_Z, c->pb.N, c->pb.n_shell, tol, c->d_red);
     e = cudaGetLastError();
     return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "state check kernels");
 }

@@ -347,7 +347,7 @@ qpfrg_status qpfrg_create(const qpfrg_lattice *lattice, int n_p, const qpfrg_fin
             if ((s = dev_alloc(c, &t.Bpp[h], nb, "pp operand")) || (s = dev_alloc(c, &t.Bcr[h], nb, "cr operand")) ||
                 (s = dev_alloc(c, &t.Bd[h], nbd, "d operand")))
                 return fail(s);
-        if ((s = dev_alloc(c, &t.VT, n3, "V transpose")) || (s = dev_alloc(c, &c->d_tc_err, 1, "tc error flag")))
+        if ((s = dev_alloc(c, &t.VT, 3 * n3, "row-factor tables")) || (s = dev_alloc(c, &c->d_tc_err, 1, "tc error flag")))
             return fail(s);
         // tile pads (rows past N, k past the reduction length) stay zero
         for (int h = 0; h < 2 && e == cudaSuccess; ++h) {
@@ -371,33 +371,39 @@ qpfrg_status qpfrg_create(const qpfrg_lattice *lattice, int n_p, const qpfrg_fin
     if (e != cudaSuccess) return fail(cuda_fail(c, e, "cudaMallocHost"));
     if (c->opt.sigma_ode && (s = gflow_alloc(c)) != QPFRG_OK) return fail(s);
 
-    // C4v-irreducible patches 0..floor(N/8) and each patch's representative
-    if (pb.mode == QPFRG_GRID_WEDGE) {
-        const int q = (int)N / 4;
+    // C4v-irreducible patches (wedges 0..floor(N_a/8), every shell) and each
+    // patch's representative (its index in the irreducible list)
+    if (pb.mode == QPFRG_GRID_WEDGE || pb.mode == QPFRG_GRID_SHELL) {
+        const int ns = pb.n_shell, Na = (int)N / ns, q = Na / 4;
         std::vector<int> jirr, rep(N);
-        for (int j = 0; 8 * j <= (int)N; ++j) jirr.push_back(j);
+        for (int w = 0; 8 * w <= Na; ++w)
+            for (int sh = 0; sh < ns; ++sh) jirr.push_back(w * ns + sh);
         for (int j = 0; j < (int)N; ++j) {
-            int r = j % q;
+            int r = (j / ns) % q;
             if (2 * r > q) r = q - r;
-            rep[j] = r;
+            rep[j] = r * ns + j % ns;
         }
         c->n_irr = (int)jirr.size();
-        // frequency grid: zone-edge patches j = m N/4 get slots of their own
-        std::vector<int> jgrid(jirr), repgrid(rep);
-        for (int m = 1; m < 4; ++m) {
-            repgrid[m * q] = (int)jgrid.size();
-            jgrid.push_back(m * q);
-        }
-        c->n_grid = (int)jgrid.size();
         if ((s = dev_alloc(c, &c->d_jirr, jirr.size(), "irreducible patches")) ||
-            (s = dev_alloc(c, &c->d_rep, N, "representatives")) ||
-            (s = dev_alloc(c, &c->d_jgrid, jgrid.size(), "grid targets")) ||
-            (s = dev_alloc(c, &c->d_repgrid, N, "grid representatives")))
+            (s = dev_alloc(c, &c->d_rep, N, "representatives")))
             return fail(s);
         cudaMemcpy(c->d_jirr, jirr.data(), jirr.size() * sizeof(int), cudaMemcpyHostToDevice);
         cudaMemcpy(c->d_rep, rep.data(), N * sizeof(int), cudaMemcpyHostToDevice);
-        cudaMemcpy(c->d_jgrid, jgrid.data(), jgrid.size() * sizeof(int), cudaMemcpyHostToDevice);
-        cudaMemcpy(c->d_repgrid, repgrid.data(), N * sizeof(int), cudaMemcpyHostToDevice);
+        if (pb.mode == QPFRG_GRID_WEDGE) {
+            // frequency grid of the wedge kernels: zone-edge patches j = m N/4
+            // get slots of their own
+            std::vector<int> jgrid(jirr), repgrid(rep);
+            for (int m = 1; m < 4; ++m) {
+                repgrid[m * q] = (int)jgrid.size();
+                jgrid.push_back(m * q);
+            }
+            c->n_grid = (int)jgrid.size();
+            if ((s = dev_alloc(c, &c->d_jgrid, jgrid.size(), "grid targets")) ||
+                (s = dev_alloc(c, &c->d_repgrid, N, "grid representatives")))
+                return fail(s);
+            cudaMemcpy(c->d_jgrid, jgrid.data(), jgrid.size() * sizeof(int), cudaMemcpyHostToDevice);
+            cudaMemcpy(c->d_repgrid, repgrid.data(), N * sizeof(int), cudaMemcpyHostToDevice);
+        }
     }
 
     // state: V = U, Z = 1 at lambda0
@@ -410,7 +416,7 @@ qpfrg_status qpfrg_create(const qpfrg_lattice *lattice, int n_p, const qpfrg_fin
     if (e != cudaSuccess) return fail(cuda_fail(c, e, "init Z"));
     c->lambda = lambda0;
     c->lambda_end = c->opt.lambda_end;
-    c->c4v_state = pb.mode == QPFRG_GRID_WEDGE;
+    c->c4v_state = pb.mode == QPFRG_GRID_WEDGE || pb.mode == QPFRG_GRID_SHELL;
     c->steps = 0;
     c->status = QPFRG_FLOW_RUNNING;
     c->max_abs_v = std::fabs(U);
@@ -684,7 +690,7 @@ static qpfrg_status make_child(qpfrg_ctx *parent, double U, double lambda0, doub
     c->max_abs_v = std::fabs(U);
     c->lambda_c = 0.0;
     c->pending = false;
-    c->c4v_state = c->pb.mode == QPFRG_GRID_WEDGE;
+    c->c4v_state = c->pb.mode == QPFRG_GRID_WEDGE || c->pb.mode == QPFRG_GRID_SHELL;
     *out = c;
     return QPFRG_OK;
 }
@@ -844,7 +850,7 @@ qpfrg_status qpfrg_set_state(qpfrg_t c, const void *h_buf, size_t bytes)
     // V and Z to the rounding level of the precision that produced them (a
     // mixed-precision flow keeps it only to FP32 rounding).  A rejected image
     // leaves the state untouched.
-    const bool wedge = c->pb.mode == QPFRG_GRID_WEDGE;
+    const bool wedge = c->pb.mode == QPFRG_GRID_WEDGE || c->pb.mode == QPFRG_GRID_SHELL;
     const double tol = c->opt.precision == QPFRG_FP64 ? 1e-12 : 1e-5;
     cudaError_t e = cudaMemcpyAsync(c->d_k, V, n3_of(c) * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)

@@ -122,7 +122,7 @@ struct TcBuffers {
     __nv_bfloat16 *Bpp[2] = {nullptr, nullptr};   // [Npad][Kp]
     __nv_bfloat16 *Bcr[2] = {nullptr, nullptr};   // [Npad][Kp]
     __nv_bfloat16 *Bd[2] = {nullptr, nullptr};    // [Npad][Kpd]
-    float *VT = nullptr;                          // [N][N][N]
+    float *VT = nullptr;                          // row-factor tables [3][N^2][N] (tc_prep)
     int Npad = 0;
     long Kp = 0, Kpd = 0;                         // N^2 up to 64 and 2 Kp (d: halves at 0 and Kp)
     long RT = 0, KB = 0;                          // row tiles (N^2 / 128) and k blocks (Kp / 64) of the table
@@ -130,17 +130,16 @@ struct TcBuffers {
     CUtensorMap tmTab;                            // TMA map of the FP32 weighted loop-kernel table
 };
 
-// Element offset of (row r, reduction index k) in the tile layout of an
-// operand with `rows` rows per tile (128 for A, Npad for B) and reduction
-// length Kp (a multiple of 64): tiles ordered (row tile, k tile), each tile
-// in the canonical K-major no-swizzle order of the tcgen05 descriptors (core
-// matrices of 8 rows x 8 elements; K-adjacent core matrices rows/8 apart).
+// Element offset of (row r, reduction index k) in the tile layout of a BF16
+// operand with `rows` rows per tile (Npad for B) and reduction length Kp (a
+// multiple of 64): tiles ordered (row tile, k tile), each tile in the K-major
+// 128-byte-swizzle order of the tcgen05 descriptors: row rr's 64 elements
+// (128 B) at rr * 64, its 8-element chunk c stored at chunk c ^ (rr % 8).
 __host__ __device__ inline long tile_index(long r, long k, int rows, long Kp)
 {
     const long rt = r / rows, rr = r - rt * rows;
     const long kt = k >> 6, kk = k & 63;
-    return (rt * (Kp >> 6) + kt) * (long)rows * 64 + ((((kk >> 3) * (rows >> 3) + (rr >> 3)) << 6) | ((rr & 7) << 3) |
-                                                      (kk & 7));
+    return (rt * (Kp >> 6) + kt) * (long)rows * 64 + rr * 64 + ((((kk >> 3) ^ (rr & 7)) << 3) | (kk & 7));
 }
 
 // FP64 projection of a momentum onto its patch.  Lattice: nearest lattice
@@ -337,7 +336,7 @@ qpfrg_status gflow_enqueue_stages(qpfrg_ctx *c, double x, double h);
 // Per-flow vertex operands of the batched tensor-core contraction (batch.cu)
 struct TcPrepFlow {
     const float *Vf;             // stage vertex (FP32)
-    float *VT;                   // VT[j][l][b] = V[b][j][l]
+    float *VT;                   // row-factor tables of cr and d, [3][N^2][N]
     __nv_bfloat16 *B[3][2];      // B operands of pp, cr, d: hi, lo (tiles)
 };
 qpfrg_status launch_tc_prep_batch(qpfrg_ctx *c, const TcPrepFlow *d_flows, const int *d_status, const double *d_h_tab,

@@ -1290,21 +1290,22 @@ qpfrg_status launch_sigma_z(qpfrg_ctx *c, double T, const double *d_V, const dou
     return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "z_update_kernel");
 }
 
-// Whether (V, Z) keep the C4v symmetry of the wedge patches: flag set when an
-// image V(g k1, g k2, g k3) or Z(g k) differs from the original by more than
-// tol (1 + |v|), g running over the rotations j -> j + m N/4 and the
-// reflections j -> -j + m N/4 of the patch index.
-__global__ void c4v_check_kernel(const double *V, const double *Z, int N, double tol, unsigned long long *flag)
+// Whether (V, Z) keep the C4v symmetry of the angular patches: flag set when
+// an image V(g k1, g k2, g k3) or Z(g k) differs from the original by more
+// than tol (1 + |v|), g running over the rotations w -> w + m N_a/4 and the
+// reflections w -> -w + m N_a/4 of the wedge w of patch j = w ns + s.
+__global__ void c4v_check_kernel(const double *V, const double *Z, int N, int ns, double tol,
+                                 unsigned long long *flag)
 {
     const long NN = (long)N * N, n3 = NN * N;
-    const int q = N / 4;
+    const int Na = N / ns, q = Na / 4;
     for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < n3; idx += (long)gridDim.x * blockDim.x) {
         const int i = (int)(idx / NN), j = (int)((idx / N) % N), l = (int)(idx % N);
         const double v = V[idx];
         bool bad = false;
         for (int g = 1; g < 8; ++g) {
             const int m = g & 3, sg = g < 4 ? 1 : -1;
-            auto img = [&](int x) { return ((sg * x + m * q) % N + N) % N; };
+            auto img = [&](int x) { return ((sg * (x / ns) + m * q) % Na + Na) % Na * ns + x % ns; };
             const double w = V[((long)img(i) * N + img(j)) * N + img(l)];
             bad = bad || fabs(w - v) > tol * (1.0 + fabs(v));
             if (idx < N && Z) bad = bad || fabs(Z[img((int)idx)] - Z[idx]) > tol * (1.0 + fabs(Z[idx]));
@@ -1316,12 +1317,12 @@ __global__ void c4v_check_kernel(const double *V, const double *Z, int N, double
 static qpfrg_status c4v_check(qpfrg_ctx *c, const double *d_V, const double *d_Z, bool &sym)
 {
     sym = false;
-    const int N = c->pb.N;
-    if (N % 4 != 0) return QPFRG_OK;
+    const int N = c->pb.N, ns = c->pb.n_shell;
+    if ((N / ns) % 4 != 0) return QPFRG_OK;
     cudaError_t e = cudaMemsetAsync(c->d_red, 0, sizeof(unsigned long long), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "memset symmetry flag");
     const long n3 = (long)N * N * N;
-    c4v_check_kernel<<<(int)std::min<long>((n3 + 255) / 256, 152L * 8), 256, 0, c->stream>>>(d_V, d_Z, N, 1e-5,
+    c4v_check_kernel<<<(int)std::min<long>((n3 + 255) / 256, 152L * 8), 256, 0, c->stream>>>(d_V, d_Z, N, ns, 1e-5,
                                                                                             c->d_red);
     unsigned long long flag = 1;
     if ((e = cudaGetLastError()) != cudaSuccess ||

@@ -22,15 +22,13 @@
 // B blocks (pre-formed per stage by tc_prep_kernel); the
 // producer warps 0-3 (one A row per thread) read their rows, scale by the
 // vertex factor and overwrite them, in place, with BF16 hi and lo in the
-// K-major no-swizzle order of the MMA descriptors.  The A layout puts each
-// 8-row group's 64 k contiguously (8-row groups 1024 B apart, K-adjacent core
-// matrices 128 B apart), so a warp's 32 rows of hi occupy exactly the bytes
-// of its 32 raw rows of columns 0-31 and its lo those of columns 32-63: a
-// warp converts its rows with no barrier beyond its own lanes.  The thread of
-// warp 4 then issues the MMAs and commits each block to the stage's "empty"
-// mbarrier, after which the stage is refilled.  Every wait is bounded by a
-// clock budget and aborts the CTA (error flag, bounded drain, tensor memory
-// freed).
+// K-major 128-byte-swizzle layout of the MMA descriptors (both operands): a
+// row of 64 BF16 is 128 bytes, so row r of A_hi occupies exactly the bytes of
+// raw row r of columns 0-31 and row r of A_lo those of columns 32-63 -- each
+// thread overwrites only what it has read itself.  The thread of warp 4 then
+// issues the MMAs and commits each block to the stage's "empty" mbarrier,
+// after which the stage is refilled.  Every wait is bounded by a clock budget
+// and aborts the CTA (error flag, bounded drain, tensor memory freed).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -80,7 +78,8 @@ struct TcFusedArgs {
     int nkb_half;                     // k blocks per half of the d reduction (Kp / 64)
     long RT, KB;                      // row tiles and k blocks per family of the tiled table
     int ch;                           // 0 pp, 1 cr, 2 d
-    const float *Vf, *VT;             // stage vertex [k1][k2][k3] and VT[j][l][b] = V[b][j][l]
+    const float *Vf, *VT;             // stage vertex [k1][k2][k3]; factor tables of cr and d (tc_prep)
+    int fw;                           // row stride of the staged factor rows (odd), 0: not staged
     double *out;
     double scale;
     unsigned *err;
@@ -90,69 +89,33 @@ struct TcFusedArgs {
     long long test_wait;
 };
 
-// Vertex factors of row Q for the 64 columns of a k block starting at kk0
-// (within the table row).  N8: N % 8 == 0, so every 8-column chunk lies
-// within one first loop patch a and no chunk passes N^2.
-template <bool N8>
-__device__ __forceinline__ void row_factors(const TcFusedArgs &A, const float *Vf, const float *VT, int Q, bool valid,
-                                            int kk0, bool second, float (&f)[64])
+// The vertex factor of A row Q at column k = (a, b) is a row of a factor
+// table F[Q][x] (tc_prep_kernel): x = a for pp (F = V itself, Q = (i,j)) and d
+// (F1 = 2V[i,a,l] - V[a,i,l] for the first half of the reduction, F2 =
+// -V[i,a,l] for the second, Q = (i,l)), x = b for cr (V[b,j,l], Q = (l,j)).
+// Each CTA needs the x range its k blocks touch, per half: seg_lo[h] and
+// seg_n[h] (seg_n = 0 when the CTA has no block in half h).
+__host__ __device__ inline void factor_segments(int ch, int N, int kb0, int kb1, int nkb_half, int (&lo)[2],
+                                                int (&n)[2])
 {
-    const int N = A.N;
     const int NN = N * N;
-    if (!valid) {
-#pragma unroll
-        for (int e = 0; e < 64; ++e) f[e] = 0.f;
-        return;
-    }
-    const int qa = Q / N, qb = Q - qa * N;
-    if (N8) {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int k = kk0 + 8 * c, a = k / N, b = k - a * N;
-            if (A.ch == 1) {
-                // row (j,l) = (qb, qa): V[b][j][l] = VT[((j N + l) N + b]
-                const float4 *vt = reinterpret_cast<const float4 *>(VT + ((long)qb * N + qa) * N + b);
-                const float4 c0 = __ldg(vt), c1 = __ldg(vt + 1);
-                f[8 * c + 0] = c0.x; f[8 * c + 1] = c0.y; f[8 * c + 2] = c0.z; f[8 * c + 3] = c0.w;
-                f[8 * c + 4] = c1.x; f[8 * c + 5] = c1.y; f[8 * c + 6] = c1.z; f[8 * c + 7] = c1.w;
-            } else {
-                float fac;
-                if (A.ch == 0) {
-                    fac = __ldg(Vf + (long)Q * N + a);
-                } else {
-                    // Q = (i,l) = (qa, qb)
-                    const float v_ial = __ldg(Vf + ((long)qa * N + a) * N + qb);
-                    fac = second ? -v_ial : 2.f * v_ial - __ldg(Vf + ((long)a * N + qa) * N + qb);
-                }
-#pragma unroll
-                for (int e = 0; e < 8; ++e) f[8 * c + e] = fac;
-            }
+    for (int h = 0; h < 2; ++h) {
+        const int s0 = h == 0 ? kb0 : (kb0 > nkb_half ? kb0 : nkb_half) - nkb_half;
+        const int s1 = h == 0 ? (ch == 2 ? (kb1 < nkb_half ? kb1 : nkb_half) : kb1) : (ch == 2 ? kb1 - nkb_half : 0);
+        lo[h] = 0;
+        n[h] = 0;
+        if (s1 <= s0) continue;
+        if (ch == 1) {
+            n[h] = N;    // every b
+            continue;
         }
-    } else {
-        int a = kk0 / N, b = kk0 - (kk0 / N) * N;
-#pragma unroll
-        for (int e = 0; e < 64; ++e) {
-            float fac = 0.f;
-            if (kk0 + e < NN) {
-                if (A.ch == 0) {
-                    fac = __ldg(Vf + (long)Q * N + a);
-                } else if (A.ch == 1) {
-                    fac = __ldg(VT + ((long)qb * N + qa) * N + b);
-                } else {
-                    const float v_ial = __ldg(Vf + ((long)qa * N + a) * N + qb);
-                    fac = second ? -v_ial : 2.f * v_ial - __ldg(Vf + ((long)a * N + qa) * N + qb);
-                }
-            }
-            f[e] = fac;
-            if (++b == N) {
-                b = 0;
-                ++a;
-            }
-        }
+        const int k_first = s0 * 64, k_last = (s1 * 64 < NN ? s1 * 64 : NN) - 1;
+        lo[h] = k_first / N;
+        n[h] = k_last / N - lo[h] + 1;
     }
 }
 
-template <int S, bool N8>
+template <int S, bool N8, bool STG>
 __global__ void __launch_bounds__(kFusedThreads, 1)
     tc_fused_kernel(const __grid_constant__ CUtensorMap mTab, const __grid_constant__ CUtensorMap mBhi,
                     const __grid_constant__ CUtensorMap mBlo, TcFusedArgs A)
@@ -225,18 +188,39 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         const int rr = tid;
         const int Q = m0 + rr;
         const bool valid = Q < A.M;
-        // raw row rr of the half h, 16-byte chunk c: rr 128 + (c ^ (rr % 8)) 16
-        // (128-byte swizzle); A row rr, k chunk kc: (rr / 8) 1024 + kc 128 + (rr % 8) 16
+        // raw row rr of the half h (columns 32 h .. 32 h + 31), 16-byte chunk c:
+        // h 16 KB + rr 128 + (c ^ (rr % 8)) 16 (128-byte swizzle); A_hi row rr,
+        // 8-wide k chunk kc: rr 128 + (kc ^ (rr % 8)) 16, A_lo the same + 16 KB
+        // (the 128-byte-swizzled K-major layout of the MMA): the thread's
+        // converted row occupies exactly its own raw row's bytes
         const uint32_t raw_row = (uint32_t)rr * 128, sw = (uint32_t)(rr & 7);
-        const uint32_t a_row = (uint32_t)(rr >> 3) * 1024 + (uint32_t)(rr & 7) * 16;
+        // this row's factor rows (per half of the reduction) and the x ranges
+        // the CTA's k blocks touch
+        const long n3 = (long)NN * N;
+        const float *frow0 = (A.ch == 0 ? Vf : (A.ch == 1 ? VT : VT + n3)) + (long)(valid ? Q : 0) * N;
+        const float *frow1 = VT + 2 * n3 + (long)(valid ? Q : 0) * N;
+        int seg_lo[2], seg_n[2];
+        factor_segments(A.ch, N, kb0, kb1, A.nkb_half, seg_lo, seg_n);
+        // staged: the thread copies its own factor row segments into shared
+        // memory once (row stride fw, odd: the lanes' rows hit distinct banks);
+        // only this thread reads them
+        float *fs = reinterpret_cast<float *>(sbase + (size_t)S * stage_bytes) + (size_t)rr * (STG ? A.fw : 0);
+        if (STG) {
+            for (int t = 0; t < seg_n[0]; ++t) fs[t] = valid ? __ldg(frow0 + seg_lo[0] + t) : 0.f;
+            for (int t = 0; t < seg_n[1]; ++t) fs[seg_n[0] + t] = valid ? __ldg(frow1 + seg_lo[1] + t) : 0.f;
+        }
+        // factor of table column x (a or b) in half h
+        auto factor = [&](int h, int x) -> float {
+            if (STG) return fs[(h ? seg_n[0] - seg_lo[1] : -seg_lo[0]) + x];
+            return valid ? __ldg((h ? frow1 : frow0) + x) : 0.f;
+        };
         bool ok = true;
         for (int it = 0; it < nkb && ok; ++it) {
             const int s = it % S;
             const int kb = kb0 + it;
             const bool second = A.ch == 2 && kb >= A.nkb_half;
+            const int h = second ? 1 : 0;
             const int kk0 = (kb - (second ? A.nkb_half : 0)) * BK;
-            float f[64];
-            row_factors<N8>(A, Vf, VT, Q, valid, kk0, second, f);     // loads in flight during the wait
             const bool got = mbar_wait_abortable(smem_u32(&rfull[s]), (uint32_t)((it / S) & 1), abort_v);
             if (!__all_sync(0xffffffffu, got)) {
                 ok = false;
@@ -245,31 +229,67 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
             unsigned char *st = sbase + (size_t)s * stage_bytes;
             float v[64];
 #pragma unroll
-            for (int h = 0; h < 2; ++h)
+            for (int hh = 0; hh < 2; ++hh)
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
-                    const float4 x = *reinterpret_cast<const float4 *>(st + h * (kRawBytes / 2) + raw_row +
+                    const float4 x = *reinterpret_cast<const float4 *>(st + hh * (kRawBytes / 2) + raw_row +
                                                                        ((c ^ sw) << 4));
-                    v[32 * h + 4 * c + 0] = x.x;
-                    v[32 * h + 4 * c + 1] = x.y;
-                    v[32 * h + 4 * c + 2] = x.z;
-                    v[32 * h + 4 * c + 3] = x.w;
+                    v[32 * hh + 4 * c + 0] = x.x;
+                    v[32 * hh + 4 * c + 1] = x.y;
+                    v[32 * hh + 4 * c + 2] = x.z;
+                    v[32 * hh + 4 * c + 3] = x.w;
                 }
-            __syncwarp();      // the warp's raw rows are read before they are overwritten
+            // (a, b) of the block's first column; N8: a chunk of 8 columns
+            // lies in one a and never passes N^2
+            int a = kk0 / N, b = kk0 - a * N;
 #pragma unroll
             for (int kc = 0; kc < 8; ++kc) {
+                float f[8];
+                if (N8) {
+                    if (A.ch == 1 && !STG) {
+                        // 8 consecutive b (b % 8 == 0, N % 8 == 0): two aligned 16-byte loads
+                        float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = c0;
+                        if (valid) {
+                            c0 = __ldg(reinterpret_cast<const float4 *>(frow0 + b));
+                            c1 = __ldg(reinterpret_cast<const float4 *>(frow0 + b) + 1);
+                        }
+                        f[0] = c0.x; f[1] = c0.y; f[2] = c0.z; f[3] = c0.w;
+                        f[4] = c1.x; f[5] = c1.y; f[6] = c1.z; f[7] = c1.w;
+                    } else if (A.ch == 1) {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) f[e] = factor(h, b + e);
+                    } else {
+                        const float fa = factor(h, a);
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) f[e] = fa;
+                    }
+                    b += 8;
+                    if (b >= N) {
+                        b -= N;
+                        ++a;
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        f[e] = kk0 + 8 * kc + e < NN ? factor(h, A.ch == 1 ? b : a) : 0.f;
+                        if (++b == N) {
+                            b = 0;
+                            ++a;
+                        }
+                    }
+                }
                 uint4 hi, lo;
                 uint32_t *hp = &hi.x, *lp = &lo.x;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const float x0 = v[8 * kc + 2 * q] * f[8 * kc + 2 * q];
-                    const float x1 = v[8 * kc + 2 * q + 1] * f[8 * kc + 2 * q + 1];
+                    const float x0 = v[8 * kc + 2 * q] * f[2 * q];
+                    const float x1 = v[8 * kc + 2 * q + 1] * f[2 * q + 1];
                     const __nv_bfloat162 hh = __floats2bfloat162_rn(x0, x1);
                     hp[q] = *reinterpret_cast<const uint32_t *>(&hh);
                     lp[q] = pack_bf16x2(x0 - __low2float(hh), x1 - __high2float(hh));
                 }
-                *reinterpret_cast<uint4 *>(st + a_row + kc * 128) = hi;
-                *reinterpret_cast<uint4 *>(st + kRawBytes / 2 + a_row + kc * 128) = lo;
+                *reinterpret_cast<uint4 *>(st + raw_row + ((kc ^ sw) << 4)) = hi;
+                *reinterpret_cast<uint4 *>(st + kRawBytes / 2 + raw_row + ((kc ^ sw) << 4)) = lo;
             }
             fence_async_shared();
             mbar_arrive(smem_u32(&full[s]));
@@ -321,12 +341,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
             const uint32_t sb = base + (uint32_t)s * stage_bytes;
 #pragma unroll
             for (int ks = 0; ks < BK / 16; ++ks) {
-                const uint32_t a_off = (uint32_t)(ks * 256);                  // two 128-byte core matrices
-                const uint32_t b_off = (uint32_t)(2 * ks * (Npad / 8) * 128);
-                const uint64_t ahi = make_desc(sb + a_off, 128, 1024);
-                const uint64_t alo = make_desc(sb + kRawBytes / 2 + a_off, 128, 1024);
-                const uint64_t bhi = make_desc(sb + kRawBytes + b_off, (Npad / 8) * 128, 128);
-                const uint64_t blo = make_desc(sb + kRawBytes + b_bytes + b_off, (Npad / 8) * 128, 128);
+                const uint32_t k_off = (uint32_t)(ks * 32);                   // 16 BF16 along the swizzled row
+                const uint64_t ahi = make_desc_sw128(sb + k_off, 1024);
+                const uint64_t alo = make_desc_sw128(sb + kRawBytes / 2 + k_off, 1024);
+                const uint64_t bhi = make_desc_sw128(sb + kRawBytes + k_off, 1024);
+                const uint64_t blo = make_desc_sw128(sb + kRawBytes + b_bytes + k_off, 1024);
                 const uint32_t acc = (i > 0 || ks > 0) ? 1u : 0u;
                 mma_bf16(tmem, ahi, bhi, idesc, acc);
                 mma_bf16(tmem, ahi, blo, idesc, 1u);
@@ -393,28 +412,14 @@ static qpfrg_status launch_fused(qpfrg_ctx *c, int ch, TcFusedArgs &A, int nz, i
     const int N = c->pb.N, Npad = t.Npad;
     const long NN = (long)N * N;
     const long Kp = ch == 2 ? t.Kpd : t.Kp;
-    const size_t stage_bytes = kRawBytes + 2 * (size_t)Npad * tc::BK * 2;
-    // as many stages as fit beside the kernel's static shared memory (barriers)
-    // and the 1 KB of alignment slack within the 227 KB a block may opt into
-    cudaFuncAttributes fa{};
-    cudaError_t e = cudaFuncGetAttributes(&fa, tc_fused_kernel<4, true>);
-    if (e != cudaSuccess) return cuda_fail(c, e, "tc_fused attributes");
-    const size_t smem_max = 227 * 1024 - 1024 - fa.sharedSizeBytes;
-    int S = (int)std::min<size_t>(4, smem_max / stage_bytes);
-    if (Npad % 16 != 0 || Npad > 256 || N > 256 || (N & 1) || S < 2) {
+    if (Npad % 16 != 0 || Npad > 256 || N > 256 || (N & 1)) {
         c->err = "tensor-core contraction: unsupported shape";
         return QPFRG_ERR_UNSUPPORTED;
     }
-    const size_t smem = S * stage_bytes + 1024;
-    const bool n8 = (N & 7) == 0;
-    auto kern = n8 ? (S == 4 ? tc_fused_kernel<4, true> : (S == 3 ? tc_fused_kernel<3, true> : tc_fused_kernel<2, true>))
-                   : (S == 4 ? tc_fused_kernel<4, false>
-                             : (S == 3 ? tc_fused_kernel<3, false> : tc_fused_kernel<2, false>));
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_fail(c, e, "tc_fused smem attribute");
     const int M = (int)NN;
     const int mtiles = div_up(M, tc::BM);
     const int nkb = (int)(Kp / tc::BK);
+    const int nkb_half = (int)(t.Kp / tc::BK);
     // split K so that the grid fills whole waves of the 152 SMs (one CTA per SM)
     int splits = 1;
     double best = -1.0;
@@ -430,6 +435,41 @@ static qpfrg_status launch_fused(qpfrg_ctx *c, int ch, TcFusedArgs &A, int nz, i
     if (c->tune.tc_splits[ch] > 0) splits = std::min(c->tune.tc_splits[ch], nkb);
     const int kb_per = div_up(nkb, splits);
     splits = div_up(nkb, kb_per);
+    // the factor rows the widest split touches, staged in shared memory when
+    // they fit beside at least two stages (row stride odd)
+    int wmax = 1;
+    for (int y = 0; y < splits; ++y) {
+        int lo[2], n[2];
+        factor_segments(ch, N, y * kb_per, std::min(nkb, (y + 1) * kb_per), nkb_half, lo, n);
+        wmax = std::max(wmax, n[0] + n[1]);
+    }
+    const int fw = wmax | 1;
+    const size_t stage_bytes = kRawBytes + 2 * (size_t)Npad * tc::BK * 2;
+    const size_t fbytes = (size_t)tc::BM * fw * sizeof(float);
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, tc_fused_kernel<4, true, true>);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tc_fused attributes");
+    // 227 KB a block may opt into, less the static barriers and 1 KB of alignment slack
+    const size_t avail = 227 * 1024 - 1024 - fa.sharedSizeBytes;
+    int S = avail > fbytes ? (int)std::min<size_t>(4, (avail - fbytes) / stage_bytes) : 0;
+    const bool stg = S >= 2;
+    if (!stg) S = (int)std::min<size_t>(4, avail / stage_bytes);
+    if (S < 2) {
+        c->err = "tensor-core contraction: unsupported shape";
+        return QPFRG_ERR_UNSUPPORTED;
+    }
+    const size_t smem = S * stage_bytes + 1024 + (stg ? fbytes : 0);
+    using KernT = void (*)(const CUtensorMap, const CUtensorMap, const CUtensorMap, TcFusedArgs);
+    static const KernT table[3][2][2] = {
+        {{tc_fused_kernel<2, false, false>, tc_fused_kernel<2, false, true>},
+         {tc_fused_kernel<2, true, false>, tc_fused_kernel<2, true, true>}},
+        {{tc_fused_kernel<3, false, false>, tc_fused_kernel<3, false, true>},
+         {tc_fused_kernel<3, true, false>, tc_fused_kernel<3, true, true>}},
+        {{tc_fused_kernel<4, false, false>, tc_fused_kernel<4, false, true>},
+         {tc_fused_kernel<4, true, false>, tc_fused_kernel<4, true, true>}}};
+    const KernT kern = table[S - 2][(N & 7) == 0 ? 1 : 0][stg ? 1 : 0];
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tc_fused smem attribute");
     A.M = M;
     A.Ncol = N;
     A.Npad = Npad;
@@ -440,6 +480,7 @@ static qpfrg_status launch_fused(qpfrg_ctx *c, int ch, TcFusedArgs &A, int nz, i
     A.RT = t.RT;
     A.KB = t.KB;
     A.ch = ch;
+    A.fw = stg ? fw : 0;
     A.err = c->d_tc_err;
     A.test_wait = std::getenv("QPFRG_TEST_TC_WAIT") ? 10000000LL : 0;   // ~5 ms
     prof_begin(c);

@@ -18,8 +18,10 @@ namespace qpfrg {
 // BF16 hi/lo and stored in tiles (tile_index, Npad rows per tile):
 // pp: V[a,b,n];  cr: V[n,a,b];  d: V[b,n,a] at k and V[n,b,a] at Kp + k, so
 // that each half of the d reduction starts on a 64-wide block;  pads (n >= N,
-// k >= N^2 within a half) are written as zeros;  plus VT[j][l][b] = V[b][j][l]
-// for the cr factor.
+// k >= N^2 within a half) are written as zeros;  plus the row-factor tables
+// of the A operands, rows in transfer order: VT[0][Q = (l,j)][b] = V[b,j,l]
+// (cr), VT[1][Q = (i,l)][a] = 2 V[i,a,l] - V[a,i,l] and VT[2][Q][a] =
+// -V[i,a,l] (the two halves of d).
 struct TcPrepArgs {
     const float *V;
     int N, Npad;
@@ -33,7 +35,7 @@ __device__ __forceinline__ void tc_prep_body(const TcPrepArgs &t)
     const int N = t.N, Npad = t.Npad;
     const long NN = (long)N * N, n3 = NN * N, Kp = t.Kp;
     const long s_pp = (long)Npad * Kp, s_d = 2 * s_pp;
-    const long total = 2 * s_pp + s_d + n3;
+    const long total = 2 * s_pp + s_d + 3 * n3;
     const float *V = t.V;
     for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
         if (idx < 2 * s_pp + s_d) {
@@ -62,9 +64,15 @@ __device__ __forceinline__ void tc_prep_body(const TcPrepArgs &t)
             dst[0][o] = hi;
             dst[1][o] = lo;
         } else {
-            const long o = idx - (2 * s_pp + s_d);     // o = (j N + l) N + b
-            const int b = (int)(o % N), jl = (int)(o / N);
-            t.VT[o] = V[(long)b * NN + jl];
+            const long o = idx - (2 * s_pp + s_d);
+            const int part = (int)(o / n3);
+            const long r = o - part * n3;             // Q N + x
+            const int x = (int)(r % N), Q = (int)(r / N), q1 = Q / N, q2 = Q - q1 * N;
+            float v;
+            if (part == 0) v = V[((long)x * N + q2) * N + q1];                         // Q = (l,j): V[b,j,l]
+            else if (part == 1) v = 2.f * V[((long)q1 * N + x) * N + q2] - V[((long)x * N + q1) * N + q2];
+            else v = -V[((long)q1 * N + x) * N + q2];                                 // Q = (i,l): -V[i,a,l]
+            t.VT[o] = v;
         }
     }
 }
@@ -94,7 +102,7 @@ qpfrg_status launch_tc_prep_batch(qpfrg_ctx *c, const TcPrepFlow *d_flows, const
 {
     const int N = c->pb.N;
     const long NN = (long)N * N;
-    const long total = 4 * (long)c->tc.Npad * c->tc.Kp + NN * N;
+    const long total = 4 * (long)c->tc.Npad * c->tc.Kp + 3 * NN * N;
     const int blocks = (int)std::min<long>((total + 255) / 256, 152L * 4);
     TcPrepArgs t{};
     t.N = N;
@@ -112,7 +120,7 @@ qpfrg_status launch_tc_prep(qpfrg_ctx *c)
 {
     const int N = c->pb.N;
     const long NN = (long)N * N;
-    const long total = 4 * (long)c->tc.Npad * c->tc.Kp + NN * N;
+    const long total = 4 * (long)c->tc.Npad * c->tc.Kp + 3 * NN * N;
     int blocks = (int)std::min<long>((total + 255) / 256, 152L * 16);
     TcPrepArgs t;
     t.V = c->d_Vf;

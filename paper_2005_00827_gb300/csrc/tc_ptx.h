@@ -30,6 +30,21 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint
     return d;                     // layout type 0 (no swizzle), base offset 0
 }
 
+// Shared-memory matrix descriptor of a K-major operand in the 128-byte swizzle
+// layout (rows of 128 B, the 16-byte chunks of row r XOR-permuted by r % 8,
+// 8-row groups sbo apart, the tile on a 1024-byte boundary); the start address
+// may step along K inside the 128-byte row (32 B per K16 slice of BF16).
+__device__ __forceinline__ uint64_t make_desc_sw128(uint32_t saddr, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;      // leading byte offset: unused for swizzled K-major (16 B)
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1u << 46;      // descriptor version
+    d |= (uint64_t)2u << 61;      // 128-byte swizzle
+    return d;
+}
+
 // Instruction descriptor of kind::f16: F32 accumulator, BF16 A and B, both
 // K-major, N >> 3 at bit 17, M >> 4 at bit 24.
 __host__ __device__ constexpr uint32_t make_idesc(int M, int N)

@@ -29,6 +29,18 @@ def splitmix64(seed: int):
         yield (z >> 11) * (1.0 / (1 << 53))
 
 
+def splitmix64_array(seed: int, count: int) -> np.ndarray:
+    """The first `count` values of splitmix64(seed) at once (numpy uint64
+    arithmetic wraps modulo 2^64 as the generator's masks do)."""
+    with np.errstate(over="ignore"):
+        k = np.arange(1, count + 1, dtype=np.uint64)
+        z = np.uint64(seed & MASK64) + k * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z ^= z >> np.uint64(31)
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+
+
 def c4v_patch_maps(N: int, n_shell: int = 1):
     """The 8 index permutations of the angular patches under C4v (wedge
     centres at 2 pi w / N_a, N_a = N / n_shell a multiple of 4; patch
@@ -56,8 +68,7 @@ def c4v_symmetrise(V: np.ndarray, n_shell: int = 1) -> np.ndarray:
 def random_vertex(N: int, U: float, seed: int = 1, amp: float = 0.5, c4v: bool = True,
                   n_shell: int = 1) -> np.ndarray:
     """V = U + amp U s with s uniform in [-1, 1] (splitmix64), FP64, [k1][k2][k3]."""
-    gen = splitmix64(seed)
-    s = np.fromiter((2.0 * next(gen) - 1.0 for _ in range(N ** 3)), dtype=np.float64, count=N ** 3)
+    s = 2.0 * splitmix64_array(seed, N ** 3) - 1.0
     V = (U + amp * U * s).reshape(N, N, N)
     return c4v_symmetrise(V, n_shell) if c4v else V
 

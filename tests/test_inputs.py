@@ -33,3 +33,20 @@ def test_random_vertex_is_c4v_symmetric_and_seeded():
     for g in inputs.c4v_patch_maps(16):
         assert np.allclose(V[np.ix_(g, g, g)], V, rtol=0, atol=1e-15)
     assert np.all(V > 2.0 * 0.5 - 1e-12) and np.all(V < 2.0 * 1.5 + 1e-12)
+
+
+def test_splitmix64_array_equals_the_generator():
+    for seed in (0, 1, 20050082, (1 << 64) - 5):
+        g = inputs.splitmix64(seed)
+        ref = np.array([next(g) for _ in range(2000)])
+        assert np.array_equal(inputs.splitmix64_array(seed, 2000), ref)
+
+
+def test_shell_patch_maps_keep_the_shell():
+    N, ns = 24, 3
+    for g in inputs.c4v_patch_maps(N, ns):
+        assert sorted(g) == list(range(N))
+        assert np.array_equal(g % ns, np.arange(N) % ns)
+    V = inputs.random_vertex(N, 2.0, seed=5, n_shell=ns)
+    for g in inputs.c4v_patch_maps(N, ns):
+        assert np.allclose(V[np.ix_(g, g, g)], V, rtol=0, atol=1e-15)
