@@ -58,6 +58,10 @@ SIGMA_FP32_PER_PAIR, SIGMA_MUFU_PER_PAIR = 20, 4
 # included (ncu smsp__inst_executed x 32 / evaluations at np96_n32:
 # 5.71e8 x 32 / 2.27e8)
 BUBBLE_ISSUE_AS_BUILT, SIGMA_ISSUE_AS_BUILT = 80, 36
+# the self-energy pair with its patch read from the patch-of-r table: the 18
+# slots that locate r's patch give way to one 8-byte load per 8 records and
+# a byte extraction (about 2 slots per pair)
+SIGMA_ISSUE_AS_BUILT_TABLE = 20
 ISSUE_LANES_PER_SM, MUFU_PER_SM, N_SM = 128, 16, 152
 
 
@@ -258,6 +262,7 @@ def run_qpfrg(args):
     prof = api.qpfrg_profile(ctx.h)
     api.qpfrg_set_profiling(ctx.h, False)
     value, ms = aggregate(ms, 4.0 * steps_done, world, device="cuda")
+    table_bytes = api.qpfrg_sigma_table(ctx.h)[0]
 
     # end to end: state uploaded from pinned host memory, one step, state read back
     nbytes = api.qpfrg_state_size(ctx.h)
@@ -348,7 +353,8 @@ def run_qpfrg(args):
             fp32, mufu, built = BUBBLE_FP32_PER_EVAL, BUBBLE_MUFU_PER_EVAL, BUBBLE_ISSUE_AS_BUILT
         else:
             units = sigma_units(N, n)
-            fp32, mufu, built = SIGMA_FP32_PER_PAIR, SIGMA_MUFU_PER_PAIR, SIGMA_ISSUE_AS_BUILT
+            fp32, mufu = SIGMA_FP32_PER_PAIR, SIGMA_MUFU_PER_PAIR
+            built = SIGMA_ISSUE_AS_BUILT_TABLE if table_bytes else SIGMA_ISSUE_AS_BUILT
         peak_units = N_SM * clk_mhz * 1e6 / alu_clk_per_unit(fp32, mufu)
         avg_s = kern[dom][0] / kern[dom][1] / 1e3
         achieved = units / avg_s
@@ -400,6 +406,7 @@ def run_qpfrg(args):
                    f"{2 * N * N * M / 1e9:.2f} GB, bubble tables)", "parallelism": "replicas",
                    "tuning": tuning},
         "e2e": e2e, "gpu_launches": int(sum(v[1] for v in prof.values())), "rhs_work": work,
+        "sigma_table_bytes": table_bytes,
         "kernels_ms": {k: round(v[0], 3) for k, v in kern.items()},
         "kernel_launches": {k: v[1] for k, v in kern.items()},
         "roofline": roof, "rhs_roofline": rhs_roof, "clocks": clk, **extra,

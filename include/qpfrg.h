@@ -139,6 +139,11 @@ typedef struct {
     int katanin;                 /* nonzero: Katanin factor K on the S lines (App. A.5)  */
     int a_mode;                  /* 0: patch average of A, 1: its minimum, 2: its maximum
                                     (the bracket flows of App. B), 3: one-loop term dropped */
+    int sigma_table;             /* >= 0: the FP32 wedge self-energy of a C4v-symmetric state
+                                    reads the patch of r = k + p - q from a table built on
+                                    first use (N_irr M^2 bytes: 126 GB at N_p = 96, 32 x 32),
+                                    when it fits in 60 % of the free device memory; < 0: it
+                                    decides every patch per pair.  Same sums either way. */
 } qpfrg_options;
 
 typedef struct {
@@ -326,6 +331,21 @@ qpfrg_status qpfrg_profile_get(qpfrg_t ctx, int id, double *ms, long long *launc
  * reduction is off (lattice mode, no_loop_symmetry). */
 qpfrg_status qpfrg_rhs_work(qpfrg_t ctx, long long *loop_evals, long long *loop_evals_full,
                             long long *rows_unreduced);
+
+/* The patch-of-r table of the flow's self-energy (options.sigma_table),
+ * for verification: *bytes = its size (0 while not built: it is built by the
+ * first Z evaluation of a C4v-symmetric state in the FP32 wedge path, when it
+ * fits), and, when h_out is not NULL, count bytes from offset copied into
+ * h_out (host memory; blocks until done).  Byte (jidx, a, iq, i), at
+ * (((jidx N + a) P/8 + i/8) M + iq) 8 + i mod 8, is the patch of r = k_j + p - q for the
+ * irreducible target j = jidx (patches 0 .. N/8), p = a P + i (fine points in
+ * their storage order) and q the fine point iq of the kernel's angular-minor
+ * order: iq = b P + t' with q = b P + (t' mod n_theta) n_r + t' / n_theta.
+ * A byte N denotes patch 0 (the kernel's slot for the wedge past the last
+ * ray between wedges N-1 and 0).
+ * Errors: QPFRG_ERR_INVALID for a range outside the table. */
+qpfrg_status qpfrg_sigma_table(qpfrg_t ctx, size_t *bytes, long long offset, long long count,
+                               unsigned char *h_out);
 
 /* Launch shapes of the hot kernels; 0 in a field selects the built-in
  * heuristic.  The paper has no counterpart: these are GPU schedule choices.

@@ -32,7 +32,7 @@ EXPORTS = (
     "qpfrg_geometry", "qpfrg_set_profiling", "qpfrg_profile_reset", "qpfrg_profile_count",
     "qpfrg_profile_name", "qpfrg_profile_get", "qpfrg_last_error", "qpfrg_version", "qpfrg_destroy",
     "qpfrg_zfactor_static", "qpfrg_flow_batch", "qpfrg_autotune", "qpfrg_set_tuning", "qpfrg_rhs_work",
-    "qpfrg_spectral", "qpfrg_read_sigma_flow",
+    "qpfrg_spectral", "qpfrg_read_sigma_flow", "qpfrg_sigma_table",
 )
 
 
@@ -58,7 +58,7 @@ class qpfrg_options(C.Structure):
                 ("step", C.c_double), ("lambda_end", C.c_double), ("z_max", C.c_double),
                 ("max_steps", C.c_int), ("T_fixed", C.c_double), ("timeout_s", C.c_double),
                 ("autotune", C.c_int), ("no_loop_symmetry", C.c_int), ("sigma_ode", C.c_int),
-                ("katanin", C.c_int), ("a_mode", C.c_int)]
+                ("katanin", C.c_int), ("a_mode", C.c_int), ("sigma_table", C.c_int)]
 
 
 class qpfrg_tuning(C.Structure):
@@ -140,6 +140,8 @@ def load(build_if_missing: bool = True):
     L.qpfrg_spectral.argtypes = [_P, _P, _P, _P, _P, _P]
     L.qpfrg_spectral.restype = C.c_int
     L.qpfrg_rhs_work.argtypes = [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
+    L.qpfrg_sigma_table.argtypes = [_P, C.POINTER(C.c_size_t), C.c_longlong, C.c_longlong, _P]
+    L.qpfrg_sigma_table.restype = C.c_int
     L.qpfrg_rhs_work.restype = C.c_int
     L.qpfrg_destroy.argtypes = [_P]
     L.qpfrg_destroy.restype = None
@@ -319,6 +321,19 @@ def qpfrg_rhs_work(ctx) -> dict:
     a, b, r = C.c_longlong(), C.c_longlong(), C.c_longlong()
     _check(ctx, load().qpfrg_rhs_work(ctx, C.byref(a), C.byref(b), C.byref(r)))
     return dict(loop_evals=a.value, loop_evals_full=b.value, rows_unreduced=r.value)
+
+
+def qpfrg_sigma_table(ctx, offset=0, count=0):
+    """Size of the self-energy's patch-of-r table (0 while not built) and, for
+    count > 0, the bytes [offset, offset + count) as a numpy uint8 array."""
+    import numpy as np
+    n = C.c_size_t()
+    _check(ctx, load().qpfrg_sigma_table(ctx, C.byref(n), 0, 0, None))
+    if count <= 0:
+        return n.value, None
+    out = np.zeros(count, dtype=np.uint8)
+    _check(ctx, load().qpfrg_sigma_table(ctx, None, int(offset), int(count), out.ctypes.data_as(_P)))
+    return n.value, out
 
 
 def qpfrg_last_error(ctx) -> str:

@@ -18,7 +18,7 @@ namespace {
 const char *const kKernelNames[K_COUNT] = {
     "partner_map", "bubble", "contract_pp", "contract_cr", "contract_d", "sigma_z",
     "sigma_hist", "sigma_grid", "z_update", "rk_stage", "rk_final", "convert_f32",
-    "tc_prep", "tc_fused_pp", "tc_fused_cr", "tc_fused_d", "kp_table",
+    "tc_prep", "tc_fused_pp", "tc_fused_cr", "tc_fused_d", "kp_table", "rtab_build",
 };
 
 struct PendingEvent {
@@ -184,7 +184,8 @@ void qpfrg_destroy(qpfrg_t c)
                         c->d_part, c->d_B, c->d_ones, c->d_sig, c->d_hist, c->d_jirr, c->d_rep,
                         c->tc.Bpp[0], c->tc.Bpp[1], c->tc.Bcr[0], c->tc.Bcr[1], c->tc.Bd[0], c->tc.Bd[1],
                         c->tc.VT, c->d_tc_err, c->d_xij, c->d_bnd, c->d_qxl, c->d_qyl, c->d_kp, c->d_kcs, c->d_xij_f,
-                        c->d_ptab, c->d_jgrid, c->d_repgrid, c->d_lrepQ, c->d_lnimg, c->d_limg, c->d_ltask};
+                        c->d_ptab, c->d_jgrid, c->d_repgrid, c->d_lrepQ, c->d_lnimg, c->d_limg, c->d_ltask,
+                        c->d_rtab};
         for (void *p : ptrs)
             if (p) cudaFree(p);
     }
@@ -649,6 +650,7 @@ static qpfrg_status make_child(qpfrg_ctx *parent, double U, double lambda0, doub
     qpfrg_ctx *c = new (std::nothrow) qpfrg_ctx(*parent);
     if (!c) return QPFRG_ERR_OOM;
     c->shares_geometry = true;
+    c->rtab_tried = true;   // a child reads the parent's table (if built) and never builds its own
     c->profiler = new (std::nothrow) Profiler();
     c->prof = false;
     for (auto &sl : c->slots) sl = ProfileSlot();

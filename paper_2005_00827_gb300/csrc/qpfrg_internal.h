@@ -71,6 +71,7 @@ enum KernelId {
     K_TC_CR,
     K_TC_D,
     K_KP_TABLE,
+    K_RTAB,
     K_COUNT
 };
 
@@ -223,6 +224,8 @@ struct qpfrg_ctx {
     float *d_qxl = nullptr, *d_qyl = nullptr;   // M: FP32 residuals kx - (float)kx, ky - (float)ky
     float4 *d_kp = nullptr;      // [target][p]: k_j + p as FP32 hi/lo pairs (self-energy scratch)
     float4 *d_kcs = nullptr;     // [target]: cos/sin of k_j (self-energy scratch)
+    uint8_t *d_rtab = nullptr;   // patch of r per (irreducible target, p, q) of the flow's Z (sigma.cu)
+    bool rtab_tried = false;     // built, or found not to fit, once per context
     uint8_t *d_ptab = nullptr;   // W rows x kProjStride bytes: cell table of the FP32 wedge projection (wedge mode, N <= 254)
     double *d_Qpp = nullptr, *d_Qph = nullptr;  // N^2 x 2 transfer momenta (FP64)
     uint8_t *d_part = nullptr;   // 2 x N^2 x M partner patches (pp family, then ph)

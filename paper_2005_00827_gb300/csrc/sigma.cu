@@ -496,6 +496,7 @@ struct SigmaFastArgs {
     const float *xij_f, *qxl, *qyl;
     const float4 *kp, *kcs, *bnd;
     const uint8_t *ptab;
+    const uint8_t *rtab;    // patch of r per (target, p, q) (RT launches; rtab_build_kernel)
     const int *jlist;
     double *sig;
     float t, tp, mu, eta2, invT, cT, twoT, fourT;   // cT = log2(e) / T
@@ -584,11 +585,70 @@ __device__ __noinline__ int sf_slow_patch(const SigmaFastArgs &A, int jidx, int 
     return c;
 }
 
+// The patch of r = k_j + p - q for every target of the list (position jidx),
+// every loop point p = a P + i and every loop point q (angular-minor index iq,
+// the order in which sigma_fast_kernel walks them), one byte each at
+// rtab[(((jidx N + a) P/8 + i/8) M + iq) 8 + i % 8]: a thread reads the bytes
+// of eight records as one 8-byte word, and the words of a warp's 32 loop
+// points q are contiguous (256 B): the same decisions as the kernel's table
+// path and its guarded slow path, so a launch that reads them gives the same
+// sums.  They depend on the geometry only (targets, fine grid), so one build
+// serves every later call.  Grid (ceil(M / 256), N, targets), 256 threads.
+constexpr size_t kRtabTabBytes = ((size_t)kProjW * kProjStride + 15) / 16 * 16;
+constexpr size_t kRtabSmem = kRtabTabBytes + (size_t)SF_SLOTS * sizeof(float2);
+
+__global__ void __launch_bounds__(256) rtab_build_kernel(SigmaFastArgs A, uint8_t *__restrict__ rtab)
+{
+    const int N = A.pb.N, M = A.pb.M, PP = A.pb.P;
+    const int a = blockIdx.y, jidx = blockIdx.z;
+    const int j = A.jlist ? A.jlist[jidx] : jidx;
+    const int tid = threadIdx.x;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *tab = smem_raw;                                      // the cell table
+    float2 *ray = reinterpret_cast<float2 *>(smem_raw + kRtabTabBytes); // rays between wedges
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(A.ptab);
+        uint4 *dst = reinterpret_cast<uint4 *>(tab);
+        const int n16 = (kProjW * kProjStride + 15) / 16;
+        for (int i = tid; i < n16; i += blockDim.x) dst[i] = src[i];
+        for (int i = tid; i < SF_SLOTS; i += blockDim.x) {
+            const float4 bd = A.bnd[i == N ? 0 : (i < N ? i : 0)];
+            ray[i] = i <= N ? make_float2(bd.x, bd.z) : make_float2(0.f, 0.f);
+        }
+    }
+    __syncthreads();
+    const unsigned char *tabc = tab + (kProjW / 2) * (kProjStride + 1);   // the cell of the origin
+    const int iq = blockIdx.x * 256 + tid;
+    if (iq >= M) return;
+    const int b = iq / PP, rem = iq - b * PP;
+    const int qq = b * PP + (rem % A.pb.n_theta) * A.pb.n_r + rem / A.pb.n_theta;
+    const int qx = angle_fx(A.kx64[qq]), qy = angle_fx(A.ky64[qq]);
+    // the thread's P bytes, as P/8 words of eight records (P a multiple of 16)
+    uint2 *out = reinterpret_cast<uint2 *>(rtab) + ((long)jidx * N + a) * (long)(PP / 8) * M + iq;
+    for (int i0 = 0; i0 < PP; i0 += 8) {
+        unsigned w[2] = {0u, 0u};
+        for (int i = i0; i < i0 + 8; ++i) {
+            const int p = a * PP + i;
+            const float4 k4 = A.kp[(long)jidx * M + p];
+            const int kx = angle_fx((double)k4.x + (double)k4.y), ky = angle_fx((double)k4.z + (double)k4.w);
+            float x, y;
+            bool slow;
+            int c = fx_patch(kx, ky, qx, qy, tabc, ray, x, y, slow);
+            if (slow) {
+                const bool edge = fmaxf(fabsf(x), fabsf(y)) > kFxEdge;
+                c = sf_slow_patch(A, jidx, j, p, qq, x * kRadPerFx, y * kRadPerFx, edge, A.bnd);
+            }
+            w[(i - i0) >> 2] |= (unsigned)c << (8 * ((i - i0) & 3));
+        }
+        out[(long)(i0 >> 3) * M] = make_uint2(w[0], w[1]);
+    }
+}
+
 // UNIB: every block of 256 SF_QPT loop points q lies in one patch b (P a
 // multiple of 256 SF_QPT), so the vertex weight is a per-patch table:
 // cz[c] = (Z_c (2 V_jab^2 - V_jab V_jac), -, -2t l_c, -mu l_c); otherwise
 // cz[c] = (Z_c, Z_c V_jac, -2t l_c, -mu l_c) and the weight is formed per pair.
-template <bool TP0, bool UNIB>
+template <bool TP0, bool UNIB, bool RT>
 __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
 {
     const int N = A.pb.N, M = A.pb.M;
@@ -626,7 +686,7 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
     float *rC = reinterpret_cast<float *>(smem_raw + L.rC);     // x_j + x_p + 2T
     unsigned char *tab = smem_raw + L.tab;
 
-    {
+    if (!RT) {
         const uint4 *src = reinterpret_cast<const uint4 *>(A.ptab);
         uint4 *dst = reinterpret_cast<uint4 *>(tab);
         const int n16 = (kProjW * kProjStride + 15) / 16;
@@ -709,11 +769,13 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
         float fqp[SF_QPT], fcqp[SF_QPT], v2[SF_QPT], vab[SF_QPT], mxq[SF_QPT];
         float2 acc = make_float2(0.f, 0.f);     // the SF_QPT = 2 loop points as the two lanes
         int qi[SF_QPT], qx[SF_QPT], qy[SF_QPT];
+        const uint8_t *rq[SF_QPT];   // RT: the patch-of-r rows of this thread's loop points q
 #pragma unroll
         for (int k = 0; k < SF_QPT; ++k) {
             const int iq = blk * (256 * SF_QPT) + k * 256 + tid;   // angular-minor index
             const bool valid = iq < M;
             const int ii = valid ? iq : M - 1;
+            rq[k] = RT ? A.rtab + (((long)jidx * N + a) * (long)(PP / 8) * M + ii) * 8 : nullptr;
             const int b = ii / PP, rem = ii - b * PP;
             const int qq = b * PP + (rem % A.pb.n_theta) * A.pb.n_r + rem / A.pb.n_theta;
             qi[k] = qq;
@@ -740,6 +802,77 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
                 stage(p0, cnt);
                 __syncthreads();
             }
+            // the arithmetic of two records (ra, rb, upp) and their 2 x SF_QPT
+            // patches c: the two loop points q of a record as the lanes of
+            // packed FP32x2 operations where the operands pair up
+            auto pair_math = [&](const float4 (&ra)[2], const float4 (&rb)[2], const float (&upp)[2],
+                                 const int (&c)[2][SF_QPT]) {
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    float2 xr, amp, sum;
+                    float2 fr, aq, dq;
+#pragma unroll
+                    for (int k = 0; k < SF_QPT; ++k) {
+                        const float4 z = cz[c[r][k]];
+                        // (cos r_x, cos r_y) by angle addition
+                        const float2 cr2 = __ffma2_rn(make_float2(ra[r].z, ra[r].w), cq[k],
+                                                      __fmul2_rn(make_float2(rb[r].x, rb[r].y), sq[k]));
+                        float x = fmaf(cr2.x + cr2.y, z.z, z.w);       // Z-scaled line energy of r / (T ln 2)
+                        if (!TP0) x = fmaf(cr2.x * cr2.y, cd[c[r][k]], x);
+                        const float ex = ex2_approx(x);
+                        const float a = rb[r].z * fcqp[k];
+                        const float d = fmaf(rb[r].w, fqp[k], -a);
+                        const float w = UNIB ? z.x : fmaf(-vab[k], z.y, z.x * v2[k]);
+                        const float sm = upp[r] + mxq[k];
+                        if (k == 0) { xr.x = x; fr.x = ex; aq.x = a; dq.x = d; amp.x = w; sum.x = sm; }
+                        else        { xr.y = x; fr.y = ex; aq.y = a; dq.y = d; amp.y = w; sum.y = sm; }
+                    }
+                    const float2 g = __fadd2_rn(fr, one2);
+                    fr = make_float2(rcp_approx(g.x), rcp_approx(g.y));
+                    const float2 F = __ffma2_rn(fr, dq, aq);           // A + f_r (B - A)
+                    amp = __fmul2_rn(amp, F);
+                    // d0 = xi_j - E, E = x_q + x_r - x_p
+                    const float2 d0 = __ffma2_rn(xr, ntln2, sum);
+                    const float2 u = __ffma2_rn(d0, d0, nkchord);
+                    const float2 den = __ffma2_rn(__fmul2_rn(eta2x4, d0), d0, __fmul2_rn(u, u));
+                    acc = __ffma2_rn(__fmul2_rn(amp, u), make_float2(rcp_approx(den.x), rcp_approx(den.y)), acc);
+                }
+            };
+            if (RT) {
+                // eight records per trip: their patches for each loop point q
+                // are one 8-byte word of the table, loaded one trip ahead
+                // (word of records i .. i+7 at rq + i M)
+                uint2 wn[SF_QPT];
+#pragma unroll
+                for (int k = 0; k < SF_QPT; ++k) wn[k] = __ldcs(reinterpret_cast<const uint2 *>(rq[k] + (long)p0 * M));
+                for (int i = 0; i < cnt; i += 8) {
+                    uint2 w[SF_QPT];
+#pragma unroll
+                    for (int k = 0; k < SF_QPT; ++k) {
+                        w[k] = wn[k];
+                        if (i + 8 < cnt) wn[k] = __ldcs(reinterpret_cast<const uint2 *>(rq[k] + (long)(p0 + i + 8) * M));
+                    }
+#pragma unroll 2
+                    for (int s2 = 0; s2 < 4; ++s2) {
+                        float4 ra[2], rb[2];
+                        float upp[2];
+                        int c[2][SF_QPT];
+#pragma unroll
+                        for (int r = 0; r < 2; ++r) {
+                            ra[r] = rA[i + 2 * s2 + r];
+                            rb[r] = rB[i + 2 * s2 + r];
+                            upp[r] = rC[i + 2 * s2 + r];
+#pragma unroll
+                            for (int k = 0; k < SF_QPT; ++k) {
+                                const int byte = 2 * s2 + r;
+                                const unsigned word = byte < 4 ? w[k].x : w[k].y;
+                                c[r][k] = (int)((word >> (8 * (byte & 3))) & 255u);
+                            }
+                        }
+                        pair_math(ra, rb, upp, c);
+                    }
+                }
+            } else {
             // two records per iteration: the patches of all 2 x SF_QPT pairs
             // first, one rarely taken branch for the guarded ones, then the
             // arithmetic of all of them (one large block for the scheduler);
@@ -785,38 +918,8 @@ __global__ void __launch_bounds__(256, 2) sigma_fast_kernel(SigmaFastArgs A)
                             }
                         }
                 }
-                // the arithmetic: the two loop points q of a record as the
-                // lanes of packed FP32x2 operations where the operands pair up
-#pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    float2 xr, amp, sum;
-                    float2 fr, aq, dq;
-#pragma unroll
-                    for (int k = 0; k < SF_QPT; ++k) {
-                        const float4 z = cz[c[r][k]];
-                        // (cos r_x, cos r_y) by angle addition
-                        const float2 cr2 = __ffma2_rn(make_float2(ra[r].z, ra[r].w), cq[k],
-                                                      __fmul2_rn(make_float2(rb[r].x, rb[r].y), sq[k]));
-                        float x = fmaf(cr2.x + cr2.y, z.z, z.w);       // Z-scaled line energy of r / (T ln 2)
-                        if (!TP0) x = fmaf(cr2.x * cr2.y, cd[c[r][k]], x);
-                        const float ex = ex2_approx(x);
-                        const float a = rb[r].z * fcqp[k];
-                        const float d = fmaf(rb[r].w, fqp[k], -a);
-                        const float w = UNIB ? z.x : fmaf(-vab[k], z.y, z.x * v2[k]);
-                        const float sm = upp[r] + mxq[k];
-                        if (k == 0) { xr.x = x; fr.x = ex; aq.x = a; dq.x = d; amp.x = w; sum.x = sm; }
-                        else        { xr.y = x; fr.y = ex; aq.y = a; dq.y = d; amp.y = w; sum.y = sm; }
-                    }
-                    const float2 g = __fadd2_rn(fr, one2);
-                    fr = make_float2(rcp_approx(g.x), rcp_approx(g.y));
-                    const float2 F = __ffma2_rn(fr, dq, aq);           // A + f_r (B - A)
-                    amp = __fmul2_rn(amp, F);
-                    // d0 = xi_j - E, E = x_q + x_r - x_p
-                    const float2 d0 = __ffma2_rn(xr, ntln2, sum);
-                    const float2 u = __ffma2_rn(d0, d0, nkchord);
-                    const float2 den = __ffma2_rn(__fmul2_rn(eta2x4, d0), d0, __fmul2_rn(u, u));
-                    acc = __ffma2_rn(__fmul2_rn(amp, u), make_float2(rcp_approx(den.x), rcp_approx(den.y)), acc);
-                }
+                pair_math(ra, rb, upp, c);
+            }
             }
         }
         vsum -= (double)acc.x + (double)acc.y;   // the chord term is -u / den
@@ -1197,15 +1300,47 @@ static qpfrg_status launch_sigma_fast(qpfrg_ctx *c, double T, const double *d_V,
     // below 1e-4, shrinking with N) and left out on the frequency grid.
     A.mirror = (jlist != nullptr && c->pb.n_theta % 2 == 0) ? (grid_mode ? 2 : 1) : 0;
     const bool unib = c->pb.P % (256 * SF_QPT) == 0;
+    // The flow's Z on the C4v-irreducible targets reads the patches of r from
+    // a table built on first use (one byte per target, p and q: N_irr M^2
+    // bytes, 126 GB at np96_n32), when it fits in 60 % of the free device
+    // memory and options.sigma_table >= 0; otherwise it decides them per pair.
+    // (record passes of a multiple of 8 records: P a multiple of 16, mirror halves included)
+    const bool rt_list = !grid_mode && jlist != nullptr && jlist == c->d_jirr && nj == c->n_irr &&
+                         c->pb.P % 16 == 0 && c->pb.P <= SF_PCH;
+    if (rt_list && !c->rtab_tried && c->opt.sigma_table >= 0) {
+        c->rtab_tried = true;
+        const size_t bytes = (size_t)nj * c->pb.N * (size_t)c->pb.P * (size_t)c->pb.M;
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && bytes <= fr / 10 * 6) {
+            if (cudaMalloc((void **)&c->d_rtab, bytes) == cudaSuccess) {
+                cudaError_t e = cudaFuncSetAttribute(rtab_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)kRtabSmem);
+                if (e != cudaSuccess) return cuda_fail(c, e, "rtab smem attribute");
+                prof_begin(c);
+                rtab_build_kernel<<<dim3(div_up(c->pb.M, 256), c->pb.N, nj), 256, kRtabSmem, c->stream>>>(A,
+                                                                                                        c->d_rtab);
+                prof_end(c, K_RTAB);
+                if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "rtab_build_kernel");
+            } else {
+                c->d_rtab = nullptr;
+                cudaGetLastError();   // not enough memory: decide per pair
+            }
+        }
+    }
+    const bool rt = rt_list && c->d_rtab != nullptr;
+    A.rtab = rt ? c->d_rtab : nullptr;
     using Kern = void (*)(SigmaFastArgs);
     Kern kern;
     if (grid_mode)
         kern = c->pb.tp == 0.0
                    ? (unib ? sigma_grid_fast_kernel<true, true> : sigma_grid_fast_kernel<true, false>)
                    : (unib ? sigma_grid_fast_kernel<false, true> : sigma_grid_fast_kernel<false, false>);
+    else if (rt)
+        kern = c->pb.tp == 0.0 ? (unib ? sigma_fast_kernel<true, true, true> : sigma_fast_kernel<true, false, true>)
+                               : (unib ? sigma_fast_kernel<false, true, true> : sigma_fast_kernel<false, false, true>);
     else
-        kern = c->pb.tp == 0.0 ? (unib ? sigma_fast_kernel<true, true> : sigma_fast_kernel<true, false>)
-                               : (unib ? sigma_fast_kernel<false, true> : sigma_fast_kernel<false, false>);
+        kern = c->pb.tp == 0.0 ? (unib ? sigma_fast_kernel<true, true, false> : sigma_fast_kernel<true, false, false>)
+                               : (unib ? sigma_fast_kernel<false, true, false> : sigma_fast_kernel<false, false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(c, e, "sigma_fast smem attribute");
     // grid mode: one CTA per (patch a, target) takes every q block, so that the

@@ -225,6 +225,22 @@ qpfrg_status loop_tasks(qpfrg_ctx *c, int qchunk, int *ntask)
 
 }  // namespace qpfrg
 
+extern "C" qpfrg_status qpfrg_sigma_table(qpfrg_t c, size_t *bytes, long long offset, long long count,
+                                          unsigned char *h_out)
+{
+    if (!c) return QPFRG_ERR_INVALID;
+    const size_t size = c->d_rtab ? (size_t)c->n_irr * c->pb.N * (size_t)c->pb.M * (size_t)c->pb.P : 0;
+    if (bytes) *bytes = size;
+    if (!h_out) return QPFRG_OK;
+    if (offset < 0 || count < 0 || (size_t)offset + (size_t)count > size) {
+        c->err = "qpfrg_sigma_table: range outside the table";
+        return QPFRG_ERR_INVALID;
+    }
+    cudaError_t e = cudaMemcpyAsync(h_out, c->d_rtab + offset, (size_t)count, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? QPFRG_OK : qpfrg::cuda_fail(c, e, "qpfrg_sigma_table");
+}
+
 extern "C" qpfrg_status qpfrg_rhs_work(qpfrg_t c, long long *loop_evals, long long *loop_evals_full,
                                        long long *rows_unreduced)
 {

@@ -298,3 +298,50 @@ def test_profiler_counts_launches():
         prof = api.qpfrg_profile(c.h)
     assert prof["bubble"][1] == 8 and prof["contract_pp"][1] == 8 and prof["rk_final"][1] == 2
     assert prof["bubble"][0] > 0
+
+
+def test_sigma_table_holds_the_fp64_projection():
+    """The self-energy's patch-of-r table (built by the first Z of a
+    C4v-symmetric state): 40 000 sampled entries against the oracle's FP64
+    projection of r = (k_j + p) - q (a byte N stands for patch 0), with the context's own exported
+    geometry; and Z with the table against Z decided per pair (1e-6: the
+    FP64 atomics of the CTA sums add in a run-dependent order)."""
+    import torch
+    N, n = 48, 16
+    o = Oracle(N, n, n)
+    res = []
+    for table in (0, -1):
+        with api.Context(N, n, n, U=3.0, lambda0=1.0, precision=api.QPFRG_MIXED, lambda_end=0.05, z_feedback=1,
+                         sigma_table=table) as c:
+            api.qpfrg_step(c.h, 2)
+            Z = zeros(N)
+            api.qpfrg_read_state(c.h, None, Z)
+            torch.cuda.synchronize()
+            size, _ = api.qpfrg_sigma_table(c.h)
+            if table == 0:
+                kf, fine = api.qpfrg_geometry(c.h)
+                M, P, nirr = len(fine), n * n, N // 8 + 1
+                assert size == nirr * N * M * P
+                rng = np.random.default_rng(17)
+                idx = np.sort(rng.integers(0, size, 40000))
+                got = np.array([api.qpfrg_sigma_table(c.h, int(x), 1)[1][0] for x in idx])
+            else:
+                assert size == 0
+        res.append(Z.cpu().numpy())
+    assert np.abs(res[0] - res[1]).max() < 1e-6
+    bad = 0
+    for x, g in zip(idx, got):
+        # byte (((j N + a) P/8 + i/8) M + iq) 8 + i % 8
+        word, i8 = divmod(int(x), 8)
+        grp, iq = divmod(word, M)
+        i = (grp % (P // 8)) * 8 + i8
+        a = (grp // (P // 8)) % N
+        j = grp // ((P // 8) * N)
+        b, t = divmod(iq, P)
+        q = b * P + (t % n) * n + t // n
+        p = a * P + i
+        rx = (kf[j, 0] + fine[p, 0]) - fine[q, 0]
+        ry = (kf[j, 1] + fine[p, 1]) - fine[q, 1]
+        # a byte N is the kernel's second slot of patch 0 (past the last ray)
+        bad += int(o.proj(rx, ry) != int(g) % N)
+    assert bad == 0
