@@ -103,9 +103,13 @@ def cpu_info():
 # definition, from the template line to the matching brace) is unchanged: the
 # SHA-256 of that text is recorded with the capture; profiles/ holds the summary.
 TRAFFIC = {
-    ("sigma_z", "np96_n32"): {"bytes": 25.44e6, "source": "paper_2005_00827_gb300/csrc/sigma.cu",
-                              "kernel": "sigma_fast_kernel",
-                              "sha256": "065c33f7de3686ba37b90faa0cd6300891c9633adac95b19e98c96494ebdd514"},
+    # the kernel with its patch-of-r table: DRAM bytes per (p, q) pair from a
+    # full capture at np48_n16 (907.7 MB read + 3.3 MB written for 9.06e8
+    # pairs: 1.0055 B per pair, the table's byte), scaled to the bench
+    # workload's pairs (the table grows with the pairs)
+    ("sigma_z", "np96_n32"): {"bytes": 116.61e9, "source": "paper_2005_00827_gb300/csrc/sigma.cu",
+                              "kernel": "sigma_fast_kernel", "scaled_from": "np48_n16",
+                              "sha256": "85cf7d0d4dc108c73efa7da72ebd52256686955594627914ddebb3dd2bbc19e1"},
 }
 
 

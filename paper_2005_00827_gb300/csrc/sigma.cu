@@ -595,7 +595,7 @@ __device__ __noinline__ int sf_slow_patch(const SigmaFastArgs &A, int jidx, int 
 // sums.  They depend on the geometry only (targets, fine grid), so one build
 // serves every later call.  Grid (ceil(M / 256), N, targets), 256 threads.
 constexpr size_t kRtabTabBytes = ((size_t)kProjW * kProjStride + 15) / 16 * 16;
-constexpr size_t kRtabSmem = kRtabTabBytes + (size_t)SF_SLOTS * sizeof(float2);
+constexpr size_t kRtabSmem = kRtabTabBytes + (size_t)SF_SLOTS * sizeof(float2);   // + P int2 records
 
 __global__ void __launch_bounds__(256) rtab_build_kernel(SigmaFastArgs A, uint8_t *__restrict__ rtab)
 {
@@ -606,6 +606,7 @@ __global__ void __launch_bounds__(256) rtab_build_kernel(SigmaFastArgs A, uint8_
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *tab = smem_raw;                                      // the cell table
     float2 *ray = reinterpret_cast<float2 *>(smem_raw + kRtabTabBytes); // rays between wedges
+    int2 *rec = reinterpret_cast<int2 *>(ray + SF_SLOTS);               // k_j + p of the patch (fixed point)
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(A.ptab);
         uint4 *dst = reinterpret_cast<uint4 *>(tab);
@@ -614,6 +615,10 @@ __global__ void __launch_bounds__(256) rtab_build_kernel(SigmaFastArgs A, uint8_
         for (int i = tid; i < SF_SLOTS; i += blockDim.x) {
             const float4 bd = A.bnd[i == N ? 0 : (i < N ? i : 0)];
             ray[i] = i <= N ? make_float2(bd.x, bd.z) : make_float2(0.f, 0.f);
+        }
+        for (int i = tid; i < PP; i += blockDim.x) {
+            const float4 k4 = A.kp[(long)jidx * M + a * PP + i];
+            rec[i] = make_int2(angle_fx((double)k4.x + (double)k4.y), angle_fx((double)k4.z + (double)k4.w));
         }
     }
     __syncthreads();
@@ -629,11 +634,10 @@ __global__ void __launch_bounds__(256) rtab_build_kernel(SigmaFastArgs A, uint8_
         unsigned w[2] = {0u, 0u};
         for (int i = i0; i < i0 + 8; ++i) {
             const int p = a * PP + i;
-            const float4 k4 = A.kp[(long)jidx * M + p];
-            const int kx = angle_fx((double)k4.x + (double)k4.y), ky = angle_fx((double)k4.z + (double)k4.w);
+            const int2 kr = rec[i];
             float x, y;
             bool slow;
-            int c = fx_patch(kx, ky, qx, qy, tabc, ray, x, y, slow);
+            int c = fx_patch(kr.x, kr.y, qx, qy, tabc, ray, x, y, slow);
             if (slow) {
                 const bool edge = fmaxf(fabsf(x), fabsf(y)) > kFxEdge;
                 c = sf_slow_patch(A, jidx, j, p, qq, x * kRadPerFx, y * kRadPerFx, edge, A.bnd);
@@ -1313,12 +1317,13 @@ static qpfrg_status launch_sigma_fast(qpfrg_ctx *c, double T, const double *d_V,
         size_t fr = 0, tot = 0;
         if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && bytes <= fr / 10 * 6) {
             if (cudaMalloc((void **)&c->d_rtab, bytes) == cudaSuccess) {
+                const size_t smem_b = kRtabSmem + (size_t)c->pb.P * sizeof(int2);
                 cudaError_t e = cudaFuncSetAttribute(rtab_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     (int)kRtabSmem);
+                                                     (int)smem_b);
                 if (e != cudaSuccess) return cuda_fail(c, e, "rtab smem attribute");
                 prof_begin(c);
-                rtab_build_kernel<<<dim3(div_up(c->pb.M, 256), c->pb.N, nj), 256, kRtabSmem, c->stream>>>(A,
-                                                                                                        c->d_rtab);
+                rtab_build_kernel<<<dim3(div_up(c->pb.M, 256), c->pb.N, nj), 256, smem_b, c->stream>>>(A,
+                                                                                                      c->d_rtab);
                 prof_end(c, K_RTAB);
                 if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "rtab_build_kernel");
             } else {
