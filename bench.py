@@ -58,10 +58,10 @@ SIGMA_FP32_PER_PAIR, SIGMA_MUFU_PER_PAIR = 20, 4
 # included (ncu smsp__inst_executed x 32 / evaluations at np96_n32:
 # 5.71e8 x 32 / 2.27e8)
 BUBBLE_ISSUE_AS_BUILT, SIGMA_ISSUE_AS_BUILT = 80, 36
-# the self-energy pair with its patch read from the patch-of-r table: the 18
-# slots that locate r's patch give way to one 8-byte load per 8 records and
-# a byte extraction (about 2 slots per pair)
-SIGMA_ISSUE_AS_BUILT_TABLE = 20
+# the self-energy pair with its patch read from the patch-of-r table: measured
+# instructions per pair (ncu smsp__inst_executed x 32 / pairs at np48_n16:
+# 7.03e8 x 32 / 9.06e8)
+SIGMA_ISSUE_AS_BUILT_TABLE = 24.8
 ISSUE_LANES_PER_SM, MUFU_PER_SM, N_SM = 128, 16, 152
 
 
@@ -569,6 +569,52 @@ def shell224(api, inputs, stream):
     return res
 
 
+def run_fig4(args):
+    """The comparison grid of Fig. 4 (Sec. 3.2) as our own curves: the
+    crossover scale U*(T) of the interaction flow at fixed T (U* = g_c^2 U,
+    g_c where the largest coupling first exceeds 100 U, the paper's
+    criterion), for the particle-hole channels alone, the full one-loop flow,
+    self-energy feedback through the single-scale propagator (the Sigma ODE
+    with Z feedback) and the Katanin-corrected flow; 48 angular patches (8 x 8
+    fine points per patch) and 32 x 7 = 224 energy-shell patches (4 x 4 fine
+    points per patch).  Prints its own line."""
+    import time
+
+    import torch
+
+    from paper_2005_00827_gb300 import api
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    U, dg, g_end = 1.0, 0.05, 6.0
+    temps = (0.1, 0.15, 0.2, 0.3)
+    variants = {
+        "ph_only": dict(channel_mask=api.QPFRG_CH_CR | api.QPFRG_CH_D),
+        "one_loop": dict(),
+        "s_feedback": dict(sigma_ode=1, z_feedback=1),
+        "katanin": dict(sigma_ode=1, z_feedback=1, katanin=1),
+    }
+    grids = {"np48": dict(N=48, n=8), "np224_s7": dict(N=224, n=4, mode=api.QPFRG_GRID_SHELL, n_shell=7)}
+    t0 = time.time()
+    curves = {}
+    for gname, gkw in grids.items():
+        for vname, vkw in variants.items():
+            pts = []
+            for T in temps:
+                kw = dict(gkw)
+                N, n = kw.pop("N"), kw.pop("n")
+                with api.Context(N, n, n, U=U, lambda0=0.0, regulator=api.QPFRG_REG_INTERACTION, T_fixed=T,
+                                 eta=0.05, step=dg, lambda_end=g_end, stop_abs_v=100.0 * U,
+                                 precision=api.QPFRG_MIXED, stream=stream.cuda_stream, **kw, **vkw) as c:
+                    r = api.qpfrg_flow(c.h).as_dict()
+                pts.append({"T": T, "status": r["status"], "g_c": r["lambda_c"] if r["status"] == "DIVERGED" else None,
+                            "U_star": r["lambda_c"] ** 2 * U if r["status"] == "DIVERGED" else None,
+                            "steps": r["steps"]})
+            curves[f"{vname}@{gname}"] = pts
+    print(json.dumps({"mode": "fig4", "criterion": "max|V| > 100 U, U* = g_c^2 U", "U": U, "dg": dg,
+                      "precision": "mixed", "curves": curves, "seconds": time.time() - t0}))
+
+
 def run_sweep(args):
     """The 128-flow phase-boundary sweep (N_p in {24,48,72,96}, 16 x 16 fine
     grid, Z = 1, seeded draws) through qpfrg_flow_batch: complete flows/s."""
@@ -721,6 +767,8 @@ def main():
         run_reference(args)
     elif args.rhs_only:
         run_rhs_only(args)
+    elif args.workload == "fig4":
+        run_fig4(args)
     elif args.workload == "sweep128":
         run_sweep(args)
     else:
