@@ -588,6 +588,7 @@ def run_fig4(args):
     stream = torch.cuda.current_stream()
     U, dg, g_end = 1.0, 0.05, 6.0
     temps = (0.1, 0.15, 0.2, 0.3)
+    prec = {"mixed": api.QPFRG_MIXED, "tc": api.QPFRG_MIXED_TC, "fp64": api.QPFRG_FP64}[args.precision]
     variants = {
         "ph_only": dict(channel_mask=api.QPFRG_CH_CR | api.QPFRG_CH_D),
         "one_loop": dict(),
@@ -605,14 +606,14 @@ def run_fig4(args):
                 N, n = kw.pop("N"), kw.pop("n")
                 with api.Context(N, n, n, U=U, lambda0=0.0, regulator=api.QPFRG_REG_INTERACTION, T_fixed=T,
                                  eta=0.05, step=dg, lambda_end=g_end, stop_abs_v=100.0 * U,
-                                 precision=api.QPFRG_MIXED, stream=stream.cuda_stream, **kw, **vkw) as c:
+                                 precision=prec, stream=stream.cuda_stream, **kw, **vkw) as c:
                     r = api.qpfrg_flow(c.h).as_dict()
                 pts.append({"T": T, "status": r["status"], "g_c": r["lambda_c"] if r["status"] == "DIVERGED" else None,
                             "U_star": r["lambda_c"] ** 2 * U if r["status"] == "DIVERGED" else None,
                             "steps": r["steps"]})
             curves[f"{vname}@{gname}"] = pts
     print(json.dumps({"mode": "fig4", "criterion": "max|V| > 100 U, U* = g_c^2 U", "U": U, "dg": dg,
-                      "precision": "mixed", "curves": curves, "seconds": time.time() - t0}))
+                      "precision": args.precision, "curves": curves, "seconds": time.time() - t0}))
 
 
 def run_sweep(args):
