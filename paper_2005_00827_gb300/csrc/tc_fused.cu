@@ -42,8 +42,9 @@ namespace qpfrg {
 
 namespace {
 
-constexpr int kProducers = 128;                 // threads forming A (one row each)
-constexpr int kFusedThreads = kProducers + 32;  // + the TMA / MMA warp
+constexpr int kProducers = 256;                 // threads forming A (two per row)
+constexpr int kMmaWarp = kProducers / 32;       // the TMA / MMA warp
+constexpr int kFusedThreads = kProducers + 32;
 constexpr uint32_t kRawBytes = tc::BM * tc::BK * 4;   // FP32 table block = hi + lo of A
 
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar)
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    if (warp == 4) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                          smem_u32(&tmem_slot)),
                      "r"(tmem_cols));
@@ -183,9 +184,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     const uint32_t tmem = tmem_slot;
     volatile int *abort_v = &abort_flag;
 
-    if (warp < 4) {
-        // ---- producers: thread tid owns row rr = tid of every block ----
-        const int rr = tid;
+    if (warp < kMmaWarp) {
+        // ---- producers: warp w owns rows 16 w .. 16 w + 15 of every block,
+        // lanes l and l + 16 the two halves (columns 0-31, 32-63) of row 16 w + l ----
+        const int lane = tid & 31;
+        const int rr = (warp << 4) | (lane & 15), hh = lane >> 4;
         const int Q = m0 + rr;
         const bool valid = Q < A.M;
         // raw row rr of the half h (columns 32 h .. 32 h + 31), 16-byte chunk c:
@@ -201,13 +204,14 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         const float *frow1 = VT + 2 * n3 + (long)(valid ? Q : 0) * N;
         int seg_lo[2], seg_n[2];
         factor_segments(A.ch, N, kb0, kb1, A.nkb_half, seg_lo, seg_n);
-        // staged: the thread copies its own factor row segments into shared
-        // memory once (row stride fw, odd: the lanes' rows hit distinct banks);
-        // only this thread reads them
+        // staged: the row's two threads copy its factor row segments into
+        // shared memory once (row stride fw, odd: the rows hit distinct banks);
+        // only they read them, after the warp's barrier
         float *fs = reinterpret_cast<float *>(sbase + (size_t)S * stage_bytes) + (size_t)rr * (STG ? A.fw : 0);
         if (STG) {
-            for (int t = 0; t < seg_n[0]; ++t) fs[t] = valid ? __ldg(frow0 + seg_lo[0] + t) : 0.f;
-            for (int t = 0; t < seg_n[1]; ++t) fs[seg_n[0] + t] = valid ? __ldg(frow1 + seg_lo[1] + t) : 0.f;
+            for (int t = hh; t < seg_n[0]; t += 2) fs[t] = valid ? __ldg(frow0 + seg_lo[0] + t) : 0.f;
+            for (int t = hh; t < seg_n[1]; t += 2) fs[seg_n[0] + t] = valid ? __ldg(frow1 + seg_lo[1] + t) : 0.f;
+            __syncwarp();
         }
         // factor of table column x (a or b) in half h
         auto factor = [&](int h, int x) -> float {
@@ -227,23 +231,27 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                 break;
             }
             unsigned char *st = sbase + (size_t)s * stage_bytes;
-            float v[64];
+            // this thread's half row: columns 32 hh .. 32 hh + 31
+            float v[32];
 #pragma unroll
-            for (int hh = 0; hh < 2; ++hh)
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const float4 x = *reinterpret_cast<const float4 *>(st + hh * (kRawBytes / 2) + raw_row +
-                                                                       ((c ^ sw) << 4));
-                    v[32 * hh + 4 * c + 0] = x.x;
-                    v[32 * hh + 4 * c + 1] = x.y;
-                    v[32 * hh + 4 * c + 2] = x.z;
-                    v[32 * hh + 4 * c + 3] = x.w;
-                }
-            // (a, b) of the block's first column; N8: a chunk of 8 columns
+            for (int c = 0; c < 8; ++c) {
+                const float4 x = *reinterpret_cast<const float4 *>(st + hh * (kRawBytes / 2) + raw_row +
+                                                                   ((c ^ sw) << 4));
+                v[4 * c + 0] = x.x;
+                v[4 * c + 1] = x.y;
+                v[4 * c + 2] = x.z;
+                v[4 * c + 3] = x.w;
+            }
+            // both halves of every row of the warp read before any is overwritten
+            // (the row's lo chunks 0-3 lie in the other half's bytes)
+            __syncwarp();
+            // (a, b) of the thread's first column; N8: a chunk of 8 columns
             // lies in one a and never passes N^2
-            int a = kk0 / N, b = kk0 - a * N;
+            const int kt0 = kk0 + 32 * hh;
+            int a = kt0 / N, b = kt0 - a * N;
 #pragma unroll
-            for (int kc = 0; kc < 8; ++kc) {
+            for (int kcl = 0; kcl < 4; ++kcl) {
+                const int kc = 4 * hh + kcl;
                 float f[8];
                 if (N8) {
                     if (A.ch == 1 && !STG) {
@@ -271,7 +279,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                 } else {
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
-                        f[e] = kk0 + 8 * kc + e < NN ? factor(h, A.ch == 1 ? b : a) : 0.f;
+                        f[e] = kt0 + 8 * kcl + e < NN ? factor(h, A.ch == 1 ? b : a) : 0.f;
                         if (++b == N) {
                             b = 0;
                             ++a;
@@ -282,8 +290,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                 uint32_t *hp = &hi.x, *lp = &lo.x;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const float x0 = v[8 * kc + 2 * q] * f[2 * q];
-                    const float x1 = v[8 * kc + 2 * q + 1] * f[2 * q + 1];
+                    const float x0 = v[8 * kcl + 2 * q] * f[2 * q];
+                    const float x1 = v[8 * kcl + 2 * q + 1] * f[2 * q + 1];
                     const __nv_bfloat162 hh = __floats2bfloat162_rn(x0, x1);
                     hp[q] = *reinterpret_cast<const uint32_t *>(&hh);
                     lp[q] = pack_bf16x2(x0 - __low2float(hh), x1 - __high2float(hh));
@@ -300,7 +308,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
             const int last = nkb - 1;
             if (!mbar_wait_abortable(smem_u32(&empty[last % S]), (uint32_t)((last / S) & 1), abort_v)) abort_flag = 1;
         }
-    } else if (tid == 128 && nkb > 0) {
+    } else if (tid == kProducers && nkb > 0) {
         // ---- table and B copies, MMAs ----
         const long tile0 = ((long)fam * A.RT + blockIdx.x) * A.KB;   // first k block of this row tile
         auto issue = [&](int kb, int s) {
@@ -378,13 +386,16 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (abort_flag) {
         if (tid == 0) atomicOr(A.err, 1u);
-    } else if (nkb > 0 && warp < 4) {
-        // epilogue: warp w reads accumulator rows 32w .. 32w+31 (its TMEM lanes)
-        const int Q = m0 + tid;
+    } else if (nkb > 0 && warp < kMmaWarp) {
+        // epilogue: warp w reads accumulator rows 32 (w % 4) .. +31 (the TMEM
+        // lanes of its rank in the warpgroup); warps 0-3 take the even
+        // 16-column chunks, warps 4-7 the odd ones
+        const int lane = tid & 31, wq = warp & 3;
+        const int Q = m0 + 32 * wq + lane;
         const int qa = Q / N, qb = Q - qa * N;
-        for (int c0 = 0; c0 < Npad; c0 += 16) {
+        for (int c0 = 16 * (warp >> 2); c0 < Npad; c0 += 32) {
             float v[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            tmem_ld16(tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)c0, v);
             if (Q < A.M) {
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
@@ -401,7 +412,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
-    if (warp == 4) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tmem_cols));
+    if (warp == kMmaWarp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tmem_cols));
 }
 
 // Shape of the launch of channel ch: stage count, split-K, grid; fills A's
