@@ -370,10 +370,12 @@ typedef struct {
  * self-energy of the wedge grid (q blocks per CTA) -- one untimed and one
  * timed launch each with CUDA events on the context's stream, keeps the
  * fastest in the context and reports them in *out (may be NULL).  The call
- * waits for its work.  It writes only scratch buffers (bubble tables or formed
- * operands, the RK stage buffer, the Z work buffer), never the flow state, and
- * the profiler does not count its launches.  QPFRG_ERR_INVALID for a bad
- * lambda (as qpfrg_rhs). */
+ * waits for its work.  It writes only scratch buffers (the loop-kernel table,
+ * the tensor-core B operands, the RK stage buffer, the Z work buffer) and, on
+ * its first self-energy launch, may build the patch-of-r table (a function of
+ * the geometry only, options.sigma_table); never the flow state, and the
+ * profiler does not count its launches.  QPFRG_ERR_INVALID for a bad lambda
+ * (as qpfrg_rhs). */
 qpfrg_status qpfrg_autotune(qpfrg_t ctx, double lambda, qpfrg_tuning *out);
 
 /* Apply launch shapes (e.g. those qpfrg_autotune found on another context of

@@ -306,7 +306,7 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
     // 2 nwarp rows (two transfers per warp) of N accumulators and a sink (slot
     // N) for lanes without points, so that a change of partner is one add of
     // the finished run; the row stride N + 2 is even, keeping every row 8-byte
-    // aligned for form_row's float2 reads
+    // aligned (an odd stride once misaligned 8-byte reads of these rows)
     const int RS = N + 2;
     R *rows = Zs + N;
     R *Ks = rows + 2 * nwarp * RS;                          // N Katanin factors
