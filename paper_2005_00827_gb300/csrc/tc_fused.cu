@@ -43,8 +43,9 @@ namespace qpfrg {
 namespace {
 
 constexpr int kProducers = 256;                 // threads forming A (two per row)
-constexpr int kMmaWarp = kProducers / 32;       // the TMA / MMA warp
-constexpr int kFusedThreads = kProducers + 32;
+constexpr int kMmaWarp = kProducers / 32;       // the MMA warp (one issuing thread)
+constexpr int kCopyWarp = kMmaWarp + 1;         // the TMA copy warp (one issuing thread)
+constexpr int kFusedThreads = kProducers + 64;
 constexpr uint32_t kRawBytes = tc::BM * tc::BK * 4;   // FP32 table block = hi + lo of A
 
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar)
@@ -209,8 +210,24 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         // only they read them, after the warp's barrier
         float *fs = reinterpret_cast<float *>(sbase + (size_t)S * stage_bytes) + (size_t)rr * (STG ? A.fw : 0);
         if (STG) {
-            for (int t = hh; t < seg_n[0]; t += 2) fs[t] = valid ? __ldg(frow0 + seg_lo[0] + t) : 0.f;
-            for (int t = hh; t < seg_n[1]; t += 2) fs[seg_n[0] + t] = valid ? __ldg(frow1 + seg_lo[1] + t) : 0.f;
+            // eight loads in flight per thread (a dependent one-by-one copy cost
+            // a DRAM round trip per value)
+            for (int g = 0; g < 2; ++g) {
+                const float *src = (g ? frow1 + seg_lo[1] : frow0 + seg_lo[0]);
+                float *dst = fs + (g ? seg_n[0] : 0);
+                const int n = seg_n[g];
+                for (int t0 = hh; t0 < n; t0 += 16) {
+                    float tmp[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int t = t0 + 2 * u;
+                        tmp[u] = (valid && t < n) ? __ldg(src + t) : 0.f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (t0 + 2 * u < n) dst[t0 + 2 * u] = tmp[u];
+                }
+            }
             __syncwarp();
         }
         // factor of table column x (a or b) in half h
@@ -308,10 +325,17 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
             const int last = nkb - 1;
             if (!mbar_wait_abortable(smem_u32(&empty[last % S]), (uint32_t)((last / S) & 1), abort_v)) abort_flag = 1;
         }
-    } else if (tid == kProducers && nkb > 0) {
-        // ---- table and B copies, MMAs ----
+    } else if (tid == kCopyWarp * 32 && nkb > 0) {
+        // ---- table and B copies: stage s is refilled as soon as the products
+        // of its previous block are done ----
         const long tile0 = ((long)fam * A.RT + blockIdx.x) * A.KB;   // first k block of this row tile
-        auto issue = [&](int kb, int s) {
+        int issued = 0;
+        for (; issued < nkb; ++issued) {
+            const int s = issued % S;
+            if (issued >= S &&
+                !mbar_wait_abortable(smem_u32(&empty[s]), (uint32_t)(((issued / S) - 1) & 1), abort_v))
+                break;
+            const int kb = kb0 + issued;
             const uint32_t sb = base + (uint32_t)s * stage_bytes;
             const bool second = A.ch == 2 && kb >= A.nkb_half;
             const int kbl = kb - (second ? A.nkb_half : 0);           // k block within the table row
@@ -323,9 +347,17 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
             const int yb = kb * (Npad / 2);
             tma_load_2d(sb + kRawBytes, mhi, 0, yb, rb);
             tma_load_2d(sb + kRawBytes + b_bytes, mlo, 0, yb, rb);
-        };
+        }
+        if (issued < nkb) {
+            abort_flag = 1;
+            // drain (bounded): the copies in flight land
+            for (int j = issued > S ? issued - S : 0; j < issued; ++j)
+                mbar_wait_bounded(smem_u32(&rfull[j % S]), (uint32_t)((j / S) & 1));
+        }
+    } else if (tid == kMmaWarp * 32 && nkb > 0) {
+        // ---- MMAs ----
         const uint32_t idesc = make_idesc(BM, Npad);
-        int issued = 0, consumed = 0;
+        int consumed = 0;
         bool ok = true;
         if (A.test_wait > 0) {
             // a wait that runs out: nothing ever arrives on `never`
@@ -336,7 +368,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                     break;
                 }
         }
-        for (; ok && issued < S && issued < nkb; ++issued) issue(kb0 + issued, issued);
         for (int i = 0; i < nkb && ok; ++i) {
             const int s = i % S;
             // the A rows formed, and (already complete by then) the B copies
@@ -361,22 +392,10 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
             }
             mma_commit(smem_u32(&empty[s]));
             consumed = i + 1;
-            // refill the stage of block i-1 once its products are done
-            if (i >= 1 && issued < nkb) {
-                const int j = i - 1;
-                if (!mbar_wait_abortable(smem_u32(&empty[j % S]), (uint32_t)((j / S) & 1), abort_v)) {
-                    ok = false;
-                    break;
-                }
-                issue(kb0 + issued, issued % S);
-                ++issued;
-            }
         }
         if (!ok) {
             abort_flag = 1;
-            // drain (bounded): the copies issued land and the products committed end
-            for (int j = consumed; j < issued; ++j)
-                mbar_wait_bounded(smem_u32(&rfull[j % S]), (uint32_t)((j / S) & 1));
+            // drain (bounded): the products committed end
             if (consumed > 0)
                 mbar_wait_bounded(smem_u32(&empty[(consumed - 1) % S]), (uint32_t)(((consumed - 1) / S) & 1));
         }
