@@ -17,18 +17,20 @@
 //
 // The table of the tensor-core path is stored in tiles (tc_table_index:
 // [f][row tile][k block][half][128 rows][32 floats]), so a 128 x 64 block is
-// two contiguous 16 KB boxes.  Per 64-wide k block and stage: one thread
-// (warp 4) loads the raw FP32 block (two TMA boxes, 128-byte swizzle) and the
-// B blocks (pre-formed per stage by tc_prep_kernel); the
-// producer warps 0-3 (one A row per thread) read their rows, scale by the
-// vertex factor and overwrite them, in place, with BF16 hi and lo in the
-// K-major 128-byte-swizzle layout of the MMA descriptors (both operands): a
-// row of 64 BF16 is 128 bytes, so row r of A_hi occupies exactly the bytes of
-// raw row r of columns 0-31 and row r of A_lo those of columns 32-63 -- each
-// thread overwrites only what it has read itself.  The thread of warp 4 then
-// issues the MMAs and commits each block to the stage's "empty" mbarrier,
-// after which the stage is refilled.  Every wait is bounded by a clock budget
-// and aborts the CTA (error flag, bounded drain, tensor memory freed).
+// two contiguous 16 KB boxes.  Per 64-wide k block and stage, one thread of the
+// copy warp (warp 9) loads the raw FP32 block (two TMA boxes, 128-byte
+// swizzle) and the B blocks (pre-formed per stage by tc_prep_kernel), refilling
+// a stage as soon as the products of its previous block have committed.  The
+// producer warps 0-7 (two threads per A row, one per 32-column half) read
+// their half rows, scale them by the vertex factors (staged once per CTA in
+// shared memory where they fit) and overwrite them, in place, with BF16 hi and
+// lo in the K-major 128-byte-swizzle layout of the MMA descriptors (both
+// operands): a row of 64 BF16 is 128 bytes, so row r of A_hi occupies exactly
+// the bytes of raw row r of columns 0-31 and row r of A_lo those of columns
+// 32-63 -- the two threads of a row read both halves before either writes.
+// One thread of warp 8 issues the MMAs and commits each block to the stage's
+// "empty" mbarrier.  Every wait is bounded by a clock budget and aborts the CTA
+// (error flag, bounded drain, tensor memory freed).
 #include <cuda_bf16.h>
 
 #include <algorithm>
