@@ -131,8 +131,12 @@ typedef struct {
     double timeout_s;            /* wall-clock budget of one qpfrg_flow call (<=0: none) */
     int autotune;                /* qpfrg_flow_batch: nonzero tunes the launch shapes of
                                     each patch-count group (qpfrg_autotune) before stepping */
-    int no_loop_symmetry;        /* nonzero: evaluate every loop-kernel row instead of one
-                                    row per C4v orbit of (transfer, patch) (wedge mode) */
+    int no_loop_symmetry;        /* 0: C4v reductions on (wedge and shell modes): one
+                                    loop-kernel row per orbit of (transfer, patch), and
+                                    with QPFRG_MIXED_TC and a C4v-symmetric V and Z one
+                                    contraction row per orbit of transfers, expanded;
+                                    2: the loop-kernel orbits only; other nonzero: every
+                                    loop-kernel row and every contraction row evaluated */
     /* interaction flow only: the self-energy ODE of App. A.2-A.5 (state V,
        Sigma, Sigma'; see qpfrg_read_sigma_flow) */
     int sigma_ode;               /* nonzero: carry Sigma, Sigma' and feed Z (z_feedback) */

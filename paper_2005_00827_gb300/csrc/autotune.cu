@@ -77,7 +77,8 @@ extern "C" qpfrg_status qpfrg_autotune(qpfrg_t c, double lambda, qpfrg_tuning *o
             for (int q : cand) {
                 if (q > NN && q != cand[0]) break;
                 c->tune.bubble_qchunk = q;
-                const double ms = time_launch(c, ev, [&] { return launch_bubbles(c, lambda, c->d_Z, c->c4v_state); }, st);
+                const double ms = time_launch(
+                    c, ev, [&] { return launch_bubbles(c, lambda, c->d_Z, c->c4v_state, nullptr, c->c4v_state); }, st);
                 if (ms < 0.0) break;
                 if (ms < best) {
                     best = ms;
@@ -88,7 +89,7 @@ extern "C" qpfrg_status qpfrg_autotune(qpfrg_t c, double lambda, qpfrg_tuning *o
             c->tune.bubble_qchunk = pick;
             best_b = best;
             // leave the loop-kernel rows of the fastest shape for the contraction below
-            if ((st = launch_bubbles(c, lambda, c->d_Z, c->c4v_state)) != QPFRG_OK) break;
+            if ((st = launch_bubbles(c, lambda, c->d_Z, c->c4v_state, nullptr, c->c4v_state)) != QPFRG_OK) break;
         }
         // tensor-core contraction: split-K per channel (0 = the wave-filling heuristic)
         if (c->opt.precision == QPFRG_MIXED_TC) {

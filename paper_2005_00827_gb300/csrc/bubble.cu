@@ -42,7 +42,9 @@ struct BubbleArgs {
     int qchunk;
     // C4v-reduced launch (symmetry.cu; tasks == nullptr: every row evaluated):
     // CTA task (family, patch, first representative, count); per
-    // representative its transfer and its image rows (Q', a' | g << 16)
+    // representative its transfer and its image rows (Q', a' | g << 16); img
+    // == nullptr with tasks: the contraction's representative rows, each
+    // written once to row kq of the compact table
     const int4 *tasks;
     const int *repQ;
     const int *nimg;
@@ -488,11 +490,13 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
             if (head) row_add(&row[key], v, A.fscale);
             __syncwarp();
             const int kq = Q0 + h * nwarp;
-            // the row's image rows: (Q', a', g) of the representative, or the row itself
-            const int nimg = A.repQ ? A.nimg[kq] : 1;
+            // the row's image rows: (Q', a', g) of the representative, or the
+            // row itself (unreduced launch: row Q; representative rows of the
+            // contraction's row orbits: row kq of the compact table)
+            const int nimg = A.img ? A.nimg[kq] : 1;
             for (int im = 0; im < nimg; ++im) {
                 int Qi = kq, ai = a, g = 0;
-                if (A.repQ) {
+                if (A.img) {
                     const int2 e = A.img[8 * (long)kq + im];
                     Qi = e.x;
                     ai = e.y & 0xffff;
@@ -539,7 +543,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) bubble_kernel(Bub
 template <typename R>
 static qpfrg_status launch_r(qpfrg_ctx *c, double lambda, const double *d_Z, const double *d_K, bool z_symmetric,
                              const FineTable<R> &fine, const TransferTable<R> &qpp, const TransferTable<R> &qph,
-                             R thr)
+                             R thr, bool compact = false)
 {
     const Problem &pb = c->pb;
     BubbleArgs<R> A{};
@@ -579,7 +583,14 @@ static qpfrg_status launch_r(qpfrg_ctx *c, double lambda, const double *d_Z, con
     // quasi-particle lines depend on Z, which must then be symmetric)
     const bool red = c->loop_red && (pb.propagator == QPFRG_PROP_PAPER || z_symmetric);
     int ntask = 0;
-    if (red) {
+    if (compact) {
+        // representative rows of the contraction's row orbits, all patches a
+        A.qchunk = std::max(8, A.qchunk);
+        qpfrg_status st = row_tasks(c, A.qchunk, &ntask);
+        if (st != QPFRG_OK) return st;
+        A.tasks = c->d_rtask;
+        A.repQ = c->d_rrep;
+    } else if (red) {
         qpfrg_status st = loop_tasks(c, A.qchunk, &ntask);
         if (st != QPFRG_OK) return st;
         A.tasks = c->d_ltask;
@@ -597,7 +608,7 @@ static qpfrg_status launch_r(qpfrg_ctx *c, double lambda, const double *d_Z, con
     auto kern = pb.tp == 0.0 ? bubble_kernel<R, true> : bubble_kernel<R, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(c, e, "bubble smem attribute");
-    const dim3 grid = red ? dim3(ntask) : dim3(pb.N, qchunks, 2);
+    const dim3 grid = (compact || red) ? dim3(ntask) : dim3(pb.N, qchunks, 2);
     prof_begin(c);
     kern<<<grid, nthr, smem, c->stream>>>(A);
     prof_end(c, K_BUBBLE);
@@ -605,15 +616,21 @@ static qpfrg_status launch_r(qpfrg_ctx *c, double lambda, const double *d_Z, con
     return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "bubble_kernel");
 }
 
-qpfrg_status launch_bubbles(qpfrg_ctx *c, double lambda, const double *d_Z, bool z_symmetric, const double *d_K)
+qpfrg_status launch_bubbles(qpfrg_ctx *c, double lambda, const double *d_Z, bool z_symmetric, const double *d_K,
+                            bool state_symmetric)
 {
+    c->rows_compact = false;
     if (c->opt.precision == QPFRG_FP64)
         return launch_r<double>(c, lambda, d_Z, d_K, z_symmetric, c->f64, c->qpp64, c->qph64, 1e-5);
     if (c->opt.precision == QPFRG_MIXED_TC) {
         qpfrg_status s = launch_tc_prep(c);       // B operands and V^T of this stage
         if (s != QPFRG_OK) return s;
     }
-    return launch_r<float>(c, lambda, d_Z, d_K, z_symmetric, c->f32, c->qpp32, c->qph32, 2e-2f);
+    const bool compact = c->rows_ok && state_symmetric && c->opt.precision == QPFRG_MIXED_TC;
+    const qpfrg_status s =
+        launch_r<float>(c, lambda, d_Z, d_K, z_symmetric, c->f32, c->qpp32, c->qph32, 2e-2f, compact);
+    c->rows_compact = compact && s == QPFRG_OK;
+    return s;
 }
 
 // The loop kernel alone into an explicit buffer (batched flows): the table

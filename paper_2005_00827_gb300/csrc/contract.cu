@@ -13,6 +13,8 @@
 // permuted view of V:
 //   pp: r = (i,j), n = l;  cr: r = (j,l), n = i;  d: r = (i,l), n = j.
 // Output: out[index(r,n)] += scale * sign * sum.
+#include <algorithm>
+
 #include "qpfrg_internal.h"
 
 namespace qpfrg {
@@ -170,15 +172,59 @@ static qpfrg_status launch_all(qpfrg_ctx *c, const VR *V, double scale, double *
     return QPFRG_OK;
 }
 
+// Expansion of the representative rows (row orbits, symmetry.cu): with a
+// C4v-symmetric state each channel's output is invariant, out(g t) = out(t),
+// so row Q = g rep of a channel at column n is the representative's row at
+// column g^-1 n.  One thread per output triple (k1, k2, k3) adds the three
+// channels' values: pp row (k1, k2) column k3, cr row (k3, k2) column k1,
+// d row (k1, k3) column k2 (the row/column roles of the channel GEMMs above).
+__global__ void rows_expand_kernel(const double *__restrict__ outc, const int *__restrict__ rowmap, int nr, int N,
+                                   int ns, unsigned channels, double *__restrict__ out)
+{
+    const long NN = (long)N * N, n3 = NN * N;
+    const long ch_stride = (long)nr * N;
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n3; t += (long)gridDim.x * blockDim.x) {
+        const int k1 = (int)(t / NN), k2 = (int)((t / N) % N), k3 = (int)(t % N);
+        double v = 0.0;
+        auto take = [&](int ch, int x, int y, int n) {
+            const int e = __ldg(rowmap + (long)x * N + y);
+            const int m = e & 0xffffff, g = e >> 24;
+            v += __ldg(outc + ch * ch_stride + (long)m * N + c4v_apply(c4v_inverse(g), n, N, ns));
+        };
+        if (channels & QPFRG_CH_PP) take(0, k1, k2, k3);
+        if (channels & QPFRG_CH_CR) take(1, k3, k2, k1);
+        if (channels & QPFRG_CH_D) take(2, k1, k3, k2);
+        out[t] += v;
+    }
+}
+
 qpfrg_status launch_contractions(qpfrg_ctx *c, const void *d_Vin, double scale, double *d_out)
 {
     if (c->opt.precision == QPFRG_MIXED_TC) {
         // the weighted tables of this stage, formed into A tiles inside the contraction
         const unsigned ch = c->pb.channels;
         qpfrg_status s = QPFRG_OK;
-        if ((ch & QPFRG_CH_PP) && (s = launch_tc_fused(c, 0, -scale, d_out, K_TC_PP))) return s;
-        if ((ch & QPFRG_CH_CR) && (s = launch_tc_fused(c, 1, -scale, d_out, K_TC_CR))) return s;
-        if ((ch & QPFRG_CH_D) && (s = launch_tc_fused(c, 2, scale, d_out, K_TC_D))) return s;
+        // representative rows only (row orbits): into the compact rows, then expanded
+        double *dst[3] = {d_out, d_out, d_out};
+        if (c->rows_compact) {
+            const long per = (long)c->n_rrep * c->pb.N;
+            cudaError_t e = cudaMemsetAsync(c->d_outc, 0, 3 * per * sizeof(double), c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "memset representative rows");
+            for (int k = 0; k < 3; ++k) dst[k] = c->d_outc + k * per;
+        }
+        if ((ch & QPFRG_CH_PP) && (s = launch_tc_fused(c, 0, -scale, dst[0], K_TC_PP))) return s;
+        if ((ch & QPFRG_CH_CR) && (s = launch_tc_fused(c, 1, -scale, dst[1], K_TC_CR))) return s;
+        if ((ch & QPFRG_CH_D) && (s = launch_tc_fused(c, 2, scale, dst[2], K_TC_D))) return s;
+        if (c->rows_compact) {
+            const long n3 = (long)c->pb.N * c->pb.N * c->pb.N;
+            const int grid = (int)std::min<long>((n3 + 255) / 256, 152L * 8);
+            prof_begin(c);
+            rows_expand_kernel<<<grid, 256, 0, c->stream>>>(c->d_outc, c->d_rowmap, c->n_rrep, c->pb.N,
+                                                            c->pb.n_shell, ch, d_out);
+            prof_end(c, K_ROWS_EXPAND);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_fail(c, e, "rows_expand_kernel");
+        }
         return QPFRG_OK;
     }
     if (c->opt.precision == QPFRG_FP64)

@@ -157,7 +157,7 @@ qpfrg_status gflow_enqueue_stages(qpfrg_ctx *c, double x, double h)
         const double gs = x + cst[st] * h;
         if ((s = zka(c, yst, gs)) != QPFRG_OK) return s;
         // vertex: loop kernels with Z and K on the lines, contraction
-        if ((s = launch_bubbles(c, gs, Zs, true, c->opt.katanin ? Ks : nullptr)) != QPFRG_OK) return s;
+        if ((s = launch_bubbles(c, gs, Zs, true, c->opt.katanin ? Ks : nullptr, c->c4v_state)) != QPFRG_OK) return s;
         if ((e = cudaMemsetAsync(c->d_k, 0, n3 * sizeof(double), c->stream)) != cudaSuccess)
             return cuda_fail(c, e, "memset k");
         if ((s = launch_contractions(c, Vin, 1.0, c->d_k)) != QPFRG_OK) return s;

@@ -18,7 +18,7 @@ namespace {
 const char *const kKernelNames[K_COUNT] = {
     "partner_map", "bubble", "contract_pp", "contract_cr", "contract_d", "sigma_z",
     "sigma_hist", "sigma_grid", "z_update", "rk_stage", "rk_final", "convert_f32",
-    "tc_prep", "tc_fused_pp", "tc_fused_cr", "tc_fused_d", "kp_table", "rtab_build",
+    "tc_prep", "tc_fused_pp", "tc_fused_cr", "tc_fused_d", "kp_table", "rtab_build", "rows_expand",
 };
 
 struct PendingEvent {
@@ -185,7 +185,7 @@ void qpfrg_destroy(qpfrg_t c)
                         c->tc.Bpp[0], c->tc.Bpp[1], c->tc.Bcr[0], c->tc.Bcr[1], c->tc.Bd[0], c->tc.Bd[1],
                         c->tc.VT, c->d_tc_err, c->d_xij, c->d_bnd, c->d_qxl, c->d_qyl, c->d_kp, c->d_kcs, c->d_xij_f,
                         c->d_ptab, c->d_jgrid, c->d_repgrid, c->d_lrepQ, c->d_lnimg, c->d_limg, c->d_ltask,
-                        c->d_rtab};
+                        c->d_rtab, c->d_rrep, c->d_rowmap, c->d_rtask, c->d_outc};
         for (void *p : ptrs)
             if (p) cudaFree(p);
     }
@@ -442,7 +442,18 @@ qpfrg_status qpfrg_rhs(qpfrg_t c, double lambda, const double *d_V, const double
         if ((s = launch_convert_f32(c, d_V, c->d_Vf, n3)) != QPFRG_OK) return s;
         Vin = c->d_Vf;
     }
-    if ((s = launch_bubbles(c, lambda, d_Z ? d_Z : c->d_ones, d_Z == nullptr)) != QPFRG_OK) return s;
+    // row orbits of the tensor-core contraction need a C4v-symmetric V and Z:
+    // tested on the device (relative 1e-12 of max|V|, max|Z|) and read back
+    bool sym = false;
+    if (c->rows_ok) {
+        if ((s = launch_state_check(c, d_V, d_Z ? d_Z : c->d_ones, true, 1e-12)) != QPFRG_OK) return s;
+        cudaError_t e = cudaMemcpyAsync(&c->h_red[4], &c->d_red[4], sizeof(unsigned long long),
+                                        cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "C4v test of the RHS input");
+        sym = c->h_red[4] == 0;
+    }
+    if ((s = launch_bubbles(c, lambda, d_Z ? d_Z : c->d_ones, d_Z == nullptr, nullptr, sym)) != QPFRG_OK) return s;
     cudaError_t e = cudaMemsetAsync(d_dV, 0, n3 * sizeof(double), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "memset dV");
     return launch_contractions(c, Vin, 1.0, d_dV);
@@ -530,7 +541,7 @@ static qpfrg_status enqueue_step(qpfrg_ctx *c)
         const double xs = x + cst[st] * h;
         const double lam = tflow ? std::exp(xs) : xs;
         const double scale = tflow ? lam : 1.0;   // dV/d ln T = T dV/dT
-        if ((s = launch_bubbles(c, lam, c->d_Z, c->c4v_state)) != QPFRG_OK) return s;
+        if ((s = launch_bubbles(c, lam, c->d_Z, c->c4v_state, nullptr, c->c4v_state)) != QPFRG_OK) return s;
         if ((e = cudaMemsetAsync(c->d_k, 0, n3 * sizeof(double), c->stream)) != cudaSuccess)
             return cuda_fail(c, e, "memset k");
         if ((s = launch_contractions(c, Vin, scale, c->d_k)) != QPFRG_OK) return s;
@@ -651,6 +662,7 @@ static qpfrg_status make_child(qpfrg_ctx *parent, double U, double lambda0, doub
     if (!c) return QPFRG_ERR_OOM;
     c->shares_geometry = true;
     c->rtab_tried = true;   // a child reads the parent's table (if built) and never builds its own
+    c->rows_ok = c->rows_compact = false;   // batched flows contract every row
     c->profiler = new (std::nothrow) Profiler();
     c->prof = false;
     for (auto &sl : c->slots) sl = ProfileSlot();

@@ -72,6 +72,7 @@ enum KernelId {
     K_TC_D,
     K_KP_TABLE,
     K_RTAB,
+    K_ROWS_EXPAND,
     K_COUNT
 };
 
@@ -195,6 +196,21 @@ struct LoopGroup {
     int fam, a, start, count;
 };
 
+// C4v element g = m | (reflection << 2) acting on patch j (ns energy shells
+// per wedge, N_a = N / ns wedges): wedge w -> +-w + m N_a / 4 (mod N_a), the
+// shell kept.
+__host__ __device__ inline int c4v_apply(int g, int j, int N, int ns)
+{
+    const int Na = N / ns, w = j / ns, sh = j - w * ns;
+    const int off = (g & 3) * (Na / 4);
+    int r = (g & 4) ? off - w : w + off;
+    r %= Na;
+    return (r < 0 ? r + Na : r) * ns + sh;
+}
+
+// inverse element: rotations by m -> by 4 - m; every reflection is an involution
+__host__ __device__ inline int c4v_inverse(int g) { return (g & 4) ? g : ((4 - (g & 3)) & 3); }
+
 }  // namespace qpfrg
 
 struct qpfrg_ctx {
@@ -243,6 +259,21 @@ struct qpfrg_ctx {
     int ltask_qchunk = 0, n_ltask = 0;
     long long loop_evals_red = 0;   // loop-kernel evaluations of one reduced RHS
     long loop_mismatch_rows = 0;    // rows evaluated by themselves (covariance broken)
+
+    // C4v row orbits of the tensor-core contraction (symmetry.cu): with a
+    // C4v-symmetric state (V, Z) every channel's output row Q = (x, y) at
+    // column n equals its representative's row at column g^-1 n, Q = g rep, so
+    // only representative rows are tabled and contracted and the result is
+    // expanded (contract.cu).  Built when every loop-kernel row is covariant.
+    bool rows_ok = false;
+    bool rows_compact = false;   // the table of the current RHS holds representative rows only
+    int n_rrep = 0;
+    int *d_rrep = nullptr;       // Q of each representative row
+    int *d_rowmap = nullptr;     // per Q: representative index | g << 24, Q = g rep
+    int4 *d_rtask = nullptr;     // (family, patch, first representative, count) per loop-kernel CTA
+    int rtask_qchunk = 0, n_rtask = 0;
+    double *d_outc = nullptr;    // [channel][representative][n] contraction rows
+    long long loop_evals_rows = 0;  // loop-kernel evaluations of one RHS on representative rows
 
     // bubble tables B[f][Q][a][b] (FP32 or FP64 according to precision)
     void *d_B = nullptr;
@@ -309,14 +340,18 @@ qpfrg_status upload_geometry(qpfrg_ctx *c);
 // z_symmetric: Z is C4v symmetric (needed by the reduced launch with
 // quasi-particle lines, whose loop kernels depend on Z).
 // d_K: Katanin factors of the interaction flow's S line (nullptr = 1).
+// state_symmetric: V and Z are C4v symmetric, so that (tensor-core precision,
+// row orbits built) only representative rows are tabled; sets c->rows_compact
+// for the contraction of the same RHS.
 qpfrg_status launch_bubbles(qpfrg_ctx *c, double lambda, const double *d_Z, bool z_symmetric,
-                            const double *d_K = nullptr);
+                            const double *d_K = nullptr, bool state_symmetric = false);
 
 qpfrg_status launch_loop_rows(qpfrg_ctx *c, double lambda, float *rows, const int *active);
 
 // symmetry.cu: C4v orbits of the loop-kernel rows and the reduced launch's tasks
 qpfrg_status build_loop_orbits(qpfrg_ctx *c);
 qpfrg_status loop_tasks(qpfrg_ctx *c, int qchunk, int *ntask);
+qpfrg_status row_tasks(qpfrg_ctx *c, int qchunk, int *ntask);
 
 // contract.cu: d_out (N^3 FP64) += scale * contraction of the bubble tables.
 // V input is FP64 (precision FP64) or FP32 (MIXED).

@@ -23,19 +23,6 @@
 
 namespace qpfrg {
 
-// g = m | (reflection << 2) acting on a patch index (ns shells per wedge)
-__host__ __device__ inline int c4v_apply(int g, int j, int N, int ns)
-{
-    const int Na = N / ns, w = j / ns, sh = j - w * ns;
-    const int off = (g & 3) * (Na / 4);
-    int r = (g & 4) ? off - w : w + off;
-    r %= Na;
-    return (r < 0 ? r + Na : r) * ns + sh;
-}
-
-// inverse element: rotations by m -> by 4 - m; every reflection is an involution
-__host__ __device__ inline int c4v_inverse(int g) { return (g & 4) ? g : ((4 - (g & 3)) & 3); }
-
 // flag[f][Q N + a] = 1 where the partner-map row (f, Q, a) is not the image
 // of its representative's row under g.  rep[Q N + a] = representative's Q N + a,
 // gof[Q N + a] = g with (Q, a) = g (representative).
@@ -70,10 +57,58 @@ __global__ void check_covariance_kernel(const uint8_t *__restrict__ part, const 
     }
 }
 
+// Row orbits of the tensor-core contraction: the representative of the
+// transfer pair Q = (x, y) is its image g Q = (g x, g y) with the smallest
+// index; rowmap[Q] = (representative index | g << 24) with Q = g rep.  Only
+// built when every loop-kernel row passed the covariance check, so that the
+// table rows of the images are exactly the representative's, permuted.
+static qpfrg_status build_row_orbits(qpfrg_ctx *c)
+{
+    const int N = c->pb.N, ns = c->pb.n_shell;
+    const long NN = (long)N * N;
+    std::vector<int> repidx(NN, -1), reps, rowmap(NN);
+    // in increasing Q the representative (the orbit's smallest index, <= Q)
+    // is always met first
+    for (long Q = 0; Q < NN; ++Q) {
+        const int x = (int)(Q / N), y = (int)(Q - (long)x * N);
+        long best = -1;
+        int bg = 0;
+        for (int g = 0; g < 8; ++g) {
+            const long gQ = (long)c4v_apply(g, x, N, ns) * N + c4v_apply(g, y, N, ns);
+            if (best < 0 || gQ < best) {
+                best = gQ;
+                bg = g;
+            }
+        }
+        if (best == Q) {
+            repidx[Q] = (int)reps.size();
+            reps.push_back((int)Q);
+        }
+        // bg maps Q onto its representative: Q = bg^-1 rep
+        rowmap[Q] = repidx[best] | (c4v_inverse(bg) << 24);
+    }
+    const int nr = (int)reps.size();
+    cudaError_t e;
+    if ((e = cudaMalloc((void **)&c->d_rrep, nr * sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc((void **)&c->d_rowmap, NN * sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc((void **)&c->d_rtask, (2L * N * ((nr + 7) / 8) + 8) * sizeof(int4))) != cudaSuccess ||
+        (e = cudaMalloc((void **)&c->d_outc, 3L * nr * N * sizeof(double))) != cudaSuccess)
+        return cuda_fail(c, e, "cudaMalloc(row orbits)");
+    e = cudaMemcpy(c->d_rrep, reps.data(), nr * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_rowmap, rowmap.data(), NN * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "upload row orbits");
+    c->n_rrep = nr;
+    c->rtask_qchunk = 0;
+    c->loop_evals_rows = 2LL * nr * c->pb.M;
+    c->rows_ok = true;
+    return QPFRG_OK;
+}
+
 qpfrg_status build_loop_orbits(qpfrg_ctx *c)
 {
     c->loop_red = false;
-    if ((c->pb.mode != QPFRG_GRID_WEDGE && c->pb.mode != QPFRG_GRID_SHELL) || c->opt.no_loop_symmetry)
+    if ((c->pb.mode != QPFRG_GRID_WEDGE && c->pb.mode != QPFRG_GRID_SHELL) ||
+        (c->opt.no_loop_symmetry != 0 && c->opt.no_loop_symmetry != 2))
         return QPFRG_OK;
     const int N = c->pb.N, ns = c->pb.n_shell;
     if ((N / ns) % 4 != 0) return QPFRG_OK;
@@ -196,6 +231,8 @@ qpfrg_status build_loop_orbits(qpfrg_ctx *c)
     c->loop_evals_red = evals;
     c->loop_mismatch_rows = mism;
     c->loop_red = true;
+    if (mism == 0 && c->opt.precision == QPFRG_MIXED_TC && c->opt.no_loop_symmetry == 0)
+        return build_row_orbits(c);
     return QPFRG_OK;
 }
 
@@ -223,6 +260,31 @@ qpfrg_status loop_tasks(qpfrg_ctx *c, int qchunk, int *ntask)
     return QPFRG_OK;
 }
 
+// Tasks of the loop-kernel launch on representative rows: (family, patch,
+// first representative, count) per CTA, chunks of qchunk rows (qchunk >= 8).
+qpfrg_status row_tasks(qpfrg_ctx *c, int qchunk, int *ntask)
+{
+    if (c->rtask_qchunk == qchunk) {
+        *ntask = c->n_rtask;
+        return QPFRG_OK;
+    }
+    if (qchunk < 8) {
+        c->err = "row tasks: chunk below 8 rows";
+        return QPFRG_ERR_INVALID;
+    }
+    std::vector<int4> t;
+    for (int f = 0; f < 2; ++f)
+        for (int a = 0; a < c->pb.N; ++a)
+            for (int s0 = 0; s0 < c->n_rrep; s0 += qchunk) t.push_back(make_int4(f, a, s0, std::min(qchunk, c->n_rrep - s0)));
+    cudaError_t e = cudaMemcpyAsync(c->d_rtask, t.data(), t.size() * sizeof(int4), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "upload row tasks");
+    c->rtask_qchunk = qchunk;
+    c->n_rtask = (int)t.size();
+    *ntask = c->n_rtask;
+    return QPFRG_OK;
+}
+
 }  // namespace qpfrg
 
 extern "C" qpfrg_status qpfrg_sigma_table(qpfrg_t c, size_t *bytes, long long offset, long long count,
@@ -246,7 +308,7 @@ extern "C" qpfrg_status qpfrg_rhs_work(qpfrg_t c, long long *loop_evals, long lo
 {
     if (!c) return QPFRG_ERR_INVALID;
     const long long full = 2LL * c->pb.N * c->pb.N * c->pb.M;
-    if (loop_evals) *loop_evals = c->loop_red ? c->loop_evals_red : full;
+    if (loop_evals) *loop_evals = c->rows_compact ? c->loop_evals_rows : (c->loop_red ? c->loop_evals_red : full);
     if (loop_evals_full) *loop_evals_full = full;
     if (rows_unreduced) *rows_unreduced = c->loop_red ? c->loop_mismatch_rows : 0;
     return QPFRG_OK;

@@ -82,6 +82,10 @@ struct TcFusedArgs {
     int nkb_half;                     // k blocks per half of the d reduction (Kp / 64)
     long RT, KB;                      // row tiles and k blocks per family of the tiled table
     int ch;                           // 0 pp, 1 cr, 2 d
+    // row orbits: A row m is the transfer pair rows[m] (table row m of the
+    // compact table), output row m of out[m][n]; nullptr: row m is Q = m,
+    // written to the channel's place in the N^3 output
+    const int *rows;
     const float *Vf, *VT;             // stage vertex [k1][k2][k3]; factor tables of cr and d (tc_prep)
     int fw;                           // row stride of the staged factor rows (odd), 0: not staged
     double *out;
@@ -192,8 +196,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         // lanes l and l + 16 the two halves (columns 0-31, 32-63) of row 16 w + l ----
         const int lane = tid & 31;
         const int rr = (warp << 4) | (lane & 15), hh = lane >> 4;
-        const int Q = m0 + rr;
-        const bool valid = Q < A.M;
+        const bool valid = m0 + rr < A.M;
+        const int Q = !valid ? 0 : (A.rows ? A.rows[m0 + rr] : m0 + rr);   // transfer pair of the row
         // raw row rr of the half h (columns 32 h .. 32 h + 31), 16-byte chunk c:
         // h 16 KB + rr 128 + (c ^ (rr % 8)) 16 (128-byte swizzle); A_hi row rr,
         // 8-wide k chunk kc: rr 128 + (kc ^ (rr % 8)) 16, A_lo the same + 16 KB
@@ -203,8 +207,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         // this row's factor rows (per half of the reduction) and the x ranges
         // the CTA's k blocks touch
         const long n3 = (long)NN * N;
-        const float *frow0 = (A.ch == 0 ? Vf : (A.ch == 1 ? VT : VT + n3)) + (long)(valid ? Q : 0) * N;
-        const float *frow1 = VT + 2 * n3 + (long)(valid ? Q : 0) * N;
+        const float *frow0 = (A.ch == 0 ? Vf : (A.ch == 1 ? VT : VT + n3)) + (long)Q * N;
+        const float *frow1 = VT + 2 * n3 + (long)Q * N;
         int seg_lo[2], seg_n[2];
         factor_segments(A.ch, N, kb0, kb1, A.nkb_half, seg_lo, seg_n);
         // staged: the row's two threads copy its factor row segments into
@@ -412,7 +416,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         // lanes of its rank in the warpgroup); warps 0-3 take the even
         // 16-column chunks, warps 4-7 the odd ones
         const int lane = tid & 31, wq = warp & 3;
-        const int Q = m0 + 32 * wq + lane;
+        const int Q = m0 + 32 * wq + lane;          // row (compact index with row orbits)
         const int qa = Q / N, qb = Q - qa * N;
         for (int c0 = 16 * (warp >> 2); c0 < Npad; c0 += 32) {
             float v[16];
@@ -423,7 +427,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                     const int n = c0 + q;
                     if (n >= A.Ncol) continue;
                     long o;
-                    if (A.ch == 0) o = (long)Q * N + n;                          // (i, j, n)
+                    if (A.ch == 0 || A.rows) o = (long)Q * N + n;                // (i, j, n); compact rows [m][n]
                     else if (A.ch == 1) o = (long)n * NN + (long)qb * N + qa;     // (n, j, l)
                     else o = ((long)qa * N + n) * N + qb;                         // (i, n, l)
                     atomicAdd(&out[o], scale * (double)v[q]);
@@ -448,7 +452,7 @@ static qpfrg_status launch_fused(qpfrg_ctx *c, int ch, TcFusedArgs &A, int nz, i
         c->err = "tensor-core contraction: unsupported shape";
         return QPFRG_ERR_UNSUPPORTED;
     }
-    const int M = (int)NN;
+    const int M = A.rows ? c->n_rrep : (int)NN;
     const int mtiles = div_up(M, tc::BM);
     const int nkb = (int)(Kp / tc::BK);
     const int nkb_half = (int)(t.Kp / tc::BK);
@@ -531,6 +535,7 @@ qpfrg_status launch_tc_fused(qpfrg_ctx *c, int ch, double scale, double *out, in
     A.VT = c->tc.VT;
     A.out = out;
     A.scale = scale;
+    A.rows = c->rows_compact ? c->d_rrep : nullptr;
     return launch_fused(c, ch, A, 1, kid);
 }
 

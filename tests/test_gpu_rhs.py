@@ -128,15 +128,18 @@ def test_loop_symmetry_matches_unreduced(case, prec):
     otherwise.  Checked on qpfrg_rhs and on one flow step from a symmetric
     (V, Z) state (the path that reduces with quasi-particle lines, whose loop
     kernels depend on Z); the work report says how many evaluations the
-    reduced RHS does."""
+    reduced RHS does.  With tensor cores the symmetric state also takes the
+    row orbits of the contraction (one output row per orbit of transfer pairs,
+    expanded); no_loop_symmetry = 2 keeps the loop-kernel orbits only."""
     import torch
     N, nt, nr, reg, prop, lam = case
-    if prec == api.QPFRG_MIXED_TC and (N * N) % 8:
+    tc = prec == api.QPFRG_MIXED_TC
+    if tc and (N * N) % 8:
         pytest.skip("tensor-core path needs N^2 % 8 == 0")
     V = inputs.random_vertex(N, 2.0, seed=N + 1, c4v=True)
     Z = inputs.z_profile(N, "aniso")
     out, step, work = {}, {}, {}
-    for nosym in (0, 1):
+    for nosym in ((0, 1, 2) if tc else (0, 1)):
         opts = dict(precision=prec, propagator=prop, T_fixed=0.15, no_loop_symmetry=nosym)
         lam0 = 0.0 if reg == 1 else 1.0
         if reg == 1:
@@ -153,10 +156,17 @@ def test_loop_symmetry_matches_unreduced(case, prec):
             step[nosym] = Vs.cpu().numpy() - V.ravel()
             work[nosym] = api.qpfrg_rhs_work(ctx.h)
     tol = 1e-12 if prec == api.QPFRG_FP64 else 1e-5
-    assert normwise(out[0], out[1]) < tol
-    assert normwise(step[0], step[1]) < tol
+    for k in out:
+        assert normwise(out[k], out[1]) < tol
+        assert normwise(step[k], step[1]) < tol
     full = 2 * N * N * N * nt * nr
     assert work[1]["loop_evals"] == full and work[0]["loop_evals_full"] == full
     if nt % 2 == 0:
         assert work[0]["rows_unreduced"] == 0
         assert work[0]["loop_evals"] < full / 6
+        if tc:
+            # row orbits: every patch of each representative transfer pair
+            maps = inputs.c4v_patch_maps(N)
+            reps = {min(g[x] * N + g[y] for g in maps) for x in range(N) for y in range(N)}
+            assert work[0]["loop_evals"] == 2 * len(reps) * N * nt * nr
+            assert work[2]["loop_evals"] < full / 6 and work[2]["loop_evals"] != work[0]["loop_evals"]

@@ -29,18 +29,28 @@ def normwise(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
-@pytest.mark.parametrize("case", [(16, 4, 4, 0, 7), (24, 4, 6, 0, 7), (16, 1, 1, 1, 7), (16, 4, 4, 0, 1),
-                                  (16, 4, 4, 0, 2), (16, 4, 4, 0, 4), (36, 1, 1, 1, 7), (20, 2, 4, 0, 7)],
-                         ids=["w16", "w24_ragged", "lat4", "pp_only", "cr_only", "d_only", "lat6", "w20_ragged_k"])
+@pytest.mark.parametrize("case", [(16, 4, 4, 0, 7, 1), (24, 4, 6, 0, 7, 1), (16, 1, 1, 1, 7, 0), (16, 4, 4, 0, 1, 1),
+                                  (16, 4, 4, 0, 2, 1), (16, 4, 4, 0, 4, 1), (36, 1, 1, 1, 7, 0), (20, 2, 4, 0, 7, 1),
+                                  (16, 4, 4, 0, 7, 0), (24, 4, 6, 0, 7, 0), (20, 2, 4, 0, 2, 0)],
+                         ids=["w16", "w24_ragged", "lat4", "pp_only", "cr_only", "d_only", "lat6", "w20_ragged_k",
+                              "w16_asym", "w24_asym", "w20_cr_asym"])
 def test_tc_rhs_matches_oracle(case):
-    N, nt, nr, mode, ch = case
+    """Symmetric (V, Z) in wedge mode take the row orbits of the contraction
+    (representative rows, expanded); the asymmetric vertices and the lattice
+    take every row."""
+    N, nt, nr, mode, ch, sym = case
     T = 0.25
-    V = inputs.random_vertex(N, 2.0, seed=N + 3, c4v=(mode == 0))
+    V = inputs.random_vertex(N, 2.0, seed=N + 3, c4v=bool(sym))
     Z = inputs.z_profile(N, "aniso") if mode == 0 else np.random.default_rng(1).uniform(0.8, 1.0, N)
     ref = Oracle(N, nt, nr, mode=mode, channels=ch).rhs(T, V, Z)
     with api.Context(N, nt, nr, U=2.0, mode=mode, precision=TC, channel_mask=ch) as ctx:
         got = gpu_rhs(ctx, T, V, Z)
+        evals = api.qpfrg_rhs_work(ctx.h)["loop_evals"]
     assert normwise(got, ref) < 1e-4
+    if mode == 0:
+        maps = inputs.c4v_patch_maps(N)
+        reps = {min(g[x] * N + g[y] for g in maps) for x in range(N) for y in range(N)}
+        assert (evals == 2 * len(reps) * N * nt * nr) == bool(sym)
 
 
 def test_tc_rhs_full_size_sampled():
