@@ -385,15 +385,20 @@ def run_qpfrg(args):
     tc = [k for k in ("tc_fused_pp", "tc_fused_cr", "tc_fused_d") if k in kern]
     if len(tc) == 3:
         # The channel GEMMs stream the FP32 weighted table: pp its pp family
-        # (N^4 floats), cr the ph family, d the ph family twice (K = 2 N^2):
-        # 16 N^4 bytes per RHS, against the HBM copy peak.  On the tensor
-        # cores: three BF16 products (hi hi, hi lo, lo hi) of N^2 rows, N
-        # columns and K = N^2 (pp, cr) + 2 N^2 (d): 24 N^5 flop per RHS.
-        nbytes, flop = 16.0 * N ** 4, 24.0 * N ** 5
+        # (R rows of N^2 floats), cr the ph family, d the ph family twice
+        # (K = 2 N^2): 16 R N^2 bytes per RHS, against the HBM copy peak.  On
+        # the tensor cores: three BF16 products (hi hi, hi lo, lo hi) of R rows,
+        # N columns and K = N^2 (pp, cr) + 2 N^2 (d): 24 R N^3 flop per RHS.
+        # R = N^2, or the row orbits of a C4v-symmetric state (their table,
+        # written by the loop kernels just before, mostly stays in L2).
+        R = float(work.get("contraction_rows") or N * N)
+        nbytes, flop = 16.0 * R * N ** 2, 24.0 * R * N ** 3
         t_s = sum(kern[k][0] / kern[k][1] for k in tc) / 1e3
         bf16 = float(peaks.get("bf16_tflops", 1900.0))
         rhs_roof["tc_fused"] = {"bound": "hbm", "achieved": nbytes / t_s / 1e9, "peak": hbm, "unit": "GB/s",
                                 "frac": nbytes / t_s / 1e9 / hbm, "bytes_per_rhs": nbytes, "ms_per_rhs": t_s * 1e3,
+                                "rows": R, "expand_ms_per_rhs": (kern["rows_expand"][0] / kern["rows_expand"][1]
+                                                                 if "rows_expand" in kern else 0.0),
                                 "peak_source": f"{peak_kind} hbm_gbs",
                                 "tensor": {"achieved": flop / t_s / 1e12, "peak": bf16, "unit": "TFLOP/s",
                                            "frac": flop / t_s / 1e12 / bf16, "flop_per_rhs": flop,

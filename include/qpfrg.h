@@ -326,15 +326,22 @@ qpfrg_status qpfrg_profile_get(qpfrg_t ctx, int id, double *ms, long long *launc
  * checks byte by byte on its partner maps at creation (rows that differ are
  * evaluated by themselves; C4v moves the wedge of a patch and keeps its
  * energy shell).  With quasi-particle lines (QPFRG_PROP_QP) the
- * reduction needs a C4v-symmetric Z.
- *   loop_evals: loop-kernel evaluations of one reduced RHS;
+ * reduction needs a C4v-symmetric Z.  With QPFRG_MIXED_TC, every row
+ * covariant and a C4v-symmetric V and Z (the flow's state, or a qpfrg_rhs
+ * input that passes a device test at 1e-12 relative), each channel's output
+ * is C4v invariant too: then only one output row per orbit of transfer pairs
+ * Q = (x, y) is tabled (all its patches a) and contracted, and every other
+ * row is its representative's with the columns permuted (row orbits).
+ *   loop_evals: loop-kernel evaluations of the context's last RHS;
  *   loop_evals_full: 2 N^2 M, the evaluations of the unreduced RHS;
  *   rows_unreduced: rows evaluated by themselves because the covariance check
- *     failed for them.
+ *     failed for them;
+ *   contraction_rows: rows of each channel GEMM in the last RHS (N^2, or the
+ *     number of row orbits).
  * All outputs may be NULL; loop_evals equals loop_evals_full when the
  * reduction is off (lattice mode, no_loop_symmetry). */
 qpfrg_status qpfrg_rhs_work(qpfrg_t ctx, long long *loop_evals, long long *loop_evals_full,
-                            long long *rows_unreduced);
+                            long long *rows_unreduced, long long *contraction_rows);
 
 /* The patch-of-r table of the flow's self-energy (options.sigma_table),
  * for verification: *bytes = its size (0 while not built: it is built by the

@@ -139,7 +139,7 @@ def load(build_if_missing: bool = True):
     L.qpfrg_read_sigma_flow.restype = C.c_int
     L.qpfrg_spectral.argtypes = [_P, _P, _P, _P, _P, _P]
     L.qpfrg_spectral.restype = C.c_int
-    L.qpfrg_rhs_work.argtypes = [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
+    L.qpfrg_rhs_work.argtypes = [_P] + [C.POINTER(C.c_longlong)] * 4
     L.qpfrg_sigma_table.argtypes = [_P, C.POINTER(C.c_size_t), C.c_longlong, C.c_longlong, _P]
     L.qpfrg_sigma_table.restype = C.c_int
     L.qpfrg_rhs_work.restype = C.c_int
@@ -316,11 +316,12 @@ def qpfrg_read_sigma_flow(ctx, slopes, sigma, zka):
 
 
 def qpfrg_rhs_work(ctx) -> dict:
-    """Loop-kernel evaluations of one RHS (C4v-reduced and full) and the rows
-    evaluated by themselves because their partner maps broke covariance."""
-    a, b, r = C.c_longlong(), C.c_longlong(), C.c_longlong()
-    _check(ctx, load().qpfrg_rhs_work(ctx, C.byref(a), C.byref(b), C.byref(r)))
-    return dict(loop_evals=a.value, loop_evals_full=b.value, rows_unreduced=r.value)
+    """Loop-kernel evaluations of the last RHS (C4v-reduced) and of the full
+    one, the rows evaluated by themselves because their partner maps broke
+    covariance, and the rows of each channel GEMM (N^2, or the row orbits)."""
+    a, b, r, m = C.c_longlong(), C.c_longlong(), C.c_longlong(), C.c_longlong()
+    _check(ctx, load().qpfrg_rhs_work(ctx, C.byref(a), C.byref(b), C.byref(r), C.byref(m)))
+    return dict(loop_evals=a.value, loop_evals_full=b.value, rows_unreduced=r.value, contraction_rows=m.value)
 
 
 def qpfrg_sigma_table(ctx, offset=0, count=0):

@@ -304,12 +304,13 @@ extern "C" qpfrg_status qpfrg_sigma_table(qpfrg_t c, size_t *bytes, long long of
 }
 
 extern "C" qpfrg_status qpfrg_rhs_work(qpfrg_t c, long long *loop_evals, long long *loop_evals_full,
-                                       long long *rows_unreduced)
+                                       long long *rows_unreduced, long long *contraction_rows)
 {
     if (!c) return QPFRG_ERR_INVALID;
     const long long full = 2LL * c->pb.N * c->pb.N * c->pb.M;
     if (loop_evals) *loop_evals = c->rows_compact ? c->loop_evals_rows : (c->loop_red ? c->loop_evals_red : full);
     if (loop_evals_full) *loop_evals_full = full;
     if (rows_unreduced) *rows_unreduced = c->loop_red ? c->loop_mismatch_rows : 0;
+    if (contraction_rows) *contraction_rows = c->rows_compact ? c->n_rrep : (long long)c->pb.N * c->pb.N;
     return QPFRG_OK;
 }

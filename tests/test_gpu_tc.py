@@ -45,12 +45,13 @@ def test_tc_rhs_matches_oracle(case):
     ref = Oracle(N, nt, nr, mode=mode, channels=ch).rhs(T, V, Z)
     with api.Context(N, nt, nr, U=2.0, mode=mode, precision=TC, channel_mask=ch) as ctx:
         got = gpu_rhs(ctx, T, V, Z)
-        evals = api.qpfrg_rhs_work(ctx.h)["loop_evals"]
+        work = api.qpfrg_rhs_work(ctx.h)
     assert normwise(got, ref) < 1e-4
     if mode == 0:
         maps = inputs.c4v_patch_maps(N)
         reps = {min(g[x] * N + g[y] for g in maps) for x in range(N) for y in range(N)}
-        assert (evals == 2 * len(reps) * N * nt * nr) == bool(sym)
+        assert (work["loop_evals"] == 2 * len(reps) * N * nt * nr) == bool(sym)
+        assert work["contraction_rows"] == (len(reps) if sym else N * N)
 
 
 def test_tc_rhs_full_size_sampled():
