@@ -315,7 +315,7 @@ def run_qpfrg(args):
     for name, pr, reps in forms:
         with api.Context(N, n, n, U=U, precision=pr, stream=stream.cuda_stream) as c2:
             if tuning is not None:
-                api.qpfrg_set_tuning(c2.h, tuning["bubble_qchunk"], tuning["sigma_qblocks"], tuning["tc_splits"])
+                api.qpfrg_set_tuning(c2.h, tuning["bubble_qchunk"], tuning["sigma_qblocks"], tuning["tc_splits"], tuning["bubble_transfers"])
             api.qpfrg_rhs(c2.h, 0.1, dV_t, Z_t, out)
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -448,7 +448,7 @@ def full_flow(api, inputs, workload, prec, name, stream, tuning=None):
     with api.Context(N, n, n, U=wl["U"], lambda0=1.0, precision=prec, lambda_end=wl["T_end"],
                      z_feedback=int(wl["z_feedback"]), eta=0.02, stream=stream.cuda_stream) as c:
         if tuning is not None:
-            api.qpfrg_set_tuning(c.h, tuning["bubble_qchunk"], tuning["sigma_qblocks"], tuning["tc_splits"])
+            api.qpfrg_set_tuning(c.h, tuning["bubble_qchunk"], tuning["sigma_qblocks"], tuning["tc_splits"], tuning["bubble_transfers"])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         r = api.qpfrg_flow(c.h)
@@ -715,7 +715,12 @@ def run_rhs_only(args):
     V = torch.from_numpy(inputs.random_vertex(N, U, seed=1, n_shell=ns).ravel()).cuda()
     Z = torch.from_numpy(inputs.z_profile(N, "aniso", n_shell=ns)).cuda()
     out = torch.empty(N ** 3, dtype=torch.float64, device="cuda")
+    tuning = None
     with api.Context(N, n, n, U=U, precision=prec, mode=mode, n_shell=ns, stream=stream.cuda_stream) as c:
+        if args.tune:
+            tuning = api.qpfrg_autotune(c.h, 0.1)
+        elif args.bubble_transfers:
+            api.qpfrg_set_tuning(c.h, bubble_transfers=args.bubble_transfers)
         for _ in range(args.warmup):
             api.qpfrg_rhs(c.h, 0.1, V, Z, out)
         torch.cuda.synchronize()
@@ -744,7 +749,7 @@ def run_rhs_only(args):
                       "rhs_per_s": args.steps / (ms / 1e3), "ms_per_rhs": ms / args.steps,
                       "kernels_ms_per_rhs": {k: v[0] / args.steps for k, v in prof.items() if v[1] > 0},
                       "launches": {k: v[1] for k, v in prof.items() if v[1] > 0},
-                      "sigma_z_ms": sig_ms}))
+                      "sigma_z_ms": sig_ms, "tuning": tuning, "bubble_transfers": args.bubble_transfers}))
 
 
 def main():
@@ -766,6 +771,9 @@ def main():
     p.add_argument("--rhs-only", choices=["mixed", "tc", "fp64"],
                    help="time right-hand sides of one context only (kernel captures); prints its own line")
     p.add_argument("--sigma", action="store_true", help="--rhs-only: also time one Z evaluation")
+    p.add_argument("--tune", action="store_true", help="--rhs-only: qpfrg_autotune the context first")
+    p.add_argument("--bubble-transfers", type=int, default=0, choices=[0, 2, 4],
+                   help="--rhs-only: transfers per warp pass of the loop kernels (0: built-in)")
     args = p.parse_args()
     if args.warmup < 3 and args.impl == "qpfrg":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

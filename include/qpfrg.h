@@ -367,16 +367,20 @@ qpfrg_status qpfrg_sigma_table(qpfrg_t ctx, size_t *bytes, long long offset, lon
  *   tc_splits[3]:   split-K factors of the pp, cr and d tensor-core
  *                   contractions, clipped to the number of 64-wide k blocks;
  *   ms_bubble, ms_sigma, ms_contract: fastest times found by qpfrg_autotune
- *                   (outputs; ignored by qpfrg_set_tuning). */
+ *                   (outputs; ignored by qpfrg_set_tuning);
+ *   bubble_transfers: transfers a warp of the FP32 loop kernels carries per
+ *                   pass over the patch's points, 2 or 4 (0: 2). */
 typedef struct {
     int bubble_qchunk;
     int sigma_qblocks;
     int tc_splits[3];
     double ms_bubble, ms_sigma, ms_contract;
+    int bubble_transfers;
 } qpfrg_tuning;
 
 /* Project-written autotuner: times candidate launch shapes on the context's
- * own state at Lambda = lambda -- the loop kernels (transfers per CTA), the
+ * own state at Lambda = lambda -- the loop kernels (transfers per CTA and per
+ * warp pass), the
  * tensor-core contraction of each channel (split-K; QPFRG_MIXED_TC), the FP32
  * self-energy of the wedge grid (q blocks per CTA) -- one untimed and one
  * timed launch each with CUDA events on the context's stream, keeps the
@@ -390,7 +394,8 @@ typedef struct {
 qpfrg_status qpfrg_autotune(qpfrg_t ctx, double lambda, qpfrg_tuning *out);
 
 /* Apply launch shapes (e.g. those qpfrg_autotune found on another context of
- * the same size).  QPFRG_ERR_INVALID for a negative field or sigma_qblocks > 64. */
+ * the same size).  QPFRG_ERR_INVALID for a negative field, sigma_qblocks > 64
+ * or bubble_transfers other than 0, 2, 4. */
 qpfrg_status qpfrg_set_tuning(qpfrg_t ctx, const qpfrg_tuning *t);
 
 /* ---------------------------------------------------------------------------

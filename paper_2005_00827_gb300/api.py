@@ -63,12 +63,13 @@ class qpfrg_options(C.Structure):
 
 class qpfrg_tuning(C.Structure):
     _fields_ = [("bubble_qchunk", C.c_int), ("sigma_qblocks", C.c_int), ("tc_splits", C.c_int * 3),
-                ("ms_bubble", C.c_double), ("ms_sigma", C.c_double), ("ms_contract", C.c_double)]
+                ("ms_bubble", C.c_double), ("ms_sigma", C.c_double), ("ms_contract", C.c_double),
+                ("bubble_transfers", C.c_int)]
 
     def as_dict(self):
         return dict(bubble_qchunk=self.bubble_qchunk, sigma_qblocks=self.sigma_qblocks,
                     tc_splits=list(self.tc_splits), ms_bubble=self.ms_bubble, ms_sigma=self.ms_sigma,
-                    ms_contract=self.ms_contract)
+                    ms_contract=self.ms_contract, bubble_transfers=self.bubble_transfers)
 
 
 class qpfrg_flow_result(C.Structure):
@@ -278,9 +279,10 @@ def qpfrg_autotune(ctx, lam: float) -> dict:
     return t.as_dict()
 
 
-def qpfrg_set_tuning(ctx, bubble_qchunk=0, sigma_qblocks=0, tc_splits=(0, 0, 0)):
+def qpfrg_set_tuning(ctx, bubble_qchunk=0, sigma_qblocks=0, tc_splits=(0, 0, 0), bubble_transfers=0):
     t = qpfrg_tuning()
     t.bubble_qchunk, t.sigma_qblocks = int(bubble_qchunk), int(sigma_qblocks)
+    t.bubble_transfers = int(bubble_transfers)
     for i in range(3):
         t.tc_splits[i] = int(tc_splits[i])
     _check(ctx, load().qpfrg_set_tuning(ctx, C.byref(t)))

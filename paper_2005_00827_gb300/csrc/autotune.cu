@@ -69,24 +69,29 @@ extern "C" qpfrg_status qpfrg_autotune(qpfrg_t c, double lambda, qpfrg_tuning *o
             if ((st = launch_convert_f32(c, c->d_V, c->d_Vf, n3)) != QPFRG_OK) break;
             Vin = c->d_Vf;
         }
-        // loop kernels: transfers per CTA
+        // loop kernels: transfers per CTA and per warp pass (4 only in FP32)
         {
             const int cand[] = {8, 16, 32, 64, 128, 256};
-            int pick = 0;
+            int pick = 0, pick_h = 2;
             double best = 1e300;
-            for (int q : cand) {
-                if (q > NN && q != cand[0]) break;
-                c->tune.bubble_qchunk = q;
-                const double ms = time_launch(
-                    c, ev, [&] { return launch_bubbles(c, lambda, c->d_Z, c->c4v_state, nullptr, c->c4v_state); }, st);
-                if (ms < 0.0) break;
-                if (ms < best) {
-                    best = ms;
-                    pick = q;
+            for (int hw = 2; hw <= (mixed ? 4 : 2) && st == QPFRG_OK; hw += 2)
+                for (int q : cand) {
+                    if (q > NN && q != cand[0]) break;
+                    c->tune.bubble_qchunk = q;
+                    c->tune.bubble_transfers = hw;
+                    const double ms = time_launch(
+                        c, ev,
+                        [&] { return launch_bubbles(c, lambda, c->d_Z, c->c4v_state, nullptr, c->c4v_state); }, st);
+                    if (ms < 0.0) break;
+                    if (ms < best) {
+                        best = ms;
+                        pick = q;
+                        pick_h = hw;
+                    }
                 }
-            }
             if (st != QPFRG_OK) break;
             c->tune.bubble_qchunk = pick;
+            c->tune.bubble_transfers = pick_h;
             best_b = best;
             // leave the loop-kernel rows of the fastest shape for the contraction below
             if ((st = launch_bubbles(c, lambda, c->d_Z, c->c4v_state, nullptr, c->c4v_state)) != QPFRG_OK) break;
@@ -138,6 +143,7 @@ extern "C" qpfrg_status qpfrg_autotune(qpfrg_t c, double lambda, qpfrg_tuning *o
     if (st != QPFRG_OK) return st;
     if (out) {
         out->bubble_qchunk = c->tune.bubble_qchunk;
+        out->bubble_transfers = c->tune.bubble_transfers;
         out->sigma_qblocks = c->tune.sigma_qblocks;
         for (int i = 0; i < 3; ++i) out->tc_splits[i] = c->tune.tc_splits[i];
         out->ms_bubble = best_b;
@@ -151,11 +157,13 @@ extern "C" qpfrg_status qpfrg_set_tuning(qpfrg_t c, const qpfrg_tuning *t)
 {
     if (!c || !t) return QPFRG_ERR_INVALID;
     if (t->bubble_qchunk < 0 || t->sigma_qblocks < 0 || t->sigma_qblocks > 64 || t->tc_splits[0] < 0 ||
-        t->tc_splits[1] < 0 || t->tc_splits[2] < 0) {
-        c->err = "negative launch shape";
+        t->tc_splits[1] < 0 || t->tc_splits[2] < 0 ||
+        (t->bubble_transfers != 0 && t->bubble_transfers != 2 && t->bubble_transfers != 4)) {
+        c->err = "invalid launch shape";
         return QPFRG_ERR_INVALID;
     }
     c->tune.bubble_qchunk = t->bubble_qchunk;
+    c->tune.bubble_transfers = t->bubble_transfers;
     c->tune.sigma_qblocks = t->sigma_qblocks;
     for (int i = 0; i < 3; ++i) c->tune.tc_splits[i] = t->tc_splits[i];
     return QPFRG_OK;

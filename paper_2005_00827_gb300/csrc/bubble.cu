@@ -289,8 +289,9 @@ __device__ __forceinline__ void table_row(const BubbleArgs<R> &A, const R *row, 
 //
 // Rows k in [q0, q1): the transfer Q = k (unreduced launch) or the
 // representative k of the C4v-reduced launch, Q = repQ[k], written to each of
-// its image rows.
-template <typename R, bool PP, bool TFLOW, bool TP0>
+// its image rows.  A warp carries H transfers at once (H = 2 or 4): one
+// shared-memory read of a point serves all of them.
+template <typename R, bool PP, bool TFLOW, bool TP0, int H>
 __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned char *smem_raw, int a, int q0, int q1)
 {
     const int N = A.pb.N, P = A.pb.P, M = A.pb.M;
@@ -305,18 +306,18 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
     Quad<R> *pc = reinterpret_cast<Quad<R> *>(smem_raw);   // cos p_x, cos p_y, sin p_x, sin p_y
     Quad<R> *pe = pc + P;                                   // x_p, f-terms, weight
     R *Zs = reinterpret_cast<R *>(pe + P);                  // N
-    // 2 nwarp rows (two transfers per warp) of N accumulators and a sink (slot
+    // H nwarp rows (H transfers per warp) of N accumulators and a sink (slot
     // N) for lanes without points, so that a change of partner is one add of
     // the finished run; the row stride N + 2 is even, keeping every row 8-byte
     // aligned (an odd stride once misaligned 8-byte reads of these rows)
     const int RS = N + 2;
     R *rows = Zs + N;
-    R *Ks = rows + 2 * nwarp * RS;                          // N Katanin factors
+    R *Ks = rows + H * nwarp * RS;                          // N Katanin factors
     for (int i = tid; i < N; i += blockDim.x) {
         Zs[i] = A.Z ? (R)A.Z[i] : R(1);
         Ks[i] = A.K ? (R)A.K[i] : R(1);
     }
-    for (int i = tid; i < 2 * nwarp * RS; i += blockDim.x) rows[i] = R(0);
+    for (int i = tid; i < H * nwarp * RS; i += blockDim.x) rows[i] = R(0);
     __syncthreads();
     const R Za = Zs[a];
     const R invT = A.invT, thrT = A.thr * A.T, invT2 = invT * invT;
@@ -348,17 +349,17 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
     const int dt = lane / lm.lr, sl = lane & (lm.lr - 1);
     const int stride = nr;                             // local index step between a lane's rows
     const bool vec4 = nt % 4 == 0 && lm.per_chunk % 4 == 0;
-    // Each warp carries two transfers at once (independent chains for the
-    // schedulers; one shared-memory read of a point serves both).
-    for (int Q0 = q0 + warp; Q0 < q1; Q0 += 2 * nwarp) {
-        const int nq = Q0 + nwarp < q1 ? 2 : 1;       // warp-uniform
-        R cQx[2], sQx[2], cQy[2], sQy[2];
-        float2 CQ[2], SQ[2];    // FP32: (cos Q_x, cos Q_y), +-(sin Q_x, sin Q_y) (+ pp, - ph)
-        const uint8_t *prow[2];
-        int run_b[2];
-        R run_v[2];
+    // Each warp carries H transfers at once (independent chains for the
+    // schedulers; one shared-memory read of a point serves all of them).
+    for (int Q0 = q0 + warp; Q0 < q1; Q0 += H * nwarp) {
+        const int nq = min(H, (q1 - Q0 + nwarp - 1) / nwarp);   // warp-uniform, >= 1
+        R cQx[H], sQx[H], cQy[H], sQy[H];
+        float2 CQ[H], SQ[H];    // FP32: (cos Q_x, cos Q_y), +-(sin Q_x, sin Q_y) (+ pp, - ph)
+        const uint8_t *prow[H];
+        int run_b[H];
+        R run_v[H];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < H; ++h) {
             const int kq = h < nq ? Q0 + h * nwarp : Q0;
             const int Q = A.repQ ? A.repQ[kq] : kq;
             cQx[h] = Qt.cx[Q];
@@ -389,9 +390,9 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
                     if (rr + k < nrow) w |= (unsigned)__ldg(prow[h] + part_byte(t0 + rr + k, s, nt, nr)) << (8 * k);
                 return w;
             };
-            unsigned wb[2], wn[2];
+            unsigned wb[H], wn[H];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < H; ++h) {
                 wb[h] = part_word(h, 0);
                 // a lane's first run starts on its first partner patch: no flush
                 // of an empty run (all lanes flushing into one slot at once would
@@ -401,18 +402,18 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
             for (int r = 0; r < lm.per_chunk; r += 4) {
                 const int li = li0 + r * stride;
 #pragma unroll
-                for (int h = 0; h < 2; ++h) wn[h] = part_word(h, r + 4);
-                int bb[2][4];
+                for (int h = 0; h < H; ++h) wn[h] = part_word(h, r + 4);
+                int bb[H][4];
 #pragma unroll
-                for (int h = 0; h < 2; ++h)
+                for (int h = 0; h < H; ++h)
 #pragma unroll
                     for (int k = 0; k < 4; ++k) bb[h][k] = (int)__byte_perm(wb[h], 0u, 0x4440u | k);
-                // two rows at a time: the loop kernels of 2 rows x 2 transfers
+                // two rows at a time: the loop kernels of 2 rows x H transfers
                 // first (a block of independent arithmetic), then the runs in
                 // row order
 #pragma unroll
                 for (int k0 = 0; k0 < 4; k0 += 2) {
-                    R vv[2][2];
+                    R vv[2][H];
 #pragma unroll
                     for (int kk = 0; kk < 2; ++kk) {
                         const int k = k0 + kk;
@@ -420,27 +421,30 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
                         const int lk = ok ? li + k * stride : 0;
                         const Quad<R> c4 = pc[lk], e4 = pe[lk];
                         if constexpr (sizeof(R) == 4 && TFLOW) {
-                            // FP32 temperature flow: the two transfers are the two
+                            // FP32 temperature flow: transfers h and h + 1 are the two
                             // lanes of packed FP32x2 arithmetic
                             const float2 cp = make_float2(c4.x, c4.y), sp = make_float2(c4.z, c4.w);
-                            float2 xq2;
 #pragma unroll
-                            for (int h = 0; h < 2; ++h) {
-                                // (cos q_x, cos q_y) of the partner by angle addition:
-                                // pp: cos(Q - p) = cQ cp + sQ sp;  ph: cos(p + Q) = cp cQ - sp sQ
-                                const float2 cq = __ffma2_rn(cp, CQ[h], __fmul2_rn(sp, SQ[h]));
-                                float xq = TP0 ? -2.f * t * (cq.x + cq.y) - mu
-                                               : -2.f * t * (cq.x + cq.y) - 4.f * tp * cq.x * cq.y - mu;
-                                if (qp) xq *= Zs[bb[h][k]];
-                                if (h == 0) xq2.x = xq;
-                                else xq2.y = xq;
+                            for (int h2 = 0; h2 < H; h2 += 2) {
+                                float2 xq2;
+#pragma unroll
+                                for (int h = h2; h < h2 + 2; ++h) {
+                                    // (cos q_x, cos q_y) of the partner by angle addition:
+                                    // pp: cos(Q - p) = cQ cp + sQ sp;  ph: cos(p + Q) = cp cQ - sp sQ
+                                    const float2 cq = __ffma2_rn(cp, CQ[h], __fmul2_rn(sp, SQ[h]));
+                                    float xq = TP0 ? -2.f * t * (cq.x + cq.y) - mu
+                                                   : -2.f * t * (cq.x + cq.y) - 4.f * tp * cq.x * cq.y - mu;
+                                    if (qp) xq *= Zs[bb[h][k]];
+                                    if (h == h2) xq2.x = xq;
+                                    else xq2.y = xq;
+                                }
+                                const float2 v = loop_T2(pp, e4.x, e4.y, e4.w, xq2, invT, invT2, kexp, thrT);
+                                vv[kk][h2] = v.x;
+                                vv[kk][h2 + 1] = v.y;
                             }
-                            const float2 v = loop_T2(pp, e4.x, e4.y, e4.w, xq2, invT, invT2, kexp, thrT);
-                            vv[kk][0] = v.x;
-                            vv[kk][1] = v.y;
                         } else {
 #pragma unroll
-                            for (int h = 0; h < 2; ++h) {
+                            for (int h = 0; h < H; ++h) {
                                 const R cqx = pp ? cQx[h] * c4.x + sQx[h] * c4.z : c4.x * cQx[h] - c4.z * sQx[h];
                                 const R cqy = pp ? cQy[h] * c4.y + sQy[h] * c4.w : c4.y * cQy[h] - c4.w * sQy[h];
                                 // t' = 0 (the nested lattice): the product term drops at compile time
@@ -457,22 +461,22 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
                         const int k = k0 + kk;
                         if (r + k >= nrow) continue;
 #pragma unroll
-                        for (int h = 0; h < 2; ++h) {
+                        for (int h = 0; h < H; ++h) {
                             if (h >= nq) break;
                             const int b = bb[h][k];
                             const bool change = b != run_b[h];
-                            if (change) row_add(&rows[(2 * warp + h) * RS + run_b[h]], run_v[h], A.fscale);
+                            if (change) row_add(&rows[(H * warp + h) * RS + run_b[h]], run_v[h], A.fscale);
                             run_v[h] = (change ? R(0) : run_v[h]) + vv[kk][h];
                             run_b[h] = b;
                         }
                     }
                 }
 #pragma unroll
-                for (int h = 0; h < 2; ++h) wb[h] = wn[h];
+                for (int h = 0; h < H; ++h) wb[h] = wn[h];
             }
         }
         for (int h = 0; h < nq; ++h) {
-            R *row = rows + (2 * warp + h) * RS;
+            R *row = rows + (H * warp + h) * RS;
             // last runs: segmented sum over lanes with equal partner patch, one
             // atomic per segment head
             const int key = run_b[h];
@@ -511,8 +515,8 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
     }
 }
 
-template <typename R, bool TP0>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) bubble_kernel(BubbleArgs<R> A)
+template <typename R, bool TP0, int H>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? (H == 2 ? 3 : 2) : 1) bubble_kernel(BubbleArgs<R> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (A.active && *A.active == 0) return;      // uniform over the grid
@@ -532,11 +536,11 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 3 : 1) bubble_kernel(Bub
         q1 = (int)min((long)q0 + A.qchunk, NN);
     }
     if (fam == 0) {
-        if (tflow) bubble_body<R, true, true, TP0>(A, smem_raw, a, q0, q1);
-        else bubble_body<R, true, false, TP0>(A, smem_raw, a, q0, q1);
+        if (tflow) bubble_body<R, true, true, TP0, H>(A, smem_raw, a, q0, q1);
+        else bubble_body<R, true, false, TP0, H>(A, smem_raw, a, q0, q1);
     } else {
-        if (tflow) bubble_body<R, false, true, TP0>(A, smem_raw, a, q0, q1);
-        else bubble_body<R, false, false, TP0>(A, smem_raw, a, q0, q1);
+        if (tflow) bubble_body<R, false, true, TP0, H>(A, smem_raw, a, q0, q1);
+        else bubble_body<R, false, false, TP0, H>(A, smem_raw, a, q0, q1);
     }
 }
 
@@ -598,14 +602,19 @@ static qpfrg_status launch_r(qpfrg_ctx *c, double lambda, const double *d_Z, con
         A.nimg = c->d_lnimg;
         A.img = c->d_limg;
     }
+    // transfers per warp pass: 4 only in FP32 (the packed pairs of the
+    // temperature flow), 2 otherwise or when tuned so
+    const int H = (sizeof(R) == 4 && c->tune.bubble_transfers == 4) ? 4 : 2;
     const int nthr = 256;
-    const size_t smem =
-        2 * (size_t)pb.P * sizeof(Quad<R>) + (2 * (size_t)pb.N + 2 * (nthr / 32) * (size_t)(pb.N + 2)) * sizeof(R);
+    const size_t smem = 2 * (size_t)pb.P * sizeof(Quad<R>) +
+                        (2 * (size_t)pb.N + (size_t)H * (nthr / 32) * (size_t)(pb.N + 2)) * sizeof(R);
     if (smem > 200 * 1024) {
         c->err = "fine grid too large for the loop-kernel launch";
         return QPFRG_ERR_UNSUPPORTED;
     }
-    auto kern = pb.tp == 0.0 ? bubble_kernel<R, true> : bubble_kernel<R, false>;
+    void (*kern)(BubbleArgs<R>) = pb.tp == 0.0 ? bubble_kernel<R, true, 2> : bubble_kernel<R, false, 2>;
+    if constexpr (sizeof(R) == 4)
+        if (H == 4) kern = pb.tp == 0.0 ? bubble_kernel<R, true, 4> : bubble_kernel<R, false, 4>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(c, e, "bubble smem attribute");
     const dim3 grid = (compact || red) ? dim3(ntask) : dim3(pb.N, qchunks, 2);

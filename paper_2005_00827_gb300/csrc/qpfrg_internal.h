@@ -79,6 +79,7 @@ enum KernelId {
 // Launch shapes chosen by qpfrg_autotune (0 = built-in heuristic).
 struct Tuning {
     int bubble_qchunk = 0;      // transfers per loop-kernel CTA
+    int bubble_transfers = 0;   // transfers per warp pass of the FP32 loop kernels (2 or 4; 0: 2)
     int sigma_qblocks = 0;      // blocks of 512 loop points q per self-energy CTA
     int tc_splits[3] = {0, 0, 0};   // split-K factors of the pp, cr, d contractions
 };

@@ -42,6 +42,7 @@ def test_autotune_returns_candidate_shapes_and_keeps_results():
         t = api.qpfrg_autotune(c.h, 0.3)
         after = rhs(c, 0.3, V, Z)
     assert t["bubble_qchunk"] in (8, 16, 32, 64, 128, 256)
+    assert t["bubble_transfers"] in (2, 4)
     assert t["sigma_qblocks"] in (1, 2, 4, 8)
     assert all(s in (0, 1, 2, 3, 4, 6, 8, 12, 16) for s in t["tc_splits"])
     assert t["ms_bubble"] > 0 and t["ms_sigma"] > 0 and t["ms_contract"] > 0
@@ -58,8 +59,9 @@ def test_extreme_shapes_agree(prec):
     res = []
     with api.Context(N, n, n, U=2.0, precision=prec) as c:
         for shape in (dict(bubble_qchunk=8, sigma_qblocks=1, tc_splits=(1, 1, 1)),
-                      dict(bubble_qchunk=256, sigma_qblocks=8, tc_splits=(16, 16, 16)),
-                      dict(bubble_qchunk=32, sigma_qblocks=3, tc_splits=(3, 2, 5))):
+                      dict(bubble_qchunk=256, sigma_qblocks=8, tc_splits=(16, 16, 16), bubble_transfers=4),
+                      dict(bubble_qchunk=32, sigma_qblocks=3, tc_splits=(3, 2, 5), bubble_transfers=4),
+                      dict(bubble_qchunk=8, bubble_transfers=4)):
             api.qpfrg_set_tuning(c.h, **shape)
             res.append((rhs(c, 0.2, V, Z), zfac(c, 0.2, V, Z)))
     for r, z in res[1:]:
@@ -73,6 +75,8 @@ def test_set_tuning_rejects_negative_shapes():
             api.qpfrg_set_tuning(c.h, bubble_qchunk=-1)
         with pytest.raises(api.QpfrgError):
             api.qpfrg_set_tuning(c.h, sigma_qblocks=65)
+        with pytest.raises(api.QpfrgError):
+            api.qpfrg_set_tuning(c.h, bubble_transfers=3)
 
 
 def test_batch_with_autotune_matches_batch_without():
