@@ -229,6 +229,21 @@ __device__ __forceinline__ void row_add(float *slot, float v, float fscale)
     atomicAdd(reinterpret_cast<int *>(slot), __float2int_rn(v * fscale));
 }
 __device__ __forceinline__ void row_add(double *slot, double v, float) { atomicAdd(slot, v); }
+// the same add, predicated: the FP32 path issues it as one predicated shared
+// reduction (no branch around it), the FP64 path branches
+__device__ __forceinline__ void row_add_if(float *slot, float v, float fscale, bool p)
+{
+    const int iv = __float2int_rn(v * fscale);
+    const unsigned addr = (unsigned)__cvta_generic_to_shared(slot);
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q red.shared.add.s32 [%0], %1;\n\t}" ::"r"(addr),
+        "r"(iv), "r"((int)p)
+        : "memory");
+}
+__device__ __forceinline__ void row_add_if(double *slot, double v, float, bool p)
+{
+    if (p) atomicAdd(slot, v);
+}
 __device__ __forceinline__ float row_get(const float *slot, float finv)
 {
     return (float)*reinterpret_cast<const int *>(slot) * finv;
@@ -291,7 +306,7 @@ __device__ __forceinline__ void table_row(const BubbleArgs<R> &A, const R *row, 
 // representative k of the C4v-reduced launch, Q = repQ[k], written to each of
 // its image rows.  A warp carries H transfers at once (H = 2 or 4): one
 // shared-memory read of a point serves all of them.
-template <typename R, bool PP, bool TFLOW, bool TP0, int H>
+template <typename R, bool PP, bool TFLOW, bool TP0, int H, bool FULL>
 __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned char *smem_raw, int a, int q0, int q1)
 {
     const int N = A.pb.N, P = A.pb.P, M = A.pb.M;
@@ -376,14 +391,15 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
             const int s = ch * 32 + sl;
             // rows of this lane in the chunk: t = dt per_chunk + r < n_theta
             const int t0 = dt * lm.per_chunk;
-            const int nrow = (s < nr && t0 < nt) ? min(lm.per_chunk, nt - t0) : 0;
+            // FULL: every lane has per_chunk rows (a multiple of 4), read as words
+            const int nrow = FULL ? lm.per_chunk : ((s < nr && t0 < nt) ? min(lm.per_chunk, nt - t0) : 0);
             const int li0 = t0 * nr + s;     // staged point of the lane's first row
             // partner bytes of the rows rr .. rr+3 of transfer h as one word
             // (one aligned 4-byte load, coalesced over the warp's radii, where
             // n_theta and the row blocks are multiples of 4), loaded one group ahead
             auto part_word = [&](int h, int rr) -> unsigned {
                 if (rr >= nrow || h >= nq) return 0u;
-                if (vec4)
+                if (FULL || vec4)
                     return __ldg(reinterpret_cast<const unsigned *>(prow[h] + part_byte(t0 + rr, s, nt, nr)));
                 unsigned w = 0u;
                 for (int k = 0; k < 4; ++k)
@@ -417,7 +433,7 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
 #pragma unroll
                     for (int kk = 0; kk < 2; ++kk) {
                         const int k = k0 + kk;
-                        const bool ok = r + k < nrow;
+                        const bool ok = FULL || r + k < nrow;
                         const int lk = ok ? li + k * stride : 0;
                         const Quad<R> c4 = pc[lk], e4 = pe[lk];
                         if constexpr (sizeof(R) == 4 && TFLOW) {
@@ -459,13 +475,13 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
 #pragma unroll
                     for (int kk = 0; kk < 2; ++kk) {
                         const int k = k0 + kk;
-                        if (r + k >= nrow) continue;
+                        if (!FULL && r + k >= nrow) continue;
 #pragma unroll
                         for (int h = 0; h < H; ++h) {
                             if (h >= nq) break;
                             const int b = bb[h][k];
                             const bool change = b != run_b[h];
-                            if (change) row_add(&rows[(H * warp + h) * RS + run_b[h]], run_v[h], A.fscale);
+                            row_add_if(&rows[(H * warp + h) * RS + run_b[h]], run_v[h], A.fscale, change);
                             run_v[h] = (change ? R(0) : run_v[h]) + vv[kk][h];
                             run_b[h] = b;
                         }
@@ -515,7 +531,7 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
     }
 }
 
-template <typename R, bool TP0, int H>
+template <typename R, bool TP0, int H, bool FULL>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (H == 2 ? 3 : 2) : 1) bubble_kernel(BubbleArgs<R> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -536,11 +552,11 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? (H == 2 ? 3 : 2) : 1) bu
         q1 = (int)min((long)q0 + A.qchunk, NN);
     }
     if (fam == 0) {
-        if (tflow) bubble_body<R, true, true, TP0, H>(A, smem_raw, a, q0, q1);
-        else bubble_body<R, true, false, TP0, H>(A, smem_raw, a, q0, q1);
+        if (tflow) bubble_body<R, true, true, TP0, H, FULL>(A, smem_raw, a, q0, q1);
+        else bubble_body<R, true, false, TP0, H, FULL>(A, smem_raw, a, q0, q1);
     } else {
-        if (tflow) bubble_body<R, false, true, TP0, H>(A, smem_raw, a, q0, q1);
-        else bubble_body<R, false, false, TP0, H>(A, smem_raw, a, q0, q1);
+        if (tflow) bubble_body<R, false, true, TP0, H, FULL>(A, smem_raw, a, q0, q1);
+        else bubble_body<R, false, false, TP0, H, FULL>(A, smem_raw, a, q0, q1);
     }
 }
 
@@ -612,9 +628,14 @@ static qpfrg_status launch_r(qpfrg_ctx *c, double lambda, const double *d_Z, con
         c->err = "fine grid too large for the loop-kernel launch";
         return QPFRG_ERR_UNSUPPORTED;
     }
-    void (*kern)(BubbleArgs<R>) = pb.tp == 0.0 ? bubble_kernel<R, true, 2> : bubble_kernel<R, false, 2>;
+    // every lane with the same whole number of 4-row groups: no per-row bounds tests
+    const LaneMap lm(pb.n_theta, pb.n_r);
+    const bool full = pb.n_theta % 4 == 0 && lm.per_chunk % 4 == 0 &&
+                      (pb.n_r >= 32 ? pb.n_r % 32 == 0 : (lm.lr == pb.n_r && pb.n_theta % lm.apr == 0));
+    void (*kern)(BubbleArgs<R>) = pb.tp == 0.0 ? bubble_kernel<R, true, 2, false> : bubble_kernel<R, false, 2, false>;
+    if (full) kern = pb.tp == 0.0 ? bubble_kernel<R, true, 2, true> : bubble_kernel<R, false, 2, true>;
     if constexpr (sizeof(R) == 4)
-        if (H == 4) kern = pb.tp == 0.0 ? bubble_kernel<R, true, 4> : bubble_kernel<R, false, 4>;
+        if (H == 4) kern = pb.tp == 0.0 ? bubble_kernel<R, true, 4, false> : bubble_kernel<R, false, 4, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(c, e, "bubble smem attribute");
     const dim3 grid = (compact || red) ? dim3(ntask) : dim3(pb.N, qchunks, 2);

@@ -172,29 +172,40 @@ static qpfrg_status launch_all(qpfrg_ctx *c, const VR *V, double scale, double *
     return QPFRG_OK;
 }
 
+// C4v element g on patch j (wedge part, ns shells per wedge, Na wedges)
+__device__ __forceinline__ int c4v_patch(int g, int j, int ns, int Na)
+{
+    const int w = ns == 1 ? j : j / ns, sh = j - w * ns;
+    const int off = (g & 3) * (Na >> 2);
+    int r = (g & 4) ? off - w : w + off;      // in (-Na, 2 Na)
+    r = r >= Na ? r - Na : (r < 0 ? r + Na : r);
+    return r * ns + sh;
+}
+
 // Expansion of the representative rows (row orbits, symmetry.cu): with a
 // C4v-symmetric state each channel's output is invariant, out(g t) = out(t),
 // so row Q = g rep of a channel at column n is the representative's row at
 // column g^-1 n.  One thread per output triple (k1, k2, k3) adds the three
 // channels' values: pp row (k1, k2) column k3, cr row (k3, k2) column k1,
 // d row (k1, k3) column k2 (the row/column roles of the channel GEMMs above).
+// Block (k2, k1), thread k3.
 __global__ void rows_expand_kernel(const double *__restrict__ outc, const int *__restrict__ rowmap, int nr, int N,
                                    int ns, unsigned channels, double *__restrict__ out)
 {
-    const long NN = (long)N * N, n3 = NN * N;
+    const int k2 = blockIdx.x, k1 = blockIdx.y, Na = N / ns;
     const long ch_stride = (long)nr * N;
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n3; t += (long)gridDim.x * blockDim.x) {
-        const int k1 = (int)(t / NN), k2 = (int)((t / N) % N), k3 = (int)(t % N);
+    double *row = out + ((long)k1 * N + k2) * N;
+    const int e_pp = __ldg(rowmap + k1 * N + k2);
+    for (int k3 = threadIdx.x; k3 < N; k3 += blockDim.x) {
         double v = 0.0;
-        auto take = [&](int ch, int x, int y, int n) {
-            const int e = __ldg(rowmap + (long)x * N + y);
-            const int m = e & 0xffffff, g = e >> 24;
-            v += __ldg(outc + ch * ch_stride + (long)m * N + c4v_apply(c4v_inverse(g), n, N, ns));
+        auto take = [&](int ch, int e, int n) {
+            const int m = e & 0xffffff, gi = c4v_inverse(e >> 24);
+            v += __ldg(outc + ch * ch_stride + (long)m * N + c4v_patch(gi, n, ns, Na));
         };
-        if (channels & QPFRG_CH_PP) take(0, k1, k2, k3);
-        if (channels & QPFRG_CH_CR) take(1, k3, k2, k1);
-        if (channels & QPFRG_CH_D) take(2, k1, k3, k2);
-        out[t] += v;
+        if (channels & QPFRG_CH_PP) take(0, e_pp, k3);
+        if (channels & QPFRG_CH_CR) take(1, __ldg(rowmap + k3 * N + k2), k1);
+        if (channels & QPFRG_CH_D) take(2, __ldg(rowmap + k1 * N + k3), k2);
+        row[k3] += v;
     }
 }
 
@@ -216,11 +227,10 @@ qpfrg_status launch_contractions(qpfrg_ctx *c, const void *d_Vin, double scale, 
         if ((ch & QPFRG_CH_CR) && (s = launch_tc_fused(c, 1, -scale, dst[1], K_TC_CR))) return s;
         if ((ch & QPFRG_CH_D) && (s = launch_tc_fused(c, 2, scale, dst[2], K_TC_D))) return s;
         if (c->rows_compact) {
-            const long n3 = (long)c->pb.N * c->pb.N * c->pb.N;
-            const int grid = (int)std::min<long>((n3 + 255) / 256, 152L * 8);
+            const int N = c->pb.N, thr = std::min(256, (N + 31) / 32 * 32);
             prof_begin(c);
-            rows_expand_kernel<<<grid, 256, 0, c->stream>>>(c->d_outc, c->d_rowmap, c->n_rrep, c->pb.N,
-                                                            c->pb.n_shell, ch, d_out);
+            rows_expand_kernel<<<dim3(N, N), thr, 0, c->stream>>>(c->d_outc, c->d_rowmap, c->n_rrep, N,
+                                                                  c->pb.n_shell, ch, d_out);
             prof_end(c, K_ROWS_EXPAND);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return cuda_fail(c, e, "rows_expand_kernel");

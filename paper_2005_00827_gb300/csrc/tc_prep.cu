@@ -30,49 +30,68 @@ struct TcPrepArgs {
     float *VT;
 };
 
+// Job blockIdx.y: 0, 1, 2 the pp, cr, d operands, one thread per row n and
+// 8 consecutive k (one 16-byte chunk of hi and of lo in the tile layout;
+// neighbouring threads take neighbouring rows, so the pp reads are coalesced);
+// 3, 4, 5 the three factor tables, one element per thread.  32-bit indices:
+// N <= 256 keeps N^3 and Npad K_pd below 2^31.
 __device__ __forceinline__ void tc_prep_body(const TcPrepArgs &t)
 {
-    const int N = t.N, Npad = t.Npad;
-    const long NN = (long)N * N, n3 = NN * N, Kp = t.Kp;
-    const long s_pp = (long)Npad * Kp, s_d = 2 * s_pp;
-    const long total = 2 * s_pp + s_d + 3 * n3;
+    const int N = t.N, Npad = t.Npad, job = blockIdx.y;
+    const int NN = N * N, Kp = (int)t.Kp;
     const float *V = t.V;
-    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
-        if (idx < 2 * s_pp + s_d) {
-            int which;
-            long loc;
-            if (idx < s_pp) { which = 0; loc = idx; }
-            else if (idx < 2 * s_pp) { which = 1; loc = idx - s_pp; }
-            else { which = 2; loc = idx - 2 * s_pp; }
-            const long K = which == 2 ? 2 * Kp : Kp;
-            const int n = (int)(loc / K);
-            const long k = loc - (long)n * K;
-            const bool second = k >= Kp;
-            const long kk = second ? k - Kp : k;
-            float v = 0.f;
-            if (n < N && kk < NN) {
-                const int a = (int)(kk / N), b = (int)(kk - (long)a * N);
-                if (which == 0) v = V[kk * N + n];
-                else if (which == 1) v = V[(long)n * NN + kk];
-                else if (!second) v = V[((long)b * N + n) * N + a];
-                else v = V[((long)n * N + b) * N + a];
+    const int stride = gridDim.x * blockDim.x;
+    const int g0 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (job < 3) {
+        const int K = job == 2 ? 2 * Kp : Kp;
+        const int total = Npad * (K / 8);
+        __nv_bfloat16 *const dhi = job == 0 ? t.Bpp[0] : (job == 1 ? t.Bcr[0] : t.Bd[0]);
+        __nv_bfloat16 *const dlo = job == 0 ? t.Bpp[1] : (job == 1 ? t.Bcr[1] : t.Bd[1]);
+        for (int g = g0; g < total; g += stride) {
+            const int n = g % Npad, k0 = (g / Npad) * 8;
+            const bool second = k0 >= Kp;
+            const int kk0 = second ? k0 - Kp : k0;
+            int a = kk0 / N, b = kk0 - a * N;
+            uint4 hi, lo;
+            uint32_t *hp = &hi.x, *lp = &lo.x;
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+                float x[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    float v = 0.f;
+                    if (n < N && kk0 + e + u < NN) {
+                        if (job == 0) v = V[(kk0 + e + u) * N + n];
+                        else if (job == 1) v = V[n * NN + kk0 + e + u];
+                        else if (!second) v = V[(b * N + n) * N + a];
+                        else v = V[(n * N + b) * N + a];
+                    }
+                    x[u] = v;
+                    if (++b == N) {
+                        b = 0;
+                        ++a;
+                    }
+                }
+                const __nv_bfloat162 h2 = __floats2bfloat162_rn(x[0], x[1]);
+                const __nv_bfloat162 l2 = __floats2bfloat162_rn(x[0] - __low2float(h2), x[1] - __high2float(h2));
+                hp[e / 2] = *reinterpret_cast<const uint32_t *>(&h2);
+                lp[e / 2] = *reinterpret_cast<const uint32_t *>(&l2);
             }
-            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-            const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-            __nv_bfloat16 *const *dst = which == 0 ? t.Bpp : (which == 1 ? t.Bcr : t.Bd);
-            const long o = tile_index(n, k, Npad, which == 2 ? t.Kpd : t.Kp);
-            dst[0][o] = hi;
-            dst[1][o] = lo;
-        } else {
-            const long o = idx - (2 * s_pp + s_d);
-            const int part = (int)(o / n3);
-            const long r = o - part * n3;             // Q N + x
-            const int x = (int)(r % N), Q = (int)(r / N), q1 = Q / N, q2 = Q - q1 * N;
+            // k0 % 8 == 0: the chunk's 8 elements are contiguous in the tile (16-byte aligned)
+            const long o = tile_index(n, k0, Npad, K);
+            *reinterpret_cast<uint4 *>(dhi + o) = hi;
+            *reinterpret_cast<uint4 *>(dlo + o) = lo;
+        }
+    } else {
+        const int part = job - 3, n3 = NN * N;
+        float *VT = t.VT + (long)part * n3;
+        for (int o = g0; o < n3; o += stride) {
+            const int x = o % N, Q = o / N, q1 = Q / N, q2 = Q - q1 * N;
             float v;
-            if (part == 0) v = V[((long)x * N + q2) * N + q1];                         // Q = (l,j): V[b,j,l]
-            else if (part == 1) v = 2.f * V[((long)q1 * N + x) * N + q2] - V[((long)x * N + q1) * N + q2];
-            else v = -V[((long)q1 * N + x) * N + q2];                                 // Q = (i,l): -V[i,a,l]
-            t.VT[o] = v;
+            if (part == 0) v = V[(x * N + q2) * N + q1];                                  // Q = (l,j): V[b,j,l]
+            else if (part == 1) v = 2.f * V[(q1 * N + x) * N + q2] - V[(x * N + q1) * N + q2];
+            else v = -V[(q1 * N + x) * N + q2];                                         // Q = (i,l): -V[i,a,l]
+            VT[o] = v;
         }
     }
 }
@@ -84,7 +103,7 @@ __global__ void tc_prep_kernel(TcPrepArgs t) { tc_prep_body(t); }
 __global__ void tc_prep_batch_kernel(TcPrepArgs t, const TcPrepFlow *flows, const int *status, const double *h_tab,
                                      int step, int nflows)
 {
-    const int f = blockIdx.y;
+    const int f = blockIdx.z;
     if (status[f] != QPFRG_FLOW_RUNNING || h_tab[(long)step * nflows + f] == 0.0) return;
     const TcPrepFlow &p = flows[f];
     t.V = p.Vf;
@@ -102,15 +121,15 @@ qpfrg_status launch_tc_prep_batch(qpfrg_ctx *c, const TcPrepFlow *d_flows, const
 {
     const int N = c->pb.N;
     const long NN = (long)N * N;
-    const long total = 4 * (long)c->tc.Npad * c->tc.Kp + 3 * NN * N;
-    const int blocks = (int)std::min<long>((total + 255) / 256, 152L * 4);
+    const long total = std::max((long)c->tc.Npad * c->tc.Kp / 4, NN * N);   // the largest job
+    const int blocks = (int)std::min<long>((total + 255) / 256, 152L);
     TcPrepArgs t{};
     t.N = N;
     t.Npad = c->tc.Npad;
     t.Kp = c->tc.Kp;
     t.Kpd = c->tc.Kpd;
     prof_begin(c);
-    tc_prep_batch_kernel<<<dim3(blocks, nflows), 256, 0, c->stream>>>(t, d_flows, d_status, d_h_tab, step, nflows);
+    tc_prep_batch_kernel<<<dim3(blocks, 6, nflows), 256, 0, c->stream>>>(t, d_flows, d_status, d_h_tab, step, nflows);
     prof_end(c, K_TC_PREP);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "tc_prep_batch_kernel");
@@ -120,8 +139,8 @@ qpfrg_status launch_tc_prep(qpfrg_ctx *c)
 {
     const int N = c->pb.N;
     const long NN = (long)N * N;
-    const long total = 4 * (long)c->tc.Npad * c->tc.Kp + 3 * NN * N;
-    int blocks = (int)std::min<long>((total + 255) / 256, 152L * 16);
+    const long total = std::max((long)c->tc.Npad * c->tc.Kp / 4, NN * N);   // the largest job
+    const int blocks = (int)std::min<long>((total + 255) / 256, 152L * 4);
     TcPrepArgs t;
     t.V = c->d_Vf;
     t.N = N;
@@ -135,7 +154,7 @@ qpfrg_status launch_tc_prep(qpfrg_ctx *c)
     }
     t.VT = c->tc.VT;
     prof_begin(c);
-    tc_prep_kernel<<<blocks, 256, 0, c->stream>>>(t);
+    tc_prep_kernel<<<dim3(blocks, 6), 256, 0, c->stream>>>(t);
     prof_end(c, K_TC_PREP);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "tc_prep_kernel");
