@@ -38,17 +38,20 @@ struct FlowArrays {
     double *x, *m_old, *lambda_c, *max_v;
 };
 
-// RK4 bookkeeping of every running flow with a step, grid.y = flow; k is
-// cleared after use (the contractions add into it); the final stage also
+// RK4 bookkeeping of every running flow with a step, grid.y = flow; k (and
+// the representative rows outc of the row orbits, nc values per flow) are
+// cleared after use (the contractions add into them); the final stage also
 // refreshes the FP32 copy for the next step and reduces max|V| and finiteness.
 __global__ void rk_batch_kernel(int stage, const TcPrepFlow *pf, double *const *V, double *const *k,
-                                double *const *acc, const double *h_tab, const int *status, int step, int nflows,
-                                unsigned long long *red, long n)
+                                double *const *acc, double *const *outc, long nc, const double *h_tab,
+                                const int *status, int step, int nflows, unsigned long long *red, long n)
 {
     const int f = blockIdx.y;
     const double h = h_tab[(long)step * nflows + f];
     if (status[f] != QPFRG_FLOW_RUNNING || h == 0.0) return;
     double *Vf64 = V[f], *kf = k[f], *af = acc[f];
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nc; i += (long)gridDim.x * blockDim.x)
+        outc[f][i] = 0.0;
     float *Vf = const_cast<float *>(pf[f].Vf);
     const double c_next = stage == 3 ? h : 0.5 * h;
     double m = 0.0;
@@ -149,6 +152,9 @@ struct Group {
     float **d_rows = nullptr;
     TcPrepFlow *d_pf = nullptr;
     double **d_V = nullptr, **d_k = nullptr, **d_acc = nullptr;
+    bool compact = false;              // row orbits: representative rows, expanded per flow
+    double **d_outc = nullptr;         // per flow: [ch][representative][n]
+    long nc = 0;                       // values per flow of d_outc
     const float **d_Vf = nullptr, **d_VT = nullptr;
     CUtensorMap *d_maps = nullptr;
     CUtensorMap *d_tmaps = nullptr;    // table map per slot
@@ -254,6 +260,20 @@ qpfrg_status setup_group(Group &g, const qpfrg_lattice *lattice, const qpfrg_fin
     if ((e = cudaMemsetAsync(k, 0, F * n3 * sizeof(double), g.stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(B, 0, F * bper * sizeof(__nv_bfloat16), g.stream)) != cudaSuccess)
         return cuda_fail(c, e, "clear batch buffers");
+    // every flow starts at V = U with Z = 1, C4v symmetric, and stays so:
+    // the row orbits apply to the whole batch when the context built them
+    g.compact = c->rows_ok;
+    double *outc = nullptr;
+    std::vector<double *> poutc(F, nullptr);
+    if (g.compact) {
+        g.nc = 3L * c->n_rrep * N;
+        if ((s = galloc(g, &outc, F * g.nc, "batch representative rows")) ||
+            (s = galloc(g, &g.d_outc, F, "batch representative row ptrs")))
+            return s;
+        if ((e = cudaMemsetAsync(outc, 0, F * g.nc * sizeof(double), g.stream)) != cudaSuccess)
+            return cuda_fail(c, e, "clear batch representative rows");
+        for (int i = 0; i < F; ++i) poutc[i] = outc + i * g.nc;
+    }
     std::vector<double> hv(n3);
     std::vector<float> hf(n3);
     std::vector<TcPrepFlow> pf(F);
@@ -340,7 +360,8 @@ qpfrg_status setup_group(Group &g, const qpfrg_lattice *lattice, const qpfrg_fin
                {g.d_h, g.h_tab.data(), g.h_tab.size() * sizeof(double)},
                {g.d_slot, g.slot_tab.data(), g.slot_tab.size()},
                {g.d_rows, g.rows.data(), g.nslots * sizeof(float *)},
-               {g.d_tmaps, tmaps.data(), g.nslots * sizeof(CUtensorMap)}};
+               {g.d_tmaps, tmaps.data(), g.nslots * sizeof(CUtensorMap)},
+               {g.d_outc, poutc.data(), g.compact ? F * sizeof(double *) : 0}};
     for (const Up &u : ups)
         if (u.bytes && (e = cudaMemcpy(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice)) != cudaSuccess)
             return cuda_fail(c, e, "batch upload");
@@ -350,7 +371,7 @@ qpfrg_status setup_group(Group &g, const qpfrg_lattice *lattice, const qpfrg_fin
     const int qchunk = c->tune.bubble_qchunk > 0 ? (int)std::min<long>(c->tune.bubble_qchunk, (long)N * N)
                                                  : (int)std::max(8L, std::min(64L, (long)N * N / 16));
     int ntask = 0;
-    return loop_tasks(c, qchunk, &ntask);
+    return g.compact ? row_tasks(c, std::max(8, qchunk), &ntask) : loop_tasks(c, qchunk, &ntask);
 }
 
 // Enqueue step k of the group on its stream.
@@ -364,7 +385,7 @@ qpfrg_status enqueue_group_step(Group &g, int k, double stop)
         const auto &sx = g.slot_xh[k];
         for (int sl = 0; sl < (int)sx.size(); ++sl) {
             const double T = std::exp(sx[sl].first + cst[st] * sx[sl].second);
-            if ((s = launch_loop_rows(c, T, g.rows[sl], g.d_act + sl)) != QPFRG_OK) return s;
+            if ((s = launch_loop_rows(c, T, g.rows[sl], g.d_act + sl, g.compact)) != QPFRG_OK) return s;
         }
         if ((s = launch_tc_prep_batch(c, g.d_pf, g.st.status, g.d_h, k, g.F)) != QPFRG_OK) return s;
         TcBatch bt{};
@@ -379,16 +400,19 @@ qpfrg_status enqueue_group_step(Group &g, int k, double stop)
         bt.Vf = g.d_Vf;
         bt.VT = g.d_VT;
         bt.out = g.d_k;
+        bt.outc = g.compact ? g.d_outc : nullptr;
         bt.maps = g.d_maps;
         bt.tab_maps = g.d_tmaps;
         const unsigned ch = c->pb.channels;
         if ((ch & QPFRG_CH_PP) && (s = launch_tc_fused_batch(c, 0, bt, -1.0))) return s;
         if ((ch & QPFRG_CH_CR) && (s = launch_tc_fused_batch(c, 1, bt, -1.0))) return s;
         if ((ch & QPFRG_CH_D) && (s = launch_tc_fused_batch(c, 2, bt, 1.0))) return s;
+        if (g.compact && (s = launch_rows_expand_batch(c, bt)) != QPFRG_OK) return s;
         const int blocks = (int)std::min<long>((n3 + 255) / 256, 152L * 4 / std::max(1, g.F / 8 + 1) + 1);
         prof_begin(c);
-        rk_batch_kernel<<<dim3(blocks, g.F), 256, 0, g.stream>>>(st + 1, g.d_pf, g.d_V, g.d_k, g.d_acc, g.d_h,
-                                                                 g.st.status, k, g.F, g.d_red, n3);
+        rk_batch_kernel<<<dim3(blocks, g.F), 256, 0, g.stream>>>(st + 1, g.d_pf, g.d_V, g.d_k, g.d_acc, g.d_outc,
+                                                                 g.compact ? g.nc : 0, g.d_h, g.st.status, k, g.F,
+                                                                 g.d_red, n3);
         prof_end(c, st < 3 ? K_RK_STAGE : K_RK_FINAL);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(c, e, "rk_batch_kernel");

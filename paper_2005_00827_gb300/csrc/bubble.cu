@@ -664,13 +664,15 @@ qpfrg_status launch_bubbles(qpfrg_ctx *c, double lambda, const double *d_Z, bool
 }
 
 // The loop kernel alone into an explicit buffer (batched flows): the table
-// B[f][Q][a][b] at Lambda with Z = 1; every CTA returns at once when
-// *active == 0.  No vertex operands are prepared.
-qpfrg_status launch_loop_rows(qpfrg_ctx *c, double lambda, float *rows, const int *active)
+// B[f][Q][a][b] at Lambda with Z = 1 (compact: the representative rows of the
+// row orbits); every CTA returns at once when *active == 0.  No vertex
+// operands are prepared.
+qpfrg_status launch_loop_rows(qpfrg_ctx *c, double lambda, float *rows, const int *active, bool compact)
 {
     c->loop_out = rows;
     c->loop_active = active;
-    const qpfrg_status s = launch_r<float>(c, lambda, c->d_ones, nullptr, true, c->f32, c->qpp32, c->qph32, 2e-2f);
+    const qpfrg_status s =
+        launch_r<float>(c, lambda, c->d_ones, nullptr, true, c->f32, c->qpp32, c->qph32, 2e-2f, compact && c->rows_ok);
     c->loop_out = nullptr;
     c->loop_active = nullptr;
     return s;

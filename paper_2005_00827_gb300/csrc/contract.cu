@@ -188,11 +188,11 @@ __device__ __forceinline__ int c4v_patch(int g, int j, int ns, int Na)
 // column g^-1 n.  One thread per output triple (k1, k2, k3) adds the three
 // channels' values: pp row (k1, k2) column k3, cr row (k3, k2) column k1,
 // d row (k1, k3) column k2 (the row/column roles of the channel GEMMs above).
-// Block (k2, k1), thread k3.
-__global__ void rows_expand_kernel(const double *__restrict__ outc, const int *__restrict__ rowmap, int nr, int N,
-                                   int ns, unsigned channels, double *__restrict__ out)
+// Row (k1, k2) of out, threads over k3.
+__device__ __forceinline__ void expand_row(const double *__restrict__ outc, const int *__restrict__ rowmap, int nr,
+                                           int N, int ns, unsigned channels, double *__restrict__ out, int k1, int k2)
 {
-    const int k2 = blockIdx.x, k1 = blockIdx.y, Na = N / ns;
+    const int Na = N / ns;
     const long ch_stride = (long)nr * N;
     double *row = out + ((long)k1 * N + k2) * N;
     const int e_pp = __ldg(rowmap + k1 * N + k2);
@@ -207,6 +207,34 @@ __global__ void rows_expand_kernel(const double *__restrict__ outc, const int *_
         if (channels & QPFRG_CH_D) take(2, __ldg(rowmap + k1 * N + k3), k2);
         row[k3] += v;
     }
+}
+
+// Block (k2, k1), thread k3.
+__global__ void rows_expand_kernel(const double *__restrict__ outc, const int *__restrict__ rowmap, int nr, int N,
+                                   int ns, unsigned channels, double *__restrict__ out)
+{
+    expand_row(outc, rowmap, nr, N, ns, channels, out, blockIdx.y, blockIdx.x);
+}
+
+// Batched flows: grid.z = flow; flows that are not running or have no step
+// at this row of the schedule return at once.
+__global__ void rows_expand_batch_kernel(TcBatch bt, const int *__restrict__ rowmap, int nr, int N, int ns,
+                                         unsigned channels)
+{
+    const int f = blockIdx.z;
+    if (bt.status[f] != QPFRG_FLOW_RUNNING || bt.h_tab[(long)bt.step * bt.nflows + f] == 0.0) return;
+    expand_row(bt.outc[f], rowmap, nr, N, ns, channels, bt.out[f], blockIdx.y, blockIdx.x);
+}
+
+qpfrg_status launch_rows_expand_batch(qpfrg_ctx *c, const TcBatch &bt)
+{
+    const int N = c->pb.N, thr = std::min(256, (N + 31) / 32 * 32);
+    prof_begin(c);
+    rows_expand_batch_kernel<<<dim3(N, N, bt.nflows), thr, 0, c->stream>>>(bt, c->d_rowmap, c->n_rrep, N,
+                                                                           c->pb.n_shell, c->pb.channels);
+    prof_end(c, K_ROWS_EXPAND);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "rows_expand_batch_kernel");
 }
 
 qpfrg_status launch_contractions(qpfrg_ctx *c, const void *d_Vin, double scale, double *d_out)

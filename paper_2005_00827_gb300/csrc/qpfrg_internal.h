@@ -347,7 +347,7 @@ qpfrg_status upload_geometry(qpfrg_ctx *c);
 qpfrg_status launch_bubbles(qpfrg_ctx *c, double lambda, const double *d_Z, bool z_symmetric,
                             const double *d_K = nullptr, bool state_symmetric = false);
 
-qpfrg_status launch_loop_rows(qpfrg_ctx *c, double lambda, float *rows, const int *active);
+qpfrg_status launch_loop_rows(qpfrg_ctx *c, double lambda, float *rows, const int *active, bool compact = false);
 
 // symmetry.cu: C4v orbits of the loop-kernel rows and the reduced launch's tasks
 qpfrg_status build_loop_orbits(qpfrg_ctx *c);
@@ -399,11 +399,15 @@ struct TcBatch {
     float *const *rows;               // table per slot
     const float *const *Vf, *const *VT;
     double *const *out;
+    double *const *outc;              // per flow: [ch][representative][n] rows (row orbits), nullptr: every row
     const CUtensorMap *maps;          // [flow][ch][hi, lo]
     const CUtensorMap *tab_maps;      // table map per slot
 };
 
 qpfrg_status launch_tc_fused_batch(qpfrg_ctx *c, int ch, const TcBatch &bt, double sign);
+// contract.cu: out_f += the expansion of the representative rows outc_f of
+// every running flow f with a step at this row of the schedule
+qpfrg_status launch_rows_expand_batch(qpfrg_ctx *c, const TcBatch &bt);
 
 // batch.cu: batched temperature flows (qpfrg_flow_batch)
 bool batch_device_path(const qpfrg_fine_grid *grid, qpfrg_regulator regulator, const qpfrg_options &opt, int n,

@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         mtab = Bt.tab_maps + Bt.slot_tab[sf];
         Vf = Bt.Vf[f];
         VT = Bt.VT[f];
-        out = Bt.out[f];
+        out = Bt.outc ? Bt.outc[f] + (long)A.ch * A.M * A.N : Bt.out[f];
         scale *= exp(Bt.x[f] + Bt.cst * h);      // dV/d ln T = T dV/dT at the stage temperature
         mhi = Bt.maps + 6L * f + 2 * A.ch;
         mlo = mhi + 1;
@@ -546,6 +546,7 @@ qpfrg_status launch_tc_fused_batch(qpfrg_ctx *c, int ch, const TcBatch &bt, doub
     TcFusedArgs A{};
     A.scale = sign;
     A.batch = bt;
+    A.rows = bt.outc ? c->d_rrep : nullptr;
     return launch_fused(c, ch, A, bt.nflows, K_TC_PP + ch);
 }
 

@@ -75,9 +75,8 @@ def test_batch_device_path_config4_shapes_match_single_flows():
     FP32 partial sums add in another order: step counts and statuses agree
     exactly, Lambda_c to 1e-5 and max|V| at the last step (past |V| = 20,
     where the flow amplifies rounding) to the tensor-core tolerance 1e-4.
-    The batched path contracts every row, so the single flows do too
-    (no_loop_symmetry = 2: loop-kernel orbits, no row orbits); the row
-    orbits' own sums are checked against the oracle elsewhere."""
+    Both sides take the row orbits of the contraction (every flow's state
+    stays C4v symmetric)."""
     import torch
     n = 16
     specs = [(d["N"], d["U"], 1.0, d["T_end"]) for d in inputs.batch_specs(16)]
@@ -90,7 +89,7 @@ def test_batch_device_path_config4_shapes_match_single_flows():
     statuses = set()
     for (N, U, T0, Tend), r in zip(specs, res):
         with api.Context(N, n, n, U=U, lambda0=T0, precision=api.QPFRG_MIXED_TC, lambda_end=Tend,
-                         stream=stream, no_loop_symmetry=2) as c:
+                         stream=stream) as c:
             single = api.qpfrg_flow(c.h).as_dict()
         assert r["status"] == single["status"] and r["steps"] == single["steps"]
         assert r["lam"] == pytest.approx(single["lam"], rel=1e-12)
