@@ -229,20 +229,21 @@ __device__ __forceinline__ void row_add(float *slot, float v, float fscale)
     atomicAdd(reinterpret_cast<int *>(slot), __float2int_rn(v * fscale));
 }
 __device__ __forceinline__ void row_add(double *slot, double v, float) { atomicAdd(slot, v); }
-// the same add, predicated: the FP32 path issues it as one predicated shared
-// reduction (no branch around it), the FP64 path branches
-__device__ __forceinline__ void row_add_if(float *slot, float v, float fscale, bool p)
+// the run's flush when the partner patch b differs from the run's patch rb:
+// the FP32 path issues it as one shared reduction predicated on that test (no
+// branch around it), the FP64 path branches
+__device__ __forceinline__ void row_add_if(float *slot, float v, float fscale, int b, int rb)
 {
     const int iv = __float2int_rn(v * fscale);
     const unsigned addr = (unsigned)__cvta_generic_to_shared(slot);
     asm volatile(
-        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q red.shared.add.s32 [%0], %1;\n\t}" ::"r"(addr),
-        "r"(iv), "r"((int)p)
+        "{\n\t.reg .pred q;\n\tsetp.ne.s32 q, %2, %3;\n\t@q red.shared.add.s32 [%0], %1;\n\t}" ::"r"(addr),
+        "r"(iv), "r"(b), "r"(rb)
         : "memory");
 }
-__device__ __forceinline__ void row_add_if(double *slot, double v, float, bool p)
+__device__ __forceinline__ void row_add_if(double *slot, double v, float, int b, int rb)
 {
-    if (p) atomicAdd(slot, v);
+    if (b != rb) atomicAdd(slot, v);
 }
 __device__ __forceinline__ float row_get(const float *slot, float finv)
 {
@@ -476,12 +477,15 @@ __device__ __forceinline__ void bubble_body(const BubbleArgs<R> &A, unsigned cha
                     for (int kk = 0; kk < 2; ++kk) {
                         const int k = k0 + kk;
                         if (!FULL && r + k >= nrow) continue;
+                        // every transfer slot of the warp updates its run: a slot
+                        // past nq (the warp's last pass only) repeats transfer 0
+                        // into its own row, which is never written out and is
+                        // cleared when the CTA starts
 #pragma unroll
                         for (int h = 0; h < H; ++h) {
-                            if (h >= nq) break;
                             const int b = bb[h][k];
                             const bool change = b != run_b[h];
-                            row_add_if(&rows[(H * warp + h) * RS + run_b[h]], run_v[h], A.fscale, change);
+                            row_add_if(&rows[(H * warp + h) * RS + run_b[h]], run_v[h], A.fscale, b, run_b[h]);
                             run_v[h] = (change ? R(0) : run_v[h]) + vv[kk][h];
                             run_b[h] = b;
                         }

@@ -216,21 +216,21 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         // only they read them, after the warp's barrier
         float *fs = reinterpret_cast<float *>(sbase + (size_t)S * stage_bytes) + (size_t)rr * (STG ? A.fw : 0);
         if (STG) {
-            // eight loads in flight per thread (a dependent one-by-one copy cost
-            // a DRAM round trip per value)
+            // 24 loads in flight per thread (a dependent one-by-one copy cost
+            // a DRAM round trip per value; the cr rows are N values long)
             for (int g = 0; g < 2; ++g) {
                 const float *src = (g ? frow1 + seg_lo[1] : frow0 + seg_lo[0]);
                 float *dst = fs + (g ? seg_n[0] : 0);
                 const int n = seg_n[g];
-                for (int t0 = hh; t0 < n; t0 += 16) {
-                    float tmp[8];
+                for (int t0 = hh; t0 < n; t0 += 48) {
+                    float tmp[24];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
+                    for (int u = 0; u < 24; ++u) {
                         const int t = t0 + 2 * u;
                         tmp[u] = (valid && t < n) ? __ldg(src + t) : 0.f;
                     }
 #pragma unroll
-                    for (int u = 0; u < 8; ++u)
+                    for (int u = 0; u < 24; ++u)
                         if (t0 + 2 * u < n) dst[t0 + 2 * u] = tmp[u];
                 }
             }
