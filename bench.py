@@ -54,10 +54,10 @@ BUBBLE_FP32_PER_EVAL, BUBBLE_MUFU_PER_EVAL = 14, 2
 SIGMA_FP32_PER_PAIR, SIGMA_MUFU_PER_PAIR = 20, 4
 # issue slots per unit as built: the self-energy's per-pair formula (a packed
 # FP32x2 instruction counts one half per pair); the loop kernels' measured
-# instructions per computed evaluation, the write-out of the C4v image rows
-# included (ncu smsp__inst_executed x 32 / evaluations at np96_n32:
-# 5.71e8 x 32 / 2.27e8)
-BUBBLE_ISSUE_AS_BUILT, SIGMA_ISSUE_AS_BUILT = 80, 36
+# instructions per computed evaluation on the representative rows of the row
+# orbits (ncu smsp__inst_executed x 32 / evaluations at np96_n32:
+# 3.49e8 x 32 / 2.27e8)
+BUBBLE_ISSUE_AS_BUILT, SIGMA_ISSUE_AS_BUILT = 49, 36
 # the self-energy pair with its patch read from the patch-of-r table: measured
 # instructions per pair (ncu smsp__inst_executed x 32 / pairs at np48_n16:
 # 7.03e8 x 32 / 9.06e8)
