@@ -47,11 +47,13 @@ UNIT = "RHS/s"
 # loop-kernel evaluation: ~14 FP32 operations (partner dispersion by angle
 # addition, the loop kernel, weight and deposit) + 1 ex2 + 1 reciprocal; per
 # self-energy pair: ~20 FP32 operations + 1 ex2 + 1 reciprocal (Fermi factor
-# of r) + 2 complex reciprocals (the two chord frequencies), counted as 4 MUFU.
-# The time bound is the slowest pipe: FP32 and MUFU operations share the
-# 128 issue lanes per SM per clock, MUFU alone runs 16 per SM per clock.
-BUBBLE_FP32_PER_EVAL, BUBBLE_MUFU_PER_EVAL = 14, 2
-SIGMA_FP32_PER_PAIR, SIGMA_MUFU_PER_PAIR = 20, 4
+# of r) + 2 complex reciprocals (the two chord frequencies, one reciprocal
+# each).  The time bound is the slowest pipe: every operation takes one of the
+# 128 issue lanes per SM per clock, and the MUFU pipe runs ex2 and rcp at their
+# own rates, measured on the device by qpfrg_alu_rates (GB300: ex2 32, rcp 16
+# per SM per clock; nominal 16 each where the probe is unavailable).
+BUBBLE_FP32_PER_EVAL, BUBBLE_EX2_PER_EVAL, BUBBLE_RCP_PER_EVAL = 14, 1, 1
+SIGMA_FP32_PER_PAIR, SIGMA_EX2_PER_PAIR, SIGMA_RCP_PER_PAIR = 20, 1, 3
 # issue slots per unit as built: the self-energy's per-pair formula (a packed
 # FP32x2 instruction counts one half per pair); the loop kernels' measured
 # instructions per computed evaluation on the representative rows of the row
@@ -62,12 +64,23 @@ BUBBLE_ISSUE_AS_BUILT, SIGMA_ISSUE_AS_BUILT = 49, 36
 # instructions per pair (ncu smsp__inst_executed x 32 / pairs at np48_n16:
 # 7.03e8 x 32 / 9.06e8)
 SIGMA_ISSUE_AS_BUILT_TABLE = 24.8
-ISSUE_LANES_PER_SM, MUFU_PER_SM, N_SM = 128, 16, 152
+ISSUE_LANES_PER_SM, NOMINAL_MUFU_PER_SM, N_SM = 128, 16, 152
 
 
-def alu_clk_per_unit(fp32, mufu):
-    """SM clocks per unit of work at the slowest pipe (issue lanes or MUFU)."""
-    return max((fp32 + mufu) / ISSUE_LANES_PER_SM, mufu / MUFU_PER_SM)
+def alu_clk_per_unit(fp32, ex2, rcp, rates):
+    """SM clocks per unit of work at the slowest pipe: the issue lanes, or the
+    MUFU pipe at its ex2 and rcp rates (results per SM per clock)."""
+    return max((fp32 + ex2 + rcp) / ISSUE_LANES_PER_SM, ex2 / rates["ex2"] + rcp / rates["rcp"])
+
+
+def alu_rates(api):
+    """MUFU rates of this device (qpfrg_alu_rates), else the nominal ones."""
+    try:
+        r = api.qpfrg_alu_rates()
+        return {"ex2": r["ex2"], "rcp": r["rcp"], "ffma": r["ffma"], "source": "measured (qpfrg_alu_rates)"}
+    except Exception as e:   # noqa: BLE001 - the figure is informative only
+        return {"ex2": NOMINAL_MUFU_PER_SM, "rcp": NOMINAL_MUFU_PER_SM, "ffma": ISSUE_LANES_PER_SM,
+                "source": f"nominal ({e})"}
 
 
 def sigma_units(N, n):
@@ -347,19 +360,22 @@ def run_qpfrg(args):
     kern = {k: v for k, v in prof.items() if v[1] > 0}
     dom = max(kern, key=lambda k: kern[k][0])
     M = N * n * n
-    peak_note = (f"derived, not measured: {N_SM} SM x {clk_mhz:.0f} MHz ({peak_kind} sm_max_mhz) x nominal "
-                 f"{ISSUE_LANES_PER_SM} FP32 issue lanes and {MUFU_PER_SM} MUFU per SM per clock "
-                 "(MEASURED_PEAKS.json holds no FP32 or MUFU figure)")
+    rates = alu_rates(api)
+    peak_note = (f"derived: {N_SM} SM x {clk_mhz:.0f} MHz ({peak_kind} sm_max_mhz) x the slower of "
+                 f"{ISSUE_LANES_PER_SM} issue lanes per SM per clock (nominal) and the MUFU pipe at "
+                 f"ex2 {rates['ex2']:.1f}, rcp {rates['rcp']:.1f} per SM per clock ({rates['source']}; "
+                 "MEASURED_PEAKS.json holds no FP32 or MUFU figure)")
     roof = None
     if dom in ("bubble", "sigma_z"):
         if dom == "bubble":
             units = bubble_units(N, M, work["loop_evals"])
-            fp32, mufu, built = BUBBLE_FP32_PER_EVAL, BUBBLE_MUFU_PER_EVAL, BUBBLE_ISSUE_AS_BUILT
+            fp32, ex2, rcp = BUBBLE_FP32_PER_EVAL, BUBBLE_EX2_PER_EVAL, BUBBLE_RCP_PER_EVAL
+            built = BUBBLE_ISSUE_AS_BUILT
         else:
             units = sigma_units(N, n)
-            fp32, mufu = SIGMA_FP32_PER_PAIR, SIGMA_MUFU_PER_PAIR
+            fp32, ex2, rcp = SIGMA_FP32_PER_PAIR, SIGMA_EX2_PER_PAIR, SIGMA_RCP_PER_PAIR
             built = SIGMA_ISSUE_AS_BUILT_TABLE if table_bytes else SIGMA_ISSUE_AS_BUILT
-        peak_units = N_SM * clk_mhz * 1e6 / alu_clk_per_unit(fp32, mufu)
+        peak_units = N_SM * clk_mhz * 1e6 / alu_clk_per_unit(fp32, ex2, rcp, rates)
         avg_s = kern[dom][0] / kern[dom][1] / 1e3
         achieved = units / avg_s
         built_peak = N_SM * clk_mhz * 1e6 * ISSUE_LANES_PER_SM / built
@@ -367,7 +383,8 @@ def run_qpfrg(args):
                 "unit": "Geval/s" if dom == "bubble" else "Gpair/s", "frac": achieved / peak_units,
                 "traffic": traffic_bytes(dom, args.workload), "traffic_unit": "bytes per launch",
                 "units_per_launch": units, "ms_per_launch": avg_s * 1e3,
-                "work_per_unit": f"{fp32} FP32 + {mufu} MUFU (algorithmic)",
+                "work_per_unit": f"{fp32} FP32 + {ex2} ex2 + {rcp} rcp (algorithmic)",
+                "alu_rates_per_sm_clk": {k: rates[k] for k in ("ex2", "rcp", "ffma")},
                 "peak_source": peak_note,
                 "issue_efficiency": {"issue_slots_as_built": built, "peak": built_peak / 1e9,
                                      "frac": achieved / built_peak}}
@@ -378,7 +395,8 @@ def run_qpfrg(args):
         evals = 2.0 * N * N * M
         red = bubble_units(N, M, work["loop_evals"])
         b_s = kern["bubble"][0] / kern["bubble"][1] / 1e3
-        b_peak = N_SM * clk_mhz * 1e6 / alu_clk_per_unit(BUBBLE_FP32_PER_EVAL, BUBBLE_MUFU_PER_EVAL)
+        b_peak = N_SM * clk_mhz * 1e6 / alu_clk_per_unit(BUBBLE_FP32_PER_EVAL, BUBBLE_EX2_PER_EVAL,
+                                                          BUBBLE_RCP_PER_EVAL, rates)
         rhs_roof["bubble"] = {"bound": "alu", "achieved": red / b_s / 1e9, "peak": b_peak / 1e9, "unit": "Geval/s",
                               "frac": red / b_s / b_peak, "evals_per_rhs": evals, "evals_computed": red,
                               "peak_source": peak_note}

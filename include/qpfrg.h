@@ -432,6 +432,16 @@ qpfrg_status qpfrg_zfactor_static(const qpfrg_lattice *lattice, int n_p, int n_f
                                   const double *d_V, const double *d_Z, double T, double eta,
                                   void *cuda_stream, double *d_Z_out);
 
+/* Measured ALU rates of the current device, for the rooflines of the
+ * ALU-bound kernels (no counterpart in the paper): results per SM per clock of
+ * ex2.approx.f32, rcp.approx.f32 and FP32 FMA, each from one launch of eight
+ * independent dependency chains per thread, 8 CTAs of 256 threads per SM,
+ * timed in SM clocks (clock64, the longest CTA), after one warm-up launch.
+ * Synchronous on the legacy default stream; allocates and frees two small
+ * device buffers.  Outputs may be NULL.  QPFRG_ERR_CUDA without a device,
+ * QPFRG_ERR_OOM when the buffers cannot be allocated. */
+qpfrg_status qpfrg_alu_rates(double *ex2_per_sm_clk, double *rcp_per_sm_clk, double *ffma_per_sm_clk);
+
 const char  *qpfrg_last_error(qpfrg_t ctx);   /* never NULL; ctx may be NULL */
 const char  *qpfrg_version(void);
 void         qpfrg_destroy(qpfrg_t ctx);      /* frees device memory; NULL is a no-op */

@@ -32,7 +32,7 @@ EXPORTS = (
     "qpfrg_geometry", "qpfrg_set_profiling", "qpfrg_profile_reset", "qpfrg_profile_count",
     "qpfrg_profile_name", "qpfrg_profile_get", "qpfrg_last_error", "qpfrg_version", "qpfrg_destroy",
     "qpfrg_zfactor_static", "qpfrg_flow_batch", "qpfrg_autotune", "qpfrg_set_tuning", "qpfrg_rhs_work",
-    "qpfrg_spectral", "qpfrg_read_sigma_flow", "qpfrg_sigma_table",
+    "qpfrg_spectral", "qpfrg_read_sigma_flow", "qpfrg_sigma_table", "qpfrg_alu_rates",
 )
 
 
@@ -129,6 +129,8 @@ def load(build_if_missing: bool = True):
     L.qpfrg_last_error.argtypes = [_P]
     L.qpfrg_last_error.restype = C.c_char_p
     L.qpfrg_version.restype = C.c_char_p
+    L.qpfrg_alu_rates.argtypes = [C.POINTER(C.c_double)] * 3
+    L.qpfrg_alu_rates.restype = C.c_int
     L.qpfrg_zfactor_static.argtypes = [C.POINTER(qpfrg_lattice), C.c_int, C.c_int, C.c_int, C.c_int, _P, _P,
                                        _P, _P, C.c_double, C.c_double, _P, _P]
     L.qpfrg_zfactor_static.restype = C.c_int
@@ -345,6 +347,16 @@ def qpfrg_last_error(ctx) -> str:
 
 def qpfrg_version() -> str:
     return load().qpfrg_version().decode()
+
+
+def qpfrg_alu_rates() -> dict:
+    """Measured ex2.approx, rcp.approx and FP32 FMA results per SM per clock
+    of the current device."""
+    e, r, f = C.c_double(), C.c_double(), C.c_double()
+    st = load().qpfrg_alu_rates(C.byref(e), C.byref(r), C.byref(f))
+    if st != 0:
+        raise QpfrgError(st, "qpfrg_alu_rates failed")
+    return dict(ex2=e.value, rcp=r.value, ffma=f.value)
 
 
 def qpfrg_destroy(ctx):

@@ -40,3 +40,15 @@ def test_recorded_traffic_matches_the_current_kernels():
         assert bench.kernel_text(path, t["kernel"]) is not None
         got = bench.traffic_bytes(kern, wl)
         assert got is None or got == t["bytes"]
+
+
+def test_alu_bound_takes_the_slower_pipe():
+    """Issue lanes against the MUFU pipe at its ex2 and rcp rates: the
+    self-energy pair (20 FP32 + 1 ex2 + 3 rcp) is MUFU bound at GB300's measured
+    rates (ex2 32, rcp 16 per SM per clock) and at the nominal 16 and 16; the
+    loop-kernel evaluation (14 + 1 + 1) is issue bound at both."""
+    measured, nominal = {"ex2": 32.0, "rcp": 16.0}, {"ex2": 16.0, "rcp": 16.0}
+    assert bench.alu_clk_per_unit(20, 1, 3, measured) == 1 / 32 + 3 / 16
+    assert bench.alu_clk_per_unit(20, 1, 3, nominal) == 4 / 16
+    assert bench.alu_clk_per_unit(14, 1, 1, measured) == 16 / 128
+    assert bench.alu_clk_per_unit(14, 1, 1, nominal) == 16 / 128
