@@ -567,12 +567,12 @@ def shell224(api, inputs, stream):
     res = {"workload": "np224_s7", "N_p": N, "shells": ns, "fine_grid": f"{n}x{n} per patch",
            "precision": "tc"}
     with api.Context(N, n, n, **kw) as c:
-        api.qpfrg_rhs(c.h, 0.1, V, Z, out)
+        api.qpfrg_rhs(c.h, args.lam, V, Z, out)
         api.qpfrg_selfenergy(c.h, 0.1, V, Z, None, None, zo)
         torch.cuda.synchronize()
         a.record(stream)
         for _ in range(3):
-            api.qpfrg_rhs(c.h, 0.1, V, Z, out)
+            api.qpfrg_rhs(c.h, args.lam, V, Z, out)
         b.record(stream)
         torch.cuda.synchronize()
         res["rhs_per_s"] = 3 / (a.elapsed_time(b) / 1e3)
@@ -736,18 +736,18 @@ def run_rhs_only(args):
     tuning = None
     with api.Context(N, n, n, U=U, precision=prec, mode=mode, n_shell=ns, stream=stream.cuda_stream) as c:
         if args.tune:
-            tuning = api.qpfrg_autotune(c.h, 0.1)
+            tuning = api.qpfrg_autotune(c.h, args.lam)
         elif args.bubble_transfers:
             api.qpfrg_set_tuning(c.h, bubble_transfers=args.bubble_transfers)
         for _ in range(args.warmup):
-            api.qpfrg_rhs(c.h, 0.1, V, Z, out)
+            api.qpfrg_rhs(c.h, args.lam, V, Z, out)
         torch.cuda.synchronize()
         api.qpfrg_set_profiling(c.h, True)
         api.qpfrg_profile_reset(c.h)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         for _ in range(args.steps):
-            api.qpfrg_rhs(c.h, 0.1, V, Z, out)
+            api.qpfrg_rhs(c.h, args.lam, V, Z, out)
         b.record(stream)
         torch.cuda.synchronize()
         prof = api.qpfrg_profile(c.h)
@@ -763,7 +763,7 @@ def run_rhs_only(args):
             b.record(stream)
             torch.cuda.synchronize()
             sig_ms = a.elapsed_time(b)
-    print(json.dumps({"mode": "rhs_only", "workload": args.workload, "precision": args.rhs_only,
+    print(json.dumps({"mode": "rhs_only", "workload": args.workload, "precision": args.rhs_only, "T": args.lam,
                       "rhs_per_s": args.steps / (ms / 1e3), "ms_per_rhs": ms / args.steps,
                       "kernels_ms_per_rhs": {k: v[0] / args.steps for k, v in prof.items() if v[1] > 0},
                       "launches": {k: v[1] for k, v in prof.items() if v[1] > 0},
@@ -790,6 +790,7 @@ def main():
                    help="time right-hand sides of one context only (kernel captures); prints its own line")
     p.add_argument("--sigma", action="store_true", help="--rhs-only: also time one Z evaluation")
     p.add_argument("--tune", action="store_true", help="--rhs-only: qpfrg_autotune the context first")
+    p.add_argument("--lam", type=float, default=0.1, help="--rhs-only: temperature of the right-hand sides")
     p.add_argument("--bubble-transfers", type=int, default=0, choices=[0, 2, 4],
                    help="--rhs-only: transfers per warp pass of the loop kernels (0: built-in)")
     args = p.parse_args()

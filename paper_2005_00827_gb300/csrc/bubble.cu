@@ -650,19 +650,28 @@ static qpfrg_status launch_r(qpfrg_ctx *c, double lambda, const double *d_Z, con
     return e == cudaSuccess ? QPFRG_OK : cuda_fail(c, e, "bubble_kernel");
 }
 
+// Width of the near-degenerate window |x_p -+ x_q| < thr T (midpoint
+// derivative instead of the difference quotient).  The quotient loses about
+// eps / thr of relative accuracy to cancellation, the midpoint derivative is
+// off by about thr^2 / 24 (times the loop kernel's third derivative in units
+// of T); the two balance near thr = eps^(1/3): 1e-5 in FP64, 6e-3 in FP32
+// (eps of the FP32 loop kernel ~3e-7 with ex2.approx).
+constexpr double kThrF64 = 1e-5;
+constexpr float kThrF32 = 6e-3f;
+
 qpfrg_status launch_bubbles(qpfrg_ctx *c, double lambda, const double *d_Z, bool z_symmetric, const double *d_K,
                             bool state_symmetric)
 {
     c->rows_compact = false;
     if (c->opt.precision == QPFRG_FP64)
-        return launch_r<double>(c, lambda, d_Z, d_K, z_symmetric, c->f64, c->qpp64, c->qph64, 1e-5);
+        return launch_r<double>(c, lambda, d_Z, d_K, z_symmetric, c->f64, c->qpp64, c->qph64, kThrF64);
     if (c->opt.precision == QPFRG_MIXED_TC) {
         qpfrg_status s = launch_tc_prep(c);       // B operands and V^T of this stage
         if (s != QPFRG_OK) return s;
     }
     const bool compact = c->rows_ok && state_symmetric && c->opt.precision == QPFRG_MIXED_TC;
     const qpfrg_status s =
-        launch_r<float>(c, lambda, d_Z, d_K, z_symmetric, c->f32, c->qpp32, c->qph32, 2e-2f, compact);
+        launch_r<float>(c, lambda, d_Z, d_K, z_symmetric, c->f32, c->qpp32, c->qph32, kThrF32, compact);
     c->rows_compact = compact && s == QPFRG_OK;
     return s;
 }
@@ -676,7 +685,7 @@ qpfrg_status launch_loop_rows(qpfrg_ctx *c, double lambda, float *rows, const in
     c->loop_out = rows;
     c->loop_active = active;
     const qpfrg_status s =
-        launch_r<float>(c, lambda, c->d_ones, nullptr, true, c->f32, c->qpp32, c->qph32, 2e-2f, compact && c->rows_ok);
+        launch_r<float>(c, lambda, c->d_ones, nullptr, true, c->f32, c->qpp32, c->qph32, kThrF32, compact && c->rows_ok);
     c->loop_out = nullptr;
     c->loop_active = nullptr;
     return s;
