@@ -52,3 +52,16 @@ def test_alu_bound_takes_the_slower_pipe():
     assert bench.alu_clk_per_unit(20, 1, 3, nominal) == 4 / 16
     assert bench.alu_clk_per_unit(14, 1, 1, measured) == 16 / 128
     assert bench.alu_clk_per_unit(14, 1, 1, nominal) == 16 / 128
+
+
+def test_bench_functions_bind_their_arguments():
+    """Every function of bench.py that reads `args` receives or binds it (the
+    default bench line runs helpers that take no command-line arguments)."""
+    import ast
+    tree = ast.parse(open(os.path.join(bench.ROOT, "bench.py")).read())
+    for fn in (n for n in ast.walk(tree) if isinstance(n, ast.FunctionDef)):
+        params = {a.arg for a in fn.args.args}
+        uses = any(isinstance(n, ast.Name) and n.id == "args" for n in ast.walk(fn))
+        bound = any(isinstance(t, ast.Name) and t.id == "args"
+                    for n in ast.walk(fn) if isinstance(n, ast.Assign) for t in n.targets)
+        assert not uses or "args" in params or bound, fn.name
