@@ -14,7 +14,10 @@
 // Launch shape: one CTA of 8 warps per (patch a, chunk of Q, family) -- or,
 // in wedge mode, per task of the C4v-reduced launch (symmetry.cu: one row per
 // orbit of (Q, a) under the point group, written to every image row with its
-// columns permuted).  The CTA stages its wedge's fine points in shared
+// columns permuted; or, for the tensor-core contraction of a C4v-symmetric
+// state, the representative transfer pairs of the row orbits with every patch
+// a, each row written once to the compact table).  The CTA stages its wedge's
+// fine points in shared
 // memory; each warp takes one transfer at a time, streams its partner-patch
 // bytes (coalesced) and bins the loop kernels into a private row of N
 // accumulators.  Output: the weighted tables B_f[Q][a][b] (FP64, or FP32 for

@@ -15,6 +15,12 @@
 // image).  Covariance is not assumed: check_covariance_kernel compares every
 // image row of the partner maps with its representative's row, byte by byte,
 // and a row that differs anywhere is evaluated by itself.
+//
+// When every row is covariant and V and Z are C4v symmetric, each channel's
+// output is invariant as well, dV_ch(g k1, g k2, g k3) = dV_ch(k1, k2, k3), so
+// the tensor-core contraction needs one output row per orbit of transfer pairs
+// Q only (build_row_orbits: representatives, and per pair Q its
+// representative and the g with Q = g rep); contract.cu expands the rows.
 #include <algorithm>
 #include <cstring>
 #include <vector>
