@@ -245,3 +245,56 @@ def test_interaction_flow_scales_with_g():
     Z = np.ones(lat.K)
     r1, r2 = o.rhs(1.0, V, Z), o.rhs(0.37, V, Z)
     assert normwise(r2, 0.37 * r1) < 1e-14
+
+
+@pytest.mark.parametrize("ch", [1, 2, 4], ids=["pp", "cr", "d"])
+def test_each_channel_is_c4v_invariant(ch):
+    """The premise of the contraction's row orbits: for a C4v-symmetric V and
+    Z every channel's contribution is invariant by itself."""
+    N, n = 16, 4
+    V = inputs.random_vertex(N, 2.0, seed=5, c4v=True)
+    Z = inputs.z_profile(N, "aniso")
+    dV = Oracle(N, n, n, channels=ch).rhs(0.2, V, Z)
+    assert np.abs(dV).max() > 0
+    for g in inputs.c4v_patch_maps(N):
+        assert normwise(dV[np.ix_(g, g, g)], dV) < 1e-12
+
+
+def test_row_orbit_expansion_rebuilds_every_channel():
+    """The row-orbit expansion restated on the oracle's channels: a channel
+    GEMM row is a transfer pair Q = (x, y), its column n (pp: row (k1, k2),
+    column k3; cr: row (k3, k2), column k1; d: row (k1, k3), column k2); keeping
+    only the representative rows (the image of Q with the smallest index) and
+    reading row Q = g rep at column g^-1 n reproduces the whole channel."""
+    N, n = 16, 4
+    V = inputs.random_vertex(N, 2.0, seed=6, c4v=True)
+    Z = inputs.z_profile(N, "aniso")
+    maps = inputs.c4v_patch_maps(N)
+    # representative of every pair and the element g with Q = g(rep)
+    rep, gof = {}, {}
+    for x in range(N):
+        for y in range(N):
+            imgs = [(int(g[x]) * N + int(g[y]), k) for k, g in enumerate(maps)]
+            best, k = min(imgs)
+            rep[(x, y)] = divmod(best, N)
+            gof[(x, y)] = k          # maps[k] sends (x, y) to its representative
+    reps = sorted(set(rep.values()))
+    assert len(reps) == (N * N + 16) // 8          # Burnside: 256 pairs, 16 fixed by the mirrors
+    for ch, row_col in ((1, lambda k1, k2, k3: ((k1, k2), k3)), (2, lambda k1, k2, k3: ((k3, k2), k1)),
+                        (4, lambda k1, k2, k3: ((k1, k3), k2))):
+        full = Oracle(N, n, n, channels=ch).rhs(0.2, V, Z)
+        # the channel's GEMM output rows out[(x, y)][col] = full at the triple they fill
+        out = {}
+        for k1 in range(N):
+            for k2 in range(N):
+                for k3 in range(N):
+                    q, col = row_col(k1, k2, k3)
+                    out.setdefault(q, np.zeros(N))[col] = full[k1, k2, k3]
+        rebuilt = np.empty_like(full)
+        for k1 in range(N):
+            for k2 in range(N):
+                for k3 in range(N):
+                    q, col = row_col(k1, k2, k3)
+                    g = maps[gof[q]]                  # rep = g(q), so q = g^-1(rep), col -> g(col)
+                    rebuilt[k1, k2, k3] = out[rep[q]][int(g[col])]
+        assert normwise(rebuilt, full) < 1e-12
