@@ -187,7 +187,12 @@ qpfrg_status qpfrg_create(const qpfrg_lattice *lattice, int n_p, const qpfrg_fin
  * dL/dT (T-flow) or g Z_a Z_b (Z_a + Z_b) L (g-flow).
  * d_V: N^3 FP64 input, d_Z: N FP64 input (NULL = all ones), d_dV: N^3 FP64
  * output (may not alias d_V).  lambda = T (T-flow, > 0) or g (g-flow).
- * Uses the context's precision.  The context's flow state is not changed. */
+ * Uses the context's precision.  The context's flow state is not changed.
+ * With QPFRG_MIXED_TC and the contraction's row orbits available (see
+ * qpfrg_rhs_work) the call first tests V and Z for C4v symmetry on the device
+ * (1e-12 of max|V|, max|Z|) and waits for that test on the context's stream:
+ * a symmetric input contracts one row per orbit of transfer pairs, any other
+ * every row.  Otherwise the work is only enqueued. */
 qpfrg_status qpfrg_rhs(qpfrg_t ctx, double lambda, const double *d_V, const double *d_Z,
                        double *d_dV);
 
