@@ -58,8 +58,8 @@ SIGMA_FP32_PER_PAIR, SIGMA_EX2_PER_PAIR, SIGMA_RCP_PER_PAIR = 20, 1, 3
 # FP32x2 instruction counts one half per pair); the loop kernels' measured
 # instructions per computed evaluation on the representative rows of the row
 # orbits (ncu smsp__inst_executed x 32 / evaluations at np96_n32:
-# 3.49e8 x 32 / 2.27e8)
-BUBBLE_ISSUE_AS_BUILT, SIGMA_ISSUE_AS_BUILT = 49, 36
+# 3.29e8 x 32 / 2.27e8)
+BUBBLE_ISSUE_AS_BUILT, SIGMA_ISSUE_AS_BUILT = 46.4, 36
 # the self-energy pair with its patch read from the patch-of-r table: measured
 # instructions per pair (ncu smsp__inst_executed x 32 / pairs at np48_n16:
 # 7.03e8 x 32 / 9.06e8)
