@@ -65,11 +65,14 @@ def test_sigma_ode_flow_matches_oracle(var, prec):
         assert np.abs(got - want).max() < 1e-4 * np.abs(want).max()
 
 
-@pytest.mark.parametrize("prec,rel", [(api.QPFRG_FP64, 1e-9), (api.QPFRG_MIXED, 5e-3)], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("prec,rel", [(api.QPFRG_FP64, 1e-9), (api.QPFRG_MIXED, 5e-3), (api.QPFRG_MIXED_TC, 5e-3)],
+                         ids=["fp64", "mixed", "tc"])
 def test_sigma_ode_divergence_with_katanin(prec, rel):
     """Flow to strong coupling (max|V| > 20) with Z feedback and the Katanin
     factor, N = 16, T = 0.1: the divergence scale g_c (U* = g_c^2 U, Sec.
-    3.2) against the oracle, and above the one of the flow without feedback."""
+    3.2) against the oracle, and above the one of the flow without feedback.
+    In tensor-core precision the symmetric state takes the contraction's row
+    orbits, with the Katanin factors in the loop-kernel weights."""
     N, n, U, dg = 16, 4, 2.0, 0.1
     o = Oracle(N, n, n, regulator=REG_INTERACTION, T_fixed=0.1, eta=ETA)
     ref = o.gflow(U, g_end=3.0, dg=dg, z_feedback=True, katanin=True)
